@@ -1,0 +1,186 @@
+"""Pins for oracle.amg / oracle.hashing: generator, strength, distance-2 MIS, aggregation,
+tentative and smoothed prolongators."""
+import os
+from collections import deque
+
+import numpy as np
+import pytest
+import scipy.sparse as sp
+
+import workloads as W
+from oracle import amg, fem, hashing, mg
+
+GOLD = os.path.join(os.path.dirname(__file__), "golden", "splitmix64.txt")
+
+
+def test_splitmix64_published_outputs():
+    for line in open(GOLD):
+        if line.startswith("#") or not line.strip():
+            continue
+        k, hexv = line.split()
+        ctr = (int(k) * hashing.GOLDEN) % (1 << 64)
+        assert int(hashing.splitmix64(np.uint64(ctr))) == int(hexv, 16)
+
+
+@pytest.mark.parametrize("ratio,strong", [(2.0, True), (10.0, False), (1e9, False)])
+def test_strength_soft_layer(ratio, strong):
+    """Nodes across a one-element-wide layer softer by ``ratio`` than its surroundings are
+    disconnected once the jump is about an order of magnitude (Eq. 10 with beta = 0.003)."""
+    nx, ny = 6, 6
+    E = np.full((ny, nx), ratio)
+    E[:, 2] = 1.0
+    K = fem.assemble(2, nx, ny, 1, E.ravel(), fem.element_stiffness(2, 0.3))
+    S = amg.strength(K, 2, 0.003)
+    i, j = W.node_id(nx, ny, 2, 3), W.node_id(nx, ny, 3, 3)
+    assert bool(S[i, j]) == strong and bool(S[j, i]) == strong
+
+
+def test_strength_uniform_all_strong():
+    nx, ny = 4, 3
+    K = fem.assemble(2, nx, ny, 1, np.ones(nx * ny), fem.element_stiffness(2, 0.3))
+    S = amg.strength(K, 2, 0.003)
+    # every node is strongly connected to all of its 8 (or fewer) grid neighbours
+    nn = (nx + 1) * (ny + 1)
+    deg = np.diff(S.indptr)
+    for n in range(nn):
+        i, j = n % (nx + 1), n // (nx + 1)
+        exp = sum(1 for di in (-1, 0, 1) for dj in (-1, 0, 1)
+                  if (di or dj) and 0 <= i + di <= nx and 0 <= j + dj <= ny)
+        assert deg[n] == exp
+
+
+def _dist2_sets(S):
+    n = S.shape[0]
+    out = []
+    for s in range(n):
+        seen = {s: 0}
+        dq = deque([s])
+        while dq:
+            u = dq.popleft()
+            if seen[u] == 2:
+                continue
+            for v in S.indices[S.indptr[u]:S.indptr[u + 1]]:
+                if v not in seen:
+                    seen[v] = seen[u] + 1
+                    dq.append(v)
+        out.append(set(seen) - {s})
+    return out
+
+
+def _small_strength(seed):
+    p = W.random_problem(2, 10, 7, seed=seed, contrast="threshold")
+    A = fem.masked_operator(fem.stiffness(p), p.fixed)
+    return amg.strength(A, 2, 0.003)
+
+
+@pytest.mark.parametrize("seed", [0, 1, 2])
+def test_mis2_is_greedy_distance2_mis(seed):
+    """The synchronous rounds give the lexicographically-first distance-2 MIS in descending
+    key order (brute-force greedy over BFS neighbourhoods)."""
+    S = _small_strength(seed)
+    roots, keys, isolated = amg.mis2(S, level=0)
+    N2 = _dist2_sets(S)
+    greedy = np.zeros(S.shape[0], bool)
+    for v in np.argsort(-keys.astype(np.float64), kind="stable"):
+        if isolated[v]:
+            continue
+        if not any(greedy[u] for u in N2[v]):
+            greedy[v] = True
+    assert np.array_equal(roots, greedy)
+    # independence at distance 2 and maximality
+    for v in np.flatnonzero(roots):
+        assert not any(roots[u] for u in N2[v])
+    for v in np.flatnonzero(~roots & ~isolated):
+        assert any(roots[u] for u in N2[v])
+
+
+@pytest.mark.parametrize("seed", [0, 3])
+def test_aggregates_valid(seed):
+    S = _small_strength(seed)
+    agg, n_agg = amg.aggregate(S, level=0)
+    roots, keys, isolated = amg.mis2(S, 0)
+    assert np.all((agg >= 0) == ~isolated)
+    assert n_agg == roots.sum()
+    # aggregate ids ordered by root index; each aggregate connected in S and has one root
+    assert np.array_equal(agg[np.flatnonzero(roots)], np.arange(n_agg))
+    for a in range(n_agg):
+        nodes = set(np.flatnonzero(agg == a))
+        start = next(iter(nodes))
+        seen = {start}
+        dq = deque([start])
+        while dq:
+            u = dq.popleft()
+            for v in S.indices[S.indptr[u]:S.indptr[u + 1]]:
+                if v in nodes and v not in seen:
+                    seen.add(v)
+                    dq.append(v)
+        assert seen == nodes
+        assert sum(roots[list(nodes)]) == 1
+
+
+def test_no_aggregate_spans_solid_void():
+    p = W.random_problem(2, 24, 12, seed=5, contrast="threshold")
+    A = fem.masked_operator(fem.stiffness(p), p.fixed)
+    S = amg.strength(A, 2, 0.003)
+    agg, n_agg = amg.aggregate(S, 0)
+    nx, ny = p.nx, p.ny
+    rho = p.rho.reshape(ny, nx)
+    kind = np.zeros((ny + 1, nx + 1), int)  # 1 = all adjacent elements solid, 2 = all void
+    for j in range(ny + 1):
+        for i in range(nx + 1):
+            r = rho[max(j - 1, 0):j + 1, max(i - 1, 0):i + 1]
+            kind[j, i] = 1 if r.min() == 1 else (2 if r.max() == 0 else 0)
+    kind = kind.ravel()
+    for a in range(n_agg):
+        ks = set(kind[agg == a])
+        assert not ({1, 2} <= ks)
+
+
+def test_mgs_qr():
+    rng = np.random.default_rng(1)
+    B = rng.standard_normal((9, 3))
+    Q, R = amg.mgs_qr(B)
+    assert np.allclose(Q.T @ Q, np.eye(3), atol=1e-14)
+    assert np.allclose(Q @ R, B, atol=1e-14)
+    assert np.all(np.diag(R) > 0) and np.allclose(np.tril(R, -1), 0)
+    # rank deficient: third column = first + second
+    B[:, 2] = B[:, 0] + B[:, 1]
+    Q, R = amg.mgs_qr(B)
+    assert np.all(Q[:, 2] == 0) and R[2, 2] == 0
+    assert np.allclose(Q @ R, B, atol=1e-13)
+
+
+@pytest.mark.parametrize("dim,grid", [(2, (12, 8, 1)), (3, (5, 4, 4))])
+def test_tentative_and_smoothed_prolongator(dim, grid):
+    p = W.random_problem(dim, *grid, seed=6, contrast="minmax")
+    A = fem.masked_operator(fem.stiffness(p), p.fixed)
+    B = fem.rigid_body_modes(dim, fem.node_coords(dim, p.nx, p.ny, p.nz))
+    lev = amg.sa_level(A, B, dim, 0)
+    T, Bc, P, agg = lev["T"], lev["Bc"], lev["P"], lev["agg"]
+    Td = T.toarray()
+    live = np.abs(Td).sum(axis=0) > 0
+    G = Td.T @ Td
+    assert np.allclose(G[np.ix_(live, live)], np.eye(live.sum()), atol=1e-13)
+    aggregated = np.repeat(agg >= 0, dim)
+    assert np.allclose((Td @ Bc)[aggregated], B[aggregated], atol=1e-10)
+    assert np.allclose((Td @ Bc)[~aggregated], 0)
+    # P B_c = B_agg - omega D^-1 A B_agg
+    Dinv = amg.block_diag_inv(A, dim)
+    Bag = B * aggregated[:, None]
+    rhs = Bag - lev["omega"] * np.stack([amg.apply_block_diag(Dinv, A @ Bag[:, c]) for c in range(B.shape[1])], 1)
+    assert np.allclose(P @ Bc, rhs, atol=1e-9 * np.abs(B).max())
+    Ac = lev["Ac"].toarray()
+    assert np.abs(Ac - Ac.T).max() <= 1e-12 * np.abs(Ac).max()
+    assert np.linalg.eigvalsh(Ac).min() > 0
+    # omega from the spectral radius: D^-1 A similar to an SPD matrix, rho within (0, 2*dim^2]
+    assert 0.0 < lev["omega"] < 4.0 / 3.0 / 1.0
+
+
+def test_spectral_radius_estimate():
+    p = W.random_problem(2, 8, 6, seed=7, contrast="minmax")
+    A = fem.masked_operator(fem.stiffness(p), p.fixed)
+    Dinv = amg.block_diag_inv(A, 2)
+    rho = amg.spectral_radius_DinvA(A, Dinv, 0)
+    ev = np.linalg.eigvals(amg.block_diag_matrix(Dinv).toarray() @ A.toarray())
+    true = np.abs(ev).max()
+    assert 0.8 * true <= rho <= true * (1 + 1e-12)

@@ -1,0 +1,126 @@
+"""Pins for oracle.mg (V-cycle, hierarchies) and oracle.krylov (PCG / FCG)."""
+import numpy as np
+import pytest
+import scipy.sparse as sp
+
+import workloads as W
+from oracle import fem, gmg, krylov, mg, solve
+
+
+def _hier(kind, p):
+    if kind == "gmg":
+        return solve.build(p, pc="gmg", n_levels=3)
+    if kind == "amg":
+        return solve.build(p, pc="amg", cap=60)
+    return solve.build(p, pc="hybrid", n_geo=2, cap=60)
+
+
+@pytest.mark.parametrize("kind", ["gmg", "amg", "hybrid"])
+def test_vcycle_symmetric_and_contracting(kind):
+    p = W.random_problem(2, 16, 8, seed=8, contrast="minmax")
+    H = _hier(kind, p)
+    A = H.A[0]
+    n = A.shape[0]
+    rng = np.random.default_rng(0)
+    x, y = rng.standard_normal(n), rng.standard_normal(n)
+    Mx, My = mg.vcycle(H, x), mg.vcycle(H, y)
+    assert abs(x @ My - y @ Mx) <= 1e-10 * abs(x @ My)
+    # M^-1 SPD on random vectors
+    assert x @ Mx > 0 and y @ My > 0
+    # error propagation I - M^-1 A contracts in the A-norm
+    e = rng.standard_normal(n)
+    e2 = e - mg.vcycle(H, A @ e)
+    assert np.sqrt(e2 @ (A @ e2)) < np.sqrt(e @ (A @ e))
+
+
+def test_one_level_is_exact():
+    p = W.random_problem(2, 6, 4, seed=9, contrast="minmax")
+    H = solve.build(p, pc="gmg", n_levels=1)
+    b = np.random.default_rng(1).standard_normal(p.n)
+    assert np.allclose(H.A[0] @ mg.vcycle(H, b), b, atol=1e-9 * np.abs(b).max())
+
+
+def test_vcycle_matches_algorithm1_by_hand():
+    """Two-level cycle written out with dense matrices: pre-smooth, restrict, exact coarse
+    solve, prolong, post-smooth."""
+    p = W.random_problem(2, 6, 4, seed=10, contrast="minmax")
+    H = solve.build(p, pc="gmg", n_levels=2)
+    A, P = H.A[0].toarray(), H.P[0].toarray()
+    Ac = P.T @ A @ P
+    n = A.shape[0]
+    Db = np.zeros_like(A)
+    for i in range(0, n, 2):
+        Db[i:i + 2, i:i + 2] = A[i:i + 2, i:i + 2]
+    Dinv = np.linalg.inv(Db)
+    b = np.random.default_rng(2).standard_normal(n)
+    x = 0.5 * Dinv @ b
+    x = x + P @ np.linalg.solve(Ac, P.T @ (b - A @ x))
+    x = x + 0.5 * Dinv @ (b - A @ x)
+    assert np.allclose(mg.vcycle(H, b), x, rtol=1e-10, atol=1e-12 * np.abs(x).max())
+
+
+def test_gmg_iterations_bounded_under_refinement():
+    """Uniform density: GMG-PCG iteration counts stay roughly constant as the grid is refined
+    (Sec. 3.2: multigrid convergence independent of the grid size)."""
+    its = []
+    for s in (1, 2, 4):
+        p = W.mbb_beam(24 * s, 8 * s)
+        r = solve.solve(p, pc="gmg", n_levels=2 + s // 2 + (s == 4))
+        its.append(int(r["iterations"][0]))
+    assert max(its) <= 2.0 * min(its) + 4
+
+
+@pytest.mark.parametrize("pc,kw", [("gmg", dict(n_levels=4)), ("amg", dict(cap=130)),
+                                  ("hybrid", dict(n_geo=2, cap=130))])
+def test_pcg_matches_direct_mbb(pc, kw):
+    p = W.mbb_beam(96, 32)
+    ref = solve.direct(p)
+    r = solve.solve(p, pc=pc, rtol=1e-10, **kw)
+    assert r["rel_residual"][0] <= 1e-10 * 1.01
+    err = np.linalg.norm(r["u"] - ref["u"]) / np.linalg.norm(ref["u"])
+    assert err < 1e-8
+    assert r["compliance"][0] == pytest.approx(ref["compliance"][0], rel=1e-9)
+
+
+def test_pcg_exact_in_n_steps_and_zero_rhs():
+    rng = np.random.default_rng(3)
+    Q = rng.standard_normal((12, 12))
+    A = Q @ Q.T + 12 * np.eye(12)
+    b = rng.standard_normal(12)
+    x, it, _ = krylov.pcg(A, b, rtol=1e-13, max_iter=100)
+    assert it <= 12 + 2
+    assert np.allclose(x, np.linalg.solve(A, b), rtol=1e-10)
+    x0, it0, _ = krylov.pcg(A, np.zeros(12))
+    assert it0 == 0 and np.all(x0 == 0)
+
+
+def test_fcg_equals_pcg_for_fixed_spd_preconditioner():
+    rng = np.random.default_rng(4)
+    Q = rng.standard_normal((30, 30))
+    A = Q @ Q.T + np.eye(30)
+    Minv = np.diag(1.0 / np.diag(A))
+    b = rng.standard_normal(30)
+    x1, i1, h1 = krylov.pcg(A, b, M=lambda r: Minv @ r, rtol=1e-10)
+    x2, i2, h2 = krylov.pcg(A, b, M=lambda r: Minv @ r, rtol=1e-10, flexible=True)
+    assert abs(i1 - i2) <= 2
+    assert np.allclose(h1[:20], h2[:20], rtol=1e-8)  # before the n-step finite-precision tail
+    assert np.allclose(x1, x2, rtol=1e-8)
+
+
+def test_warm_start_from_solution_takes_zero_iterations():
+    p = W.mbb_beam(24, 8)
+    ref = solve.direct(p)
+    r = solve.solve(p, pc="gmg", n_levels=2, x0=ref["u"])
+    assert r["iterations"][0] == 0
+
+
+@pytest.mark.parametrize("dim", [2, 3])
+def test_patch_test_through_pcg(dim):
+    p = W.patch_tension(dim, 8, 4, 4, sigma=1.0, E=1.0)
+    r = solve.solve(p, pc="gmg", n_levels=2, rtol=1e-12)
+    X = fem.node_coords(dim, p.nx, p.ny, p.nz)
+    ex = np.zeros_like(X)
+    ex[:, 0] = X[:, 0]
+    for c in range(1, dim):
+        ex[:, c] = -0.3 * X[:, c]
+    assert np.allclose(r["u"][0].reshape(-1, dim), ex, atol=1e-9)
