@@ -1,0 +1,168 @@
+/*
+ * tomg -- multigrid-preconditioned conjugate-gradient solve of the SIMP-penalised
+ * linear-elasticity system K(rho) u = f on structured quad4 (2D) / hex8 (3D) grids,
+ * for NVIDIA GB300 (sm_103a).  C ABI: plain pointers and sizes, no C++ or torch types.
+ *
+ * The calls follow the problem statement of Peetz & Elbanna, "On the use of multigrid
+ * preconditioners for topology optimization" (Sec. 2.1 Eq. 1-2, Sec. 3.1-3.2, Sec. 4):
+ *   grid dims, density rho, E0 / Emin / p / nu, loads f, fixed DOFs, tolerance and
+ *   preconditioner type in; displacements u, compliance f^T u and iteration count out.
+ *
+ * Conventions (the paper fixes none of them):
+ *   nodes    n = i + (nx+1) (j + (ny+1) k), x fastest; DOF = dim * n + c (interleaved)
+ *   elements e = i + nx (j + ny k); unit elements; local node a = (a&1, a>>1&1, a>>2&1)
+ *   vectors of several right-hand sides are column-major n x nrhs (RHS r at offset r*n)
+ *
+ * Errors: every call returns a tomg_status; nothing throws across the ABI.  On an error the
+ * message is available from tomg_last_error() (thread-local).  Pointers flagged "on_device"
+ * must be device pointers on the context's device, ordered with respect to the context's
+ * stream (the caller synchronises its own producers).  Inputs are copied; outputs are
+ * caller-owned.  Handles are not thread-safe: one thread per problem at a time.
+ */
+#ifndef TOMG_H
+#define TOMG_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct tomg_ctx tomg_ctx;
+typedef struct tomg_problem tomg_problem;
+
+typedef enum {
+  TOMG_OK = 0,
+  TOMG_NOT_CONVERGED = 1,   /* max_iter reached; u, iterations and residual still written   */
+  TOMG_E_INVALID = -1,      /* bad argument (size, index, NaN density, missing setup ...)   */
+  TOMG_E_OOM = -2,          /* device allocation failed                                      */
+  TOMG_E_CUDA = -3,         /* CUDA runtime error (message in tomg_last_error)               */
+  TOMG_E_BREAKDOWN = -4,    /* p^T A p <= 0, NaN, or a non-SPD coarse operator               */
+  TOMG_E_TIMEOUT = -5,      /* a bounded device wait expired                                  */
+  TOMG_E_BUDGET = -6        /* serving: request larger than the memory budget                */
+} tomg_status;
+
+/* Preconditioner hierarchy (Sec. 3.2; Sec. 4 for AMG and the hybrid of Sec. 4.3). */
+typedef enum {
+  TOMG_PC_GMG = 0,      /* geometric levels: bilinear/trilinear P, Galerkin P^T A P          */
+  TOMG_PC_AMG = 1,      /* smoothed aggregation from the fine operator, rigid-body modes      */
+  TOMG_PC_HYBRID = 2,   /* n_geo_levels geometric levels, smoothed aggregation below          */
+  TOMG_PC_JACOBI = 3    /* point-block Jacobi only (no hierarchy)                             */
+} tomg_pc;
+
+/* Arithmetic of the V-cycle; the outer Krylov loop, its residual and dots are always FP64. */
+typedef enum {
+  TOMG_PREC_FP64 = 0,         /* FP64 V-cycle inside FP64 PCG                                 */
+  TOMG_PREC_FP32_VCYCLE = 1   /* FP32 V-cycle inside FP64 flexible CG (Notay 2000)            */
+} tomg_prec;
+
+typedef struct {
+  int pc;              /* tomg_pc                                              default GMG  */
+  int prec;            /* tomg_prec                                            default FP64 */
+  double rtol;         /* stop when ||b - K u||_2 <= rtol ||b||_2 (true residual)  1e-8     */
+  int max_iter;        /* outer iterations                                         1000     */
+  int n_levels;        /* GMG levels incl. the fine grid; 0 = from max_coarse_dofs  0       */
+  int max_coarse_dofs; /* coarsest level has fewer DOFs than this                   2000    */
+  int n_geo_levels;    /* hybrid: geometric levels incl. the fine grid             3        */
+  int smoother;        /* 0 = weighted point-block Jacobi (Sec. 4.1)               0        */
+  double omega;        /* Jacobi weight (Sec. 4.1)                                 0.5      */
+  int n_pre, n_post;   /* smoothing sweeps (one each)                              1, 1     */
+  double soc_beta;     /* strength-of-connection threshold (Eq. 10)                0.003    */
+  int check_every;     /* outer iterations between host convergence polls          4        */
+  int use_graph;       /* capture the outer iteration in a CUDA graph              1        */
+  int max_levels;      /* cap on the number of levels                              25       */
+} tomg_options;
+
+typedef struct {
+  int iterations;        /* outer iterations (updates of u)                               */
+  double rel_residual;   /* true ||b - K u||_2 / ||b||_2 in FP64, b = f on free DOFs       */
+  double compliance;     /* f^T u (Eq. 1)                                                  */
+  double setup_ms;       /* hierarchy build of the last tomg_setup                         */
+  double solve_ms;       /* this right-hand side's solve, device time                      */
+  int status;            /* tomg_status of this right-hand side                            */
+} tomg_result;
+
+typedef struct {
+  int kind;              /* 0 matrix-free element operator, 1 structured 3^d stencil, 2 BSR */
+  int block;             /* DOFs per node on this level                                     */
+  int64_t n_nodes;       /* nodes (aggregates on AMG levels)                                */
+  int64_t n_dofs;        /* block * n_nodes                                                 */
+  int64_t nnzb;          /* stored blocks (stencil: 3^d per node incl. out-of-grid zeros)   */
+  int nx, ny, nz;        /* element counts on geometric levels, 0 on AMG levels             */
+  int geometric;         /* 1 if the transfer to the next level is geometric                */
+} tomg_level_info;
+
+/* ---- context ------------------------------------------------------------------------- */
+/* Create a context on CUDA device `device`.  `cuda_stream` (a cudaStream_t, may be NULL)
+ * is used for all work; NULL creates a private non-blocking stream. */
+tomg_status tomg_ctx_create(tomg_ctx** out, int device, void* cuda_stream);
+tomg_status tomg_ctx_destroy(tomg_ctx* ctx);
+const char* tomg_last_error(void);
+void tomg_options_default(tomg_options* opt);
+
+/* ---- problem (Sec. 2.1) -------------------------------------------------------------- */
+/* A structured grid problem.  dim = 2 (quad4, plane stress, nz ignored) or 3 (hex8).
+ * E(rho) = Emin + (E0 - Emin) rho^penal (Eq. 2); nu = Poisson ratio.
+ * E_INVALID for non-positive sizes, E0 <= 0, Emin < 0, nu outside (-1, 0.5). */
+tomg_status tomg_problem_create(tomg_ctx* ctx, int dim, int nx, int ny, int nz, double E0,
+                                double Emin, double penal, double nu, tomg_problem** out);
+tomg_status tomg_problem_destroy(tomg_problem* prob);
+/* Problem sizes: DOFs, nodes, elements (any pointer may be NULL). */
+tomg_status tomg_problem_sizes(const tomg_problem* prob, int64_t* n_dofs, int64_t* n_nodes,
+                               int64_t* n_elems);
+/* Fixed (zero-displacement) DOFs, `count` indices in [0, n_dofs), host array, copied.
+ * Duplicates are allowed.  E_INVALID on an index out of range.  Invalidates the setup. */
+tomg_status tomg_set_fixed_dofs(tomg_problem* prob, const int64_t* dofs, int64_t count);
+/* Element densities rho (n_elems doubles, host or device), copied.  E_INVALID if any value
+ * is negative or NaN (checked on the device for device input).  Marks the hierarchy stale. */
+tomg_status tomg_set_density(tomg_problem* prob, const double* rho, int on_device);
+
+/* ---- preconditioner setup (Sec. 3.2, Eq. 9; Sec. 4) ------------------------------------ */
+/* Builds (or refreshes) the hierarchy for the current density: SIMP moduli, Galerkin coarse
+ * operators, point-block smoother diagonals, AMG aggregation / prolongators, coarse dense
+ * Cholesky.  opt = NULL uses the defaults. */
+tomg_status tomg_setup(tomg_problem* prob, const tomg_options* opt);
+
+/* ---- solve (Sec. 3.1, Sec. 4) -------------------------------------------------------------
+ * Solves K(rho) u = f for `nrhs` right-hand sides (f and u column-major n x nrhs, host or
+ * device per on_device).  u is read as the initial guess (warm start; zeros for a cold
+ * start) and overwritten with the solution; fixed DOFs of u are returned as 0.  results has
+ * nrhs entries.  Returns the worst status over the right-hand sides. f = 0 gives u = 0 in 0
+ * iterations.  Requires a setup for the current density (E_INVALID otherwise). */
+tomg_status tomg_solve(tomg_problem* prob, int nrhs, const double* f, double* u, int on_device,
+                       tomg_result* results);
+
+/* ---- hierarchy introspection and single steps (parity checking) ------------------------- */
+tomg_status tomg_num_levels(const tomg_problem* prob, int* n_levels);
+tomg_status tomg_level_info_get(const tomg_problem* prob, int level, tomg_level_info* info);
+/* Level operator as block CSR (row_ptr n_nodes+1, col nnzb, val nnzb*block*block, row-major
+ * blocks), FP64, host arrays.  Call with NULL arrays to get nnzb only.  Stencil levels drop
+ * their out-of-grid blocks, so nnzb may be smaller than tomg_level_info.nnzb.  Level 0 is
+ * assembled on the fly from the matrix-free operator. */
+tomg_status tomg_level_export(tomg_problem* prob, int level, int64_t* nnzb, int64_t* row_ptr,
+                              int64_t* col, double* val);
+/* Prolongation P of level -> level+1 as block CSR (fine rows, coarse block columns, blocks
+ * block(level) x block(level+1)), host arrays; NULL arrays return nnzb only. */
+tomg_status tomg_prolongation_export(tomg_problem* prob, int level, int64_t* nnzb,
+                                     int64_t* row_ptr, int64_t* col, double* val);
+/* AMG levels: aggregate id of every node of `level` (-1 = unaggregated), host array. */
+tomg_status tomg_aggregates_export(tomg_problem* prob, int level, int64_t* agg);
+/* y = A_level x in the given tomg_prec (FP32 math for FP32_VCYCLE), double in/out. */
+tomg_status tomg_level_apply(tomg_problem* prob, int level, int prec, const double* x, double* y,
+                             int on_device);
+/* z = M r: one V-cycle of the current setup (its precision), double in/out. */
+tomg_status tomg_vcycle(tomg_problem* prob, const double* r, double* z, int on_device);
+/* Coarsest-level direct solve x = A_c^{-1} b (FP64), host or device arrays. */
+tomg_status tomg_coarse_solve(tomg_problem* prob, const double* b, double* x, int on_device);
+/* SIMP moduli E_e (Eq. 2) of the current density, n_elems doubles. */
+tomg_status tomg_moduli(tomg_problem* prob, double* E, int on_device);
+/* Element stiffness matrix of the problem for E = 1 (dim*2^dim squared, row-major). */
+tomg_status tomg_element_stiffness(const tomg_problem* prob, double* Ke);
+/* Number of kernels this library launched since the context was created. */
+tomg_status tomg_kernel_launches(const tomg_ctx* ctx, int64_t* count);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* TOMG_H */

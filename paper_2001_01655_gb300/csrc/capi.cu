@@ -1,0 +1,346 @@
+// C ABI of the tomg library (declared in include/tomg.h): argument checks, error capture and
+// host/device marshalling around the runtime in solver.cu.  No exception crosses the ABI.
+#include <cstdarg>
+#include <cstring>
+
+#include "solver.h"
+
+namespace tomg {
+
+int64_t g_launches = 0;
+static thread_local char g_err[1024] = "";
+
+void set_error(const char* fmt, ...) {
+  va_list ap;
+  va_start(ap, fmt);
+  vsnprintf(g_err, sizeof(g_err), fmt, ap);
+  va_end(ap);
+}
+const char* get_error() { return g_err; }
+
+int num_sms() {
+  static int sms = 0;
+  if (!sms) {
+    int dev = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    if (sms <= 0) sms = 1;
+  }
+  return sms;
+}
+
+namespace {
+
+template <class F>
+tomg_status guarded(F&& fn) {
+  try {
+    return fn();
+  } catch (const Error& e) {
+    return e.st;
+  } catch (const std::bad_alloc&) {
+    set_error("host allocation failed");
+    return TOMG_E_OOM;
+  } catch (...) {
+    set_error("unexpected internal error");
+    return TOMG_E_CUDA;
+  }
+}
+
+// device view of a caller array: the pointer itself (device) or a staged copy (host)
+struct DevArray {
+  DBuf<double> buf;
+  const double* p = nullptr;
+  DevArray(const double* src, int64_t n, int on_device, cudaStream_t s) {
+    if (on_device) { p = src; return; }
+    buf.resize(n > 0 ? n : 1);
+    if (n) CK(cudaMemcpyAsync(buf.p, src, n * 8, cudaMemcpyHostToDevice, s));
+    p = buf.p;
+  }
+};
+struct DevOut {
+  DBuf<double> buf;
+  double* p = nullptr;
+  double* dst;
+  int64_t n;
+  int on_device;
+  cudaStream_t s;
+  DevOut(double* d, int64_t count, int on_dev, cudaStream_t st) : dst(d), n(count), on_device(on_dev), s(st) {
+    if (on_device) { p = d; return; }
+    buf.resize(n > 0 ? n : 1);
+    p = buf.p;
+  }
+  void commit() {
+    if (!on_device && n) CK(cudaMemcpyAsync(dst, p, n * 8, cudaMemcpyDeviceToHost, s));
+    CK(cudaStreamSynchronize(s));
+  }
+};
+
+void set_device(const tomg_ctx* c) { CK(cudaSetDevice(c->device)); }
+
+}  // namespace
+}  // namespace tomg
+
+using namespace tomg;
+
+extern "C" {
+
+const char* tomg_last_error(void) { return get_error(); }
+
+void tomg_options_default(tomg_options* o) {
+  if (!o) return;
+  memset(o, 0, sizeof(*o));
+  o->pc = TOMG_PC_GMG;
+  o->prec = TOMG_PREC_FP64;
+  o->rtol = 1e-8;
+  o->max_iter = 1000;
+  o->n_levels = 0;
+  o->max_coarse_dofs = 2000;
+  o->n_geo_levels = 3;
+  o->smoother = 0;
+  o->omega = 0.5;
+  o->n_pre = 1;
+  o->n_post = 1;
+  o->soc_beta = 0.003;
+  o->check_every = 4;
+  o->use_graph = 2;
+  o->max_levels = 25;
+}
+
+tomg_status tomg_ctx_create(tomg_ctx** out, int device, void* cuda_stream) {
+  return guarded([&]() -> tomg_status {
+    if (!out) TOMG_THROW(TOMG_E_INVALID, "null output handle");
+    int ndev = 0;
+    CK(cudaGetDeviceCount(&ndev));
+    if (device < 0 || device >= ndev) TOMG_THROW(TOMG_E_INVALID, "device %d not present (%d devices)", device, ndev);
+    CK(cudaSetDevice(device));
+    auto* c = new tomg_ctx();
+    c->device = device;
+    if (cuda_stream) {
+      c->stream = (cudaStream_t)cuda_stream;
+    } else {
+      cudaError_t e = cudaStreamCreateWithFlags(&c->stream, cudaStreamNonBlocking);
+      if (e != cudaSuccess) { delete c; CK(e); }
+      c->own_stream = true;
+    }
+    c->launches0 = g_launches;
+    *out = c;
+    return TOMG_OK;
+  });
+}
+
+tomg_status tomg_ctx_destroy(tomg_ctx* c) {
+  return guarded([&]() -> tomg_status {
+    if (!c) return TOMG_OK;
+    if (c->own_stream && c->stream) cudaStreamDestroy(c->stream);
+    delete c;
+    return TOMG_OK;
+  });
+}
+
+tomg_status tomg_kernel_launches(const tomg_ctx* c, int64_t* count) {
+  if (!c || !count) { set_error("null argument"); return TOMG_E_INVALID; }
+  *count = g_launches - c->launches0;
+  return TOMG_OK;
+}
+
+tomg_status tomg_problem_create(tomg_ctx* c, int dim, int nx, int ny, int nz, double E0,
+                                double Emin, double penal, double nu, tomg_problem** out) {
+  return guarded([&]() -> tomg_status {
+    if (!c || !out) TOMG_THROW(TOMG_E_INVALID, "null argument");
+    if (dim != 2 && dim != 3) TOMG_THROW(TOMG_E_INVALID, "dim must be 2 or 3");
+    if (nx < 1 || ny < 1 || (dim == 3 && nz < 1)) TOMG_THROW(TOMG_E_INVALID, "grid sizes must be >= 1");
+    if (!(E0 > 0.0) || !(Emin >= 0.0) || !(penal >= 0.0) || !(nu > -1.0) || !(nu < 0.5))
+      TOMG_THROW(TOMG_E_INVALID, "invalid material constants");
+    const int64_t nn = (int64_t)(nx + 1) * (ny + 1) * (dim == 3 ? nz + 1 : 1);
+    if (nn * dim >= 0x7fffffffLL) TOMG_THROW(TOMG_E_INVALID, "grid too large");
+    set_device(c);
+    auto* P = new tomg_problem();
+    P->ctx = c;
+    P->dim = dim; P->nx = nx; P->ny = ny; P->nz = dim == 3 ? nz : 1;
+    P->E0 = E0; P->Emin = Emin; P->penal = penal; P->nu = nu;
+    P->nn = nn;
+    P->n = nn * dim;
+    P->nel = (int64_t)nx * ny * (dim == 3 ? nz : 1);
+    try {
+      problem_init(P);
+    } catch (...) {
+      delete P;
+      throw;
+    }
+    *out = P;
+    return TOMG_OK;
+  });
+}
+
+tomg_status tomg_problem_destroy(tomg_problem* P) {
+  return guarded([&]() -> tomg_status {
+    if (!P) return TOMG_OK;
+    set_device(P->ctx);
+    cudaStreamSynchronize(P->ctx->stream);
+    delete P;
+    return TOMG_OK;
+  });
+}
+
+tomg_status tomg_problem_sizes(const tomg_problem* P, int64_t* n, int64_t* nn, int64_t* nel) {
+  if (!P) { set_error("null problem"); return TOMG_E_INVALID; }
+  if (n) *n = P->n;
+  if (nn) *nn = P->nn;
+  if (nel) *nel = P->nel;
+  return TOMG_OK;
+}
+
+tomg_status tomg_set_fixed_dofs(tomg_problem* P, const int64_t* dofs, int64_t count) {
+  return guarded([&]() -> tomg_status {
+    if (!P) TOMG_THROW(TOMG_E_INVALID, "null problem");
+    set_device(P->ctx);
+    set_fixed(P, dofs, count);
+    return TOMG_OK;
+  });
+}
+
+tomg_status tomg_set_density(tomg_problem* P, const double* rho, int on_device) {
+  return guarded([&]() -> tomg_status {
+    if (!P) TOMG_THROW(TOMG_E_INVALID, "null problem");
+    set_device(P->ctx);
+    set_density(P, rho, on_device);
+    return TOMG_OK;
+  });
+}
+
+tomg_status tomg_setup(tomg_problem* P, const tomg_options* opt) {
+  return guarded([&]() -> tomg_status {
+    if (!P) TOMG_THROW(TOMG_E_INVALID, "null problem");
+    set_device(P->ctx);
+    tomg_options o;
+    if (opt) o = *opt;
+    else tomg_options_default(&o);
+    setup(P, o);
+    return TOMG_OK;
+  });
+}
+
+tomg_status tomg_solve(tomg_problem* P, int nrhs, const double* f, double* u, int on_device,
+                       tomg_result* results) {
+  return guarded([&]() -> tomg_status {
+    if (!P) TOMG_THROW(TOMG_E_INVALID, "null problem");
+    set_device(P->ctx);
+    return solve(P, nrhs, f, u, on_device, results);
+  });
+}
+
+tomg_status tomg_num_levels(const tomg_problem* P, int* n) {
+  if (!P || !n) { set_error("null argument"); return TOMG_E_INVALID; }
+  if (!P->setup_valid) { set_error("no valid setup"); return TOMG_E_INVALID; }
+  *n = (int)P->L.size();
+  return TOMG_OK;
+}
+
+tomg_status tomg_level_info_get(const tomg_problem* P, int level, tomg_level_info* info) {
+  if (!P || !info) { set_error("null argument"); return TOMG_E_INVALID; }
+  if (!P->setup_valid || level < 0 || level >= (int)P->L.size()) { set_error("bad level"); return TOMG_E_INVALID; }
+  const Level& L = *P->L[level];
+  info->kind = L.kind;
+  info->block = L.b;
+  info->n_nodes = L.nn;
+  info->n_dofs = L.n;
+  info->nnzb = L.kind == KIND_BSR ? L.nnzb : L.nn * (P->dim == 3 ? 27 : 9);
+  info->nx = L.geometric ? L.g.nx : 0;
+  info->ny = L.geometric ? L.g.ny : 0;
+  info->nz = L.geometric ? L.g.nz : 0;
+  info->geometric = L.geo_next ? 1 : 0;
+  return TOMG_OK;
+}
+
+tomg_status tomg_level_export(tomg_problem* P, int level, int64_t* nnzb, int64_t* rp, int64_t* ci,
+                              double* val) {
+  return guarded([&]() -> tomg_status {
+    if (!P || !nnzb) TOMG_THROW(TOMG_E_INVALID, "null argument");
+    set_device(P->ctx);
+    level_export(P, level, nnzb, rp, ci, val);
+    return TOMG_OK;
+  });
+}
+
+tomg_status tomg_prolongation_export(tomg_problem* P, int level, int64_t* nnzb, int64_t* rp,
+                                     int64_t* ci, double* val) {
+  return guarded([&]() -> tomg_status {
+    if (!P || !nnzb) TOMG_THROW(TOMG_E_INVALID, "null argument");
+    set_device(P->ctx);
+    prolong_export(P, level, nnzb, rp, ci, val);
+    return TOMG_OK;
+  });
+}
+
+tomg_status tomg_aggregates_export(tomg_problem* P, int level, int64_t* agg) {
+  return guarded([&]() -> tomg_status {
+    if (!P || !agg) TOMG_THROW(TOMG_E_INVALID, "null argument");
+    if (!P->setup_valid || level < 0 || level + 1 >= (int)P->L.size() || P->L[level]->geo_next)
+      TOMG_THROW(TOMG_E_INVALID, "level %d has no aggregation", level);
+    set_device(P->ctx);
+    const Level& L = *P->L[level];
+    std::vector<int> h(L.nn);
+    CK(cudaMemcpy(h.data(), L.agg.p, L.nn * sizeof(int), cudaMemcpyDeviceToHost));
+    for (int64_t i = 0; i < L.nn; i++) agg[i] = h[i];
+    return TOMG_OK;
+  });
+}
+
+tomg_status tomg_level_apply(tomg_problem* P, int level, int prec, const double* x, double* y,
+                             int on_device) {
+  return guarded([&]() -> tomg_status {
+    if (!P || !x || !y) TOMG_THROW(TOMG_E_INVALID, "null argument");
+    if (!P->setup_valid || level < 0 || level >= (int)P->L.size()) TOMG_THROW(TOMG_E_INVALID, "bad level");
+    set_device(P->ctx);
+    const int64_t n = P->L[level]->n;
+    DevArray xin(x, n, on_device, P->ctx->stream);
+    DevOut yout(y, n, on_device, P->ctx->stream);
+    level_apply(P, level, prec, xin.p, yout.p);
+    yout.commit();
+    return TOMG_OK;
+  });
+}
+
+tomg_status tomg_vcycle(tomg_problem* P, const double* r, double* z, int on_device) {
+  return guarded([&]() -> tomg_status {
+    if (!P || !r || !z) TOMG_THROW(TOMG_E_INVALID, "null argument");
+    set_device(P->ctx);
+    DevArray rin(r, P->n, on_device, P->ctx->stream);
+    DevOut zout(z, P->n, on_device, P->ctx->stream);
+    vcycle_apply(P, rin.p, zout.p);
+    zout.commit();
+    return TOMG_OK;
+  });
+}
+
+tomg_status tomg_coarse_solve(tomg_problem* P, const double* b, double* x, int on_device) {
+  return guarded([&]() -> tomg_status {
+    if (!P || !b || !x) TOMG_THROW(TOMG_E_INVALID, "null argument");
+    if (!P->setup_valid) TOMG_THROW(TOMG_E_INVALID, "no valid setup");
+    set_device(P->ctx);
+    DevArray bin(b, P->nc, on_device, P->ctx->stream);
+    DevOut xout(x, P->nc, on_device, P->ctx->stream);
+    coarse_apply(P, bin.p, xout.p);
+    xout.commit();
+    return TOMG_OK;
+  });
+}
+
+tomg_status tomg_moduli(tomg_problem* P, double* E, int on_device) {
+  return guarded([&]() -> tomg_status {
+    if (!P || !E) TOMG_THROW(TOMG_E_INVALID, "null argument");
+    if (!P->have_density) TOMG_THROW(TOMG_E_INVALID, "no density set");
+    set_device(P->ctx);
+    CK(cudaMemcpyAsync(E, P->E64.p, P->nel * 8, on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost, P->ctx->stream));
+    CK(cudaStreamSynchronize(P->ctx->stream));
+    return TOMG_OK;
+  });
+}
+
+tomg_status tomg_element_stiffness(const tomg_problem* P, double* Ke) {
+  if (!P || !Ke) { set_error("null argument"); return TOMG_E_INVALID; }
+  memcpy(Ke, P->Ke_host.data(), P->Ke_host.size() * sizeof(double));
+  return TOMG_OK;
+}
+
+}  // extern "C"

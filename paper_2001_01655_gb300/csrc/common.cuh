@@ -1,0 +1,183 @@
+// Shared definitions of the tomg CUDA library: error handling, device buffers, launch
+// accounting, kernel-side helpers.  Everything here is project code for sm_103a.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+#include <stdio.h>
+#include <string>
+#include <vector>
+
+#include "../../include/tomg.h"
+
+namespace tomg {
+
+// ---------------------------------------------------------------------------------------
+// errors
+void set_error(const char* fmt, ...);
+const char* get_error();
+
+struct Error {
+  tomg_status st;
+};
+
+#define TOMG_THROW(status, ...)          \
+  do {                                   \
+    ::tomg::set_error(__VA_ARGS__);      \
+    throw ::tomg::Error{status};         \
+  } while (0)
+
+#define CK(call)                                                                        \
+  do {                                                                                  \
+    cudaError_t e_ = (call);                                                            \
+    if (e_ != cudaSuccess) {                                                            \
+      if (e_ == cudaErrorMemoryAllocation)                                              \
+        TOMG_THROW(TOMG_E_OOM, "%s:%d %s: %s", __FILE__, __LINE__, #call,               \
+                   cudaGetErrorString(e_));                                             \
+      TOMG_THROW(TOMG_E_CUDA, "%s:%d %s: %s", __FILE__, __LINE__, #call,                \
+                 cudaGetErrorString(e_));                                               \
+    }                                                                                   \
+  } while (0)
+
+// count of kernels launched by this library (per process; contexts read deltas)
+extern int64_t g_launches;
+
+#define LAUNCH(kernel, grid, block, smem, stream, ...)                      \
+  do {                                                                     \
+    kernel<<<(grid), (block), (smem), (stream)>>>(__VA_ARGS__);            \
+    ::tomg::g_launches++;                                                  \
+    CK(cudaGetLastError());                                                \
+  } while (0)
+
+// ---------------------------------------------------------------------------------------
+// device buffers (owning, move-only)
+template <class T>
+struct DBuf {
+  T* p = nullptr;
+  size_t n = 0;
+  DBuf() = default;
+  DBuf(const DBuf&) = delete;
+  DBuf& operator=(const DBuf&) = delete;
+  DBuf(DBuf&& o) noexcept : p(o.p), n(o.n) { o.p = nullptr; o.n = 0; }
+  DBuf& operator=(DBuf&& o) noexcept {
+    if (this != &o) { release(); p = o.p; n = o.n; o.p = nullptr; o.n = 0; }
+    return *this;
+  }
+  ~DBuf() { release(); }
+  void release() {
+    if (p) cudaFree(p);
+    p = nullptr;
+    n = 0;
+  }
+  // (re)allocate to exactly `count` elements (keeps the buffer if already that size)
+  void resize(size_t count) {
+    if (count == n && p) return;
+    release();
+    if (count == 0) return;
+    CK(cudaMalloc((void**)&p, count * sizeof(T)));
+    n = count;
+  }
+  void zero(cudaStream_t s) {
+    if (n) CK(cudaMemsetAsync(p, 0, n * sizeof(T), s));
+  }
+  size_t bytes() const { return n * sizeof(T); }
+};
+
+inline int ceil_div(int64_t a, int64_t b) { return (int)((a + b - 1) / b); }
+
+// number of SMs of the current device (cached)
+int num_sms();
+
+// ---------------------------------------------------------------------------------------
+// kernel-side helpers
+template <class T>
+__device__ __forceinline__ T ldg(const T* p) { return __ldg(p); }
+
+// deterministic block reduction of one double per thread (fixed tree order);
+// result valid in thread 0.  blockDim.x must be a multiple of 32 and <= 1024.
+__device__ __forceinline__ double block_sum(double v, double* sh) {
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+  int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  if (lane == 0) sh[w] = v;
+  __syncthreads();
+  int nw = blockDim.x >> 5;
+  v = (threadIdx.x < nw) ? sh[threadIdx.x] : 0.0;
+  if (w == 0)
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+  __syncthreads();
+  return v;
+}
+
+// early-exit flag shared by the solve loop: kernels become no-ops once the solve is done
+__device__ __forceinline__ bool solve_done(const int* done) { return done && *(volatile const int*)done; }
+
+}  // namespace tomg
+
+namespace tomg {
+// Inverse of a small SPD block (row-major B x B, FP64) through its Cholesky factor.
+// Returns false if a pivot is not positive (the block is then left unchanged in Ainv = 0).
+template <int B>
+__device__ __forceinline__ bool spd_inverse(const double* A, double* Ainv) {
+  double L[B][B];
+#pragma unroll
+  for (int i = 0; i < B; i++)
+#pragma unroll
+    for (int j = 0; j < B; j++) L[i][j] = 0.0;
+  bool ok = true;
+#pragma unroll
+  for (int j = 0; j < B; j++) {
+    double d = A[j * B + j];
+#pragma unroll
+    for (int k = 0; k < j; k++) d -= L[j][k] * L[j][k];
+    if (!(d > 0.0)) ok = false;
+    double ljj = ok ? sqrt(d) : 1.0;
+    L[j][j] = ljj;
+#pragma unroll
+    for (int i = j + 1; i < B; i++) {
+      double v = A[i * B + j];
+#pragma unroll
+      for (int k = 0; k < j; k++) v -= L[i][k] * L[j][k];
+      L[i][j] = v / ljj;
+    }
+  }
+  // columns of L^-1, then Ainv = L^-T L^-1
+  double Li[B][B];
+#pragma unroll
+  for (int c = 0; c < B; c++) {
+#pragma unroll
+    for (int i = 0; i < B; i++) {
+      double v = (i == c) ? 1.0 : 0.0;
+#pragma unroll
+      for (int k = 0; k < i; k++) v -= L[i][k] * Li[k][c];
+      Li[i][c] = v / L[i][i];
+    }
+  }
+#pragma unroll
+  for (int i = 0; i < B; i++)
+#pragma unroll
+    for (int j = 0; j < B; j++) {
+      double v = 0.0;
+#pragma unroll
+      for (int k = 0; k < B; k++) v += Li[k][i] * Li[k][j];
+      Ainv[i * B + j] = ok ? v : 0.0;
+    }
+  return ok;
+}
+
+// linear node index <-> grid coordinates
+__device__ __forceinline__ void node_ijk(int64_t node, int nx, int ny, int dim, int& i, int& j,
+                                         int& k) {
+  i = (int)(node % (nx + 1));
+  int64_t r = node / (nx + 1);
+  if (dim == 3) {
+    j = (int)(r % (ny + 1));
+    k = (int)(r / (ny + 1));
+  } else {
+    j = (int)r;
+    k = 0;
+  }
+}
+__device__ __forceinline__ int64_t node_id(int i, int j, int k, int nx, int ny) {
+  return (int64_t)i + (int64_t)(nx + 1) * ((int64_t)j + (int64_t)(ny + 1) * k);
+}
+}  // namespace tomg

@@ -1,0 +1,460 @@
+// Smoothed-aggregation setup on the device (Sec. 3.2 AMG, Sec. 4 "block fashion" strength,
+// rigid-body candidates, Jacobi-smoothed tentative prolongator):
+//   strength   ||A_ij||_F^2 > beta ||A_ii||_F ||A_jj||_F, one value per node   (Eq. 10)
+//   aggregates distance-2 maximal independent set in synchronous rounds with splitmix64
+//              priorities (Bell, Dalton & Olson 2012), then two attachment phases
+//   tentative  modified Gram-Schmidt QR of the candidates on every aggregate
+//   smoothing  P = T - omega D^-1 A T, omega = 4 / (3 rho(D^-1 A)), rho by power iteration
+// splitmix64 is written here from its published definition (Steele, Lea & Flood 2014).
+#include "ops.h"
+
+namespace tomg {
+
+namespace {
+
+constexpr uint64_t SALT_MIS = 0x4D495332ull;
+constexpr uint64_t SALT_POWER = 0x504F5752ull;
+constexpr uint64_t TOP = ~0ull;
+enum { UND = 0, IN = 1, OUT = 2 };
+
+__host__ __device__ __forceinline__ uint64_t splitmix64(uint64_t x) {
+  uint64_t z = x + 0x9E3779B97F4A7C15ull;
+  z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+  z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+  return z ^ (z >> 31);
+}
+__device__ __forceinline__ uint64_t mis_key(int64_t i, int level) {
+  const uint64_t h = splitmix64((uint64_t)i + (SALT_MIS << 24) + ((uint64_t)level << 40));
+  return ((h >> 33) << 32) + (uint64_t)i + 1ull;
+}
+
+__device__ __forceinline__ double block_fro(const double* blk, int bb) {
+  double s = 0.0;
+  for (int t = 0; t < bb; t++) s += blk[t] * blk[t];
+  return sqrt(s);
+}
+
+__global__ void k_diag_fro(int nbr, int b, const int* __restrict__ rp, const int* __restrict__ ci,
+                           const double* __restrict__ V, double* dnorm) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= nbr) return;
+  double d = 0.0;
+  for (int p = rp[i]; p < rp[i + 1]; p++)
+    if (ci[p] == i) d = block_fro(V + (int64_t)p * b * b, b * b);
+  dnorm[i] = d;
+}
+
+__global__ void k_strength(int nbr, int b, const int* __restrict__ rp, const int* __restrict__ ci,
+                           const double* __restrict__ V, const double* __restrict__ dnorm,
+                           double beta, int* counts, const int* __restrict__ srp, int* sci) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= nbr) return;
+  int cnt = 0;
+  int64_t pos = srp ? srp[i] : 0;
+  for (int p = rp[i]; p < rp[i + 1]; p++) {
+    const int j = ci[p];
+    if (j == i) continue;
+    const double F = block_fro(V + (int64_t)p * b * b, b * b);
+    if (F * F > beta * dnorm[i] * dnorm[j]) {
+      if (srp) sci[pos++] = j;
+      cnt++;
+    }
+  }
+  if (counts) counts[i] = cnt;
+}
+
+__global__ void k_mis_init(int n, const int* __restrict__ srp, int* state) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  state[i] = (srp[i + 1] == srp[i]) ? OUT : UND;
+}
+__global__ void k_mis_values(int n, int level, const int* __restrict__ state, uint64_t* v) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  const int st = state[i];
+  v[i] = (st == IN) ? TOP : (st == UND ? mis_key(i, level) : 0ull);
+}
+__global__ void k_neigh_max(int n, const int* __restrict__ srp, const int* __restrict__ sci,
+                            const uint64_t* __restrict__ v, uint64_t* m) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  uint64_t best = v[i];
+  for (int p = srp[i]; p < srp[i + 1]; p++) best = max(best, v[sci[p]]);
+  m[i] = best;
+}
+__global__ void k_mis_update(int n, int level, const int* __restrict__ srp,
+                             const int* __restrict__ sci, const uint64_t* __restrict__ m1,
+                             int* state, int* undecided) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  if (state[i] != UND) return;
+  uint64_t m2 = m1[i];
+  for (int p = srp[i]; p < srp[i + 1]; p++) m2 = max(m2, m1[sci[p]]);
+  int st = UND;
+  if (m2 == TOP) st = OUT;
+  else if (m2 == mis_key(i, level)) st = IN;
+  state[i] = st;
+  if (st == UND) atomicAdd(undecided, 1);
+}
+
+__global__ void k_root_flags(int n, const int* __restrict__ state, int* flags) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < n) flags[i] = (state[i] == IN) ? 1 : 0;
+}
+__global__ void k_agg_phase1(int n, const int* __restrict__ srp, const int* __restrict__ sci,
+                             const int* __restrict__ state, const int* __restrict__ root_scan,
+                             int* agg1) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  int a = -1;
+  if (state[i] == IN) {
+    a = root_scan[i];
+  } else if (srp[i + 1] > srp[i]) {
+    for (int p = srp[i]; p < srp[i + 1]; p++) {
+      const int j = sci[p];
+      if (state[j] == IN) { a = root_scan[j]; break; }
+    }
+  }
+  agg1[i] = a;
+}
+__global__ void k_agg_phase2(int n, int level, const int* __restrict__ srp,
+                             const int* __restrict__ sci, const int* __restrict__ agg1, int* agg2,
+                             int* failures) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  int a = agg1[i];
+  if (a < 0 && srp[i + 1] > srp[i]) {
+    uint64_t best = 0;
+    for (int p = srp[i]; p < srp[i + 1]; p++) {
+      const int j = sci[p];
+      if (agg1[j] < 0) continue;
+      const uint64_t kj = mis_key(j, level);
+      if (kj > best) { best = kj; a = agg1[j]; }
+    }
+    if (a < 0) atomicAdd(failures, 1);
+  }
+  agg2[i] = a;
+}
+
+// members of each aggregate in ascending node order (counting sort + per-aggregate sort)
+__global__ void k_agg_count(int n, const int* __restrict__ agg, int* cnt) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < n && agg[i] >= 0) atomicAdd(&cnt[agg[i]], 1);
+}
+__global__ void k_agg_scatter(int n, const int* __restrict__ agg, const int* __restrict__ start,
+                              int* cursor, int* members) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n || agg[i] < 0) return;
+  const int a = agg[i];
+  members[start[a] + atomicAdd(&cursor[a], 1)] = i;
+}
+__global__ void k_agg_sort(int n_agg, const int* __restrict__ start, int* members) {
+  const int a = blockIdx.x * blockDim.x + threadIdx.x;
+  if (a >= n_agg) return;
+  const int s = start[a], e = start[a + 1];
+  for (int p = s + 1; p < e; p++) {
+    const int v = members[p];
+    int q = p - 1;
+    while (q >= s && members[q] > v) { members[q + 1] = members[q]; q--; }
+    members[q + 1] = v;
+  }
+}
+
+__global__ void k_T_pattern(int n, const int* __restrict__ agg, int* flags) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < n) flags[i] = agg[i] >= 0 ? 1 : 0;
+}
+__global__ void k_T_cols(int n, const int* __restrict__ agg, int* Tci, const int* __restrict__ Trp) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < n && agg[i] >= 0) Tci[Trp[i]] = agg[i];
+}
+
+// one warp per aggregate: modified Gram-Schmidt on the aggregate's rows of B (m x k), written
+// in place into the T blocks (b x k per member node); R goes to Bc (k x k per aggregate)
+__global__ void k_tentative(int n_agg, int b, int k, const int* __restrict__ start,
+                            const int* __restrict__ members, const int* __restrict__ Trp,
+                            const double* __restrict__ B, double* TV, double* Bc) {
+  const int a = (blockIdx.x * blockDim.x + threadIdx.x) >> 5, lane = threadIdx.x & 31;
+  if (a >= n_agg) return;
+  const int s = start[a], e = start[a + 1];
+  const int m = (e - s) * b;
+  // row t of the aggregate = member (t / b), component (t % b)
+  auto tv = [&](int t, int c) -> double& {
+    const int node = members[s + t / b];
+    return TV[((int64_t)Trp[node] * b + (t % b)) * k + c];
+  };
+  for (int t = lane; t < m; t += 32) {
+    const int node = members[s + t / b];
+    for (int c = 0; c < k; c++) tv(t, c) = B[((int64_t)node * b + (t % b)) * k + c];
+  }
+  __syncwarp();
+  double* R = Bc + (int64_t)a * k * k;
+  for (int t = lane; t < k * k; t += 32) R[t] = 0.0;
+  __syncwarp();
+  for (int c = 0; c < k; c++) {
+    double n0 = 0.0;
+    for (int t = lane; t < m; t += 32) n0 += tv(t, c) * tv(t, c);
+    for (int o = 16; o > 0; o >>= 1) n0 += __shfl_xor_sync(0xffffffffu, n0, o);
+    n0 = sqrt(n0);
+    for (int j = 0; j < c; j++) {
+      double d = 0.0;
+      for (int t = lane; t < m; t += 32) d += tv(t, j) * tv(t, c);
+      for (int o = 16; o > 0; o >>= 1) d += __shfl_xor_sync(0xffffffffu, d, o);
+      if (lane == 0) R[j * k + c] = d;
+      for (int t = lane; t < m; t += 32) tv(t, c) -= d * tv(t, j);
+      __syncwarp();
+    }
+    double nr = 0.0;
+    for (int t = lane; t < m; t += 32) nr += tv(t, c) * tv(t, c);
+    for (int o = 16; o > 0; o >>= 1) nr += __shfl_xor_sync(0xffffffffu, nr, o);
+    nr = sqrt(nr);
+    const bool live = n0 > 0.0 && nr > 1e-8 * n0;
+    for (int t = lane; t < m; t += 32) tv(t, c) = live ? tv(t, c) / nr : 0.0;
+    if (lane == 0) R[c * k + c] = live ? nr : 0.0;
+    __syncwarp();
+  }
+}
+
+__global__ void k_power_init(int64_t n, int level, double* v) {
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  const uint64_t h = splitmix64((uint64_t)i + SALT_POWER + (uint64_t)level);
+  v[i] = (double)(h >> 11) * 0x1.0p-53 - 0.5;
+}
+// w = Dinv (A v); partial sums of w.w per block
+template <int B>
+__global__ void k_power_step(int nbr, const int* __restrict__ rp, const int* __restrict__ ci,
+                             const double* __restrict__ V, const double* __restrict__ Dinv,
+                             const double* __restrict__ v, double* w, double* partials) {
+  __shared__ double sred[32];
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  double ss = 0.0;
+  if (i < nbr) {
+    double acc[B];
+    for (int r = 0; r < B; r++) acc[r] = 0.0;
+    for (int p = rp[i]; p < rp[i + 1]; p++) {
+      const int j = ci[p];
+      const double* blk = V + (int64_t)p * B * B;
+      for (int r = 0; r < B; r++)
+        for (int c = 0; c < B; c++) acc[r] += blk[r * B + c] * v[(int64_t)B * j + c];
+    }
+    const double* D = Dinv + (int64_t)B * B * i;
+    for (int r = 0; r < B; r++) {
+      double t = 0.0;
+      for (int c = 0; c < B; c++) t += D[r * B + c] * acc[c];
+      w[(int64_t)B * i + r] = t;
+      ss += t * t;
+    }
+  }
+  const double tot = block_sum(ss, sred);
+  if (threadIdx.x == 0) partials[blockIdx.x] = tot;
+}
+__global__ void k_sumsq_partials(int64_t n, const double* __restrict__ v, double* partials) {
+  __shared__ double sred[32];
+  double ss = 0.0;
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+    ss += v[i] * v[i];
+  const double tot = block_sum(ss, sred);
+  if (threadIdx.x == 0) partials[blockIdx.x] = tot;
+}
+__global__ void k_scale(int64_t n, double* v, double s) {
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < n) v[i] *= s;
+}
+
+__global__ void k_smooth_P(int nbr, int b, int k, const int* __restrict__ rp,
+                           const int* __restrict__ ci, const double* __restrict__ ATV,
+                           const int* __restrict__ agg, const int* __restrict__ Trp,
+                           const double* __restrict__ TV, const double* __restrict__ Dinv,
+                           double omega, double* PV) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= nbr) return;
+  const double* D = Dinv + (int64_t)b * b * i;
+  for (int p = rp[i]; p < rp[i + 1]; p++) {
+    const double* X = ATV + (int64_t)p * b * k;
+    double* Y = PV + (int64_t)p * b * k;
+    const bool own = (agg[i] >= 0 && ci[p] == agg[i]);
+    const double* Tb = own ? TV + (int64_t)Trp[i] * b * k : nullptr;
+    for (int r = 0; r < b; r++)
+      for (int c = 0; c < k; c++) {
+        double t = 0.0;
+        for (int q = 0; q < b; q++) t += D[r * b + q] * X[q * k + c];
+        Y[r * k + c] = (own ? Tb[r * k + c] : 0.0) - omega * t;
+      }
+  }
+}
+
+__global__ void k_fix_zero_rows(int nbr, int b, const int* __restrict__ rp,
+                                const int* __restrict__ ci, double* V) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= nbr) return;
+  for (int r = 0; r < b; r++) {
+    bool zero = true;
+    for (int p = rp[i]; p < rp[i + 1] && zero; p++)
+      for (int c = 0; c < b; c++)
+        if (V[((int64_t)p * b + r) * b + c] != 0.0) { zero = false; break; }
+    if (!zero) continue;
+    for (int p = rp[i]; p < rp[i + 1]; p++)
+      if (ci[p] == i) V[((int64_t)p * b + r) * b + r] = 1.0;
+  }
+}
+
+__global__ void k_rbm(int dim, int nx, int ny, int nz, const double* __restrict__ xs,
+                      const double* __restrict__ ys, const double* __restrict__ zs, double* B) {
+  const int64_t nn = (int64_t)(nx + 1) * (ny + 1) * (dim == 3 ? nz + 1 : 1);
+  const int64_t node = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (node >= nn) return;
+  int i, j, k;
+  node_ijk(node, nx, ny, dim, i, j, k);
+  const double x = xs[i], y = ys[j];
+  if (dim == 2) {
+    double* r0 = B + (2 * node) * 3;
+    double* r1 = r0 + 3;
+    r0[0] = 1.0; r0[1] = 0.0; r0[2] = -y;
+    r1[0] = 0.0; r1[1] = 1.0; r1[2] = x;
+  } else {
+    const double z = zs[k];
+    double* r0 = B + (3 * node) * 6;
+    double* r1 = r0 + 6;
+    double* r2 = r1 + 6;
+    // [tx, ty, tz, rot_x (0,-z,y), rot_y (z,0,-x), rot_z (-y,x,0)]
+    r0[0] = 1; r0[1] = 0; r0[2] = 0; r0[3] = 0.0; r0[4] = z;    r0[5] = -y;
+    r1[0] = 0; r1[1] = 1; r1[2] = 0; r1[3] = -z;  r1[4] = 0.0;  r1[5] = x;
+    r2[0] = 0; r2[1] = 0; r2[2] = 1; r2[3] = y;   r2[4] = -x;   r2[5] = 0.0;
+  }
+}
+
+}  // namespace
+
+void amg_strength_counts(cudaStream_t s, const Bsr& A, const double* V, double beta, int* counts) {
+  DBuf<double> dn;
+  dn.resize(A.nbr);
+  LAUNCH(k_diag_fro, ceil_div(A.nbr, 256), 256, 0, s, A.nbr, A.br, A.rp, A.ci, V, dn.p);
+  LAUNCH(k_strength, ceil_div(A.nbr, 256), 256, 0, s, A.nbr, A.br, A.rp, A.ci, V, dn.p, beta,
+         counts, (const int*)nullptr, (int*)nullptr);
+  CK(cudaStreamSynchronize(s));
+}
+
+void amg_strength_fill(cudaStream_t s, const Bsr& A, const double* V, double beta, const int* srp,
+                       int* sci) {
+  DBuf<double> dn;
+  dn.resize(A.nbr);
+  LAUNCH(k_diag_fro, ceil_div(A.nbr, 256), 256, 0, s, A.nbr, A.br, A.rp, A.ci, V, dn.p);
+  LAUNCH(k_strength, ceil_div(A.nbr, 256), 256, 0, s, A.nbr, A.br, A.rp, A.ci, V, dn.p, beta,
+         (int*)nullptr, srp, sci);
+  CK(cudaStreamSynchronize(s));
+}
+
+int amg_mis2(cudaStream_t s, int n, const int* srp, const int* sci, int level, int* state,
+             uint64_t* v, uint64_t* m1, int* flag_host, int* flag_dev) {
+  const int g = ceil_div(n, 256);
+  LAUNCH(k_mis_init, g, 256, 0, s, n, srp, state);
+  int rounds = 0;
+  while (true) {
+    CK(cudaMemsetAsync(flag_dev, 0, sizeof(int), s));
+    LAUNCH(k_mis_values, g, 256, 0, s, n, level, state, v);
+    LAUNCH(k_neigh_max, g, 256, 0, s, n, srp, sci, v, m1);
+    LAUNCH(k_mis_update, g, 256, 0, s, n, level, srp, sci, m1, state, flag_dev);
+    CK(cudaMemcpyAsync(flag_host, flag_dev, sizeof(int), cudaMemcpyDeviceToHost, s));
+    CK(cudaStreamSynchronize(s));
+    rounds++;
+    if (*flag_host == 0) break;
+    if (rounds > 100000) TOMG_THROW(TOMG_E_BREAKDOWN, "MIS-2 did not terminate");
+  }
+  return rounds;
+}
+
+int amg_aggregate(cudaStream_t s, int n, const int* srp, const int* sci, int level,
+                  const int* state, int* agg, int* root_scan) {
+  DBuf<int> flags, agg1, fail;
+  flags.resize(n);
+  agg1.resize(n);
+  fail.resize(1);
+  fail.zero(s);
+  const int g = ceil_div(n, 256);
+  LAUNCH(k_root_flags, g, 256, 0, s, n, state, flags.p);
+  const int n_agg = (int)exclusive_scan(s, flags.p, root_scan, n);
+  LAUNCH(k_agg_phase1, g, 256, 0, s, n, srp, sci, state, root_scan, agg1.p);
+  LAUNCH(k_agg_phase2, g, 256, 0, s, n, level, srp, sci, agg1.p, agg, fail.p);
+  int nf = 0;
+  CK(cudaMemcpyAsync(&nf, fail.p, sizeof(int), cudaMemcpyDeviceToHost, s));
+  CK(cudaStreamSynchronize(s));
+  if (nf) TOMG_THROW(TOMG_E_BREAKDOWN, "%d nodes left unaggregated", nf);
+  return n_agg;
+}
+
+void amg_tentative(cudaStream_t s, int n, int b, int k, int n_agg, const int* agg,
+                   const double* B, int* Trp, int* Tci, double* TV, double* Bc) {
+  const int g = ceil_div(n, 256);
+  DBuf<int> flags, cnt, start, cursor, members;
+  flags.resize(n);
+  LAUNCH(k_T_pattern, g, 256, 0, s, n, agg, flags.p);
+  const int64_t nT = exclusive_scan(s, flags.p, Trp, n);
+  LAUNCH(k_T_cols, g, 256, 0, s, n, agg, Tci, Trp);
+  cnt.resize(n_agg + 1);
+  start.resize(n_agg + 1);
+  cursor.resize(n_agg + 1);
+  members.resize(nT > 0 ? nT : 1);
+  cnt.zero(s);
+  cursor.zero(s);
+  LAUNCH(k_agg_count, g, 256, 0, s, n, agg, cnt.p);
+  exclusive_scan(s, cnt.p, start.p, n_agg);
+  LAUNCH(k_agg_scatter, g, 256, 0, s, n, agg, start.p, cursor.p, members.p);
+  LAUNCH(k_agg_sort, ceil_div(n_agg, 128), 128, 0, s, n_agg, start.p, members.p);
+  LAUNCH(k_tentative, ceil_div((int64_t)n_agg * 32, 128), 128, 0, s, n_agg, b, k, start.p,
+         members.p, Trp, B, TV, Bc);
+  CK(cudaStreamSynchronize(s));
+}
+
+double amg_spectral_radius(cudaStream_t s, const Bsr& A, const double* V, const double* Dinv,
+                           int level, int iters, double* v, double* w, double* partials) {
+  const int64_t n = (int64_t)A.nbr * A.br;
+  const int gb = ceil_div(A.nbr, 256);
+  const int gp = 256;
+  std::vector<double> hp(std::max(gb, gp));
+  auto norm = [&](const double* x) {
+    LAUNCH(k_sumsq_partials, gp, 256, 0, s, n, x, partials);
+    CK(cudaMemcpyAsync(hp.data(), partials, sizeof(double) * gp, cudaMemcpyDeviceToHost, s));
+    CK(cudaStreamSynchronize(s));
+    double t = 0.0;
+    for (int q = 0; q < gp; q++) t += hp[q];
+    return sqrt(t);
+  };
+  LAUNCH(k_power_init, ceil_div(n, 256), 256, 0, s, n, level, v);
+  double nv = norm(v);
+  LAUNCH(k_scale, ceil_div(n, 256), 256, 0, s, n, v, 1.0 / nv);
+  double rho = 0.0;
+  for (int it = 0; it < iters; it++) {
+    if (A.br == 2) LAUNCH(k_power_step<2>, gb, 256, 0, s, A.nbr, A.rp, A.ci, V, Dinv, v, w, partials);
+    else if (A.br == 3) LAUNCH(k_power_step<3>, gb, 256, 0, s, A.nbr, A.rp, A.ci, V, Dinv, v, w, partials);
+    else if (A.br == 6) LAUNCH(k_power_step<6>, gb, 256, 0, s, A.nbr, A.rp, A.ci, V, Dinv, v, w, partials);
+    else TOMG_THROW(TOMG_E_INVALID, "unsupported block %d", A.br);
+    CK(cudaMemcpyAsync(hp.data(), partials, sizeof(double) * gb, cudaMemcpyDeviceToHost, s));
+    CK(cudaStreamSynchronize(s));
+    double t = 0.0;
+    for (int q = 0; q < gb; q++) t += hp[q];
+    rho = sqrt(t);
+    if (!(rho > 0.0)) TOMG_THROW(TOMG_E_BREAKDOWN, "power iteration collapsed");
+    LAUNCH(k_scale, ceil_div(n, 256), 256, 0, s, n, w, 1.0 / rho);
+    std::swap(v, w);
+  }
+  return rho;
+}
+
+void amg_smooth_prolongator(cudaStream_t s, const Bsr& AT, const double* ATV, const int* agg,
+                            const double* TV, const int* Trp, const double* Dinv, double omega,
+                            int b, double* PV) {
+  LAUNCH(k_smooth_P, ceil_div(AT.nbr, 128), 128, 0, s, AT.nbr, b, AT.bc, AT.rp, AT.ci, ATV, agg,
+         Trp, TV, Dinv, omega, PV);
+}
+
+void amg_fix_zero_rows(cudaStream_t s, const Bsr& A, double* V) {
+  LAUNCH(k_fix_zero_rows, ceil_div(A.nbr, 128), 128, 0, s, A.nbr, A.br, A.rp, A.ci, V);
+}
+
+void rigid_body_modes(cudaStream_t s, const Geo& g, const double* xs, const double* ys,
+                      const double* zs, double* B) {
+  LAUNCH(k_rbm, ceil_div(g.nodes(), 256), 256, 0, s, g.dim, g.nx, g.ny, g.nz, xs, ys, zs, B);
+}
+
+}  // namespace tomg

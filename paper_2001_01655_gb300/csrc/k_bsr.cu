@@ -1,0 +1,432 @@
+// Block-CSR (BSR) kernels for the algebraic levels (Sec. 3.2, Sec. 4): SpMV / residual /
+// point-block Jacobi, rectangular transfers with P and R = P^T, block diagonal inverses,
+// transpose, the two-phase SpGEMM used for A T, A P and P^T (A P) (Eq. 9), prefix sums.
+//
+// SpGEMM: symbolic phase with one warp per output row and an open-addressing hash table in
+// shared memory (global memory for rows whose candidate count exceeds the shared table);
+// columns of each output row are sorted by rank counting, so the result is canonical.
+// Numeric phase: one lane per output block, A's row walked in order and B's row searched by
+// bisection, so every block is accumulated in a fixed order (deterministic).
+#include "ops.h"
+
+namespace tomg {
+
+namespace {
+
+template <class T, int B, int MODE>
+__global__ void __launch_bounds__(256) k_bsr(int nbr, const int* __restrict__ rp,
+                                             const int* __restrict__ ci, const T* __restrict__ V,
+                                             const T* __restrict__ x, T* __restrict__ y,
+                                             const T* __restrict__ b, const T* __restrict__ Dinv,
+                                             T omega, const int* done) {
+  if (solve_done(done)) return;
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= nbr) return;
+  T acc[B];
+#pragma unroll
+  for (int r = 0; r < B; r++) acc[r] = T(0);
+  for (int p = rp[i]; p < rp[i + 1]; p++) {
+    const int j = ci[p];
+    const T* blk = V + (int64_t)p * B * B;
+    T xv[B];
+#pragma unroll
+    for (int c = 0; c < B; c++) xv[c] = x[(int64_t)B * j + c];
+#pragma unroll
+    for (int r = 0; r < B; r++)
+#pragma unroll
+      for (int c = 0; c < B; c++) acc[r] += blk[r * B + c] * xv[c];
+  }
+  if (MODE == MODE_APPLY) {
+#pragma unroll
+    for (int r = 0; r < B; r++) y[(int64_t)B * i + r] = acc[r];
+  } else if (MODE == MODE_RESID) {
+#pragma unroll
+    for (int r = 0; r < B; r++) y[(int64_t)B * i + r] = b[(int64_t)B * i + r] - acc[r];
+  } else {
+    T res[B];
+#pragma unroll
+    for (int r = 0; r < B; r++) res[r] = b[(int64_t)B * i + r] - acc[r];
+    const T* D = Dinv + (int64_t)B * B * i;
+#pragma unroll
+    for (int r = 0; r < B; r++) {
+      T v = T(0);
+#pragma unroll
+      for (int c = 0; c < B; c++) v += D[r * B + c] * res[c];
+      y[(int64_t)B * i + r] = x[(int64_t)B * i + r] + omega * v;
+    }
+  }
+}
+
+template <class T, int BR, int BC>
+__global__ void k_bsr_rect(int nbr, const int* __restrict__ rp, const int* __restrict__ ci,
+                           const T* __restrict__ V, const T* __restrict__ x, T* __restrict__ y,
+                           int accumulate, const int* done) {
+  if (solve_done(done)) return;
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= nbr) return;
+  T acc[BR];
+#pragma unroll
+  for (int r = 0; r < BR; r++) acc[r] = accumulate ? y[(int64_t)BR * i + r] : T(0);
+  for (int p = rp[i]; p < rp[i + 1]; p++) {
+    const int j = ci[p];
+    const T* blk = V + (int64_t)p * BR * BC;
+#pragma unroll
+    for (int c = 0; c < BC; c++) {
+      const T xv = x[(int64_t)BC * j + c];
+#pragma unroll
+      for (int r = 0; r < BR; r++) acc[r] += blk[r * BC + c] * xv;
+    }
+  }
+#pragma unroll
+  for (int r = 0; r < BR; r++) y[(int64_t)BR * i + r] = acc[r];
+}
+
+template <int B>
+__global__ void k_bsr_diag(int nbr, const int* __restrict__ rp, const int* __restrict__ ci,
+                           const double* __restrict__ V, double* Dinv64, float* Dinv32) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= nbr) return;
+  double D[B * B], Di[B * B];
+  for (int t = 0; t < B * B; t++) D[t] = 0.0;
+  for (int p = rp[i]; p < rp[i + 1]; p++)
+    if (ci[p] == i)
+      for (int t = 0; t < B * B; t++) D[t] = V[(int64_t)p * B * B + t];
+  spd_inverse<B>(D, Di);
+  for (int t = 0; t < B * B; t++) {
+    Dinv64[(int64_t)B * B * i + t] = Di[t];
+    Dinv32[(int64_t)B * B * i + t] = (float)Di[t];
+  }
+}
+
+__global__ void k_bsr_dense(int nbr, int b, int64_t n, const int* __restrict__ rp,
+                            const int* __restrict__ ci, const double* __restrict__ V, double* A) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= nbr) return;
+  for (int p = rp[i]; p < rp[i + 1]; p++) {
+    const int j = ci[p];
+    for (int r = 0; r < b; r++)
+      for (int c = 0; c < b; c++) A[((int64_t)b * i + r) * n + (int64_t)b * j + c] = V[((int64_t)p * b + r) * b + c];
+  }
+}
+
+__global__ void k_col_counts(int nbr, const int* __restrict__ rp, const int* __restrict__ ci,
+                             int* counts) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= nbr) return;
+  for (int p = rp[i]; p < rp[i + 1]; p++) atomicAdd(&counts[ci[p]], 1);
+}
+
+__global__ void k_transpose_scatter(int nbr, const int* __restrict__ rp, const int* __restrict__ ci,
+                                    const int* __restrict__ rpT, int* cursor, int* rowT, int* srcT) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= nbr) return;
+  for (int p = rp[i]; p < rp[i + 1]; p++) {
+    const int j = ci[p];
+    const int pos = rpT[j] + atomicAdd(&cursor[j], 1);
+    rowT[pos] = i;
+    srcT[pos] = p;
+  }
+}
+
+// sort each row of the transpose by column (insertion sort; rows are short) and copy blocks
+__global__ void k_transpose_finish(int nbc, int br, int bc, const int* __restrict__ rpT, int* rowT,
+                                   int* srcT, const double* __restrict__ V, double* VT) {
+  const int j = blockIdx.x * blockDim.x + threadIdx.x;
+  if (j >= nbc) return;
+  const int a = rpT[j], e = rpT[j + 1];
+  for (int p = a + 1; p < e; p++) {
+    const int kr = rowT[p], ks = srcT[p];
+    int q = p - 1;
+    while (q >= a && rowT[q] > kr) {
+      rowT[q + 1] = rowT[q];
+      srcT[q + 1] = srcT[q];
+      q--;
+    }
+    rowT[q + 1] = kr;
+    srcT[q + 1] = ks;
+  }
+  for (int p = a; p < e; p++) {
+    const double* src = V + (int64_t)srcT[p] * br * bc;
+    double* dst = VT + (int64_t)p * br * bc;
+    for (int r = 0; r < br; r++)
+      for (int c = 0; c < bc; c++) dst[c * br + r] = src[r * bc + c];
+  }
+}
+
+// ------------------------------- SpGEMM ------------------------------------------------
+constexpr int SPG_WARPS = 4;
+constexpr int SPG_SMEM_T = 2048;
+
+__device__ __forceinline__ int next_pow2(int x) { return x <= 1 ? 1 : 1 << (32 - __clz(x - 1)); }
+__device__ __forceinline__ int warp_sum_int(int v) {
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  return v;
+}
+__device__ __forceinline__ unsigned hash_col(int key) { return (unsigned)key * 2654435761u; }
+
+// per-row hash table size when it does not fit in shared memory (0 otherwise)
+__global__ void k_spgemm_big(int nrows, const int* __restrict__ Arp, const int* __restrict__ Aci,
+                             const int* __restrict__ Brp, int* big) {
+  const int row = blockIdx.x * blockDim.x + threadIdx.x;
+  if (row >= nrows) return;
+  int ub = 0;
+  for (int a = Arp[row]; a < Arp[row + 1]; a++) ub += Brp[Aci[a] + 1] - Brp[Aci[a]];
+  const int T = max(64, next_pow2(2 * ub));
+  big[row] = (T > SPG_SMEM_T) ? T : 0;
+}
+
+__global__ void __launch_bounds__(32 * SPG_WARPS)
+    k_spgemm_sym(int nrows, const int* __restrict__ Arp, const int* __restrict__ Aci,
+                 const int* __restrict__ Brp, const int* __restrict__ Bci,
+                 const int* __restrict__ goff, int* gtable, int* countsC,
+                 const int* __restrict__ rpC, int* ciC) {
+  __shared__ int tab[SPG_WARPS][SPG_SMEM_T];
+  const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int row = blockIdx.x * SPG_WARPS + w;
+  if (row >= nrows) return;  // warp-uniform
+  int ub = 0;
+  for (int a = Arp[row] + lane; a < Arp[row + 1]; a += 32) ub += Brp[Aci[a] + 1] - Brp[Aci[a]];
+  ub = warp_sum_int(ub);
+  const int T = max(64, next_pow2(2 * ub));
+  int* table = (T <= SPG_SMEM_T) ? tab[w] : gtable + goff[row];
+  for (int s = lane; s < T; s += 32) table[s] = -1;
+  __syncwarp();
+  int newc = 0;
+  for (int a = Arp[row]; a < Arp[row + 1]; a++) {
+    const int k = Aci[a];
+    for (int q = Brp[k] + lane; q < Brp[k + 1]; q += 32) {
+      const int key = Bci[q];
+      unsigned h = hash_col(key) & (unsigned)(T - 1);
+      while (true) {
+        const int prev = atomicCAS(&table[h], -1, key);
+        if (prev == -1) { newc++; break; }
+        if (prev == key) break;
+        h = (h + 1) & (unsigned)(T - 1);
+      }
+    }
+  }
+  newc = warp_sum_int(newc);
+  __syncwarp();
+  if (countsC) {
+    if (lane == 0) countsC[row] = newc;
+    return;
+  }
+  const int base = rpC[row];
+  for (int s = lane; s < T; s += 32) {
+    const int key = table[s];
+    if (key == -1) continue;
+    int rank = 0;
+    for (int t = 0; t < T; t++) {
+      const int v = table[t];
+      rank += (v != -1 && v < key) ? 1 : 0;
+    }
+    ciC[base + rank] = key;
+  }
+}
+
+__global__ void k_spgemm_num(int nrows, int br, int bk, int bc, const int* __restrict__ Arp,
+                             const int* __restrict__ Aci, const double* __restrict__ VA,
+                             const int* __restrict__ Brp, const int* __restrict__ Bci,
+                             const double* __restrict__ VB, const int* __restrict__ Crp,
+                             const int* __restrict__ Cci, double* VC) {
+  const int w = (blockIdx.x * blockDim.x + threadIdx.x) >> 5, lane = threadIdx.x & 31;
+  if (w >= nrows) return;
+  const int row = w;
+  for (int pc = Crp[row] + lane; pc < Crp[row + 1]; pc += 32) {
+    const int j = Cci[pc];
+    double acc[36];
+    for (int t = 0; t < br * bc; t++) acc[t] = 0.0;
+    for (int a = Arp[row]; a < Arp[row + 1]; a++) {
+      const int k = Aci[a];
+      const int lo = Brp[k], hi = Brp[k + 1];
+      if (lo == hi) continue;
+      int l = lo, h = hi;
+      while (l < h) {
+        const int mid = (l + h) >> 1;
+        if (Bci[mid] < j) l = mid + 1;
+        else h = mid;
+      }
+      if (l >= hi || Bci[l] != j) continue;
+      const double* Ab = VA + (int64_t)a * br * bk;
+      const double* Bb = VB + (int64_t)l * bk * bc;
+      for (int r = 0; r < br; r++)
+        for (int t = 0; t < bk; t++) {
+          const double av = Ab[r * bk + t];
+          for (int c = 0; c < bc; c++) acc[r * bc + c] += av * Bb[t * bc + c];
+        }
+    }
+    double* Cb = VC + (int64_t)pc * br * bc;
+    for (int t = 0; t < br * bc; t++) Cb[t] = acc[t];
+  }
+}
+
+template <class A, class B>
+__global__ void k_cast(const A* __restrict__ a, B* __restrict__ b, int64_t n) {
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < n) b[i] = (B)a[i];
+}
+
+// ------------------------------- scan --------------------------------------------------
+constexpr int SCAN_B = 1024;
+__global__ void k_scan_block(const int* __restrict__ in, int* out, int64_t n, int* sums) {
+  __shared__ int warp_tot[32];
+  const int64_t i = (int64_t)blockIdx.x * SCAN_B + threadIdx.x;
+  const int v = (i < n) ? in[i] : 0;
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  int x = v;
+  for (int o = 1; o < 32; o <<= 1) {
+    const int y = __shfl_up_sync(0xffffffffu, x, o);
+    if (lane >= o) x += y;
+  }
+  if (lane == 31) warp_tot[w] = x;
+  __syncthreads();
+  if (w == 0) {
+    int t = warp_tot[lane];
+    for (int o = 1; o < 32; o <<= 1) {
+      const int y = __shfl_up_sync(0xffffffffu, t, o);
+      if (lane >= o) t += y;
+    }
+    warp_tot[lane] = t;
+  }
+  __syncthreads();
+  const int incl = x + (w > 0 ? warp_tot[w - 1] : 0);
+  if (i < n) out[i] = incl - v;
+  if (threadIdx.x == SCAN_B - 1) sums[blockIdx.x] = incl;
+}
+__global__ void k_scan_add(int* out, int64_t n, const int* offs) {
+  const int64_t i = (int64_t)blockIdx.x * SCAN_B + threadIdx.x;
+  if (i < n) out[i] += offs[blockIdx.x];
+}
+
+void scan_rec(cudaStream_t s, const int* in, int* out, int64_t n, int* total_dev) {
+  // writes exclusive scan of in[0..n) to out[0..n) and the total to *total_dev
+  const int nb = ceil_div(n, SCAN_B);
+  DBuf<int> sums, offs;
+  sums.resize(nb);
+  offs.resize(nb + 1);
+  LAUNCH(k_scan_block, nb, SCAN_B, 0, s, in, out, n, sums.p);
+  if (nb == 1) {
+    CK(cudaMemcpyAsync(total_dev, sums.p, sizeof(int), cudaMemcpyDeviceToDevice, s));
+  } else {
+    scan_rec(s, sums.p, offs.p, nb, total_dev);
+    LAUNCH(k_scan_add, nb, SCAN_B, 0, s, out, n, offs.p);
+  }
+  CK(cudaStreamSynchronize(s));  // temporaries are freed on return
+}
+
+}  // namespace
+
+template <class T>
+void bsr_op(cudaStream_t s, int mode, const Bsr& A, const T* V, const T* x, T* y, const T* b,
+            const T* Dinv, double omega, const int* done) {
+  const int grid = ceil_div(A.nbr, 128);
+#define BOP(B, M) LAUNCH((k_bsr<T, B, M>), grid, 128, 0, s, A.nbr, A.rp, A.ci, V, x, y, b, Dinv, (T)omega, done)
+#define BMODES(B)                                   \
+  if (mode == MODE_APPLY) BOP(B, MODE_APPLY);       \
+  else if (mode == MODE_RESID) BOP(B, MODE_RESID);  \
+  else BOP(B, MODE_JACOBI);
+  if (A.br == 2) { BMODES(2) }
+  else if (A.br == 3) { BMODES(3) }
+  else if (A.br == 6) { BMODES(6) }
+  else TOMG_THROW(TOMG_E_INVALID, "unsupported block size %d", A.br);
+#undef BMODES
+#undef BOP
+}
+template void bsr_op<float>(cudaStream_t, int, const Bsr&, const float*, const float*, float*,
+                            const float*, const float*, double, const int*);
+template void bsr_op<double>(cudaStream_t, int, const Bsr&, const double*, const double*, double*,
+                             const double*, const double*, double, const int*);
+
+template <class T>
+void bsr_spmv_rect(cudaStream_t s, const Bsr& A, const T* V, const T* x, T* y, int accumulate,
+                   const int* done) {
+  const int grid = ceil_div(A.nbr, 128);
+#define RECT(R, C)                                                                               \
+  if (A.br == R && A.bc == C) {                                                                  \
+    LAUNCH((k_bsr_rect<T, R, C>), grid, 128, 0, s, A.nbr, A.rp, A.ci, V, x, y, accumulate, done); \
+    return;                                                                                      \
+  }
+  RECT(2, 2) RECT(3, 3) RECT(6, 6) RECT(2, 3) RECT(3, 2) RECT(3, 6) RECT(6, 3)
+#undef RECT
+  TOMG_THROW(TOMG_E_INVALID, "unsupported transfer block %dx%d", A.br, A.bc);
+}
+template void bsr_spmv_rect<float>(cudaStream_t, const Bsr&, const float*, const float*, float*,
+                                   int, const int*);
+template void bsr_spmv_rect<double>(cudaStream_t, const Bsr&, const double*, const double*,
+                                    double*, int, const int*);
+
+void bsr_block_diag_inv(cudaStream_t s, const Bsr& A, const double* V, double* D64, float* D32) {
+  const int grid = ceil_div(A.nbr, 128);
+  if (A.br == 2) LAUNCH(k_bsr_diag<2>, grid, 128, 0, s, A.nbr, A.rp, A.ci, V, D64, D32);
+  else if (A.br == 3) LAUNCH(k_bsr_diag<3>, grid, 128, 0, s, A.nbr, A.rp, A.ci, V, D64, D32);
+  else if (A.br == 6) LAUNCH(k_bsr_diag<6>, grid, 128, 0, s, A.nbr, A.rp, A.ci, V, D64, D32);
+  else TOMG_THROW(TOMG_E_INVALID, "unsupported block size %d", A.br);
+}
+
+void bsr_to_dense(cudaStream_t s, const Bsr& A, const double* V, double* Ad) {
+  const int64_t n = (int64_t)A.nbr * A.br;
+  CK(cudaMemsetAsync(Ad, 0, sizeof(double) * n * n, s));
+  LAUNCH(k_bsr_dense, ceil_div(A.nbr, 128), 128, 0, s, A.nbr, A.br, n, A.rp, A.ci, V, Ad);
+}
+
+void bsr_col_counts(cudaStream_t s, const Bsr& A, int* counts) {
+  CK(cudaMemsetAsync(counts, 0, sizeof(int) * A.nbc, s));
+  LAUNCH(k_col_counts, ceil_div(A.nbr, 256), 256, 0, s, A.nbr, A.rp, A.ci, counts);
+}
+
+void bsr_transpose_fill(cudaStream_t s, const Bsr& A, const double* V, const int* rpT, int* ciT,
+                        double* VT, int* cursor) {
+  DBuf<int> src;
+  src.resize(A.nnzb > 0 ? A.nnzb : 1);
+  CK(cudaMemsetAsync(cursor, 0, sizeof(int) * A.nbc, s));
+  LAUNCH(k_transpose_scatter, ceil_div(A.nbr, 256), 256, 0, s, A.nbr, A.rp, A.ci, rpT, cursor,
+         ciT, src.p);
+  LAUNCH(k_transpose_finish, ceil_div(A.nbc, 128), 128, 0, s, A.nbc, A.br, A.bc, rpT, ciT, src.p,
+         V, VT);
+  CK(cudaStreamSynchronize(s));
+}
+
+void spgemm_counts(cudaStream_t s, const Bsr& A, const Bsr& B, int* counts, SpgemmWork& w) {
+  w.big.resize(A.nbr + 1);
+  w.goff.resize(A.nbr + 1);
+  LAUNCH(k_spgemm_big, ceil_div(A.nbr, 256), 256, 0, s, A.nbr, A.rp, A.ci, B.rp, w.big.p);
+  const int64_t tot = exclusive_scan(s, w.big.p, w.goff.p, A.nbr);
+  if (tot > 0x7fffffffLL) TOMG_THROW(TOMG_E_OOM, "SpGEMM hash tables too large (%lld)", (long long)tot);
+  w.gtable.resize(tot > 0 ? tot : 1);
+  LAUNCH(k_spgemm_sym, ceil_div(A.nbr, SPG_WARPS), 32 * SPG_WARPS, 0, s, A.nbr, A.rp, A.ci, B.rp,
+         B.ci, w.goff.p, w.gtable.p, counts, (const int*)nullptr, (int*)nullptr);
+}
+
+void spgemm_fill(cudaStream_t s, const Bsr& A, const Bsr& B, const int* rpC, int* ciC,
+                 SpgemmWork& w) {
+  LAUNCH(k_spgemm_sym, ceil_div(A.nbr, SPG_WARPS), 32 * SPG_WARPS, 0, s, A.nbr, A.rp, A.ci, B.rp,
+         B.ci, w.goff.p, w.gtable.p, (int*)nullptr, rpC, ciC);
+}
+
+void spgemm_numeric(cudaStream_t s, const Bsr& A, const double* VA, const Bsr& B, const double* VB,
+                    const Bsr& C, double* VC) {
+  if (A.br * B.bc > 36) TOMG_THROW(TOMG_E_INVALID, "SpGEMM block too large");
+  LAUNCH(k_spgemm_num, ceil_div((int64_t)A.nbr * 32, 128), 128, 0, s, A.nbr, A.br, A.bc, B.bc,
+         A.rp, A.ci, VA, B.rp, B.ci, VB, C.rp, C.ci, VC);
+}
+
+void cast_f64_f32(cudaStream_t s, const double* a, float* b, int64_t n) {
+  if (n > 0) LAUNCH((k_cast<double, float>), ceil_div(n, 256), 256, 0, s, a, b, n);
+}
+void cast_f32_f64(cudaStream_t s, const float* a, double* b, int64_t n) {
+  if (n > 0) LAUNCH((k_cast<float, double>), ceil_div(n, 256), 256, 0, s, a, b, n);
+}
+
+int64_t exclusive_scan(cudaStream_t s, const int* in, int* out, int64_t n) {
+  if (n == 0) {
+    CK(cudaMemsetAsync(out, 0, sizeof(int), s));
+    return 0;
+  }
+  scan_rec(s, in, out, n, out + n);
+  int tot = 0;
+  CK(cudaMemcpyAsync(&tot, out + n, sizeof(int), cudaMemcpyDeviceToHost, s));
+  CK(cudaStreamSynchronize(s));
+  return tot;
+}
+
+}  // namespace tomg

@@ -1,0 +1,418 @@
+// Geometric levels (Sec. 3.2): operators stored as structured 3^d nodal stencils (no column
+// indices), bilinear / trilinear transfers built from the coarse grid's shape functions, and
+// the Galerkin product A_c = P^T A P (Eq. 9) computed directly on the stencils.
+//
+// Coarsening: ceil(n/2) coarse elements per axis, coarse node I at fine position min(2I, n);
+// 1D weights are 1 at a coincident node and 1/2 at a fine node midway between two coarse
+// nodes.  Stencil layout (SoA, coalesced over nodes):
+//   S[((o * b + r) * b + c) * n_nodes + node],  o = (ox+1) + 3 (oy+1) + 9 (oz+1).
+#include "ops.h"
+
+namespace tomg {
+
+namespace {
+
+__device__ __forceinline__ double w1(int p, int I, int nf) {
+  const int pI = min(2 * I, nf);
+  if (p == pI) return 1.0;
+  const int d = p - pI;
+  if (d != 1 && d != -1) return 0.0;
+  if ((p & 1) == 0 || p == nf) return 0.0;  // p is itself a coarse position
+  return 0.5;
+}
+
+template <int DIM>
+__device__ __forceinline__ bool in_grid(int i, int j, int k, int nx, int ny, int nz) {
+  return i >= 0 && i <= nx && j >= 0 && j <= ny && (DIM == 2 || (k >= 0 && k <= nz));
+}
+
+template <class T, int DIM, int MODE>
+__global__ void __launch_bounds__(256) k_stencil(int nx, int ny, int nz, const T* __restrict__ S,
+                                                 const T* __restrict__ x, T* __restrict__ y,
+                                                 const T* __restrict__ b,
+                                                 const T* __restrict__ Dinv, T omega,
+                                                 const int* done) {
+  constexpr int NO = (DIM == 3) ? 27 : 9, BB = DIM * DIM;
+  if (solve_done(done)) return;
+  const int64_t nn = (int64_t)(nx + 1) * (ny + 1) * (DIM == 3 ? nz + 1 : 1);
+  const int64_t node = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (node >= nn) return;
+  int i, j, k;
+  node_ijk(node, nx, ny, DIM, i, j, k);
+  T acc[DIM];
+#pragma unroll
+  for (int c = 0; c < DIM; c++) acc[c] = T(0);
+#pragma unroll
+  for (int o = 0; o < NO; o++) {
+    const int ox = o % 3 - 1, oy = (o / 3) % 3 - 1, oz = (DIM == 3) ? o / 9 - 1 : 0;
+    if (!in_grid<DIM>(i + ox, j + oy, k + oz, nx, ny, nz)) continue;
+    const int64_t nb = node_id(i + ox, j + oy, k + oz, nx, ny);
+    T xv[DIM];
+#pragma unroll
+    for (int c = 0; c < DIM; c++) xv[c] = x[DIM * nb + c];
+#pragma unroll
+    for (int r = 0; r < DIM; r++)
+#pragma unroll
+      for (int c = 0; c < DIM; c++) acc[r] += S[((int64_t)o * BB + r * DIM + c) * nn + node] * xv[c];
+  }
+  if (MODE == MODE_APPLY) {
+#pragma unroll
+    for (int c = 0; c < DIM; c++) y[DIM * node + c] = acc[c];
+  } else if (MODE == MODE_RESID) {
+#pragma unroll
+    for (int c = 0; c < DIM; c++) y[DIM * node + c] = b[DIM * node + c] - acc[c];
+  } else {
+    T r[DIM];
+#pragma unroll
+    for (int c = 0; c < DIM; c++) r[c] = b[DIM * node + c] - acc[c];
+    const T* D = Dinv + (int64_t)BB * node;
+#pragma unroll
+    for (int c = 0; c < DIM; c++) {
+      T v = T(0);
+#pragma unroll
+      for (int c2 = 0; c2 < DIM; c2++) v += D[c * DIM + c2] * r[c2];
+      y[DIM * node + c] = x[DIM * node + c] + omega * v;
+    }
+  }
+}
+
+template <int DIM>
+__global__ void k_stencil_diag(int nx, int ny, int nz, const double* __restrict__ S, double* Dinv64,
+                               float* Dinv32) {
+  constexpr int BB = DIM * DIM, CENTER = (DIM == 3) ? 13 : 4;
+  const int64_t nn = (int64_t)(nx + 1) * (ny + 1) * (DIM == 3 ? nz + 1 : 1);
+  const int64_t node = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (node >= nn) return;
+  double D[BB], Di[BB];
+  for (int t = 0; t < BB; t++) D[t] = S[((int64_t)CENTER * BB + t) * nn + node];
+  spd_inverse<DIM>(D, Di);
+  for (int t = 0; t < BB; t++) {
+    Dinv64[BB * node + t] = Di[t];
+    Dinv32[BB * node + t] = (float)Di[t];
+  }
+}
+
+// per-axis list of (fine offset from pI, stencil offset, weight) with nonzero weight product
+struct AxisPairs {
+  int n;
+  int di[9], o[9];
+  double w[9];
+};
+__device__ __forceinline__ void axis_pairs(int I, int J, int nf, AxisPairs& L) {
+  L.n = 0;
+  const int pI = min(2 * I, nf);
+  for (int d = -1; d <= 1; d++) {
+    const int p = pI + d;
+    if (p < 0 || p > nf) continue;
+    const double wi = w1(p, I, nf);
+    if (wi == 0.0) continue;
+    for (int o = -1; o <= 1; o++) {
+      const int q = p + o;
+      if (q < 0 || q > nf) continue;
+      const double wj = w1(q, J, nf);
+      if (wj == 0.0) continue;
+      L.di[L.n] = p;
+      L.o[L.n] = o;
+      L.w[L.n] = wi * wj;
+      L.n++;
+    }
+  }
+}
+
+template <int DIM>
+__global__ void k_rap(int fnx, int fny, int fnz, int cnx, int cny, int cnz,
+                      const double* __restrict__ Sf, double* __restrict__ Sc) {
+  constexpr int BB = DIM * DIM;
+  const int64_t nnc = (int64_t)(cnx + 1) * (cny + 1) * (DIM == 3 ? cnz + 1 : 1);
+  const int64_t nnf = (int64_t)(fnx + 1) * (fny + 1) * (DIM == 3 ? fnz + 1 : 1);
+  const int64_t I = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  const int O = blockIdx.y;
+  if (I >= nnc) return;
+  int Ix, Iy, Iz;
+  node_ijk(I, cnx, cny, DIM, Ix, Iy, Iz);
+  const int Ox = O % 3 - 1, Oy = (O / 3) % 3 - 1, Oz = (DIM == 3) ? O / 9 - 1 : 0;
+  const int Jx = Ix + Ox, Jy = Iy + Oy, Jz = Iz + Oz;
+  double acc[BB];
+#pragma unroll
+  for (int t = 0; t < BB; t++) acc[t] = 0.0;
+  if (in_grid<DIM>(Jx, Jy, Jz, cnx, cny, cnz)) {
+    AxisPairs Lx, Ly, Lz;
+    axis_pairs(Ix, Jx, fnx, Lx);
+    axis_pairs(Iy, Jy, fny, Ly);
+    if (DIM == 3) axis_pairs(Iz, Jz, fnz, Lz);
+    else { Lz.n = 1; Lz.di[0] = 0; Lz.o[0] = 0; Lz.w[0] = 1.0; }
+    for (int c = 0; c < Lz.n; c++)
+      for (int bq = 0; bq < Ly.n; bq++)
+        for (int a = 0; a < Lx.n; a++) {
+          const double wt = Lx.w[a] * Ly.w[bq] * Lz.w[c];
+          const int64_t fi = node_id(Lx.di[a], Ly.di[bq], Lz.di[c], fnx, fny);
+          const int oi = (Lx.o[a] + 1) + 3 * (Ly.o[bq] + 1) + (DIM == 3 ? 9 * (Lz.o[c] + 1) : 0);
+#pragma unroll
+          for (int t = 0; t < BB; t++) acc[t] += wt * Sf[((int64_t)oi * BB + t) * nnf + fi];
+        }
+  }
+#pragma unroll
+  for (int t = 0; t < BB; t++) Sc[((int64_t)O * BB + t) * nnc + I] = acc[t];
+}
+
+template <class T, int DIM>
+__global__ void k_restrict(int fnx, int fny, int fnz, int cnx, int cny, int cnz,
+                           const T* __restrict__ rf, T* __restrict__ bc, const int* done) {
+  if (solve_done(done)) return;
+  const int64_t nnc = (int64_t)(cnx + 1) * (cny + 1) * (DIM == 3 ? cnz + 1 : 1);
+  const int64_t I = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (I >= nnc) return;
+  int Ix, Iy, Iz;
+  node_ijk(I, cnx, cny, DIM, Ix, Iy, Iz);
+  T acc[DIM];
+#pragma unroll
+  for (int c = 0; c < DIM; c++) acc[c] = T(0);
+  const int px = min(2 * Ix, fnx), py = min(2 * Iy, fny), pz = (DIM == 3) ? min(2 * Iz, fnz) : 0;
+  for (int dz = (DIM == 3 ? -1 : 0); dz <= (DIM == 3 ? 1 : 0); dz++) {
+    const int z = pz + dz;
+    if (DIM == 3 && (z < 0 || z > fnz)) continue;
+    const double wz = (DIM == 3) ? w1(z, Iz, fnz) : 1.0;
+    if (wz == 0.0) continue;
+    for (int dy = -1; dy <= 1; dy++) {
+      const int yy = py + dy;
+      if (yy < 0 || yy > fny) continue;
+      const double wy = w1(yy, Iy, fny);
+      if (wy == 0.0) continue;
+      for (int dx = -1; dx <= 1; dx++) {
+        const int xx = px + dx;
+        if (xx < 0 || xx > fnx) continue;
+        const double wx = w1(xx, Ix, fnx);
+        if (wx == 0.0) continue;
+        const T w = (T)(wx * wy * wz);
+        const int64_t fi = node_id(xx, yy, z, fnx, fny);
+#pragma unroll
+        for (int c = 0; c < DIM; c++) acc[c] += w * rf[DIM * fi + c];
+      }
+    }
+  }
+#pragma unroll
+  for (int c = 0; c < DIM; c++) bc[DIM * I + c] = acc[c];
+}
+
+// coarse nodes interpolating fine position p along an axis: returns count (1 or 2)
+__device__ __forceinline__ int coarse_of(int p, int nf, int* I, double* w) {
+  const int nc = (nf + 1) / 2;
+  if (p == nf) { I[0] = nc; w[0] = 1.0; return 1; }
+  if ((p & 1) == 0) { I[0] = p / 2; w[0] = 1.0; return 1; }
+  I[0] = (p - 1) / 2; w[0] = 0.5;
+  I[1] = (p + 1) / 2; w[1] = 0.5;
+  return 2;
+}
+
+template <class T, int DIM>
+__global__ void k_prolong_add(int fnx, int fny, int fnz, int cnx, int cny, int cnz,
+                              const T* __restrict__ xc, T* __restrict__ xf, const int* done) {
+  if (solve_done(done)) return;
+  const int64_t nnf = (int64_t)(fnx + 1) * (fny + 1) * (DIM == 3 ? fnz + 1 : 1);
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= nnf) return;
+  int x, y, z;
+  node_ijk(i, fnx, fny, DIM, x, y, z);
+  int Ix[2], Iy[2], Iz[2] = {0, 0};
+  double wx[2], wy[2], wz[2] = {1.0, 0.0};
+  const int nxs = coarse_of(x, fnx, Ix, wx), nys = coarse_of(y, fny, Iy, wy);
+  const int nzs = (DIM == 3) ? coarse_of(z, fnz, Iz, wz) : 1;
+  T acc[DIM];
+#pragma unroll
+  for (int c = 0; c < DIM; c++) acc[c] = xf[DIM * i + c];
+  for (int c3 = 0; c3 < nzs; c3++)
+    for (int b = 0; b < nys; b++)
+      for (int a = 0; a < nxs; a++) {
+        const T w = (T)(wx[a] * wy[b] * wz[c3]);
+        const int64_t I = node_id(Ix[a], Iy[b], Iz[c3], cnx, cny);
+#pragma unroll
+        for (int c = 0; c < DIM; c++) acc[c] += w * xc[DIM * I + c];
+      }
+#pragma unroll
+  for (int c = 0; c < DIM; c++) xf[DIM * i + c] = acc[c];
+}
+
+template <int DIM>
+__global__ void k_stencil_dense(int nx, int ny, int nz, const double* __restrict__ S, double* A) {
+  constexpr int NO = (DIM == 3) ? 27 : 9, BB = DIM * DIM;
+  const int64_t nn = (int64_t)(nx + 1) * (ny + 1) * (DIM == 3 ? nz + 1 : 1);
+  const int64_t node = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (node >= nn) return;
+  const int64_t n = DIM * nn;
+  int i, j, k;
+  node_ijk(node, nx, ny, DIM, i, j, k);
+  for (int o = 0; o < NO; o++) {
+    const int ox = o % 3 - 1, oy = (o / 3) % 3 - 1, oz = (DIM == 3) ? o / 9 - 1 : 0;
+    if (!in_grid<DIM>(i + ox, j + oy, k + oz, nx, ny, nz)) continue;
+    const int64_t nb = node_id(i + ox, j + oy, k + oz, nx, ny);
+    for (int r = 0; r < DIM; r++)
+      for (int c = 0; c < DIM; c++)
+        A[(DIM * node + r) * n + DIM * nb + c] = S[((int64_t)o * BB + r * DIM + c) * nn + node];
+  }
+}
+
+template <int DIM>
+__global__ void k_stencil_counts(int nx, int ny, int nz, int* counts) {
+  constexpr int NO = (DIM == 3) ? 27 : 9;
+  const int64_t nn = (int64_t)(nx + 1) * (ny + 1) * (DIM == 3 ? nz + 1 : 1);
+  const int64_t node = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (node >= nn) return;
+  int i, j, k;
+  node_ijk(node, nx, ny, DIM, i, j, k);
+  int cnt = 0;
+  for (int o = 0; o < NO; o++) {
+    const int ox = o % 3 - 1, oy = (o / 3) % 3 - 1, oz = (DIM == 3) ? o / 9 - 1 : 0;
+    cnt += in_grid<DIM>(i + ox, j + oy, k + oz, nx, ny, nz) ? 1 : 0;
+  }
+  counts[node] = cnt;
+}
+
+template <int DIM>
+__global__ void k_stencil_bsr(int nx, int ny, int nz, const double* __restrict__ S,
+                              const int* __restrict__ rp, int* ci, double* val) {
+  constexpr int NO = (DIM == 3) ? 27 : 9, BB = DIM * DIM;
+  const int64_t nn = (int64_t)(nx + 1) * (ny + 1) * (DIM == 3 ? nz + 1 : 1);
+  const int64_t node = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (node >= nn) return;
+  int i, j, k;
+  node_ijk(node, nx, ny, DIM, i, j, k);
+  int64_t pos = rp[node];
+  for (int o = 0; o < NO; o++) {
+    const int ox = o % 3 - 1, oy = (o / 3) % 3 - 1, oz = (DIM == 3) ? o / 9 - 1 : 0;
+    if (!in_grid<DIM>(i + ox, j + oy, k + oz, nx, ny, nz)) continue;
+    ci[pos] = (int)node_id(i + ox, j + oy, k + oz, nx, ny);
+    for (int t = 0; t < BB; t++) val[pos * BB + t] = S[((int64_t)o * BB + t) * nn + node];
+    pos++;
+  }
+}
+
+template <int DIM>
+__global__ void k_geoP(int fnx, int fny, int fnz, int cnx, int cny, const int* rp, int* counts,
+                       int* ci, double* val) {
+  const int64_t nnf = (int64_t)(fnx + 1) * (fny + 1) * (DIM == 3 ? fnz + 1 : 1);
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= nnf) return;
+  int x, y, z;
+  node_ijk(i, fnx, fny, DIM, x, y, z);
+  int Ix[2], Iy[2], Iz[2] = {0, 0};
+  double wx[2], wy[2], wz[2] = {1.0, 0.0};
+  const int nxs = coarse_of(x, fnx, Ix, wx), nys = coarse_of(y, fny, Iy, wy);
+  const int nzs = (DIM == 3) ? coarse_of(z, fnz, Iz, wz) : 1;
+  if (counts) { counts[i] = nxs * nys * nzs; return; }
+  int64_t pos = rp[i];
+  for (int c3 = 0; c3 < nzs; c3++)
+    for (int b = 0; b < nys; b++)
+      for (int a = 0; a < nxs; a++) {
+        ci[pos] = (int)node_id(Ix[a], Iy[b], Iz[c3], cnx, cny);
+        const double w = wx[a] * wy[b] * wz[c3];
+        for (int r = 0; r < DIM; r++)
+          for (int c = 0; c < DIM; c++) val[pos * DIM * DIM + r * DIM + c] = (r == c) ? w : 0.0;
+        pos++;
+      }
+}
+
+}  // namespace
+
+template <class T>
+void stencil_op(cudaStream_t s, int mode, const Geo& g, const T* S, const T* x, T* y, const T* b,
+                const T* Dinv, double omega, const int* done) {
+  const int64_t nn = g.nodes();
+  const int grid = ceil_div(nn, 256);
+#define STN(D, M) LAUNCH((k_stencil<T, D, M>), grid, 256, 0, s, g.nx, g.ny, g.nz, S, x, y, b, Dinv, (T)omega, done)
+  if (g.dim == 2) {
+    if (mode == MODE_APPLY) STN(2, MODE_APPLY);
+    else if (mode == MODE_RESID) STN(2, MODE_RESID);
+    else STN(2, MODE_JACOBI);
+  } else {
+    if (mode == MODE_APPLY) STN(3, MODE_APPLY);
+    else if (mode == MODE_RESID) STN(3, MODE_RESID);
+    else STN(3, MODE_JACOBI);
+  }
+#undef STN
+}
+template void stencil_op<float>(cudaStream_t, int, const Geo&, const float*, const float*, float*,
+                                const float*, const float*, double, const int*);
+template void stencil_op<double>(cudaStream_t, int, const Geo&, const double*, const double*,
+                                 double*, const double*, const double*, double, const int*);
+
+void stencil_block_diag_inv(cudaStream_t s, const Geo& g, const double* S, double* Dinv64,
+                            float* Dinv32) {
+  const int grid = ceil_div(g.nodes(), 128);
+  if (g.dim == 2) LAUNCH(k_stencil_diag<2>, grid, 128, 0, s, g.nx, g.ny, g.nz, S, Dinv64, Dinv32);
+  else LAUNCH(k_stencil_diag<3>, grid, 128, 0, s, g.nx, g.ny, g.nz, S, Dinv64, Dinv32);
+}
+
+void stencil_rap(cudaStream_t s, const Geo& f, const Geo& c, const double* Sf, double* Sc) {
+  dim3 grid(ceil_div(c.nodes(), 128), f.dim == 3 ? 27 : 9);
+  if (f.dim == 2) LAUNCH(k_rap<2>, grid, 128, 0, s, f.nx, f.ny, f.nz, c.nx, c.ny, c.nz, Sf, Sc);
+  else LAUNCH(k_rap<3>, grid, 128, 0, s, f.nx, f.ny, f.nz, c.nx, c.ny, c.nz, Sf, Sc);
+}
+
+template <class T>
+void geo_restrict(cudaStream_t s, const Geo& f, const Geo& c, const T* rf, T* bc, const int* done) {
+  const int grid = ceil_div(c.nodes(), 256);
+  if (f.dim == 2)
+    LAUNCH((k_restrict<T, 2>), grid, 256, 0, s, f.nx, f.ny, f.nz, c.nx, c.ny, c.nz, rf, bc, done);
+  else
+    LAUNCH((k_restrict<T, 3>), grid, 256, 0, s, f.nx, f.ny, f.nz, c.nx, c.ny, c.nz, rf, bc, done);
+}
+template void geo_restrict<float>(cudaStream_t, const Geo&, const Geo&, const float*, float*,
+                                  const int*);
+template void geo_restrict<double>(cudaStream_t, const Geo&, const Geo&, const double*, double*,
+                                   const int*);
+
+template <class T>
+void geo_prolong_add(cudaStream_t s, const Geo& f, const Geo& c, const T* xc, T* xf,
+                     const int* done) {
+  const int grid = ceil_div(f.nodes(), 256);
+  if (f.dim == 2)
+    LAUNCH((k_prolong_add<T, 2>), grid, 256, 0, s, f.nx, f.ny, f.nz, c.nx, c.ny, c.nz, xc, xf, done);
+  else
+    LAUNCH((k_prolong_add<T, 3>), grid, 256, 0, s, f.nx, f.ny, f.nz, c.nx, c.ny, c.nz, xc, xf, done);
+}
+template void geo_prolong_add<float>(cudaStream_t, const Geo&, const Geo&, const float*, float*,
+                                     const int*);
+template void geo_prolong_add<double>(cudaStream_t, const Geo&, const Geo&, const double*, double*,
+                                      const int*);
+
+void stencil_to_dense(cudaStream_t s, const Geo& g, const double* S, double* A) {
+  const int64_t n = g.dim * g.nodes();
+  CK(cudaMemsetAsync(A, 0, sizeof(double) * n * n, s));
+  const int grid = ceil_div(g.nodes(), 128);
+  if (g.dim == 2) LAUNCH(k_stencil_dense<2>, grid, 128, 0, s, g.nx, g.ny, g.nz, S, A);
+  else LAUNCH(k_stencil_dense<3>, grid, 128, 0, s, g.nx, g.ny, g.nz, S, A);
+}
+
+void stencil_row_counts(cudaStream_t s, const Geo& g, int* counts) {
+  const int grid = ceil_div(g.nodes(), 256);
+  if (g.dim == 2) LAUNCH(k_stencil_counts<2>, grid, 256, 0, s, g.nx, g.ny, g.nz, counts);
+  else LAUNCH(k_stencil_counts<3>, grid, 256, 0, s, g.nx, g.ny, g.nz, counts);
+}
+
+void stencil_to_bsr(cudaStream_t s, const Geo& g, const double* S, const int* rp, int* ci,
+                    double* val) {
+  const int grid = ceil_div(g.nodes(), 128);
+  if (g.dim == 2) LAUNCH(k_stencil_bsr<2>, grid, 128, 0, s, g.nx, g.ny, g.nz, S, rp, ci, val);
+  else LAUNCH(k_stencil_bsr<3>, grid, 128, 0, s, g.nx, g.ny, g.nz, S, rp, ci, val);
+}
+
+void geo_prolong_counts(cudaStream_t s, const Geo& f, const Geo& c, int* counts) {
+  const int grid = ceil_div(f.nodes(), 256);
+  if (f.dim == 2)
+    LAUNCH(k_geoP<2>, grid, 256, 0, s, f.nx, f.ny, f.nz, c.nx, c.ny, (const int*)nullptr, counts,
+           (int*)nullptr, (double*)nullptr);
+  else
+    LAUNCH(k_geoP<3>, grid, 256, 0, s, f.nx, f.ny, f.nz, c.nx, c.ny, (const int*)nullptr, counts,
+           (int*)nullptr, (double*)nullptr);
+}
+
+void geo_prolong_fill(cudaStream_t s, const Geo& f, const Geo& c, const int* rp, int* ci,
+                      double* val) {
+  const int grid = ceil_div(f.nodes(), 256);
+  if (f.dim == 2)
+    LAUNCH(k_geoP<2>, grid, 256, 0, s, f.nx, f.ny, f.nz, c.nx, c.ny, rp, (int*)nullptr, ci, val);
+  else
+    LAUNCH(k_geoP<3>, grid, 256, 0, s, f.nx, f.ny, f.nz, c.nx, c.ny, rp, (int*)nullptr, ci, val);
+}
+
+}  // namespace tomg

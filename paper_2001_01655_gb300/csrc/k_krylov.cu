@@ -1,0 +1,318 @@
+// Outer Krylov loop kernels (Sec. 3.1 CG; flexible CG after Notay 2000 for the FP32 V-cycle),
+// deterministic FP64 reductions, precision casts, the first Jacobi sweep from x = 0 and the
+// coarsest-level direct solve (Sec. 3.2: dense Cholesky factorisation at setup, explicit
+// inverse applied as a GEMV in every V-cycle).
+//
+// Reductions: every kernel that produces a dot product writes one FP64 partial per block
+// (fixed tree inside the block); a single-block "finish" kernel adds the partials in a fixed
+// order and updates the device-resident scalar state, so no host round trip is needed per
+// iteration and results do not depend on scheduling.
+#include "ops.h"
+
+namespace tomg {
+
+namespace {
+
+constexpr int RED_THREADS = 256;
+constexpr int RED_MAX_BLOCKS = 1216;  // 8 blocks per SM on the 152-SM GB300
+
+__global__ void __launch_bounds__(RED_THREADS) k_dot(const double* __restrict__ x,
+                                                     const double* __restrict__ y, int64_t n,
+                                                     double* partials, const int* done) {
+  __shared__ double sred[32];
+  if (solve_done(done)) return;
+  double s = 0.0;
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+    s += x[i] * y[i];
+  s = block_sum(s, sred);
+  if (threadIdx.x == 0) partials[blockIdx.x] = s;
+}
+
+__global__ void __launch_bounds__(1024) k_finish(int kind, const double* __restrict__ pa, int na,
+                                                 const double* __restrict__ pb, int nb,
+                                                 Scalars* sc) {
+  __shared__ double sred[32];
+  if (kind != FIN_INIT && sc->done) return;
+  double a = 0.0, b = 0.0;
+  for (int i = threadIdx.x; i < na; i += blockDim.x) a += pa[i];
+  for (int i = threadIdx.x; i < nb; i += blockDim.x) b += pb[i];
+  a = block_sum(a, sred);
+  b = block_sum(b, sred);
+  if (threadIdx.x != 0) return;
+  switch (kind) {
+    case FIN_INIT:  // a = r.r, b = b.b
+      sc->rr = a;
+      sc->bb = b;
+      sc->tol2 = sc->rtol2 * b;
+      sc->it = 0;
+      sc->status = TOMG_OK;
+      sc->done = (b == 0.0 || a <= sc->tol2) ? 1 : 0;
+      if (a != a) { sc->status = TOMG_E_BREAKDOWN; sc->done = 1; }
+      break;
+    case FIN_RZ0:
+      sc->rz = a;
+      if (!(a > 0.0)) { sc->status = TOMG_E_BREAKDOWN; sc->done = 1; }
+      break;
+    case FIN_ALPHA:
+      sc->pq = a;
+      if (!(a > 0.0)) { sc->status = TOMG_E_BREAKDOWN; sc->done = 1; break; }
+      sc->alpha = sc->rz / a;
+      break;
+    case FIN_RR:
+      sc->rr = a;
+      sc->it += 1;
+      if (a != a) { sc->status = TOMG_E_BREAKDOWN; sc->done = 1; }
+      else if (a <= sc->tol2) { sc->done = 1; }
+      else if (sc->it >= sc->max_iter) { sc->status = TOMG_NOT_CONVERGED; sc->done = 1; }
+      break;
+    case FIN_BETA:  // a = z.r (new), b = z.q
+      if (!(a > 0.0)) { sc->status = TOMG_E_BREAKDOWN; sc->done = 1; break; }
+      sc->rz_new = a;
+      sc->zq = b;
+      sc->beta = sc->flexible ? (-sc->alpha * b / sc->rz) : (a / sc->rz);
+      sc->rz = a;
+      break;
+  }
+}
+
+__global__ void __launch_bounds__(RED_THREADS) k_xr(double* __restrict__ x, double* __restrict__ r,
+                                                    const double* __restrict__ p,
+                                                    const double* __restrict__ q, int64_t n,
+                                                    const Scalars* sc, double* partials) {
+  __shared__ double sred[32];
+  if (sc->done) return;
+  const double alpha = sc->alpha;
+  double s = 0.0;
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+    x[i] += alpha * p[i];
+    const double ri = r[i] - alpha * q[i];
+    r[i] = ri;
+    s += ri * ri;
+  }
+  s = block_sum(s, sred);
+  if (threadIdx.x == 0) partials[blockIdx.x] = s;
+}
+
+__global__ void k_p(double* __restrict__ p, const double* __restrict__ z, int64_t n,
+                    const Scalars* sc) {
+  if (sc->done) return;
+  const double beta = sc->beta;
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+    p[i] = z[i] + beta * p[i];
+}
+
+template <class T>
+__global__ void __launch_bounds__(RED_THREADS) k_zdots(const T* __restrict__ z, double* z64,
+                                                       const double* __restrict__ r,
+                                                       const double* __restrict__ q, int64_t n,
+                                                       double* pa, double* pb, const int* done) {
+  __shared__ double sred[32];
+  if (solve_done(done)) return;
+  double a = 0.0, b = 0.0;
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+    const double zi = (double)z[i];
+    if ((const void*)z != (const void*)z64) z64[i] = zi;
+    a += zi * r[i];
+    if (q) b += zi * q[i];
+  }
+  a = block_sum(a, sred);
+  b = block_sum(b, sred);
+  if (threadIdx.x == 0) {
+    pa[blockIdx.x] = a;
+    if (pb) pb[blockIdx.x] = b;
+  }
+}
+
+template <class T>
+__global__ void k_cast_in(const double* __restrict__ a, T* __restrict__ b, int64_t n,
+                          const int* done) {
+  if (solve_done(done)) return;
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+    b[i] = (T)a[i];
+}
+
+__global__ void k_mask_vec(const double* __restrict__ f, double* __restrict__ b,
+                           const uint8_t* __restrict__ mask, int dim, int64_t nn) {
+  const int64_t node = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (node >= nn) return;
+  const unsigned m = mask[node];
+  for (int c = 0; c < dim; c++) b[dim * node + c] = ((m >> c) & 1u) ? 0.0 : f[dim * node + c];
+}
+
+template <class T, int B>
+__global__ void k_jacobi0(int64_t nodes, const T* __restrict__ Dinv, const T* __restrict__ b,
+                          T* __restrict__ x, T omega, const int* done) {
+  if (solve_done(done)) return;
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= nodes) return;
+  const T* D = Dinv + (int64_t)B * B * i;
+  T bv[B];
+#pragma unroll
+  for (int c = 0; c < B; c++) bv[c] = b[B * i + c];
+#pragma unroll
+  for (int r = 0; r < B; r++) {
+    T v = T(0);
+#pragma unroll
+    for (int c = 0; c < B; c++) v += D[r * B + c] * bv[c];
+    x[B * i + r] = omega * v;
+  }
+}
+
+template <class T>
+__global__ void k_gemv(int n, const T* __restrict__ A, const T* __restrict__ b, T* __restrict__ x,
+                       const int* done) {
+  if (solve_done(done)) return;
+  const int row = (blockIdx.x * blockDim.x + threadIdx.x) >> 5, lane = threadIdx.x & 31;
+  if (row >= n) return;
+  T s = T(0);
+  const T* a = A + (int64_t)row * n;
+  for (int c = lane; c < n; c += 32) s += a[c] * b[c];
+  for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+  if (lane == 0) x[row] = s;
+}
+
+// right-looking Cholesky, one launch per column k: L[:,k] from column k of the (updated) A,
+// trailing lower triangle updated with the rank-1 term
+__global__ void k_chol_col(int n, int k, double* A, double* L, int* fail) {
+  const double akk = A[(int64_t)k * n + k];
+  const int i = k + blockIdx.y * blockDim.y + threadIdx.y;
+  const int j = k + blockIdx.x * blockDim.x + threadIdx.x;
+  if (!(akk > 0.0)) {
+    if (i == k && j == k) atomicCAS(fail, 0, k + 1);
+    return;
+  }
+  if (i >= n || j > i) return;
+  if (j == k) {
+    L[(int64_t)i * n + k] = A[(int64_t)i * n + k] / sqrt(akk);
+    return;
+  }
+  A[(int64_t)i * n + j] -= A[(int64_t)i * n + k] * A[(int64_t)j * n + k] / akk;
+}
+
+// Linv = L^-1 (lower triangular), one thread per column
+__global__ void k_trinv(int n, const double* __restrict__ L, double* Li) {
+  const int c = blockIdx.x * blockDim.x + threadIdx.x;
+  if (c >= n) return;
+  for (int r = 0; r < c; r++) Li[(int64_t)r * n + c] = 0.0;
+  for (int r = c; r < n; r++) {
+    double v = (r == c) ? 1.0 : 0.0;
+    for (int t = c; t < r; t++) v -= L[(int64_t)r * n + t] * Li[(int64_t)t * n + c];
+    Li[(int64_t)r * n + c] = v / L[(int64_t)r * n + r];
+  }
+}
+
+// Ainv = Linv^T Linv, computed for i >= j and mirrored (exactly symmetric)
+__global__ void k_ltl(int n, const double* __restrict__ Li, double* Ainv) {
+  const int i = blockIdx.y * blockDim.y + threadIdx.y;
+  const int j = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n || j > i) return;
+  double v = 0.0;
+  for (int t = i; t < n; t++) v += Li[(int64_t)t * n + i] * Li[(int64_t)t * n + j];
+  Ainv[(int64_t)i * n + j] = v;
+  Ainv[(int64_t)j * n + i] = v;
+}
+
+__global__ void k_set_cond(cudaGraphConditionalHandle h, const Scalars* sc) {
+  cudaGraphSetConditional(h, sc->done ? 0u : 1u);
+}
+
+inline int grid_for(int64_t n) { return std::max(1, std::min(RED_MAX_BLOCKS, ceil_div(n, RED_THREADS * 4))); }
+
+}  // namespace
+
+int red_blocks(int64_t n) { return grid_for(n); }
+
+void dot_partials(cudaStream_t s, const double* x, const double* y, int64_t n, double* partials,
+                  const int* done) {
+  LAUNCH(k_dot, grid_for(n), RED_THREADS, 0, s, x, y, n, partials, done);
+}
+
+void finish(cudaStream_t s, int kind, const double* pa, int na, const double* pb, int nb,
+            Scalars* sc) {
+  LAUNCH(k_finish, 1, 1024, 0, s, kind, pa, na, pb, nb, sc);
+}
+
+void xr_update(cudaStream_t s, double* x, double* r, const double* p, const double* q, int64_t n,
+               const Scalars* sc, double* partials) {
+  LAUNCH(k_xr, grid_for(n), RED_THREADS, 0, s, x, r, p, q, n, sc, partials);
+}
+
+void p_update(cudaStream_t s, double* p, const double* z, int64_t n, const Scalars* sc) {
+  LAUNCH(k_p, grid_for(n), RED_THREADS, 0, s, p, z, n, sc);
+}
+
+template <class T>
+void z_dots(cudaStream_t s, const T* z, double* z64, const double* r, const double* q, int64_t n,
+            double* pa, double* pb, const int* done) {
+  LAUNCH((k_zdots<T>), grid_for(n), RED_THREADS, 0, s, z, z64, r, q, n, pa, pb, done);
+}
+template void z_dots<float>(cudaStream_t, const float*, double*, const double*, const double*,
+                            int64_t, double*, double*, const int*);
+template void z_dots<double>(cudaStream_t, const double*, double*, const double*, const double*,
+                             int64_t, double*, double*, const int*);
+
+template <class T>
+void cast_in(cudaStream_t s, const double* a, T* b, int64_t n, const int* done) {
+  LAUNCH((k_cast_in<T>), grid_for(n), RED_THREADS, 0, s, a, b, n, done);
+}
+template void cast_in<float>(cudaStream_t, const double*, float*, int64_t, const int*);
+template void cast_in<double>(cudaStream_t, const double*, double*, int64_t, const int*);
+
+void copy_f64(cudaStream_t s, const double* a, double* b, int64_t n, const int* done) {
+  cast_in<double>(s, a, b, n, done);
+}
+
+void mask_vec(cudaStream_t s, const double* f, double* b, const uint8_t* mask, int dim, int64_t nn) {
+  LAUNCH(k_mask_vec, ceil_div(nn, 256), 256, 0, s, f, b, mask, dim, nn);
+}
+
+template <class T>
+void jacobi0(cudaStream_t s, int bs, int64_t nodes, const T* Dinv, const T* b, T* x, double omega,
+             const int* done) {
+  const int g = ceil_div(nodes, 256);
+  if (bs == 2) LAUNCH((k_jacobi0<T, 2>), g, 256, 0, s, nodes, Dinv, b, x, (T)omega, done);
+  else if (bs == 3) LAUNCH((k_jacobi0<T, 3>), g, 256, 0, s, nodes, Dinv, b, x, (T)omega, done);
+  else if (bs == 6) LAUNCH((k_jacobi0<T, 6>), g, 256, 0, s, nodes, Dinv, b, x, (T)omega, done);
+  else TOMG_THROW(TOMG_E_INVALID, "unsupported block size %d", bs);
+}
+template void jacobi0<float>(cudaStream_t, int, int64_t, const float*, const float*, float*,
+                             double, const int*);
+template void jacobi0<double>(cudaStream_t, int, int64_t, const double*, const double*, double*,
+                              double, const int*);
+
+template <class T>
+void dense_gemv(cudaStream_t s, int n, const T* Ainv, const T* b, T* x, const int* done) {
+  LAUNCH((k_gemv<T>), ceil_div((int64_t)n * 32, 256), 256, 0, s, n, Ainv, b, x, done);
+}
+template void dense_gemv<float>(cudaStream_t, int, const float*, const float*, float*, const int*);
+template void dense_gemv<double>(cudaStream_t, int, const double*, const double*, double*,
+                                 const int*);
+
+int dense_spd_inverse(cudaStream_t s, int n, double* A, double* work) {
+  double* L = work;
+  double* Li = work + (size_t)n * n;
+  DBuf<int> fail;
+  fail.resize(1);
+  fail.zero(s);
+  CK(cudaMemsetAsync(L, 0, sizeof(double) * n * n, s));
+  for (int k = 0; k < n; k++) {
+    const int m = n - k;
+    dim3 blk(16, 16), grd(ceil_div(m, 16), ceil_div(m, 16));
+    LAUNCH(k_chol_col, grd, blk, 0, s, n, k, A, L, fail.p);
+  }
+  int f = 0;
+  CK(cudaMemcpyAsync(&f, fail.p, sizeof(int), cudaMemcpyDeviceToHost, s));
+  CK(cudaStreamSynchronize(s));
+  if (f) return f;
+  LAUNCH(k_trinv, ceil_div(n, 64), 64, 0, s, n, L, Li);
+  dim3 blk(16, 16), grd(ceil_div(n, 16), ceil_div(n, 16));
+  LAUNCH(k_ltl, grd, blk, 0, s, n, Li, A);
+  CK(cudaStreamSynchronize(s));
+  return 0;
+}
+
+void set_conditional(cudaStream_t s, cudaGraphConditionalHandle h, const Scalars* sc) {
+  LAUNCH(k_set_cond, 1, 1, 0, s, h, sc);
+}
+
+}  // namespace tomg

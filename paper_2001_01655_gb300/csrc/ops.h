@@ -1,0 +1,161 @@
+// Host-side launchers of the tomg kernels (one translation unit per kernel family).
+// All launches are asynchronous on the given stream; `done` (nullable) is the solve's
+// device flag: once it is set the solve-loop kernels return immediately.
+#pragma once
+
+#include "common.cuh"
+
+namespace tomg {
+
+enum OpMode { MODE_APPLY = 0, MODE_RESID = 1, MODE_JACOBI = 2 };
+
+// ---------------- level 0: matrix-free SIMP element-by-element operator ----------------
+// A = M (sum_e E_e Ke) M + (I - M), M = free-DOF mask (mask byte per node, bit c = DOF c
+// fixed).  MODE_APPLY y = A x; MODE_RESID y = b - A x; MODE_JACOBI y = x + w Dinv (b - A x).
+// dot_partials (nullable, MODE_APPLY only): one FP64 partial of x . y per block.
+struct Ebe {
+  int dim, nx, ny, nz;
+  const void* Ke;  // T[nd*nd], nd = dim * 2^dim
+  const void* E;   // T[n_elems]
+  const uint8_t* mask;
+};
+template <class T>
+void ebe_op(cudaStream_t s, int mode, const Ebe& op, const T* x, T* y, const T* b,
+            const T* Dinv, double omega, const int* done, double* dot_partials);
+int ebe_blocks(const Ebe& op);  // number of blocks (= number of dot partials) of ebe_op
+// point-block diagonal inverse of the level-0 operator, FP64 and FP32 copies
+void ebe_block_diag_inv(cudaStream_t s, const Ebe& op64, double* Dinv64, float* Dinv32);
+// level-0 operator assembled as a structured 3^dim stencil, FP64, SoA layout
+// S[((o * dim + r) * dim + c) * n_nodes + node], o = (ox+1) + 3 (oy+1) + 9 (oz+1)
+void ebe_assemble_stencil(cudaStream_t s, const Ebe& op64, double* S);
+// E = Emin + (E0 - Emin) rho^p in FP64 and FP32; *bad set to 1 if rho < 0 or NaN
+void simp_moduli(cudaStream_t s, int64_t nel, const double* rho, double E0, double Emin,
+                 double penal, double* E64, float* E32, int* bad);
+
+// ---------------- geometric levels: structured stencils and transfers -----------------
+struct Geo {
+  int dim, nx, ny, nz;  // element counts of this level (nz = 1 in 2D)
+  int64_t nodes() const { return (int64_t)(nx + 1) * (ny + 1) * (dim == 3 ? nz + 1 : 1); }
+};
+inline int stencil_q(int dim) { return dim == 3 ? 27 * 9 : 9 * 4; }
+template <class T>
+void stencil_op(cudaStream_t s, int mode, const Geo& g, const T* S, const T* x, T* y, const T* b,
+                const T* Dinv, double omega, const int* done);
+void stencil_block_diag_inv(cudaStream_t s, const Geo& g, const double* S, double* Dinv64,
+                            float* Dinv32);
+// Galerkin product with bilinear / trilinear P (coarse node I at fine position min(2I, n))
+void stencil_rap(cudaStream_t s, const Geo& fine, const Geo& coarse, const double* Sf, double* Sc);
+template <class T>
+void geo_restrict(cudaStream_t s, const Geo& fine, const Geo& coarse, const T* rf, T* bc,
+                  const int* done);
+template <class T>
+void geo_prolong_add(cudaStream_t s, const Geo& fine, const Geo& coarse, const T* xc, T* xf,
+                     const int* done);
+// stencil -> dense (n x n, row-major) and stencil -> BSR (two calls: counts then fill)
+void stencil_to_dense(cudaStream_t s, const Geo& g, const double* S, double* Adense);
+void stencil_row_counts(cudaStream_t s, const Geo& g, int* counts);
+void stencil_to_bsr(cudaStream_t s, const Geo& g, const double* S, const int* rowptr, int* col,
+                    double* val);
+// geometric prolongation as BSR (dim x dim blocks w I): counts then fill
+void geo_prolong_counts(cudaStream_t s, const Geo& fine, const Geo& coarse, int* counts);
+void geo_prolong_fill(cudaStream_t s, const Geo& fine, const Geo& coarse, const int* rowptr,
+                      int* col, double* val);
+
+// ---------------- block CSR (BSR) ------------------------------------------------------
+struct Bsr {
+  int nbr = 0, nbc = 0, br = 0, bc = 0;
+  int64_t nnzb = 0;
+  const int* rp = nullptr;
+  const int* ci = nullptr;
+};
+template <class T>
+void bsr_op(cudaStream_t s, int mode, const Bsr& A, const T* V, const T* x, T* y, const T* b,
+            const T* Dinv, double omega, const int* done);
+// y (+)= A x for rectangular blocks (transfers): accumulate = 1 adds into y
+template <class T>
+void bsr_spmv_rect(cudaStream_t s, const Bsr& A, const T* V, const T* x, T* y, int accumulate,
+                   const int* done);
+void bsr_block_diag_inv(cudaStream_t s, const Bsr& A, const double* V, double* Dinv64,
+                        float* Dinv32);
+void bsr_to_dense(cudaStream_t s, const Bsr& A, const double* V, double* Adense);
+// transpose: rowptr of A^T from column counts, then fill (rows of A^T sorted)
+void bsr_col_counts(cudaStream_t s, const Bsr& A, int* counts /* nbc, zeroed inside */);
+void bsr_transpose_fill(cudaStream_t s, const Bsr& A, const double* V, const int* rpT, int* ciT,
+                        double* VT, int* cursor /* nbc scratch */);
+// SpGEMM C = A B (FP64): symbolic counts, symbolic fill (sorted columns), numeric
+struct SpgemmWork {
+  DBuf<int> big, goff, gtable;  // per-row hash-table sizes / offsets for rows too long for smem
+};
+void spgemm_counts(cudaStream_t s, const Bsr& A, const Bsr& B, int* counts, SpgemmWork& w);
+void spgemm_fill(cudaStream_t s, const Bsr& A, const Bsr& B, const int* rpC, int* ciC,
+                 SpgemmWork& w);
+void spgemm_numeric(cudaStream_t s, const Bsr& A, const double* VA, const Bsr& B,
+                    const double* VB, const Bsr& C, double* VC);
+void cast_f64_f32(cudaStream_t s, const double* a, float* b, int64_t n);
+void cast_f32_f64(cudaStream_t s, const float* a, double* b, int64_t n);
+
+// ---------------- prefix sums --------------------------------------------------------
+// exclusive scan of n ints into out (n+1 entries; out[n] = total); returns total (syncs)
+int64_t exclusive_scan(cudaStream_t s, const int* in, int* out, int64_t n);
+
+// ---------------- smoothed aggregation ------------------------------------------------
+void amg_strength_counts(cudaStream_t s, const Bsr& A, const double* V, double beta, int* counts);
+void amg_strength_fill(cudaStream_t s, const Bsr& A, const double* V, double beta, const int* srp,
+                       int* sci);
+// distance-2 MIS rounds; returns number of rounds
+int amg_mis2(cudaStream_t s, int n, const int* srp, const int* sci, int level, int* state,
+             uint64_t* v, uint64_t* m1, int* flag_host_pinned, int* flag_dev);
+// aggregates from MIS-2 states: agg (n), returns number of aggregates
+int amg_aggregate(cudaStream_t s, int n, const int* srp, const int* sci, int level,
+                  const int* state, int* agg, int* root_scan);
+// tentative prolongator: T as BSR (one block per aggregated node), Bc (n_agg*k x k)
+void amg_tentative(cudaStream_t s, int n_nodes, int b, int k, int n_agg, const int* agg,
+                   const double* B, int* Trp, int* Tci, double* TV, double* Bc);
+// spectral radius of D^-1 A by power iteration (FP64), returns rho (syncs)
+double amg_spectral_radius(cudaStream_t s, const Bsr& A, const double* V, const double* Dinv,
+                           int level, int iters, double* v, double* w, double* partials);
+// P = T - omega Dinv (A T) on the pattern of AT
+void amg_smooth_prolongator(cudaStream_t s, const Bsr& AT, const double* ATV, const int* agg,
+                            const double* TV, const int* Trp, const double* Dinv, double omega,
+                            int b, double* PV);
+// coarse DOFs with an all-zero row get a unit diagonal
+void amg_fix_zero_rows(cudaStream_t s, const Bsr& A, double* V);
+// rigid-body modes at node coordinates (dim 2: 3 modes, dim 3: 6 modes), n x k row-major
+void rigid_body_modes(cudaStream_t s, const Geo& g, const double* xs, const double* ys,
+                      const double* zs, double* B);
+
+// ---------------- Krylov vectors, reductions, coarse solve -----------------------------
+struct Scalars {     // device-resident state of one outer solve
+  double bb, rr, rz, pq, zq, rz_new, alpha, beta, rtol2, tol2;
+  int done, it, status, max_iter, flexible, pad;
+};
+int red_blocks(int64_t n);
+void dot_partials(cudaStream_t s, const double* x, const double* y, int64_t n, double* partials,
+                  const int* done);
+// finish kernels (single block): combine partials and update the scalar state
+enum FinishKind { FIN_INIT = 0, FIN_RZ0 = 1, FIN_ALPHA = 2, FIN_RR = 3, FIN_BETA = 4 };
+void finish(cudaStream_t s, int kind, const double* partA, int nA, const double* partB, int nB,
+            Scalars* sc);
+void xr_update(cudaStream_t s, double* x, double* r, const double* p, const double* q, int64_t n,
+               const Scalars* sc, double* partials);
+void p_update(cudaStream_t s, double* p, const double* z, int64_t n, const Scalars* sc);
+// z64 = (double) z (T = float) or z itself; partials of z.r and z.q
+template <class T>
+void z_dots(cudaStream_t s, const T* z, double* z64, const double* r, const double* q, int64_t n,
+            double* partA, double* partB, const int* done);
+template <class T>
+void cast_in(cudaStream_t s, const double* a, T* b, int64_t n, const int* done);
+void copy_f64(cudaStream_t s, const double* a, double* b, int64_t n, const int* done);
+void mask_vec(cudaStream_t s, const double* f, double* b, const uint8_t* mask, int dim, int64_t nn);
+// x = w Dinv b (first Jacobi sweep from x = 0), block size bs
+template <class T>
+void jacobi0(cudaStream_t s, int bs, int64_t nodes, const T* Dinv, const T* b, T* x, double omega,
+             const int* done);
+// coarse solve x = Ainv b (dense GEMV)
+template <class T>
+void dense_gemv(cudaStream_t s, int n, const T* Ainv, const T* b, T* x, const int* done);
+// dense SPD inverse via Cholesky (FP64, in place: A -> A^-1); returns 0 or row of failure+1
+int dense_spd_inverse(cudaStream_t s, int n, double* A, double* work);
+void set_conditional(cudaStream_t s, cudaGraphConditionalHandle h, const Scalars* sc);
+
+}  // namespace tomg

@@ -1,0 +1,126 @@
+// Host runtime of the tomg library: problem state, hierarchy setup, V-cycle, outer Krylov
+// loop and its CUDA-graph capture.
+#pragma once
+
+#include <memory>
+
+#include "ops.h"
+
+struct tomg_ctx {
+  int device = 0;
+  cudaStream_t stream = nullptr;
+  bool own_stream = false;
+  int64_t launches0 = 0;
+};
+
+namespace tomg {
+
+enum LevelKind { KIND_EBE = 0, KIND_STENCIL = 1, KIND_BSR = 2 };
+
+struct Level {
+  int kind = KIND_EBE;
+  int b = 2;          // DOFs per node
+  int64_t nn = 0;     // nodes
+  int64_t n = 0;      // DOFs
+  Geo g{2, 0, 0, 1};  // geometric levels
+  bool geometric = false;
+  bool geo_next = false;  // transfer to the next level is geometric
+  // structured stencil (geometric levels >= 1; level 0 during setup)
+  DBuf<double> S64;
+  DBuf<float> S32;
+  // block CSR (AMG levels; the level an AMG part starts from, during setup)
+  DBuf<int> rp, ci;
+  DBuf<double> V64;
+  DBuf<float> V32;
+  int64_t nnzb = 0;
+  // point-block diagonal inverse
+  DBuf<double> D64;
+  DBuf<float> D32;
+  // algebraic transfer to the next level: P (n x nc) and R = P^T
+  int bc = 0;
+  DBuf<int> Prp, Pci, Rrp, Rci;
+  DBuf<double> Pv64, Rv64;
+  DBuf<float> Pv32, Rv32;
+  int64_t Pnnzb = 0;
+  DBuf<int> agg;
+  // V-cycle work vectors
+  DBuf<double> b64, x64, r64, y64;
+  DBuf<float> b32, x32, r32, y32;
+
+  Bsr bsr() const {
+    Bsr A;
+    A.nbr = A.nbc = (int)nn;
+    A.br = A.bc = b;
+    A.nnzb = nnzb;
+    A.rp = rp.p;
+    A.ci = ci.p;
+    return A;
+  }
+  Bsr Pmat(int64_t nn_next) const {
+    Bsr A;
+    A.nbr = (int)nn; A.nbc = (int)nn_next; A.br = b; A.bc = bc; A.nnzb = Pnnzb;
+    A.rp = Prp.p; A.ci = Pci.p;
+    return A;
+  }
+  Bsr Rmat(int64_t nn_next) const {
+    Bsr A;
+    A.nbr = (int)nn_next; A.nbc = (int)nn; A.br = bc; A.bc = b; A.nnzb = Pnnzb;
+    A.rp = Rrp.p; A.ci = Rci.p;
+    return A;
+  }
+};
+
+}  // namespace tomg
+
+struct tomg_problem {
+  tomg_ctx* ctx = nullptr;
+  int dim = 2, nx = 0, ny = 0, nz = 1;
+  double E0 = 1, Emin = 1e-9, penal = 3, nu = 0.3;
+  int64_t nn = 0, n = 0, nel = 0;
+  std::vector<double> Ke_host;
+  tomg::DBuf<double> Ke64;
+  tomg::DBuf<float> Ke32;
+  tomg::DBuf<uint8_t> mask;
+  bool have_density = false;
+  tomg::DBuf<double> rho, E64;
+  tomg::DBuf<float> E32;
+  // hierarchy
+  bool setup_valid = false;
+  tomg_options opt{};
+  double setup_ms = 0.0;
+  bool jacobi_only = false;
+  std::vector<std::unique_ptr<tomg::Level>> L;
+  int nc = 0;  // coarsest DOFs
+  tomg::DBuf<double> Ainv64;
+  tomg::DBuf<float> Ainv32;
+  // outer Krylov state (one right-hand side at a time)
+  tomg::DBuf<double> f, bvec, x, r, p, q, z, t;
+  tomg::DBuf<double> partA, partB, partE;
+  tomg::DBuf<tomg::Scalars> sc;
+  tomg::Scalars* sc_host = nullptr;  // pinned
+  int* flag_host = nullptr;          // pinned
+  tomg::DBuf<int> flag_dev;
+  // captured outer iteration
+  cudaGraph_t graph = nullptr;
+  cudaGraphExec_t gexec = nullptr;
+  int graph_mode = 0;         // 0 none, 1 one-iteration graph, 2 conditional while loop
+  int64_t kernels_per_iter = 0;
+  cudaEvent_t ev0 = nullptr, ev1 = nullptr;
+  ~tomg_problem();
+};
+
+namespace tomg {
+void problem_init(tomg_problem* P);
+void set_fixed(tomg_problem* P, const int64_t* dofs, int64_t count);
+void set_density(tomg_problem* P, const double* rho, int on_device);
+void setup(tomg_problem* P, const tomg_options& opt);
+tomg_status solve(tomg_problem* P, int nrhs, const double* f, double* u, int on_device,
+                  tomg_result* res);
+// single steps for parity checks
+void level_apply(tomg_problem* P, int level, int prec, const double* x, double* y);
+void vcycle_apply(tomg_problem* P, const double* r, double* z);
+void coarse_apply(tomg_problem* P, const double* b, double* x);
+void level_export(tomg_problem* P, int level, int64_t* nnzb, int64_t* rp, int64_t* ci, double* v);
+void prolong_export(tomg_problem* P, int level, int64_t* nnzb, int64_t* rp, int64_t* ci, double* v);
+void element_stiffness_host(int dim, double nu, std::vector<double>& Ke);
+}  // namespace tomg

@@ -1,0 +1,305 @@
+"""ctypes binding of the tomg C ABI (include/tomg.h): argument marshalling only.
+
+Every step of the solve runs in the CUDA library ``_build/libtomg.so``; this module converts
+numpy arrays (host) and torch CUDA tensors (device) to pointers and raises on error statuses.
+There is no fallback: if the library is missing or no GPU is present, calls raise.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+
+import numpy as np
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "_build", "libtomg.so")
+
+OK, NOT_CONVERGED, E_INVALID, E_OOM, E_CUDA, E_BREAKDOWN, E_TIMEOUT, E_BUDGET = 0, 1, -1, -2, -3, -4, -5, -6
+PC = {"gmg": 0, "amg": 1, "hybrid": 2, "jacobi": 3}
+PREC = {"fp64": 0, "fp32": 1}
+
+
+class TomgError(RuntimeError):
+    def __init__(self, status, msg):
+        super().__init__("tomg status %d: %s" % (status, msg))
+        self.status = status
+
+
+class Options(C.Structure):
+    _fields_ = [("pc", C.c_int), ("prec", C.c_int), ("rtol", C.c_double), ("max_iter", C.c_int),
+                ("n_levels", C.c_int), ("max_coarse_dofs", C.c_int), ("n_geo_levels", C.c_int),
+                ("smoother", C.c_int), ("omega", C.c_double), ("n_pre", C.c_int),
+                ("n_post", C.c_int), ("soc_beta", C.c_double), ("check_every", C.c_int),
+                ("use_graph", C.c_int), ("max_levels", C.c_int)]
+
+
+class Result(C.Structure):
+    _fields_ = [("iterations", C.c_int), ("rel_residual", C.c_double), ("compliance", C.c_double),
+                ("setup_ms", C.c_double), ("solve_ms", C.c_double), ("status", C.c_int)]
+
+    def as_dict(self):
+        return {k: getattr(self, k) for k, _ in self._fields_}
+
+
+class LevelInfo(C.Structure):
+    _fields_ = [("kind", C.c_int), ("block", C.c_int), ("n_nodes", C.c_int64),
+                ("n_dofs", C.c_int64), ("nnzb", C.c_int64), ("nx", C.c_int), ("ny", C.c_int),
+                ("nz", C.c_int), ("geometric", C.c_int)]
+
+
+_lib = None
+_P = C.c_void_p
+_D = C.POINTER(C.c_double)
+_I64 = C.POINTER(C.c_int64)
+
+_SIGS = {
+    "tomg_last_error": (C.c_char_p, []),
+    "tomg_options_default": (None, [C.POINTER(Options)]),
+    "tomg_ctx_create": (C.c_int, [C.POINTER(_P), C.c_int, _P]),
+    "tomg_ctx_destroy": (C.c_int, [_P]),
+    "tomg_kernel_launches": (C.c_int, [_P, _I64]),
+    "tomg_problem_create": (C.c_int, [_P, C.c_int, C.c_int, C.c_int, C.c_int, C.c_double,
+                                      C.c_double, C.c_double, C.c_double, C.POINTER(_P)]),
+    "tomg_problem_destroy": (C.c_int, [_P]),
+    "tomg_problem_sizes": (C.c_int, [_P, _I64, _I64, _I64]),
+    "tomg_set_fixed_dofs": (C.c_int, [_P, _I64, C.c_int64]),
+    "tomg_set_density": (C.c_int, [_P, _P, C.c_int]),
+    "tomg_setup": (C.c_int, [_P, C.POINTER(Options)]),
+    "tomg_solve": (C.c_int, [_P, C.c_int, _P, _P, C.c_int, C.POINTER(Result)]),
+    "tomg_num_levels": (C.c_int, [_P, C.POINTER(C.c_int)]),
+    "tomg_level_info_get": (C.c_int, [_P, C.c_int, C.POINTER(LevelInfo)]),
+    "tomg_level_export": (C.c_int, [_P, C.c_int, _I64, _P, _P, _P]),
+    "tomg_prolongation_export": (C.c_int, [_P, C.c_int, _I64, _P, _P, _P]),
+    "tomg_aggregates_export": (C.c_int, [_P, C.c_int, _P]),
+    "tomg_level_apply": (C.c_int, [_P, C.c_int, C.c_int, _P, _P, C.c_int]),
+    "tomg_vcycle": (C.c_int, [_P, _P, _P, C.c_int]),
+    "tomg_coarse_solve": (C.c_int, [_P, _P, _P, C.c_int]),
+    "tomg_moduli": (C.c_int, [_P, _P, C.c_int]),
+    "tomg_element_stiffness": (C.c_int, [_P, _P]),
+}
+
+
+def load(path: str = LIB_PATH):
+    """Load the CUDA library (raises if it has not been built)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(path):
+        raise RuntimeError("tomg CUDA library not built (%s); run paper_2001_01655_gb300.build" % path)
+    lib = C.CDLL(path)
+    for name, (res, args) in _SIGS.items():
+        fn = getattr(lib, name)
+        fn.restype = res
+        fn.argtypes = args
+    _lib = lib
+    return lib
+
+
+def _check(st, allow_not_converged=True):
+    if st == OK or (allow_not_converged and st == NOT_CONVERGED):
+        return st
+    raise TomgError(st, load().tomg_last_error().decode())
+
+
+def default_options(**kw) -> Options:
+    o = Options()
+    load().tomg_options_default(C.byref(o))
+    for k, v in kw.items():
+        if k == "pc" and isinstance(v, str):
+            v = PC[v]
+        if k == "prec" and isinstance(v, str):
+            v = PREC[v]
+        setattr(o, k, v)
+    return o
+
+
+def _is_torch(a):
+    return type(a).__module__.startswith("torch")
+
+
+def _ptr(a, dtype):
+    """(pointer, on_device, keepalive) for a numpy array or a torch tensor."""
+    if _is_torch(a):
+        import torch
+        want = torch.float64 if dtype == np.float64 else torch.int64
+        if a.dtype != want or not a.is_contiguous():
+            raise TypeError("expected a contiguous %s tensor" % want)
+        return C.c_void_p(a.data_ptr()), 1 if a.is_cuda else 0, a
+    arr = np.ascontiguousarray(a, dtype=dtype)
+    return C.c_void_p(arr.ctypes.data), 0, arr
+
+
+class Context:
+    """A device and a stream; ``stream`` may be a torch.cuda.Stream or a raw handle."""
+
+    def __init__(self, device: int = 0, stream=None):
+        lib = load()
+        h = C.c_void_p()
+        raw = None
+        if stream is not None:
+            raw = C.c_void_p(getattr(stream, "cuda_stream", stream))
+        _check(lib.tomg_ctx_create(C.byref(h), device, raw))
+        self.h = h
+        self.device = device
+
+    def kernel_launches(self) -> int:
+        v = C.c_int64()
+        _check(load().tomg_kernel_launches(self.h, C.byref(v)))
+        return v.value
+
+    def close(self):
+        if self.h:
+            load().tomg_ctx_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+class Problem:
+    """SIMP elasticity problem on a structured grid (Sec. 2.1)."""
+
+    def __init__(self, ctx: Context, dim, nx, ny, nz=1, E0=1.0, Emin=1e-9, penal=3.0, nu=0.3):
+        lib = load()
+        h = C.c_void_p()
+        _check(lib.tomg_problem_create(ctx.h, dim, nx, ny, nz, E0, Emin, penal, nu, C.byref(h)))
+        self.h, self.ctx = h, ctx
+        self.dim, self.nx, self.ny, self.nz = dim, nx, ny, nz
+        n, nn, ne = C.c_int64(), C.c_int64(), C.c_int64()
+        _check(lib.tomg_problem_sizes(h, C.byref(n), C.byref(nn), C.byref(ne)))
+        self.n, self.nn, self.nel = n.value, nn.value, ne.value
+        self.last_results = []
+
+    @classmethod
+    def from_workload(cls, ctx, p):
+        """Create from a :class:`workloads.Problem` (density and fixed DOFs set)."""
+        P = cls(ctx, p.dim, p.nx, p.ny, p.nz, p.E0, p.Emin, p.penal, p.nu)
+        P.set_fixed_dofs(p.fixed)
+        P.set_density(p.rho)
+        return P
+
+    def close(self):
+        if getattr(self, "h", None):
+            load().tomg_problem_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def set_fixed_dofs(self, dofs):
+        a = np.ascontiguousarray(np.asarray(dofs, dtype=np.int64).ravel())
+        _check(load().tomg_set_fixed_dofs(self.h, a.ctypes.data_as(_I64), len(a)))
+
+    def set_density(self, rho):
+        p, dev, keep = _ptr(rho, np.float64)
+        if not dev and np.asarray(keep).size != self.nel:
+            raise ValueError("density has %d entries, expected %d" % (np.asarray(keep).size, self.nel))
+        _check(load().tomg_set_density(self.h, p, dev))
+
+    def setup(self, opt: Options | None = None, **kw):
+        o = opt if opt is not None else default_options(**kw)
+        _check(load().tomg_setup(self.h, C.byref(o)))
+        self.opt = o
+
+    def solve(self, f, u0=None):
+        """Solve for right-hand sides f: numpy (nrhs, n) / (n,) on the host, or a CUDA tensor of
+        the same shape (device path).  Returns (u, [result dicts]); u has f's shape and kind."""
+        if _is_torch(f):
+            import torch
+            nrhs = 1 if f.dim() == 1 else f.shape[0]
+            u = torch.zeros_like(f) if u0 is None else u0.clone().contiguous()
+        else:
+            f = np.ascontiguousarray(f, dtype=np.float64)
+            nrhs = 1 if f.ndim == 1 else f.shape[0]
+            u = np.zeros_like(f) if u0 is None else np.array(u0, dtype=np.float64, copy=True)
+        fp, dev, keepf = _ptr(f, np.float64)
+        up, _, keepu = _ptr(u, np.float64)
+        res = (Result * max(nrhs, 1))()
+        st = load().tomg_solve(self.h, nrhs, fp, up, dev, res)
+        _check(st)
+        self.last_results = [res[i].as_dict() for i in range(nrhs)]
+        return u, self.last_results
+
+    # ---- introspection / single steps --------------------------------------------------
+    def num_levels(self):
+        v = C.c_int()
+        _check(load().tomg_num_levels(self.h, C.byref(v)))
+        return v.value
+
+    def level_info(self, level):
+        li = LevelInfo()
+        _check(load().tomg_level_info_get(self.h, level, C.byref(li)))
+        return {k: getattr(li, k) for k, _ in li._fields_}
+
+    def _bsr_export(self, fn, level, rows_blocks, br, bc):
+        import scipy.sparse as sp
+        nnzb = C.c_int64()
+        _check(fn(self.h, level, C.byref(nnzb), None, None, None))
+        nb = nnzb.value
+        rp = np.zeros(rows_blocks + 1, np.int64)
+        ci = np.zeros(max(nb, 1), np.int64)
+        val = np.zeros(max(nb, 1) * br * bc)
+        _check(fn(self.h, level, C.byref(nnzb), C.c_void_p(rp.ctypes.data),
+                  C.c_void_p(ci.ctypes.data), C.c_void_p(val.ctypes.data)))
+        return rp, ci[:nb], val[:nb * br * bc].reshape(nb, br, bc)
+
+    def level_matrix(self, level):
+        """Level operator as a scipy CSR matrix (FP64)."""
+        import scipy.sparse as sp
+        li = self.level_info(level)
+        b, nn = li["block"], li["n_nodes"]
+        rp, ci, val = self._bsr_export(load().tomg_level_export, level, nn, b, b)
+        return sp.bsr_matrix((val, ci, rp), shape=(nn * b, nn * b)).tocsr()
+
+    def prolongation(self, level):
+        import scipy.sparse as sp
+        li, lc = self.level_info(level), self.level_info(level + 1)
+        b, bc, nn = li["block"], lc["block"], li["n_nodes"]
+        rp, ci, val = self._bsr_export(load().tomg_prolongation_export, level, nn, b, bc)
+        return sp.bsr_matrix((val, ci, rp), shape=(nn * b, lc["n_nodes"] * bc)).tocsr()
+
+    def aggregates(self, level):
+        li = self.level_info(level)
+        a = np.zeros(li["n_nodes"], np.int64)
+        _check(load().tomg_aggregates_export(self.h, level, C.c_void_p(a.ctypes.data)))
+        return a
+
+    def _vec_call(self, fn, x, n_out, *pre):
+        if _is_torch(x):
+            import torch
+            y = torch.zeros(n_out, dtype=torch.float64, device=x.device)
+        else:
+            x = np.ascontiguousarray(x, dtype=np.float64)
+            y = np.zeros(n_out)
+        xp, dev, keepx = _ptr(x, np.float64)
+        yp, _, keepy = _ptr(y, np.float64)
+        _check(fn(self.h, *pre, xp, yp, dev))
+        return y
+
+    def level_apply(self, level, x, prec="fp64"):
+        li = self.level_info(level)
+        return self._vec_call(load().tomg_level_apply, x, li["n_dofs"], level, PREC.get(prec, prec))
+
+    def vcycle(self, r):
+        return self._vec_call(load().tomg_vcycle, r, self.n)
+
+    def coarse_solve(self, b):
+        nl = self.num_levels()
+        return self._vec_call(load().tomg_coarse_solve, b, self.level_info(nl - 1)["n_dofs"])
+
+    def moduli(self):
+        E = np.zeros(self.nel)
+        _check(load().tomg_moduli(self.h, C.c_void_p(E.ctypes.data), 0))
+        return E
+
+    def element_stiffness(self):
+        nd = self.dim * (1 << self.dim)
+        Ke = np.zeros((nd, nd))
+        _check(load().tomg_element_stiffness(self.h, C.c_void_p(Ke.ctypes.data)))
+        return Ke

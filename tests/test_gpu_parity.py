@@ -1,0 +1,217 @@
+"""GPU parity: every step of the CUDA path, called through the C ABI, against the CPU oracle on
+the same seeded inputs.  Tolerances: FP64 steps 1e-12 relative (rounding order only), FP32
+steps 1e-5 relative to the operator scale, solves: true relative residual <= 1e-8 and
+displacement / compliance relative error <= 1e-6 against the oracle's direct solve."""
+import numpy as np
+import pytest
+
+import workloads as W
+from oracle import amg, fem, gmg, mg, solve as osolve
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def ctx(lib):
+    return lib.Context(0)
+
+
+def make(lib, ctx, p):
+    return lib.Problem.from_workload(ctx, p)
+
+
+def relerr(a, b):
+    nb = np.linalg.norm(b)
+    return np.linalg.norm(np.asarray(a) - np.asarray(b)) / (nb if nb > 0 else 1.0)
+
+
+GRIDS = [(2, (37, 23, 1)), (2, (1, 1, 1)), (2, (2, 1, 1)), (2, (64, 33, 1)),
+         (3, (13, 7, 5)), (3, (1, 1, 1)), (3, (3, 2, 1)), (3, (9, 8, 7))]
+
+
+@pytest.mark.parametrize("dim", [2, 3])
+def test_element_stiffness(lib, ctx, dim):
+    P = lib.Problem(ctx, dim, 2, 2, 2)
+    assert np.abs(P.element_stiffness() - fem.element_stiffness(dim, 0.3)).max() < 1e-15
+
+
+def test_simp_moduli(lib, ctx):
+    p = W.random_problem(2, 31, 17, seed=3, contrast="minmax")
+    P = make(lib, ctx, p)
+    E = P.moduli()
+    ref = fem.simp(p.rho, p.E0, p.Emin, p.penal)
+    assert np.allclose(E, ref, rtol=1e-15, atol=0)
+
+
+@pytest.mark.parametrize("dim,grid", GRIDS)
+@pytest.mark.parametrize("prec", ["fp64", "fp32"])
+def test_fine_operator_apply(lib, ctx, dim, grid, prec):
+    p = W.random_problem(dim, *grid, seed=11, contrast="minmax")
+    P = make(lib, ctx, p)
+    P.setup(pc="jacobi")
+    A0 = mg.fine_operator(p)
+    x = np.random.default_rng(0).standard_normal(p.n)
+    y = P.level_apply(0, x, prec)
+    ref = A0 @ x
+    scale = abs(A0) @ np.abs(x)  # |A| |x|: the rounding scale of every entry
+    tol = 1e-13 if prec == "fp64" else 2e-6
+    assert np.all(np.abs(y - ref) <= tol * scale + 1e-300)
+
+
+@pytest.mark.parametrize("dim,grid,L", [(2, (37, 23, 1), 4), (2, (20, 10, 1), 3),
+                                         (3, (9, 7, 5), 3), (3, (8, 8, 8), 3)])
+def test_gmg_hierarchy(lib, ctx, dim, grid, L):
+    p = W.random_problem(dim, *grid, seed=12, contrast="threshold")
+    P = make(lib, ctx, p)
+    P.setup(pc="gmg", n_levels=L)
+    H = osolve.build(p, pc="gmg", n_levels=L)
+    assert P.num_levels() == L
+    for l in range(L):
+        Ag = P.level_matrix(l)
+        Ar = H.A[l]
+        d = abs(Ag - Ar)
+        assert d.max() <= 1e-13 * abs(Ar).max(), l
+        if l < L - 1:
+            Pg = P.prolongation(l)
+            assert abs(Pg - H.P[l]).max() == 0.0
+        x = np.random.default_rng(l).standard_normal(Ar.shape[0])
+        assert relerr(P.level_apply(l, x, "fp64"), Ar @ x) < 1e-13
+        assert relerr(P.level_apply(l, x, "fp32"), Ar @ x) < 1e-5
+
+
+@pytest.mark.parametrize("pc,kw", [("gmg", dict(n_levels=3)), ("amg", dict(max_coarse_dofs=80)),
+                                   ("hybrid", dict(n_geo_levels=2, max_coarse_dofs=80))])
+@pytest.mark.parametrize("dim,grid", [(2, (30, 14, 1)), (3, (8, 6, 5))])
+def test_vcycle(lib, ctx, pc, kw, dim, grid):
+    p = W.random_problem(dim, *grid, seed=13, contrast="minmax")
+    P = make(lib, ctx, p)
+    P.setup(pc=pc, prec="fp64", **kw)
+    if pc == "gmg":
+        H = osolve.build(p, pc="gmg", n_levels=kw["n_levels"])
+    elif pc == "amg":
+        H = osolve.build(p, pc="amg", cap=kw["max_coarse_dofs"])
+    else:
+        H = osolve.build(p, pc="hybrid", n_geo=kw["n_geo_levels"], cap=kw["max_coarse_dofs"])
+    assert P.num_levels() == H.n_levels
+    r = np.random.default_rng(1).standard_normal(p.n)
+    z = P.vcycle(r)
+    zr = mg.vcycle(H, r)
+    assert relerr(z, zr) < 1e-9
+    P.setup(pc=pc, prec="fp32", **kw)
+    assert relerr(P.vcycle(r), zr) < 1e-3
+    # coarsest-level direct solve
+    nc = H.A[-1].shape[0]
+    bc = np.random.default_rng(2).standard_normal(nc)
+    assert relerr(P.coarse_solve(bc), np.linalg.solve(H.A[-1].toarray(), bc)) < 1e-8
+
+
+@pytest.mark.parametrize("dim,grid", [(2, (30, 14, 1)), (2, (45, 21, 1)), (3, (8, 6, 5))])
+def test_amg_setup_parity(lib, ctx, dim, grid):
+    p = W.random_problem(dim, *grid, seed=14, contrast="threshold")
+    P = make(lib, ctx, p)
+    P.setup(pc="amg", max_coarse_dofs=60)
+    A0 = mg.fine_operator(p)
+    B = fem.rigid_body_modes(dim, fem.node_coords(dim, p.nx, p.ny, p.nz))
+    lev = amg.sa_level(A0, B, dim, 0)
+    agg = P.aggregates(0)
+    assert np.array_equal(agg, lev["agg"])  # bit-exact aggregates
+    Pg = P.prolongation(0)
+    assert abs(Pg - lev["P"]).max() <= 1e-11 * abs(lev["P"]).max()
+    Ac = P.level_matrix(1)
+    assert abs(Ac - lev["Ac"]).max() <= 1e-10 * abs(lev["Ac"]).max()
+
+
+@pytest.mark.parametrize("pc,kw,okw", [
+    ("gmg", dict(n_levels=4), dict(n_levels=4)),
+    ("amg", dict(max_coarse_dofs=200), dict(cap=200)),
+    ("hybrid", dict(n_geo_levels=2, max_coarse_dofs=200), dict(n_geo=2, cap=200))])
+@pytest.mark.parametrize("prec", ["fp64", "fp32"])
+@pytest.mark.parametrize("case", ["mbb", "cant2d", "cant3d"])
+def test_solve_vs_direct(lib, ctx, pc, kw, okw, prec, case):
+    if case == "mbb":
+        p = W.mbb_beam(96, 32)
+    elif case == "cant2d":
+        p = W.cantilever_2d(96, 48, seed=0, sigma=4.0)
+    else:
+        p = W.cantilever_3d(16, 8, 8, seed=0, sigma=2.0)
+    P = make(lib, ctx, p)
+    P.setup(pc=pc, prec=prec, rtol=1e-8, **kw)
+    u, res = P.solve(p.f)
+    ref = osolve.direct(p)
+    r = res[0]
+    assert r["status"] == 0, r
+    A0 = mg.fine_operator(p)
+    b = fem.free_mask(p.n, p.fixed) * p.f[0]
+    true_rel = np.linalg.norm(b - A0 @ u[0]) / np.linalg.norm(b)
+    assert true_rel <= 1.05e-8 and r["rel_residual"] <= 1e-8
+    assert relerr(u, ref["u"]) <= 1e-6
+    assert abs(r["compliance"] - ref["compliance"][0]) <= 1e-6 * abs(ref["compliance"][0])
+    if prec == "fp64" and pc == "gmg":
+        # same hierarchy, same algorithm: iteration counts agree up to rounding drift, which a
+        # 1e9-contrast problem accumulates over a few hundred iterations (1 %)
+        o = osolve.solve(p, pc="gmg", **okw)
+        oi = int(o["iterations"][0])
+        assert abs(oi - r["iterations"]) <= max(1, int(0.01 * oi))
+
+
+def test_zero_rhs_and_warm_start(lib, ctx):
+    p = W.mbb_beam(48, 16)
+    P = make(lib, ctx, p)
+    P.setup(pc="gmg", n_levels=3)
+    u, res = P.solve(np.zeros_like(p.f))
+    assert res[0]["iterations"] == 0 and np.all(u == 0) and res[0]["status"] == 0
+    u, res = P.solve(p.f)
+    u2, res2 = P.solve(p.f, u0=u)
+    assert res2[0]["iterations"] <= 1
+    assert relerr(u2, u) < 1e-7
+
+
+def test_multi_rhs_and_device_path(lib, ctx):
+    import torch
+    p = W.random_problem(2, 40, 20, seed=15, contrast="minmax", nrhs=3)
+    P = make(lib, ctx, p)
+    P.setup(pc="gmg", n_levels=3, prec="fp32")
+    U, res = P.solve(p.f)
+    assert len(res) == 3
+    for j in range(3):
+        u1, _ = P.solve(p.f[j])
+        assert relerr(U[j], u1) < 1e-12
+    ft = torch.tensor(p.f, dtype=torch.float64, device="cuda:0")
+    Ud, resd = P.solve(ft)
+    assert relerr(Ud.cpu().numpy(), U) < 1e-12
+    ref = osolve.direct(p)
+    assert relerr(U, ref["u"]) < 1e-6
+
+
+def test_invalid_inputs(lib, ctx):
+    p = W.mbb_beam(8, 4)
+    P = lib.Problem(ctx, 2, 8, 4)
+    with pytest.raises(lib.TomgError) as e:
+        P.set_fixed_dofs([P.n])
+    assert e.value.status == lib.E_INVALID
+    rho = p.rho.copy()
+    rho[3] = np.nan
+    with pytest.raises(lib.TomgError):
+        P.set_density(rho)
+    rho[3] = -0.1
+    with pytest.raises(lib.TomgError):
+        P.set_density(rho)
+    P.set_density(p.rho)
+    with pytest.raises(lib.TomgError):
+        P.solve(p.f)  # no setup yet
+    with pytest.raises(lib.TomgError):
+        lib.Problem(ctx, 4, 8, 4)
+    with pytest.raises(lib.TomgError):
+        P.setup(pc="gmg", omega=3.0)
+
+
+@pytest.mark.parametrize("use_graph", [0, 1, 2])
+def test_graph_modes_identical(lib, ctx, use_graph):
+    p = W.cantilever_2d(64, 32, seed=1, sigma=3.0)
+    P = make(lib, ctx, p)
+    P.setup(pc="gmg", n_levels=4, prec="fp32", use_graph=0)
+    u0, r0 = P.solve(p.f)
+    P.setup(pc="gmg", n_levels=4, prec="fp32", use_graph=use_graph)
+    u1, r1 = P.solve(p.f)
+    assert r0[0]["iterations"] == r1[0]["iterations"]
+    assert np.array_equal(u0, u1)  # deterministic reductions: bit-identical

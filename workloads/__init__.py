@@ -113,6 +113,8 @@ def _members(field_: np.ndarray, volfrac: float, plate: int = 2) -> np.ndarray:
 
 def _minmax(field_: np.ndarray, lo: float) -> np.ndarray:
     a, b = field_.min(), field_.max()
+    if b == a:  # single element: uniform solid
+        return np.ones_like(field_)
     return lo + (1.0 - lo) * (field_ - a) / (b - a)
 
 
