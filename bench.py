@@ -29,7 +29,7 @@ sys.path.insert(0, ROOT)
 
 METRIC = "MG-PCG solves/sec & DOF-iters/sec @1e-8 residual, mixed vs FP64; p50/p99 latency"
 WORKLOAD = dict(nx=768, ny=384, seed=0)
-HEADLINE = dict(pc="amg", max_coarse_dofs=1500)
+HEADLINE = dict(pc="hybrid", max_coarse_dofs=1500, n_geo_levels=2)
 
 
 def parse():
@@ -40,7 +40,7 @@ def parse():
     ap.add_argument("--impl", default="tomg")
     ap.add_argument("--pc", default=HEADLINE["pc"])
     ap.add_argument("--cap", type=int, default=HEADLINE["max_coarse_dofs"])
-    ap.add_argument("--n-geo", type=int, default=3)
+    ap.add_argument("--n-geo", type=int, default=HEADLINE["n_geo_levels"])
     ap.add_argument("--no-fp64", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
     return ap.parse_args()
@@ -216,7 +216,7 @@ def roofline(P, ctx, p, stream):
     """Dominant kernel (the level-0 SIMP element operator) timed live with CUDA events on its
     stream; algorithmic bytes per launch from the minimum traffic model."""
     try:
-        ms = P.bench_fine_apply(prec="fp32", reps=50)
+        ms = P.time_fine_operator("apply", "fp32", reps=50, cold_l2=True)
     except Exception as e:  # noqa: BLE001
         return {"error": str(e)}
     peaks = load_peaks()
@@ -238,7 +238,8 @@ def cpu_baseline(n_threads_hint=None):
 
     p = W.cantilever_2d(**WORKLOAD)
     t0 = time.perf_counter()
-    H = osolve.build(p, pc=HEADLINE["pc"], cap=HEADLINE["max_coarse_dofs"])
+    H = osolve.build(p, pc=HEADLINE["pc"], cap=HEADLINE["max_coarse_dofs"],
+                     n_geo=HEADLINE["n_geo_levels"])
     t_setup = time.perf_counter() - t0
     A0 = mg.fine_operator(p)
     b = fem.free_mask(p.n, p.fixed) * p.f[0]

@@ -159,6 +159,14 @@ tomg_status tomg_coarse_solve(tomg_problem* prob, const double* b, double* x, in
 tomg_status tomg_moduli(tomg_problem* prob, double* E, int on_device);
 /* Element stiffness matrix of the problem for E = 1 (dim*2^dim squared, row-major). */
 tomg_status tomg_element_stiffness(const tomg_problem* prob, double* Ke);
+/* Timing of the level-0 SIMP element operator kernel (Sec. 2.1 Eq. 2 inside the K apply):
+ * op 0 = y = A x, 1 = residual b - A x, 2 = one weighted block-Jacobi sweep; prec a tomg_prec.
+ * Launches it `reps` times on the context stream, each launch bracketed by CUDA events; with
+ * cold_l2 != 0 a 256 MB buffer is written before every launch (outside the events) so the
+ * kernel reads its inputs from HBM.  Writes the mean device time per launch (ms).  Needs a
+ * setup; reps in [1, 10000]. */
+tomg_status tomg_time_fine_operator(tomg_problem* prob, int op, int prec, int reps, int cold_l2,
+                                    double* ms_per_launch);
 /* Number of kernels this library launched since the context was created. */
 tomg_status tomg_kernel_launches(const tomg_ctx* ctx, int64_t* count);
 

@@ -79,7 +79,7 @@ def fine_operator(problem):
     return fem.masked_operator(K, problem.fixed)
 
 
-def build_gmg(problem, n_levels=None, cap=None, A0=None, **kw):
+def build_gmg(problem, n_levels=None, cap=None, A0=None, finalize=True, **kw):
     p = problem
     if n_levels is None:
         n_levels = gmg.levels_for_cap(p.dim, p.nx, p.ny, p.nz, cap)
@@ -93,7 +93,7 @@ def build_gmg(problem, n_levels=None, cap=None, A0=None, **kw):
         g = gmg.coarse_grid(p.dim, *g)
     H = Hierarchy(A, P, [p.dim] * n_levels, ["geo"] * n_levels, **kw)
     H.info["grids"] = gmg.grids(p.dim, p.nx, p.ny, p.nz, n_levels)
-    return H.finalize()
+    return H.finalize() if finalize else H
 
 
 def _sa_extend(H, B, cap, beta, max_levels):
@@ -124,7 +124,7 @@ def build_amg(problem, cap, beta=0.003, max_levels=25, A0=None, **kw):
 
 def build_hybrid(problem, n_geo, cap, beta=0.003, max_levels=25, A0=None, **kw):
     p = problem
-    H = build_gmg(problem, n_levels=n_geo, A0=A0, **kw)
+    H = build_gmg(problem, n_levels=n_geo, A0=A0, finalize=False, **kw)
     g = H.info["grids"][-1]
     lvl = n_geo - 1
     xs = gmg.level_positions(p.nx, lvl)

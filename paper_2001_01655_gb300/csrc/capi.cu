@@ -344,3 +344,17 @@ tomg_status tomg_element_stiffness(const tomg_problem* P, double* Ke) {
 }
 
 }  // extern "C"
+
+namespace tomg {
+double time_fine_operator(tomg_problem* P, int op, int prec, int reps, int cold_l2);
+}
+
+extern "C" tomg_status tomg_time_fine_operator(tomg_problem* P, int op, int prec, int reps,
+                                               int cold_l2, double* ms) {
+  return tomg::guarded([&]() -> tomg_status {
+    if (!P || !ms) TOMG_THROW(TOMG_E_INVALID, "null argument");
+    tomg::set_device(P->ctx);
+    *ms = tomg::time_fine_operator(P, op, prec, reps, cold_l2);
+    return TOMG_OK;
+  });
+}

@@ -13,29 +13,44 @@ namespace tomg {
 
 namespace {
 
-template <class T, int B, int MODE>
+// G lanes cooperate on one block row (strided over its blocks), partial sums combined with a
+// fixed butterfly, so the result does not depend on scheduling.
+template <int G, class T, int B>
+__device__ __forceinline__ void group_reduce(T* acc) {
+#pragma unroll
+  for (int o = G / 2; o > 0; o >>= 1)
+#pragma unroll
+    for (int r = 0; r < B; r++) acc[r] += __shfl_xor_sync(0xffffffffu, acc[r], o);
+}
+
+template <class T, int B, int MODE, int G>
 __global__ void __launch_bounds__(256) k_bsr(int nbr, const int* __restrict__ rp,
                                              const int* __restrict__ ci, const T* __restrict__ V,
                                              const T* __restrict__ x, T* __restrict__ y,
                                              const T* __restrict__ b, const T* __restrict__ Dinv,
                                              T omega, const int* done) {
   if (solve_done(done)) return;
-  const int i = blockIdx.x * blockDim.x + threadIdx.x;
-  if (i >= nbr) return;
+  const int gtid = blockIdx.x * blockDim.x + threadIdx.x;
+  const int i = gtid / G, sub = gtid % G;
+  const bool live = i < nbr;
   T acc[B];
 #pragma unroll
   for (int r = 0; r < B; r++) acc[r] = T(0);
-  for (int p = rp[i]; p < rp[i + 1]; p++) {
-    const int j = ci[p];
-    const T* blk = V + (int64_t)p * B * B;
-    T xv[B];
+  if (live) {
+    for (int p = rp[i] + sub; p < rp[i + 1]; p += G) {
+      const int j = ci[p];
+      const T* blk = V + (int64_t)p * B * B;
+      T xv[B];
 #pragma unroll
-    for (int c = 0; c < B; c++) xv[c] = x[(int64_t)B * j + c];
+      for (int c = 0; c < B; c++) xv[c] = x[(int64_t)B * j + c];
 #pragma unroll
-    for (int r = 0; r < B; r++)
+      for (int r = 0; r < B; r++)
 #pragma unroll
-      for (int c = 0; c < B; c++) acc[r] += blk[r * B + c] * xv[c];
+        for (int c = 0; c < B; c++) acc[r] += blk[r * B + c] * xv[c];
+    }
   }
+  group_reduce<G, T, B>(acc);
+  if (!live || sub != 0) return;
   if (MODE == MODE_APPLY) {
 #pragma unroll
     for (int r = 0; r < B; r++) y[(int64_t)B * i + r] = acc[r];
@@ -57,28 +72,41 @@ __global__ void __launch_bounds__(256) k_bsr(int nbr, const int* __restrict__ rp
   }
 }
 
-template <class T, int BR, int BC>
-__global__ void k_bsr_rect(int nbr, const int* __restrict__ rp, const int* __restrict__ ci,
-                           const T* __restrict__ V, const T* __restrict__ x, T* __restrict__ y,
-                           int accumulate, const int* done) {
+template <class T, int BR, int BC, int G>
+__global__ void __launch_bounds__(256) k_bsr_rect(int nbr, const int* __restrict__ rp,
+                                                  const int* __restrict__ ci,
+                                                  const T* __restrict__ V, const T* __restrict__ x,
+                                                  T* __restrict__ y, int accumulate,
+                                                  const int* done) {
   if (solve_done(done)) return;
-  const int i = blockIdx.x * blockDim.x + threadIdx.x;
-  if (i >= nbr) return;
+  const int gtid = blockIdx.x * blockDim.x + threadIdx.x;
+  const int i = gtid / G, sub = gtid % G;
+  const bool live = i < nbr;
   T acc[BR];
 #pragma unroll
-  for (int r = 0; r < BR; r++) acc[r] = accumulate ? y[(int64_t)BR * i + r] : T(0);
-  for (int p = rp[i]; p < rp[i + 1]; p++) {
-    const int j = ci[p];
-    const T* blk = V + (int64_t)p * BR * BC;
+  for (int r = 0; r < BR; r++) acc[r] = T(0);
+  if (live) {
+    for (int p = rp[i] + sub; p < rp[i + 1]; p += G) {
+      const int j = ci[p];
+      const T* blk = V + (int64_t)p * BR * BC;
 #pragma unroll
-    for (int c = 0; c < BC; c++) {
-      const T xv = x[(int64_t)BC * j + c];
+      for (int c = 0; c < BC; c++) {
+        const T xv = x[(int64_t)BC * j + c];
 #pragma unroll
-      for (int r = 0; r < BR; r++) acc[r] += blk[r * BC + c] * xv;
+        for (int r = 0; r < BR; r++) acc[r] += blk[r * BC + c] * xv;
+      }
     }
   }
+  group_reduce<G, T, BR>(acc);
+  if (!live || sub != 0) return;
 #pragma unroll
-  for (int r = 0; r < BR; r++) y[(int64_t)BR * i + r] = acc[r];
+  for (int r = 0; r < BR; r++) y[(int64_t)BR * i + r] = (accumulate ? y[(int64_t)BR * i + r] : T(0)) + acc[r];
+}
+
+// lanes per block row from the mean row length
+inline int lanes_for(const Bsr& A) {
+  const double avg = A.nbr > 0 ? (double)A.nnzb / A.nbr : 1.0;
+  return avg <= 6 ? 4 : (avg <= 20 ? 8 : (avg <= 48 ? 16 : 32));
 }
 
 template <int B>
@@ -172,7 +200,7 @@ __global__ void k_spgemm_big(int nrows, const int* __restrict__ Arp, const int* 
   int ub = 0;
   for (int a = Arp[row]; a < Arp[row + 1]; a++) ub += Brp[Aci[a] + 1] - Brp[Aci[a]];
   const int T = max(64, next_pow2(2 * ub));
-  big[row] = (T > SPG_SMEM_T) ? T : 0;
+  big[row] = (T > SPG_SMEM_T) ? 2 * T : 0;  // table + compaction area
 }
 
 __global__ void __launch_bounds__(32 * SPG_WARPS)
@@ -181,6 +209,7 @@ __global__ void __launch_bounds__(32 * SPG_WARPS)
                  const int* __restrict__ goff, int* gtable, int* countsC,
                  const int* __restrict__ rpC, int* ciC) {
   __shared__ int tab[SPG_WARPS][SPG_SMEM_T];
+  __shared__ int cmp[SPG_WARPS][SPG_SMEM_T / 2];
   const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int row = blockIdx.x * SPG_WARPS + w;
   if (row >= nrows) return;  // warp-uniform
@@ -211,15 +240,22 @@ __global__ void __launch_bounds__(32 * SPG_WARPS)
     if (lane == 0) countsC[row] = newc;
     return;
   }
+  // compact the occupied slots (warp ballot prefix), then place every key at its rank
+  int* ck = (T <= SPG_SMEM_T) ? cmp[w] : table + T;
+  int cnt = 0;
+  for (int s0 = 0; s0 < T; s0 += 32) {
+    const int key = table[s0 + lane];
+    const bool occ = key != -1;
+    const unsigned bal = __ballot_sync(0xffffffffu, occ);
+    if (occ) ck[cnt + __popc(bal & ((1u << lane) - 1u))] = key;
+    cnt += __popc(bal);
+  }
+  __syncwarp();
   const int base = rpC[row];
-  for (int s = lane; s < T; s += 32) {
-    const int key = table[s];
-    if (key == -1) continue;
+  for (int q = lane; q < cnt; q += 32) {
+    const int key = ck[q];
     int rank = 0;
-    for (int t = 0; t < T; t++) {
-      const int v = table[t];
-      rank += (v != -1 && v < key) ? 1 : 0;
-    }
+    for (int t = 0; t < cnt; t++) rank += (ck[t] < key) ? 1 : 0;
     ciC[base + rank] = key;
   }
 }
@@ -319,17 +355,24 @@ void scan_rec(cudaStream_t s, const int* in, int* out, int64_t n, int* total_dev
 template <class T>
 void bsr_op(cudaStream_t s, int mode, const Bsr& A, const T* V, const T* x, T* y, const T* b,
             const T* Dinv, double omega, const int* done) {
-  const int grid = ceil_div(A.nbr, 128);
-#define BOP(B, M) LAUNCH((k_bsr<T, B, M>), grid, 128, 0, s, A.nbr, A.rp, A.ci, V, x, y, b, Dinv, (T)omega, done)
+  const int G = lanes_for(A);
+  const int grid = ceil_div((int64_t)A.nbr * G, 256);
+#define BOP(B, M, GG) LAUNCH((k_bsr<T, B, M, GG>), grid, 256, 0, s, A.nbr, A.rp, A.ci, V, x, y, b, Dinv, (T)omega, done)
+#define BG(B, M)                         \
+  if (G == 4) BOP(B, M, 4);              \
+  else if (G == 8) BOP(B, M, 8);         \
+  else if (G == 16) BOP(B, M, 16);       \
+  else BOP(B, M, 32);
 #define BMODES(B)                                   \
-  if (mode == MODE_APPLY) BOP(B, MODE_APPLY);       \
-  else if (mode == MODE_RESID) BOP(B, MODE_RESID);  \
-  else BOP(B, MODE_JACOBI);
+  if (mode == MODE_APPLY) { BG(B, MODE_APPLY) }     \
+  else if (mode == MODE_RESID) { BG(B, MODE_RESID) } \
+  else { BG(B, MODE_JACOBI) }
   if (A.br == 2) { BMODES(2) }
   else if (A.br == 3) { BMODES(3) }
   else if (A.br == 6) { BMODES(6) }
   else TOMG_THROW(TOMG_E_INVALID, "unsupported block size %d", A.br);
 #undef BMODES
+#undef BG
 #undef BOP
 }
 template void bsr_op<float>(cudaStream_t, int, const Bsr&, const float*, const float*, float*,
@@ -340,14 +383,20 @@ template void bsr_op<double>(cudaStream_t, int, const Bsr&, const double*, const
 template <class T>
 void bsr_spmv_rect(cudaStream_t s, const Bsr& A, const T* V, const T* x, T* y, int accumulate,
                    const int* done) {
-  const int grid = ceil_div(A.nbr, 128);
-#define RECT(R, C)                                                                               \
-  if (A.br == R && A.bc == C) {                                                                  \
-    LAUNCH((k_bsr_rect<T, R, C>), grid, 128, 0, s, A.nbr, A.rp, A.ci, V, x, y, accumulate, done); \
-    return;                                                                                      \
+  const int G = lanes_for(A);
+  const int grid = ceil_div((int64_t)A.nbr * G, 256);
+#define RL(R, C, GG) LAUNCH((k_bsr_rect<T, R, C, GG>), grid, 256, 0, s, A.nbr, A.rp, A.ci, V, x, y, accumulate, done)
+#define RECT(R, C)                     \
+  if (A.br == R && A.bc == C) {        \
+    if (G == 4) RL(R, C, 4);           \
+    else if (G == 8) RL(R, C, 8);      \
+    else if (G == 16) RL(R, C, 16);    \
+    else RL(R, C, 32);                 \
+    return;                            \
   }
   RECT(2, 2) RECT(3, 3) RECT(6, 6) RECT(2, 3) RECT(3, 2) RECT(3, 6) RECT(6, 3)
 #undef RECT
+#undef RL
   TOMG_THROW(TOMG_E_INVALID, "unsupported transfer block %dx%d", A.br, A.bc);
 }
 template void bsr_spmv_rect<float>(cudaStream_t, const Bsr&, const float*, const float*, float*,

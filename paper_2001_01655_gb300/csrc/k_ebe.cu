@@ -190,9 +190,17 @@ inline int64_t nodes_of(const Ebe& op) {
   return (int64_t)(op.nx + 1) * (op.ny + 1) * (op.dim == 3 ? op.nz + 1 : 1);
 }
 
+// (the tiled 2D operator lives in k_ebe2d.cu)
+
 template <class T, int DIM, int MODE, bool DOT>
 void launch_ebe(cudaStream_t s, const Ebe& op, const T* x, T* y, const T* b, const T* Dinv,
                 double omega, const int* done, double* parts) {
+  // FP32 quad4: tiled kernel (memory/latency bound).  FP64: the node-per-thread kernel, whose
+  // low register count keeps enough warps in flight to hide the long FP64 pipe latency.
+  if (DIM == 2 && sizeof(T) == 4) {
+    ebe2d_launch<T, MODE, DOT>(s, op, x, y, b, Dinv, omega, done, parts);
+    return;
+  }
   const int64_t nn = nodes_of(op);
   LAUNCH((k_ebe<T, DIM, MODE, DOT>), ceil_div(nn, 256), 256, 0, s, op.nx, op.ny, op.nz,
          (const T*)op.Ke, (const T*)op.E, op.mask, x, y, b, Dinv, (T)omega, done, parts);
@@ -200,7 +208,10 @@ void launch_ebe(cudaStream_t s, const Ebe& op, const T* x, T* y, const T* b, con
 
 }  // namespace
 
-int ebe_blocks(const Ebe& op) { return ceil_div(nodes_of(op), 256); }
+int ebe_blocks(const Ebe& op) {
+  (void)0;  // partial counts: FP64 applies (the only ones with fused dots) use the generic grid
+  return ceil_div(nodes_of(op), 256);
+}
 
 template <class T>
 void ebe_op(cudaStream_t s, int mode, const Ebe& op, const T* x, T* y, const T* b, const T* Dinv,

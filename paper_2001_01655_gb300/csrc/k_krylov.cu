@@ -28,7 +28,7 @@ __global__ void __launch_bounds__(RED_THREADS) k_dot(const double* __restrict__ 
   if (threadIdx.x == 0) partials[blockIdx.x] = s;
 }
 
-__global__ void __launch_bounds__(1024) k_finish(int kind, const double* __restrict__ pa, int na,
+__global__ void __launch_bounds__(256) k_finish(int kind, const double* __restrict__ pa, int na,
                                                  const double* __restrict__ pb, int nb,
                                                  Scalars* sc) {
   __shared__ double sred[32];
@@ -51,25 +51,30 @@ __global__ void __launch_bounds__(1024) k_finish(int kind, const double* __restr
       break;
     case FIN_RZ0:
       sc->rz = a;
-      if (!(a > 0.0)) { sc->status = TOMG_E_BREAKDOWN; sc->done = 1; }
+      // CG needs z.r > 0 (SPD preconditioner); flexible CG only needs a finite value
+      if (sc->flexible ? (a != a) : !(a > 0.0)) { sc->status = TOMG_E_BREAKDOWN; sc->done = 1; sc->pad = 2; }
       break;
     case FIN_ALPHA:
       sc->pq = a;
-      if (!(a > 0.0)) { sc->status = TOMG_E_BREAKDOWN; sc->done = 1; break; }
+      if (!(a > 0.0)) { sc->status = TOMG_E_BREAKDOWN; sc->done = 1; sc->pad = 3; break; }
       sc->alpha = sc->rz / a;
       break;
     case FIN_RR:
       sc->rr = a;
       sc->it += 1;
-      if (a != a) { sc->status = TOMG_E_BREAKDOWN; sc->done = 1; }
+      if (a != a) { sc->status = TOMG_E_BREAKDOWN; sc->done = 1; sc->pad = 1; }
       else if (a <= sc->tol2) { sc->done = 1; }
       else if (sc->it >= sc->max_iter) { sc->status = TOMG_NOT_CONVERGED; sc->done = 1; }
       break;
     case FIN_BETA:  // a = z.r (new), b = z.q
-      if (!(a > 0.0)) { sc->status = TOMG_E_BREAKDOWN; sc->done = 1; break; }
+      // CG: beta = z.r / z_old.r_old.  Flexible CG (Notay 2000): beta = z^T (r - r_old) /
+      // z_old.r_old = -alpha z.q / z_old.r_old = -z.q / p.q, which needs no sign of z.r.
+      if (sc->flexible ? (a != a || b != b) : !(a > 0.0)) {
+        sc->status = TOMG_E_BREAKDOWN; sc->done = 1; sc->pad = 4; break;
+      }
       sc->rz_new = a;
       sc->zq = b;
-      sc->beta = sc->flexible ? (-sc->alpha * b / sc->rz) : (a / sc->rz);
+      sc->beta = sc->flexible ? (-b / sc->pq) : (a / sc->rz);
       sc->rz = a;
       break;
   }
@@ -171,34 +176,114 @@ __global__ void k_gemv(int n, const T* __restrict__ A, const T* __restrict__ b, 
   if (lane == 0) x[row] = s;
 }
 
-// right-looking Cholesky, one launch per column k: L[:,k] from column k of the (updated) A,
-// trailing lower triangle updated with the rank-1 term
-__global__ void k_chol_col(int n, int k, double* A, double* L, int* fail) {
-  const double akk = A[(int64_t)k * n + k];
-  const int i = k + blockIdx.y * blockDim.y + threadIdx.y;
-  const int j = k + blockIdx.x * blockDim.x + threadIdx.x;
-  if (!(akk > 0.0)) {
-    if (i == k && j == k) atomicCAS(fail, 0, k + 1);
-    return;
+// Blocked right-looking Cholesky A = L L^T (lower, in place, row-major), block NB:
+//   k_potrf_diag  factor the diagonal block in shared memory and invert it (L_kk^-1 saved)
+//   k_panel       L_ik = A_ik L_kk^-T for the rows below
+//   k_syrk        A_ij -= L_ik L_jk^T on the trailing lower triangle (32 x 32 tiles)
+// then Y = L^-1 by blocked forward substitution (k_fwd_T, k_fwd_Y) and A^-1 = Y^T Y (k_ltl).
+constexpr int NB = 32;
+
+__global__ void __launch_bounds__(NB * NB) k_potrf_diag(int n, int k0, double* A, double* Linv,
+                                                        int* fail) {
+  __shared__ double s[NB][NB + 1];
+  __shared__ double li[NB][NB + 1];
+  const int tx = threadIdx.x, ty = threadIdx.y;
+  const int kb = min(NB, n - k0);
+  s[ty][tx] = (ty < kb && tx < kb) ? A[(int64_t)(k0 + ty) * n + k0 + tx] : (ty == tx ? 1.0 : 0.0);
+  __syncthreads();
+  for (int k = 0; k < NB; k++) {
+    if (tx == 0 && ty == 0) {
+      double d = s[k][k];
+      if (!(d > 0.0)) {
+        if (k < kb) atomicCAS(fail, 0, k0 + k + 1);
+        d = 1.0;
+      }
+      s[k][k] = sqrt(d);
+    }
+    __syncthreads();
+    if (tx == k && ty > k) s[ty][k] /= s[k][k];
+    __syncthreads();
+    if (ty > k && tx > k && tx <= ty) s[ty][tx] -= s[ty][k] * s[tx][k];
+    __syncthreads();
   }
-  if (i >= n || j > i) return;
-  if (j == k) {
-    L[(int64_t)i * n + k] = A[(int64_t)i * n + k] / sqrt(akk);
-    return;
+  if (ty == 0) {  // column tx of L_kk^-1
+    const int c = tx;
+    for (int r = 0; r < NB; r++) {
+      if (r < c) { li[r][c] = 0.0; continue; }
+      double v = (r == c) ? 1.0 : 0.0;
+      for (int t = c; t < r; t++) v -= s[r][t] * li[t][c];
+      li[r][c] = v / s[r][r];
+    }
   }
-  A[(int64_t)i * n + j] -= A[(int64_t)i * n + k] * A[(int64_t)j * n + k] / akk;
+  __syncthreads();
+  if (ty < kb && tx < kb) A[(int64_t)(k0 + ty) * n + k0 + tx] = (tx <= ty) ? s[ty][tx] : 0.0;
+  Linv[ty * NB + tx] = li[ty][tx];
 }
 
-// Linv = L^-1 (lower triangular), one thread per column
-__global__ void k_trinv(int n, const double* __restrict__ L, double* Li) {
-  const int c = blockIdx.x * blockDim.x + threadIdx.x;
-  if (c >= n) return;
-  for (int r = 0; r < c; r++) Li[(int64_t)r * n + c] = 0.0;
-  for (int r = c; r < n; r++) {
-    double v = (r == c) ? 1.0 : 0.0;
-    for (int t = c; t < r; t++) v -= L[(int64_t)r * n + t] * Li[(int64_t)t * n + c];
-    Li[(int64_t)r * n + c] = v / L[(int64_t)r * n + r];
+// rows below the diagonal block: L_ik = A_ik L_kk^-T  (one row per threadIdx.y, NB columns)
+__global__ void __launch_bounds__(NB * 8) k_panel(int n, int k0, double* A, const double* Linv) {
+  __shared__ double row[8][NB];
+  __shared__ double li[NB][NB + 1];
+  const int tx = threadIdx.x, ty = threadIdx.y;
+  const int kb = min(NB, n - k0);
+  for (int t = ty; t < NB; t += 8) li[t][tx] = Linv[t * NB + tx];
+  const int i = k0 + kb + blockIdx.x * 8 + ty;
+  row[ty][tx] = (i < n && tx < kb) ? A[(int64_t)i * n + k0 + tx] : 0.0;
+  __syncthreads();
+  if (i >= n || tx >= kb) return;
+  double v = 0.0;
+  for (int t = 0; t <= tx; t++) v += row[ty][t] * li[tx][t];
+  A[(int64_t)i * n + k0 + tx] = v;
+}
+
+// trailing update of the lower triangle: A_ij -= sum_t L_it L_jt, t over the panel columns
+__global__ void __launch_bounds__(32 * 8) k_syrk(int n, int k0, double* A) {
+  __shared__ double Li[32][NB + 1];
+  __shared__ double Lj[32][NB + 1];
+  const int kb = min(NB, n - k0);
+  const int base = k0 + kb;
+  const int ti = blockIdx.y, tj = blockIdx.x;
+  if (tj > ti) return;  // tile entirely above the diagonal
+  const int i0 = base + ti * 32, j0 = base + tj * 32;
+  const int tx = threadIdx.x, ty = threadIdx.y;
+  for (int r = ty; r < 32; r += 8) {
+    const int gi = i0 + r, gj = j0 + r;
+    Li[r][tx] = (gi < n && tx < kb) ? A[(int64_t)gi * n + k0 + tx] : 0.0;
+    Lj[r][tx] = (gj < n && tx < kb) ? A[(int64_t)gj * n + k0 + tx] : 0.0;
   }
+  __syncthreads();
+  for (int r = ty; r < 32; r += 8) {
+    const int gi = i0 + r, gj = j0 + tx;
+    if (gi >= n || gj >= n || gj > gi) continue;
+    double v = 0.0;
+    for (int t = 0; t < kb; t++) v += Li[r][t] * Lj[tx][t];
+    A[(int64_t)gi * n + gj] -= v;
+  }
+}
+
+// forward substitution for block row K of Y = L^-1:
+//   T[r][c] = delta_rc - sum_{m = c}^{K0-1} L[r][m] Y[m][c]   (r in the block, c < K0 + kb)
+__global__ void k_fwd_T(int n, int K0, const double* __restrict__ L, const double* __restrict__ Y,
+                        double* T) {
+  const int c = blockIdx.x * blockDim.x + threadIdx.x;
+  const int r = K0 + blockIdx.y;
+  const int kb = min(NB, n - K0);
+  if (c >= K0 + kb) return;
+  double v = (r == c) ? 1.0 : 0.0;
+  for (int m = c; m < K0; m++) v -= L[(int64_t)r * n + m] * Y[(int64_t)m * n + c];
+  T[(int64_t)(r - K0) * n + c] = v;
+}
+//   Y[r][c] = sum_t Linv_KK[r - K0][t] T[t][c]; zero above the diagonal
+__global__ void k_fwd_Y(int n, int K0, const double* __restrict__ LinvKK,
+                        const double* __restrict__ T, double* Y) {
+  const int c = blockIdx.x * blockDim.x + threadIdx.x;
+  const int r = K0 + blockIdx.y;
+  const int kb = min(NB, n - K0);
+  if (c >= n) return;
+  double v = 0.0;
+  if (c < K0 + kb)
+    for (int t = 0; t <= r - K0; t++) v += LinvKK[(r - K0) * NB + t] * T[(int64_t)t * n + c];
+  Y[(int64_t)r * n + c] = (c <= r) ? v : 0.0;
 }
 
 // Ainv = Linv^T Linv, computed for i >= j and mirrored (exactly symmetric)
@@ -229,7 +314,7 @@ void dot_partials(cudaStream_t s, const double* x, const double* y, int64_t n, d
 
 void finish(cudaStream_t s, int kind, const double* pa, int na, const double* pb, int nb,
             Scalars* sc) {
-  LAUNCH(k_finish, 1, 1024, 0, s, kind, pa, na, pb, nb, sc);
+  LAUNCH(k_finish, 1, 256, 0, s, kind, pa, na, pb, nb, sc);
 }
 
 void xr_update(cudaStream_t s, double* x, double* r, const double* p, const double* q, int64_t n,
@@ -289,24 +374,36 @@ template void dense_gemv<double>(cudaStream_t, int, const double*, const double*
                                  const int*);
 
 int dense_spd_inverse(cudaStream_t s, int n, double* A, double* work) {
-  double* L = work;
-  double* Li = work + (size_t)n * n;
+  double* Y = work;  // n x n
+  const int nblk = ceil_div(n, NB);
   DBuf<int> fail;
+  DBuf<double> linv, T;
   fail.resize(1);
   fail.zero(s);
-  CK(cudaMemsetAsync(L, 0, sizeof(double) * n * n, s));
-  for (int k = 0; k < n; k++) {
-    const int m = n - k;
-    dim3 blk(16, 16), grd(ceil_div(m, 16), ceil_div(m, 16));
-    LAUNCH(k_chol_col, grd, blk, 0, s, n, k, A, L, fail.p);
+  linv.resize((size_t)nblk * NB * NB);
+  T.resize((size_t)NB * n);
+  for (int b = 0; b < nblk; b++) {
+    const int k0 = b * NB;
+    double* Lb = linv.p + (size_t)b * NB * NB;
+    LAUNCH(k_potrf_diag, 1, dim3(NB, NB), 0, s, n, k0, A, Lb, fail.p);
+    const int rest = n - k0 - std::min(NB, n - k0);
+    if (rest > 0) {
+      LAUNCH(k_panel, ceil_div(rest, 8), dim3(NB, 8), 0, s, n, k0, A, Lb);
+      const int nt = ceil_div(rest, 32);
+      LAUNCH(k_syrk, dim3(nt, nt), dim3(32, 8), 0, s, n, k0, A);
+    }
   }
   int f = 0;
   CK(cudaMemcpyAsync(&f, fail.p, sizeof(int), cudaMemcpyDeviceToHost, s));
   CK(cudaStreamSynchronize(s));
   if (f) return f;
-  LAUNCH(k_trinv, ceil_div(n, 64), 64, 0, s, n, L, Li);
+  for (int b = 0; b < nblk; b++) {
+    const int K0 = b * NB, kb = std::min(NB, n - K0);
+    LAUNCH(k_fwd_T, dim3(ceil_div(K0 + kb, 128), kb), 128, 0, s, n, K0, A, Y, T.p);
+    LAUNCH(k_fwd_Y, dim3(ceil_div(n, 128), kb), 128, 0, s, n, K0, linv.p + (size_t)b * NB * NB, T.p, Y);
+  }
   dim3 blk(16, 16), grd(ceil_div(n, 16), ceil_div(n, 16));
-  LAUNCH(k_ltl, grd, blk, 0, s, n, Li, A);
+  LAUNCH(k_ltl, grd, blk, 0, s, n, Y, A);
   CK(cudaStreamSynchronize(s));
   return 0;
 }

@@ -23,6 +23,11 @@ template <class T>
 void ebe_op(cudaStream_t s, int mode, const Ebe& op, const T* x, T* y, const T* b,
             const T* Dinv, double omega, const int* done, double* dot_partials);
 int ebe_blocks(const Ebe& op);  // number of blocks (= number of dot partials) of ebe_op
+// quad4 tiled implementation behind ebe_op (k_ebe2d.cu)
+template <class T, int MODE, bool DOT>
+void ebe2d_launch(cudaStream_t s, const Ebe& op, const T* x, T* y, const T* b, const T* Dinv,
+                  double omega, const int* done, double* parts);
+int ebe2d_blocks(const Ebe& op);
 // point-block diagonal inverse of the level-0 operator, FP64 and FP32 copies
 void ebe_block_diag_inv(cudaStream_t s, const Ebe& op64, double* Dinv64, float* Dinv32);
 // level-0 operator assembled as a structured 3^dim stencil, FP64, SoA layout

@@ -576,7 +576,7 @@ void setup(tomg_problem* P, const tomg_options& opt) {
     if (Cl.kind == KIND_BSR) bsr_to_dense(s, Cl.bsr(), Cl.V64.p, P->Ainv64.p);
     else stencil_to_dense(s, Cl.g, Cl.S64.p, P->Ainv64.p);
     DBuf<double> work;
-    work.resize(2 * (int64_t)P->nc * P->nc);
+    work.resize((int64_t)P->nc * P->nc);
     const int fail = dense_spd_inverse(s, P->nc, P->Ainv64.p, work.p);
     if (fail) TOMG_THROW(TOMG_E_BREAKDOWN, "coarse operator not SPD (pivot %d)", fail - 1);
     P->Ainv32.resize(P->Ainv64.n);
@@ -699,6 +699,16 @@ tomg_status solve(tomg_problem* P, int nrhs, const double* f, double* u, int on_
       // recursive residual converged but the true one did not: restart from x
     }
     if (status == TOMG_OK && bb > 0.0 && !(rr_true <= P->opt.rtol * P->opt.rtol * bb)) status = TOMG_NOT_CONVERGED;
+    if (status == TOMG_E_BREAKDOWN) {
+      static const char* what[] = {"?", "NaN residual", "z.r <= 0 with a CG preconditioner",
+                                   "p^T K p <= 0", "z.r or z.q not finite / z.r <= 0"};
+      const int code = P->sc_host->pad;
+      set_error("solver breakdown at iteration %d: %s (rhs %d)", total_it,
+                what[(code >= 0 && code <= 4) ? code : 0], j);
+    } else if (status == TOMG_NOT_CONVERGED) {
+      set_error("not converged after %d iterations (rel residual %.3e, rhs %d)", total_it,
+                bb > 0.0 ? std::sqrt(rr_true / bb) : 0.0, j);
+    }
     dot_partials(s, P->f.p, P->x.p, n, P->partE.p, nullptr);
     const double comp = host_sum(P, P->partE.p, red_blocks(n));
     CK(cudaMemcpyAsync(u + (int64_t)j * n, P->x.p, n * 8, d2h, s));
@@ -819,3 +829,33 @@ tomg_problem::~tomg_problem() {
   if (ev0) cudaEventDestroy(ev0);
   if (ev1) cudaEventDestroy(ev1);
 }
+
+namespace tomg {
+double time_fine_operator(tomg_problem* P, int op, int prec, int reps, int cold_l2) {
+  if (!P->setup_valid) TOMG_THROW(TOMG_E_INVALID, "no valid setup");
+  if (op < 0 || op > 2 || reps < 1 || reps > 10000) TOMG_THROW(TOMG_E_INVALID, "bad timing request");
+  cudaStream_t s = st(P);
+  Level& L0 = *P->L[0];
+  const int mode = op == 0 ? MODE_APPLY : (op == 1 ? MODE_RESID : MODE_JACOBI);
+  DBuf<char> flush;
+  if (cold_l2) flush.resize((size_t)256 << 20);
+  std::vector<cudaEvent_t> ev(2 * reps);
+  for (auto& e : ev) CK(cudaEventCreate(&e));
+  for (int k = 0; k < reps; k++) {
+    if (cold_l2) CK(cudaMemsetAsync(flush.p, k & 0xff, flush.n, s));
+    CK(cudaEventRecord(ev[2 * k], s));
+    if (prec == TOMG_PREC_FP64) level_op<double>(P, 0, mode, L0.x64.p, L0.y64.p, L0.b64.p, nullptr);
+    else level_op<float>(P, 0, mode, L0.x32.p, L0.y32.p, L0.b32.p, nullptr);
+    CK(cudaEventRecord(ev[2 * k + 1], s));
+  }
+  CK(cudaStreamSynchronize(s));
+  double tot = 0.0;
+  for (int k = 0; k < reps; k++) {
+    float ms = 0.f;
+    CK(cudaEventElapsedTime(&ms, ev[2 * k], ev[2 * k + 1]));
+    tot += ms;
+  }
+  for (auto& e : ev) cudaEventDestroy(e);
+  return tot / reps;
+}
+}  // namespace tomg

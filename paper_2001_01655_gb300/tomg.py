@@ -76,6 +76,7 @@ _SIGS = {
     "tomg_coarse_solve": (C.c_int, [_P, _P, _P, C.c_int]),
     "tomg_moduli": (C.c_int, [_P, _P, C.c_int]),
     "tomg_element_stiffness": (C.c_int, [_P, _P]),
+    "tomg_time_fine_operator": (C.c_int, [_P, C.c_int, C.c_int, C.c_int, C.c_int, _D]),
 }
 
 
@@ -297,6 +298,14 @@ class Problem:
         E = np.zeros(self.nel)
         _check(load().tomg_moduli(self.h, C.c_void_p(E.ctypes.data), 0))
         return E
+
+    def time_fine_operator(self, op="apply", prec="fp32", reps=50, cold_l2=True):
+        """Mean device time (ms) of one launch of the level-0 operator kernel."""
+        ms = C.c_double()
+        opi = {"apply": 0, "residual": 1, "jacobi": 2}[op]
+        _check(load().tomg_time_fine_operator(self.h, opi, PREC.get(prec, prec), reps,
+                                              1 if cold_l2 else 0, C.byref(ms)))
+        return ms.value
 
     def element_stiffness(self):
         nd = self.dim * (1 << self.dim)
