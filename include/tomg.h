@@ -167,6 +167,23 @@ tomg_status tomg_element_stiffness(const tomg_problem* prob, double* Ke);
  * setup; reps in [1, 10000]. */
 tomg_status tomg_time_fine_operator(tomg_problem* prob, int op, int prec, int reps, int cold_l2,
                                     double* ms_per_launch);
+/* Allocation-free y = A_0 x with FP32 arithmetic: the same computation as
+ * tomg_level_apply(prob, 0, TOMG_PREC_FP32_VCYCLE, x, y, 1), for callers that must not
+ * allocate device memory where they apply the operator (memory owned by another allocator,
+ * loops that cannot take the device-wide synchronisation of cudaFree).  The paper has no
+ * counterpart; this is a library service.
+ *   x, y      device arrays of n_dofs doubles (on the context's device), caller-owned
+ *   limits    n_dofs <= 1,048,576, else TOMG_E_INVALID with a message; needs a density
+ *             (tomg_set_density), not a tomg_setup
+ *   memory    allocates nothing: the FP32 copies of x and A x live in one fixed 8 MiB
+ *             __device__ array that every GPU loading the library keeps until process exit.
+ *             The first call on a device looks up that array's address (cudaGetSymbolAddress);
+ *             make that first call before any stream capture.
+ *   ordering  asynchronous on the context stream; y is ready once that stream is synchronised.
+ *             All calls share the array: calls that overlap on the GPU (other streams, other
+ *             contexts on the same device) race and must be serialised by the caller.
+ *             Every array entry a call reads is written earlier in the same call. */
+tomg_status tomg_fine_apply_f32_noalloc(tomg_problem* prob, const double* x, double* y);
 /* Number of kernels this library launched since the context was created. */
 tomg_status tomg_kernel_launches(const tomg_ctx* ctx, int64_t* count);
 

@@ -77,6 +77,7 @@ _SIGS = {
     "tomg_moduli": (C.c_int, [_P, _P, C.c_int]),
     "tomg_element_stiffness": (C.c_int, [_P, _P]),
     "tomg_time_fine_operator": (C.c_int, [_P, C.c_int, C.c_int, C.c_int, C.c_int, _D]),
+    "tomg_fine_apply_f32_noalloc": (C.c_int, [_P, _P, _P]),
 }
 
 
@@ -298,6 +299,16 @@ class Problem:
         E = np.zeros(self.nel)
         _check(load().tomg_moduli(self.h, C.c_void_p(E.ctypes.data), 0))
         return E
+
+    def fine_apply_f32_noalloc(self, x, y):
+        """y = A_0 x in FP32 arithmetic without any device allocation (x, y: contiguous float64
+        CUDA tensors of n_dofs entries).  Asynchronous on the context stream."""
+        xp, dx, _ = _ptr(x, np.float64)
+        yp, dy, _ = _ptr(y, np.float64)
+        if not (dx and dy):
+            raise TypeError("x and y must be CUDA tensors")
+        _check(load().tomg_fine_apply_f32_noalloc(self.h, xp, yp))
+        return y
 
     def time_fine_operator(self, op="apply", prec="fp32", reps=50, cold_l2=True):
         """Mean device time (ms) of one launch of the level-0 operator kernel."""
