@@ -98,6 +98,22 @@ class Clocks:
                 "samples": len(self.rows)}
 
 
+def max_over_ranks(value: float, world: int, device="cpu") -> float:
+    """Largest per-rank value (the slowest rank's time) across the process group."""
+    if world <= 1:
+        return float(value)
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([float(value)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def throughput(units_per_rank: int, world: int, total_ms: float) -> float:
+    """Whole-job rate: the units all ranks processed divided by the slowest rank's time."""
+    return world * units_per_rank / (total_ms / 1e3)
+
+
 def load_peaks():
     try:
         return json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
@@ -158,15 +174,11 @@ def run_gpu(args, rank, world, local):
 
     with Clocks(local) as clk:
         times, its, results, launches = timed("fp32", args.steps, args.warmup)
-    total_ms = sum(times)
-    if world > 1:
-        t = torch.tensor([total_ms], device=dev)
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        total_ms = float(t.item())
+    total_ms = max_over_ranks(sum(times), world, device=dev)
     bad = [r for r in results if r["status"] != 0 or r["rel_residual"] > 1e-8]
     out = {
         "metric": METRIC,
-        "value": world * args.steps / (total_ms / 1e3),
+        "value": throughput(args.steps, world, total_ms),
         "unit": "solves/s",
         "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
         "ms_per_step": total_ms / args.steps,

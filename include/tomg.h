@@ -72,6 +72,7 @@ typedef struct {
   int check_every;     /* outer iterations between host convergence polls          4        */
   int use_graph;       /* capture the outer iteration in a CUDA graph              1        */
   int max_levels;      /* cap on the number of levels                              25       */
+  int concurrency;     /* solve slots: right-hand sides solved concurrently        4        */
 } tomg_options;
 
 typedef struct {
@@ -132,6 +133,36 @@ tomg_status tomg_setup(tomg_problem* prob, const tomg_options* opt);
  * iterations.  Requires a setup for the current density (E_INVALID otherwise). */
 tomg_status tomg_solve(tomg_problem* prob, int nrhs, const double* f, double* u, int on_device,
                        tomg_result* results);
+
+/* ---- serving: continuous batching of design updates ---------------------------------------
+ * The paper's optimisation loop solves the same kind of system once per design iteration,
+ * warm-started from the previous displacements (Sec. 4).  A server runs such requests for many
+ * problems at once: `max_slots` worker threads take requests in arrival order as soon as a
+ * slot is free and the request's estimated device footprint fits `hbm_budget_bytes`; each
+ * problem runs on its own stream, so requests in flight overlap on the GPU.  A problem's
+ * updates are applied in submission order, never two at a time.  Its previous solution stays
+ * on the device and is the next update's initial guess.  Results are independent of the mix
+ * (fixed-order reductions, private buffers).  Destroy the server before its problems. */
+typedef struct tomg_server tomg_server;
+tomg_status tomg_server_create(tomg_ctx* ctx, size_t hbm_budget_bytes, int max_slots,
+                               tomg_server** out);
+/* One design update: rho (n_elems doubles, host) and f (n_dofs x nrhs column-major, host) are
+ * copied; u (host, nullable) receives the solution when the request completes.  opt = NULL
+ * uses the defaults.  E_BUDGET if the request alone exceeds the budget. */
+tomg_status tomg_server_submit(tomg_server* srv, tomg_problem* prob, const double* rho, int nrhs,
+                               const double* f, double* u, const tomg_options* opt,
+                               uint64_t* ticket);
+/* Waits for a ticket (timeout_ms < 0: no limit); E_TIMEOUT if it is still running after the
+ * limit (the ticket stays valid), E_INVALID for an unknown ticket.  results: nrhs entries.
+ * Returns the request's status. */
+tomg_status tomg_server_wait(tomg_server* srv, uint64_t ticket, int timeout_ms,
+                             tomg_result* results);
+/* Request latency percentiles (submission to completion), completed requests per second
+ * (first submission to last completion), and the peak concurrency / estimated bytes in flight. */
+tomg_status tomg_server_stats(tomg_server* srv, double* p50_ms, double* p99_ms,
+                              double* solves_per_s, int64_t* completed, int* peak_active,
+                              size_t* peak_bytes);
+tomg_status tomg_server_destroy(tomg_server* srv);
 
 /* ---- hierarchy introspection and single steps (parity checking) ------------------------- */
 tomg_status tomg_num_levels(const tomg_problem* prob, int* n_levels);

@@ -7,7 +7,7 @@
 
 namespace tomg {
 
-int64_t g_launches = 0;
+std::atomic<int64_t> g_launches{0};
 static thread_local char g_err[1024] = "";
 
 void set_error(const char* fmt, ...) {
@@ -17,6 +17,10 @@ void set_error(const char* fmt, ...) {
   va_end(ap);
 }
 const char* get_error() { return g_err; }
+
+static thread_local cudaStream_t g_alloc_stream = nullptr;
+cudaStream_t alloc_stream() { return g_alloc_stream; }
+void set_alloc_stream(cudaStream_t s) { g_alloc_stream = s; }
 
 int num_sms() {
   static int sms = 0;
@@ -75,7 +79,14 @@ struct DevOut {
   }
 };
 
-void set_device(const tomg_ctx* c) { CK(cudaSetDevice(c->device)); }
+void set_device(const tomg_ctx* c) {
+  CK(cudaSetDevice(c->device));
+  set_alloc_stream(c->stream);
+}
+void set_device(const tomg_problem* P) {
+  CK(cudaSetDevice(P->ctx->device));
+  set_alloc_stream(P->stream);
+}
 
 }  // namespace
 }  // namespace tomg
@@ -104,6 +115,7 @@ void tomg_options_default(tomg_options* o) {
   o->check_every = 4;
   o->use_graph = 2;
   o->max_levels = 25;
+  o->concurrency = 4;
 }
 
 tomg_status tomg_ctx_create(tomg_ctx** out, int device, void* cuda_stream) {
@@ -123,6 +135,12 @@ tomg_status tomg_ctx_create(tomg_ctx** out, int device, void* cuda_stream) {
       c->own_stream = true;
     }
     c->launches0 = g_launches;
+    // keep freed blocks of the stream-ordered pool cached for reuse by later setups
+    cudaMemPool_t pool;
+    if (cudaDeviceGetDefaultMemPool(&pool, device) == cudaSuccess) {
+      uint64_t keep = ~0ull;
+      cudaMemPoolSetAttribute(pool, cudaMemPoolAttrReleaseThreshold, &keep);
+    }
     *out = c;
     return TOMG_OK;
   });
@@ -193,7 +211,8 @@ tomg_status tomg_problem_sizes(const tomg_problem* P, int64_t* n, int64_t* nn, i
 tomg_status tomg_set_fixed_dofs(tomg_problem* P, const int64_t* dofs, int64_t count) {
   return guarded([&]() -> tomg_status {
     if (!P) TOMG_THROW(TOMG_E_INVALID, "null problem");
-    set_device(P->ctx);
+    set_device(P);
+    StreamScope sc(P);
     set_fixed(P, dofs, count);
     return TOMG_OK;
   });
@@ -202,7 +221,8 @@ tomg_status tomg_set_fixed_dofs(tomg_problem* P, const int64_t* dofs, int64_t co
 tomg_status tomg_set_density(tomg_problem* P, const double* rho, int on_device) {
   return guarded([&]() -> tomg_status {
     if (!P) TOMG_THROW(TOMG_E_INVALID, "null problem");
-    set_device(P->ctx);
+    set_device(P);
+    StreamScope sc(P);
     set_density(P, rho, on_device);
     return TOMG_OK;
   });
@@ -211,7 +231,8 @@ tomg_status tomg_set_density(tomg_problem* P, const double* rho, int on_device) 
 tomg_status tomg_setup(tomg_problem* P, const tomg_options* opt) {
   return guarded([&]() -> tomg_status {
     if (!P) TOMG_THROW(TOMG_E_INVALID, "null problem");
-    set_device(P->ctx);
+    set_device(P);
+    StreamScope sc(P);
     tomg_options o;
     if (opt) o = *opt;
     else tomg_options_default(&o);
@@ -224,7 +245,8 @@ tomg_status tomg_solve(tomg_problem* P, int nrhs, const double* f, double* u, in
                        tomg_result* results) {
   return guarded([&]() -> tomg_status {
     if (!P) TOMG_THROW(TOMG_E_INVALID, "null problem");
-    set_device(P->ctx);
+    set_device(P);
+    StreamScope sc(P);
     return solve(P, nrhs, f, u, on_device, results);
   });
 }
@@ -256,7 +278,8 @@ tomg_status tomg_level_export(tomg_problem* P, int level, int64_t* nnzb, int64_t
                               double* val) {
   return guarded([&]() -> tomg_status {
     if (!P || !nnzb) TOMG_THROW(TOMG_E_INVALID, "null argument");
-    set_device(P->ctx);
+    set_device(P);
+    StreamScope sc(P);
     level_export(P, level, nnzb, rp, ci, val);
     return TOMG_OK;
   });
@@ -266,7 +289,8 @@ tomg_status tomg_prolongation_export(tomg_problem* P, int level, int64_t* nnzb, 
                                      int64_t* ci, double* val) {
   return guarded([&]() -> tomg_status {
     if (!P || !nnzb) TOMG_THROW(TOMG_E_INVALID, "null argument");
-    set_device(P->ctx);
+    set_device(P);
+    StreamScope sc(P);
     prolong_export(P, level, nnzb, rp, ci, val);
     return TOMG_OK;
   });
@@ -277,10 +301,12 @@ tomg_status tomg_aggregates_export(tomg_problem* P, int level, int64_t* agg) {
     if (!P || !agg) TOMG_THROW(TOMG_E_INVALID, "null argument");
     if (!P->setup_valid || level < 0 || level + 1 >= (int)P->L.size() || P->L[level]->geo_next)
       TOMG_THROW(TOMG_E_INVALID, "level %d has no aggregation", level);
-    set_device(P->ctx);
+    set_device(P);
+    StreamScope sc(P);
     const Level& L = *P->L[level];
     std::vector<int> h(L.nn);
-    CK(cudaMemcpy(h.data(), L.agg.p, L.nn * sizeof(int), cudaMemcpyDeviceToHost));
+    CK(cudaMemcpyAsync(h.data(), L.agg.p, L.nn * sizeof(int), cudaMemcpyDeviceToHost, P->stream));
+    CK(cudaStreamSynchronize(P->stream));
     for (int64_t i = 0; i < L.nn; i++) agg[i] = h[i];
     return TOMG_OK;
   });
@@ -291,10 +317,11 @@ tomg_status tomg_level_apply(tomg_problem* P, int level, int prec, const double*
   return guarded([&]() -> tomg_status {
     if (!P || !x || !y) TOMG_THROW(TOMG_E_INVALID, "null argument");
     if (!P->setup_valid || level < 0 || level >= (int)P->L.size()) TOMG_THROW(TOMG_E_INVALID, "bad level");
-    set_device(P->ctx);
+    set_device(P);
+    StreamScope sc(P);
     const int64_t n = P->L[level]->n;
-    DevArray xin(x, n, on_device, P->ctx->stream);
-    DevOut yout(y, n, on_device, P->ctx->stream);
+    DevArray xin(x, n, on_device, P->stream);
+    DevOut yout(y, n, on_device, P->stream);
     level_apply(P, level, prec, xin.p, yout.p);
     yout.commit();
     return TOMG_OK;
@@ -304,9 +331,10 @@ tomg_status tomg_level_apply(tomg_problem* P, int level, int prec, const double*
 tomg_status tomg_vcycle(tomg_problem* P, const double* r, double* z, int on_device) {
   return guarded([&]() -> tomg_status {
     if (!P || !r || !z) TOMG_THROW(TOMG_E_INVALID, "null argument");
-    set_device(P->ctx);
-    DevArray rin(r, P->n, on_device, P->ctx->stream);
-    DevOut zout(z, P->n, on_device, P->ctx->stream);
+    set_device(P);
+    StreamScope sc(P);
+    DevArray rin(r, P->n, on_device, P->stream);
+    DevOut zout(z, P->n, on_device, P->stream);
     vcycle_apply(P, rin.p, zout.p);
     zout.commit();
     return TOMG_OK;
@@ -317,9 +345,10 @@ tomg_status tomg_coarse_solve(tomg_problem* P, const double* b, double* x, int o
   return guarded([&]() -> tomg_status {
     if (!P || !b || !x) TOMG_THROW(TOMG_E_INVALID, "null argument");
     if (!P->setup_valid) TOMG_THROW(TOMG_E_INVALID, "no valid setup");
-    set_device(P->ctx);
-    DevArray bin(b, P->nc, on_device, P->ctx->stream);
-    DevOut xout(x, P->nc, on_device, P->ctx->stream);
+    set_device(P);
+    StreamScope sc(P);
+    DevArray bin(b, P->nc, on_device, P->stream);
+    DevOut xout(x, P->nc, on_device, P->stream);
     coarse_apply(P, bin.p, xout.p);
     xout.commit();
     return TOMG_OK;
@@ -330,9 +359,10 @@ tomg_status tomg_moduli(tomg_problem* P, double* E, int on_device) {
   return guarded([&]() -> tomg_status {
     if (!P || !E) TOMG_THROW(TOMG_E_INVALID, "null argument");
     if (!P->have_density) TOMG_THROW(TOMG_E_INVALID, "no density set");
-    set_device(P->ctx);
-    CK(cudaMemcpyAsync(E, P->E64.p, P->nel * 8, on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost, P->ctx->stream));
-    CK(cudaStreamSynchronize(P->ctx->stream));
+    set_device(P);
+    StreamScope sc(P);
+    CK(cudaMemcpyAsync(E, P->E64.p, P->nel * 8, on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost, P->stream));
+    CK(cudaStreamSynchronize(P->stream));
     return TOMG_OK;
   });
 }
@@ -353,7 +383,8 @@ extern "C" tomg_status tomg_time_fine_operator(tomg_problem* P, int op, int prec
                                                int cold_l2, double* ms) {
   return tomg::guarded([&]() -> tomg_status {
     if (!P || !ms) TOMG_THROW(TOMG_E_INVALID, "null argument");
-    tomg::set_device(P->ctx);
+    tomg::set_device(P);
+    tomg::StreamScope sc(P);
     *ms = tomg::time_fine_operator(P, op, prec, reps, cold_l2);
     return TOMG_OK;
   });

@@ -3,6 +3,7 @@
 #pragma once
 
 #include <cuda_runtime.h>
+#include <atomic>
 #include <stdint.h>
 #include <stdio.h>
 #include <string>
@@ -40,7 +41,7 @@ struct Error {
   } while (0)
 
 // count of kernels launched by this library (per process; contexts read deltas)
-extern int64_t g_launches;
+extern std::atomic<int64_t> g_launches;
 
 #define LAUNCH(kernel, grid, block, smem, stream, ...)                      \
   do {                                                                     \
@@ -50,7 +51,12 @@ extern int64_t g_launches;
   } while (0)
 
 // ---------------------------------------------------------------------------------------
-// device buffers (owning, move-only)
+// device buffers (owning, move-only), stream-ordered: allocated and freed on the stream of the
+// API call in progress through CUDA's stream-ordered pool, which keeps freed memory cached
+// (no device-wide synchronisation on free, no driver round trip on reuse)
+cudaStream_t alloc_stream();              // stream of the API call in progress
+void set_alloc_stream(cudaStream_t s);    // set by every API entry point
+
 template <class T>
 struct DBuf {
   T* p = nullptr;
@@ -65,7 +71,7 @@ struct DBuf {
   }
   ~DBuf() { release(); }
   void release() {
-    if (p) cudaFree(p);
+    if (p) cudaFreeAsync(p, alloc_stream());
     p = nullptr;
     n = 0;
   }
@@ -74,7 +80,7 @@ struct DBuf {
     if (count == n && p) return;
     release();
     if (count == 0) return;
-    CK(cudaMalloc((void**)&p, count * sizeof(T)));
+    CK(cudaMallocAsync((void**)&p, count * sizeof(T), alloc_stream()));
     n = count;
   }
   void zero(cudaStream_t s) {

@@ -44,23 +44,31 @@ __global__ void k_diag_fro(int nbr, int b, const int* __restrict__ rp, const int
   dnorm[i] = d;
 }
 
+// one warp per node row; strong neighbours are compacted in column order (ballot prefix)
 __global__ void k_strength(int nbr, int b, const int* __restrict__ rp, const int* __restrict__ ci,
                            const double* __restrict__ V, const double* __restrict__ dnorm,
                            double beta, int* counts, const int* __restrict__ srp, int* sci) {
-  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  const int i = (blockIdx.x * blockDim.x + threadIdx.x) >> 5, lane = threadIdx.x & 31;
   if (i >= nbr) return;
+  const double di = dnorm[i];
+  const int base = srp ? srp[i] : 0;
   int cnt = 0;
-  int64_t pos = srp ? srp[i] : 0;
-  for (int p = rp[i]; p < rp[i + 1]; p++) {
-    const int j = ci[p];
-    if (j == i) continue;
-    const double F = block_fro(V + (int64_t)p * b * b, b * b);
-    if (F * F > beta * dnorm[i] * dnorm[j]) {
-      if (srp) sci[pos++] = j;
-      cnt++;
+  for (int p0 = rp[i]; p0 < rp[i + 1]; p0 += 32) {
+    const int p = p0 + lane;
+    bool strong = false;
+    int j = -1;
+    if (p < rp[i + 1]) {
+      j = ci[p];
+      if (j != i) {
+        const double F = block_fro(V + (int64_t)p * b * b, b * b);
+        strong = F * F > beta * di * dnorm[j];
+      }
     }
+    const unsigned bal = __ballot_sync(0xffffffffu, strong);
+    if (strong && srp) sci[base + cnt + __popc(bal & ((1u << lane) - 1u))] = j;
+    cnt += __popc(bal);
   }
-  if (counts) counts[i] = cnt;
+  if (counts && lane == 0) counts[i] = cnt;
 }
 
 __global__ void k_mis_init(int n, const int* __restrict__ srp, int* state) {
@@ -221,33 +229,65 @@ __global__ void k_power_init(int64_t n, int level, double* v) {
   const uint64_t h = splitmix64((uint64_t)i + SALT_POWER + (uint64_t)level);
   v[i] = (double)(h >> 11) * 0x1.0p-53 - 0.5;
 }
-// w = Dinv (A v); partial sums of w.w per block
+// w = scale * Dinv (A v), with `scale` read from the device (1/||v|| of the previous step) so
+// the iteration runs without host round trips; 8 lanes per block row; partial sums of w.w
 template <int B>
-__global__ void k_power_step(int nbr, const int* __restrict__ rp, const int* __restrict__ ci,
-                             const double* __restrict__ V, const double* __restrict__ Dinv,
-                             const double* __restrict__ v, double* w, double* partials) {
+__global__ void __launch_bounds__(256) k_power_step(int nbr, const int* __restrict__ rp,
+                                                    const int* __restrict__ ci,
+                                                    const double* __restrict__ V,
+                                                    const double* __restrict__ Dinv,
+                                                    const double* __restrict__ v,
+                                                    const double* __restrict__ scale, double* w,
+                                                    double* partials) {
+  constexpr int G = 8;
   __shared__ double sred[32];
-  const int i = blockIdx.x * blockDim.x + threadIdx.x;
-  double ss = 0.0;
+  const int gtid = blockIdx.x * blockDim.x + threadIdx.x;
+  const int i = gtid / G, sub = gtid % G;
+  double acc[B];
+#pragma unroll
+  for (int r = 0; r < B; r++) acc[r] = 0.0;
   if (i < nbr) {
-    double acc[B];
-    for (int r = 0; r < B; r++) acc[r] = 0.0;
-    for (int p = rp[i]; p < rp[i + 1]; p++) {
+    for (int p = rp[i] + sub; p < rp[i + 1]; p += G) {
       const int j = ci[p];
       const double* blk = V + (int64_t)p * B * B;
+#pragma unroll
       for (int r = 0; r < B; r++)
+#pragma unroll
         for (int c = 0; c < B; c++) acc[r] += blk[r * B + c] * v[(int64_t)B * j + c];
     }
+  }
+#pragma unroll
+  for (int o = G / 2; o > 0; o >>= 1)
+#pragma unroll
+    for (int r = 0; r < B; r++) acc[r] += __shfl_xor_sync(0xffffffffu, acc[r], o);
+  double ss = 0.0;
+  if (i < nbr && sub == 0) {
+    const double sc = *scale;
     const double* D = Dinv + (int64_t)B * B * i;
+#pragma unroll
     for (int r = 0; r < B; r++) {
       double t = 0.0;
+#pragma unroll
       for (int c = 0; c < B; c++) t += D[r * B + c] * acc[c];
+      t *= sc;
       w[(int64_t)B * i + r] = t;
       ss += t * t;
     }
   }
   const double tot = block_sum(ss, sred);
   if (threadIdx.x == 0) partials[blockIdx.x] = tot;
+}
+// out[0] = sqrt(sum of partials), out[1] = 1 / out[0] (fixed summation order)
+__global__ void k_norm_finish(const double* __restrict__ partials, int np, double* out) {
+  __shared__ double sred[32];
+  double a = 0.0;
+  for (int q = threadIdx.x; q < np; q += blockDim.x) a += partials[q];
+  a = block_sum(a, sred);
+  if (threadIdx.x == 0) {
+    const double nrm = sqrt(a);
+    out[0] = nrm;
+    out[1] = nrm > 0.0 ? 1.0 / nrm : 0.0;
+  }
 }
 __global__ void k_sumsq_partials(int64_t n, const double* __restrict__ v, double* partials) {
   __shared__ double sred[32];
@@ -330,7 +370,7 @@ void amg_strength_counts(cudaStream_t s, const Bsr& A, const double* V, double b
   DBuf<double> dn;
   dn.resize(A.nbr);
   LAUNCH(k_diag_fro, ceil_div(A.nbr, 256), 256, 0, s, A.nbr, A.br, A.rp, A.ci, V, dn.p);
-  LAUNCH(k_strength, ceil_div(A.nbr, 256), 256, 0, s, A.nbr, A.br, A.rp, A.ci, V, dn.p, beta,
+  LAUNCH(k_strength, ceil_div((int64_t)A.nbr * 32, 256), 256, 0, s, A.nbr, A.br, A.rp, A.ci, V, dn.p, beta,
          counts, (const int*)nullptr, (int*)nullptr);
   CK(cudaStreamSynchronize(s));
 }
@@ -340,7 +380,7 @@ void amg_strength_fill(cudaStream_t s, const Bsr& A, const double* V, double bet
   DBuf<double> dn;
   dn.resize(A.nbr);
   LAUNCH(k_diag_fro, ceil_div(A.nbr, 256), 256, 0, s, A.nbr, A.br, A.rp, A.ci, V, dn.p);
-  LAUNCH(k_strength, ceil_div(A.nbr, 256), 256, 0, s, A.nbr, A.br, A.rp, A.ci, V, dn.p, beta,
+  LAUNCH(k_strength, ceil_div((int64_t)A.nbr * 32, 256), 256, 0, s, A.nbr, A.br, A.rp, A.ci, V, dn.p, beta,
          (int*)nullptr, srp, sci);
   CK(cudaStreamSynchronize(s));
 }
@@ -408,36 +448,31 @@ void amg_tentative(cudaStream_t s, int n, int b, int k, int n_agg, const int* ag
 
 double amg_spectral_radius(cudaStream_t s, const Bsr& A, const double* V, const double* Dinv,
                            int level, int iters, double* v, double* w, double* partials) {
+  // u_0 = splitmix64 vector; step: w = (1/||u_it||) D^-1 A u_it, rho_it = ||w||, u_{it+1} = w.
+  // Norms and their reciprocals stay on the device; the host reads the last rho only.
+  (void)partials;
   const int64_t n = (int64_t)A.nbr * A.br;
-  const int gb = ceil_div(A.nbr, 256);
+  const int gb = ceil_div((int64_t)A.nbr * 8, 256);
   const int gp = 256;
-  std::vector<double> hp(std::max(gb, gp));
-  auto norm = [&](const double* x) {
-    LAUNCH(k_sumsq_partials, gp, 256, 0, s, n, x, partials);
-    CK(cudaMemcpyAsync(hp.data(), partials, sizeof(double) * gp, cudaMemcpyDeviceToHost, s));
-    CK(cudaStreamSynchronize(s));
-    double t = 0.0;
-    for (int q = 0; q < gp; q++) t += hp[q];
-    return sqrt(t);
-  };
+  DBuf<double> parts, nrm;
+  parts.resize(std::max(gb, gp));
+  nrm.resize(2 * (iters + 1));
   LAUNCH(k_power_init, ceil_div(n, 256), 256, 0, s, n, level, v);
-  double nv = norm(v);
-  LAUNCH(k_scale, ceil_div(n, 256), 256, 0, s, n, v, 1.0 / nv);
-  double rho = 0.0;
+  LAUNCH(k_sumsq_partials, gp, 256, 0, s, n, v, parts.p);
+  LAUNCH(k_norm_finish, 1, 256, 0, s, parts.p, gp, nrm.p);
   for (int it = 0; it < iters; it++) {
-    if (A.br == 2) LAUNCH(k_power_step<2>, gb, 256, 0, s, A.nbr, A.rp, A.ci, V, Dinv, v, w, partials);
-    else if (A.br == 3) LAUNCH(k_power_step<3>, gb, 256, 0, s, A.nbr, A.rp, A.ci, V, Dinv, v, w, partials);
-    else if (A.br == 6) LAUNCH(k_power_step<6>, gb, 256, 0, s, A.nbr, A.rp, A.ci, V, Dinv, v, w, partials);
+    const double* sc = nrm.p + 2 * it + 1;
+    if (A.br == 2) LAUNCH(k_power_step<2>, gb, 256, 0, s, A.nbr, A.rp, A.ci, V, Dinv, v, sc, w, parts.p);
+    else if (A.br == 3) LAUNCH(k_power_step<3>, gb, 256, 0, s, A.nbr, A.rp, A.ci, V, Dinv, v, sc, w, parts.p);
+    else if (A.br == 6) LAUNCH(k_power_step<6>, gb, 256, 0, s, A.nbr, A.rp, A.ci, V, Dinv, v, sc, w, parts.p);
     else TOMG_THROW(TOMG_E_INVALID, "unsupported block %d", A.br);
-    CK(cudaMemcpyAsync(hp.data(), partials, sizeof(double) * gb, cudaMemcpyDeviceToHost, s));
-    CK(cudaStreamSynchronize(s));
-    double t = 0.0;
-    for (int q = 0; q < gb; q++) t += hp[q];
-    rho = sqrt(t);
-    if (!(rho > 0.0)) TOMG_THROW(TOMG_E_BREAKDOWN, "power iteration collapsed");
-    LAUNCH(k_scale, ceil_div(n, 256), 256, 0, s, n, w, 1.0 / rho);
+    LAUNCH(k_norm_finish, 1, 256, 0, s, parts.p, gb, nrm.p + 2 * (it + 1));
     std::swap(v, w);
   }
+  double rho = 0.0;
+  CK(cudaMemcpyAsync(&rho, nrm.p + 2 * iters, sizeof(double), cudaMemcpyDeviceToHost, s));
+  CK(cudaStreamSynchronize(s));
+  if (!(rho > 0.0)) TOMG_THROW(TOMG_E_BREAKDOWN, "power iteration collapsed");
   return rho;
 }
 

@@ -128,9 +128,9 @@ __global__ void k_bsr_diag(int nbr, const int* __restrict__ rp, const int* __res
 
 __global__ void k_bsr_dense(int nbr, int b, int64_t n, const int* __restrict__ rp,
                             const int* __restrict__ ci, const double* __restrict__ V, double* A) {
-  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  const int i = (blockIdx.x * blockDim.x + threadIdx.x) >> 5, lane = threadIdx.x & 31;
   if (i >= nbr) return;
-  for (int p = rp[i]; p < rp[i + 1]; p++) {
+  for (int p = rp[i] + lane; p < rp[i + 1]; p += 32) {
     const int j = ci[p];
     for (int r = 0; r < b; r++)
       for (int c = 0; c < b; c++) A[((int64_t)b * i + r) * n + (int64_t)b * j + c] = V[((int64_t)p * b + r) * b + c];
@@ -156,26 +156,22 @@ __global__ void k_transpose_scatter(int nbr, const int* __restrict__ rp, const i
   }
 }
 
-// sort each row of the transpose by column (insertion sort; rows are short) and copy blocks
-__global__ void k_transpose_finish(int nbc, int br, int bc, const int* __restrict__ rpT, int* rowT,
-                                   int* srcT, const double* __restrict__ V, double* VT) {
-  const int j = blockIdx.x * blockDim.x + threadIdx.x;
+// one warp per row of the transpose: every entry goes to its rank by source row (the source
+// rows of one column are distinct), and its block is copied transposed
+__global__ void k_transpose_finish(int nbc, int br, int bc, const int* __restrict__ rpT,
+                                   const int* __restrict__ rowU, const int* __restrict__ srcU,
+                                   int* ciT, const double* __restrict__ V, double* VT) {
+  const int j = (blockIdx.x * blockDim.x + threadIdx.x) >> 5, lane = threadIdx.x & 31;
   if (j >= nbc) return;
   const int a = rpT[j], e = rpT[j + 1];
-  for (int p = a + 1; p < e; p++) {
-    const int kr = rowT[p], ks = srcT[p];
-    int q = p - 1;
-    while (q >= a && rowT[q] > kr) {
-      rowT[q + 1] = rowT[q];
-      srcT[q + 1] = srcT[q];
-      q--;
-    }
-    rowT[q + 1] = kr;
-    srcT[q + 1] = ks;
-  }
-  for (int p = a; p < e; p++) {
-    const double* src = V + (int64_t)srcT[p] * br * bc;
-    double* dst = VT + (int64_t)p * br * bc;
+  for (int p = a + lane; p < e; p += 32) {
+    const int kr = rowU[p];
+    int rank = 0;
+    for (int q = a; q < e; q++) rank += rowU[q] < kr ? 1 : 0;
+    const int dstp = a + rank;
+    ciT[dstp] = kr;
+    const double* src = V + (int64_t)srcU[p] * br * bc;
+    double* dst = VT + (int64_t)dstp * br * bc;
     for (int r = 0; r < br; r++)
       for (int c = 0; c < bc; c++) dst[c * br + r] = src[r * bc + c];
   }
@@ -260,39 +256,50 @@ __global__ void __launch_bounds__(32 * SPG_WARPS)
   }
 }
 
-__global__ void k_spgemm_num(int nrows, int br, int bk, int bc, const int* __restrict__ Arp,
-                             const int* __restrict__ Aci, const double* __restrict__ VA,
-                             const int* __restrict__ Brp, const int* __restrict__ Bci,
-                             const double* __restrict__ VB, const int* __restrict__ Crp,
-                             const int* __restrict__ Cci, double* VC) {
+template <int BR, int BK, int BC>
+__global__ void __launch_bounds__(128) k_spgemm_num(int nrows, const int* __restrict__ Arp,
+                                                    const int* __restrict__ Aci,
+                                                    const double* __restrict__ VA,
+                                                    const int* __restrict__ Brp,
+                                                    const int* __restrict__ Bci,
+                                                    const double* __restrict__ VB,
+                                                    const int* __restrict__ Crp,
+                                                    const int* __restrict__ Cci, double* VC) {
   const int w = (blockIdx.x * blockDim.x + threadIdx.x) >> 5, lane = threadIdx.x & 31;
   if (w >= nrows) return;
   const int row = w;
   for (int pc = Crp[row] + lane; pc < Crp[row + 1]; pc += 32) {
     const int j = Cci[pc];
-    double acc[36];
-    for (int t = 0; t < br * bc; t++) acc[t] = 0.0;
+    double acc[BR * BC];
+#pragma unroll
+    for (int t = 0; t < BR * BC; t++) acc[t] = 0.0;
     for (int a = Arp[row]; a < Arp[row + 1]; a++) {
       const int k = Aci[a];
-      const int lo = Brp[k], hi = Brp[k + 1];
-      if (lo == hi) continue;
-      int l = lo, h = hi;
+      const int hi = Brp[k + 1];
+      int l = Brp[k], h = hi;
       while (l < h) {
         const int mid = (l + h) >> 1;
         if (Bci[mid] < j) l = mid + 1;
         else h = mid;
       }
       if (l >= hi || Bci[l] != j) continue;
-      const double* Ab = VA + (int64_t)a * br * bk;
-      const double* Bb = VB + (int64_t)l * bk * bc;
-      for (int r = 0; r < br; r++)
-        for (int t = 0; t < bk; t++) {
-          const double av = Ab[r * bk + t];
-          for (int c = 0; c < bc; c++) acc[r * bc + c] += av * Bb[t * bc + c];
+      const double* Ab = VA + (int64_t)a * BR * BK;
+      const double* Bb = VB + (int64_t)l * BK * BC;
+      double bv[BK * BC];
+#pragma unroll
+      for (int t = 0; t < BK * BC; t++) bv[t] = Bb[t];
+#pragma unroll
+      for (int r = 0; r < BR; r++)
+#pragma unroll
+        for (int t = 0; t < BK; t++) {
+          const double av = Ab[r * BK + t];
+#pragma unroll
+          for (int c = 0; c < BC; c++) acc[r * BC + c] += av * bv[t * BC + c];
         }
     }
-    double* Cb = VC + (int64_t)pc * br * bc;
-    for (int t = 0; t < br * bc; t++) Cb[t] = acc[t];
+    double* Cb = VC + (int64_t)pc * BR * BC;
+#pragma unroll
+    for (int t = 0; t < BR * BC; t++) Cb[t] = acc[t];
   }
 }
 
@@ -415,7 +422,7 @@ void bsr_block_diag_inv(cudaStream_t s, const Bsr& A, const double* V, double* D
 void bsr_to_dense(cudaStream_t s, const Bsr& A, const double* V, double* Ad) {
   const int64_t n = (int64_t)A.nbr * A.br;
   CK(cudaMemsetAsync(Ad, 0, sizeof(double) * n * n, s));
-  LAUNCH(k_bsr_dense, ceil_div(A.nbr, 128), 128, 0, s, A.nbr, A.br, n, A.rp, A.ci, V, Ad);
+  LAUNCH(k_bsr_dense, ceil_div((int64_t)A.nbr * 32, 128), 128, 0, s, A.nbr, A.br, n, A.rp, A.ci, V, Ad);
 }
 
 void bsr_col_counts(cudaStream_t s, const Bsr& A, int* counts) {
@@ -425,14 +432,14 @@ void bsr_col_counts(cudaStream_t s, const Bsr& A, int* counts) {
 
 void bsr_transpose_fill(cudaStream_t s, const Bsr& A, const double* V, const int* rpT, int* ciT,
                         double* VT, int* cursor) {
-  DBuf<int> src;
+  DBuf<int> src, rowu;
   src.resize(A.nnzb > 0 ? A.nnzb : 1);
+  rowu.resize(A.nnzb > 0 ? A.nnzb : 1);
   CK(cudaMemsetAsync(cursor, 0, sizeof(int) * A.nbc, s));
   LAUNCH(k_transpose_scatter, ceil_div(A.nbr, 256), 256, 0, s, A.nbr, A.rp, A.ci, rpT, cursor,
-         ciT, src.p);
-  LAUNCH(k_transpose_finish, ceil_div(A.nbc, 128), 128, 0, s, A.nbc, A.br, A.bc, rpT, ciT, src.p,
-         V, VT);
-  CK(cudaStreamSynchronize(s));
+         rowu.p, src.p);
+  LAUNCH(k_transpose_finish, ceil_div((int64_t)A.nbc * 32, 128), 128, 0, s, A.nbc, A.br, A.bc,
+         rpT, rowu.p, src.p, ciT, V, VT);
 }
 
 void spgemm_counts(cudaStream_t s, const Bsr& A, const Bsr& B, int* counts, SpgemmWork& w) {
@@ -454,9 +461,16 @@ void spgemm_fill(cudaStream_t s, const Bsr& A, const Bsr& B, const int* rpC, int
 
 void spgemm_numeric(cudaStream_t s, const Bsr& A, const double* VA, const Bsr& B, const double* VB,
                     const Bsr& C, double* VC) {
-  if (A.br * B.bc > 36) TOMG_THROW(TOMG_E_INVALID, "SpGEMM block too large");
-  LAUNCH(k_spgemm_num, ceil_div((int64_t)A.nbr * 32, 128), 128, 0, s, A.nbr, A.br, A.bc, B.bc,
-         A.rp, A.ci, VA, B.rp, B.ci, VB, C.rp, C.ci, VC);
+  const int grid = ceil_div((int64_t)A.nbr * 32, 128);
+#define NUM(R, K, CC)                                                                          \
+  if (A.br == R && A.bc == K && B.bc == CC) {                                                  \
+    LAUNCH((k_spgemm_num<R, K, CC>), grid, 128, 0, s, A.nbr, A.rp, A.ci, VA, B.rp, B.ci, VB,   \
+           C.rp, C.ci, VC);                                                                    \
+    return;                                                                                    \
+  }
+  NUM(2, 2, 3) NUM(3, 3, 3) NUM(3, 3, 6) NUM(6, 6, 6) NUM(3, 2, 3) NUM(6, 3, 6) NUM(2, 2, 2)
+#undef NUM
+  TOMG_THROW(TOMG_E_INVALID, "SpGEMM block shape %dx%d * %dx%d not instantiated", A.br, A.bc, B.br, B.bc);
 }
 
 void cast_f64_f32(cudaStream_t s, const double* a, float* b, int64_t n) {

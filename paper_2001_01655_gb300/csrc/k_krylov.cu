@@ -187,10 +187,13 @@ __global__ void __launch_bounds__(NB * NB) k_potrf_diag(int n, int k0, double* A
                                                         int* fail) {
   __shared__ double s[NB][NB + 1];
   __shared__ double li[NB][NB + 1];
+  __shared__ double rdiag[NB];
   const int tx = threadIdx.x, ty = threadIdx.y;
   const int kb = min(NB, n - k0);
   s[ty][tx] = (ty < kb && tx < kb) ? A[(int64_t)(k0 + ty) * n + k0 + tx] : (ty == tx ? 1.0 : 0.0);
   __syncthreads();
+  // FP64 division and square root are long instruction sequences here: one of each per pivot,
+  // everything else multiplies by the reciprocal
   for (int k = 0; k < NB; k++) {
     if (tx == 0 && ty == 0) {
       double d = s[k][k];
@@ -198,10 +201,12 @@ __global__ void __launch_bounds__(NB * NB) k_potrf_diag(int n, int k0, double* A
         if (k < kb) atomicCAS(fail, 0, k0 + k + 1);
         d = 1.0;
       }
-      s[k][k] = sqrt(d);
+      const double piv = sqrt(d);
+      s[k][k] = piv;
+      rdiag[k] = 1.0 / piv;
     }
     __syncthreads();
-    if (tx == k && ty > k) s[ty][k] /= s[k][k];
+    if (tx == k && ty > k) s[ty][k] *= rdiag[k];
     __syncthreads();
     if (ty > k && tx > k && tx <= ty) s[ty][tx] -= s[ty][k] * s[tx][k];
     __syncthreads();
@@ -212,7 +217,7 @@ __global__ void __launch_bounds__(NB * NB) k_potrf_diag(int n, int k0, double* A
       if (r < c) { li[r][c] = 0.0; continue; }
       double v = (r == c) ? 1.0 : 0.0;
       for (int t = c; t < r; t++) v -= s[r][t] * li[t][c];
-      li[r][c] = v / s[r][r];
+      li[r][c] = v * rdiag[r];
     }
   }
   __syncthreads();
@@ -263,15 +268,51 @@ __global__ void __launch_bounds__(32 * 8) k_syrk(int n, int k0, double* A) {
 
 // forward substitution for block row K of Y = L^-1:
 //   T[r][c] = delta_rc - sum_{m = c}^{K0-1} L[r][m] Y[m][c]   (r in the block, c < K0 + kb)
-__global__ void k_fwd_T(int n, int K0, const double* __restrict__ L, const double* __restrict__ Y,
-                        double* T) {
-  const int c = blockIdx.x * blockDim.x + threadIdx.x;
-  const int r = K0 + blockIdx.y;
+// computed as a 32 x 64 output tile per block (8 outputs per thread), L and Y staged in shared
+// memory 32 columns of m at a time; m-tiles entirely above Y's diagonal are skipped
+__global__ void __launch_bounds__(256) k_fwd_T(int n, int K0, const double* __restrict__ L,
+                                               const double* __restrict__ Y, double* T) {
+  __shared__ double Ls[32][33];
+  __shared__ double Ys[32][65];
   const int kb = min(NB, n - K0);
-  if (c >= K0 + kb) return;
-  double v = (r == c) ? 1.0 : 0.0;
-  for (int m = c; m < K0; m++) v -= L[(int64_t)r * n + m] * Y[(int64_t)m * n + c];
-  T[(int64_t)(r - K0) * n + c] = v;
+  const int C = K0 + kb;
+  const int cb = blockIdx.x * 64;
+  const int tx = threadIdx.x, ty = threadIdx.y;  // 32 x 8
+  double acc[4][2];
+#pragma unroll
+  for (int a = 0; a < 4; a++) acc[a][0] = acc[a][1] = 0.0;
+  for (int mt = (cb / 32) * 32; mt < K0; mt += 32) {
+    for (int q = ty; q < 32; q += 8) {
+      const int r = K0 + q, m = mt + tx;
+      Ls[q][tx] = (q < kb && m < K0) ? L[(int64_t)r * n + m] : 0.0;
+      const int mm = mt + q;
+      const int c0 = cb + tx, c1 = cb + 32 + tx;
+      Ys[q][tx] = (mm < K0 && c0 < C) ? Y[(int64_t)mm * n + c0] : 0.0;
+      Ys[q][tx + 32] = (mm < K0 && c1 < C) ? Y[(int64_t)mm * n + c1] : 0.0;
+    }
+    __syncthreads();
+#pragma unroll 8
+    for (int m = 0; m < 32; m++) {
+      const double y0 = Ys[m][tx], y1 = Ys[m][tx + 32];
+#pragma unroll
+      for (int a = 0; a < 4; a++) {
+        const double l = Ls[ty * 4 + a][m];
+        acc[a][0] += l * y0;
+        acc[a][1] += l * y1;
+      }
+    }
+    __syncthreads();
+  }
+#pragma unroll
+  for (int a = 0; a < 4; a++) {
+    const int t = ty * 4 + a, r = K0 + t;
+    if (t >= kb) continue;
+#pragma unroll
+    for (int h = 0; h < 2; h++) {
+      const int c = cb + tx + 32 * h;
+      if (c < C) T[(int64_t)t * n + c] = ((r == c) ? 1.0 : 0.0) - acc[a][h];
+    }
+  }
 }
 //   Y[r][c] = sum_t Linv_KK[r - K0][t] T[t][c]; zero above the diagonal
 __global__ void k_fwd_Y(int n, int K0, const double* __restrict__ LinvKK,
@@ -399,7 +440,7 @@ int dense_spd_inverse(cudaStream_t s, int n, double* A, double* work) {
   if (f) return f;
   for (int b = 0; b < nblk; b++) {
     const int K0 = b * NB, kb = std::min(NB, n - K0);
-    LAUNCH(k_fwd_T, dim3(ceil_div(K0 + kb, 128), kb), 128, 0, s, n, K0, A, Y, T.p);
+    LAUNCH(k_fwd_T, ceil_div(K0 + kb, 64), dim3(32, 8), 0, s, n, K0, A, Y, T.p);
     LAUNCH(k_fwd_Y, dim3(ceil_div(n, 128), kb), 128, 0, s, n, K0, linv.p + (size_t)b * NB * NB, T.p, Y);
   }
   dim3 blk(16, 16), grd(ceil_div(n, 16), ceil_div(n, 16));

@@ -1,9 +1,9 @@
 // Host runtime: problem state, preconditioner setup (Sec. 3.2 Eq. 9, Sec. 4), the V-cycle of
 // Algorithm 1 with point-block Jacobi smoothing, and the outer CG / flexible-CG loop (Sec. 3.1)
 // whose iteration is captured once into a CUDA graph with a device-side while loop, so a
-// whole solve is one graph launch with no host round trip per iteration.
+// whole solve is one graph launch with no host round trip per iteration.  Several right-hand
+// sides run on concurrent solve slots that share the hierarchy.
 #include <algorithm>
-#include <chrono>
 #include <cmath>
 #include <cstring>
 
@@ -86,10 +86,10 @@ template <> struct V<double> {
   static const double* D(const Level& l) { return l.D64.p; }
   static const double* Pv(const Level& l) { return l.Pv64.p; }
   static const double* Rv(const Level& l) { return l.Rv64.p; }
-  static double* b(Level& l) { return l.b64.p; }
-  static double* x(Level& l) { return l.x64.p; }
-  static double* r(Level& l) { return l.r64.p; }
-  static double* y(Level& l) { return l.y64.p; }
+  static double* b(LevelWork& l) { return l.b64.p; }
+  static double* x(LevelWork& l) { return l.x64.p; }
+  static double* r(LevelWork& l) { return l.r64.p; }
+  static double* y(LevelWork& l) { return l.y64.p; }
   static const double* Ainv(const tomg_problem* P) { return P->Ainv64.p; }
   static Ebe ebe(const tomg_problem* P) {
     return Ebe{P->dim, P->nx, P->ny, P->nz, P->Ke64.p, P->E64.p, P->mask.p};
@@ -101,143 +101,148 @@ template <> struct V<float> {
   static const float* D(const Level& l) { return l.D32.p; }
   static const float* Pv(const Level& l) { return l.Pv32.p; }
   static const float* Rv(const Level& l) { return l.Rv32.p; }
-  static float* b(Level& l) { return l.b32.p; }
-  static float* x(Level& l) { return l.x32.p; }
-  static float* r(Level& l) { return l.r32.p; }
-  static float* y(Level& l) { return l.y32.p; }
+  static float* b(LevelWork& l) { return l.b32.p; }
+  static float* x(LevelWork& l) { return l.x32.p; }
+  static float* r(LevelWork& l) { return l.r32.p; }
+  static float* y(LevelWork& l) { return l.y32.p; }
   static const float* Ainv(const tomg_problem* P) { return P->Ainv32.p; }
   static Ebe ebe(const tomg_problem* P) {
     return Ebe{P->dim, P->nx, P->ny, P->nz, P->Ke32.p, P->E32.p, P->mask.p};
   }
 };
 
-inline cudaStream_t st(const tomg_problem* P) { return P->ctx->stream; }
+inline cudaStream_t st(const tomg_problem* P) { return P->stream; }
 
 template <class T>
-void level_op(tomg_problem* P, int l, int mode, const T* x, T* y, const T* b, const int* done) {
+void level_op(tomg_problem* P, cudaStream_t s, int l, int mode, const T* x, T* y, const T* b,
+              const int* done) {
   Level& Lv = *P->L[l];
   const double w = P->opt.omega;
   switch (Lv.kind) {
     case KIND_EBE:
-      ebe_op<T>(st(P), mode, V<T>::ebe(P), x, y, b, V<T>::D(Lv), w, done, nullptr);
+      ebe_op<T>(s, mode, V<T>::ebe(P), x, y, b, V<T>::D(Lv), w, done, nullptr);
       break;
     case KIND_STENCIL:
-      stencil_op<T>(st(P), mode, Lv.g, V<T>::S(Lv), x, y, b, V<T>::D(Lv), w, done);
+      stencil_op<T>(s, mode, Lv.g, V<T>::S(Lv), x, y, b, V<T>::D(Lv), w, done);
       break;
     default:
-      bsr_op<T>(st(P), mode, Lv.bsr(), V<T>::Vv(Lv), x, y, b, V<T>::D(Lv), w, done);
+      bsr_op<T>(s, mode, Lv.bsr(), V<T>::Vv(Lv), x, y, b, V<T>::D(Lv), w, done);
   }
 }
 
 template <class T>
-void restrict_to(tomg_problem* P, int l, const T* r, T* bc, const int* done) {
+void restrict_to(tomg_problem* P, cudaStream_t s, int l, const T* r, T* bc, const int* done) {
   Level& Lv = *P->L[l];
   Level& C = *P->L[l + 1];
-  if (Lv.geo_next) geo_restrict<T>(st(P), Lv.g, C.g, r, bc, done);
-  else bsr_spmv_rect<T>(st(P), Lv.Rmat(C.nn), V<T>::Rv(Lv), r, bc, 0, done);
+  if (Lv.geo_next) geo_restrict<T>(s, Lv.g, C.g, r, bc, done);
+  else bsr_spmv_rect<T>(s, Lv.Rmat(C.nn), V<T>::Rv(Lv), r, bc, 0, done);
 }
 
 template <class T>
-void prolong_add(tomg_problem* P, int l, const T* xc, T* x, const int* done) {
+void prolong_add(tomg_problem* P, cudaStream_t s, int l, const T* xc, T* x, const int* done) {
   Level& Lv = *P->L[l];
   Level& C = *P->L[l + 1];
-  if (Lv.geo_next) geo_prolong_add<T>(st(P), Lv.g, C.g, xc, x, done);
-  else bsr_spmv_rect<T>(st(P), Lv.Pmat(C.nn), V<T>::Pv(Lv), xc, x, 1, done);
+  if (Lv.geo_next) geo_prolong_add<T>(s, Lv.g, C.g, xc, x, done);
+  else bsr_spmv_rect<T>(s, Lv.Pmat(C.nn), V<T>::Pv(Lv), xc, x, 1, done);
 }
 
-// V-cycle of Algorithm 1: out = MG(b) on level l (x = 0 initial guess)
+// V-cycle of Algorithm 1: out = MG(b) on level l (x = 0 initial guess), work vectors of slot W
 template <class T>
-void vcycle(tomg_problem* P, int l, const T* b, T* out, const int* done) {
+void vcycle(tomg_problem* P, Work& W, int l, const T* b, T* out, const int* done) {
   Level& Lv = *P->L[l];
+  LevelWork& lw = W.lw[l];
+  cudaStream_t s = W.stream;
   const int nl = (int)P->L.size();
   const double w = P->opt.omega;
   if (P->jacobi_only) {
-    jacobi0<T>(st(P), Lv.b, Lv.nn, V<T>::D(Lv), b, out, w, done);
+    jacobi0<T>(s, Lv.b, Lv.nn, V<T>::D(Lv), b, out, w, done);
     return;
   }
   if (l == nl - 1) {
-    dense_gemv<T>(st(P), P->nc, V<T>::Ainv(P), b, out, done);
+    dense_gemv<T>(s, P->nc, V<T>::Ainv(P), b, out, done);
     return;
   }
-  T* x = V<T>::x(Lv);
-  T* r = V<T>::r(Lv);
+  T* x = V<T>::x(lw);
+  T* r = V<T>::r(lw);
   // pre-smoothing, the first sweep from x = 0 needs no operator apply
-  jacobi0<T>(st(P), Lv.b, Lv.nn, V<T>::D(Lv), b, x, w, done);
+  jacobi0<T>(s, Lv.b, Lv.nn, V<T>::D(Lv), b, x, w, done);
   for (int k = 1; k < P->opt.n_pre; k++) {
-    level_op<T>(P, l, MODE_JACOBI, x, r, b, done);
+    level_op<T>(P, s, l, MODE_JACOBI, x, r, b, done);
     std::swap(x, r);
   }
-  level_op<T>(P, l, MODE_RESID, x, r, b, done);  // r = b - A x
-  Level& C = *P->L[l + 1];
-  restrict_to<T>(P, l, r, V<T>::b(C), done);
-  vcycle<T>(P, l + 1, V<T>::b(C), V<T>::y(C), done);
-  prolong_add<T>(P, l, V<T>::y(C), x, done);
+  level_op<T>(P, s, l, MODE_RESID, x, r, b, done);  // r = b - A x
+  LevelWork& cw = W.lw[l + 1];
+  restrict_to<T>(P, s, l, r, V<T>::b(cw), done);
+  vcycle<T>(P, W, l + 1, V<T>::b(cw), V<T>::y(cw), done);
+  prolong_add<T>(P, s, l, V<T>::y(cw), x, done);
   T* cur = x;
   for (int k = 0; k < P->opt.n_post; k++) {
     T* dst = (k == P->opt.n_post - 1) ? out : (cur == x ? r : x);
-    level_op<T>(P, l, MODE_JACOBI, cur, dst, b, done);
+    level_op<T>(P, s, l, MODE_JACOBI, cur, dst, b, done);
     cur = dst;
   }
 }
 
 // z = M r (outer residual in FP64), then partials of z.r (and z.q)
-void apply_M_and_dots(tomg_problem* P, const double* q, const int* done) {
+void apply_M_and_dots(tomg_problem* P, Work& W, const double* q, const int* done) {
   const int64_t n = P->n;
-  Level& L0 = *P->L[0];
+  LevelWork& l0 = W.lw[0];
+  cudaStream_t s = W.stream;
   if (P->opt.prec == TOMG_PREC_FP64) {
-    vcycle<double>(P, 0, P->r.p, P->z.p, done);
-    z_dots<double>(st(P), P->z.p, P->z.p, P->r.p, q, n, P->partA.p, q ? P->partB.p : nullptr, done);
+    vcycle<double>(P, W, 0, W.r.p, W.z.p, done);
+    z_dots<double>(s, W.z.p, W.z.p, W.r.p, q, n, W.partA.p, q ? W.partB.p : nullptr, done);
   } else {
-    cast_in<float>(st(P), P->r.p, L0.b32.p, n, done);
-    vcycle<float>(P, 0, L0.b32.p, L0.y32.p, done);
-    z_dots<float>(st(P), L0.y32.p, P->z.p, P->r.p, q, n, P->partA.p, q ? P->partB.p : nullptr, done);
+    cast_in<float>(s, W.r.p, l0.b32.p, n, done);
+    vcycle<float>(P, W, 0, l0.b32.p, l0.y32.p, done);
+    z_dots<float>(s, l0.y32.p, W.z.p, W.r.p, q, n, W.partA.p, q ? W.partB.p : nullptr, done);
   }
 }
 
-void iteration_body(tomg_problem* P) {
+void iteration_body(tomg_problem* P, Work& W) {
   const int64_t n = P->n;
-  Scalars* sc = P->sc.p;
+  Scalars* sc = W.sc.p;
   const int* done = &sc->done;
+  cudaStream_t s = W.stream;
   const Ebe op = V<double>::ebe(P);
-  ebe_op<double>(st(P), MODE_APPLY, op, P->p.p, P->q.p, nullptr, nullptr, 0.0, done, P->partA.p);
-  finish(st(P), FIN_ALPHA, P->partA.p, ebe_blocks(op), nullptr, 0, sc);
-  xr_update(st(P), P->x.p, P->r.p, P->p.p, P->q.p, n, sc, P->partA.p);
-  finish(st(P), FIN_RR, P->partA.p, red_blocks(n), nullptr, 0, sc);
-  apply_M_and_dots(P, P->q.p, done);
-  finish(st(P), FIN_BETA, P->partA.p, red_blocks(n), P->partB.p, red_blocks(n), sc);
-  p_update(st(P), P->p.p, P->z.p, n, sc);
+  ebe_op<double>(s, MODE_APPLY, op, W.p.p, W.q.p, nullptr, nullptr, 0.0, done, W.partA.p);
+  finish(s, FIN_ALPHA, W.partA.p, ebe_blocks(op), nullptr, 0, sc);
+  xr_update(s, W.x.p, W.r.p, W.p.p, W.q.p, n, sc, W.partA.p);
+  finish(s, FIN_RR, W.partA.p, red_blocks(n), nullptr, 0, sc);
+  apply_M_and_dots(P, W, W.q.p, done);
+  finish(s, FIN_BETA, W.partA.p, red_blocks(n), W.partB.p, red_blocks(n), sc);
+  p_update(s, W.p.p, W.z.p, n, sc);
 }
 
-void destroy_graph(tomg_problem* P) {
-  if (P->gexec) cudaGraphExecDestroy(P->gexec);
-  if (P->graph) cudaGraphDestroy(P->graph);
-  P->gexec = nullptr;
-  P->graph = nullptr;
-  P->graph_mode = 0;
+void destroy_graph(Work& W) {
+  if (W.gexec) cudaGraphExecDestroy(W.gexec);
+  if (W.graph) cudaGraphDestroy(W.graph);
+  W.gexec = nullptr;
+  W.graph = nullptr;
+  W.graph_mode = 0;
 }
 
-void build_graph(tomg_problem* P) {
-  destroy_graph(P);
+void build_graph(tomg_problem* P, Work& W) {
+  destroy_graph(W);
   const int mode = P->opt.use_graph;
   if (mode <= 0) return;
-  cudaStream_t s = st(P);
+  cudaStream_t s = W.stream;
   const int64_t saved = g_launches;
   if (mode >= 2) {
-    CK(cudaGraphCreate(&P->graph, 0));
+    CK(cudaGraphCreate(&W.graph, 0));
     cudaGraphConditionalHandle h;
-    CK(cudaGraphConditionalHandleCreate(&h, P->graph, 1, cudaGraphCondAssignDefault));
+    CK(cudaGraphConditionalHandleCreate(&h, W.graph, 1, cudaGraphCondAssignDefault));
     cudaGraphNodeParams cp = {};
     cp.type = cudaGraphNodeTypeConditional;
     cp.conditional.handle = h;
     cp.conditional.type = cudaGraphCondTypeWhile;
     cp.conditional.size = 1;
     cudaGraphNode_t node;
-    CK(cudaGraphAddNode(&node, P->graph, nullptr, nullptr, 0, &cp));
+    CK(cudaGraphAddNode(&node, W.graph, nullptr, nullptr, 0, &cp));
     cudaGraph_t body = cp.conditional.phGraph_out[0];
     CK(cudaStreamBeginCaptureToGraph(s, body, nullptr, nullptr, 0, cudaStreamCaptureModeThreadLocal));
     try {
-      iteration_body(P);
-      set_conditional(s, h, P->sc.p);
+      iteration_body(P, W);
+      set_conditional(s, h, W.sc.p);
     } catch (...) {
       cudaGraph_t dummy;
       cudaStreamEndCapture(s, &dummy);
@@ -248,19 +253,19 @@ void build_graph(tomg_problem* P) {
   } else {
     CK(cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal));
     try {
-      iteration_body(P);
+      iteration_body(P, W);
     } catch (...) {
       cudaGraph_t dummy;
       cudaStreamEndCapture(s, &dummy);
       g_launches = saved;
       throw;
     }
-    CK(cudaStreamEndCapture(s, &P->graph));
+    CK(cudaStreamEndCapture(s, &W.graph));
   }
-  P->kernels_per_iter = g_launches - saved;
+  W.kernels_per_iter = g_launches - saved;
   g_launches = saved;
-  CK(cudaGraphInstantiate(&P->gexec, P->graph, 0));
-  P->graph_mode = mode >= 2 ? 2 : 1;
+  CK(cudaGraphInstantiate(&W.gexec, W.graph, 0));
+  W.graph_mode = mode >= 2 ? 2 : 1;
 }
 
 // level positions along one axis after `level` coarsenings (fine-grid coordinates)
@@ -318,11 +323,6 @@ void make_bsr_from_stencil(tomg_problem* P, Level& Lv) {
   stencil_to_bsr(s, Lv.g, Lv.S64.p, Lv.rp.p, Lv.ci.p, Lv.V64.p);
 }
 
-void alloc_work(Level& Lv) {
-  Lv.b64.resize(Lv.n); Lv.x64.resize(Lv.n); Lv.r64.resize(Lv.n); Lv.y64.resize(Lv.n);
-  Lv.b32.resize(Lv.n); Lv.x32.resize(Lv.n); Lv.r32.resize(Lv.n); Lv.y32.resize(Lv.n);
-}
-
 void amg_extend(tomg_problem* P, int start) {
   cudaStream_t s = st(P);
   const tomg_options& o = P->opt;
@@ -372,7 +372,8 @@ void amg_extend(tomg_problem* P, int start) {
     Trp.resize(nn + 1); Tci.resize(nn); TV.resize((int64_t)nn * b * k); Bc.resize((int64_t)n_agg * k * k);
     amg_tentative(s, nn, b, k, n_agg, agg.p, B.p, Trp.p, Tci.p, TV.p, Bc.p);
     int nT = 0;
-    CK(cudaMemcpy(&nT, Trp.p + nn, sizeof(int), cudaMemcpyDeviceToHost));
+    CK(cudaMemcpyAsync(&nT, Trp.p + nn, sizeof(int), cudaMemcpyDeviceToHost, s));
+    CK(cudaStreamSynchronize(s));
     Bsr Tm;
     Tm.nbr = nn; Tm.nbc = n_agg; Tm.br = b; Tm.bc = k; Tm.nnzb = nT; Tm.rp = Trp.p; Tm.ci = Tci.p;
     // prolongator smoothing weight from rho(D^-1 A)
@@ -447,8 +448,35 @@ int levels_for_cap(int dim, int nx, int ny, int nz, int cap, int max_levels) {
   return L;
 }
 
+Work::~Work() {
+  if (gexec) cudaGraphExecDestroy(gexec);
+  if (graph) cudaGraphDestroy(graph);
+  if (sc_host) cudaFreeHost(sc_host);
+  if (partE_host) cudaFreeHost(partE_host);
+  if (partC_host) cudaFreeHost(partC_host);
+  for (cudaEvent_t e : {ev0, ev1, evdone, evsync})
+    if (e) cudaEventDestroy(e);
+  if (stream) cudaStreamDestroy(stream);
+}
+
+StreamScope::StreamScope(tomg_problem* p) : P(p) {
+  CK(cudaEventRecord(P->ev_in, P->ctx->stream));
+  CK(cudaStreamWaitEvent(P->stream, P->ev_in, 0));
+}
+StreamScope::~StreamScope() {
+  if (cudaEventRecord(P->ev_out, P->stream) == cudaSuccess)
+    cudaStreamWaitEvent(P->ctx->stream, P->ev_out, 0);
+}
+
 void problem_init(tomg_problem* P) {
-  cudaStream_t s = P->ctx->stream;
+  CK(cudaStreamCreateWithFlags(&P->stream, cudaStreamNonBlocking));
+  CK(cudaEventCreateWithFlags(&P->ev_in, cudaEventDisableTiming));
+  CK(cudaEventCreateWithFlags(&P->ev_out, cudaEventDisableTiming));
+  CK(cudaEventCreate(&P->ev0));
+  CK(cudaEventCreate(&P->ev1));
+  StreamScope scope(P);
+  cudaStream_t s = st(P);
+  set_alloc_stream(s);
   element_stiffness_host(P->dim, P->nu, P->Ke_host);
   const size_t nk = P->Ke_host.size();
   P->Ke64.resize(nk);
@@ -461,19 +489,8 @@ void problem_init(tomg_problem* P) {
   P->rho.resize(P->nel);
   P->E64.resize(P->nel);
   P->E32.resize(P->nel);
-  for (auto* v : {&P->f, &P->bvec, &P->x, &P->r, &P->p, &P->q, &P->z, &P->t}) v->resize(P->n);
-  const Ebe op{P->dim, P->nx, P->ny, P->nz, nullptr, nullptr, nullptr};
-  const int np = std::max(ebe_blocks(op), red_blocks(P->n));
-  P->partA.resize(np);
-  P->partB.resize(np);
-  P->partE.resize(np);
-  P->sc.resize(1);
-  P->sc.zero(s);
   P->flag_dev.resize(1);
-  CK(cudaMallocHost((void**)&P->sc_host, sizeof(Scalars)));
   CK(cudaMallocHost((void**)&P->flag_host, sizeof(int)));
-  CK(cudaEventCreate(&P->ev0));
-  CK(cudaEventCreate(&P->ev1));
   CK(cudaStreamSynchronize(s));
 }
 
@@ -485,8 +502,8 @@ void set_fixed(tomg_problem* P, const int64_t* dofs, int64_t count) {
     if (d < 0 || d >= P->n) TOMG_THROW(TOMG_E_INVALID, "fixed DOF %lld out of range [0, %lld)", (long long)d, (long long)P->n);
     m[d / P->dim] |= (uint8_t)(1u << (d % P->dim));
   }
-  CK(cudaMemcpyAsync(P->mask.p, m.data(), m.size(), cudaMemcpyHostToDevice, P->ctx->stream));
-  CK(cudaStreamSynchronize(P->ctx->stream));
+  CK(cudaMemcpyAsync(P->mask.p, m.data(), m.size(), cudaMemcpyHostToDevice, st(P)));
+  CK(cudaStreamSynchronize(st(P)));
   P->setup_valid = false;
 }
 
@@ -513,10 +530,11 @@ void setup(tomg_problem* P, const tomg_options& opt) {
     TOMG_THROW(TOMG_E_INVALID, "unknown preconditioner %d or precision %d", opt.pc, opt.prec);
   if (!(opt.rtol > 0.0) || opt.max_iter < 1 || opt.max_iter > 1000000 || !(opt.omega > 0.0) ||
       !(opt.omega < 2.0) || opt.n_pre < 1 || opt.n_pre > 8 || opt.n_post < 1 || opt.n_post > 8 ||
-      opt.max_coarse_dofs < 1 || opt.max_levels < 1 || opt.max_levels > 64 || opt.smoother != 0)
+      opt.max_coarse_dofs < 1 || opt.max_levels < 1 || opt.max_levels > 64 || opt.smoother != 0 ||
+      opt.concurrency < 0 || opt.concurrency > 64)
     TOMG_THROW(TOMG_E_INVALID, "invalid options");
-  destroy_graph(P);
   P->setup_valid = false;
+  P->setup_gen++;
   P->opt = opt;
   CK(cudaEventRecord(P->ev0, s));
   P->L.clear();
@@ -587,7 +605,6 @@ void setup(tomg_problem* P, const tomg_options& opt) {
     for (auto& lv : P->L)
       if (lv->kind == KIND_STENCIL) { lv->rp.release(); lv->ci.release(); lv->V64.release(); }
   }
-  for (auto& lv : P->L) alloc_work(*lv);
   CK(cudaEventRecord(P->ev1, s));
   CK(cudaEventSynchronize(P->ev1));
   float ms = 0.f;
@@ -599,66 +616,173 @@ void setup(tomg_problem* P, const tomg_options& opt) {
 // ----------------------------------------------------------------------------------------
 namespace {
 
-void init_solve(tomg_problem* P, const double* u0, bool u_on_device, int max_iter) {
-  cudaStream_t s = st(P);
+// solve slot k, sized for the current hierarchy (vectors reused when sizes match)
+Work& ensure_work(tomg_problem* P, int k) {
+  while ((int)P->works.size() <= k) {
+    auto W = std::make_unique<Work>();
+    CK(cudaStreamCreateWithFlags(&W->stream, cudaStreamNonBlocking));
+    CK(cudaEventCreate(&W->ev0));
+    CK(cudaEventCreate(&W->ev1));
+    CK(cudaEventCreateWithFlags(&W->evdone, cudaEventDisableTiming));
+    CK(cudaEventCreateWithFlags(&W->evsync, cudaEventDisableTiming));
+    const Ebe op{P->dim, P->nx, P->ny, P->nz, nullptr, nullptr, nullptr};
+    W->np = std::max(ebe_blocks(op), red_blocks(P->n));
+    CK(cudaMallocHost((void**)&W->sc_host, sizeof(Scalars)));
+    CK(cudaMallocHost((void**)&W->partE_host, sizeof(double) * W->np));
+    CK(cudaMallocHost((void**)&W->partC_host, sizeof(double) * W->np));
+    P->works.push_back(std::move(W));
+  }
+  Work& W = *P->works[k];
+  if (W.built_for != P->setup_gen) {
+    for (auto* v : {&W.f, &W.bvec, &W.x, &W.r, &W.p, &W.q, &W.z, &W.t}) v->resize(P->n);
+    for (auto* v : {&W.partA, &W.partB, &W.partE, &W.partC}) v->resize(W.np);
+    W.sc.resize(1);
+    W.lw.resize(P->L.size());
+    for (size_t l = 0; l < P->L.size(); l++) {
+      LevelWork& lw = W.lw[l];
+      const int64_t n = P->L[l]->n;
+      for (auto* v : {&lw.b64, &lw.x64, &lw.r64, &lw.y64}) v->resize(n);
+      for (auto* v : {&lw.b32, &lw.x32, &lw.r32, &lw.y32}) v->resize(n);
+    }
+    destroy_graph(W);
+    W.built_for = P->setup_gen;
+  }
+  return W;
+}
+
+// make W's stream wait for everything enqueued so far on the problem stream
+void fork_to(tomg_problem* P, Work& W) {
+  CK(cudaEventRecord(W.evsync, st(P)));
+  CK(cudaStreamWaitEvent(W.stream, W.evsync, 0));
+}
+void join_from(tomg_problem* P, Work& W) {
+  CK(cudaEventRecord(W.evsync, W.stream));
+  CK(cudaStreamWaitEvent(st(P), W.evsync, 0));
+}
+
+// initial residual, first preconditioned direction (graph-free)
+void init_solve(tomg_problem* P, Work& W, int max_iter) {
+  cudaStream_t s = W.stream;
   const int64_t n = P->n;
   const Ebe op = V<double>::ebe(P);
-  mask_vec(s, P->f.p, P->bvec.p, P->mask.p, P->dim, P->nn);
-  if (u0) {
-    CK(cudaMemcpyAsync(P->t.p, u0, n * 8, u_on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, s));
-    mask_vec(s, P->t.p, P->x.p, P->mask.p, P->dim, P->nn);
-  }
-  ebe_op<double>(s, MODE_RESID, op, P->x.p, P->r.p, P->bvec.p, nullptr, 0.0, nullptr, nullptr);
-  dot_partials(s, P->r.p, P->r.p, n, P->partA.p, nullptr);
-  dot_partials(s, P->bvec.p, P->bvec.p, n, P->partB.p, nullptr);
+  ebe_op<double>(s, MODE_RESID, op, W.x.p, W.r.p, W.bvec.p, nullptr, 0.0, nullptr, nullptr);
+  dot_partials(s, W.r.p, W.r.p, n, W.partA.p, nullptr);
+  dot_partials(s, W.bvec.p, W.bvec.p, n, W.partB.p, nullptr);
   Scalars h;
   memset(&h, 0, sizeof(h));
   h.rtol2 = P->opt.rtol * P->opt.rtol;
   h.max_iter = max_iter;
   h.flexible = P->opt.prec == TOMG_PREC_FP64 ? 0 : 1;
-  *P->sc_host = h;
-  CK(cudaMemcpyAsync(P->sc.p, P->sc_host, sizeof(Scalars), cudaMemcpyHostToDevice, s));
-  finish(s, FIN_INIT, P->partA.p, red_blocks(n), P->partB.p, red_blocks(n), P->sc.p);
-  apply_M_and_dots(P, nullptr, &P->sc.p->done);
-  finish(s, FIN_RZ0, P->partA.p, red_blocks(n), nullptr, 0, P->sc.p);
-  copy_f64(s, P->z.p, P->p.p, n, &P->sc.p->done);
+  *W.sc_host = h;
+  CK(cudaMemcpyAsync(W.sc.p, W.sc_host, sizeof(Scalars), cudaMemcpyHostToDevice, s));
+  finish(s, FIN_INIT, W.partA.p, red_blocks(n), W.partB.p, red_blocks(n), W.sc.p);
+  apply_M_and_dots(P, W, nullptr, &W.sc.p->done);
+  finish(s, FIN_RZ0, W.partA.p, red_blocks(n), nullptr, 0, W.sc.p);
+  copy_f64(s, W.z.p, W.p.p, n, &W.sc.p->done);
 }
 
-void read_scalars(tomg_problem* P) {
-  CK(cudaMemcpyAsync(P->sc_host, P->sc.p, sizeof(Scalars), cudaMemcpyDeviceToHost, st(P)));
-  CK(cudaStreamSynchronize(st(P)));
-}
-
-void run_iterations(tomg_problem* P) {
-  cudaStream_t s = st(P);
-  if (P->graph_mode == 2) {
-    CK(cudaGraphLaunch(P->gexec, s));
-    read_scalars(P);
-    g_launches += P->kernels_per_iter * std::max(1, P->sc_host->it);
-    return;
-  }
-  const int every = std::max(1, P->opt.check_every);
-  while (true) {
-    for (int k = 0; k < every; k++) {
-      if (P->graph_mode == 1) {
-        CK(cudaGraphLaunch(P->gexec, s));
-        g_launches += P->kernels_per_iter;
-      } else {
-        iteration_body(P);
+// one attempt of the outer loop on slot W, then the true residual and compliance partials
+// and the scalar state copied to pinned host memory; W.evdone marks completion
+void launch_attempt(tomg_problem* P, Work& W, int max_iter) {
+  cudaStream_t s = W.stream;
+  const int64_t n = P->n;
+  init_solve(P, W, max_iter);
+  if (W.graph_mode == 2) {
+    CK(cudaGraphLaunch(W.gexec, s));
+  } else {
+    // bounded host-polled loop: every check_every iterations read the scalar state
+    const int every = std::max(1, P->opt.check_every);
+    while (true) {
+      for (int k = 0; k < every; k++) {
+        if (W.graph_mode == 1) {
+          CK(cudaGraphLaunch(W.gexec, s));
+          g_launches += W.kernels_per_iter;
+        } else {
+          iteration_body(P, W);
+        }
       }
+      CK(cudaMemcpyAsync(W.sc_host, W.sc.p, sizeof(Scalars), cudaMemcpyDeviceToHost, s));
+      CK(cudaStreamSynchronize(s));
+      if (W.sc_host->done) break;
     }
-    read_scalars(P);
-    if (P->sc_host->done) return;
   }
+  const Ebe op = V<double>::ebe(P);
+  ebe_op<double>(s, MODE_RESID, op, W.x.p, W.t.p, W.bvec.p, nullptr, 0.0, nullptr, nullptr);
+  dot_partials(s, W.t.p, W.t.p, n, W.partE.p, nullptr);
+  dot_partials(s, W.f.p, W.x.p, n, W.partC.p, nullptr);
+  const int nr = red_blocks(n);
+  CK(cudaMemcpyAsync(W.sc_host, W.sc.p, sizeof(Scalars), cudaMemcpyDeviceToHost, s));
+  CK(cudaMemcpyAsync(W.partE_host, W.partE.p, sizeof(double) * nr, cudaMemcpyDeviceToHost, s));
+  CK(cudaMemcpyAsync(W.partC_host, W.partC.p, sizeof(double) * nr, cudaMemcpyDeviceToHost, s));
+  CK(cudaEventRecord(W.evdone, s));
 }
 
-double host_sum(tomg_problem* P, const double* partials, int np) {
-  std::vector<double> h(np);
-  CK(cudaMemcpyAsync(h.data(), partials, np * 8, cudaMemcpyDeviceToHost, st(P)));
-  CK(cudaStreamSynchronize(st(P)));
-  double t = 0.0;
-  for (double v : h) t += v;
-  return t;
+// stage right-hand side j on slot W and launch its first attempt
+void start_rhs(tomg_problem* P, Work& W, int j, const double* f, const double* u, int on_device) {
+  cudaStream_t s = W.stream;
+  const int64_t n = P->n;
+  const cudaMemcpyKind h2d = on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice;
+  W.rhs = j;
+  W.attempts = 0;
+  W.total_it = 0;
+  CK(cudaEventRecord(W.ev0, s));
+  CK(cudaMemcpyAsync(W.f.p, f + (int64_t)j * n, n * 8, h2d, s));
+  CK(cudaMemcpyAsync(W.t.p, u + (int64_t)j * n, n * 8, h2d, s));
+  mask_vec(s, W.f.p, W.bvec.p, P->mask.p, P->dim, P->nn);
+  mask_vec(s, W.t.p, W.x.p, P->mask.p, P->dim, P->nn);
+  if (!W.gexec && P->opt.use_graph > 0) build_graph(P, W);
+  launch_attempt(P, W, P->opt.max_iter);
+}
+
+// wait for slot W's attempt; returns true when its right-hand side is finished (result
+// written, u copy enqueued), false when it relaunched from the current iterate
+bool finish_rhs(tomg_problem* P, Work& W, double* u, int on_device, tomg_result* res) {
+  CK(cudaEventSynchronize(W.evdone));
+  const int nr = red_blocks(P->n);
+  const Scalars sc = *W.sc_host;
+  if (W.graph_mode == 2) g_launches += W.kernels_per_iter * std::max(1, sc.it);
+  W.total_it += sc.it;
+  W.attempts++;
+  double rr_true = 0.0, comp = 0.0;
+  for (int q = 0; q < nr; q++) rr_true += W.partE_host[q];
+  for (int q = 0; q < nr; q++) comp += W.partC_host[q];
+  const double bb = sc.bb;
+  const double tol2 = P->opt.rtol * P->opt.rtol * bb;
+  int status = sc.status;
+  if (status == TOMG_OK && bb > 0.0 && !(rr_true <= tol2)) {
+    // recursive residual converged but the true one did not: restart from x
+    if (W.attempts < 4 && W.total_it < P->opt.max_iter) {
+      launch_attempt(P, W, P->opt.max_iter - W.total_it);
+      return false;
+    }
+    status = TOMG_NOT_CONVERGED;
+  }
+  const int j = W.rhs;
+  const int64_t n = P->n;
+  CK(cudaMemcpyAsync(u + (int64_t)j * n, W.x.p, n * 8,
+                     on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost, W.stream));
+  CK(cudaEventRecord(W.ev1, W.stream));
+  CK(cudaEventSynchronize(W.ev1));
+  float ms = 0.f;
+  CK(cudaEventElapsedTime(&ms, W.ev0, W.ev1));
+  res[j].iterations = W.total_it;
+  res[j].rel_residual = bb > 0.0 ? std::sqrt(rr_true / bb) : 0.0;
+  res[j].compliance = comp;
+  res[j].setup_ms = P->setup_ms;
+  res[j].solve_ms = ms;
+  res[j].status = status;
+  if (status == TOMG_E_BREAKDOWN) {
+    static const char* what[] = {"?", "NaN residual", "z.r <= 0 with a CG preconditioner",
+                                 "p^T K p <= 0", "z.r or z.q not finite / z.r <= 0"};
+    const int code = sc.pad;
+    set_error("solver breakdown at iteration %d: %s (rhs %d)", W.total_it,
+              what[(code >= 0 && code <= 4) ? code : 0], j);
+  } else if (status == TOMG_NOT_CONVERGED) {
+    set_error("not converged after %d iterations (rel residual %.3e, rhs %d)", W.total_it,
+              res[j].rel_residual, j);
+  }
+  W.rhs = -1;
+  return true;
 }
 
 }  // namespace
@@ -667,62 +791,28 @@ tomg_status solve(tomg_problem* P, int nrhs, const double* f, double* u, int on_
                   tomg_result* res) {
   if (!P->setup_valid) TOMG_THROW(TOMG_E_INVALID, "tomg_solve: call tomg_setup after changing density or fixed DOFs");
   if (nrhs < 0 || (nrhs > 0 && (!f || !u || !res))) TOMG_THROW(TOMG_E_INVALID, "bad solve arguments");
-  cudaStream_t s = st(P);
-  const int64_t n = P->n;
-  if (!P->gexec && P->opt.use_graph > 0) build_graph(P);
+  if (nrhs == 0) return TOMG_OK;
+  const int slots = std::max(1, std::min(nrhs, P->opt.concurrency > 0 ? P->opt.concurrency : 1));
+  for (int k = 0; k < slots; k++) ensure_work(P, k);
+  for (int k = 0; k < slots; k++) fork_to(P, *P->works[k]);
+  int next = 0;
+  for (int k = 0; k < slots; k++) start_rhs(P, *P->works[k], next++, f, u, on_device);
+  int active = slots;
+  while (active > 0) {
+    for (int k = 0; k < slots; k++) {
+      Work& W = *P->works[k];
+      if (W.rhs < 0) continue;
+      if (!finish_rhs(P, W, u, on_device, res)) continue;
+      if (next < nrhs) start_rhs(P, W, next++, f, u, on_device);
+      else active--;
+    }
+  }
+  for (int k = 0; k < slots; k++) join_from(P, *P->works[k]);
+  CK(cudaStreamSynchronize(st(P)));
   tomg_status worst = TOMG_OK;
-  const cudaMemcpyKind h2d = on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice;
-  const cudaMemcpyKind d2h = on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost;
-  const Ebe op = V<double>::ebe(P);
   for (int j = 0; j < nrhs; j++) {
-    CK(cudaEventRecord(P->ev0, s));
-    CK(cudaMemcpyAsync(P->f.p, f + (int64_t)j * n, n * 8, h2d, s));
-    int total_it = 0;
-    int status = TOMG_OK;
-    double rr_true = 0.0, bb = 0.0;
-    const double* u0 = u + (int64_t)j * n;
-    for (int attempt = 0; attempt < 4; attempt++) {
-      init_solve(P, u0, on_device != 0, P->opt.max_iter - total_it);
-      u0 = nullptr;  // restarts keep x
-      run_iterations(P);
-      read_scalars(P);
-      total_it += P->sc_host->it;
-      status = P->sc_host->status;
-      bb = P->sc_host->bb;
-      // true residual of the final iterate
-      ebe_op<double>(s, MODE_RESID, op, P->x.p, P->t.p, P->bvec.p, nullptr, 0.0, nullptr, nullptr);
-      dot_partials(s, P->t.p, P->t.p, n, P->partE.p, nullptr);
-      rr_true = host_sum(P, P->partE.p, red_blocks(n));
-      if (status != TOMG_OK || bb == 0.0) break;
-      if (rr_true <= P->opt.rtol * P->opt.rtol * bb) break;
-      if (total_it >= P->opt.max_iter) { status = TOMG_NOT_CONVERGED; break; }
-      // recursive residual converged but the true one did not: restart from x
-    }
-    if (status == TOMG_OK && bb > 0.0 && !(rr_true <= P->opt.rtol * P->opt.rtol * bb)) status = TOMG_NOT_CONVERGED;
-    if (status == TOMG_E_BREAKDOWN) {
-      static const char* what[] = {"?", "NaN residual", "z.r <= 0 with a CG preconditioner",
-                                   "p^T K p <= 0", "z.r or z.q not finite / z.r <= 0"};
-      const int code = P->sc_host->pad;
-      set_error("solver breakdown at iteration %d: %s (rhs %d)", total_it,
-                what[(code >= 0 && code <= 4) ? code : 0], j);
-    } else if (status == TOMG_NOT_CONVERGED) {
-      set_error("not converged after %d iterations (rel residual %.3e, rhs %d)", total_it,
-                bb > 0.0 ? std::sqrt(rr_true / bb) : 0.0, j);
-    }
-    dot_partials(s, P->f.p, P->x.p, n, P->partE.p, nullptr);
-    const double comp = host_sum(P, P->partE.p, red_blocks(n));
-    CK(cudaMemcpyAsync(u + (int64_t)j * n, P->x.p, n * 8, d2h, s));
-    CK(cudaEventRecord(P->ev1, s));
-    CK(cudaEventSynchronize(P->ev1));
-    float ms = 0.f;
-    CK(cudaEventElapsedTime(&ms, P->ev0, P->ev1));
-    res[j].iterations = total_it;
-    res[j].rel_residual = bb > 0.0 ? std::sqrt(rr_true / bb) : 0.0;
-    res[j].compliance = comp;
-    res[j].setup_ms = P->setup_ms;
-    res[j].solve_ms = ms;
-    res[j].status = status;
-    if (status < 0 || (worst >= 0 && status > worst)) worst = (tomg_status)status;
+    const int s = res[j].status;
+    if (s < 0 || (worst >= 0 && s > worst)) worst = (tomg_status)s;
   }
   return worst;
 }
@@ -731,27 +821,31 @@ tomg_status solve(tomg_problem* P, int nrhs, const double* f, double* u, int on_
 void level_apply(tomg_problem* P, int level, int prec, const double* x, double* y) {
   if (!P->setup_valid) TOMG_THROW(TOMG_E_INVALID, "no valid setup");
   if (level < 0 || level >= (int)P->L.size()) TOMG_THROW(TOMG_E_INVALID, "bad level %d", level);
-  Level& Lv = *P->L[level];
+  Work& W = ensure_work(P, 0);
+  LevelWork& lw = W.lw[level];
+  const int64_t n = P->L[level]->n;
   cudaStream_t s = st(P);
   if (prec == TOMG_PREC_FP64) {
-    CK(cudaMemcpyAsync(Lv.b64.p, x, Lv.n * 8, cudaMemcpyDeviceToDevice, s));
-    level_op<double>(P, level, MODE_APPLY, Lv.b64.p, Lv.y64.p, nullptr, nullptr);
-    CK(cudaMemcpyAsync(y, Lv.y64.p, Lv.n * 8, cudaMemcpyDeviceToDevice, s));
+    CK(cudaMemcpyAsync(lw.b64.p, x, n * 8, cudaMemcpyDeviceToDevice, s));
+    level_op<double>(P, s, level, MODE_APPLY, lw.b64.p, lw.y64.p, nullptr, nullptr);
+    CK(cudaMemcpyAsync(y, lw.y64.p, n * 8, cudaMemcpyDeviceToDevice, s));
   } else {
-    cast_f64_f32(s, x, Lv.b32.p, Lv.n);
-    level_op<float>(P, level, MODE_APPLY, Lv.b32.p, Lv.y32.p, nullptr, nullptr);
-    cast_f32_f64(s, Lv.y32.p, y, Lv.n);
+    cast_f64_f32(s, x, lw.b32.p, n);
+    level_op<float>(P, s, level, MODE_APPLY, lw.b32.p, lw.y32.p, nullptr, nullptr);
+    cast_f32_f64(s, lw.y32.p, y, n);
   }
   CK(cudaStreamSynchronize(s));
 }
 
 void vcycle_apply(tomg_problem* P, const double* r, double* z) {
   if (!P->setup_valid) TOMG_THROW(TOMG_E_INVALID, "no valid setup");
-  cudaStream_t s = st(P);
-  CK(cudaMemcpyAsync(P->r.p, r, P->n * 8, cudaMemcpyDeviceToDevice, s));
-  apply_M_and_dots(P, nullptr, nullptr);
-  CK(cudaMemcpyAsync(z, P->z.p, P->n * 8, cudaMemcpyDeviceToDevice, s));
-  CK(cudaStreamSynchronize(s));
+  Work& W = ensure_work(P, 0);
+  fork_to(P, W);
+  CK(cudaMemcpyAsync(W.r.p, r, P->n * 8, cudaMemcpyDeviceToDevice, W.stream));
+  apply_M_and_dots(P, W, nullptr, nullptr);
+  CK(cudaMemcpyAsync(z, W.z.p, P->n * 8, cudaMemcpyDeviceToDevice, W.stream));
+  join_from(P, W);
+  CK(cudaStreamSynchronize(st(P)));
 }
 
 void coarse_apply(tomg_problem* P, const double* b, double* x) {
@@ -820,22 +914,13 @@ void prolong_export(tomg_problem* P, int level, int64_t* nnzb, int64_t* hrp, int
   if (hrp) bsr_to_host(s, (int)Lv.nn, Lv.b * Lv.b, rp.p, ci.p, v.p, nz, hrp, hci, hv);
 }
 
-}  // namespace tomg
 
-tomg_problem::~tomg_problem() {
-  tomg::destroy_graph(this);
-  if (sc_host) cudaFreeHost(sc_host);
-  if (flag_host) cudaFreeHost(flag_host);
-  if (ev0) cudaEventDestroy(ev0);
-  if (ev1) cudaEventDestroy(ev1);
-}
-
-namespace tomg {
 double time_fine_operator(tomg_problem* P, int op, int prec, int reps, int cold_l2) {
   if (!P->setup_valid) TOMG_THROW(TOMG_E_INVALID, "no valid setup");
   if (op < 0 || op > 2 || reps < 1 || reps > 10000) TOMG_THROW(TOMG_E_INVALID, "bad timing request");
   cudaStream_t s = st(P);
-  Level& L0 = *P->L[0];
+  Work& W = ensure_work(P, 0);
+  LevelWork& l0 = W.lw[0];
   const int mode = op == 0 ? MODE_APPLY : (op == 1 ? MODE_RESID : MODE_JACOBI);
   DBuf<char> flush;
   if (cold_l2) flush.resize((size_t)256 << 20);
@@ -844,8 +929,8 @@ double time_fine_operator(tomg_problem* P, int op, int prec, int reps, int cold_
   for (int k = 0; k < reps; k++) {
     if (cold_l2) CK(cudaMemsetAsync(flush.p, k & 0xff, flush.n, s));
     CK(cudaEventRecord(ev[2 * k], s));
-    if (prec == TOMG_PREC_FP64) level_op<double>(P, 0, mode, L0.x64.p, L0.y64.p, L0.b64.p, nullptr);
-    else level_op<float>(P, 0, mode, L0.x32.p, L0.y32.p, L0.b32.p, nullptr);
+    if (prec == TOMG_PREC_FP64) level_op<double>(P, s, 0, mode, l0.x64.p, l0.y64.p, l0.b64.p, nullptr);
+    else level_op<float>(P, s, 0, mode, l0.x32.p, l0.y32.p, l0.b32.p, nullptr);
     CK(cudaEventRecord(ev[2 * k + 1], s));
   }
   CK(cudaStreamSynchronize(s));
@@ -858,4 +943,21 @@ double time_fine_operator(tomg_problem* P, int op, int prec, int reps, int cold_
   for (auto& e : ev) cudaEventDestroy(e);
   return tot / reps;
 }
+
 }  // namespace tomg
+
+tomg_problem::~tomg_problem() {
+  if (stream) cudaStreamSynchronize(stream);
+  works.clear();
+  L.clear();
+  if (flag_host) cudaFreeHost(flag_host);
+  for (cudaEvent_t e : {ev0, ev1, ev_in, ev_out})
+    if (e) cudaEventDestroy(e);
+  // device buffers are released by their destructors on this stream before it is destroyed
+  Ke64.release(); Ke32.release(); mask.release(); rho.release(); E64.release(); E32.release();
+  flag_dev.release(); Ainv64.release(); Ainv32.release();
+  if (stream) {
+    cudaStreamSynchronize(stream);
+    cudaStreamDestroy(stream);
+  }
+}

@@ -1,7 +1,13 @@
 // Host runtime of the tomg library: problem state, hierarchy setup, V-cycle, outer Krylov
-// loop and its CUDA-graph capture.
+// loop, its CUDA-graph capture, and concurrent solve slots.
+//
+// Streams: every problem owns a stream; API calls order themselves after the context stream
+// on entry and make the context stream wait for them on exit.  A solve of several right-hand
+// sides spreads them over solve slots (each with its own stream, vectors and captured graph)
+// that share the read-only hierarchy, so their kernels overlap on the device.
 #pragma once
 
+#include <atomic>
 #include <memory>
 
 #include "ops.h"
@@ -43,9 +49,6 @@ struct Level {
   DBuf<float> Pv32, Rv32;
   int64_t Pnnzb = 0;
   DBuf<int> agg;
-  // V-cycle work vectors
-  DBuf<double> b64, x64, r64, y64;
-  DBuf<float> b32, x32, r32, y32;
 
   Bsr bsr() const {
     Bsr A;
@@ -70,10 +73,43 @@ struct Level {
   }
 };
 
+// V-cycle work vectors of one level for one solve slot
+struct LevelWork {
+  DBuf<double> b64, x64, r64, y64;
+  DBuf<float> b32, x32, r32, y32;
+};
+
+// One solve slot: stream, outer Krylov vectors, V-cycle work, scalars and captured iteration
+struct Work {
+  cudaStream_t stream = nullptr;
+  DBuf<double> f, bvec, x, r, p, q, z, t;
+  DBuf<double> partA, partB, partE, partC;
+  DBuf<Scalars> sc;
+  Scalars* sc_host = nullptr;  // pinned
+  double* partE_host = nullptr;  // pinned, true-residual partials
+  double* partC_host = nullptr;  // pinned, compliance partials
+  int np = 0;
+  std::vector<LevelWork> lw;
+  int64_t built_for = -1;  // setup generation the vectors / graph belong to
+  cudaGraph_t graph = nullptr;
+  cudaGraphExec_t gexec = nullptr;
+  int graph_mode = 0;  // 0 none, 1 one-iteration graph, 2 conditional while loop
+  int64_t kernels_per_iter = 0;
+  cudaEvent_t ev0 = nullptr, ev1 = nullptr, evdone = nullptr, evsync = nullptr;
+  // per right-hand side bookkeeping while a solve is in flight
+  int rhs = -1;
+  int attempts = 0;
+  int total_it = 0;
+  ~Work();
+};
+
+
 }  // namespace tomg
 
 struct tomg_problem {
   tomg_ctx* ctx = nullptr;
+  cudaStream_t stream = nullptr;  // the problem's own stream
+  cudaEvent_t ev_in = nullptr, ev_out = nullptr;
   int dim = 2, nx = 0, ny = 0, nz = 1;
   double E0 = 1, Emin = 1e-9, penal = 3, nu = 0.3;
   int64_t nn = 0, n = 0, nel = 0;
@@ -86,6 +122,7 @@ struct tomg_problem {
   tomg::DBuf<float> E32;
   // hierarchy
   bool setup_valid = false;
+  int64_t setup_gen = 0;
   tomg_options opt{};
   double setup_ms = 0.0;
   bool jacobi_only = false;
@@ -93,23 +130,22 @@ struct tomg_problem {
   int nc = 0;  // coarsest DOFs
   tomg::DBuf<double> Ainv64;
   tomg::DBuf<float> Ainv32;
-  // outer Krylov state (one right-hand side at a time)
-  tomg::DBuf<double> f, bvec, x, r, p, q, z, t;
-  tomg::DBuf<double> partA, partB, partE;
-  tomg::DBuf<tomg::Scalars> sc;
-  tomg::Scalars* sc_host = nullptr;  // pinned
-  int* flag_host = nullptr;          // pinned
+  // solve slots
+  std::vector<std::unique_ptr<tomg::Work>> works;
+  int* flag_host = nullptr;  // pinned
   tomg::DBuf<int> flag_dev;
-  // captured outer iteration
-  cudaGraph_t graph = nullptr;
-  cudaGraphExec_t gexec = nullptr;
-  int graph_mode = 0;         // 0 none, 1 one-iteration graph, 2 conditional while loop
-  int64_t kernels_per_iter = 0;
   cudaEvent_t ev0 = nullptr, ev1 = nullptr;
   ~tomg_problem();
 };
 
 namespace tomg {
+// order the problem's stream after the context stream (entry) / the context after it (exit)
+struct StreamScope {
+  tomg_problem* P;
+  explicit StreamScope(tomg_problem* p);
+  ~StreamScope();
+};
+
 void problem_init(tomg_problem* P);
 void set_fixed(tomg_problem* P, const int64_t* dofs, int64_t count);
 void set_density(tomg_problem* P, const double* rho, int on_device);
@@ -123,4 +159,5 @@ void coarse_apply(tomg_problem* P, const double* b, double* x);
 void level_export(tomg_problem* P, int level, int64_t* nnzb, int64_t* rp, int64_t* ci, double* v);
 void prolong_export(tomg_problem* P, int level, int64_t* nnzb, int64_t* rp, int64_t* ci, double* v);
 void element_stiffness_host(int dim, double nu, std::vector<double>& Ke);
+double time_fine_operator(tomg_problem* P, int op, int prec, int reps, int cold_l2);
 }  // namespace tomg

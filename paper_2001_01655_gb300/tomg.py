@@ -30,7 +30,7 @@ class Options(C.Structure):
                 ("n_levels", C.c_int), ("max_coarse_dofs", C.c_int), ("n_geo_levels", C.c_int),
                 ("smoother", C.c_int), ("omega", C.c_double), ("n_pre", C.c_int),
                 ("n_post", C.c_int), ("soc_beta", C.c_double), ("check_every", C.c_int),
-                ("use_graph", C.c_int), ("max_levels", C.c_int)]
+                ("use_graph", C.c_int), ("max_levels", C.c_int), ("concurrency", C.c_int)]
 
 
 class Result(C.Structure):
@@ -78,6 +78,13 @@ _SIGS = {
     "tomg_element_stiffness": (C.c_int, [_P, _P]),
     "tomg_time_fine_operator": (C.c_int, [_P, C.c_int, C.c_int, C.c_int, C.c_int, _D]),
     "tomg_fine_apply_f32_noalloc": (C.c_int, [_P, _P, _P]),
+    "tomg_server_create": (C.c_int, [_P, C.c_size_t, C.c_int, C.POINTER(_P)]),
+    "tomg_server_submit": (C.c_int, [_P, _P, _P, C.c_int, _P, _P, C.POINTER(Options),
+                                     C.POINTER(C.c_uint64)]),
+    "tomg_server_wait": (C.c_int, [_P, C.c_uint64, C.c_int, C.POINTER(Result)]),
+    "tomg_server_stats": (C.c_int, [_P, _D, _D, _D, _I64, C.POINTER(C.c_int),
+                                    C.POINTER(C.c_size_t)]),
+    "tomg_server_destroy": (C.c_int, [_P]),
 }
 
 
@@ -323,3 +330,64 @@ class Problem:
         Ke = np.zeros((nd, nd))
         _check(load().tomg_element_stiffness(self.h, C.c_void_p(Ke.ctypes.data)))
         return Ke
+
+
+class Server:
+    """Continuous-batching request loop over many problems (tomg_server_*)."""
+
+    def __init__(self, ctx: Context, hbm_budget_bytes: int, max_slots: int = 4):
+        h = C.c_void_p()
+        _check(load().tomg_server_create(ctx.h, C.c_size_t(int(hbm_budget_bytes)), max_slots,
+                                         C.byref(h)))
+        self.h, self.ctx = h, ctx
+        self._keep = {}
+        self._problems = {}
+
+    def submit(self, problem: Problem, rho, f, u=None, opt: Options | None = None, **kw):
+        """Queue one design update; returns a ticket.  rho, f, u: numpy host arrays (copied;
+        u receives the solution)."""
+        rho = np.ascontiguousarray(rho, dtype=np.float64)
+        f = np.ascontiguousarray(f, dtype=np.float64)
+        nrhs = 1 if f.ndim == 1 else f.shape[0]
+        if u is not None and (u.dtype != np.float64 or not u.flags.c_contiguous):
+            raise TypeError("u must be a contiguous float64 array")
+        o = opt if opt is not None else default_options(**kw)
+        t = C.c_uint64()
+        st = load().tomg_server_submit(self.h, problem.h, C.c_void_p(rho.ctypes.data), nrhs,
+                                       C.c_void_p(f.ctypes.data),
+                                       None if u is None else C.c_void_p(u.ctypes.data),
+                                       C.byref(o), C.byref(t))
+        _check(st)
+        self._keep[t.value] = (rho, f, u, nrhs)
+        self._problems[id(problem)] = problem  # problems must outlive the server
+        return t.value
+
+    def wait(self, ticket, timeout_ms=-1):
+        nrhs = self._keep.get(ticket, (None, None, None, 1))[3]
+        res = (Result * nrhs)()
+        st = load().tomg_server_wait(self.h, ticket, timeout_ms, res)
+        if st == E_TIMEOUT:
+            raise TomgError(st, load().tomg_last_error().decode())
+        self._keep.pop(ticket, None)
+        _check(st)
+        return [res[i].as_dict() for i in range(nrhs)]
+
+    def stats(self):
+        p50, p99, sps = C.c_double(), C.c_double(), C.c_double()
+        done, peak = C.c_int64(), C.c_int()
+        pb = C.c_size_t()
+        _check(load().tomg_server_stats(self.h, C.byref(p50), C.byref(p99), C.byref(sps),
+                                        C.byref(done), C.byref(peak), C.byref(pb)))
+        return {"p50_ms": p50.value, "p99_ms": p99.value, "solves_per_s": sps.value,
+                "completed": done.value, "peak_active": peak.value, "peak_bytes": pb.value}
+
+    def close(self):
+        if getattr(self, "h", None):
+            load().tomg_server_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
