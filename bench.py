@@ -41,6 +41,14 @@ def parse():
     ap.add_argument("--pc", default=HEADLINE["pc"])
     ap.add_argument("--cap", type=int, default=HEADLINE["max_coarse_dofs"])
     ap.add_argument("--n-geo", type=int, default=HEADLINE["n_geo_levels"])
+    ap.add_argument("--graph-mode", type=int, default=2,
+                    help="2: whole solve in one graph (device while loop); 1: one graph per "
+                         "iteration (host polls); 0: no graphs")
+    ap.add_argument("--serving", type=int, default=24,
+                    help="requests of the mixed-size serving stream replayed after the main "
+                         "measurement (0: skip)")
+    ap.add_argument("--serving-updates", type=int, default=2)
+    ap.add_argument("--slots", type=int, default=4)
     ap.add_argument("--no-fp64", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
     return ap.parse_args()
@@ -137,7 +145,7 @@ def run_gpu(args, rank, world, local):
     u_d = torch.zeros_like(f_d)
     flush = torch.empty(256 << 20, dtype=torch.int8, device=dev)  # 256 MB > 129 MB L2
     opts = dict(pc=args.pc, max_coarse_dofs=args.cap, n_geo_levels=args.n_geo, rtol=1e-8,
-                max_iter=2000)
+                max_iter=2000, use_graph=args.graph_mode)
 
     def step(prec):
         u_d.zero_()
@@ -221,7 +229,46 @@ def run_gpu(args, rank, world, local):
                   "h2d_bytes_per_step": int(rho_h.nbytes + 2 * f_h.nbytes),
                   "d2h_bytes_per_step": int(f_h.nbytes)}
     out["roofline"] = roofline(P, ctx, p, stream)
+    if args.serving > 0:
+        out["serving"] = serving_run(tomg, ctx, args.serving, args.serving_updates, args.slots)
     return out
+
+
+def serving_run(tomg, ctx, n_requests, n_updates, slots):
+    """Replay the mixed 2D/3D request stream (Poisson arrivals, 5 % density noise per update)
+    through the continuous-batching server; every update of a request is submitted at the
+    request's arrival time and warm-starts from the previous one on the device."""
+    import workloads as W
+    stream = W.serving_stream(n_requests=n_requests, n_updates=n_updates)
+    opt = dict(pc="hybrid", prec="fp32", n_geo_levels=3, max_coarse_dofs=1000, concurrency=1,
+               max_iter=2000)
+    probs = []
+    for r in stream:
+        p = W.serving_problem(r, 0)
+        P = tomg.Problem(ctx, p.dim, p.nx, p.ny, p.nz, p.E0, p.Emin, p.penal, p.nu)
+        P.set_fixed_dofs(p.fixed)
+        dens = [W.serving_density(r, k) for k in range(n_updates)]
+        probs.append((P, p, dens))
+    srv = tomg.Server(ctx, 64 << 30, slots)
+    t0 = time.perf_counter()
+    tickets = []
+    for (P, p, dens), r in zip(probs, stream):
+        wait = r["t_arrive"] - (time.perf_counter() - t0)
+        if wait > 0:
+            time.sleep(wait)
+        for k in range(n_updates):
+            tickets.append(srv.submit(P, dens[k], p.f[0], **opt))
+    statuses = [srv.wait(t)[0]["status"] for t in tickets]
+    wall = time.perf_counter() - t0
+    st = srv.stats()
+    srv.close()
+    dofs = sorted({p.n for _, p, _ in probs})
+    return {"requests": n_requests, "updates_per_request": n_updates, "slots": slots,
+            "solves": len(tickets), "solves_per_s": len(tickets) / wall,
+            "p50_ms": st["p50_ms"], "p99_ms": st["p99_ms"], "peak_active": st["peak_active"],
+            "converged": int(sum(s == 0 for s in statuses)), "dofs_min": dofs[0],
+            "dofs_max": dofs[-1], "preconditioner": "hybrid (3 geometric levels + SA-AMG < 1000 DOFs)",
+            "arrivals": "Poisson, 50 requests/s; each request's updates queued on arrival"}
 
 
 def roofline(P, ctx, p, stream):

@@ -18,6 +18,10 @@ void set_error(const char* fmt, ...) {
 }
 const char* get_error() { return g_err; }
 
+static thread_local bool g_pdl = false;
+bool pdl_enabled() { return g_pdl; }
+void set_pdl(bool on) { g_pdl = on; }
+
 static thread_local cudaStream_t g_alloc_stream = nullptr;
 cudaStream_t alloc_stream() { return g_alloc_stream; }
 void set_alloc_stream(cudaStream_t s) { g_alloc_stream = s; }

@@ -43,11 +43,38 @@ struct Error {
 // count of kernels launched by this library (per process; contexts read deltas)
 extern std::atomic<int64_t> g_launches;
 
-#define LAUNCH(kernel, grid, block, smem, stream, ...)                      \
-  do {                                                                     \
-    kernel<<<(grid), (block), (smem), (stream)>>>(__VA_ARGS__);            \
-    ::tomg::g_launches++;                                                  \
-    CK(cudaGetLastError());                                                \
+// Programmatic dependent launch for the captured solve loop: while enabled (on this thread),
+// kernels are launched with programmatic stream serialisation, so the next kernel of the
+// chain is scheduled while the current one drains.  Every kernel of the loop starts with
+// pdl_prologue(): it lets its dependants launch, then waits until its predecessor grid has
+// completed and its writes are visible, before touching any data.
+bool pdl_enabled();
+void set_pdl(bool on);
+
+__device__ __forceinline__ void pdl_prologue() {
+  asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
+  asm volatile("griddepcontrol.wait;" ::: "memory");
+}
+
+#define LAUNCH(kernel, grid, block, smem, strm_, ...)                                   \
+  do {                                                                                 \
+    if (::tomg::pdl_enabled()) {                                                       \
+      cudaLaunchConfig_t cfg_ = {};                                                    \
+      cfg_.gridDim = dim3(grid);                                                       \
+      cfg_.blockDim = dim3(block);                                                     \
+      cfg_.dynamicSmemBytes = (smem);                                                  \
+      cfg_.stream = (strm_);                                                           \
+      cudaLaunchAttribute at_[1];                                                      \
+      at_[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;                  \
+      at_[0].val.programmaticStreamSerializationAllowed = 1;                           \
+      cfg_.attrs = at_;                                                                \
+      cfg_.numAttrs = 1;                                                               \
+      CK(cudaLaunchKernelEx(&cfg_, kernel, __VA_ARGS__));                              \
+    } else {                                                                           \
+      kernel<<<(grid), (block), (smem), (strm_)>>>(__VA_ARGS__);                       \
+    }                                                                                  \
+    ::tomg::g_launches++;                                                              \
+    CK(cudaGetLastError());                                                            \
   } while (0)
 
 // ---------------------------------------------------------------------------------------

@@ -29,6 +29,7 @@ __global__ void __launch_bounds__(256) k_bsr(int nbr, const int* __restrict__ rp
                                              const T* __restrict__ x, T* __restrict__ y,
                                              const T* __restrict__ b, const T* __restrict__ Dinv,
                                              T omega, const int* done) {
+  pdl_prologue();
   if (solve_done(done)) return;
   const int gtid = blockIdx.x * blockDim.x + threadIdx.x;
   const int i = gtid / G, sub = gtid % G;
@@ -78,6 +79,7 @@ __global__ void __launch_bounds__(256) k_bsr_rect(int nbr, const int* __restrict
                                                   const T* __restrict__ V, const T* __restrict__ x,
                                                   T* __restrict__ y, int accumulate,
                                                   const int* done) {
+  pdl_prologue();
   if (solve_done(done)) return;
   const int gtid = blockIdx.x * blockDim.x + threadIdx.x;
   const int i = gtid / G, sub = gtid % G;

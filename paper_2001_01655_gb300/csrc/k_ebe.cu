@@ -21,6 +21,7 @@ __global__ void __launch_bounds__(256) k_ebe(int nx, int ny, int nz, const T* __
   constexpr int NN = 1 << DIM, ND = DIM * NN;
   __shared__ T sKe[ND * ND];
   __shared__ double sred[32];
+  pdl_prologue();
   if (solve_done(done)) return;
   for (int t = threadIdx.x; t < ND * ND; t += blockDim.x) sKe[t] = Ke[t];
   __syncthreads();
@@ -197,6 +198,12 @@ void launch_ebe(cudaStream_t s, const Ebe& op, const T* x, T* y, const T* b, con
                 double omega, const int* done, double* parts) {
   // FP32 quad4: tiled kernel (memory/latency bound).  FP64: the node-per-thread kernel, whose
   // low register count keeps enough warps in flight to hide the long FP64 pipe latency.
+  if (DIM == 3 && sizeof(T) == 4 && !DOT) {
+    ebe3d_launch(s, MODE, op, reinterpret_cast<const float*>(x), reinterpret_cast<float*>(y),
+                 reinterpret_cast<const float*>(b), reinterpret_cast<const float*>(Dinv), omega,
+                 done);
+    return;
+  }
   if (DIM == 2 && sizeof(T) == 4) {
     ebe2d_launch<T, MODE, DOT>(s, op, x, y, b, Dinv, omega, done, parts);
     return;

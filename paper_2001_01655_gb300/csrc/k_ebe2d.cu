@@ -32,6 +32,7 @@ __global__ void __launch_bounds__(BX * BY) k_ebe2(int nx, int ny, const T* __res
   __shared__ V2 sx[TH + 2][BX + 2];
   __shared__ T sE[TH + 1][BX + 1];
   __shared__ double red[BX * BY / 32];
+  pdl_prologue();
   if (solve_done(done)) return;
   const int tid = threadIdx.y * BX + threadIdx.x;
   const int i0 = blockIdx.x * BX, j0 = blockIdx.y * TH;

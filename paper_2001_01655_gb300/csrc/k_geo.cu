@@ -33,6 +33,7 @@ __global__ void __launch_bounds__(256) k_stencil(int nx, int ny, int nz, const T
                                                  const T* __restrict__ Dinv, T omega,
                                                  const int* done) {
   constexpr int NO = (DIM == 3) ? 27 : 9, BB = DIM * DIM;
+  pdl_prologue();
   if (solve_done(done)) return;
   const int64_t nn = (int64_t)(nx + 1) * (ny + 1) * (DIM == 3 ? nz + 1 : 1);
   const int64_t node = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
@@ -74,6 +75,50 @@ __global__ void __launch_bounds__(256) k_stencil(int nx, int ny, int nz, const T
       y[DIM * node + c] = x[DIM * node + c] + omega * v;
     }
   }
+}
+
+// y = S x with one FP64 partial of x . y per block (the outer CG apply on the assembled
+// fine-level stencil: 9 / 27 node blocks per row instead of 4 / 8 element products)
+template <int DIM>
+__global__ void __launch_bounds__(256) k_stencil_apply_dot(int nx, int ny, int nz,
+                                                           const double* __restrict__ S,
+                                                           const double* __restrict__ x,
+                                                           double* __restrict__ y,
+                                                           const int* done, double* partials) {
+  constexpr int NO = (DIM == 3) ? 27 : 9, BB = DIM * DIM;
+  __shared__ double sred[32];
+  pdl_prologue();
+  if (solve_done(done)) return;
+  const int64_t nn = (int64_t)(nx + 1) * (ny + 1) * (DIM == 3 ? nz + 1 : 1);
+  const int64_t node = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  double dotv = 0.0;
+  if (node < nn) {
+    int i, j, k;
+    node_ijk(node, nx, ny, DIM, i, j, k);
+    double acc[DIM];
+#pragma unroll
+    for (int c = 0; c < DIM; c++) acc[c] = 0.0;
+#pragma unroll
+    for (int o = 0; o < NO; o++) {
+      const int ox = o % 3 - 1, oy = (o / 3) % 3 - 1, oz = (DIM == 3) ? o / 9 - 1 : 0;
+      if (!in_grid<DIM>(i + ox, j + oy, k + oz, nx, ny, nz)) continue;
+      const int64_t nb = node_id(i + ox, j + oy, k + oz, nx, ny);
+      double xv[DIM];
+#pragma unroll
+      for (int c = 0; c < DIM; c++) xv[c] = x[DIM * nb + c];
+#pragma unroll
+      for (int r = 0; r < DIM; r++)
+#pragma unroll
+        for (int c = 0; c < DIM; c++) acc[r] += S[((int64_t)o * BB + r * DIM + c) * nn + node] * xv[c];
+    }
+#pragma unroll
+    for (int c = 0; c < DIM; c++) {
+      y[DIM * node + c] = acc[c];
+      dotv += x[DIM * node + c] * acc[c];
+    }
+  }
+  const double tot = block_sum(dotv, sred);
+  if (threadIdx.x == 0) partials[blockIdx.x] = tot;
 }
 
 template <int DIM>
@@ -158,6 +203,7 @@ __global__ void k_rap(int fnx, int fny, int fnz, int cnx, int cny, int cnz,
 template <class T, int DIM>
 __global__ void k_restrict(int fnx, int fny, int fnz, int cnx, int cny, int cnz,
                            const T* __restrict__ rf, T* __restrict__ bc, const int* done) {
+  pdl_prologue();
   if (solve_done(done)) return;
   const int64_t nnc = (int64_t)(cnx + 1) * (cny + 1) * (DIM == 3 ? cnz + 1 : 1);
   const int64_t I = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
@@ -207,6 +253,7 @@ __device__ __forceinline__ int coarse_of(int p, int nf, int* I, double* w) {
 template <class T, int DIM>
 __global__ void k_prolong_add(int fnx, int fny, int fnz, int cnx, int cny, int cnz,
                               const T* __restrict__ xc, T* __restrict__ xf, const int* done) {
+  pdl_prologue();
   if (solve_done(done)) return;
   const int64_t nnf = (int64_t)(fnx + 1) * (fny + 1) * (DIM == 3 ? fnz + 1 : 1);
   const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
@@ -334,6 +381,17 @@ template void stencil_op<float>(cudaStream_t, int, const Geo&, const float*, con
                                 const float*, const float*, double, const int*);
 template void stencil_op<double>(cudaStream_t, int, const Geo&, const double*, const double*,
                                  double*, const double*, const double*, double, const int*);
+
+int stencil_blocks(const Geo& g) { return ceil_div(g.nodes(), 256); }
+
+void stencil_apply_dot(cudaStream_t s, const Geo& g, const double* S, const double* x, double* y,
+                       const int* done, double* partials) {
+  const int grid = stencil_blocks(g);
+  if (g.dim == 2)
+    LAUNCH(k_stencil_apply_dot<2>, grid, 256, 0, s, g.nx, g.ny, g.nz, S, x, y, done, partials);
+  else
+    LAUNCH(k_stencil_apply_dot<3>, grid, 256, 0, s, g.nx, g.ny, g.nz, S, x, y, done, partials);
+}
 
 void stencil_block_diag_inv(cudaStream_t s, const Geo& g, const double* S, double* Dinv64,
                             float* Dinv32) {

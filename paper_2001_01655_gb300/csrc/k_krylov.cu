@@ -20,6 +20,7 @@ __global__ void __launch_bounds__(RED_THREADS) k_dot(const double* __restrict__ 
                                                      const double* __restrict__ y, int64_t n,
                                                      double* partials, const int* done) {
   __shared__ double sred[32];
+  pdl_prologue();
   if (solve_done(done)) return;
   double s = 0.0;
   for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
@@ -32,6 +33,7 @@ __global__ void __launch_bounds__(256) k_finish(int kind, const double* __restri
                                                  const double* __restrict__ pb, int nb,
                                                  Scalars* sc) {
   __shared__ double sred[32];
+  pdl_prologue();
   if (kind != FIN_INIT && sc->done) return;
   double a = 0.0, b = 0.0;
   for (int i = threadIdx.x; i < na; i += blockDim.x) a += pa[i];
@@ -85,6 +87,7 @@ __global__ void __launch_bounds__(RED_THREADS) k_xr(double* __restrict__ x, doub
                                                     const double* __restrict__ q, int64_t n,
                                                     const Scalars* sc, double* partials) {
   __shared__ double sred[32];
+  pdl_prologue();
   if (sc->done) return;
   const double alpha = sc->alpha;
   double s = 0.0;
@@ -100,6 +103,7 @@ __global__ void __launch_bounds__(RED_THREADS) k_xr(double* __restrict__ x, doub
 
 __global__ void k_p(double* __restrict__ p, const double* __restrict__ z, int64_t n,
                     const Scalars* sc) {
+  pdl_prologue();
   if (sc->done) return;
   const double beta = sc->beta;
   for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
@@ -112,6 +116,7 @@ __global__ void __launch_bounds__(RED_THREADS) k_zdots(const T* __restrict__ z, 
                                                        const double* __restrict__ q, int64_t n,
                                                        double* pa, double* pb, const int* done) {
   __shared__ double sred[32];
+  pdl_prologue();
   if (solve_done(done)) return;
   double a = 0.0, b = 0.0;
   for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
@@ -131,6 +136,7 @@ __global__ void __launch_bounds__(RED_THREADS) k_zdots(const T* __restrict__ z, 
 template <class T>
 __global__ void k_cast_in(const double* __restrict__ a, T* __restrict__ b, int64_t n,
                           const int* done) {
+  pdl_prologue();
   if (solve_done(done)) return;
   for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
     b[i] = (T)a[i];
@@ -147,6 +153,7 @@ __global__ void k_mask_vec(const double* __restrict__ f, double* __restrict__ b,
 template <class T, int B>
 __global__ void k_jacobi0(int64_t nodes, const T* __restrict__ Dinv, const T* __restrict__ b,
                           T* __restrict__ x, T omega, const int* done) {
+  pdl_prologue();
   if (solve_done(done)) return;
   const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= nodes) return;
@@ -166,6 +173,7 @@ __global__ void k_jacobi0(int64_t nodes, const T* __restrict__ Dinv, const T* __
 template <class T>
 __global__ void k_gemv(int n, const T* __restrict__ A, const T* __restrict__ b, T* __restrict__ x,
                        const int* done) {
+  pdl_prologue();
   if (solve_done(done)) return;
   const int row = (blockIdx.x * blockDim.x + threadIdx.x) >> 5, lane = threadIdx.x & 31;
   if (row >= n) return;
@@ -339,6 +347,7 @@ __global__ void k_ltl(int n, const double* __restrict__ Li, double* Ainv) {
 }
 
 __global__ void k_set_cond(cudaGraphConditionalHandle h, const Scalars* sc) {
+  pdl_prologue();
   cudaGraphSetConditional(h, sc->done ? 0u : 1u);
 }
 

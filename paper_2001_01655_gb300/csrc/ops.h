@@ -28,6 +28,9 @@ template <class T, int MODE, bool DOT>
 void ebe2d_launch(cudaStream_t s, const Ebe& op, const T* x, T* y, const T* b, const T* Dinv,
                   double omega, const int* done, double* parts);
 int ebe2d_blocks(const Ebe& op);
+// hex8 FP32 tiled implementation behind ebe_op (k_ebe3d.cu; no fused dot)
+void ebe3d_launch(cudaStream_t s, int mode, const Ebe& op, const float* x, float* y,
+                  const float* b, const float* Dinv, double omega, const int* done);
 // point-block diagonal inverse of the level-0 operator, FP64 and FP32 copies
 void ebe_block_diag_inv(cudaStream_t s, const Ebe& op64, double* Dinv64, float* Dinv32);
 // level-0 operator assembled as a structured 3^dim stencil, FP64, SoA layout
@@ -48,6 +51,10 @@ void stencil_op(cudaStream_t s, int mode, const Geo& g, const T* S, const T* x, 
                 const T* Dinv, double omega, const int* done);
 void stencil_block_diag_inv(cudaStream_t s, const Geo& g, const double* S, double* Dinv64,
                             float* Dinv32);
+// FP64 y = S x with per-block partials of x . y (stencil_blocks(g) partials)
+void stencil_apply_dot(cudaStream_t s, const Geo& g, const double* S, const double* x, double* y,
+                       const int* done, double* partials);
+int stencil_blocks(const Geo& g);
 // Galerkin product with bilinear / trilinear P (coarse node I at fine position min(2I, n))
 void stencil_rap(cudaStream_t s, const Geo& fine, const Geo& coarse, const double* Sf, double* Sc);
 template <class T>

@@ -120,7 +120,11 @@ void level_op(tomg_problem* P, cudaStream_t s, int l, int mode, const T* x, T* y
   const double w = P->opt.omega;
   switch (Lv.kind) {
     case KIND_EBE:
-      ebe_op<T>(s, mode, V<T>::ebe(P), x, y, b, V<T>::D(Lv), w, done, nullptr);
+      // FP64: the assembled fine stencil kept by the setup halves the FP64 arithmetic
+      if (sizeof(T) == 8 && Lv.S64.p)
+        stencil_op<T>(s, mode, Lv.g, reinterpret_cast<const T*>(Lv.S64.p), x, y, b, V<T>::D(Lv), w, done);
+      else
+        ebe_op<T>(s, mode, V<T>::ebe(P), x, y, b, V<T>::D(Lv), w, done, nullptr);
       break;
     case KIND_STENCIL:
       stencil_op<T>(s, mode, Lv.g, V<T>::S(Lv), x, y, b, V<T>::D(Lv), w, done);
@@ -198,14 +202,29 @@ void apply_M_and_dots(tomg_problem* P, Work& W, const double* q, const int* done
   }
 }
 
+// FP64 outer operator K (masked): the assembled fine stencil when the setup kept it (36 / 243
+// FMAs per node instead of 72 / 600 for the element products), else the matrix-free kernel
+void fine64_apply_dot(tomg_problem* P, cudaStream_t s, const double* x, double* y, const int* done,
+                      double* partials) {
+  Level& L0 = *P->L[0];
+  if (L0.S64.p) stencil_apply_dot(s, L0.g, L0.S64.p, x, y, done, partials);
+  else ebe_op<double>(s, MODE_APPLY, V<double>::ebe(P), x, y, nullptr, nullptr, 0.0, done, partials);
+}
+int fine64_blocks(tomg_problem* P) {
+  Level& L0 = *P->L[0];
+  return L0.S64.p ? stencil_blocks(L0.g) : ebe_blocks(V<double>::ebe(P));
+}
+void fine64_resid(tomg_problem* P, cudaStream_t s, const double* x, double* y, const double* b) {
+  level_op<double>(P, s, 0, MODE_RESID, x, y, b, nullptr);
+}
+
 void iteration_body(tomg_problem* P, Work& W) {
   const int64_t n = P->n;
   Scalars* sc = W.sc.p;
   const int* done = &sc->done;
   cudaStream_t s = W.stream;
-  const Ebe op = V<double>::ebe(P);
-  ebe_op<double>(s, MODE_APPLY, op, W.p.p, W.q.p, nullptr, nullptr, 0.0, done, W.partA.p);
-  finish(s, FIN_ALPHA, W.partA.p, ebe_blocks(op), nullptr, 0, sc);
+  fine64_apply_dot(P, s, W.p.p, W.q.p, done, W.partA.p);
+  finish(s, FIN_ALPHA, W.partA.p, fine64_blocks(P), nullptr, 0, sc);
   xr_update(s, W.x.p, W.r.p, W.p.p, W.q.p, n, sc, W.partA.p);
   finish(s, FIN_RR, W.partA.p, red_blocks(n), nullptr, 0, sc);
   apply_M_and_dots(P, W, W.q.p, done);
@@ -227,6 +246,11 @@ void build_graph(tomg_problem* P, Work& W) {
   if (mode <= 0) return;
   cudaStream_t s = W.stream;
   const int64_t saved = g_launches;
+  // programmatic dependent launch between the captured kernels (TOMG_NO_PDL=1 turns it off)
+  struct PdlScope {
+    PdlScope() { set_pdl(getenv("TOMG_NO_PDL") == nullptr); }
+    ~PdlScope() { set_pdl(false); }
+  } pdl_scope;
   if (mode >= 2) {
     CK(cudaGraphCreate(&W.graph, 0));
     cudaGraphConditionalHandle h;
@@ -599,8 +623,8 @@ void setup(tomg_problem* P, const tomg_options& opt) {
     if (fail) TOMG_THROW(TOMG_E_BREAKDOWN, "coarse operator not SPD (pivot %d)", fail - 1);
     P->Ainv32.resize(P->Ainv64.n);
     cast_f64_f32(s, P->Ainv64.p, P->Ainv32.p, P->Ainv64.n);
-    // setup-only storage of the fine level
-    L0.S64.release();
+    // setup-only storage of the fine level (its FP64 stencil stays: it carries every FP64
+    // application of K, see fine64_apply_dot)
     L0.rp.release(); L0.ci.release(); L0.V64.release();
     for (auto& lv : P->L)
       if (lv->kind == KIND_STENCIL) { lv->rp.release(); lv->ci.release(); lv->V64.release(); }
@@ -664,8 +688,7 @@ void join_from(tomg_problem* P, Work& W) {
 void init_solve(tomg_problem* P, Work& W, int max_iter) {
   cudaStream_t s = W.stream;
   const int64_t n = P->n;
-  const Ebe op = V<double>::ebe(P);
-  ebe_op<double>(s, MODE_RESID, op, W.x.p, W.r.p, W.bvec.p, nullptr, 0.0, nullptr, nullptr);
+  fine64_resid(P, s, W.x.p, W.r.p, W.bvec.p);
   dot_partials(s, W.r.p, W.r.p, n, W.partA.p, nullptr);
   dot_partials(s, W.bvec.p, W.bvec.p, n, W.partB.p, nullptr);
   Scalars h;
@@ -706,8 +729,7 @@ void launch_attempt(tomg_problem* P, Work& W, int max_iter) {
       if (W.sc_host->done) break;
     }
   }
-  const Ebe op = V<double>::ebe(P);
-  ebe_op<double>(s, MODE_RESID, op, W.x.p, W.t.p, W.bvec.p, nullptr, 0.0, nullptr, nullptr);
+  fine64_resid(P, s, W.x.p, W.t.p, W.bvec.p);
   dot_partials(s, W.t.p, W.t.p, n, W.partE.p, nullptr);
   dot_partials(s, W.f.p, W.x.p, n, W.partC.p, nullptr);
   const int nr = red_blocks(n);
