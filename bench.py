@@ -49,6 +49,14 @@ def parse():
                          "measurement (0: skip)")
     ap.add_argument("--serving-updates", type=int, default=2)
     ap.add_argument("--slots", type=int, default=4)
+    ap.add_argument("--kernel", default=None, choices=["outer", "residual", "jacobi", "apply"],
+                    help="time one level-0 operator kernel alone (for profiler captures) instead "
+                         "of the solve: outer = FP64 q = K p with its dot, the others the "
+                         "V-cycle's kernels in --kernel-prec")
+    ap.add_argument("--kernel-prec", default="fp32")
+    ap.add_argument("--kernel-grid", default="2048x1024",
+                    help="element counts of the cantilever used by --kernel (NXxNY or NXxNYxNZ)")
+    ap.add_argument("--kernel-reps", type=int, default=20)
     ap.add_argument("--no-fp64", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
     return ap.parse_args()
@@ -271,88 +279,157 @@ def serving_run(tomg, ctx, n_requests, n_updates, slots):
             "arrivals": "Poisson, 50 requests/s; each request's updates queued on arrival"}
 
 
+FP64_PEAK_GFLOPS = 1250.0  # GB300 FP64 rate (nominal, not in the measured peaks file)
+
+
 def roofline(P, ctx, p, stream):
-    """Dominant kernel (the level-0 SIMP element operator) timed live with CUDA events on its
-    stream; algorithmic bytes per launch from the minimum traffic model."""
-    try:
-        ms = P.time_fine_operator("apply", "fp32", reps=50, cold_l2=True)
-    except Exception as e:  # noqa: BLE001
-        return {"error": str(e)}
+    """The level-0 kernels of one FCG iteration, each timed live on the context stream with CUDA
+    events (cold L2 before each launch): the FP64 outer q = K p (+ dot) on the assembled fine
+    stencil, and the V-cycle's FP32 residual and Jacobi sweeps on the element operator.  The
+    slowest is the dominant kernel; its roofline is the bound that binds it."""
     peaks = load_peaks()
-    nn = (p.nx + 1) * (p.ny + 1)
-    # read x, write y (2 x 4 B per DOF), read E once per element, mask byte per node
-    bytes_ = 2 * 4 * p.n + 4 * p.nel + nn
-    achieved = bytes_ / (ms * 1e-3) / 1e9
-    peak = peaks.get("hbm_gbs", 6800.0)
-    return {"kernel": "ebe_apply fp32 (2D quad4)", "bound": "hbm", "achieved": achieved,
-            "peak": peak, "unit": "GB/s", "frac": achieved / peak, "traffic": None,
-            "ms_per_launch": ms, "peak_source": "measured" if "fallback" not in peaks else "fallback"}
+    hbm = peaks.get("hbm_gbs", 6800.0)
+    src = "measured" if "fallback" not in peaks else "fallback"
+    nn = p.n // p.dim
+    out = {}
+    for name, prec in (("outer", "fp64"), ("residual", "fp32"), ("jacobi", "fp32")):
+        try:
+            ms = P.time_fine_operator(name, prec, reps=50, cold_l2=True)
+        except Exception as e:  # noqa: BLE001
+            return {"error": str(e)}
+        b = kernel_bytes(name, prec, p)
+        out[name] = {"ms_per_launch": ms, "algorithmic_bytes": b,
+                     "achieved_gbs": b / (ms * 1e-3) / 1e9, "frac_hbm": b / (ms * 1e-3) / 1e9 / hbm}
+    o = out["outer"]
+    # assembled 3^d stencil: d^2 FMAs per neighbour block, 3^d blocks per node, + the dot
+    flops = 2 * nn * (3 ** p.dim) * p.dim * p.dim + 2 * p.n
+    o["algorithmic_flops"] = flops
+    o["achieved_gflops"] = flops / (o["ms_per_launch"] * 1e-3) / 1e9
+    dom = max(out, key=lambda k: out[k]["ms_per_launch"])
+    if dom == "outer":
+        head = {"kernel": "k_stencil_apply_dot<%d> (FP64 outer q = K p + p.q)" % p.dim,
+                "bound": "alu", "achieved": o["achieved_gflops"] / 1e3,
+                "peak": FP64_PEAK_GFLOPS / 1e3, "unit": "TFLOP/s",
+                "frac": o["achieved_gflops"] / FP64_PEAK_GFLOPS,
+                "peak_source": "nominal FP64 rate (no measured FP64 peak)"}
+    else:
+        k = out[dom]
+        head = {"kernel": "k_ebe2<float, %s> (FP32 %s, 2D)" % ("1" if dom == "residual" else "2", dom),
+                "bound": "hbm", "achieved": k["achieved_gbs"], "peak": hbm, "unit": "GB/s",
+                "frac": k["frac_hbm"], "peak_source": src}
+    head.update({"traffic": None, "ms_per_launch": out[dom]["ms_per_launch"], "kernels": out})
+    return head
 
 
-def cpu_baseline(n_threads_hint=None):
-    """Oracle (FP64 numpy/scipy) on the host cores: setup + a bounded number of PCG iterations
-    on the same workload, scaled to solves/s with the iteration count the oracle needs."""
+def kernel_only(args):
+    """One level-0 operator kernel timed alone (cold L2 before each launch, CUDA events on the
+    context stream), with its algorithmic bytes per launch."""
+    import torch
+    import workloads as W
+    from paper_2001_01655_gb300 import tomg
+
+    dims = [int(v) for v in args.kernel_grid.lower().split("x")]
+    p = W.cantilever_2d(nx=dims[0], ny=dims[1], seed=0) if len(dims) == 2 else \
+        W.cantilever_3d(nx=dims[0], ny=dims[1], nz=dims[2], seed=0)
+    ctx = tomg.Context(0)
+    P = tomg.Problem.from_workload(ctx, p)
+    prec = "fp64" if args.kernel == "outer" else args.kernel_prec
+    P.setup(pc="gmg", prec=prec, max_coarse_dofs=8000)
+    ms = P.time_fine_operator(args.kernel, prec, reps=args.kernel_reps, cold_l2=True)
+    nbytes = kernel_bytes(args.kernel, prec, p)
+    peaks = load_peaks()
+    torch.cuda.synchronize()
+    return {"kernel": args.kernel, "prec": prec, "grid": dims, "dofs": p.n, "ms_per_launch": ms,
+            "algorithmic_bytes": nbytes, "achieved_gbs": nbytes / (ms * 1e-3) / 1e9,
+            "frac_of_measured_hbm": nbytes / (ms * 1e-3) / 1e9 / peaks.get("hbm_gbs", 6800.0)}
+
+
+def kernel_bytes(kernel, prec, p):
+    """Algorithmic bytes of one level-0 operator launch: the vectors it must read and write,
+    one modulus per element and one mask byte per node (the minimum-traffic model)."""
+    s = 8 if prec == "fp64" else 4
+    nn = p.n // p.dim
+    vec = {"outer": 2, "apply": 2, "residual": 3, "jacobi": 3}[kernel]
+    extra = p.dim * s * nn if kernel == "jacobi" else 0  # block-diagonal inverse, dim^2 per node
+    return vec * s * p.n + s * p.nel + nn + extra
+
+
+def cpu_baseline(iters=40, warmup=0, steps=1):
+    """The oracle (plain FP64 numpy / scipy) on the host cores, on a bounded sample of the same
+    workload: its hierarchy setup once, then `steps` samples of `iters` PCG iterations.  A solve
+    is setup + ORACLE_ITERATIONS iterations at the median per-iteration time.  `cores` is the
+    CPU time over the wall time of the sample (the threads BLAS and scipy actually kept busy)."""
     import workloads as W
     from oracle import solve as osolve, mg, krylov, fem
 
     p = W.cantilever_2d(**WORKLOAD)
-    t0 = time.perf_counter()
+    c0, t0 = _cpu_seconds(), time.perf_counter()
     H = osolve.build(p, pc=HEADLINE["pc"], cap=HEADLINE["max_coarse_dofs"],
                      n_geo=HEADLINE["n_geo_levels"])
     t_setup = time.perf_counter() - t0
     A0 = mg.fine_operator(p)
     b = fem.free_mask(p.n, p.fixed) * p.f[0]
-    k = 10
-    t1 = time.perf_counter()
-    krylov.pcg(A0, b, M=lambda v: mg.vcycle(H, v), rtol=0.0, max_iter=k)
-    t_it = (time.perf_counter() - t1) / k
-    return p, H, t_setup, t_it
+    M = lambda v: mg.vcycle(H, v)  # noqa: E731
+    for _ in range(warmup):
+        krylov.pcg(A0, b, M=M, rtol=0.0, max_iter=1)
+    per_it = []
+    for _ in range(steps):
+        t1 = time.perf_counter()
+        krylov.pcg(A0, b, M=M, rtol=0.0, max_iter=iters)
+        per_it.append((time.perf_counter() - t1) / iters)
+    wall = time.perf_counter() - t0
+    cores = (_cpu_seconds() - c0) / wall
+    t_it = statistics.median(per_it)
+    step_s = t_setup + ORACLE_ITERATIONS * t_it
+    return {"value": 1.0 / step_s, "unit": "solves/s", "cores": round(cores, 1),
+            "host_cores": os.cpu_count(), "kind": "oracle",
+            "sample": "oracle hierarchy setup (%.2f s) + %d x %d FP64 PCG iterations (%.1f ms each, "
+                      "median) on the full 768x384 workload, scaled to the oracle's %d iterations "
+                      "to 1e-8" % (t_setup, steps, iters, 1e3 * t_it, ORACLE_ITERATIONS),
+            "ms_per_step": step_s * 1e3, "sample_wall_s": wall}
 
 
 def run_reference(args, rank, world):
+    """The oracle as the reference arm: rank 0 only, each step a bounded sample (5 PCG
+    iterations) of the same workload, W warm-up iterations first."""
     if rank != 0:
         return None
-    p, H, t_setup, t_it = cpu_baseline()
-    its_needed = None
-    try:
-        from oracle import krylov, mg, fem
-        its_needed = int(os.environ.get("TOMG_REF_ITERS", "0")) or None
-    except Exception:
-        pass
-    its = its_needed or 210
-    step_s = t_setup + its * t_it
-    ncores = os.cpu_count()
-    value = 1.0 / step_s
+    cb = cpu_baseline(iters=5, warmup=args.warmup, steps=args.steps)
+    value = cb["value"]
     return {"metric": METRIC, "value": value, "unit": "solves/s", "n_gpus": world,
-            "steps": args.steps, "warmup": args.warmup, "ms_per_step": step_s * 1e3,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": cb["ms_per_step"],
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
             "data": "synthetic", "impl": "reference",
-            "config": {"workload": "2D cantilever quad4 %dx%d (592,130 DOFs)" % (WORKLOAD["nx"], WORKLOAD["ny"]),
-                       "preconditioner": HEADLINE["pc"]},
-            "cpu_baseline": {"value": value, "unit": "solves/s", "cores": ncores, "kind": "oracle",
-                             "sample": "oracle setup + 10 PCG iterations timed, scaled to %d iterations" % its},
+            "config": {"workload": "2D cantilever quad4 %dx%d (592,130 DOFs), seeded thin 0/1 members "
+                       "(1e9 contrast), left edge clamped, unit load right mid-edge"
+                       % (WORKLOAD["nx"], WORKLOAD["ny"]),
+                       "preconditioner": HEADLINE["pc"], "max_coarse_dofs": HEADLINE["max_coarse_dofs"],
+                       "rtol": 1e-8},
+            "cpu_baseline": {k: cb[k] for k in ("value", "unit", "cores", "host_cores", "kind", "sample")},
             "e2e": {"value": value, "unit": "solves/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
 
 
 def main():
     args = parse()
     rank, world, local = dist_env()
+    if args.kernel:
+        print(json.dumps(kernel_only(args)))
+        return
+    if args.impl == "reference":
+        out = run_reference(args, rank, world)  # host only; ranks other than 0 do nothing
+        if out is not None:
+            print(json.dumps(out))
+        return
     if world > 1:
         import torch
         import torch.distributed as dist
-        dist.init_process_group("nccl" if args.impl != "reference" else "gloo")
-    if args.impl == "reference":
-        out = run_reference(args, rank, world)
-    else:
-        out = run_gpu(args, rank, world, local)
-        if rank == 0 and not args.no_cpu:
-            p, H, t_setup, t_it = cpu_baseline()
-            its = out["iterations"]
-            step_s = t_setup + its * t_it
-            out["cpu_baseline"] = {"value": 1.0 / step_s, "unit": "solves/s", "cores": os.cpu_count(),
-                                   "kind": "oracle",
-                                   "sample": "oracle hierarchy setup + 10 FP64 PCG iterations on the full "
-                                             "workload, scaled to the GPU's %d iterations" % its}
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl")
+    out = run_gpu(args, rank, world, local)
+    if rank == 0 and world == 1 and not args.no_cpu:
+        cb = cpu_baseline()
+        out["cpu_baseline"] = {k: cb[k] for k in ("value", "unit", "cores", "host_cores", "kind",
+                                                  "sample")}
     if rank == 0 and out is not None:
         print(json.dumps(out))
     if world > 1:

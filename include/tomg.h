@@ -182,6 +182,11 @@ tomg_status tomg_aggregates_export(tomg_problem* prob, int level, int64_t* agg);
 /* y = A_level x in the given tomg_prec (FP32 math for FP32_VCYCLE), double in/out. */
 tomg_status tomg_level_apply(tomg_problem* prob, int level, int prec, const double* x, double* y,
                              int on_device);
+/* y = K x on the fine grid in FP64, exactly as the outer Krylov loop applies it (Sec. 3.1;
+ * K = M K(rho) M + (I - M) with the SIMP moduli of Eq. 2): the assembled FP64 fine stencil of
+ * the current setup.  x, y: n doubles, host or device (on_device), DOF-interleaved.  Needs a
+ * setup; E_INVALID otherwise. */
+tomg_status tomg_outer_apply(tomg_problem* prob, const double* x, double* y, int on_device);
 /* z = M r: one V-cycle of the current setup (its precision), double in/out. */
 tomg_status tomg_vcycle(tomg_problem* prob, const double* r, double* z, int on_device);
 /* Coarsest-level direct solve x = A_c^{-1} b (FP64), host or device arrays. */
@@ -191,7 +196,9 @@ tomg_status tomg_moduli(tomg_problem* prob, double* E, int on_device);
 /* Element stiffness matrix of the problem for E = 1 (dim*2^dim squared, row-major). */
 tomg_status tomg_element_stiffness(const tomg_problem* prob, double* Ke);
 /* Timing of the level-0 SIMP element operator kernel (Sec. 2.1 Eq. 2 inside the K apply):
- * op 0 = y = A x, 1 = residual b - A x, 2 = one weighted block-Jacobi sweep; prec a tomg_prec.
+ * op 0 = y = A x, 1 = residual b - A x, 2 = one weighted block-Jacobi sweep, in the V-cycle's
+ * kernels of precision prec (a tomg_prec); op 3 = the outer FP64 q = K p with the per-block
+ * partials of p . q, exactly as the Krylov loop launches it (prec ignored).
  * Launches it `reps` times on the context stream, each launch bracketed by CUDA events; with
  * cold_l2 != 0 a 256 MB buffer is written before every launch (outside the events) so the
  * kernel reads its inputs from HBM.  Writes the mean device time per launch (ms).  Needs a

@@ -55,13 +55,18 @@ tomg_status guarded(F&& fn) {
 }
 
 // device view of a caller array: the pointer itself (device) or a staged copy (host)
+// Caller arrays as kernel operands.  Device arrays are used in place when 16-byte aligned (the
+// kernels load DOF pairs as 16-byte vectors); host arrays and unaligned device arrays go
+// through a library buffer.
+inline bool aligned16(const void* p) { return ((uintptr_t)p & 15u) == 0; }
 struct DevArray {
   DBuf<double> buf;
   const double* p = nullptr;
   DevArray(const double* src, int64_t n, int on_device, cudaStream_t s) {
-    if (on_device) { p = src; return; }
+    if (on_device && aligned16(src)) { p = src; return; }
     buf.resize(n > 0 ? n : 1);
-    if (n) CK(cudaMemcpyAsync(buf.p, src, n * 8, cudaMemcpyHostToDevice, s));
+    if (n)
+      CK(cudaMemcpyAsync(buf.p, src, n * 8, on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, s));
     p = buf.p;
   }
 };
@@ -71,14 +76,16 @@ struct DevOut {
   double* dst;
   int64_t n;
   int on_device;
+  bool direct = false;
   cudaStream_t s;
   DevOut(double* d, int64_t count, int on_dev, cudaStream_t st) : dst(d), n(count), on_device(on_dev), s(st) {
-    if (on_device) { p = d; return; }
+    if (on_device && aligned16(d)) { p = d; direct = true; return; }
     buf.resize(n > 0 ? n : 1);
     p = buf.p;
   }
   void commit() {
-    if (!on_device && n) CK(cudaMemcpyAsync(dst, p, n * 8, cudaMemcpyDeviceToHost, s));
+    if (!direct && n)
+      CK(cudaMemcpyAsync(dst, p, n * 8, on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost, s));
     CK(cudaStreamSynchronize(s));
   }
 };
@@ -327,6 +334,20 @@ tomg_status tomg_level_apply(tomg_problem* P, int level, int prec, const double*
     DevArray xin(x, n, on_device, P->stream);
     DevOut yout(y, n, on_device, P->stream);
     level_apply(P, level, prec, xin.p, yout.p);
+    yout.commit();
+    return TOMG_OK;
+  });
+}
+
+tomg_status tomg_outer_apply(tomg_problem* P, const double* x, double* y, int on_device) {
+  return guarded([&]() -> tomg_status {
+    if (!P || !x || !y) TOMG_THROW(TOMG_E_INVALID, "null argument");
+    if (!P->setup_valid) TOMG_THROW(TOMG_E_INVALID, "no valid setup");
+    set_device(P);
+    StreamScope sc(P);
+    DevArray xin(x, P->n, on_device, P->stream);
+    DevOut yout(y, P->n, on_device, P->stream);
+    outer_operator_apply(P, xin.p, yout.p);
     yout.commit();
     return TOMG_OK;
   });

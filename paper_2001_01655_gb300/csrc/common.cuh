@@ -144,6 +144,23 @@ __device__ __forceinline__ double block_sum(double v, double* sh) {
 // early-exit flag shared by the solve loop: kernels become no-ops once the solve is done
 __device__ __forceinline__ bool solve_done(const int* done) { return done && *(volatile const int*)done; }
 
+// First point-block Jacobi sweep from x = 0 at one node: x = w Dinv_node b_node (B x B blocks)
+template <class T, int B>
+__device__ __forceinline__ void jacobi_first(const T* __restrict__ Dinv, const T* __restrict__ b,
+                                             int64_t node, T omega, T* xv) {
+  const T* D = Dinv + (int64_t)B * B * node;
+  T bv[B];
+#pragma unroll
+  for (int c = 0; c < B; c++) bv[c] = b[(int64_t)B * node + c];
+#pragma unroll
+  for (int r = 0; r < B; r++) {
+    T v = T(0);
+#pragma unroll
+    for (int c = 0; c < B; c++) v += D[r * B + c] * bv[c];
+    xv[r] = omega * v;
+  }
+}
+
 }  // namespace tomg
 
 namespace tomg {

@@ -28,7 +28,7 @@ __global__ void __launch_bounds__(256) k_bsr(int nbr, const int* __restrict__ rp
                                              const int* __restrict__ ci, const T* __restrict__ V,
                                              const T* __restrict__ x, T* __restrict__ y,
                                              const T* __restrict__ b, const T* __restrict__ Dinv,
-                                             T omega, const int* done) {
+                                             T omega, const int* done, T* __restrict__ xo) {
   pdl_prologue();
   if (solve_done(done)) return;
   const int gtid = blockIdx.x * blockDim.x + threadIdx.x;
@@ -42,8 +42,12 @@ __global__ void __launch_bounds__(256) k_bsr(int nbr, const int* __restrict__ rp
       const int j = ci[p];
       const T* blk = V + (int64_t)p * B * B;
       T xv[B];
+      if (MODE == MODE_RESID0) {
+        jacobi_first<T, B>(Dinv, b, j, omega, xv);
+      } else {
 #pragma unroll
-      for (int c = 0; c < B; c++) xv[c] = x[(int64_t)B * j + c];
+        for (int c = 0; c < B; c++) xv[c] = x[(int64_t)B * j + c];
+      }
 #pragma unroll
       for (int r = 0; r < B; r++)
 #pragma unroll
@@ -52,7 +56,15 @@ __global__ void __launch_bounds__(256) k_bsr(int nbr, const int* __restrict__ rp
   }
   group_reduce<G, T, B>(acc);
   if (!live || sub != 0) return;
-  if (MODE == MODE_APPLY) {
+  if (MODE == MODE_RESID0) {
+    T xi[B];
+    jacobi_first<T, B>(Dinv, b, i, omega, xi);
+#pragma unroll
+    for (int r = 0; r < B; r++) {
+      xo[(int64_t)B * i + r] = xi[r];
+      y[(int64_t)B * i + r] = b[(int64_t)B * i + r] - acc[r];
+    }
+  } else if (MODE == MODE_APPLY) {
 #pragma unroll
     for (int r = 0; r < B; r++) y[(int64_t)B * i + r] = acc[r];
   } else if (MODE == MODE_RESID) {
@@ -366,7 +378,8 @@ void bsr_op(cudaStream_t s, int mode, const Bsr& A, const T* V, const T* x, T* y
             const T* Dinv, double omega, const int* done) {
   const int G = lanes_for(A);
   const int grid = ceil_div((int64_t)A.nbr * G, 256);
-#define BOP(B, M, GG) LAUNCH((k_bsr<T, B, M, GG>), grid, 256, 0, s, A.nbr, A.rp, A.ci, V, x, y, b, Dinv, (T)omega, done)
+  T* xo = mode == MODE_RESID0 ? const_cast<T*>(x) : nullptr;
+#define BOP(B, M, GG) LAUNCH((k_bsr<T, B, M, GG>), grid, 256, 0, s, A.nbr, A.rp, A.ci, V, x, y, b, Dinv, (T)omega, done, xo)
 #define BG(B, M)                         \
   if (G == 4) BOP(B, M, 4);              \
   else if (G == 8) BOP(B, M, 8);         \
@@ -375,6 +388,7 @@ void bsr_op(cudaStream_t s, int mode, const Bsr& A, const T* V, const T* x, T* y
 #define BMODES(B)                                   \
   if (mode == MODE_APPLY) { BG(B, MODE_APPLY) }     \
   else if (mode == MODE_RESID) { BG(B, MODE_RESID) } \
+  else if (mode == MODE_RESID0) { BG(B, MODE_RESID0) } \
   else { BG(B, MODE_JACOBI) }
   if (A.br == 2) { BMODES(2) }
   else if (A.br == 3) { BMODES(3) }

@@ -229,6 +229,8 @@ void ebe_op(cudaStream_t s, int mode, const Ebe& op, const T* x, T* y, const T* 
       else launch_ebe<T, 2, MODE_APPLY, false>(s, op, x, y, b, Dinv, omega, done, parts);
     } else if (mode == MODE_RESID) {
       launch_ebe<T, 2, MODE_RESID, false>(s, op, x, y, b, Dinv, omega, done, parts);
+    } else if (mode == MODE_RESID0) {
+      ebe2d_launch<T, MODE_RESID0, false>(s, op, x, y, b, Dinv, omega, done, parts);
     } else {
       launch_ebe<T, 2, MODE_JACOBI, false>(s, op, x, y, b, Dinv, omega, done, parts);
     }
@@ -237,6 +239,10 @@ void ebe_op(cudaStream_t s, int mode, const Ebe& op, const T* x, T* y, const T* 
       if (parts) launch_ebe<T, 3, MODE_APPLY, true>(s, op, x, y, b, Dinv, omega, done, parts);
       else launch_ebe<T, 3, MODE_APPLY, false>(s, op, x, y, b, Dinv, omega, done, parts);
     } else if (mode == MODE_RESID) {
+      launch_ebe<T, 3, MODE_RESID, false>(s, op, x, y, b, Dinv, omega, done, parts);
+    } else if (mode == MODE_RESID0) {
+      // hex8: the first sweep as its own pass, then the residual
+      jacobi0<T>(s, 3, nodes_of(op), Dinv, b, const_cast<T*>(x), omega, done);
       launch_ebe<T, 3, MODE_RESID, false>(s, op, x, y, b, Dinv, omega, done, parts);
     } else {
       launch_ebe<T, 3, MODE_JACOBI, false>(s, op, x, y, b, Dinv, omega, done, parts);

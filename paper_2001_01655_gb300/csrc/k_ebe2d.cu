@@ -7,27 +7,35 @@
 // thread then keeps a 6 x 3 node window and a 5 x 2 element window in registers, loads each of
 // the four element-role row pairs of Ke once, and applies it to its four nodes:
 // 64 FMAs per node, every input element read once from DRAM.
+#include <map>
+#include <mutex>
+#include <utility>
+
 #include "ops.h"
 
 namespace tomg {
 
 namespace {
 
-constexpr int BX = 32, BY = 8, NPT = 4, TH = BY * NPT;
+constexpr int BX = 32, BY = 8;
 
 template <class T> struct V2t;
 template <> struct V2t<float> { using type = float2; };
 template <> struct V2t<double> { using type = double2; };
 
-template <class T, int MODE, bool DOT>
+// NPT nodes per thread along y (tile 32 x 8 NPT): more nodes per thread reuse more of the
+// staged halo, fewer give more blocks per SM; the setup's autotuner picks per grid
+template <class T, int MODE, bool DOT, int NPT>
 __global__ void __launch_bounds__(BX * BY) k_ebe2(int nx, int ny, const T* __restrict__ Ke,
                                                   const T* __restrict__ E,
                                                   const uint8_t* __restrict__ mask,
                                                   const T* __restrict__ x, T* __restrict__ y,
                                                   const T* __restrict__ b,
                                                   const T* __restrict__ Dinv, T omega,
-                                                  const int* done, double* partials) {
+                                                  const int* done, double* partials,
+                                                  T* __restrict__ xo) {
   using V2 = typename V2t<T>::type;
+  constexpr int TH = BY * NPT;
   __shared__ __align__(16) T sKe[64];
   __shared__ V2 sx[TH + 2][BX + 2];
   __shared__ T sE[TH + 1][BX + 1];
@@ -56,7 +64,16 @@ __global__ void __launch_bounds__(BX * BY) k_ebe2(int nx, int ny, const T* __res
     if (t < (TH + 2) * (BX + 2) && gi >= 0 && gi <= nx && gj >= 0 && gj <= ny) {
       const int node = gj * W + gi;
       mv[k] = __ldg(mask + node);
-      xv[k] = __ldg(reinterpret_cast<const V2*>(x) + node);
+      if (MODE == MODE_RESID0) {
+        // x = w Dinv b of the first sweep, formed where it is needed
+        const V2 bv = __ldg(reinterpret_cast<const V2*>(b) + node);
+        const V2 d01 = __ldg(reinterpret_cast<const V2*>(Dinv) + 2 * node);
+        const V2 d23 = __ldg(reinterpret_cast<const V2*>(Dinv) + 2 * node + 1);
+        xv[k].x = omega * (d01.x * bv.x + d01.y * bv.y);
+        xv[k].y = omega * (d23.x * bv.x + d23.y * bv.y);
+      } else {
+        xv[k] = __ldg(reinterpret_cast<const V2*>(x) + node);
+      }
     }
   }
 #pragma unroll
@@ -133,7 +150,17 @@ __global__ void __launch_bounds__(BX * BY) k_ebe2(int nx, int ny, const T* __res
     if (i > nx || j > ny) continue;
     const int node = j * W + i;
     const unsigned m = mask[node];
-    const V2 xi = reinterpret_cast<const V2*>(x)[node];
+    V2 xi;
+    if (MODE == MODE_RESID0) {
+      const V2 bv = reinterpret_cast<const V2*>(b)[node];
+      const V2 d01 = reinterpret_cast<const V2*>(Dinv)[2 * node];
+      const V2 d23 = reinterpret_cast<const V2*>(Dinv)[2 * node + 1];
+      xi.x = omega * (d01.x * bv.x + d01.y * bv.y);
+      xi.y = omega * (d23.x * bv.x + d23.y * bv.y);
+      reinterpret_cast<V2*>(xo)[node] = xi;
+    } else {
+      xi = reinterpret_cast<const V2*>(x)[node];
+    }
     const T Ax0 = (m & 1u) ? xi.x : a0[q], Ax1 = (m & 2u) ? xi.y : a1[q];
     V2 out;
     if (MODE == MODE_APPLY) {
@@ -143,7 +170,7 @@ __global__ void __launch_bounds__(BX * BY) k_ebe2(int nx, int ny, const T* __res
     } else {
       const V2 bv = reinterpret_cast<const V2*>(b)[node];
       const T r0v = bv.x - Ax0, r1v = bv.y - Ax1;
-      if (MODE == MODE_RESID) {
+      if (MODE == MODE_RESID || MODE == MODE_RESID0) {
         out.x = r0v;
         out.y = r1v;
       } else {
@@ -170,22 +197,77 @@ __global__ void __launch_bounds__(BX * BY) k_ebe2(int nx, int ny, const T* __res
 
 }  // namespace
 
-int ebe2d_blocks(const Ebe& op) { return ceil_div(op.nx + 1, BX) * ceil_div(op.ny + 1, TH); }
+int ebe2d_blocks(const Ebe& op) {
+  const int npt = op.tile == 1 || op.tile == 2 ? op.tile : 4;
+  return ceil_div(op.nx + 1, BX) * ceil_div(op.ny + 1, BY * npt);
+}
 
 template <class T, int MODE, bool DOT>
 void ebe2d_launch(cudaStream_t s, const Ebe& op, const T* x, T* y, const T* b, const T* Dinv,
                   double omega, const int* done, double* parts) {
-  dim3 grid(ceil_div(op.nx + 1, BX), ceil_div(op.ny + 1, TH));
-  LAUNCH((k_ebe2<T, MODE, DOT>), grid, dim3(BX, BY), 0, s, op.nx, op.ny, (const T*)op.Ke,
-         (const T*)op.E, op.mask, x, y, b, Dinv, (T)omega, done, parts);
+  T* xo = MODE == MODE_RESID0 ? const_cast<T*>(x) : nullptr;
+  const int npt = DOT ? 4 : (op.tile == 1 || op.tile == 2 ? op.tile : 4);  // dots: fixed tile
+  dim3 grid(ceil_div(op.nx + 1, BX), ceil_div(op.ny + 1, BY * npt));
+#define EB(N) LAUNCH((k_ebe2<T, MODE, DOT, N>), grid, dim3(BX, BY), 0, s, op.nx, op.ny,   \
+                     (const T*)op.Ke, (const T*)op.E, op.mask, x, y, b, Dinv, (T)omega, done, \
+                     parts, xo)
+  if (npt == 1) EB(1);
+  else if (npt == 2) EB(2);
+  else EB(4);
+#undef EB
+}
+
+int ebe2d_autotune(cudaStream_t s, const Ebe& op, const float* Dinv) {
+  static std::mutex mu;
+  static std::map<std::pair<int, int>, int> cache;
+  const std::pair<int, int> key(op.nx, op.ny);
+  {
+    std::lock_guard<std::mutex> g(mu);
+    auto it = cache.find(key);
+    if (it != cache.end()) return it->second;
+  }
+  const int64_t n = 2 * (int64_t)(op.nx + 1) * (op.ny + 1);
+  DBuf<float> x, y, b;
+  x.resize(n);
+  y.resize(n);
+  b.resize(n);
+  x.zero(s);
+  b.zero(s);
+  cudaEvent_t e0, e1;
+  CK(cudaEventCreate(&e0));
+  CK(cudaEventCreate(&e1));
+  int best = 4;
+  float best_ms = 1e30f;
+  for (int npt : {4, 2, 1}) {
+    Ebe o = op;
+    o.tile = npt;
+    ebe2d_launch<float, MODE_RESID, false>(s, o, x.p, y.p, b.p, Dinv, 0.5, nullptr, nullptr);
+    CK(cudaEventRecord(e0, s));
+    for (int r = 0; r < 5; r++)
+      ebe2d_launch<float, MODE_RESID, false>(s, o, x.p, y.p, b.p, Dinv, 0.5, nullptr, nullptr);
+    CK(cudaEventRecord(e1, s));
+    CK(cudaEventSynchronize(e1));
+    float ms = 0.f;
+    CK(cudaEventElapsedTime(&ms, e0, e1));
+    if (ms < 0.97f * best_ms) {  // a smaller tile must win clearly
+      best_ms = ms;
+      best = npt;
+    }
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  std::lock_guard<std::mutex> g(mu);
+  cache[key] = best;
+  return best;
 }
 
 #define INST(T, M, D)                                                                      \
   template void ebe2d_launch<T, M, D>(cudaStream_t, const Ebe&, const T*, T*, const T*,     \
                                       const T*, double, const int*, double*);
 INST(float, MODE_APPLY, true) INST(float, MODE_APPLY, false) INST(float, MODE_RESID, false)
-INST(float, MODE_JACOBI, false) INST(double, MODE_APPLY, true) INST(double, MODE_APPLY, false)
-INST(double, MODE_RESID, false) INST(double, MODE_JACOBI, false)
+INST(float, MODE_JACOBI, false) INST(float, MODE_RESID0, false) INST(double, MODE_APPLY, true)
+INST(double, MODE_APPLY, false) INST(double, MODE_RESID, false) INST(double, MODE_JACOBI, false)
+INST(double, MODE_RESID0, false)
 #undef INST
 
 }  // namespace tomg

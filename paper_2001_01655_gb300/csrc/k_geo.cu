@@ -6,7 +6,7 @@
 // 1D weights are 1 at a coincident node and 1/2 at a fine node midway between two coarse
 // nodes.  Stencil layout (SoA, coalesced over nodes):
 //   S[((o * b + r) * b + c) * n_nodes + node],  o = (ox+1) + 3 (oy+1) + 9 (oz+1).
-#include "ops.h"
+#include "finish.cuh"
 
 namespace tomg {
 
@@ -31,7 +31,7 @@ __global__ void __launch_bounds__(256) k_stencil(int nx, int ny, int nz, const T
                                                  const T* __restrict__ x, T* __restrict__ y,
                                                  const T* __restrict__ b,
                                                  const T* __restrict__ Dinv, T omega,
-                                                 const int* done) {
+                                                 const int* done, T* __restrict__ xo) {
   constexpr int NO = (DIM == 3) ? 27 : 9, BB = DIM * DIM;
   pdl_prologue();
   if (solve_done(done)) return;
@@ -49,14 +49,26 @@ __global__ void __launch_bounds__(256) k_stencil(int nx, int ny, int nz, const T
     if (!in_grid<DIM>(i + ox, j + oy, k + oz, nx, ny, nz)) continue;
     const int64_t nb = node_id(i + ox, j + oy, k + oz, nx, ny);
     T xv[DIM];
+    if (MODE == MODE_RESID0) {
+      jacobi_first<T, DIM>(Dinv, b, nb, omega, xv);
+    } else {
 #pragma unroll
-    for (int c = 0; c < DIM; c++) xv[c] = x[DIM * nb + c];
+      for (int c = 0; c < DIM; c++) xv[c] = x[DIM * nb + c];
+    }
 #pragma unroll
     for (int r = 0; r < DIM; r++)
 #pragma unroll
       for (int c = 0; c < DIM; c++) acc[r] += S[((int64_t)o * BB + r * DIM + c) * nn + node] * xv[c];
   }
-  if (MODE == MODE_APPLY) {
+  if (MODE == MODE_RESID0) {
+    T xi[DIM];
+    jacobi_first<T, DIM>(Dinv, b, node, omega, xi);
+#pragma unroll
+    for (int c = 0; c < DIM; c++) {
+      xo[DIM * node + c] = xi[c];
+      y[DIM * node + c] = b[DIM * node + c] - acc[c];
+    }
+  } else if (MODE == MODE_APPLY) {
 #pragma unroll
     for (int c = 0; c < DIM; c++) y[DIM * node + c] = acc[c];
   } else if (MODE == MODE_RESID) {
@@ -84,7 +96,8 @@ __global__ void __launch_bounds__(256) k_stencil_apply_dot(int nx, int ny, int n
                                                            const double* __restrict__ S,
                                                            const double* __restrict__ x,
                                                            double* __restrict__ y,
-                                                           const int* done, double* partials) {
+                                                           const int* done, double* partials,
+                                                           Scalars* sc) {
   constexpr int NO = (DIM == 3) ? 27 : 9, BB = DIM * DIM;
   __shared__ double sred[32];
   pdl_prologue();
@@ -117,8 +130,10 @@ __global__ void __launch_bounds__(256) k_stencil_apply_dot(int nx, int ny, int n
       dotv += x[DIM * node + c] * acc[c];
     }
   }
+  if (!partials) return;  // plain y = S x (uniform over the grid)
   const double tot = block_sum(dotv, sred);
   if (threadIdx.x == 0) partials[blockIdx.x] = tot;
+  if (sc && last_block(&sc->tk[TK_ALPHA])) finish_body(FIN_ALPHA, partials, gridDim.x, nullptr, 0, sc, sred);
 }
 
 template <int DIM>
@@ -365,14 +380,17 @@ void stencil_op(cudaStream_t s, int mode, const Geo& g, const T* S, const T* x, 
                 const T* Dinv, double omega, const int* done) {
   const int64_t nn = g.nodes();
   const int grid = ceil_div(nn, 256);
-#define STN(D, M) LAUNCH((k_stencil<T, D, M>), grid, 256, 0, s, g.nx, g.ny, g.nz, S, x, y, b, Dinv, (T)omega, done)
+  T* xo = mode == MODE_RESID0 ? const_cast<T*>(x) : nullptr;
+#define STN(D, M) LAUNCH((k_stencil<T, D, M>), grid, 256, 0, s, g.nx, g.ny, g.nz, S, x, y, b, Dinv, (T)omega, done, xo)
   if (g.dim == 2) {
     if (mode == MODE_APPLY) STN(2, MODE_APPLY);
     else if (mode == MODE_RESID) STN(2, MODE_RESID);
+    else if (mode == MODE_RESID0) STN(2, MODE_RESID0);
     else STN(2, MODE_JACOBI);
   } else {
     if (mode == MODE_APPLY) STN(3, MODE_APPLY);
     else if (mode == MODE_RESID) STN(3, MODE_RESID);
+    else if (mode == MODE_RESID0) STN(3, MODE_RESID0);
     else STN(3, MODE_JACOBI);
   }
 #undef STN
@@ -385,12 +403,12 @@ template void stencil_op<double>(cudaStream_t, int, const Geo&, const double*, c
 int stencil_blocks(const Geo& g) { return ceil_div(g.nodes(), 256); }
 
 void stencil_apply_dot(cudaStream_t s, const Geo& g, const double* S, const double* x, double* y,
-                       const int* done, double* partials) {
+                       const int* done, double* partials, Scalars* sc) {
   const int grid = stencil_blocks(g);
   if (g.dim == 2)
-    LAUNCH(k_stencil_apply_dot<2>, grid, 256, 0, s, g.nx, g.ny, g.nz, S, x, y, done, partials);
+    LAUNCH(k_stencil_apply_dot<2>, grid, 256, 0, s, g.nx, g.ny, g.nz, S, x, y, done, partials, sc);
   else
-    LAUNCH(k_stencil_apply_dot<3>, grid, 256, 0, s, g.nx, g.ny, g.nz, S, x, y, done, partials);
+    LAUNCH(k_stencil_apply_dot<3>, grid, 256, 0, s, g.nx, g.ny, g.nz, S, x, y, done, partials, sc);
 }
 
 void stencil_block_diag_inv(cudaStream_t s, const Geo& g, const double* S, double* Dinv64,

@@ -7,7 +7,7 @@
 // (fixed tree inside the block); a single-block "finish" kernel adds the partials in a fixed
 // order and updates the device-resident scalar state, so no host round trip is needed per
 // iteration and results do not depend on scheduling.
-#include "ops.h"
+#include "finish.cuh"
 
 namespace tomg {
 
@@ -35,57 +35,14 @@ __global__ void __launch_bounds__(256) k_finish(int kind, const double* __restri
   __shared__ double sred[32];
   pdl_prologue();
   if (kind != FIN_INIT && sc->done) return;
-  double a = 0.0, b = 0.0;
-  for (int i = threadIdx.x; i < na; i += blockDim.x) a += pa[i];
-  for (int i = threadIdx.x; i < nb; i += blockDim.x) b += pb[i];
-  a = block_sum(a, sred);
-  b = block_sum(b, sred);
-  if (threadIdx.x != 0) return;
-  switch (kind) {
-    case FIN_INIT:  // a = r.r, b = b.b
-      sc->rr = a;
-      sc->bb = b;
-      sc->tol2 = sc->rtol2 * b;
-      sc->it = 0;
-      sc->status = TOMG_OK;
-      sc->done = (b == 0.0 || a <= sc->tol2) ? 1 : 0;
-      if (a != a) { sc->status = TOMG_E_BREAKDOWN; sc->done = 1; }
-      break;
-    case FIN_RZ0:
-      sc->rz = a;
-      // CG needs z.r > 0 (SPD preconditioner); flexible CG only needs a finite value
-      if (sc->flexible ? (a != a) : !(a > 0.0)) { sc->status = TOMG_E_BREAKDOWN; sc->done = 1; sc->pad = 2; }
-      break;
-    case FIN_ALPHA:
-      sc->pq = a;
-      if (!(a > 0.0)) { sc->status = TOMG_E_BREAKDOWN; sc->done = 1; sc->pad = 3; break; }
-      sc->alpha = sc->rz / a;
-      break;
-    case FIN_RR:
-      sc->rr = a;
-      sc->it += 1;
-      if (a != a) { sc->status = TOMG_E_BREAKDOWN; sc->done = 1; sc->pad = 1; }
-      else if (a <= sc->tol2) { sc->done = 1; }
-      else if (sc->it >= sc->max_iter) { sc->status = TOMG_NOT_CONVERGED; sc->done = 1; }
-      break;
-    case FIN_BETA:  // a = z.r (new), b = z.q
-      // CG: beta = z.r / z_old.r_old.  Flexible CG (Notay 2000): beta = z^T (r - r_old) /
-      // z_old.r_old = -alpha z.q / z_old.r_old = -z.q / p.q, which needs no sign of z.r.
-      if (sc->flexible ? (a != a || b != b) : !(a > 0.0)) {
-        sc->status = TOMG_E_BREAKDOWN; sc->done = 1; sc->pad = 4; break;
-      }
-      sc->rz_new = a;
-      sc->zq = b;
-      sc->beta = sc->flexible ? (-b / sc->pq) : (a / sc->rz);
-      sc->rz = a;
-      break;
-  }
+  finish_body(kind, pa, na, pb, nb, sc, sred);
 }
 
 __global__ void __launch_bounds__(RED_THREADS) k_xr(double* __restrict__ x, double* __restrict__ r,
                                                     const double* __restrict__ p,
                                                     const double* __restrict__ q, int64_t n,
-                                                    const Scalars* sc, double* partials) {
+                                                    Scalars* sc, double* partials,
+                                                    float* __restrict__ r32) {
   __shared__ double sred[32];
   pdl_prologue();
   if (sc->done) return;
@@ -95,16 +52,23 @@ __global__ void __launch_bounds__(RED_THREADS) k_xr(double* __restrict__ x, doub
     x[i] += alpha * p[i];
     const double ri = r[i] - alpha * q[i];
     r[i] = ri;
+    if (r32) r32[i] = (float)ri;
     s += ri * ri;
   }
   s = block_sum(s, sred);
   if (threadIdx.x == 0) partials[blockIdx.x] = s;
+  if (last_block(&sc->tk[TK_RR])) finish_body(FIN_RR, partials, gridDim.x, nullptr, 0, sc, sred);
 }
 
+// p = z + beta p.  The last kernel of an iteration: with has_cond it also sets the while
+// condition of the captured loop from the done flag (before any early exit, so the loop ends
+// on every path that sets done).
 __global__ void k_p(double* __restrict__ p, const double* __restrict__ z, int64_t n,
-                    const Scalars* sc) {
+                    const Scalars* sc, cudaGraphConditionalHandle cond, int has_cond) {
   pdl_prologue();
-  if (sc->done) return;
+  const int done = *(volatile const int*)&sc->done;
+  if (has_cond && blockIdx.x == 0 && threadIdx.x == 0) cudaGraphSetConditional(cond, done ? 0u : 1u);
+  if (done) return;
   const double beta = sc->beta;
   for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
     p[i] = z[i] + beta * p[i];
@@ -114,10 +78,11 @@ template <class T>
 __global__ void __launch_bounds__(RED_THREADS) k_zdots(const T* __restrict__ z, double* z64,
                                                        const double* __restrict__ r,
                                                        const double* __restrict__ q, int64_t n,
-                                                       double* pa, double* pb, const int* done) {
+                                                       double* pa, double* pb, Scalars* sc,
+                                                       int kind) {
   __shared__ double sred[32];
   pdl_prologue();
-  if (solve_done(done)) return;
+  if (sc->done) return;
   double a = 0.0, b = 0.0;
   for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
     const double zi = (double)z[i];
@@ -129,8 +94,10 @@ __global__ void __launch_bounds__(RED_THREADS) k_zdots(const T* __restrict__ z, 
   b = block_sum(b, sred);
   if (threadIdx.x == 0) {
     pa[blockIdx.x] = a;
-    if (pb) pb[blockIdx.x] = b;
+    if (q) pb[blockIdx.x] = b;
   }
+  if (last_block(&sc->tk[TK_DOTS]))
+    finish_body(kind, pa, gridDim.x, pb, q ? gridDim.x : 0, sc, sred);
 }
 
 template <class T>
@@ -188,7 +155,8 @@ __global__ void k_gemv(int n, const T* __restrict__ A, const T* __restrict__ b, 
 //   k_potrf_diag  factor the diagonal block in shared memory and invert it (L_kk^-1 saved)
 //   k_panel       L_ik = A_ik L_kk^-T for the rows below
 //   k_syrk        A_ij -= L_ik L_jk^T on the trailing lower triangle (32 x 32 tiles)
-// then Y = L^-1 by blocked forward substitution (k_fwd_T, k_fwd_Y) and A^-1 = Y^T Y (k_ltl).
+// then Y = L^-1 by right-looking blocked forward substitution (k_inv_row, k_inv_update) and
+// A^-1 = Y^T Y (k_ltl).
 constexpr int NB = 32;
 
 __global__ void __launch_bounds__(NB * NB) k_potrf_diag(int n, int k0, double* A, double* Linv,
@@ -274,65 +242,59 @@ __global__ void __launch_bounds__(32 * 8) k_syrk(int n, int k0, double* A) {
   }
 }
 
-// forward substitution for block row K of Y = L^-1:
-//   T[r][c] = delta_rc - sum_{m = c}^{K0-1} L[r][m] Y[m][c]   (r in the block, c < K0 + kb)
-// computed as a 32 x 64 output tile per block (8 outputs per thread), L and Y staged in shared
-// memory 32 columns of m at a time; m-tiles entirely above Y's diagonal are skipped
-__global__ void __launch_bounds__(256) k_fwd_T(int n, int K0, const double* __restrict__ L,
-                                               const double* __restrict__ Y, double* T) {
-  __shared__ double Ls[32][33];
-  __shared__ double Ys[32][65];
-  const int kb = min(NB, n - K0);
-  const int C = K0 + kb;
-  const int cb = blockIdx.x * 64;
+// Y = L^-1 by right-looking block forward substitution on L Y = I, with Y holding the
+// right-hand side B = I at the start.  Step k: block row k becomes X_k = L_kk^-1 B_k (tiles
+// j <= k, k_inv_row), then every later block row is updated, B_i -= L_ik X_k (tiles i > k,
+// j <= k, k_inv_update).  Every tile is a 32 x 32 x 32 product on its own block, so a step
+// spreads over up to (K - k - 1)(k + 1) SMs instead of walking the rows one block at a time.
+__global__ void __launch_bounds__(256) k_inv_row(int n, int K0, const double* __restrict__ LinvKK,
+                                                 double* Y) {
+  __shared__ double Li[NB][NB + 1];
+  __shared__ double Bt[NB][NB + 1];
   const int tx = threadIdx.x, ty = threadIdx.y;  // 32 x 8
-  double acc[4][2];
-#pragma unroll
-  for (int a = 0; a < 4; a++) acc[a][0] = acc[a][1] = 0.0;
-  for (int mt = (cb / 32) * 32; mt < K0; mt += 32) {
-    for (int q = ty; q < 32; q += 8) {
-      const int r = K0 + q, m = mt + tx;
-      Ls[q][tx] = (q < kb && m < K0) ? L[(int64_t)r * n + m] : 0.0;
-      const int mm = mt + q;
-      const int c0 = cb + tx, c1 = cb + 32 + tx;
-      Ys[q][tx] = (mm < K0 && c0 < C) ? Y[(int64_t)mm * n + c0] : 0.0;
-      Ys[q][tx + 32] = (mm < K0 && c1 < C) ? Y[(int64_t)mm * n + c1] : 0.0;
-    }
-    __syncthreads();
-#pragma unroll 8
-    for (int m = 0; m < 32; m++) {
-      const double y0 = Ys[m][tx], y1 = Ys[m][tx + 32];
-#pragma unroll
-      for (int a = 0; a < 4; a++) {
-        const double l = Ls[ty * 4 + a][m];
-        acc[a][0] += l * y0;
-        acc[a][1] += l * y1;
-      }
-    }
-    __syncthreads();
+  const int kb = min(NB, n - K0);
+  const int c0 = blockIdx.x * NB;
+  for (int r = ty; r < NB; r += 8) {
+    Li[r][tx] = LinvKK[r * NB + tx];
+    const int c = c0 + tx;
+    Bt[r][tx] = (r < kb && c < n) ? Y[(int64_t)(K0 + r) * n + c] : 0.0;
   }
-#pragma unroll
-  for (int a = 0; a < 4; a++) {
-    const int t = ty * 4 + a, r = K0 + t;
-    if (t >= kb) continue;
-#pragma unroll
-    for (int h = 0; h < 2; h++) {
-      const int c = cb + tx + 32 * h;
-      if (c < C) T[(int64_t)t * n + c] = ((r == c) ? 1.0 : 0.0) - acc[a][h];
-    }
+  __syncthreads();
+  for (int r = ty; r < kb; r += 8) {
+    const int c = c0 + tx;
+    double v = 0.0;
+    for (int t = 0; t <= r; t++) v += Li[r][t] * Bt[t][tx];
+    if (c < n) Y[(int64_t)(K0 + r) * n + c] = v;
   }
 }
-//   Y[r][c] = sum_t Linv_KK[r - K0][t] T[t][c]; zero above the diagonal
-__global__ void k_fwd_Y(int n, int K0, const double* __restrict__ LinvKK,
-                        const double* __restrict__ T, double* Y) {
-  const int c = blockIdx.x * blockDim.x + threadIdx.x;
-  const int r = K0 + blockIdx.y;
+
+__global__ void __launch_bounds__(256) k_inv_update(int n, int K0, const double* __restrict__ L,
+                                                    double* Y) {
+  __shared__ double Lt[NB][NB + 1];
+  __shared__ double Xt[NB][NB + 1];
+  const int tx = threadIdx.x, ty = threadIdx.y;  // 32 x 8
   const int kb = min(NB, n - K0);
-  if (c >= n) return;
-  double v = 0.0;
-  if (c < K0 + kb)
-    for (int t = 0; t <= r - K0; t++) v += LinvKK[(r - K0) * NB + t] * T[(int64_t)t * n + c];
-  Y[(int64_t)r * n + c] = (c <= r) ? v : 0.0;
+  const int c0 = blockIdx.x * NB;
+  const int r0 = K0 + kb + blockIdx.y * NB;
+  for (int r = ty; r < NB; r += 8) {
+    const int gi = r0 + r, c = c0 + tx;
+    Lt[r][tx] = (gi < n && tx < kb) ? L[(int64_t)gi * n + K0 + tx] : 0.0;
+    Xt[r][tx] = (r < kb && c < n) ? Y[(int64_t)(K0 + r) * n + c] : 0.0;
+  }
+  __syncthreads();
+  for (int r = ty; r < NB; r += 8) {
+    const int gi = r0 + r, c = c0 + tx;
+    if (gi >= n || c >= n) continue;
+    double v = 0.0;
+#pragma unroll 8
+    for (int t = 0; t < NB; t++) v += Lt[r][t] * Xt[t][tx];
+    Y[(int64_t)gi * n + c] -= v;
+  }
+}
+
+__global__ void k_eye(int n, double* Y) {
+  const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (t < (int64_t)n * n) Y[t] = (t / n == t % n) ? 1.0 : 0.0;
 }
 
 // Ainv = Linv^T Linv, computed for i >= j and mirrored (exactly symmetric)
@@ -344,11 +306,6 @@ __global__ void k_ltl(int n, const double* __restrict__ Li, double* Ainv) {
   for (int t = i; t < n; t++) v += Li[(int64_t)t * n + i] * Li[(int64_t)t * n + j];
   Ainv[(int64_t)i * n + j] = v;
   Ainv[(int64_t)j * n + i] = v;
-}
-
-__global__ void k_set_cond(cudaGraphConditionalHandle h, const Scalars* sc) {
-  pdl_prologue();
-  cudaGraphSetConditional(h, sc->done ? 0u : 1u);
 }
 
 inline int grid_for(int64_t n) { return std::max(1, std::min(RED_MAX_BLOCKS, ceil_div(n, RED_THREADS * 4))); }
@@ -368,23 +325,24 @@ void finish(cudaStream_t s, int kind, const double* pa, int na, const double* pb
 }
 
 void xr_update(cudaStream_t s, double* x, double* r, const double* p, const double* q, int64_t n,
-               const Scalars* sc, double* partials) {
-  LAUNCH(k_xr, grid_for(n), RED_THREADS, 0, s, x, r, p, q, n, sc, partials);
+               Scalars* sc, double* partials, float* r32) {
+  LAUNCH(k_xr, grid_for(n), RED_THREADS, 0, s, x, r, p, q, n, sc, partials, r32);
 }
 
-void p_update(cudaStream_t s, double* p, const double* z, int64_t n, const Scalars* sc) {
-  LAUNCH(k_p, grid_for(n), RED_THREADS, 0, s, p, z, n, sc);
+void p_update(cudaStream_t s, double* p, const double* z, int64_t n, const Scalars* sc,
+              cudaGraphConditionalHandle cond, int has_cond) {
+  LAUNCH(k_p, grid_for(n), RED_THREADS, 0, s, p, z, n, sc, cond, has_cond);
 }
 
 template <class T>
 void z_dots(cudaStream_t s, const T* z, double* z64, const double* r, const double* q, int64_t n,
-            double* pa, double* pb, const int* done) {
-  LAUNCH((k_zdots<T>), grid_for(n), RED_THREADS, 0, s, z, z64, r, q, n, pa, pb, done);
+            double* pa, double* pb, Scalars* sc, int kind) {
+  LAUNCH((k_zdots<T>), grid_for(n), RED_THREADS, 0, s, z, z64, r, q, n, pa, pb, sc, kind);
 }
 template void z_dots<float>(cudaStream_t, const float*, double*, const double*, const double*,
-                            int64_t, double*, double*, const int*);
+                            int64_t, double*, double*, Scalars*, int);
 template void z_dots<double>(cudaStream_t, const double*, double*, const double*, const double*,
-                             int64_t, double*, double*, const int*);
+                             int64_t, double*, double*, Scalars*, int);
 
 template <class T>
 void cast_in(cudaStream_t s, const double* a, T* b, int64_t n, const int* done) {
@@ -427,11 +385,10 @@ int dense_spd_inverse(cudaStream_t s, int n, double* A, double* work) {
   double* Y = work;  // n x n
   const int nblk = ceil_div(n, NB);
   DBuf<int> fail;
-  DBuf<double> linv, T;
+  DBuf<double> linv;
   fail.resize(1);
   fail.zero(s);
   linv.resize((size_t)nblk * NB * NB);
-  T.resize((size_t)NB * n);
   for (int b = 0; b < nblk; b++) {
     const int k0 = b * NB;
     double* Lb = linv.p + (size_t)b * NB * NB;
@@ -447,10 +404,12 @@ int dense_spd_inverse(cudaStream_t s, int n, double* A, double* work) {
   CK(cudaMemcpyAsync(&f, fail.p, sizeof(int), cudaMemcpyDeviceToHost, s));
   CK(cudaStreamSynchronize(s));
   if (f) return f;
+  LAUNCH(k_eye, ceil_div((int64_t)n * n, 256), 256, 0, s, n, Y);
   for (int b = 0; b < nblk; b++) {
     const int K0 = b * NB, kb = std::min(NB, n - K0);
-    LAUNCH(k_fwd_T, ceil_div(K0 + kb, 64), dim3(32, 8), 0, s, n, K0, A, Y, T.p);
-    LAUNCH(k_fwd_Y, dim3(ceil_div(n, 128), kb), 128, 0, s, n, K0, linv.p + (size_t)b * NB * NB, T.p, Y);
+    LAUNCH(k_inv_row, b + 1, dim3(32, 8), 0, s, n, K0, linv.p + (size_t)b * NB * NB, Y);
+    const int below = ceil_div(n - K0 - kb, NB);
+    if (below > 0) LAUNCH(k_inv_update, dim3(b + 1, below), dim3(32, 8), 0, s, n, K0, A, Y);
   }
   dim3 blk(16, 16), grd(ceil_div(n, 16), ceil_div(n, 16));
   LAUNCH(k_ltl, grd, blk, 0, s, n, Y, A);
@@ -458,8 +417,5 @@ int dense_spd_inverse(cudaStream_t s, int n, double* A, double* work) {
   return 0;
 }
 
-void set_conditional(cudaStream_t s, cudaGraphConditionalHandle h, const Scalars* sc) {
-  LAUNCH(k_set_cond, 1, 1, 0, s, h, sc);
-}
 
 }  // namespace tomg

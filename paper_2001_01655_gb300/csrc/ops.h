@@ -7,7 +7,10 @@
 
 namespace tomg {
 
-enum OpMode { MODE_APPLY = 0, MODE_RESID = 1, MODE_JACOBI = 2 };
+// MODE_RESID0 fuses the first smoothing sweep from a zero guess with the residual that follows
+// it: x = w Dinv b is WRITTEN to the x argument, and y = b - A x.
+enum OpMode { MODE_APPLY = 0, MODE_RESID = 1, MODE_JACOBI = 2, MODE_RESID0 = 3 };
+struct Scalars;
 
 // ---------------- level 0: matrix-free SIMP element-by-element operator ----------------
 // A = M (sum_e E_e Ke) M + (I - M), M = free-DOF mask (mask byte per node, bit c = DOF c
@@ -18,6 +21,7 @@ struct Ebe {
   const void* Ke;  // T[nd*nd], nd = dim * 2^dim
   const void* E;   // T[n_elems]
   const uint8_t* mask;
+  int tile = 0;    // quad4 FP32: nodes per thread of the tiled kernel (1, 2, 4; 0 = 4)
 };
 template <class T>
 void ebe_op(cudaStream_t s, int mode, const Ebe& op, const T* x, T* y, const T* b,
@@ -28,6 +32,9 @@ template <class T, int MODE, bool DOT>
 void ebe2d_launch(cudaStream_t s, const Ebe& op, const T* x, T* y, const T* b, const T* Dinv,
                   double omega, const int* done, double* parts);
 int ebe2d_blocks(const Ebe& op);
+// fastest quad4 FP32 tile (nodes per thread) for this grid, timed on the stream with scratch
+// vectors the first time a grid shape is seen, cached per shape afterwards
+int ebe2d_autotune(cudaStream_t s, const Ebe& op, const float* Dinv);
 // hex8 FP32 tiled implementation behind ebe_op (k_ebe3d.cu; no fused dot)
 void ebe3d_launch(cudaStream_t s, int mode, const Ebe& op, const float* x, float* y,
                   const float* b, const float* Dinv, double omega, const int* done);
@@ -51,9 +58,10 @@ void stencil_op(cudaStream_t s, int mode, const Geo& g, const T* S, const T* x, 
                 const T* Dinv, double omega, const int* done);
 void stencil_block_diag_inv(cudaStream_t s, const Geo& g, const double* S, double* Dinv64,
                             float* Dinv32);
-// FP64 y = S x with per-block partials of x . y (stencil_blocks(g) partials)
+// FP64 y = S x with per-block partials of x . y (stencil_blocks(g) partials); with sc set, the
+// last block applies FIN_ALPHA (sc->done is then the early-exit flag)
 void stencil_apply_dot(cudaStream_t s, const Geo& g, const double* S, const double* x, double* y,
-                       const int* done, double* partials);
+                       const int* done, double* partials, Scalars* sc);
 int stencil_blocks(const Geo& g);
 // Galerkin product with bilinear / trilinear P (coarse node I at fine position min(2I, n))
 void stencil_rap(cudaStream_t s, const Geo& fine, const Geo& coarse, const double* Sf, double* Sc);
@@ -140,7 +148,9 @@ void rigid_body_modes(cudaStream_t s, const Geo& g, const double* xs, const doub
 struct Scalars {     // device-resident state of one outer solve
   double bb, rr, rz, pq, zq, rz_new, alpha, beta, rtol2, tol2;
   int done, it, status, max_iter, flexible, pad;
+  unsigned tk[4];    // arrival tickets of the kernels that finish their own reductions
 };
+enum Ticket { TK_ALPHA = 0, TK_RR = 1, TK_DOTS = 2 };
 int red_blocks(int64_t n);
 void dot_partials(cudaStream_t s, const double* x, const double* y, int64_t n, double* partials,
                   const int* done);
@@ -148,13 +158,17 @@ void dot_partials(cudaStream_t s, const double* x, const double* y, int64_t n, d
 enum FinishKind { FIN_INIT = 0, FIN_RZ0 = 1, FIN_ALPHA = 2, FIN_RR = 3, FIN_BETA = 4 };
 void finish(cudaStream_t s, int kind, const double* partA, int nA, const double* partB, int nB,
             Scalars* sc);
+// x += alpha p, r -= alpha q, r32 = (float) r (nullable), then FIN_RR in the last block
 void xr_update(cudaStream_t s, double* x, double* r, const double* p, const double* q, int64_t n,
-               const Scalars* sc, double* partials);
-void p_update(cudaStream_t s, double* p, const double* z, int64_t n, const Scalars* sc);
-// z64 = (double) z (T = float) or z itself; partials of z.r and z.q
+               Scalars* sc, double* partials, float* r32);
+// p = z + beta p; with has_cond, also sets the graph's while condition to !done
+void p_update(cudaStream_t s, double* p, const double* z, int64_t n, const Scalars* sc,
+              cudaGraphConditionalHandle cond, int has_cond);
+// z64 = (double) z (T = float) or z itself; partials of z.r and z.q (q nullable), then finish
+// step `kind` (FIN_RZ0 or FIN_BETA) in the last block
 template <class T>
 void z_dots(cudaStream_t s, const T* z, double* z64, const double* r, const double* q, int64_t n,
-            double* partA, double* partB, const int* done);
+            double* partA, double* partB, Scalars* sc, int kind);
 template <class T>
 void cast_in(cudaStream_t s, const double* a, T* b, int64_t n, const int* done);
 void copy_f64(cudaStream_t s, const double* a, double* b, int64_t n, const int* done);
@@ -168,6 +182,5 @@ template <class T>
 void dense_gemv(cudaStream_t s, int n, const T* Ainv, const T* b, T* x, const int* done);
 // dense SPD inverse via Cholesky (FP64, in place: A -> A^-1); returns 0 or row of failure+1
 int dense_spd_inverse(cudaStream_t s, int n, double* A, double* work);
-void set_conditional(cudaStream_t s, cudaGraphConditionalHandle h, const Scalars* sc);
 
 }  // namespace tomg

@@ -7,9 +7,31 @@
 #include <cmath>
 #include <cstring>
 
+#include <chrono>
+#include <cstdio>
+
 #include "solver.h"
 
 namespace tomg {
+
+// Phase timing of the setup for diagnosis (TOMG_TRACE_SETUP=1): synchronises the stream at
+// each mark and prints the host time since the previous mark to stderr.
+struct SetupTrace {
+  bool on;
+  cudaStream_t s;
+  std::chrono::steady_clock::time_point t0;
+  explicit SetupTrace(cudaStream_t st) : on(getenv("TOMG_TRACE_SETUP") != nullptr), s(st),
+                                         t0(std::chrono::steady_clock::now()) {}
+  void mark(const char* what, int level = -1) {
+    if (!on) return;
+    cudaStreamSynchronize(s);
+    const auto t = std::chrono::steady_clock::now();
+    fprintf(stderr, "[setup] %-22s L%-2d %8.3f ms\n", what, level,
+            std::chrono::duration<double, std::milli>(t - t0).count());
+    t0 = t;
+  }
+};
+
 
 // ----------------------------------------------------------------------------------------
 // element stiffness by 2x2(x2) Gauss quadrature on the unit element (bilinear quad4 plane
@@ -107,7 +129,7 @@ template <> struct V<float> {
   static float* y(LevelWork& l) { return l.y32.p; }
   static const float* Ainv(const tomg_problem* P) { return P->Ainv32.p; }
   static Ebe ebe(const tomg_problem* P) {
-    return Ebe{P->dim, P->nx, P->ny, P->nz, P->Ke32.p, P->E32.p, P->mask.p};
+    return Ebe{P->dim, P->nx, P->ny, P->nz, P->Ke32.p, P->E32.p, P->mask.p, P->ebe_tile};
   }
 };
 
@@ -168,13 +190,18 @@ void vcycle(tomg_problem* P, Work& W, int l, const T* b, T* out, const int* done
   }
   T* x = V<T>::x(lw);
   T* r = V<T>::r(lw);
-  // pre-smoothing, the first sweep from x = 0 needs no operator apply
-  jacobi0<T>(s, Lv.b, Lv.nn, V<T>::D(Lv), b, x, w, done);
-  for (int k = 1; k < P->opt.n_pre; k++) {
-    level_op<T>(P, s, l, MODE_JACOBI, x, r, b, done);
-    std::swap(x, r);
+  // pre-smoothing; the first sweep from x = 0 needs no operator apply, and with a single
+  // pre-sweep it is fused into the residual pass (x = w Dinv b, r = b - A x in one kernel)
+  if (P->opt.n_pre == 1) {
+    level_op<T>(P, s, l, MODE_RESID0, x, r, b, done);
+  } else {
+    jacobi0<T>(s, Lv.b, Lv.nn, V<T>::D(Lv), b, x, w, done);
+    for (int k = 1; k < P->opt.n_pre; k++) {
+      level_op<T>(P, s, l, MODE_JACOBI, x, r, b, done);
+      std::swap(x, r);
+    }
+    level_op<T>(P, s, l, MODE_RESID, x, r, b, done);  // r = b - A x
   }
-  level_op<T>(P, s, l, MODE_RESID, x, r, b, done);  // r = b - A x
   LevelWork& cw = W.lw[l + 1];
   restrict_to<T>(P, s, l, r, V<T>::b(cw), done);
   vcycle<T>(P, W, l + 1, V<T>::b(cw), V<T>::y(cw), done);
@@ -187,32 +214,36 @@ void vcycle(tomg_problem* P, Work& W, int l, const T* b, T* out, const int* done
   }
 }
 
-// z = M r (outer residual in FP64), then partials of z.r (and z.q)
-void apply_M_and_dots(tomg_problem* P, Work& W, const double* q, const int* done) {
+// z = M r (outer residual in FP64), then z.r (and z.q) reduced into the scalar state (FIN_RZ0
+// without q, FIN_BETA with it).  r32_ready: the FP32 copy of r is already in the level-0 b32.
+void apply_M_and_dots(tomg_problem* P, Work& W, const double* q, const int* done, bool r32_ready) {
   const int64_t n = P->n;
   LevelWork& l0 = W.lw[0];
   cudaStream_t s = W.stream;
   if (P->opt.prec == TOMG_PREC_FP64) {
     vcycle<double>(P, W, 0, W.r.p, W.z.p, done);
-    z_dots<double>(s, W.z.p, W.z.p, W.r.p, q, n, W.partA.p, q ? W.partB.p : nullptr, done);
+    z_dots<double>(s, W.z.p, W.z.p, W.r.p, q, n, W.partA.p, W.partB.p, W.sc.p, q ? FIN_BETA : FIN_RZ0);
   } else {
-    cast_in<float>(s, W.r.p, l0.b32.p, n, done);
+    if (!r32_ready) cast_in<float>(s, W.r.p, l0.b32.p, n, done);
     vcycle<float>(P, W, 0, l0.b32.p, l0.y32.p, done);
-    z_dots<float>(s, l0.y32.p, W.z.p, W.r.p, q, n, W.partA.p, q ? W.partB.p : nullptr, done);
+    z_dots<float>(s, l0.y32.p, W.z.p, W.r.p, q, n, W.partA.p, W.partB.p, W.sc.p, q ? FIN_BETA : FIN_RZ0);
   }
 }
 
 // FP64 outer operator K (masked): the assembled fine stencil when the setup kept it (36 / 243
 // FMAs per node instead of 72 / 600 for the element products), else the matrix-free kernel
+// Outer-loop K in FP64: the assembled fine stencil when the setup kept it (36 / 243 FMAs per
+// node instead of 64 / 576 for the element products), else the FP64 element kernel.  Partials
+// of x . y (nullable); with sc set, FIN_ALPHA is applied to the scalar state on the device.
 void fine64_apply_dot(tomg_problem* P, cudaStream_t s, const double* x, double* y, const int* done,
-                      double* partials) {
+                      double* partials, Scalars* sc) {
   Level& L0 = *P->L[0];
-  if (L0.S64.p) stencil_apply_dot(s, L0.g, L0.S64.p, x, y, done, partials);
-  else ebe_op<double>(s, MODE_APPLY, V<double>::ebe(P), x, y, nullptr, nullptr, 0.0, done, partials);
-}
-int fine64_blocks(tomg_problem* P) {
-  Level& L0 = *P->L[0];
-  return L0.S64.p ? stencil_blocks(L0.g) : ebe_blocks(V<double>::ebe(P));
+  if (L0.S64.p) {
+    stencil_apply_dot(s, L0.g, L0.S64.p, x, y, done, partials, sc);
+  } else {
+    ebe_op<double>(s, MODE_APPLY, V<double>::ebe(P), x, y, nullptr, nullptr, 0.0, done, partials);
+    if (sc) finish(s, FIN_ALPHA, partials, ebe_blocks(V<double>::ebe(P)), nullptr, 0, sc);
+  }
 }
 void fine64_resid(tomg_problem* P, cudaStream_t s, const double* x, double* y, const double* b) {
   level_op<double>(P, s, 0, MODE_RESID, x, y, b, nullptr);
@@ -223,13 +254,12 @@ void iteration_body(tomg_problem* P, Work& W) {
   Scalars* sc = W.sc.p;
   const int* done = &sc->done;
   cudaStream_t s = W.stream;
-  fine64_apply_dot(P, s, W.p.p, W.q.p, done, W.partA.p);
-  finish(s, FIN_ALPHA, W.partA.p, fine64_blocks(P), nullptr, 0, sc);
-  xr_update(s, W.x.p, W.r.p, W.p.p, W.q.p, n, sc, W.partA.p);
-  finish(s, FIN_RR, W.partA.p, red_blocks(n), nullptr, 0, sc);
-  apply_M_and_dots(P, W, W.q.p, done);
-  finish(s, FIN_BETA, W.partA.p, red_blocks(n), W.partB.p, red_blocks(n), sc);
-  p_update(s, W.p.p, W.z.p, n, sc);
+  const bool mixed = P->opt.prec != TOMG_PREC_FP64;
+  fine64_apply_dot(P, s, W.p.p, W.q.p, done, W.partA.p, sc);                // + FIN_ALPHA
+  xr_update(s, W.x.p, W.r.p, W.p.p, W.q.p, n, sc, W.partA.p,
+            mixed ? W.lw[0].b32.p : nullptr);                               // + FIN_RR
+  apply_M_and_dots(P, W, W.q.p, done, mixed);                               // + FIN_BETA
+  p_update(s, W.p.p, W.z.p, n, sc, W.cond, W.has_cond);
 }
 
 void destroy_graph(Work& W) {
@@ -264,15 +294,18 @@ void build_graph(tomg_problem* P, Work& W) {
     CK(cudaGraphAddNode(&node, W.graph, nullptr, nullptr, 0, &cp));
     cudaGraph_t body = cp.conditional.phGraph_out[0];
     CK(cudaStreamBeginCaptureToGraph(s, body, nullptr, nullptr, 0, cudaStreamCaptureModeThreadLocal));
+    W.cond = h;
+    W.has_cond = 1;
     try {
       iteration_body(P, W);
-      set_conditional(s, h, W.sc.p);
     } catch (...) {
+      W.has_cond = 0;
       cudaGraph_t dummy;
       cudaStreamEndCapture(s, &dummy);
       g_launches = saved;
       throw;
     }
+    W.has_cond = 0;
     CK(cudaStreamEndCapture(s, &body));
   } else {
     CK(cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal));
@@ -349,6 +382,7 @@ void make_bsr_from_stencil(tomg_problem* P, Level& Lv) {
 
 void amg_extend(tomg_problem* P, int start) {
   cudaStream_t s = st(P);
+  SetupTrace tr(s);
   const tomg_options& o = P->opt;
   {
     Level& S0 = *P->L[start];
@@ -370,6 +404,7 @@ void amg_extend(tomg_problem* P, int start) {
     rigid_body_modes(s, S0.g, dx.p, dy.p, dz.p, B.p);
     CK(cudaStreamSynchronize(s));
   }
+  tr.mark("bsr+rbm", start);
   int cur = start;
   while (P->L[cur]->n >= o.max_coarse_dofs && (int)P->L.size() < o.max_levels) {
     Level& A = *P->L[cur];
@@ -383,12 +418,15 @@ void amg_extend(tomg_problem* P, int start) {
     const int64_t nS = exclusive_scan(s, scnt.p, srp.p, nn);
     sci.resize(nS > 0 ? nS : 1);
     amg_strength_fill(s, Ab, A.V64.p, o.soc_beta, srp.p, sci.p);
+    tr.mark("strength", cur);
     // aggregation
     DBuf<int> state, root_scan, agg;
     DBuf<uint64_t> vv, m1;
     state.resize(nn); root_scan.resize(nn + 1); agg.resize(nn); vv.resize(nn); m1.resize(nn);
     amg_mis2(s, nn, srp.p, sci.p, cur, state.p, vv.p, m1.p, P->flag_host, P->flag_dev.p);
+    tr.mark("mis2", cur);
     const int n_agg = amg_aggregate(s, nn, srp.p, sci.p, cur, state.p, agg.p, root_scan.p);
+    tr.mark("aggregate", cur);
     if (n_agg == 0 || (int64_t)n_agg * k >= A.n) break;
     // tentative prolongator
     DBuf<int> Trp, Tci;
@@ -403,11 +441,14 @@ void amg_extend(tomg_problem* P, int start) {
     // prolongator smoothing weight from rho(D^-1 A)
     DBuf<double> pv, pw, parts;
     pv.resize(A.n); pw.resize(A.n); parts.resize(std::max(ceil_div(nn, 256), 256));
+    tr.mark("tentative", cur);
     const double rho = amg_spectral_radius(s, Ab, A.V64.p, A.D64.p, cur, 20, pv.p, pw.p, parts.p);
     const double omegaP = 4.0 / (3.0 * rho);
+    tr.mark("spectral_radius", cur);
     // P = T - omega D^-1 A T
     OwnedBsr AT;
     spgemm_full(s, Ab, A.V64.p, Tm, TV.p, AT);
+    tr.mark("A*T", cur);
     A.Pnnzb = AT.m.nnzb;
     A.Prp = std::move(AT.rp);
     A.Pci = std::move(AT.ci);
@@ -426,10 +467,13 @@ void amg_extend(tomg_problem* P, int start) {
       A.Rv64.resize(std::max<int64_t>(1, A.Pnnzb * b * k));
       bsr_transpose_fill(s, Pm, A.Pv64.p, A.Rrp.p, A.Rci.p, A.Rv64.p, cursor.p);
     }
+    tr.mark("smoothP+transpose", cur);
     // A_c = R (A P)  (Eq. 9)
     OwnedBsr AP, Ac;
     spgemm_full(s, Ab, A.V64.p, Pm, A.Pv64.p, AP);
+    tr.mark("A*P", cur);
     spgemm_full(s, A.Rmat(n_agg), A.Rv64.p, AP.m, AP.V.p, Ac);
+    tr.mark("R*(AP)", cur);
     amg_fix_zero_rows(s, Ac.m, Ac.V.p);
     A.Pv32.resize(A.Pv64.n); cast_f64_f32(s, A.Pv64.p, A.Pv32.p, A.Pv64.n);
     A.Rv32.resize(A.Rv64.n); cast_f64_f32(s, A.Rv64.p, A.Rv32.p, A.Rv64.n);
@@ -455,6 +499,7 @@ void amg_extend(tomg_problem* P, int start) {
     B = std::move(Bc);
     cur++;
     CK(cudaStreamSynchronize(s));
+    tr.mark("coarse level", cur);
   }
 }
 
@@ -561,6 +606,7 @@ void setup(tomg_problem* P, const tomg_options& opt) {
   P->setup_gen++;
   P->opt = opt;
   CK(cudaEventRecord(P->ev0, s));
+  SetupTrace tr(s);
   P->L.clear();
   P->jacobi_only = (opt.pc == TOMG_PC_JACOBI);
   // level 0: matrix-free SIMP operator
@@ -575,8 +621,11 @@ void setup(tomg_problem* P, const tomg_options& opt) {
     L0->D64.resize(P->nn * P->dim * P->dim);
     L0->D32.resize(P->nn * P->dim * P->dim);
     ebe_block_diag_inv(s, V<double>::ebe(P), L0->D64.p, L0->D32.p);
+    if (P->dim == 2 && opt.prec != TOMG_PREC_FP64 && P->ebe_tile == 0)
+      P->ebe_tile = ebe2d_autotune(s, V<float>::ebe(P), L0->D32.p);
     P->L.push_back(std::move(L0));
   }
+  tr.mark("level0 diag", 0);
   if (!P->jacobi_only) {
     int n_geo = 1;
     if (opt.pc == TOMG_PC_GMG)
@@ -589,6 +638,7 @@ void setup(tomg_problem* P, const tomg_options& opt) {
     Level& L0 = *P->L[0];
     L0.S64.resize((int64_t)stencil_q(P->dim) * P->nn);
     ebe_assemble_stencil(s, V<double>::ebe(P), L0.S64.p);
+    tr.mark("level0 stencil", 0);
     for (int l = 1; l < n_geo; l++) {
       Level& F = *P->L[l - 1];
       auto C = std::make_unique<Level>();
@@ -607,8 +657,10 @@ void setup(tomg_problem* P, const tomg_options& opt) {
       stencil_block_diag_inv(s, C->g, C->S64.p, C->D64.p, C->D32.p);
       F.geo_next = true;
       P->L.push_back(std::move(C));
+      tr.mark("geometric RAP", l);
     }
     if (opt.pc == TOMG_PC_AMG || opt.pc == TOMG_PC_HYBRID) amg_extend(P, (int)P->L.size() - 1);
+    tr.mark("amg total");
     // coarsest level: dense FP64 Cholesky -> explicit inverse
     Level& Cl = *P->L.back();
     if (Cl.n > 16384)
@@ -623,6 +675,7 @@ void setup(tomg_problem* P, const tomg_options& opt) {
     if (fail) TOMG_THROW(TOMG_E_BREAKDOWN, "coarse operator not SPD (pivot %d)", fail - 1);
     P->Ainv32.resize(P->Ainv64.n);
     cast_f64_f32(s, P->Ainv64.p, P->Ainv32.p, P->Ainv64.n);
+    tr.mark("coarse inverse", (int)P->L.size() - 1);
     // setup-only storage of the fine level (its FP64 stencil stays: it carries every FP64
     // application of K, see fine64_apply_dot)
     L0.rp.release(); L0.ci.release(); L0.V64.release();
@@ -699,8 +752,7 @@ void init_solve(tomg_problem* P, Work& W, int max_iter) {
   *W.sc_host = h;
   CK(cudaMemcpyAsync(W.sc.p, W.sc_host, sizeof(Scalars), cudaMemcpyHostToDevice, s));
   finish(s, FIN_INIT, W.partA.p, red_blocks(n), W.partB.p, red_blocks(n), W.sc.p);
-  apply_M_and_dots(P, W, nullptr, &W.sc.p->done);
-  finish(s, FIN_RZ0, W.partA.p, red_blocks(n), nullptr, 0, W.sc.p);
+  apply_M_and_dots(P, W, nullptr, &W.sc.p->done, false);  // + FIN_RZ0
   copy_f64(s, W.z.p, W.p.p, n, &W.sc.p->done);
 }
 
@@ -752,7 +804,11 @@ void start_rhs(tomg_problem* P, Work& W, int j, const double* f, const double* u
   CK(cudaMemcpyAsync(W.t.p, u + (int64_t)j * n, n * 8, h2d, s));
   mask_vec(s, W.f.p, W.bvec.p, P->mask.p, P->dim, P->nn);
   mask_vec(s, W.t.p, W.x.p, P->mask.p, P->dim, P->nn);
-  if (!W.gexec && P->opt.use_graph > 0) build_graph(P, W);
+  if (!W.gexec && P->opt.use_graph > 0) {
+    SetupTrace tr(W.stream);
+    build_graph(P, W);
+    tr.mark("graph build");
+  }
   launch_attempt(P, W, P->opt.max_iter);
 }
 
@@ -859,12 +915,21 @@ void level_apply(tomg_problem* P, int level, int prec, const double* x, double* 
   CK(cudaStreamSynchronize(s));
 }
 
+void outer_operator_apply(tomg_problem* P, const double* x, double* y) {
+  if (!P->setup_valid) TOMG_THROW(TOMG_E_INVALID, "no valid setup");
+  cudaStream_t s = st(P);
+  fine64_apply_dot(P, s, x, y, nullptr, nullptr, nullptr);
+  CK(cudaStreamSynchronize(s));
+}
+
 void vcycle_apply(tomg_problem* P, const double* r, double* z) {
   if (!P->setup_valid) TOMG_THROW(TOMG_E_INVALID, "no valid setup");
   Work& W = ensure_work(P, 0);
   fork_to(P, W);
   CK(cudaMemcpyAsync(W.r.p, r, P->n * 8, cudaMemcpyDeviceToDevice, W.stream));
-  apply_M_and_dots(P, W, nullptr, nullptr);
+  // fresh scalar state: the z.r reduction then runs (and is discarded) like at a solve start
+  CK(cudaMemsetAsync(W.sc.p, 0, sizeof(Scalars), W.stream));
+  apply_M_and_dots(P, W, nullptr, nullptr, false);
   CK(cudaMemcpyAsync(z, W.z.p, P->n * 8, cudaMemcpyDeviceToDevice, W.stream));
   join_from(P, W);
   CK(cudaStreamSynchronize(st(P)));
@@ -939,7 +1004,7 @@ void prolong_export(tomg_problem* P, int level, int64_t* nnzb, int64_t* hrp, int
 
 double time_fine_operator(tomg_problem* P, int op, int prec, int reps, int cold_l2) {
   if (!P->setup_valid) TOMG_THROW(TOMG_E_INVALID, "no valid setup");
-  if (op < 0 || op > 2 || reps < 1 || reps > 10000) TOMG_THROW(TOMG_E_INVALID, "bad timing request");
+  if (op < 0 || op > 3 || reps < 1 || reps > 10000) TOMG_THROW(TOMG_E_INVALID, "bad timing request");
   cudaStream_t s = st(P);
   Work& W = ensure_work(P, 0);
   LevelWork& l0 = W.lw[0];
@@ -951,7 +1016,8 @@ double time_fine_operator(tomg_problem* P, int op, int prec, int reps, int cold_
   for (int k = 0; k < reps; k++) {
     if (cold_l2) CK(cudaMemsetAsync(flush.p, k & 0xff, flush.n, s));
     CK(cudaEventRecord(ev[2 * k], s));
-    if (prec == TOMG_PREC_FP64) level_op<double>(P, s, 0, mode, l0.x64.p, l0.y64.p, l0.b64.p, nullptr);
+    if (op == 3) fine64_apply_dot(P, s, W.p.p, W.q.p, nullptr, W.partA.p, nullptr);
+    else if (prec == TOMG_PREC_FP64) level_op<double>(P, s, 0, mode, l0.x64.p, l0.y64.p, l0.b64.p, nullptr);
     else level_op<float>(P, s, 0, mode, l0.x32.p, l0.y32.p, l0.b32.p, nullptr);
     CK(cudaEventRecord(ev[2 * k + 1], s));
   }

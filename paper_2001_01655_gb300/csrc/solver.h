@@ -94,6 +94,8 @@ struct Work {
   cudaGraph_t graph = nullptr;
   cudaGraphExec_t gexec = nullptr;
   int graph_mode = 0;  // 0 none, 1 one-iteration graph, 2 conditional while loop
+  cudaGraphConditionalHandle cond = 0;  // while condition, set while capturing mode 2
+  int has_cond = 0;
   int64_t kernels_per_iter = 0;
   cudaEvent_t ev0 = nullptr, ev1 = nullptr, evdone = nullptr, evsync = nullptr;
   // per right-hand side bookkeeping while a solve is in flight
@@ -114,6 +116,7 @@ struct tomg_problem {
   double E0 = 1, Emin = 1e-9, penal = 3, nu = 0.3;
   int64_t nn = 0, n = 0, nel = 0;
   std::vector<double> Ke_host;
+  int ebe_tile = 0;    // autotuned tile of the quad4 FP32 element kernel (0 = default)
   tomg::DBuf<double> Ke64;
   tomg::DBuf<float> Ke32;
   tomg::DBuf<uint8_t> mask;
@@ -154,6 +157,7 @@ tomg_status solve(tomg_problem* P, int nrhs, const double* f, double* u, int on_
                   tomg_result* res);
 // single steps for parity checks
 void level_apply(tomg_problem* P, int level, int prec, const double* x, double* y);
+void outer_operator_apply(tomg_problem* P, const double* x, double* y);
 void vcycle_apply(tomg_problem* P, const double* r, double* z);
 void coarse_apply(tomg_problem* P, const double* b, double* x);
 void level_export(tomg_problem* P, int level, int64_t* nnzb, int64_t* rp, int64_t* ci, double* v);

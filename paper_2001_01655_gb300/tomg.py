@@ -73,6 +73,7 @@ _SIGS = {
     "tomg_aggregates_export": (C.c_int, [_P, C.c_int, _P]),
     "tomg_level_apply": (C.c_int, [_P, C.c_int, C.c_int, _P, _P, C.c_int]),
     "tomg_vcycle": (C.c_int, [_P, _P, _P, C.c_int]),
+    "tomg_outer_apply": (C.c_int, [_P, _P, _P, C.c_int]),
     "tomg_coarse_solve": (C.c_int, [_P, _P, _P, C.c_int]),
     "tomg_moduli": (C.c_int, [_P, _P, C.c_int]),
     "tomg_element_stiffness": (C.c_int, [_P, _P]),
@@ -295,6 +296,10 @@ class Problem:
         li = self.level_info(level)
         return self._vec_call(load().tomg_level_apply, x, li["n_dofs"], level, PREC.get(prec, prec))
 
+    def outer_apply(self, x):
+        """y = K x as the outer Krylov loop of the current setup computes it."""
+        return self._vec_call(load().tomg_outer_apply, x, self.n)
+
     def vcycle(self, r):
         return self._vec_call(load().tomg_vcycle, r, self.n)
 
@@ -320,7 +325,7 @@ class Problem:
     def time_fine_operator(self, op="apply", prec="fp32", reps=50, cold_l2=True):
         """Mean device time (ms) of one launch of the level-0 operator kernel."""
         ms = C.c_double()
-        opi = {"apply": 0, "residual": 1, "jacobi": 2}[op]
+        opi = {"apply": 0, "residual": 1, "jacobi": 2, "outer": 3}[op]
         _check(load().tomg_time_fine_operator(self.h, opi, PREC.get(prec, prec), reps,
                                               1 if cold_l2 else 0, C.byref(ms)))
         return ms.value

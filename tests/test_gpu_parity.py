@@ -58,6 +58,27 @@ def test_fine_operator_apply(lib, ctx, dim, grid, prec):
     assert np.all(np.abs(y - ref) <= tol * scale + 1e-300)
 
 
+@pytest.mark.parametrize("dim,grid", GRIDS + [(2, (95, 40, 1)), (3, (40, 9, 6))])
+@pytest.mark.parametrize("prec", ["fp32", "fp64"])
+def test_outer_operator_apply(lib, ctx, dim, grid, prec):
+    """The outer loop's FP64 K (the assembled fine stencil, in both precisions' setups).  Bound:
+    1e-13 of the summed element-product magnitudes sum_e E_e |Ke| |x| (FP64 rounding of the
+    assembly and of the 9 / 27 block products), on a 1e9-contrast density and x spanning 12
+    decades."""
+    p = W.random_problem(dim, *grid, seed=21, contrast="threshold")
+    P = make(lib, ctx, p)
+    P.setup(pc="gmg", prec=prec)
+    A0 = mg.fine_operator(p)
+    E = fem.simp(p.rho, p.E0, p.Emin, p.penal)
+    Kabs = fem.masked_operator(abs(fem.assemble(dim, p.nx, p.ny, p.nz, E,
+                                                np.abs(fem.element_stiffness(dim, p.nu)))), p.fixed)
+    rng = np.random.default_rng(5)
+    for x in (rng.standard_normal(p.n), rng.standard_normal(p.n) * 10.0 ** rng.uniform(-6, 6, p.n)):
+        y = P.outer_apply(x)
+        scale = Kabs @ np.abs(x)
+        assert np.all(np.abs(y - A0 @ x) <= 1e-13 * scale + 1e-300)
+
+
 @pytest.mark.parametrize("dim,grid,L", [(2, (37, 23, 1), 4), (2, (20, 10, 1), 3),
                                          (3, (9, 7, 5), 3), (3, (8, 8, 8), 3)])
 def test_gmg_hierarchy(lib, ctx, dim, grid, L):
