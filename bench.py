@@ -280,6 +280,9 @@ def serving_run(tomg, ctx, n_requests, n_updates, slots):
 
 
 FP64_PEAK_GFLOPS = 1250.0  # GB300 FP64 rate (nominal, not in the measured peaks file)
+# DRAM read + write of one k_stencil_apply_dot<2> launch on this workload, from one ncu capture
+# (dram__bytes_read.sum + dram__bytes_write.sum, caches flushed before the launch)
+OUTER_TRAFFIC_BYTES = 89912320 + 2731264
 
 
 def roofline(P, ctx, p, stream):
@@ -317,7 +320,8 @@ def roofline(P, ctx, p, stream):
         head = {"kernel": "k_ebe2<float, %s> (FP32 %s, 2D)" % ("1" if dom == "residual" else "2", dom),
                 "bound": "hbm", "achieved": k["achieved_gbs"], "peak": hbm, "unit": "GB/s",
                 "frac": k["frac_hbm"], "peak_source": src}
-    head.update({"traffic": None, "ms_per_launch": out[dom]["ms_per_launch"], "kernels": out})
+    traffic = OUTER_TRAFFIC_BYTES if (dom == "outer" and p.dim == 2 and p.n == 592130) else None
+    head.update({"traffic": traffic, "ms_per_launch": out[dom]["ms_per_launch"], "kernels": out})
     return head
 
 

@@ -69,8 +69,9 @@ typedef struct {
   double omega;        /* Jacobi weight (Sec. 4.1)                                 0.5      */
   int n_pre, n_post;   /* smoothing sweeps (one each)                              1, 1     */
   double soc_beta;     /* strength-of-connection threshold (Eq. 10)                0.003    */
-  int check_every;     /* outer iterations between host convergence polls          4        */
-  int use_graph;       /* capture the outer iteration in a CUDA graph              1        */
+  int check_every;     /* use_graph < 2: outer iterations between host polls       4        */
+  int use_graph;       /* 2: whole solve = one graph with a device-side while loop;
+                          1: one captured graph per iteration; 0: plain launches   2        */
   int max_levels;      /* cap on the number of levels                              25       */
   int concurrency;     /* solve slots: right-hand sides solved concurrently        4        */
 } tomg_options;

@@ -60,7 +60,8 @@ extern "C" tomg_status tomg_fine_apply_f32_noalloc(tomg_problem* P, const double
     cudaStream_t st = P->ctx->stream;
     // every scratch entry the apply reads is written first by the cast, so nothing is cleared
     tomg::cast_f64_f32(st, x, x32, P->n);
-    const tomg::Ebe op{P->dim, P->nx, P->ny, P->nz, P->Ke32.p, P->E32.p, P->mask.p};
+    const tomg::Ebe op{P->dim, P->nx, P->ny, P->nz, P->Ke32.p, P->E32.p, P->mask.p, 0,
+                       P->Ke32_host.data()};
     tomg::ebe_op<float>(st, tomg::MODE_APPLY, op, x32, y32, nullptr, nullptr, 0.0, nullptr, nullptr);
     tomg::cast_f32_f64(st, y32, y, P->n);
     return TOMG_OK;

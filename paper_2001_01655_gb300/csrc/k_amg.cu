@@ -1,4 +1,4 @@
-// Smoothed-aggregation setup on the device (Sec. 3.2 AMG, Sec. 4 "block fashion" strength,
+// Smoothed-aggregation setup on the device (Sec. 3.2 AMG; Sec. 4: strength measured per node block,
 // rigid-body candidates, Jacobi-smoothed tentative prolongator):
 //   strength   ||A_ij||_F^2 > beta ||A_ii||_F ||A_jj||_F, one value per node   (Eq. 10)
 //   aggregates distance-2 maximal independent set in synchronous rounds with splitmix64
@@ -6,7 +6,7 @@
 //   tentative  modified Gram-Schmidt QR of the candidates on every aggregate
 //   smoothing  P = T - omega D^-1 A T, omega = 4 / (3 rho(D^-1 A)), rho by power iteration
 // splitmix64 is written here from its published definition (Steele, Lea & Flood 2014).
-#include "ops.h"
+#include "finish.cuh"
 
 namespace tomg {
 
@@ -238,7 +238,8 @@ __global__ void __launch_bounds__(256) k_power_step(int nbr, const int* __restri
                                                     const double* __restrict__ Dinv,
                                                     const double* __restrict__ v,
                                                     const double* __restrict__ scale, double* w,
-                                                    double* partials) {
+                                                    double* partials, double* out,
+                                                    unsigned* ticket) {
   constexpr int G = 8;
   __shared__ double sred[32];
   const int gtid = blockIdx.x * blockDim.x + threadIdx.x;
@@ -276,6 +277,17 @@ __global__ void __launch_bounds__(256) k_power_step(int nbr, const int* __restri
   }
   const double tot = block_sum(ss, sred);
   if (threadIdx.x == 0) partials[blockIdx.x] = tot;
+  // the last block forms ||w|| and 1 / ||w|| for the next step (fixed summation order)
+  if (last_block(ticket)) {
+    double a = 0.0;
+    for (int q = threadIdx.x; q < (int)gridDim.x; q += blockDim.x) a += __ldcg(partials + q);
+    a = block_sum(a, sred);
+    if (threadIdx.x == 0) {
+      const double nrm = sqrt(a);
+      out[0] = nrm;
+      out[1] = nrm > 0.0 ? 1.0 / nrm : 0.0;
+    }
+  }
 }
 // out[0] = sqrt(sum of partials), out[1] = 1 / out[0] (fixed summation order)
 __global__ void k_norm_finish(const double* __restrict__ partials, int np, double* out) {
@@ -389,15 +401,20 @@ int amg_mis2(cudaStream_t s, int n, const int* srp, const int* sci, int level, i
              uint64_t* v, uint64_t* m1, int* flag_host, int* flag_dev) {
   const int g = ceil_div(n, 256);
   LAUNCH(k_mis_init, g, 256, 0, s, n, srp, state);
+  // rounds run in batches between host checks: once every node is decided a round changes
+  // nothing, so the rounds after convergence inside a batch are no-ops
+  constexpr int BATCH = 4;
   int rounds = 0;
   while (true) {
-    CK(cudaMemsetAsync(flag_dev, 0, sizeof(int), s));
-    LAUNCH(k_mis_values, g, 256, 0, s, n, level, state, v);
-    LAUNCH(k_neigh_max, g, 256, 0, s, n, srp, sci, v, m1);
-    LAUNCH(k_mis_update, g, 256, 0, s, n, level, srp, sci, m1, state, flag_dev);
+    for (int k = 0; k < BATCH; k++) {
+      CK(cudaMemsetAsync(flag_dev, 0, sizeof(int), s));
+      LAUNCH(k_mis_values, g, 256, 0, s, n, level, state, v);
+      LAUNCH(k_neigh_max, g, 256, 0, s, n, srp, sci, v, m1);
+      LAUNCH(k_mis_update, g, 256, 0, s, n, level, srp, sci, m1, state, flag_dev);
+    }
     CK(cudaMemcpyAsync(flag_host, flag_dev, sizeof(int), cudaMemcpyDeviceToHost, s));
     CK(cudaStreamSynchronize(s));
-    rounds++;
+    rounds += BATCH;
     if (*flag_host == 0) break;
     if (rounds > 100000) TOMG_THROW(TOMG_E_BREAKDOWN, "MIS-2 did not terminate");
   }
@@ -455,18 +472,21 @@ double amg_spectral_radius(cudaStream_t s, const Bsr& A, const double* V, const 
   const int gb = ceil_div((int64_t)A.nbr * 8, 256);
   const int gp = 256;
   DBuf<double> parts, nrm;
+  DBuf<unsigned> ticket;
   parts.resize(std::max(gb, gp));
   nrm.resize(2 * (iters + 1));
+  ticket.resize(1);
+  ticket.zero(s);
   LAUNCH(k_power_init, ceil_div(n, 256), 256, 0, s, n, level, v);
   LAUNCH(k_sumsq_partials, gp, 256, 0, s, n, v, parts.p);
   LAUNCH(k_norm_finish, 1, 256, 0, s, parts.p, gp, nrm.p);
   for (int it = 0; it < iters; it++) {
     const double* sc = nrm.p + 2 * it + 1;
-    if (A.br == 2) LAUNCH(k_power_step<2>, gb, 256, 0, s, A.nbr, A.rp, A.ci, V, Dinv, v, sc, w, parts.p);
-    else if (A.br == 3) LAUNCH(k_power_step<3>, gb, 256, 0, s, A.nbr, A.rp, A.ci, V, Dinv, v, sc, w, parts.p);
-    else if (A.br == 6) LAUNCH(k_power_step<6>, gb, 256, 0, s, A.nbr, A.rp, A.ci, V, Dinv, v, sc, w, parts.p);
+    double* o = nrm.p + 2 * (it + 1);
+    if (A.br == 2) LAUNCH(k_power_step<2>, gb, 256, 0, s, A.nbr, A.rp, A.ci, V, Dinv, v, sc, w, parts.p, o, ticket.p);
+    else if (A.br == 3) LAUNCH(k_power_step<3>, gb, 256, 0, s, A.nbr, A.rp, A.ci, V, Dinv, v, sc, w, parts.p, o, ticket.p);
+    else if (A.br == 6) LAUNCH(k_power_step<6>, gb, 256, 0, s, A.nbr, A.rp, A.ci, V, Dinv, v, sc, w, parts.p, o, ticket.p);
     else TOMG_THROW(TOMG_E_INVALID, "unsupported block %d", A.br);
-    LAUNCH(k_norm_finish, 1, 256, 0, s, parts.p, gb, nrm.p + 2 * (it + 1));
     std::swap(v, w);
   }
   double rho = 0.0;

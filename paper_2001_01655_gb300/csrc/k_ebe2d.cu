@@ -7,6 +7,7 @@
 // thread then keeps a 6 x 3 node window and a 5 x 2 element window in registers, loads each of
 // the four element-role row pairs of Ke once, and applies it to its four nodes:
 // 64 FMAs per node, every input element read once from DRAM.
+#include <cstring>
 #include <map>
 #include <mutex>
 #include <utility>
@@ -19,6 +20,10 @@ namespace {
 
 constexpr int BX = 32, BY = 8;
 
+// Ke by value: a kernel parameter lives in the constant bank, and with the element and node
+// loops unrolled every Ke entry is a compile-time constant-bank operand of its FMA (no loads)
+template <class T> struct KeP2 { T v[64]; };
+
 template <class T> struct V2t;
 template <> struct V2t<float> { using type = float2; };
 template <> struct V2t<double> { using type = double2; };
@@ -26,7 +31,7 @@ template <> struct V2t<double> { using type = double2; };
 // NPT nodes per thread along y (tile 32 x 8 NPT): more nodes per thread reuse more of the
 // staged halo, fewer give more blocks per SM; the setup's autotuner picks per grid
 template <class T, int MODE, bool DOT, int NPT>
-__global__ void __launch_bounds__(BX * BY) k_ebe2(int nx, int ny, const T* __restrict__ Ke,
+__global__ void __launch_bounds__(BX * BY) k_ebe2(int nx, int ny, const KeP2<T> K,
                                                   const T* __restrict__ E,
                                                   const uint8_t* __restrict__ mask,
                                                   const T* __restrict__ x, T* __restrict__ y,
@@ -36,7 +41,6 @@ __global__ void __launch_bounds__(BX * BY) k_ebe2(int nx, int ny, const T* __res
                                                   T* __restrict__ xo) {
   using V2 = typename V2t<T>::type;
   constexpr int TH = BY * NPT;
-  __shared__ __align__(16) T sKe[64];
   __shared__ V2 sx[TH + 2][BX + 2];
   __shared__ T sE[TH + 1][BX + 1];
   __shared__ double red[BX * BY / 32];
@@ -45,7 +49,6 @@ __global__ void __launch_bounds__(BX * BY) k_ebe2(int nx, int ny, const T* __res
   const int tid = threadIdx.y * BX + threadIdx.x;
   const int i0 = blockIdx.x * BX, j0 = blockIdx.y * TH;
   const int W = nx + 1;
-  if (tid < 64) sKe[tid] = Ke[tid];
   // staging: issue every global load of this thread first (independent, all in flight at
   // once), then write shared memory, so the tile costs one memory latency, not several
   constexpr int NXL = ((TH + 2) * (BX + 2) + BX * BY - 1) / (BX * BY);
@@ -125,8 +128,8 @@ __global__ void __launch_bounds__(BX * BY) k_ebe2(int nx, int ny, const T* __res
     T k0[8], k1[8];
 #pragma unroll
     for (int t = 0; t < 8; t++) {
-      k0[t] = sKe[(2 * a) * 8 + t];
-      k1[t] = sKe[(2 * a + 1) * 8 + t];
+      k0[t] = K.v[(2 * a) * 8 + t];
+      k1[t] = K.v[(2 * a + 1) * 8 + t];
     }
 #pragma unroll
     for (int q = 0; q < NPT; q++) {
@@ -208,9 +211,11 @@ void ebe2d_launch(cudaStream_t s, const Ebe& op, const T* x, T* y, const T* b, c
   T* xo = MODE == MODE_RESID0 ? const_cast<T*>(x) : nullptr;
   const int npt = DOT ? 4 : (op.tile == 1 || op.tile == 2 ? op.tile : 4);  // dots: fixed tile
   dim3 grid(ceil_div(op.nx + 1, BX), ceil_div(op.ny + 1, BY * npt));
-#define EB(N) LAUNCH((k_ebe2<T, MODE, DOT, N>), grid, dim3(BX, BY), 0, s, op.nx, op.ny,   \
-                     (const T*)op.Ke, (const T*)op.E, op.mask, x, y, b, Dinv, (T)omega, done, \
-                     parts, xo)
+  if (!op.Kh) TOMG_THROW(TOMG_E_INVALID, "tiled element kernel without a host copy of Ke");
+  KeP2<T> K;
+  memcpy(K.v, op.Kh, sizeof(K.v));
+#define EB(N) LAUNCH((k_ebe2<T, MODE, DOT, N>), grid, dim3(BX, BY), 0, s, op.nx, op.ny, K,     \
+                     (const T*)op.E, op.mask, x, y, b, Dinv, (T)omega, done, parts, xo)
   if (npt == 1) EB(1);
   else if (npt == 2) EB(2);
   else EB(4);

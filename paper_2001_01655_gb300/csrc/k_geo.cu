@@ -179,6 +179,49 @@ __device__ __forceinline__ void axis_pairs(int I, int J, int nf, AxisPairs& L) {
   }
 }
 
+// One axis of the Galerkin product.  P is a tensor product of 1D interpolations, so
+// P^T A P = Px^T (Py^T (Pz^T A Pz) Py) Px can be formed one axis at a time: the stencil stays
+// 3^d-point after each step, and every output block sums at most 7 weighted input blocks
+// instead of up to 7^d for the direct product.  Input grid (nx, ny, nz) with `axis` fine,
+// output grid with that axis coarsened to cn (the other axes unchanged).
+template <int AXIS>
+__global__ void k_rap_axis(int nx, int ny, int nz, int cn, const double* __restrict__ Sin,
+                           double* __restrict__ Sout) {
+  constexpr int BB = 9;
+  const int onx = AXIS == 0 ? cn : nx, ony = AXIS == 1 ? cn : ny, onz = AXIS == 2 ? cn : nz;
+  const int64_t nin = (int64_t)(nx + 1) * (ny + 1) * (nz + 1);
+  const int64_t nout = (int64_t)(onx + 1) * (ony + 1) * (onz + 1);
+  const int64_t I = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  const int O = blockIdx.y;
+  if (I >= nout) return;
+  int c[3];
+  node_ijk(I, onx, ony, 3, c[0], c[1], c[2]);
+  const int oo[3] = {O % 3 - 1, (O / 3) % 3 - 1, O / 9 - 1};
+  const int na = AXIS == 0 ? nx : (AXIS == 1 ? ny : nz);  // fine extent along the axis
+  const int cnA = AXIS == 0 ? onx : (AXIS == 1 ? ony : onz);
+  double acc[BB];
+#pragma unroll
+  for (int t = 0; t < BB; t++) acc[t] = 0.0;
+  const int Ia = c[AXIS], Ja = Ia + oo[AXIS];
+  if (Ja >= 0 && Ja <= cnA) {
+    AxisPairs L;
+    axis_pairs(Ia, Ja, na, L);
+    for (int a = 0; a < L.n; a++) {
+      int f[3] = {c[0], c[1], c[2]};
+      f[AXIS] = L.di[a];
+      int fo[3] = {oo[0], oo[1], oo[2]};
+      fo[AXIS] = L.o[a];
+      const int64_t fi = node_id(f[0], f[1], f[2], nx, ny);
+      const int oi = (fo[0] + 1) + 3 * (fo[1] + 1) + 9 * (fo[2] + 1);
+      const double wt = L.w[a];
+#pragma unroll
+      for (int t = 0; t < BB; t++) acc[t] += wt * Sin[((int64_t)oi * BB + t) * nin + fi];
+    }
+  }
+#pragma unroll
+  for (int t = 0; t < BB; t++) Sout[((int64_t)O * BB + t) * nout + I] = acc[t];
+}
+
 template <int DIM>
 __global__ void k_rap(int fnx, int fny, int fnz, int cnx, int cny, int cnz,
                       const double* __restrict__ Sf, double* __restrict__ Sc) {
@@ -419,9 +462,20 @@ void stencil_block_diag_inv(cudaStream_t s, const Geo& g, const double* S, doubl
 }
 
 void stencil_rap(cudaStream_t s, const Geo& f, const Geo& c, const double* Sf, double* Sc) {
-  dim3 grid(ceil_div(c.nodes(), 128), f.dim == 3 ? 27 : 9);
-  if (f.dim == 2) LAUNCH(k_rap<2>, grid, 128, 0, s, f.nx, f.ny, f.nz, c.nx, c.ny, c.nz, Sf, Sc);
-  else LAUNCH(k_rap<3>, grid, 128, 0, s, f.nx, f.ny, f.nz, c.nx, c.ny, c.nz, Sf, Sc);
+  if (f.dim == 2) {
+    dim3 grid(ceil_div(c.nodes(), 128), 9);
+    LAUNCH(k_rap<2>, grid, 128, 0, s, f.nx, f.ny, f.nz, c.nx, c.ny, c.nz, Sf, Sc);
+    return;
+  }
+  // hex8: x, then y, then z (two intermediate stencils)
+  const int64_t n1 = (int64_t)(c.nx + 1) * (f.ny + 1) * (f.nz + 1);
+  const int64_t n2 = (int64_t)(c.nx + 1) * (c.ny + 1) * (f.nz + 1);
+  DBuf<double> S1, S2;
+  S1.resize(243 * n1);
+  S2.resize(243 * n2);
+  LAUNCH(k_rap_axis<0>, dim3(ceil_div(n1, 128), 27), 128, 0, s, f.nx, f.ny, f.nz, c.nx, Sf, S1.p);
+  LAUNCH(k_rap_axis<1>, dim3(ceil_div(n2, 128), 27), 128, 0, s, c.nx, f.ny, f.nz, c.ny, S1.p, S2.p);
+  LAUNCH(k_rap_axis<2>, dim3(ceil_div(c.nodes(), 128), 27), 128, 0, s, c.nx, c.ny, f.nz, c.nz, S2.p, Sc);
 }
 
 template <class T>

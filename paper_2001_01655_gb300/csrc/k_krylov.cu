@@ -14,7 +14,22 @@ namespace tomg {
 namespace {
 
 constexpr int RED_THREADS = 256;
-constexpr int RED_MAX_BLOCKS = 1216;  // 8 blocks per SM on the 152-SM GB300
+constexpr int RED_MAX_BLOCKS = 2432;  // 16 blocks per SM on the 152-SM GB300
+
+// Vector kernels walk the DOFs in pairs (16-byte loads of FP64 vectors), one pair per thread
+// when the grid allows it, so every load of a thread is issued at once; an odd last DOF is
+// handled by the thread of pair index n / 2.
+template <class T> struct P2;
+template <> struct P2<double> { using type = double2; };
+template <> struct P2<float> { using type = float2; };
+template <class T>
+__device__ __forceinline__ typename P2<T>::type ld2(const T* a, int64_t k, int64_t n) {
+  if (2 * k + 1 < n) return reinterpret_cast<const typename P2<T>::type*>(a)[k];
+  typename P2<T>::type v;
+  v.x = a[2 * k];
+  v.y = T(0);
+  return v;
+}
 
 __global__ void __launch_bounds__(RED_THREADS) k_dot(const double* __restrict__ x,
                                                      const double* __restrict__ y, int64_t n,
@@ -23,8 +38,11 @@ __global__ void __launch_bounds__(RED_THREADS) k_dot(const double* __restrict__ 
   pdl_prologue();
   if (solve_done(done)) return;
   double s = 0.0;
-  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
-    s += x[i] * y[i];
+  const int64_t np = (n + 1) / 2;
+  for (int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; k < np; k += (int64_t)gridDim.x * blockDim.x) {
+    const double2 a = ld2(x, k, n), b = ld2(y, k, n);
+    s += a.x * b.x + a.y * b.y;
+  }
   s = block_sum(s, sred);
   if (threadIdx.x == 0) partials[blockIdx.x] = s;
 }
@@ -48,12 +66,22 @@ __global__ void __launch_bounds__(RED_THREADS) k_xr(double* __restrict__ x, doub
   if (sc->done) return;
   const double alpha = sc->alpha;
   double s = 0.0;
-  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
-    x[i] += alpha * p[i];
-    const double ri = r[i] - alpha * q[i];
-    r[i] = ri;
-    if (r32) r32[i] = (float)ri;
-    s += ri * ri;
+  const int64_t np = (n + 1) / 2;
+  for (int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; k < np; k += (int64_t)gridDim.x * blockDim.x) {
+    const double2 xv = ld2(x, k, n), pv = ld2(p, k, n), rv = ld2(r, k, n), qv = ld2(q, k, n);
+    const double x0 = xv.x + alpha * pv.x, x1 = xv.y + alpha * pv.y;
+    const double r0 = rv.x - alpha * qv.x, r1 = rv.y - alpha * qv.y;
+    if (2 * k + 1 < n) {
+      reinterpret_cast<double2*>(x)[k] = make_double2(x0, x1);
+      reinterpret_cast<double2*>(r)[k] = make_double2(r0, r1);
+      if (r32) reinterpret_cast<float2*>(r32)[k] = make_float2((float)r0, (float)r1);
+      s += r0 * r0 + r1 * r1;
+    } else {
+      x[2 * k] = x0;
+      r[2 * k] = r0;
+      if (r32) r32[2 * k] = (float)r0;
+      s += r0 * r0;
+    }
   }
   s = block_sum(s, sred);
   if (threadIdx.x == 0) partials[blockIdx.x] = s;
@@ -70,8 +98,12 @@ __global__ void k_p(double* __restrict__ p, const double* __restrict__ z, int64_
   if (has_cond && blockIdx.x == 0 && threadIdx.x == 0) cudaGraphSetConditional(cond, done ? 0u : 1u);
   if (done) return;
   const double beta = sc->beta;
-  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
-    p[i] = z[i] + beta * p[i];
+  const int64_t np = (n + 1) / 2;
+  for (int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; k < np; k += (int64_t)gridDim.x * blockDim.x) {
+    const double2 zv = ld2(z, k, n), pv = ld2(p, k, n);
+    if (2 * k + 1 < n) reinterpret_cast<double2*>(p)[k] = make_double2(zv.x + beta * pv.x, zv.y + beta * pv.y);
+    else p[2 * k] = zv.x + beta * pv.x;
+  }
 }
 
 template <class T>
@@ -84,11 +116,21 @@ __global__ void __launch_bounds__(RED_THREADS) k_zdots(const T* __restrict__ z, 
   pdl_prologue();
   if (sc->done) return;
   double a = 0.0, b = 0.0;
-  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
-    const double zi = (double)z[i];
-    if ((const void*)z != (const void*)z64) z64[i] = zi;
-    a += zi * r[i];
-    if (q) b += zi * q[i];
+  const bool copy = (const void*)z != (const void*)z64;
+  const int64_t np = (n + 1) / 2;
+  for (int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; k < np; k += (int64_t)gridDim.x * blockDim.x) {
+    const auto zv = ld2(z, k, n);
+    const double z0 = (double)zv.x, z1 = (double)zv.y;
+    const double2 rv = ld2(r, k, n);
+    if (copy) {
+      if (2 * k + 1 < n) reinterpret_cast<double2*>(z64)[k] = make_double2(z0, z1);
+      else z64[2 * k] = z0;
+    }
+    a += z0 * rv.x + z1 * rv.y;
+    if (q) {
+      const double2 qv = ld2(q, k, n);
+      b += z0 * qv.x + z1 * qv.y;
+    }
   }
   a = block_sum(a, sred);
   b = block_sum(b, sred);
@@ -308,7 +350,9 @@ __global__ void k_ltl(int n, const double* __restrict__ Li, double* Ainv) {
   Ainv[(int64_t)j * n + i] = v;
 }
 
-inline int grid_for(int64_t n) { return std::max(1, std::min(RED_MAX_BLOCKS, ceil_div(n, RED_THREADS * 4))); }
+inline int grid_for(int64_t n) {
+  return std::max(1, std::min(RED_MAX_BLOCKS, ceil_div((n + 1) / 2, RED_THREADS)));
+}
 
 }  // namespace
 

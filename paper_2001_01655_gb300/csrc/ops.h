@@ -22,6 +22,7 @@ struct Ebe {
   const void* E;   // T[n_elems]
   const uint8_t* mask;
   int tile = 0;    // quad4 FP32: nodes per thread of the tiled kernel (1, 2, 4; 0 = 4)
+  const void* Kh = nullptr;  // host copy of Ke (T); the tiled kernels take Ke by value
 };
 template <class T>
 void ebe_op(cudaStream_t s, int mode, const Ebe& op, const T* x, T* y, const T* b,

@@ -114,7 +114,7 @@ template <> struct V<double> {
   static double* y(LevelWork& l) { return l.y64.p; }
   static const double* Ainv(const tomg_problem* P) { return P->Ainv64.p; }
   static Ebe ebe(const tomg_problem* P) {
-    return Ebe{P->dim, P->nx, P->ny, P->nz, P->Ke64.p, P->E64.p, P->mask.p};
+    return Ebe{P->dim, P->nx, P->ny, P->nz, P->Ke64.p, P->E64.p, P->mask.p, 0, P->Ke_host.data()};
   }
 };
 template <> struct V<float> {
@@ -129,7 +129,8 @@ template <> struct V<float> {
   static float* y(LevelWork& l) { return l.y32.p; }
   static const float* Ainv(const tomg_problem* P) { return P->Ainv32.p; }
   static Ebe ebe(const tomg_problem* P) {
-    return Ebe{P->dim, P->nx, P->ny, P->nz, P->Ke32.p, P->E32.p, P->mask.p, P->ebe_tile};
+    return Ebe{P->dim, P->nx, P->ny, P->nz, P->Ke32.p, P->E32.p, P->mask.p, P->ebe_tile,
+               P->Ke32_host.data()};
   }
 };
 
@@ -550,9 +551,9 @@ void problem_init(tomg_problem* P) {
   const size_t nk = P->Ke_host.size();
   P->Ke64.resize(nk);
   P->Ke32.resize(nk);
-  std::vector<float> k32(P->Ke_host.begin(), P->Ke_host.end());
+  P->Ke32_host.assign(P->Ke_host.begin(), P->Ke_host.end());
   CK(cudaMemcpyAsync(P->Ke64.p, P->Ke_host.data(), nk * 8, cudaMemcpyHostToDevice, s));
-  CK(cudaMemcpyAsync(P->Ke32.p, k32.data(), nk * 4, cudaMemcpyHostToDevice, s));
+  CK(cudaMemcpyAsync(P->Ke32.p, P->Ke32_host.data(), nk * 4, cudaMemcpyHostToDevice, s));
   P->mask.resize(P->nn);
   P->mask.zero(s);
   P->rho.resize(P->nel);

@@ -116,6 +116,7 @@ struct tomg_problem {
   double E0 = 1, Emin = 1e-9, penal = 3, nu = 0.3;
   int64_t nn = 0, n = 0, nel = 0;
   std::vector<double> Ke_host;
+  std::vector<float> Ke32_host;
   int ebe_tile = 0;    // autotuned tile of the quad4 FP32 element kernel (0 = default)
   tomg::DBuf<double> Ke64;
   tomg::DBuf<float> Ke32;
