@@ -226,3 +226,20 @@ def test_numbering_conventions():
     e = 1 + 2 * (2 + 3 * 3)
     node = 2 + 3 * (3 + 4 * 4)
     assert list(dofs[e, 21:24]) == [3 * node, 3 * node + 1, 3 * node + 2]
+
+
+@pytest.mark.parametrize("dim,grid", [(2, (7, 5, 1)), (2, (1, 1, 1)), (3, (4, 3, 5)), (3, (1, 2, 1))])
+def test_masked_apply_rows_matches_assembled(dim, grid):
+    """The element-local row evaluation used for full-size checks equals the assembled masked
+    operator on every node (corners, edges, faces and interior; fixed and free DOFs)."""
+    nx, ny, nz = grid
+    rng = np.random.default_rng(3)
+    nn, nel, n = fem.grid_counts(dim, nx, ny, nz)
+    E = 10.0 ** rng.uniform(-9, 0, nel)
+    Ke = fem.element_stiffness(dim, 0.3)
+    fixed = rng.choice(n, size=max(1, n // 5), replace=False)
+    A = fem.masked_operator(fem.assemble(dim, nx, ny, nz, E, Ke), fixed)
+    x = rng.standard_normal(n)
+    rows = fem.masked_apply_rows(dim, nx, ny, nz, E, Ke, fixed, x, np.arange(nn))
+    ref = (A @ x).reshape(nn, dim)
+    assert np.abs(rows - ref).max() <= 1e-13 * np.abs(ref).max()
