@@ -48,6 +48,8 @@ def parse():
                     help="requests of the mixed-size serving stream replayed after the main "
                          "measurement (0: skip)")
     ap.add_argument("--serving-updates", type=int, default=2)
+    ap.add_argument("--batched", type=int, default=1,
+                    help="also time the 16 right-hand sides of the 3D 128x64x64 case (0: skip)")
     ap.add_argument("--slots", type=int, default=4)
     ap.add_argument("--kernel", default=None, choices=["outer", "residual", "jacobi", "apply"],
                     help="time one level-0 operator kernel alone (for profiler captures) instead "
@@ -239,7 +241,37 @@ def run_gpu(args, rank, world, local):
     out["roofline"] = roofline(P, ctx, p, stream)
     if args.serving > 0:
         out["serving"] = serving_run(tomg, ctx, args.serving, args.serving_updates, args.slots)
+    if args.batched:
+        out["batched"] = batched_run(tomg, ctx, args.slots)
     return out
+
+
+def batched_run(tomg, ctx, slots, reps=3):
+    """The 16 right-hand sides (8 point loads, 8 adjoint-like vectors) of the 3D hex8 128x64x64
+    case (1,635,075 DOFs) on one shared hierarchy: all 16 on `slots` concurrent solve slots,
+    against the same 16 one after another (one slot).  Median of `reps` runs, setup excluded."""
+    import workloads as W
+    p = W.batched_3d()
+    P = tomg.Problem.from_workload(ctx, p)
+    res = {}
+    for conc in (slots, 1):
+        P.setup(pc="hybrid", prec="fp32", n_geo_levels=3, max_coarse_dofs=1000, rtol=1e-8,
+                concurrency=conc)
+        P.solve(p.f[:2])  # warm-up: graphs and vectors of the slots
+        times, its, worst = [], [], 0.0
+        for _ in range(reps):
+            t0 = time.perf_counter()
+            _, r = P.solve(p.f)
+            times.append(time.perf_counter() - t0)
+            its = [x["iterations"] for x in r]
+            worst = max(worst, max(x["rel_residual"] for x in r))
+        t = statistics.median(times)
+        res[conc] = {"solves_per_s": p.nrhs / t, "ms_all_rhs": 1e3 * t,
+                     "iterations_median": statistics.median(its), "rel_residual_max": worst,
+                     "setup_ms": r[0]["setup_ms"]}
+    return {"workload": "3D cantilever hex8 128x64x64 (1,635,075 DOFs), 8 point loads + 8 "
+                        "adjoint-like right-hand sides, hybrid hierarchy, FP32 V-cycle",
+            "rhs": p.nrhs, "concurrent": dict(res[slots], slots=slots), "one_at_a_time": res[1]}
 
 
 def serving_run(tomg, ctx, n_requests, n_updates, slots):
@@ -356,6 +388,15 @@ def kernel_bytes(kernel, prec, p):
     vec = {"outer": 2, "apply": 2, "residual": 3, "jacobi": 3}[kernel]
     extra = p.dim * s * nn if kernel == "jacobi" else 0  # block-diagonal inverse, dim^2 per node
     return vec * s * p.n + s * p.nel + nn + extra
+
+
+ORACLE_ITERATIONS = 211  # the oracle's FP64 PCG (hybrid, cap 1500) reaches 1e-8 here in 211 iterations
+
+
+def _cpu_seconds():
+    import resource
+    r = resource.getrusage(resource.RUSAGE_SELF)
+    return r.ru_utime + r.ru_stime
 
 
 def cpu_baseline(iters=40, warmup=0, steps=1):

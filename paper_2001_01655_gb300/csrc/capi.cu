@@ -41,6 +41,9 @@ namespace {
 
 template <class F>
 tomg_status guarded(F&& fn) {
+  // a non-sticky error left behind by another library's runtime call in this thread would
+  // otherwise surface at our first post-launch check; every call of ours is checked itself
+  (void)cudaGetLastError();
   try {
     return fn();
   } catch (const Error& e) {

@@ -2,6 +2,10 @@
 // accounting, kernel-side helpers.  Everything here is project code for sm_103a.
 #pragma once
 
+#include <chrono>
+#include <cstdio>
+#include <cstdlib>
+
 #include <cuda_runtime.h>
 #include <atomic>
 #include <stdint.h>
@@ -142,6 +146,24 @@ __device__ __forceinline__ double block_sum(double v, double* sh) {
 }
 
 // early-exit flag shared by the solve loop: kernels become no-ops once the solve is done
+// Phase timing of the setup for diagnosis (TOMG_TRACE_SETUP=1): synchronises the stream at
+// each mark and prints the host time since the previous mark to stderr.
+struct SetupTrace {
+  bool on;
+  cudaStream_t s;
+  std::chrono::steady_clock::time_point t0;
+  explicit SetupTrace(cudaStream_t st) : on(getenv("TOMG_TRACE_SETUP") != nullptr), s(st),
+                                         t0(std::chrono::steady_clock::now()) {}
+  void mark(const char* what, int level = -1) {
+    if (!on) return;
+    cudaStreamSynchronize(s);
+    const auto t = std::chrono::steady_clock::now();
+    fprintf(stderr, "[setup] %-22s L%-2d %8.3f ms\n", what, level,
+            std::chrono::duration<double, std::milli>(t - t0).count());
+    t0 = t;
+  }
+};
+
 __device__ __forceinline__ bool solve_done(const int* done) { return done && *(volatile const int*)done; }
 
 // First point-block Jacobi sweep from x = 0 at one node: x = w Dinv_node b_node (B x B blocks)

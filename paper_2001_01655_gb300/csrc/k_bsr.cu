@@ -7,6 +7,8 @@
 // columns of each output row are sorted by rank counting, so the result is canonical.
 // Numeric phase: one lane per output block, A's row walked in order and B's row searched by
 // bisection, so every block is accumulated in a fixed order (deterministic).
+#include <algorithm>
+
 #include "ops.h"
 
 namespace tomg {
@@ -270,6 +272,63 @@ __global__ void __launch_bounds__(32 * SPG_WARPS)
   }
 }
 
+// Numeric phase for long rows of A (the coarse Galerkin products): one warp per output block,
+// the lanes split A's row and their partial blocks are combined by a fixed butterfly, so the
+// work of one output block is spread over 32 lanes instead of one (still deterministic).
+template <int BR, int BK, int BC>
+__global__ void __launch_bounds__(128) k_spgemm_num_w(int nrows, int64_t nnzC,
+                                                      const int* __restrict__ Arp,
+                                                      const int* __restrict__ Aci,
+                                                      const double* __restrict__ VA,
+                                                      const int* __restrict__ Brp,
+                                                      const int* __restrict__ Bci,
+                                                      const double* __restrict__ VB,
+                                                      const int* __restrict__ Crp,
+                                                      const int* __restrict__ Cci, double* VC) {
+  const int64_t pc = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const int lane = threadIdx.x & 31;
+  if (pc >= nnzC) return;  // warp-uniform
+  int lo = 0, hi = nrows;  // the row: Crp[lo] <= pc < Crp[lo + 1]
+  while (hi - lo > 1) {
+    const int mid = (lo + hi) >> 1;
+    if (Crp[mid] <= pc) lo = mid;
+    else hi = mid;
+  }
+  const int row = lo, j = Cci[pc];
+  double acc[BR * BC];
+#pragma unroll
+  for (int t = 0; t < BR * BC; t++) acc[t] = 0.0;
+  for (int a = Arp[row] + lane; a < Arp[row + 1]; a += 32) {
+    const int k = Aci[a];
+    const int bh = Brp[k + 1];
+    int l = Brp[k], h = bh;
+    while (l < h) {
+      const int mid = (l + h) >> 1;
+      if (Bci[mid] < j) l = mid + 1;
+      else h = mid;
+    }
+    if (l >= bh || Bci[l] != j) continue;
+    const double* Ab = VA + (int64_t)a * BR * BK;
+    const double* Bb = VB + (int64_t)l * BK * BC;
+#pragma unroll
+    for (int r = 0; r < BR; r++)
+#pragma unroll
+      for (int t = 0; t < BK; t++) {
+        const double av = Ab[r * BK + t];
+#pragma unroll
+        for (int c = 0; c < BC; c++) acc[r * BC + c] += av * Bb[t * BC + c];
+      }
+  }
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1)
+#pragma unroll
+    for (int t = 0; t < BR * BC; t++) acc[t] += __shfl_xor_sync(0xffffffffu, acc[t], o);
+  double* Cb = VC + pc * BR * BC;
+#pragma unroll
+  for (int t = 0; t < BR * BC; t++)
+    if (lane == (t & 31)) Cb[t] = acc[t];
+}
+
 template <int BR, int BK, int BC>
 __global__ void __launch_bounds__(128) k_spgemm_num(int nrows, const int* __restrict__ Arp,
                                                     const int* __restrict__ Aci,
@@ -478,8 +537,17 @@ void spgemm_fill(cudaStream_t s, const Bsr& A, const Bsr& B, const int* rpC, int
 void spgemm_numeric(cudaStream_t s, const Bsr& A, const double* VA, const Bsr& B, const double* VB,
                     const Bsr& C, double* VC) {
   const int grid = ceil_div((int64_t)A.nbr * 32, 128);
+  // few long rows (the coarsest Galerkin products): one warp per output block
+  const bool long_rows = A.nbr > 0 && A.nbr < 4096 && A.nnzb >= 12LL * A.nbr;
+  const int gridw = (int)std::max<int64_t>(1, ceil_div(C.nnzb * 32, 128));
 #define NUM(R, K, CC)                                                                          \
   if (A.br == R && A.bc == K && B.bc == CC) {                                                  \
+    if (long_rows) {                                                                           \
+      if (C.nnzb > 0)                                                                          \
+        LAUNCH((k_spgemm_num_w<R, K, CC>), gridw, 128, 0, s, A.nbr, C.nnzb, A.rp, A.ci, VA,     \
+               B.rp, B.ci, VB, C.rp, C.ci, VC);                                                \
+      return;                                                                                  \
+    }                                                                                          \
     LAUNCH((k_spgemm_num<R, K, CC>), grid, 128, 0, s, A.nbr, A.rp, A.ci, VA, B.rp, B.ci, VB,   \
            C.rp, C.ci, VC);                                                                    \
     return;                                                                                    \

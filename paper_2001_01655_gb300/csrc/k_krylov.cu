@@ -201,6 +201,18 @@ __global__ void k_gemv(int n, const T* __restrict__ A, const T* __restrict__ b, 
 // A^-1 = Y^T Y (k_ltl).
 constexpr int NB = 32;
 
+// 1 / sqrt(d) in FP64 from the FP32 hardware estimate and two Newton steps for the reciprocal
+// square root, y <- y (3 - d y^2) / 2, each of which doubles the number of correct bits
+// (about 22 -> 44 -> 88).  A few FP64 FMAs instead of an FP64 square root and division, which
+// are long sequences on GB300's narrow FP64 pipe.  Outside the FP32 range: the plain formula.
+__device__ __forceinline__ double rsqrt_newton(double d) {
+  if (!(d > 1e-30 && d < 1e30)) return 1.0 / sqrt(d);
+  double y = (double)rsqrtf((float)d);
+  y = y * (1.5 - 0.5 * d * y * y);
+  y = y * (1.5 - 0.5 * d * y * y);
+  return y;
+}
+
 __global__ void __launch_bounds__(NB * NB) k_potrf_diag(int n, int k0, double* A, double* Linv,
                                                         int* fail) {
   __shared__ double s[NB][NB + 1];
@@ -210,8 +222,7 @@ __global__ void __launch_bounds__(NB * NB) k_potrf_diag(int n, int k0, double* A
   const int kb = min(NB, n - k0);
   s[ty][tx] = (ty < kb && tx < kb) ? A[(int64_t)(k0 + ty) * n + k0 + tx] : (ty == tx ? 1.0 : 0.0);
   __syncthreads();
-  // FP64 division and square root are long instruction sequences here: one of each per pivot,
-  // everything else multiplies by the reciprocal
+  // every pivot needs 1 / sqrt(d); everything else multiplies by it
   for (int k = 0; k < NB; k++) {
     if (tx == 0 && ty == 0) {
       double d = s[k][k];
@@ -219,9 +230,9 @@ __global__ void __launch_bounds__(NB * NB) k_potrf_diag(int n, int k0, double* A
         if (k < kb) atomicCAS(fail, 0, k0 + k + 1);
         d = 1.0;
       }
-      const double piv = sqrt(d);
-      s[k][k] = piv;
-      rdiag[k] = 1.0 / piv;
+      const double y = rsqrt_newton(d);
+      s[k][k] = d * y;  // sqrt(d)
+      rdiag[k] = y;
     }
     __syncthreads();
     if (tx == k && ty > k) s[ty][k] *= rdiag[k];
@@ -426,6 +437,7 @@ template void dense_gemv<double>(cudaStream_t, int, const double*, const double*
                                  const int*);
 
 int dense_spd_inverse(cudaStream_t s, int n, double* A, double* work) {
+  SetupTrace tr(s);
   double* Y = work;  // n x n
   const int nblk = ceil_div(n, NB);
   DBuf<int> fail;
@@ -447,6 +459,7 @@ int dense_spd_inverse(cudaStream_t s, int n, double* A, double* work) {
   int f = 0;
   CK(cudaMemcpyAsync(&f, fail.p, sizeof(int), cudaMemcpyDeviceToHost, s));
   CK(cudaStreamSynchronize(s));
+  tr.mark("  cholesky");
   if (f) return f;
   LAUNCH(k_eye, ceil_div((int64_t)n * n, 256), 256, 0, s, n, Y);
   for (int b = 0; b < nblk; b++) {
@@ -455,9 +468,11 @@ int dense_spd_inverse(cudaStream_t s, int n, double* A, double* work) {
     const int below = ceil_div(n - K0 - kb, NB);
     if (below > 0) LAUNCH(k_inv_update, dim3(b + 1, below), dim3(32, 8), 0, s, n, K0, A, Y);
   }
+  tr.mark("  triangular inverse");
   dim3 blk(16, 16), grd(ceil_div(n, 16), ceil_div(n, 16));
   LAUNCH(k_ltl, grd, blk, 0, s, n, Y, A);
   CK(cudaStreamSynchronize(s));
+  tr.mark("  L^-T L^-1");
   return 0;
 }
 

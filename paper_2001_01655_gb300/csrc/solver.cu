@@ -14,23 +14,6 @@
 
 namespace tomg {
 
-// Phase timing of the setup for diagnosis (TOMG_TRACE_SETUP=1): synchronises the stream at
-// each mark and prints the host time since the previous mark to stderr.
-struct SetupTrace {
-  bool on;
-  cudaStream_t s;
-  std::chrono::steady_clock::time_point t0;
-  explicit SetupTrace(cudaStream_t st) : on(getenv("TOMG_TRACE_SETUP") != nullptr), s(st),
-                                         t0(std::chrono::steady_clock::now()) {}
-  void mark(const char* what, int level = -1) {
-    if (!on) return;
-    cudaStreamSynchronize(s);
-    const auto t = std::chrono::steady_clock::now();
-    fprintf(stderr, "[setup] %-22s L%-2d %8.3f ms\n", what, level,
-            std::chrono::duration<double, std::milli>(t - t0).count());
-    t0 = t;
-  }
-};
 
 
 // ----------------------------------------------------------------------------------------
@@ -192,8 +175,9 @@ void vcycle(tomg_problem* P, Work& W, int l, const T* b, T* out, const int* done
   T* x = V<T>::x(lw);
   T* r = V<T>::r(lw);
   // pre-smoothing; the first sweep from x = 0 needs no operator apply, and with a single
-  // pre-sweep it is fused into the residual pass (x = w Dinv b, r = b - A x in one kernel)
-  if (P->opt.n_pre == 1) {
+  // pre-sweep in FP32 it is fused into the residual pass (x = w Dinv b, r = b - A x in one
+  // kernel; forming w Dinv b at every neighbour is cheap on the FP32 pipes, not on FP64)
+  if (P->opt.n_pre == 1 && sizeof(T) == 4) {
     level_op<T>(P, s, l, MODE_RESID0, x, r, b, done);
   } else {
     jacobi0<T>(s, Lv.b, Lv.nn, V<T>::D(Lv), b, x, w, done);
@@ -357,15 +341,19 @@ void spgemm_full(cudaStream_t s, const Bsr& A, const double* VA, const Bsr& B, c
   counts.resize(A.nbr > 0 ? A.nbr : 1);
   C.rp.resize(A.nbr + 1);
   SpgemmWork w;
+  SetupTrace tr(s);
   spgemm_counts(s, A, B, counts.p, w);
   const int64_t nnz = exclusive_scan(s, counts.p, C.rp.p, A.nbr);
+  tr.mark("  spgemm count+scan");
   C.ci.resize(nnz > 0 ? nnz : 1);
   spgemm_fill(s, A, B, C.rp.p, C.ci.p, w);
+  tr.mark("  spgemm fill");
   C.m.nbr = A.nbr; C.m.nbc = B.nbc; C.m.br = A.br; C.m.bc = B.bc; C.m.nnzb = nnz;
   C.m.rp = C.rp.p; C.m.ci = C.ci.p;
   C.V.resize(std::max<int64_t>(1, nnz * A.br * B.bc));
   spgemm_numeric(s, A, VA, B, VB, C.m, C.V.p);
   CK(cudaStreamSynchronize(s));
+  tr.mark("  spgemm numeric");
 }
 
 // level operator (stencil or matrix-free level 0 via its assembled stencil) -> BSR in Lv
