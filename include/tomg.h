@@ -54,7 +54,10 @@ typedef enum {
 /* Arithmetic of the V-cycle; the outer Krylov loop, its residual and dots are always FP64. */
 typedef enum {
   TOMG_PREC_FP64 = 0,         /* FP64 V-cycle inside FP64 PCG                                 */
-  TOMG_PREC_FP32_VCYCLE = 1   /* FP32 V-cycle inside FP64 flexible CG (Notay 2000)            */
+  TOMG_PREC_FP32_VCYCLE = 1,  /* FP32 V-cycle inside FP64 flexible CG (Notay 2000)            */
+  TOMG_PREC_3XTF32_VCYCLE = 2 /* as FP32_VCYCLE, with the hex8 level-0 element contractions on
+                                 the tensor cores as 3xTF32 split products (FP32 accuracy);
+                                 quad4 problems run exactly as FP32_VCYCLE                     */
 } tomg_prec;
 
 typedef struct {

@@ -198,6 +198,12 @@ void launch_ebe(cudaStream_t s, const Ebe& op, const T* x, T* y, const T* b, con
                 double omega, const int* done, double* parts) {
   // FP32 quad4: tiled kernel (memory/latency bound).  FP64: the node-per-thread kernel, whose
   // low register count keeps enough warps in flight to hide the long FP64 pipe latency.
+  if (DIM == 3 && sizeof(T) == 4 && !DOT && op.tc) {
+    ebe3d_tc_launch(s, MODE, op, reinterpret_cast<const float*>(x), reinterpret_cast<float*>(y),
+                    reinterpret_cast<const float*>(b), reinterpret_cast<const float*>(Dinv),
+                    omega, done);
+    return;
+  }
   if (DIM == 3 && sizeof(T) == 4 && !DOT) {
     ebe3d_launch(s, MODE, op, reinterpret_cast<const float*>(x), reinterpret_cast<float*>(y),
                  reinterpret_cast<const float*>(b), reinterpret_cast<const float*>(Dinv), omega,

@@ -1,0 +1,446 @@
+// Level-0 SIMP element operator on hex8 grids (Sec. 2.1 Eq. 2, Sec. 3.1) with the element
+// contractions on the fifth-generation tensor cores: tcgen05.mma kind::tf32, operands in
+// shared memory, accumulators in tensor memory.
+//
+// The element products y_e = Ke x_e of a tile of elements form one dense product
+//   Y (elements x 24) = X (elements x 24) . Ke^T (24 x 24)
+// whose rows are the gathered element displacement vectors.  FP32 accuracy on TF32 units comes
+// from split products ("3xTF32"): x = x_hi + x_lo and Ke = K_hi + K_lo with every part a TF32
+// value, and Y = X_hi K_hi^T + X_lo K_hi^T + X_hi K_lo^T (the X_lo K_lo^T term is below FP32
+// rounding).  The three products accumulate in FP32 in the same tensor-memory tile.
+//
+// Tiling.  A block owns a column of output nodes: 31 x 7 nodes in x, y and `nz_tile` node
+// layers in z.  It walks the element layers under and inside that column.  One element layer
+// of the tile is 32 x 8 = 256 elements = two M = 128 tiles, one element per thread.  Per layer:
+//   1. the masked displacements of the next node layer (33 x 9 nodes) are staged in shared
+//      memory, and each thread keeps its element's modulus (both fetched one layer ahead);
+//   2. every thread writes its element's 24 displacements, split into TF32 hi and lo parts,
+//      as one row of the A operands in the canonical no-swizzle K-major layout;
+//   3. one thread issues 2 tiles x 3 products x 3 K-steps of M128 N32 K8 MMAs and commits them
+//      to an mbarrier (N = 32: the 24 outputs padded with zero rows of B);
+//   4. every thread reads its element's row of the accumulator (tcgen05.ld), scales it by E_e
+//      and stages it in shared memory;
+//   5. every owned node sums the contributions of the four elements of this layer around it;
+//      a node layer is complete after the element layers below and above it, and is then
+//      finished (mask, residual or Jacobi update) and written.
+// The outer ring of nodes of each tile is computed but not written: the neighbouring tile owns
+// it, so every node's sum comes from one block, in a fixed order, with no atomics.
+// All waits are bounded: an mbarrier that does not complete within the limit sets an error word
+// (read by the host after the solve) and the block releases its tensor memory and returns.
+#include <cstring>
+
+#include "ops.h"
+
+namespace tomg {
+
+namespace {
+
+constexpr int TEX = 32, TEY = 8;              // elements of one layer of the tile
+constexpr int TNX = TEX + 1, TNY = TEY + 1;   // nodes of one layer of the tile (33 x 9)
+constexpr int ONX = TEX - 1, ONY = TEY - 1;   // owned nodes per layer (31 x 7)
+constexpr int NT = TEX * TEY;                 // 256 threads, one element each
+constexpr int LAYER_NODES = TNX * TNY;        // 297
+constexpr int OWNED = ONX * ONY;              // 217
+constexpr int KD = 24;                        // element DOFs (the K of the product)
+constexpr int NB = 32;                        // N: 24 outputs padded to a multiple of 16
+// canonical K-major layout without swizzle: a core matrix is 8 rows x 16 bytes (4 TF32);
+// core matrices adjacent in K are LBO bytes apart, adjacent 8-row groups SBO bytes apart
+constexpr int LBO = 128;
+constexpr int SBO = (KD / 4) * LBO;           // 768
+constexpr int A_BYTES = (128 / 8) * SBO;      // one M = 128 operand: 12288
+constexpr int B_BYTES = (NB / 8) * SBO;       // one N = 32 operand: 3072
+constexpr int YS = 25;                        // staged element outputs: row stride (floats)
+constexpr int TMEM_COLS = 64;                 // two 128 x 32 FP32 accumulators
+
+// dynamic shared memory map (bytes from a 1024-aligned base)
+constexpr int OFF_A = 0;                                  // A_hi[2], A_lo[2]; later Y staging
+constexpr int OFF_B = OFF_A + 4 * A_BYTES;                // B_hi, B_lo
+constexpr int OFF_X = OFF_B + 2 * B_BYTES;                // x ring: 2 node layers
+constexpr int OFF_BAR = OFF_X + 2 * LAYER_NODES * 3 * 4;  // mbarrier (8 B) + TMEM address
+constexpr int SMEM_BYTES = OFF_BAR + 16;
+constexpr int SMEM_ALLOC = SMEM_BYTES + 1024;             // room to align the base
+static_assert(NT * YS * 4 <= 4 * A_BYTES, "Y staging must fit in the A operands");
+static_assert(OFF_B % 1024 == 0 && OFF_X % 16 == 0 && OFF_BAR % 8 == 0, "alignment");
+
+// instruction descriptor, kind::tf32: D FP32 (bits 4-5 = 1), A and B TF32 (bits 7-9 and
+// 10-12 = 2), both K-major (bits 15, 16 = 0), N >> 3 at bits 17-22, M >> 4 at bits 24-28
+constexpr uint32_t IDESC = (1u << 4) | (2u << 7) | (2u << 10) | ((uint32_t)(NB >> 3) << 17) |
+                           ((uint32_t)(128 >> 4) << 24);
+
+constexpr uint32_t WAIT_LIMIT = 1u << 22;  // mbarrier polls before a block gives up
+
+__device__ int g_tc_error;  // set to 1 by a block whose MMA completion wait ran out
+
+__device__ __forceinline__ uint32_t smem_u32(const void* p) {
+  return (uint32_t)__cvta_generic_to_shared(p);
+}
+
+// shared-memory matrix descriptor: start address, LBO, SBO (all >> 4), fixed 0b001 at
+// bits 46-48, base offset 0, no swizzle (bits 61-63 = 0)
+__device__ __forceinline__ uint64_t sdesc(uint32_t addr) {
+  return (uint64_t)((addr & 0x3FFFFu) >> 4) | ((uint64_t)(LBO >> 4) << 16) |
+         ((uint64_t)(SBO >> 4) << 32) | (1ull << 46);
+}
+
+// byte offset of element (row, k) in an operand of the layout above
+__host__ __device__ __forceinline__ int op_off(int row, int k) {
+  return (row >> 3) * SBO + (k >> 2) * LBO + (row & 7) * 16 + (k & 3) * 4;
+}
+
+// x rounded to the nearest TF32 value (10 explicit mantissa bits), ties away from zero
+__host__ __device__ __forceinline__ uint32_t tf32_round_bits(uint32_t u) {
+  return (u + 0x1000u) & 0xFFFFE000u;
+}
+
+__device__ __forceinline__ void mma_tf32(uint32_t d_tmem, uint64_t a, uint64_t b, uint32_t acc) {
+  asm volatile(
+      "{\n\t.reg .pred p;\n\t"
+      "setp.ne.b32 p, %4, 0;\n\t"
+      "tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, p;\n\t}\n"
+      :: "r"(d_tmem), "l"(a), "l"(b), "r"(IDESC), "r"(acc) : "memory");
+}
+
+__device__ __forceinline__ bool mbar_try(uint32_t bar, uint32_t parity) {
+  uint32_t ok;
+  asm volatile(
+      "{\n\t.reg .pred p;\n\t"
+      "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+      "selp.u32 %0, 1, 0, p;\n\t}\n"
+      : "=r"(ok) : "r"(bar), "r"(parity) : "memory");
+  return ok != 0;
+}
+
+// bounded wait for phase `parity` of the barrier; true if it completed
+__device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity) {
+  for (uint32_t i = 0; i < WAIT_LIMIT; i++)
+    if (mbar_try(bar, parity)) return true;
+  return false;
+}
+
+// this thread's TMEM lane, 24 consecutive FP32 columns from taddr; the wait for the loads is
+// part of the same asm statement, so no use of the registers can be scheduled before it
+__device__ __forceinline__ void tmem_ld24(uint32_t taddr, float* v) {
+  uint32_t r[24];
+  asm volatile(
+      "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,"
+      "%14,%15}, [%24];\n\t"
+      "tcgen05.ld.sync.aligned.32x32b.x8.b32 {%16,%17,%18,%19,%20,%21,%22,%23}, [%25];\n\t"
+      "tcgen05.wait::ld.sync.aligned;\n"
+      : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]),
+        "=r"(r[7]), "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]),
+        "=r"(r[14]), "=r"(r[15]), "=r"(r[16]), "=r"(r[17]), "=r"(r[18]), "=r"(r[19]),
+        "=r"(r[20]), "=r"(r[21]), "=r"(r[22]), "=r"(r[23])
+      : "r"(taddr), "r"(taddr + 16u)
+      : "memory");
+#pragma unroll
+  for (int i = 0; i < 24; i++) v[i] = __uint_as_float(r[i]);
+}
+
+// one node layer of the tile: masked displacements of up to two nodes per thread
+struct XPre {
+  float v[2][3];
+};
+
+__device__ __forceinline__ void x_fetch(XPre& p, int kk, int EX0, int EY0, int nx, int ny, int nz,
+                                        const uint8_t* __restrict__ mask,
+                                        const float* __restrict__ x) {
+#pragma unroll
+  for (int h = 0; h < 2; h++) {
+    const int q = threadIdx.x + h * NT;
+    p.v[h][0] = p.v[h][1] = p.v[h][2] = 0.f;
+    if (q < LAYER_NODES) {
+      const int gi = EX0 + q % TNX, gj = EY0 + q / TNX;
+      if (gi >= 0 && gi <= nx && gj >= 0 && gj <= ny && kk >= 0 && kk <= nz) {
+        const int64_t node = node_id(gi, gj, kk, nx, ny);
+        const unsigned m = __ldg(mask + node);
+#pragma unroll
+        for (int c = 0; c < 3; c++) p.v[h][c] = ((m >> c) & 1u) ? 0.f : __ldg(x + 3 * node + c);
+      }
+    }
+  }
+}
+
+__device__ __forceinline__ void x_store(const XPre& p, float* sx) {
+#pragma unroll
+  for (int h = 0; h < 2; h++) {
+    const int q = threadIdx.x + h * NT;
+    if (q < LAYER_NODES) {
+#pragma unroll
+      for (int c = 0; c < 3; c++) sx[3 * q + c] = p.v[h][c];
+    }
+  }
+}
+
+__device__ __forceinline__ float e_fetch(int ke, int EX0, int EY0, int nx, int ny, int nz,
+                                         const float* __restrict__ E) {
+  const int ge = EX0 + (int)(threadIdx.x % TEX), gf = EY0 + (int)(threadIdx.x / TEX);
+  if (ge < 0 || ge >= nx || gf < 0 || gf >= ny || ke < 0 || ke >= nz) return 0.f;
+  return __ldg(E + ge + (int64_t)nx * (gf + (int64_t)ny * ke));
+}
+
+template <int MODE>
+__global__ void __launch_bounds__(NT, 3)
+k_ebe3tc(int nx, int ny, int nz, int nz_tile, const uint4* __restrict__ Bimg,
+         const float* __restrict__ E, const uint8_t* __restrict__ mask,
+         const float* __restrict__ x, float* __restrict__ y, const float* __restrict__ b,
+         const float* __restrict__ Dinv, float omega, const int* done) {
+  extern __shared__ uint8_t smem_raw[];
+  pdl_prologue();
+  if (solve_done(done)) return;
+  uint8_t* sm = smem_raw + ((1024 - (smem_u32(smem_raw) & 1023u)) & 1023u);
+  float* sxr = reinterpret_cast<float*>(sm + OFF_X);      // [2][LAYER_NODES][3]
+  float* sY = reinterpret_cast<float*>(sm + OFF_A);       // [NT][YS] (after the MMAs)
+  uint64_t* bar = reinterpret_cast<uint64_t*>(sm + OFF_BAR);
+  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(sm + OFF_BAR + 8);
+  const uint32_t sbase = smem_u32(sm);
+  const uint32_t bar_a = smem_u32(bar);
+  const int tid = threadIdx.x, warp = tid >> 5;
+
+  const int EX0 = blockIdx.x * ONX - 1, EY0 = blockIdx.y * ONY - 1;
+  const int k0 = blockIdx.z * nz_tile;
+  const int k1 = min(k0 + nz_tile, nz + 1);  // owned node layers [k0, k1)
+
+  // tensor memory (one warp), the MMA barrier, the B operands
+  if (warp == 0) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;\n"
+                 :: "r"(smem_u32(tmem_slot)), "r"(TMEM_COLS) : "memory");
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;\n" ::: "memory");
+  }
+  if (tid == 0) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;\n" :: "r"(bar_a), "r"(1) : "memory");
+    asm volatile("fence.mbarrier_init.release.cluster;\n" ::: "memory");
+  }
+  for (int t = tid; t < 2 * B_BYTES / 16; t += NT)
+    reinterpret_cast<uint4*>(sm + OFF_B)[t] = Bimg[t];
+
+  // owned node of this thread (threads >= OWNED only help with the element work)
+  const bool owner = tid < OWNED;
+  const int onx = tid % ONX + 1, ony = tid / ONX + 1;        // local node of the layer tile
+  const int gi = EX0 + onx, gj = EY0 + ony;
+  const bool in_plane = owner && gi <= nx && gj <= ny;
+
+  XPre pre;
+  x_fetch(pre, k0 - 1, EX0, EY0, nx, ny, nz, mask, x);
+  x_store(pre, sxr + ((k0 - 1) & 1) * LAYER_NODES * 3);
+  x_fetch(pre, k0, EX0, EY0, nx, ny, nz, mask, x);
+  x_store(pre, sxr + (k0 & 1) * LAYER_NODES * 3);
+  float ev = e_fetch(k0 - 1, EX0, EY0, nx, ny, nz, E);
+  asm volatile("tcgen05.fence::before_thread_sync;\n" ::: "memory");
+  __syncthreads();
+  asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
+  const uint32_t tmem = *tmem_slot;
+
+  float acc[3] = {0.f, 0.f, 0.f};  // node layer ke: contributions gathered so far
+  uint32_t parity = 0;
+  bool failed = false;
+  const int ex = tid % TEX, ey = tid / TEX;
+  const int mt = tid >> 7, row = tid & 127;
+
+  for (int ke = k0 - 1; ke < k1; ke++) {
+    const float Ee = ev;  // modulus of this thread's element in layer ke
+    // prefetch: node layer ke + 2 and element layer ke + 1 (registers, stored at the end)
+    const bool more = ke + 2 <= k1;
+    if (more) x_fetch(pre, ke + 2, EX0, EY0, nx, ny, nz, mask, x);
+    if (ke + 1 < k1) ev = e_fetch(ke + 1, EX0, EY0, nx, ny, nz, E);
+    // finishing data of node layer ke (owned nodes), fetched ahead of the MMAs
+    float xi[3] = {0.f, 0.f, 0.f}, bi[3] = {0.f, 0.f, 0.f}, Di[9];
+    unsigned mi = 0;
+    const bool fin = in_plane && ke >= k0;
+    int64_t node = 0;
+    if (fin) {
+      node = node_id(gi, gj, ke, nx, ny);
+      mi = __ldg(mask + node);
+#pragma unroll
+      for (int c = 0; c < 3; c++) xi[c] = __ldg(x + 3 * node + c);
+      if (MODE != MODE_APPLY) {
+#pragma unroll
+        for (int c = 0; c < 3; c++) bi[c] = __ldg(b + 3 * node + c);
+      }
+      if (MODE == MODE_JACOBI) {
+#pragma unroll
+        for (int c = 0; c < 9; c++) Di[c] = __ldg(Dinv + 9 * node + c);
+      }
+    }
+
+    // A operand rows: this thread's element, local nodes bn = dx + 2 dy + 4 dz
+    {
+      const float* s0 = sxr + (ke & 1) * LAYER_NODES * 3;
+      const float* s1 = sxr + ((ke + 1) & 1) * LAYER_NODES * 3;
+      uint8_t* Ahi = sm + OFF_A + mt * A_BYTES;
+      uint8_t* Alo = sm + OFF_A + (2 + mt) * A_BYTES;
+#pragma unroll
+      for (int kc = 0; kc < 6; kc++) {
+        uint32_t hi[4], lo[4];
+#pragma unroll
+        for (int q = 0; q < 4; q++) {
+          const int k = 4 * kc + q, bn = k / 3, c = k % 3;
+          const float* sx = (bn & 4) ? s1 : s0;
+          const float v = sx[3 * ((ey + ((bn >> 1) & 1)) * TNX + ex + (bn & 1)) + c];
+          hi[q] = tf32_round_bits(__float_as_uint(v));
+          lo[q] = __float_as_uint(v - __uint_as_float(hi[q]));
+        }
+        const int off = op_off(row, 4 * kc);
+        *reinterpret_cast<uint4*>(Ahi + off) = make_uint4(hi[0], hi[1], hi[2], hi[3]);
+        *reinterpret_cast<uint4*>(Alo + off) = make_uint4(lo[0], lo[1], lo[2], lo[3]);
+      }
+    }
+    asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory");
+    __syncthreads();
+
+    if (tid == 0) {
+      asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
+#pragma unroll
+      for (int m = 0; m < 2; m++) {
+        const uint32_t d = tmem + (uint32_t)(m * NB);
+        const uint32_t ahi = sbase + OFF_A + m * A_BYTES, alo = sbase + OFF_A + (2 + m) * A_BYTES;
+        const uint32_t bhi = sbase + OFF_B, blo = sbase + OFF_B + B_BYTES;
+#pragma unroll
+        for (int p = 0; p < 3; p++) {
+          const uint32_t a = (p == 1) ? alo : ahi;
+          const uint32_t bb = (p == 2) ? blo : bhi;
+#pragma unroll
+          for (int s = 0; s < 3; s++)
+            mma_tf32(d, sdesc(a + 2 * LBO * s), sdesc(bb + 2 * LBO * s), (p | s) ? 1u : 0u);
+        }
+      }
+      asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];\n"
+                   :: "r"(bar_a) : "memory");
+    }
+    const bool ok = mbar_wait(bar_a, parity);
+    parity ^= 1u;
+    if (__syncthreads_or(!ok)) {
+      failed = true;
+      break;
+    }
+    asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
+
+    // accumulator row of this thread's element -> E_e-scaled contributions in shared memory
+    {
+      float v[24];
+      tmem_ld24(tmem + ((uint32_t)(32 * (warp & 3)) << 16) + (uint32_t)(mt * NB), v);
+#pragma unroll
+      for (int n = 0; n < 24; n++) sY[tid * YS + n] = Ee * v[n];
+    }
+    asm volatile("tcgen05.fence::before_thread_sync;\n" ::: "memory");
+    __syncthreads();
+
+    if (owner) {
+      // elements (onx-1+ex', ony-1+ey') of this layer; the node is their local node
+      // (1-ex') + 2(1-ey') at the bottom (dz = 0) or + 4 at the top (dz = 1)
+      float top[3] = {0.f, 0.f, 0.f};
+#pragma unroll
+      for (int q = 0; q < 4; q++) {
+        const int dxe = q & 1, dye = q >> 1;
+        const float* Ye = sY + ((ony - 1 + dye) * TEX + onx - 1 + dxe) * YS;
+        const int bn = (1 - dxe) + 2 * (1 - dye);
+#pragma unroll
+        for (int c = 0; c < 3; c++) {
+          acc[c] += Ye[3 * bn + c];
+          top[c] += Ye[3 * (bn + 4) + c];
+        }
+      }
+      if (fin) {
+        float Ax[3];
+#pragma unroll
+        for (int c = 0; c < 3; c++) Ax[c] = ((mi >> c) & 1u) ? xi[c] : acc[c];
+        if (MODE == MODE_APPLY) {
+#pragma unroll
+          for (int c = 0; c < 3; c++) y[3 * node + c] = Ax[c];
+        } else {
+          float r[3];
+#pragma unroll
+          for (int c = 0; c < 3; c++) r[c] = bi[c] - Ax[c];
+          if (MODE == MODE_RESID) {
+#pragma unroll
+            for (int c = 0; c < 3; c++) y[3 * node + c] = r[c];
+          } else {
+#pragma unroll
+            for (int c = 0; c < 3; c++)
+              y[3 * node + c] =
+                  xi[c] + omega * (Di[3 * c] * r[0] + Di[3 * c + 1] * r[1] + Di[3 * c + 2] * r[2]);
+          }
+        }
+      }
+#pragma unroll
+      for (int c = 0; c < 3; c++) acc[c] = top[c];
+    }
+    if (more) x_store(pre, sxr + (ke & 1) * LAYER_NODES * 3);
+    __syncthreads();
+  }
+
+  if (failed && tid == 0) atomicExch(&g_tc_error, 1);
+  if (failed) {
+    // let MMAs still in flight finish (bounded) before the tensor memory is released
+    mbar_wait(bar_a, parity ^ 1u);
+  }
+  asm volatile("tcgen05.fence::before_thread_sync;\n" ::: "memory");
+  __syncthreads();
+  if (warp == 0) {
+    asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;\n"
+                 :: "r"(tmem), "r"(TMEM_COLS) : "memory");
+  }
+}
+
+template <int MODE>
+void launch_mode(cudaStream_t s, const Ebe& op, const float* x, float* y, const float* b,
+                 const float* Dinv, double omega, const int* done) {
+  static bool attr_set = false;  // per instantiation; the attribute is per device function
+  if (!attr_set) {
+    CK(cudaFuncSetAttribute(k_ebe3tc<MODE>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                            SMEM_ALLOC));
+    attr_set = true;
+  }
+  const int nzt = op.tc_nz > 0 ? op.tc_nz : 8;
+  dim3 grid(ceil_div(op.nx + 1, ONX), ceil_div(op.ny + 1, ONY), ceil_div(op.nz + 1, nzt));
+  LAUNCH(k_ebe3tc<MODE>, grid, NT, SMEM_ALLOC, s, op.nx, op.ny, op.nz, nzt,
+         reinterpret_cast<const uint4*>(op.Ktc), (const float*)op.E, op.mask, x, y, b, Dinv,
+         (float)omega, done);
+}
+
+}  // namespace
+
+void ebe3d_tc_operand(const double* Ke, uint32_t* img) {
+  // B_hi then B_lo: row n < 24 is Ke row n (Ke is symmetric), rows 24..31 are zero
+  for (int i = 0; i < 2 * B_BYTES / 4; i++) img[i] = 0u;
+  for (int n = 0; n < KD; n++)
+    for (int k = 0; k < KD; k++) {
+      const float v = (float)Ke[n * KD + k];
+      uint32_t u;
+      memcpy(&u, &v, 4);
+      const uint32_t hi = tf32_round_bits(u);
+      float fh;
+      memcpy(&fh, &hi, 4);
+      const double rest = Ke[n * KD + k] - (double)fh;
+      const float fl = (float)rest;
+      uint32_t ul;
+      memcpy(&ul, &fl, 4);
+      const uint32_t lo = tf32_round_bits(ul);
+      img[op_off(n, k) / 4] = hi;
+      img[(B_BYTES + op_off(n, k)) / 4] = lo;
+    }
+}
+
+int ebe3d_tc_operand_words() { return 2 * B_BYTES / 4; }
+
+void ebe3d_tc_launch(cudaStream_t s, int mode, const Ebe& op, const float* x, float* y,
+                     const float* b, const float* Dinv, double omega, const int* done) {
+  if (mode == MODE_APPLY) launch_mode<MODE_APPLY>(s, op, x, y, b, Dinv, omega, done);
+  else if (mode == MODE_RESID) launch_mode<MODE_RESID>(s, op, x, y, b, Dinv, omega, done);
+  else launch_mode<MODE_JACOBI>(s, op, x, y, b, Dinv, omega, done);
+}
+
+// reads and clears the error word of the tensor-core kernel (synchronises the stream)
+bool ebe3d_tc_error(cudaStream_t s) {
+  int v = 0;
+  CK(cudaMemcpyFromSymbolAsync(&v, g_tc_error, sizeof(int), 0, cudaMemcpyDeviceToHost, s));
+  CK(cudaStreamSynchronize(s));
+  if (v) {
+    const int zero = 0;
+    CK(cudaMemcpyToSymbolAsync(g_tc_error, &zero, sizeof(int), 0, cudaMemcpyHostToDevice, s));
+    CK(cudaStreamSynchronize(s));
+  }
+  return v != 0;
+}
+
+}  // namespace tomg

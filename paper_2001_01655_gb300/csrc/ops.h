@@ -23,6 +23,11 @@ struct Ebe {
   const uint8_t* mask;
   int tile = 0;    // quad4 FP32: nodes per thread of the tiled kernel (1, 2, 4; 0 = 4)
   const void* Kh = nullptr;  // host copy of Ke (T); the tiled kernels take Ke by value
+  // hex8 FP32: element contractions on the tensor cores (3xTF32) when tc != 0; Ktc holds the
+  // split Ke operand images (ebe3d_tc_operand), tc_nz the node layers per block (0 = 8)
+  int tc = 0;
+  int tc_nz = 0;
+  const void* Ktc = nullptr;
 };
 template <class T>
 void ebe_op(cudaStream_t s, int mode, const Ebe& op, const T* x, T* y, const T* b,
@@ -39,6 +44,14 @@ int ebe2d_autotune(cudaStream_t s, const Ebe& op, const float* Dinv);
 // hex8 FP32 tiled implementation behind ebe_op (k_ebe3d.cu; no fused dot)
 void ebe3d_launch(cudaStream_t s, int mode, const Ebe& op, const float* x, float* y,
                   const float* b, const float* Dinv, double omega, const int* done);
+// hex8 FP32 on the tensor cores (k_ebe3tc.cu): tcgen05 kind::tf32 split products, same modes
+void ebe3d_tc_launch(cudaStream_t s, int mode, const Ebe& op, const float* x, float* y,
+                     const float* b, const float* Dinv, double omega, const int* done);
+// Ke (24 x 24, FP64) -> TF32 hi and lo B-operand images in the kernel's shared-memory layout
+void ebe3d_tc_operand(const double* Ke, uint32_t* img);
+int ebe3d_tc_operand_words();
+// true if a tensor-core kernel gave up waiting for its MMAs since the last call (syncs s)
+bool ebe3d_tc_error(cudaStream_t s);
 // point-block diagonal inverse of the level-0 operator, FP64 and FP32 copies
 void ebe_block_diag_inv(cudaStream_t s, const Ebe& op64, double* Dinv64, float* Dinv32);
 // level-0 operator assembled as a structured 3^dim stencil, FP64, SoA layout

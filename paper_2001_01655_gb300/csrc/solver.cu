@@ -112,12 +112,27 @@ template <> struct V<float> {
   static float* y(LevelWork& l) { return l.y32.p; }
   static const float* Ainv(const tomg_problem* P) { return P->Ainv32.p; }
   static Ebe ebe(const tomg_problem* P) {
-    return Ebe{P->dim, P->nx, P->ny, P->nz, P->Ke32.p, P->E32.p, P->mask.p, P->ebe_tile,
-               P->Ke32_host.data()};
+    Ebe op{P->dim, P->nx, P->ny, P->nz, P->Ke32.p, P->E32.p, P->mask.p, P->ebe_tile,
+           P->Ke32_host.data()};
+    const bool tc = P->tc_mode >= 0 ? P->tc_mode != 0 : P->opt.prec == TOMG_PREC_3XTF32_VCYCLE;
+    op.tc = (P->dim == 3 && tc && P->Ketc.p) ? 1 : 0;
+    op.tc_nz = P->tc_nz;
+    op.Ktc = P->Ketc.p;
+    return op;
   }
 };
 
 inline cudaStream_t st(const tomg_problem* P) { return P->stream; }
+
+// single-step calls with an explicit precision choose the hex8 FP32 kernel by that precision
+struct TcScope {
+  tomg_problem* P;
+  int saved;
+  TcScope(tomg_problem* p, int prec) : P(p), saved(p->tc_mode) {
+    P->tc_mode = prec == TOMG_PREC_3XTF32_VCYCLE ? 1 : 0;
+  }
+  ~TcScope() { P->tc_mode = saved; }
+};
 
 template <class T>
 void level_op(tomg_problem* P, cudaStream_t s, int l, int mode, const T* x, T* y, const T* b,
@@ -542,6 +557,13 @@ void problem_init(tomg_problem* P) {
   P->Ke32_host.assign(P->Ke_host.begin(), P->Ke_host.end());
   CK(cudaMemcpyAsync(P->Ke64.p, P->Ke_host.data(), nk * 8, cudaMemcpyHostToDevice, s));
   CK(cudaMemcpyAsync(P->Ke32.p, P->Ke32_host.data(), nk * 4, cudaMemcpyHostToDevice, s));
+  if (P->dim == 3) {
+    std::vector<uint32_t> img(ebe3d_tc_operand_words());
+    ebe3d_tc_operand(P->Ke_host.data(), img.data());
+    P->Ketc.resize(img.size());
+    CK(cudaMemcpyAsync(P->Ketc.p, img.data(), img.size() * 4, cudaMemcpyHostToDevice, s));
+    CK(cudaStreamSynchronize(s));  // img is a host temporary
+  }
   P->mask.resize(P->nn);
   P->mask.zero(s);
   P->rho.resize(P->nel);
@@ -584,7 +606,7 @@ void set_density(tomg_problem* P, const double* rho, int on_device) {
 void setup(tomg_problem* P, const tomg_options& opt) {
   cudaStream_t s = st(P);
   if (!P->have_density) TOMG_THROW(TOMG_E_INVALID, "tomg_setup: no density set");
-  if (opt.pc < 0 || opt.pc > 3 || opt.prec < 0 || opt.prec > 1)
+  if (opt.pc < 0 || opt.pc > 3 || opt.prec < 0 || opt.prec > 2)
     TOMG_THROW(TOMG_E_INVALID, "unknown preconditioner %d or precision %d", opt.pc, opt.prec);
   if (!(opt.rtol > 0.0) || opt.max_iter < 1 || opt.max_iter > 1000000 || !(opt.omega > 0.0) ||
       !(opt.omega < 2.0) || opt.n_pre < 1 || opt.n_pre > 8 || opt.n_post < 1 || opt.n_post > 8 ||
@@ -876,6 +898,8 @@ tomg_status solve(tomg_problem* P, int nrhs, const double* f, double* u, int on_
   }
   for (int k = 0; k < slots; k++) join_from(P, *P->works[k]);
   CK(cudaStreamSynchronize(st(P)));
+  if (P->dim == 3 && P->opt.prec == TOMG_PREC_3XTF32_VCYCLE && ebe3d_tc_error(st(P)))
+    for (int j = 0; j < nrhs; j++) res[j].status = TOMG_E_TIMEOUT;
   tomg_status worst = TOMG_OK;
   for (int j = 0; j < nrhs; j++) {
     const int s = res[j].status;
@@ -897,11 +921,14 @@ void level_apply(tomg_problem* P, int level, int prec, const double* x, double* 
     level_op<double>(P, s, level, MODE_APPLY, lw.b64.p, lw.y64.p, nullptr, nullptr);
     CK(cudaMemcpyAsync(y, lw.y64.p, n * 8, cudaMemcpyDeviceToDevice, s));
   } else {
+    TcScope tcs(P, prec);
     cast_f64_f32(s, x, lw.b32.p, n);
     level_op<float>(P, s, level, MODE_APPLY, lw.b32.p, lw.y32.p, nullptr, nullptr);
     cast_f32_f64(s, lw.y32.p, y, n);
   }
   CK(cudaStreamSynchronize(s));
+  if (P->dim == 3 && prec == TOMG_PREC_3XTF32_VCYCLE && ebe3d_tc_error(s))
+    TOMG_THROW(TOMG_E_TIMEOUT, "tensor-core element kernel: MMA completion wait expired");
 }
 
 void outer_operator_apply(tomg_problem* P, const double* x, double* y) {
@@ -1007,7 +1034,10 @@ double time_fine_operator(tomg_problem* P, int op, int prec, int reps, int cold_
     CK(cudaEventRecord(ev[2 * k], s));
     if (op == 3) fine64_apply_dot(P, s, W.p.p, W.q.p, nullptr, W.partA.p, nullptr);
     else if (prec == TOMG_PREC_FP64) level_op<double>(P, s, 0, mode, l0.x64.p, l0.y64.p, l0.b64.p, nullptr);
-    else level_op<float>(P, s, 0, mode, l0.x32.p, l0.y32.p, l0.b32.p, nullptr);
+    else {
+      TcScope tcs(P, prec);
+      level_op<float>(P, s, 0, mode, l0.x32.p, l0.y32.p, l0.b32.p, nullptr);
+    }
     CK(cudaEventRecord(ev[2 * k + 1], s));
   }
   CK(cudaStreamSynchronize(s));

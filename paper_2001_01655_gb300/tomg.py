@@ -16,7 +16,7 @@ LIB_PATH = os.path.join(HERE, "_build", "libtomg.so")
 
 OK, NOT_CONVERGED, E_INVALID, E_OOM, E_CUDA, E_BREAKDOWN, E_TIMEOUT, E_BUDGET = 0, 1, -1, -2, -3, -4, -5, -6
 PC = {"gmg": 0, "amg": 1, "hybrid": 2, "jacobi": 3}
-PREC = {"fp64": 0, "fp32": 1}
+PREC = {"fp64": 0, "fp32": 1, "tf32x3": 2}
 
 
 class TomgError(RuntimeError):
