@@ -11,7 +11,9 @@
 //
 // Tiling.  A block owns a column of output nodes: 31 x 7 nodes in x, y and `nz_tile` node
 // layers in z.  It walks the element layers under and inside that column.  One element layer
-// of the tile is 32 x 8 = 256 elements = two M = 128 tiles, one element per thread.  Per layer:
+// of the tile is 32 x 8 = 256 elements = two M = 128 tiles, one element per thread.  Per layer
+// (steps 2-3 of layer ke run while steps 4-5 of layer ke - 1 run: two A buffers, two
+// accumulator sets in tensor memory):
 //   1. the masked displacements of the next node layer (33 x 9 nodes) are staged in shared
 //      memory, and each thread keeps its element's modulus (both fetched one layer ahead);
 //   2. every thread writes its element's 24 displacements, split into TF32 hi and lo parts,
@@ -28,6 +30,9 @@
 // All waits are bounded: an mbarrier that does not complete within the limit sets an error word
 // (read by the host after the solve) and the block releases its tensor memory and returns.
 #include <cstring>
+#include <map>
+#include <mutex>
+#include <tuple>
 
 #include "ops.h"
 
@@ -50,17 +55,19 @@ constexpr int SBO = (KD / 4) * LBO;           // 768
 constexpr int A_BYTES = (128 / 8) * SBO;      // one M = 128 operand: 12288
 constexpr int B_BYTES = (NB / 8) * SBO;       // one N = 32 operand: 3072
 constexpr int YS = 25;                        // staged element outputs: row stride (floats)
-constexpr int TMEM_COLS = 64;                 // two 128 x 32 FP32 accumulators
+constexpr int TMEM_COLS = 128;                // 2 pipeline stages x 2 tiles x 32 FP32 columns
 
-// dynamic shared memory map (bytes from a 1024-aligned base)
-constexpr int OFF_A = 0;                                  // A_hi[2], A_lo[2]; later Y staging
-constexpr int OFF_B = OFF_A + 4 * A_BYTES;                // B_hi, B_lo
+// dynamic shared memory map (bytes from a 128-aligned base).  A set = A_hi[2 tiles],
+// A_lo[2 tiles] of one pipeline stage; after its MMAs it holds the staged element outputs.
+constexpr int A_SET = 4 * A_BYTES;                        // 49152
+constexpr int OFF_A = 0;                                  // two A sets
+constexpr int OFF_B = OFF_A + 2 * A_SET;                  // B_hi, B_lo
 constexpr int OFF_X = OFF_B + 2 * B_BYTES;                // x ring: 2 node layers
-constexpr int OFF_BAR = OFF_X + 2 * LAYER_NODES * 3 * 4;  // mbarrier (8 B) + TMEM address
-constexpr int SMEM_BYTES = OFF_BAR + 16;
-constexpr int SMEM_ALLOC = SMEM_BYTES + 1024;             // room to align the base
-static_assert(NT * YS * 4 <= 4 * A_BYTES, "Y staging must fit in the A operands");
-static_assert(OFF_B % 1024 == 0 && OFF_X % 16 == 0 && OFF_BAR % 8 == 0, "alignment");
+constexpr int OFF_BAR = OFF_X + 2 * LAYER_NODES * 3 * 4;  // 2 mbarriers + TMEM address
+constexpr int SMEM_BYTES = OFF_BAR + 24;
+constexpr int SMEM_ALLOC = SMEM_BYTES + 128;              // room to align the base
+static_assert(NT * YS * 4 <= A_SET, "Y staging must fit in one A set");
+static_assert(OFF_B % 128 == 0 && OFF_X % 16 == 0 && OFF_BAR % 8 == 0, "alignment");
 
 // instruction descriptor, kind::tf32: D FP32 (bits 4-5 = 1), A and B TF32 (bits 7-9 and
 // 10-12 = 2), both K-major (bits 15, 16 = 0), N >> 3 at bits 17-22, M >> 4 at bits 24-28
@@ -136,9 +143,12 @@ __device__ __forceinline__ void tmem_ld24(uint32_t taddr, float* v) {
   for (int i = 0; i < 24; i++) v[i] = __uint_as_float(r[i]);
 }
 
-// one node layer of the tile: masked displacements of up to two nodes per thread
+// one node layer of the tile: displacements and mask bits of up to two nodes per thread.  The
+// loads are independent (the mask is applied when the layer is stored), so a prefetch issued
+// at the top of a layer step never stalls the thread before the values are needed.
 struct XPre {
   float v[2][3];
+  unsigned m[2];
 };
 
 __device__ __forceinline__ void x_fetch(XPre& p, int kk, int EX0, int EY0, int nx, int ny, int nz,
@@ -148,13 +158,14 @@ __device__ __forceinline__ void x_fetch(XPre& p, int kk, int EX0, int EY0, int n
   for (int h = 0; h < 2; h++) {
     const int q = threadIdx.x + h * NT;
     p.v[h][0] = p.v[h][1] = p.v[h][2] = 0.f;
+    p.m[h] = 7u;
     if (q < LAYER_NODES) {
       const int gi = EX0 + q % TNX, gj = EY0 + q / TNX;
       if (gi >= 0 && gi <= nx && gj >= 0 && gj <= ny && kk >= 0 && kk <= nz) {
         const int64_t node = node_id(gi, gj, kk, nx, ny);
-        const unsigned m = __ldg(mask + node);
+        p.m[h] = __ldg(mask + node);
 #pragma unroll
-        for (int c = 0; c < 3; c++) p.v[h][c] = ((m >> c) & 1u) ? 0.f : __ldg(x + 3 * node + c);
+        for (int c = 0; c < 3; c++) p.v[h][c] = __ldg(x + 3 * node + c);
       }
     }
   }
@@ -166,8 +177,34 @@ __device__ __forceinline__ void x_store(const XPre& p, float* sx) {
     const int q = threadIdx.x + h * NT;
     if (q < LAYER_NODES) {
 #pragma unroll
-      for (int c = 0; c < 3; c++) sx[3 * q + c] = p.v[h][c];
+      for (int c = 0; c < 3; c++) sx[3 * q + c] = ((p.m[h] >> c) & 1u) ? 0.f : p.v[h][c];
     }
+  }
+}
+
+// what finishing an owned node needs besides its sum: x (unmasked), mask, b, block inverse
+struct FinData {
+  float x[3], b[3], D[9];
+  unsigned m;
+};
+
+template <int MODE>
+__device__ __forceinline__ void fin_fetch(FinData& f, bool valid, int64_t node,
+                                          const uint8_t* __restrict__ mask,
+                                          const float* __restrict__ x,
+                                          const float* __restrict__ b,
+                                          const float* __restrict__ Dinv) {
+  if (!valid) return;
+  f.m = __ldg(mask + node);
+#pragma unroll
+  for (int c = 0; c < 3; c++) f.x[c] = __ldg(x + 3 * node + c);
+  if (MODE != MODE_APPLY) {
+#pragma unroll
+    for (int c = 0; c < 3; c++) f.b[c] = __ldg(b + 3 * node + c);
+  }
+  if (MODE == MODE_JACOBI) {
+#pragma unroll
+    for (int c = 0; c < 9; c++) f.D[c] = __ldg(Dinv + 9 * node + c);
   }
 }
 
@@ -178,8 +215,57 @@ __device__ __forceinline__ float e_fetch(int ke, int EX0, int EY0, int nx, int n
   return __ldg(E + ge + (int64_t)nx * (gf + (int64_t)ny * ke));
 }
 
+// element layer ke of the tile -> A operands (TF32 hi and lo rows) of buffer A, from the ring
+// slots of node layers ke (bottom, local nodes 0-3) and ke + 1 (top, local nodes 4-7)
+__device__ __forceinline__ void build_a(uint8_t* A, const float* s0, const float* s1, int ex,
+                                        int ey, int mt, int row) {
+  uint8_t* Ahi = A + mt * A_BYTES;
+  uint8_t* Alo = A + (2 + mt) * A_BYTES;
+#pragma unroll
+  for (int kc = 0; kc < 6; kc++) {
+    uint32_t hi[4], lo[4];
+#pragma unroll
+    for (int q = 0; q < 4; q++) {
+      const int k = 4 * kc + q, bn = k / 3, c = k % 3;
+      const float* sx = (bn & 4) ? s1 : s0;
+      const float v = sx[3 * ((ey + ((bn >> 1) & 1)) * TNX + ex + (bn & 1)) + c];
+      hi[q] = tf32_round_bits(__float_as_uint(v));
+      lo[q] = __float_as_uint(v - __uint_as_float(hi[q]));
+    }
+    const int off = op_off(row, 4 * kc);
+    *reinterpret_cast<uint4*>(Ahi + off) = make_uint4(hi[0], hi[1], hi[2], hi[3]);
+    *reinterpret_cast<uint4*>(Alo + off) = make_uint4(lo[0], lo[1], lo[2], lo[3]);
+  }
+}
+
+// 2 M-tiles x 3 split products x 3 K-steps into the accumulators at column d, then a commit
+// to the barrier (executed by one thread)
+__device__ __forceinline__ void issue_mmas(uint32_t d, uint32_t abase, uint32_t bbase,
+                                           uint32_t bar) {
+  asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
+#pragma unroll
+  for (int m = 0; m < 2; m++) {
+    const uint32_t ahi = abase + m * A_BYTES, alo = abase + (2 + m) * A_BYTES;
+#pragma unroll
+    for (int p = 0; p < 3; p++) {
+      const uint32_t a = (p == 1) ? alo : ahi;
+      const uint32_t bb = (p == 2) ? bbase + B_BYTES : bbase;
+#pragma unroll
+      for (int s = 0; s < 3; s++)
+        mma_tf32(d + (uint32_t)(m * NB), sdesc(a + 2 * LBO * s), sdesc(bb + 2 * LBO * s),
+                 (p | s) ? 1u : 0u);
+    }
+  }
+  asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];\n"
+               :: "r"(bar) : "memory");
+}
+
+// Two-stage software pipeline over the element layers: while the tensor cores run the MMAs of
+// layer ke (A buffer and accumulators ke & 1), the threads finish layer ke - 1 (accumulators,
+// staging in the other A buffer, node sums, output).  The ring of node layers is refilled one
+// layer ahead from registers, so no global-memory latency sits between two layers' MMAs.
 template <int MODE>
-__global__ void __launch_bounds__(NT, 3)
+__global__ void __launch_bounds__(NT, 2)
 k_ebe3tc(int nx, int ny, int nz, int nz_tile, const uint4* __restrict__ Bimg,
          const float* __restrict__ E, const uint8_t* __restrict__ mask,
          const float* __restrict__ x, float* __restrict__ y, const float* __restrict__ b,
@@ -187,27 +273,27 @@ k_ebe3tc(int nx, int ny, int nz, int nz_tile, const uint4* __restrict__ Bimg,
   extern __shared__ uint8_t smem_raw[];
   pdl_prologue();
   if (solve_done(done)) return;
-  uint8_t* sm = smem_raw + ((1024 - (smem_u32(smem_raw) & 1023u)) & 1023u);
+  uint8_t* sm = smem_raw + ((128 - (smem_u32(smem_raw) & 127u)) & 127u);
   float* sxr = reinterpret_cast<float*>(sm + OFF_X);      // [2][LAYER_NODES][3]
-  float* sY = reinterpret_cast<float*>(sm + OFF_A);       // [NT][YS] (after the MMAs)
-  uint64_t* bar = reinterpret_cast<uint64_t*>(sm + OFF_BAR);
-  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(sm + OFF_BAR + 8);
+  uint64_t* bar = reinterpret_cast<uint64_t*>(sm + OFF_BAR);  // [2]
+  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(sm + OFF_BAR + 16);
   const uint32_t sbase = smem_u32(sm);
-  const uint32_t bar_a = smem_u32(bar);
+  const uint32_t bar_a[2] = {smem_u32(bar), smem_u32(bar + 1)};
   const int tid = threadIdx.x, warp = tid >> 5;
 
   const int EX0 = blockIdx.x * ONX - 1, EY0 = blockIdx.y * ONY - 1;
   const int k0 = blockIdx.z * nz_tile;
   const int k1 = min(k0 + nz_tile, nz + 1);  // owned node layers [k0, k1)
 
-  // tensor memory (one warp), the MMA barrier, the B operands
+  // tensor memory (one warp), the MMA barriers, the B operands
   if (warp == 0) {
     asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;\n"
                  :: "r"(smem_u32(tmem_slot)), "r"(TMEM_COLS) : "memory");
     asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;\n" ::: "memory");
   }
   if (tid == 0) {
-    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;\n" :: "r"(bar_a), "r"(1) : "memory");
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;\n" :: "r"(bar_a[0]), "r"(1) : "memory");
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;\n" :: "r"(bar_a[1]), "r"(1) : "memory");
     asm volatile("fence.mbarrier_init.release.cluster;\n" ::: "memory");
   }
   for (int t = tid; t < 2 * B_BYTES / 16; t += NT)
@@ -218,160 +304,125 @@ k_ebe3tc(int nx, int ny, int nz, int nz_tile, const uint4* __restrict__ Bimg,
   const int onx = tid % ONX + 1, ony = tid / ONX + 1;        // local node of the layer tile
   const int gi = EX0 + onx, gj = EY0 + ony;
   const bool in_plane = owner && gi <= nx && gj <= ny;
+  const int ex = tid % TEX, ey = tid / TEX;
+  const int mt = tid >> 7, row = tid & 127;
 
   XPre pre;
   x_fetch(pre, k0 - 1, EX0, EY0, nx, ny, nz, mask, x);
   x_store(pre, sxr + ((k0 - 1) & 1) * LAYER_NODES * 3);
   x_fetch(pre, k0, EX0, EY0, nx, ny, nz, mask, x);
   x_store(pre, sxr + (k0 & 1) * LAYER_NODES * 3);
-  float ev = e_fetch(k0 - 1, EX0, EY0, nx, ny, nz, E);
+  x_fetch(pre, k0 + 1, EX0, EY0, nx, ny, nz, mask, x);  // stored after layer k0 - 1 is built
+  float e_cur = e_fetch(k0 - 1, EX0, EY0, nx, ny, nz, E);  // modulus of element layer ke
+  float e_prev = 0.f;                                      // ... of layer ke - 1
   asm volatile("tcgen05.fence::before_thread_sync;\n" ::: "memory");
   __syncthreads();
   asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
   const uint32_t tmem = *tmem_slot;
 
-  float acc[3] = {0.f, 0.f, 0.f};  // node layer ke: contributions gathered so far
-  uint32_t parity = 0;
+  float acc[3] = {0.f, 0.f, 0.f};  // node layer ke - 1: contributions gathered so far
+  FinData fd;                      // finishing data of node layer ke - 1
+  uint32_t parity = 0;             // bit j: phase of barrier j to wait for next
   bool failed = false;
-  const int ex = tid % TEX, ey = tid / TEX;
-  const int mt = tid >> 7, row = tid & 127;
 
-  for (int ke = k0 - 1; ke < k1; ke++) {
-    const float Ee = ev;  // modulus of this thread's element in layer ke
-    // prefetch: node layer ke + 2 and element layer ke + 1 (registers, stored at the end)
-    const bool more = ke + 2 <= k1;
-    if (more) x_fetch(pre, ke + 2, EX0, EY0, nx, ny, nz, mask, x);
-    if (ke + 1 < k1) ev = e_fetch(ke + 1, EX0, EY0, nx, ny, nz, E);
-    // finishing data of node layer ke (owned nodes), fetched ahead of the MMAs
-    float xi[3] = {0.f, 0.f, 0.f}, bi[3] = {0.f, 0.f, 0.f}, Di[9];
-    unsigned mi = 0;
-    const bool fin = in_plane && ke >= k0;
-    int64_t node = 0;
-    if (fin) {
-      node = node_id(gi, gj, ke, nx, ny);
-      mi = __ldg(mask + node);
-#pragma unroll
-      for (int c = 0; c < 3; c++) xi[c] = __ldg(x + 3 * node + c);
-      if (MODE != MODE_APPLY) {
-#pragma unroll
-        for (int c = 0; c < 3; c++) bi[c] = __ldg(b + 3 * node + c);
-      }
-      if (MODE == MODE_JACOBI) {
-#pragma unroll
-        for (int c = 0; c < 9; c++) Di[c] = __ldg(Dinv + 9 * node + c);
-      }
-    }
-
-    // A operand rows: this thread's element, local nodes bn = dx + 2 dy + 4 dz
-    {
-      const float* s0 = sxr + (ke & 1) * LAYER_NODES * 3;
-      const float* s1 = sxr + ((ke + 1) & 1) * LAYER_NODES * 3;
-      uint8_t* Ahi = sm + OFF_A + mt * A_BYTES;
-      uint8_t* Alo = sm + OFF_A + (2 + mt) * A_BYTES;
-#pragma unroll
-      for (int kc = 0; kc < 6; kc++) {
-        uint32_t hi[4], lo[4];
-#pragma unroll
-        for (int q = 0; q < 4; q++) {
-          const int k = 4 * kc + q, bn = k / 3, c = k % 3;
-          const float* sx = (bn & 4) ? s1 : s0;
-          const float v = sx[3 * ((ey + ((bn >> 1) & 1)) * TNX + ex + (bn & 1)) + c];
-          hi[q] = tf32_round_bits(__float_as_uint(v));
-          lo[q] = __float_as_uint(v - __uint_as_float(hi[q]));
-        }
-        const int off = op_off(row, 4 * kc);
-        *reinterpret_cast<uint4*>(Ahi + off) = make_uint4(hi[0], hi[1], hi[2], hi[3]);
-        *reinterpret_cast<uint4*>(Alo + off) = make_uint4(lo[0], lo[1], lo[2], lo[3]);
-      }
-    }
+  for (int ke = k0 - 1; ke <= k1; ke++) {
+    const bool mma_now = ke < k1;  // the last step only finishes layer k1 - 1
+    const int j = ke & 1;
+    if (mma_now)
+      build_a(sm + OFF_A + j * A_SET, sxr + j * LAYER_NODES * 3,
+              sxr + (j ^ 1) * LAYER_NODES * 3, ex, ey, mt, row);
     asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory");
     __syncthreads();
+    if (mma_now && tid == 0)
+      issue_mmas(tmem + (uint32_t)(j * 2 * NB), sbase + OFF_A + j * A_SET, sbase + OFF_B,
+                 bar_a[j]);
+    // refill the ring: node layer ke + 2 replaces layer ke (read by the build above)
+    if (mma_now && ke + 2 <= k1) {
+      x_store(pre, sxr + j * LAYER_NODES * 3);
+      if (ke + 3 <= k1) x_fetch(pre, ke + 3, EX0, EY0, nx, ny, nz, mask, x);
+    }
+    const float e_next = (ke + 1 < k1) ? e_fetch(ke + 1, EX0, EY0, nx, ny, nz, E) : 0.f;
 
-    if (tid == 0) {
+    // finishing data of node layer ke, used one step later
+    FinData fd_next;
+    const bool fin_next = in_plane && ke >= k0 && ke < k1;
+    fin_fetch<MODE>(fd_next, fin_next, node_id(gi, gj, ke, nx, ny), mask, x, b, Dinv);
+
+    if (ke >= k0) {
+      // finish element layer ke - 1 and node layer ke - 1
+      const int jp = j ^ 1;
+      const int kn = ke - 1;  // node layer finished now
+      const bool fin = in_plane && kn >= k0;
+      const int64_t node = node_id(gi, gj, kn, nx, ny);
+      const bool ok = mbar_wait(bar_a[jp], (parity >> jp) & 1u);
+      parity ^= 1u << jp;
+      if (__syncthreads_or(!ok)) {
+        failed = true;
+        break;
+      }
       asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
+      {
+        float v[24];
+        tmem_ld24(tmem + ((uint32_t)(32 * (warp & 3)) << 16) + (uint32_t)(jp * 2 * NB + mt * NB), v);
+        float* sY = reinterpret_cast<float*>(sm + OFF_A + jp * A_SET);  // A buffer of layer ke-1
 #pragma unroll
-      for (int m = 0; m < 2; m++) {
-        const uint32_t d = tmem + (uint32_t)(m * NB);
-        const uint32_t ahi = sbase + OFF_A + m * A_BYTES, alo = sbase + OFF_A + (2 + m) * A_BYTES;
-        const uint32_t bhi = sbase + OFF_B, blo = sbase + OFF_B + B_BYTES;
-#pragma unroll
-        for (int p = 0; p < 3; p++) {
-          const uint32_t a = (p == 1) ? alo : ahi;
-          const uint32_t bb = (p == 2) ? blo : bhi;
-#pragma unroll
-          for (int s = 0; s < 3; s++)
-            mma_tf32(d, sdesc(a + 2 * LBO * s), sdesc(bb + 2 * LBO * s), (p | s) ? 1u : 0u);
-        }
+        for (int n = 0; n < 24; n++) sY[tid * YS + n] = e_prev * v[n];
       }
-      asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];\n"
-                   :: "r"(bar_a) : "memory");
-    }
-    const bool ok = mbar_wait(bar_a, parity);
-    parity ^= 1u;
-    if (__syncthreads_or(!ok)) {
-      failed = true;
-      break;
-    }
-    asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
-
-    // accumulator row of this thread's element -> E_e-scaled contributions in shared memory
-    {
-      float v[24];
-      tmem_ld24(tmem + ((uint32_t)(32 * (warp & 3)) << 16) + (uint32_t)(mt * NB), v);
+      asm volatile("tcgen05.fence::before_thread_sync;\n" ::: "memory");
+      __syncthreads();
+      if (owner) {
+        const float* sY = reinterpret_cast<const float*>(sm + OFF_A + jp * A_SET);
+        // elements (onx-1+dxe, ony-1+dye) of layer ke - 1; the node is their local node
+        // (1-dxe) + 2(1-dye) at the bottom (dz = 0) or + 4 at the top (dz = 1)
+        float top[3] = {0.f, 0.f, 0.f};
 #pragma unroll
-      for (int n = 0; n < 24; n++) sY[tid * YS + n] = Ee * v[n];
-    }
-    asm volatile("tcgen05.fence::before_thread_sync;\n" ::: "memory");
-    __syncthreads();
-
-    if (owner) {
-      // elements (onx-1+ex', ony-1+ey') of this layer; the node is their local node
-      // (1-ex') + 2(1-ey') at the bottom (dz = 0) or + 4 at the top (dz = 1)
-      float top[3] = {0.f, 0.f, 0.f};
+        for (int q = 0; q < 4; q++) {
+          const int dxe = q & 1, dye = q >> 1;
+          const float* Ye = sY + ((ony - 1 + dye) * TEX + onx - 1 + dxe) * YS;
+          const int bn = (1 - dxe) + 2 * (1 - dye);
 #pragma unroll
-      for (int q = 0; q < 4; q++) {
-        const int dxe = q & 1, dye = q >> 1;
-        const float* Ye = sY + ((ony - 1 + dye) * TEX + onx - 1 + dxe) * YS;
-        const int bn = (1 - dxe) + 2 * (1 - dye);
-#pragma unroll
-        for (int c = 0; c < 3; c++) {
-          acc[c] += Ye[3 * bn + c];
-          top[c] += Ye[3 * (bn + 4) + c];
-        }
-      }
-      if (fin) {
-        float Ax[3];
-#pragma unroll
-        for (int c = 0; c < 3; c++) Ax[c] = ((mi >> c) & 1u) ? xi[c] : acc[c];
-        if (MODE == MODE_APPLY) {
-#pragma unroll
-          for (int c = 0; c < 3; c++) y[3 * node + c] = Ax[c];
-        } else {
-          float r[3];
-#pragma unroll
-          for (int c = 0; c < 3; c++) r[c] = bi[c] - Ax[c];
-          if (MODE == MODE_RESID) {
-#pragma unroll
-            for (int c = 0; c < 3; c++) y[3 * node + c] = r[c];
-          } else {
-#pragma unroll
-            for (int c = 0; c < 3; c++)
-              y[3 * node + c] =
-                  xi[c] + omega * (Di[3 * c] * r[0] + Di[3 * c + 1] * r[1] + Di[3 * c + 2] * r[2]);
+          for (int c = 0; c < 3; c++) {
+            acc[c] += Ye[3 * bn + c];
+            top[c] += Ye[3 * (bn + 4) + c];
           }
         }
-      }
+        if (fin) {
+          float Ax[3];
 #pragma unroll
-      for (int c = 0; c < 3; c++) acc[c] = top[c];
+          for (int c = 0; c < 3; c++) Ax[c] = ((fd.m >> c) & 1u) ? fd.x[c] : acc[c];
+          if (MODE == MODE_APPLY) {
+#pragma unroll
+            for (int c = 0; c < 3; c++) y[3 * node + c] = Ax[c];
+          } else {
+            float r[3];
+#pragma unroll
+            for (int c = 0; c < 3; c++) r[c] = fd.b[c] - Ax[c];
+            if (MODE == MODE_RESID) {
+#pragma unroll
+              for (int c = 0; c < 3; c++) y[3 * node + c] = r[c];
+            } else {
+#pragma unroll
+              for (int c = 0; c < 3; c++)
+                y[3 * node + c] = fd.x[c] + omega * (fd.D[3 * c] * r[0] + fd.D[3 * c + 1] * r[1] +
+                                                     fd.D[3 * c + 2] * r[2]);
+            }
+          }
+        }
+#pragma unroll
+        for (int c = 0; c < 3; c++) acc[c] = top[c];
+      }
     }
-    if (more) x_store(pre, sxr + (ke & 1) * LAYER_NODES * 3);
+    e_prev = e_cur;
+    e_cur = e_next;
+    fd = fd_next;
     __syncthreads();
   }
 
-  if (failed && tid == 0) atomicExch(&g_tc_error, 1);
   if (failed) {
+    if (tid == 0) atomicExch(&g_tc_error, 1);
     // let MMAs still in flight finish (bounded) before the tensor memory is released
-    mbar_wait(bar_a, parity ^ 1u);
+    mbar_wait(bar_a[0], parity & 1u);
+    mbar_wait(bar_a[1], (parity >> 1) & 1u);
   }
   asm volatile("tcgen05.fence::before_thread_sync;\n" ::: "memory");
   __syncthreads();
@@ -428,6 +479,52 @@ void ebe3d_tc_launch(cudaStream_t s, int mode, const Ebe& op, const float* x, fl
   if (mode == MODE_APPLY) launch_mode<MODE_APPLY>(s, op, x, y, b, Dinv, omega, done);
   else if (mode == MODE_RESID) launch_mode<MODE_RESID>(s, op, x, y, b, Dinv, omega, done);
   else launch_mode<MODE_JACOBI>(s, op, x, y, b, Dinv, omega, done);
+}
+
+// fastest node-layer count per block for this grid: each candidate timed on the stream with
+// scratch vectors the first time a grid shape is seen, cached per shape afterwards
+int ebe3d_tc_autotune(cudaStream_t s, const Ebe& op, const float* Dinv) {
+  static std::mutex mu;
+  static std::map<std::tuple<int, int, int>, int> cache;
+  const auto key = std::make_tuple(op.nx, op.ny, op.nz);
+  {
+    std::lock_guard<std::mutex> g(mu);
+    auto it = cache.find(key);
+    if (it != cache.end()) return it->second;
+  }
+  const int64_t n = 3 * (int64_t)(op.nx + 1) * (op.ny + 1) * (op.nz + 1);
+  DBuf<float> x, y, b;
+  x.resize(n);
+  y.resize(n);
+  b.resize(n);
+  x.zero(s);
+  b.zero(s);
+  cudaEvent_t e0, e1;
+  CK(cudaEventCreate(&e0));
+  CK(cudaEventCreate(&e1));
+  int best = 8;
+  float best_ms = 1e30f;
+  for (int nzt : {8, 4, 16, 32}) {
+    if (nzt > 8 && nzt / 2 >= op.nz + 1) break;  // no more blocks to split off
+    Ebe o = op;
+    o.tc_nz = nzt;
+    launch_mode<MODE_JACOBI>(s, o, x.p, y.p, b.p, Dinv, 0.5, nullptr);
+    CK(cudaEventRecord(e0, s));
+    for (int r = 0; r < 5; r++) launch_mode<MODE_JACOBI>(s, o, x.p, y.p, b.p, Dinv, 0.5, nullptr);
+    CK(cudaEventRecord(e1, s));
+    CK(cudaEventSynchronize(e1));
+    float ms = 0.f;
+    CK(cudaEventElapsedTime(&ms, e0, e1));
+    if (ms < 0.97f * best_ms) {
+      best_ms = ms;
+      best = nzt;
+    }
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  std::lock_guard<std::mutex> g(mu);
+  cache[key] = best;
+  return best;
 }
 
 // reads and clears the error word of the tensor-core kernel (synchronises the stream)

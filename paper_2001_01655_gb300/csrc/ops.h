@@ -50,6 +50,8 @@ void ebe3d_tc_launch(cudaStream_t s, int mode, const Ebe& op, const float* x, fl
 // Ke (24 x 24, FP64) -> TF32 hi and lo B-operand images in the kernel's shared-memory layout
 void ebe3d_tc_operand(const double* Ke, uint32_t* img);
 int ebe3d_tc_operand_words();
+// fastest node layers per block (tc_nz) for this grid, timed once per grid shape and cached
+int ebe3d_tc_autotune(cudaStream_t s, const Ebe& op, const float* Dinv);
 // true if a tensor-core kernel gave up waiting for its MMAs since the last call (syncs s)
 bool ebe3d_tc_error(cudaStream_t s);
 // point-block diagonal inverse of the level-0 operator, FP64 and FP32 copies

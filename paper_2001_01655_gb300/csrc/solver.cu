@@ -634,6 +634,10 @@ void setup(tomg_problem* P, const tomg_options& opt) {
     ebe_block_diag_inv(s, V<double>::ebe(P), L0->D64.p, L0->D32.p);
     if (P->dim == 2 && opt.prec != TOMG_PREC_FP64 && P->ebe_tile == 0)
       P->ebe_tile = ebe2d_autotune(s, V<float>::ebe(P), L0->D32.p);
+    if (P->dim == 3 && opt.prec == TOMG_PREC_3XTF32_VCYCLE && P->tc_nz == 0 && P->Ketc.p) {
+      TcScope tcs(P, TOMG_PREC_3XTF32_VCYCLE);
+      P->tc_nz = ebe3d_tc_autotune(s, V<float>::ebe(P), L0->D32.p);
+    }
     P->L.push_back(std::move(L0));
   }
   tr.mark("level0 diag", 0);
