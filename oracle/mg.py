@@ -14,8 +14,21 @@ Hierarchies
   hybrid  n_geo geometric levels, then smoothed aggregation from the last geometric operator
           with rigid-body modes evaluated at that level's node coordinates (Sec. 4.3, 4.4)
 
+Smoothers
+  jacobi     weighted point-block Jacobi x + w D^-1 (b - A x), n_pre / n_post sweeps
+  chebyshev  point-block-Jacobi-preconditioned Chebyshev polynomial of degree m (the paper
+             studies a Chebyshev smoother beside Jacobi, Sec. 4.1; its SOR preconditioning is a
+             sequential sweep and is replaced by the point-block diagonal).  The polynomial is
+             the Chebyshev polynomial of D^-1 A on [lower, upper] * lambda, lambda from 20
+             power iterations (the estimate also used to smooth AMG prolongators), written as
+             the three-term recurrence of Chebyshev acceleration (Saad, Iterative Methods for
+             Sparse Linear Systems, 2nd ed., Alg. 12.1).  Pre- and post-smoothing use the same
+             polynomial, so the cycle stays symmetric.
+
 Parity: pinned (tests/test_oracle_mg.py: symmetric preconditioner, contraction < 1,
-exactness of a one-level cycle, iteration counts bounded under refinement).
+exactness of a one-level cycle, iteration counts bounded under refinement; the Chebyshev
+smoother's error propagation equals the scaled Chebyshev polynomial evaluated by
+numpy.polynomial.chebyshev on every eigenvector of D^-1 A).
 """
 from __future__ import annotations
 
@@ -37,7 +50,12 @@ class Hierarchy:
     n_pre: int = 1
     n_post: int = 1
     block: bool = True
+    smoother: str = "jacobi"      # or "chebyshev"
+    cheb_degree: int = 2
+    cheb_lower: float = 0.1       # interval [lower, upper] * lambda(D^-1 A)
+    cheb_upper: float = 1.1
     Dinv: list = field(default_factory=list)
+    lam: list = field(default_factory=list)
     chol: object = None
     info: dict = field(default_factory=dict)
 
@@ -45,6 +63,10 @@ class Hierarchy:
         self.Dinv = []
         for A, b in zip(self.A, self.bs):
             self.Dinv.append(amg.block_diag_inv(A, b if self.block else 1))
+        self.lam = []
+        if self.smoother == "chebyshev":
+            for l in range(self.n_levels - 1):
+                self.lam.append(amg.spectral_radius_DinvA(self.A[l], self.Dinv[l], l))
         Ac = self.A[-1].toarray()
         self.chol = sla.cho_factor(Ac, lower=True)
         return self
@@ -59,19 +81,66 @@ def smooth(H, l, x, b):
     return x + H.omega * amg.apply_block_diag(H.Dinv[l], b - H.A[l] @ x)
 
 
+def chebyshev_coefficients(lam_lo, lam_hi, m):
+    """Step coefficients of Chebyshev acceleration on [lam_lo, lam_hi] (Saad, Alg. 12.1):
+    d_0 = c2_0 D^-1 r_0 and d_k = c1_k d_{k-1} + c2_k D^-1 r_k, with theta = centre,
+    delta = half width, sigma = theta / delta, rho_0 = 1 / sigma,
+    rho_k = 1 / (2 sigma - rho_{k-1}), c1_k = rho_k rho_{k-1}, c2_k = 2 rho_k / delta."""
+    theta = 0.5 * (lam_hi + lam_lo)
+    delta = 0.5 * (lam_hi - lam_lo)
+    sigma = theta / delta
+    rho = 1.0 / sigma
+    c1, c2 = [0.0], [1.0 / theta]
+    for _ in range(1, m):
+        rho_new = 1.0 / (2.0 * sigma - rho)
+        c1.append(rho_new * rho)
+        c2.append(2.0 * rho_new / delta)
+        rho = rho_new
+    return c1, c2
+
+
+def chebyshev_smooth(A, Dinv, x, b, lam_lo, lam_hi, m):
+    """m steps of Chebyshev acceleration for A x = b preconditioned by the point-block
+    diagonal: x_{k+1} = x_k + d_k, d_k from the residual r_k = b - A x_k (m applies of A)."""
+    c1, c2 = chebyshev_coefficients(lam_lo, lam_hi, m)
+    d = np.zeros_like(x)
+    for k in range(m):
+        r = b - A @ x
+        d = c1[k] * d + c2[k] * amg.apply_block_diag(Dinv, r)
+        x = x + d
+    return x
+
+
+def presmooth(H, l, b):
+    if H.smoother == "chebyshev":
+        lam = H.lam[l]
+        return chebyshev_smooth(H.A[l], H.Dinv[l], np.zeros_like(b), b, H.cheb_lower * lam,
+                                H.cheb_upper * lam, H.cheb_degree)
+    x = np.zeros_like(b)
+    for _ in range(H.n_pre):
+        x = smooth(H, l, x, b)
+    return x
+
+
+def postsmooth(H, l, x, b):
+    if H.smoother == "chebyshev":
+        lam = H.lam[l]
+        return chebyshev_smooth(H.A[l], H.Dinv[l], x, b, H.cheb_lower * lam, H.cheb_upper * lam,
+                                H.cheb_degree)
+    for _ in range(H.n_post):
+        x = smooth(H, l, x, b)
+    return x
+
+
 def vcycle(H, b, l=0):
     """V-cycle multigrid, Algorithm 1 (reading stated in the module docstring)."""
     if l == H.n_levels - 1:
         return sla.cho_solve(H.chol, b)
     A = H.A[l]
-    x = np.zeros_like(b)
-    for _ in range(H.n_pre):
-        x = smooth(H, l, x, b)
+    x = presmooth(H, l, b)
     bc = H.P[l].T @ (b - A @ x)
     x = x + H.P[l] @ vcycle(H, bc, l + 1)
-    for _ in range(H.n_post):
-        x = smooth(H, l, x, b)
-    return x
+    return postsmooth(H, l, x, b)
 
 
 def fine_operator(problem):

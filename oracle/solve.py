@@ -21,8 +21,9 @@ def direct(problem):
 
 
 def build(problem, pc="gmg", n_levels=None, cap=None, n_geo=None, beta=0.003, omega=0.5,
-          A0=None):
-    kw = dict(omega=omega)
+          A0=None, smoother="jacobi", cheb_degree=2, cheb_lower=0.1, cheb_upper=1.1):
+    kw = dict(omega=omega, smoother=smoother, cheb_degree=cheb_degree, cheb_lower=cheb_lower,
+              cheb_upper=cheb_upper)
     if pc == "gmg":
         return mg.build_gmg(problem, n_levels=n_levels, cap=cap, A0=A0, **kw)
     if pc == "amg":

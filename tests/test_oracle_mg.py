@@ -7,18 +7,19 @@ import workloads as W
 from oracle import fem, gmg, krylov, mg, solve
 
 
-def _hier(kind, p):
+def _hier(kind, p, **kw):
     if kind == "gmg":
-        return solve.build(p, pc="gmg", n_levels=3)
+        return solve.build(p, pc="gmg", n_levels=3, **kw)
     if kind == "amg":
-        return solve.build(p, pc="amg", cap=60)
-    return solve.build(p, pc="hybrid", n_geo=2, cap=60)
+        return solve.build(p, pc="amg", cap=60, **kw)
+    return solve.build(p, pc="hybrid", n_geo=2, cap=60, **kw)
 
 
 @pytest.mark.parametrize("kind", ["gmg", "amg", "hybrid"])
-def test_vcycle_symmetric_and_contracting(kind):
+@pytest.mark.parametrize("smoother", ["jacobi", "chebyshev"])
+def test_vcycle_symmetric_and_contracting(kind, smoother):
     p = W.random_problem(2, 16, 8, seed=8, contrast="minmax")
-    H = _hier(kind, p)
+    H = _hier(kind, p, smoother=smoother)
     A = H.A[0]
     n = A.shape[0]
     rng = np.random.default_rng(0)
@@ -124,3 +125,63 @@ def test_patch_test_through_pcg(dim):
     for c in range(1, dim):
         ex[:, c] = -0.3 * X[:, c]
     assert np.allclose(r["u"][0].reshape(-1, dim), ex, atol=1e-9)
+
+
+def _small_spd_with_blocks():
+    p = W.random_problem(2, 6, 4, seed=17, contrast="minmax")
+    A = mg.fine_operator(p)
+    from oracle import amg
+    Dinv = amg.block_diag_inv(A, 2)
+    return A, Dinv
+
+
+@pytest.mark.parametrize("m", [1, 2, 3, 5])
+def test_chebyshev_error_is_scaled_chebyshev_polynomial(m):
+    """Error propagation of m Chebyshev steps: e_m = p_m(D^-1 A) e_0 with
+    p_m(t) = T_m((theta - t) / delta) / T_m(theta / delta) (the defining property of Chebyshev
+    acceleration on [a, b]).  On every generalized eigenvector A v = lam D v the smoother must
+    scale v by p_m(lam); T_m is evaluated by numpy's Chebyshev series routine.  A dropped term,
+    a wrong sign or an index slip in the recurrence changes p_m."""
+    import scipy.linalg as sla
+    from numpy.polynomial import chebyshev as C
+    A, Dinv = _small_spd_with_blocks()
+    Ad = A.toarray()
+    n = Ad.shape[0]
+    D = np.zeros_like(Ad)
+    for i in range(0, n, 2):
+        D[i:i + 2, i:i + 2] = np.linalg.inv(Dinv[i // 2])
+    lam, V = sla.eigh(Ad, D)
+    a, b = 0.1 * lam.max(), 1.1 * lam.max()
+    theta, delta = 0.5 * (a + b), 0.5 * (b - a)
+    Tm = np.zeros(m + 1)
+    Tm[m] = 1.0
+    p = C.chebval((theta - lam) / delta, Tm) / C.chebval(theta / delta, Tm)
+    for i in range(0, n, max(1, n // 12)):
+        v = V[:, i]
+        out = mg.chebyshev_smooth(A, Dinv, v.copy(), np.zeros(n), a, b, m)
+        assert np.allclose(out, p[i] * v, rtol=0, atol=1e-11 * np.abs(v).max()), (m, i)
+    # on [a, b] the polynomial is bounded by 1 / T_m(theta / delta)
+    inside = (lam >= a) & (lam <= b)
+    assert np.all(np.abs(p[inside]) <= 1.0 / C.chebval(theta / delta, Tm) + 1e-12)
+
+
+def test_chebyshev_degree_one_is_weighted_jacobi():
+    A, Dinv = _small_spd_with_blocks()
+    from oracle import amg
+    rng = np.random.default_rng(3)
+    x, b = rng.standard_normal(A.shape[0]), rng.standard_normal(A.shape[0])
+    lo, hi = 0.3, 3.7  # theta = 2: weight 1/2
+    ref = x + 0.5 * amg.apply_block_diag(Dinv, b - A @ x)
+    assert np.allclose(mg.chebyshev_smooth(A, Dinv, x, b, lo, hi, 1), ref, rtol=1e-14, atol=1e-14)
+
+
+@pytest.mark.parametrize("case", ["mbb", "rand"])
+def test_chebyshev_vcycle_cuts_iterations(case):
+    """A degree-2 Chebyshev smoother is a stronger smoother than one Jacobi sweep: PCG needs
+    fewer iterations (18 -> 10 on the MBB beam, 19 -> 11 on the random design)."""
+    p = W.mbb_beam(96, 32) if case == "mbb" else W.random_problem(2, 64, 32, seed=5,
+                                                                   contrast="minmax")
+    rj = solve.solve(p, pc="gmg", n_levels=4)
+    rc = solve.solve(p, pc="gmg", n_levels=4, smoother="chebyshev", cheb_degree=2)
+    assert rc["rel_residual"][0] <= 1e-8 and rj["rel_residual"][0] <= 1e-8
+    assert rc["iterations"][0] < rj["iterations"][0]
