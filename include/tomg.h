@@ -68,7 +68,10 @@ typedef struct {
   int n_levels;        /* GMG levels incl. the fine grid; 0 = from max_coarse_dofs  0       */
   int max_coarse_dofs; /* coarsest level has fewer DOFs than this                   2000    */
   int n_geo_levels;    /* hybrid: geometric levels incl. the fine grid             3        */
-  int smoother;        /* 0 = weighted point-block Jacobi (Sec. 4.1)               0        */
+  int smoother;        /* 0 = weighted point-block Jacobi (Sec. 4.1); 1 = point-block
+                          Jacobi-preconditioned Chebyshev polynomial (the paper's Chebyshev
+                          smoother study, Sec. 4.1), degree cheb_degree on
+                          [cheb_lower, cheb_upper] x lambda_max(D^-1 A) of each level  0        */
   double omega;        /* Jacobi weight (Sec. 4.1)                                 0.5      */
   int n_pre, n_post;   /* smoothing sweeps (one each)                              1, 1     */
   double soc_beta;     /* strength-of-connection threshold (Eq. 10)                0.003    */
@@ -77,6 +80,10 @@ typedef struct {
                           1: one captured graph per iteration; 0: plain launches   2        */
   int max_levels;      /* cap on the number of levels                              25       */
   int concurrency;     /* solve slots: right-hand sides solved concurrently        4        */
+  int cheb_degree;     /* Chebyshev smoother: operator applies per smoothing, 1..8  2       */
+  double cheb_lower;   /* Chebyshev interval, fractions of the 20-step power-iteration
+                          estimate of lambda_max(D^-1 A): lower                     0.1      */
+  double cheb_upper;   /*                                   upper                     1.1      */
 } tomg_options;
 
 typedef struct {

@@ -122,6 +122,9 @@ void tomg_options_default(tomg_options* o) {
   o->max_coarse_dofs = 2000;
   o->n_geo_levels = 3;
   o->smoother = 0;
+  o->cheb_degree = 2;
+  o->cheb_lower = 0.1;
+  o->cheb_upper = 1.1;
   o->omega = 0.5;
   o->n_pre = 1;
   o->n_post = 1;

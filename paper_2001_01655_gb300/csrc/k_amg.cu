@@ -496,6 +496,60 @@ double amg_spectral_radius(cudaStream_t s, const Bsr& A, const double* V, const 
   return rho;
 }
 
+// w = scale * Dinv t (B x B blocks), scale read from the device
+template <int B>
+__global__ void k_dinv_scale(int64_t nodes, const double* __restrict__ Dinv,
+                             const double* __restrict__ t, const double* __restrict__ scale,
+                             double* __restrict__ w) {
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= nodes) return;
+  const double sc = *scale;
+  const double* D = Dinv + (int64_t)B * B * i;
+#pragma unroll
+  for (int q = 0; q < B; q++) {
+    double v = 0.0;
+#pragma unroll
+    for (int c = 0; c < B; c++) v += D[q * B + c] * t[B * i + c];
+    w[B * i + q] = sc * v;
+  }
+}
+
+double spectral_radius_op(cudaStream_t s, int64_t nodes, int bs, const double* Dinv, int level,
+                          int iters, const std::function<void(const double*, double*)>& apply) {
+  // the same iteration as amg_spectral_radius, with the operator applied by the caller:
+  // u_0 = splitmix64 vector; w = (1/||u_it||) D^-1 A u_it, rho_it = ||w||, u_{it+1} = w
+  const int64_t n = nodes * bs;
+  const int gp = 256;
+  DBuf<double> v, w, t, parts, nrm;
+  v.resize(n);
+  w.resize(n);
+  t.resize(n);
+  parts.resize(gp);
+  nrm.resize(2 * (iters + 1));
+  LAUNCH(k_power_init, ceil_div(n, 256), 256, 0, s, n, level, v.p);
+  LAUNCH(k_sumsq_partials, gp, 256, 0, s, n, v.p, parts.p);
+  LAUNCH(k_norm_finish, 1, 256, 0, s, parts.p, gp, nrm.p);
+  double* a = v.p;
+  double* c = w.p;
+  for (int it = 0; it < iters; it++) {
+    apply(a, t.p);
+    const double* sc = nrm.p + 2 * it + 1;
+    const int g = ceil_div(nodes, 256);
+    if (bs == 2) LAUNCH(k_dinv_scale<2>, g, 256, 0, s, nodes, Dinv, t.p, sc, c);
+    else if (bs == 3) LAUNCH(k_dinv_scale<3>, g, 256, 0, s, nodes, Dinv, t.p, sc, c);
+    else if (bs == 6) LAUNCH(k_dinv_scale<6>, g, 256, 0, s, nodes, Dinv, t.p, sc, c);
+    else TOMG_THROW(TOMG_E_INVALID, "unsupported block %d", bs);
+    LAUNCH(k_sumsq_partials, gp, 256, 0, s, n, c, parts.p);
+    LAUNCH(k_norm_finish, 1, 256, 0, s, parts.p, gp, nrm.p + 2 * (it + 1));
+    std::swap(a, c);
+  }
+  double rho = 0.0;
+  CK(cudaMemcpyAsync(&rho, nrm.p + 2 * iters, sizeof(double), cudaMemcpyDeviceToHost, s));
+  CK(cudaStreamSynchronize(s));
+  if (!(rho > 0.0)) TOMG_THROW(TOMG_E_BREAKDOWN, "power iteration collapsed");
+  return rho;
+}
+
 void amg_smooth_prolongator(cudaStream_t s, const Bsr& AT, const double* ATV, const int* agg,
                             const double* TV, const int* Trp, const double* Dinv, double omega,
                             int b, double* PV) {

@@ -3,6 +3,8 @@
 // device flag: once it is set the solve-loop kernels return immediately.
 #pragma once
 
+#include <functional>
+
 #include "common.cuh"
 
 namespace tomg {
@@ -150,6 +152,10 @@ void amg_tentative(cudaStream_t s, int n_nodes, int b, int k, int n_agg, const i
 // spectral radius of D^-1 A by power iteration (FP64), returns rho (syncs)
 double amg_spectral_radius(cudaStream_t s, const Bsr& A, const double* V, const double* Dinv,
                            int level, int iters, double* v, double* w, double* partials);
+// spectral radius of D^-1 A for an operator applied by `apply(x, y)` (y = A x, FP64, n = nodes *
+// bs), same start vector and iteration as amg_spectral_radius; returns rho (syncs)
+double spectral_radius_op(cudaStream_t s, int64_t nodes, int bs, const double* Dinv, int level,
+                          int iters, const std::function<void(const double*, double*)>& apply);
 // P = T - omega Dinv (A T) on the pattern of AT
 void amg_smooth_prolongator(cudaStream_t s, const Bsr& AT, const double* ATV, const int* agg,
                             const double* TV, const int* Trp, const double* Dinv, double omega,
@@ -193,6 +199,11 @@ void mask_vec(cudaStream_t s, const double* f, double* b, const uint8_t* mask, i
 template <class T>
 void jacobi0(cudaStream_t s, int bs, int64_t nodes, const T* Dinv, const T* b, T* x, double omega,
              const int* done);
+// Chebyshev smoother step at every node: d = c1 d_prev + c2 Dinv r, x += d; d_prev = 0
+// (dmode 0), d (1) or x (2)
+template <class T>
+void cheb_step(cudaStream_t s, int bs, int64_t nodes, const T* Dinv, const T* r, T* x, T* d,
+               double c1, double c2, int dmode, const int* done);
 // coarse solve x = Ainv b (dense GEMV)
 template <class T>
 void dense_gemv(cudaStream_t s, int n, const T* Ainv, const T* b, T* x, const int* done);

@@ -189,6 +189,27 @@ void vcycle(tomg_problem* P, Work& W, int l, const T* b, T* out, const int* done
   }
   T* x = V<T>::x(lw);
   T* r = V<T>::r(lw);
+  if (P->opt.smoother == 1) {
+    // Chebyshev smoothing (m steps of Chebyshev acceleration, the same polynomial before and
+    // after the coarse correction): the iterate lives in `out`, its last step in x
+    const int m = P->opt.cheb_degree;
+    const T* D = V<T>::D(Lv);
+    jacobi0<T>(s, Lv.b, Lv.nn, D, b, out, Lv.cheb_c2[0], done);  // x_1 = d_0 from x_0 = 0
+    for (int k = 1; k < m; k++) {
+      level_op<T>(P, s, l, MODE_RESID, out, r, b, done);
+      cheb_step<T>(s, Lv.b, Lv.nn, D, r, out, x, Lv.cheb_c1[k], Lv.cheb_c2[k], k == 1 ? 2 : 1, done);
+    }
+    level_op<T>(P, s, l, MODE_RESID, out, r, b, done);
+    LevelWork& cw = W.lw[l + 1];
+    restrict_to<T>(P, s, l, r, V<T>::b(cw), done);
+    vcycle<T>(P, W, l + 1, V<T>::b(cw), V<T>::y(cw), done);
+    prolong_add<T>(P, s, l, V<T>::y(cw), out, done);
+    for (int k = 0; k < m; k++) {
+      level_op<T>(P, s, l, MODE_RESID, out, r, b, done);
+      cheb_step<T>(s, Lv.b, Lv.nn, D, r, out, x, Lv.cheb_c1[k], Lv.cheb_c2[k], k == 0 ? 0 : 1, done);
+    }
+    return;
+  }
   // pre-smoothing; the first sweep from x = 0 needs no operator apply, and with a single
   // pre-sweep in FP32 it is fused into the residual pass (x = w Dinv b, r = b - A x in one
   // kernel; forming w Dinv b at every neighbour is cheap on the FP32 pipes, not on FP64)
@@ -610,8 +631,10 @@ void setup(tomg_problem* P, const tomg_options& opt) {
     TOMG_THROW(TOMG_E_INVALID, "unknown preconditioner %d or precision %d", opt.pc, opt.prec);
   if (!(opt.rtol > 0.0) || opt.max_iter < 1 || opt.max_iter > 1000000 || !(opt.omega > 0.0) ||
       !(opt.omega < 2.0) || opt.n_pre < 1 || opt.n_pre > 8 || opt.n_post < 1 || opt.n_post > 8 ||
-      opt.max_coarse_dofs < 1 || opt.max_levels < 1 || opt.max_levels > 64 || opt.smoother != 0 ||
-      opt.concurrency < 0 || opt.concurrency > 64)
+      opt.max_coarse_dofs < 1 || opt.max_levels < 1 || opt.max_levels > 64 || opt.smoother < 0 ||
+      opt.smoother > 1 || opt.concurrency < 0 || opt.concurrency > 64 ||
+      (opt.smoother == 1 && (opt.cheb_degree < 1 || opt.cheb_degree > 8 ||
+                             !(opt.cheb_lower > 0.0) || !(opt.cheb_upper > opt.cheb_lower))))
     TOMG_THROW(TOMG_E_INVALID, "invalid options");
   P->setup_valid = false;
   P->setup_gen++;
@@ -691,6 +714,29 @@ void setup(tomg_problem* P, const tomg_options& opt) {
     P->Ainv32.resize(P->Ainv64.n);
     cast_f64_f32(s, P->Ainv64.p, P->Ainv32.p, P->Ainv64.n);
     tr.mark("coarse inverse", (int)P->L.size() - 1);
+    if (opt.smoother == 1) {
+      // Chebyshev smoother on every level above the coarsest: lambda_max(D^-1 A_l) by 20 power
+      // iterations, interval [lower, upper] x lambda, three-term recurrence coefficients
+      for (int l = 0; l + 1 < (int)P->L.size(); l++) {
+        Level& Lv = *P->L[l];
+        Lv.lam = spectral_radius_op(s, Lv.nn, Lv.b, Lv.D64.p, l, 20,
+                                    [&](const double* xv, double* yv) {
+                                      level_op<double>(P, s, l, MODE_APPLY, xv, yv, nullptr, nullptr);
+                                    });
+        const double a = opt.cheb_lower * Lv.lam, bnd = opt.cheb_upper * Lv.lam;
+        const double theta = 0.5 * (bnd + a), delta = 0.5 * (bnd - a), sigma = theta / delta;
+        double rho = 1.0 / sigma;
+        Lv.cheb_c1[0] = 0.0;
+        Lv.cheb_c2[0] = 1.0 / theta;
+        for (int k = 1; k < opt.cheb_degree; k++) {
+          const double rn = 1.0 / (2.0 * sigma - rho);
+          Lv.cheb_c1[k] = rn * rho;
+          Lv.cheb_c2[k] = 2.0 * rn / delta;
+          rho = rn;
+        }
+      }
+      tr.mark("chebyshev bounds");
+    }
     // setup-only storage of the fine level (its FP64 stencil stays: it carries every FP64
     // application of K, see fine64_apply_dot)
     L0.rp.release(); L0.ci.release(); L0.V64.release();

@@ -49,6 +49,9 @@ struct Level {
   DBuf<float> Pv32, Rv32;
   int64_t Pnnzb = 0;
   DBuf<int> agg;
+  // Chebyshev smoother: lambda_max(D^-1 A) estimate and the step coefficients
+  double lam = 0.0;
+  double cheb_c1[8] = {0}, cheb_c2[8] = {0};
 
   Bsr bsr() const {
     Bsr A;

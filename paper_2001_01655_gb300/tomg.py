@@ -17,6 +17,7 @@ LIB_PATH = os.path.join(HERE, "_build", "libtomg.so")
 OK, NOT_CONVERGED, E_INVALID, E_OOM, E_CUDA, E_BREAKDOWN, E_TIMEOUT, E_BUDGET = 0, 1, -1, -2, -3, -4, -5, -6
 PC = {"gmg": 0, "amg": 1, "hybrid": 2, "jacobi": 3}
 PREC = {"fp64": 0, "fp32": 1, "tf32x3": 2}
+SMOOTHER = {"jacobi": 0, "chebyshev": 1}
 
 
 class TomgError(RuntimeError):
@@ -30,7 +31,8 @@ class Options(C.Structure):
                 ("n_levels", C.c_int), ("max_coarse_dofs", C.c_int), ("n_geo_levels", C.c_int),
                 ("smoother", C.c_int), ("omega", C.c_double), ("n_pre", C.c_int),
                 ("n_post", C.c_int), ("soc_beta", C.c_double), ("check_every", C.c_int),
-                ("use_graph", C.c_int), ("max_levels", C.c_int), ("concurrency", C.c_int)]
+                ("use_graph", C.c_int), ("max_levels", C.c_int), ("concurrency", C.c_int),
+                ("cheb_degree", C.c_int), ("cheb_lower", C.c_double), ("cheb_upper", C.c_double)]
 
 
 class Result(C.Structure):
@@ -119,6 +121,8 @@ def default_options(**kw) -> Options:
             v = PC[v]
         if k == "prec" and isinstance(v, str):
             v = PREC[v]
+        if k == "smoother" and isinstance(v, str):
+            v = SMOOTHER[v]
         setattr(o, k, v)
     return o
 
