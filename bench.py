@@ -51,6 +51,12 @@ def parse():
     ap.add_argument("--batched", type=int, default=1,
                     help="also time the 16 right-hand sides of the 3D 128x64x64 case (0: skip)")
     ap.add_argument("--slots", type=int, default=4)
+    ap.add_argument("--smoother", default="jacobi", choices=["jacobi", "chebyshev"],
+                    help="V-cycle smoother of the timed solves (the paper's runs use Jacobi)")
+    ap.add_argument("--cheb-degree", type=int, default=2)
+    ap.add_argument("--batched-prec", default="tf32x3", choices=["fp32", "tf32x3"],
+                    help="V-cycle precision of the batched 3D measurement: fp32 CUDA-core or "
+                         "3xTF32 tensor-core element contractions")
     ap.add_argument("--kernel", default=None, choices=["outer", "residual", "jacobi", "apply"],
                     help="time one level-0 operator kernel alone (for profiler captures) instead "
                          "of the solve: outer = FP64 q = K p with its dot, the others the "
@@ -155,7 +161,8 @@ def run_gpu(args, rank, world, local):
     u_d = torch.zeros_like(f_d)
     flush = torch.empty(256 << 20, dtype=torch.int8, device=dev)  # 256 MB > 129 MB L2
     opts = dict(pc=args.pc, max_coarse_dofs=args.cap, n_geo_levels=args.n_geo, rtol=1e-8,
-                max_iter=2000, use_graph=args.graph_mode)
+                max_iter=2000, use_graph=args.graph_mode, smoother=args.smoother,
+                cheb_degree=args.cheb_degree)
 
     def step(prec):
         u_d.zero_()
@@ -205,6 +212,8 @@ def run_gpu(args, rank, world, local):
         "config": {"workload": "2D cantilever quad4 %dx%d (592,130 DOFs), seeded thin 0/1 members "
                    "(1e9 contrast), left edge clamped, unit load right mid-edge" % (WORKLOAD["nx"], WORKLOAD["ny"]),
                    "preconditioner": args.pc, "max_coarse_dofs": args.cap, "rtol": 1e-8,
+                   "smoother": args.smoother if args.smoother == "jacobi" else
+                   "chebyshev degree %d" % args.cheb_degree,
                    "step": "SIMP moduli + hierarchy setup + FCG solve from u = 0",
                    "l2": "flushed between timed steps (256 MB write)",
                    "parallelism": "replicas" if world > 1 else "single GPU"},
@@ -242,11 +251,12 @@ def run_gpu(args, rank, world, local):
     if args.serving > 0:
         out["serving"] = serving_run(tomg, ctx, args.serving, args.serving_updates, args.slots)
     if args.batched:
-        out["batched"] = batched_run(tomg, ctx, args.slots)
+        out["batched"] = batched_run(tomg, ctx, args.slots, prec=args.batched_prec,
+                                     smoother=args.smoother, cheb_degree=args.cheb_degree)
     return out
 
 
-def batched_run(tomg, ctx, slots, reps=3):
+def batched_run(tomg, ctx, slots, reps=3, prec="tf32x3", smoother="jacobi", cheb_degree=2):
     """The 16 right-hand sides (8 point loads, 8 adjoint-like vectors) of the 3D hex8 128x64x64
     case (1,635,075 DOFs) on one shared hierarchy: all 16 on `slots` concurrent solve slots,
     against the same 16 one after another (one slot).  Median of `reps` runs, setup excluded."""
@@ -255,8 +265,8 @@ def batched_run(tomg, ctx, slots, reps=3):
     P = tomg.Problem.from_workload(ctx, p)
     res = {}
     for conc in (slots, 1):
-        P.setup(pc="hybrid", prec="fp32", n_geo_levels=3, max_coarse_dofs=1000, rtol=1e-8,
-                concurrency=conc)
+        P.setup(pc="hybrid", prec=prec, n_geo_levels=3, max_coarse_dofs=1000, rtol=1e-8,
+                concurrency=conc, smoother=smoother, cheb_degree=cheb_degree)
         P.solve(p.f[:2])  # warm-up: graphs and vectors of the slots
         times, its, worst = [], [], 0.0
         for _ in range(reps):
@@ -270,7 +280,9 @@ def batched_run(tomg, ctx, slots, reps=3):
                      "iterations_median": statistics.median(its), "rel_residual_max": worst,
                      "setup_ms": r[0]["setup_ms"]}
     return {"workload": "3D cantilever hex8 128x64x64 (1,635,075 DOFs), 8 point loads + 8 "
-                        "adjoint-like right-hand sides, hybrid hierarchy, FP32 V-cycle",
+                        "adjoint-like right-hand sides, hybrid hierarchy, %s V-cycle" %
+                        ("FP32 (3xTF32 tensor-core element contractions)" if prec == "tf32x3"
+                         else "FP32"),
             "rhs": p.nrhs, "concurrent": dict(res[slots], slots=slots), "one_at_a_time": res[1]}
 
 

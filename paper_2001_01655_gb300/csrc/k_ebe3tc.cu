@@ -1,6 +1,6 @@
 // Level-0 SIMP element operator on hex8 grids (Sec. 2.1 Eq. 2, Sec. 3.1) with the element
-// contractions on the fifth-generation tensor cores: tcgen05.mma kind::tf32, operands in
-// shared memory, accumulators in tensor memory.
+// contractions on the fifth-generation tensor cores: tcgen05.mma kind::tf32, A operands and
+// accumulators in tensor memory, B operand (Ke) in shared memory.
 //
 // The element products y_e = Ke x_e of a tile of elements form one dense product
 //   Y (elements x 24) = X (elements x 24) . Ke^T (24 x 24)
@@ -11,20 +11,22 @@
 //
 // Tiling.  A block owns a column of output nodes: 31 x 7 nodes in x, y and `nz_tile` node
 // layers in z.  It walks the element layers under and inside that column.  One element layer
-// of the tile is 32 x 8 = 256 elements = two M = 128 tiles, one element per thread.  Per layer
-// (steps 2-3 of layer ke run while steps 4-5 of layer ke - 1 run: two A buffers, two
-// accumulator sets in tensor memory):
+// of the tile is 32 x 8 = 256 elements = two M = 128 tiles; thread (lane ex, warp ey) owns
+// element (ex, ey) and, for ex, ey >= 1, node (ex, ey) of the layer tile.  Per element layer:
 //   1. the masked displacements of the next node layer (33 x 9 nodes) are staged in shared
 //      memory, and each thread keeps its element's modulus (both fetched one layer ahead);
-//   2. every thread writes its element's 24 displacements, split into TF32 hi and lo parts,
-//      as one row of the A operands in the canonical no-swizzle K-major layout;
+//   2. every thread splits its element's 24 displacements into TF32 hi and lo parts and writes
+//      them as its row of the A operands in tensor memory (tcgen05.st: lane = row);
 //   3. one thread issues 2 tiles x 3 products x 3 K-steps of M128 N32 K8 MMAs and commits them
 //      to an mbarrier (N = 32: the 24 outputs padded with zero rows of B);
-//   4. every thread reads its element's row of the accumulator (tcgen05.ld), scales it by E_e
-//      and stages it in shared memory;
-//   5. every owned node sums the contributions of the four elements of this layer around it;
-//      a node layer is complete after the element layers below and above it, and is then
+//   4. while they run, the threads finish the previous element layer: each reads its element's
+//      accumulator row (tcgen05.ld) and scales it by E_e; node sums over the four elements of
+//      the layer around a node take the x-neighbour through a warp shuffle and the
+//      y-neighbour through shared memory;
+//   5. a node layer is complete after the element layers below and above it, and is then
 //      finished (mask, residual or Jacobi update) and written.
+// The accumulators are double-buffered (layer ke's MMAs overlap the finishing of layer ke - 1);
+// the A operands are single-buffered and rewritten once the previous layer's MMAs completed.
 // The outer ring of nodes of each tile is computed but not written: the neighbouring tile owns
 // it, so every node's sum comes from one block, in a fixed order, with no atomics.
 // All waits are bounded: an mbarrier that does not complete within the limit sets an error word
@@ -45,29 +47,28 @@ constexpr int TNX = TEX + 1, TNY = TEY + 1;   // nodes of one layer of the tile 
 constexpr int ONX = TEX - 1, ONY = TEY - 1;   // owned nodes per layer (31 x 7)
 constexpr int NT = TEX * TEY;                 // 256 threads, one element each
 constexpr int LAYER_NODES = TNX * TNY;        // 297
-constexpr int OWNED = ONX * ONY;              // 217
 constexpr int KD = 24;                        // element DOFs (the K of the product)
 constexpr int NB = 32;                        // N: 24 outputs padded to a multiple of 16
-// canonical K-major layout without swizzle: a core matrix is 8 rows x 16 bytes (4 TF32);
-// core matrices adjacent in K are LBO bytes apart, adjacent 8-row groups SBO bytes apart
+// B operand in shared memory, canonical K-major layout without swizzle: a core matrix is
+// 8 rows x 16 bytes (4 TF32); core matrices adjacent in K are LBO bytes apart, adjacent
+// 8-row groups SBO bytes apart
 constexpr int LBO = 128;
 constexpr int SBO = (KD / 4) * LBO;           // 768
-constexpr int A_BYTES = (128 / 8) * SBO;      // one M = 128 operand: 12288
 constexpr int B_BYTES = (NB / 8) * SBO;       // one N = 32 operand: 3072
-constexpr int YS = 25;                        // staged element outputs: row stride (floats)
-constexpr int TMEM_COLS = 128;                // 2 pipeline stages x 2 tiles x 32 FP32 columns
+constexpr int PS = 7;                         // staged y-pair partial sums: row stride (floats)
+// tensor memory columns: accumulators of stage j, tile m at 64 j + 32 m; A of tile m at
+// 128 + 48 m (24 hi columns, then 24 lo columns; one TF32 element per 32-bit column)
+constexpr int TMEM_COLS = 256;
+constexpr int A_COL = 128;
 
-// dynamic shared memory map (bytes from a 128-aligned base).  A set = A_hi[2 tiles],
-// A_lo[2 tiles] of one pipeline stage; after its MMAs it holds the staged element outputs.
-constexpr int A_SET = 4 * A_BYTES;                        // 49152
-constexpr int OFF_A = 0;                                  // two A sets
-constexpr int OFF_B = OFF_A + 2 * A_SET;                  // B_hi, B_lo
+// dynamic shared memory map (bytes from a 128-aligned base)
+constexpr int OFF_B = 0;                                  // B_hi, B_lo
 constexpr int OFF_X = OFF_B + 2 * B_BYTES;                // x ring: 2 node layers
-constexpr int OFF_BAR = OFF_X + 2 * LAYER_NODES * 3 * 4;  // 2 mbarriers + TMEM address
+constexpr int OFF_P = (OFF_X + 2 * LAYER_NODES * 3 * 4 + 15) / 16 * 16;  // [TEY][TEX][PS]
+constexpr int OFF_BAR = OFF_P + NT * PS * 4;              // 2 mbarriers + TMEM address
 constexpr int SMEM_BYTES = OFF_BAR + 24;
 constexpr int SMEM_ALLOC = SMEM_BYTES + 128;              // room to align the base
-static_assert(NT * YS * 4 <= A_SET, "Y staging must fit in one A set");
-static_assert(OFF_B % 128 == 0 && OFF_X % 16 == 0 && OFF_BAR % 8 == 0, "alignment");
+static_assert(OFF_X % 16 == 0 && OFF_P % 16 == 0 && OFF_BAR % 8 == 0, "alignment");
 
 // instruction descriptor, kind::tf32: D FP32 (bits 4-5 = 1), A and B TF32 (bits 7-9 and
 // 10-12 = 2), both K-major (bits 15, 16 = 0), N >> 3 at bits 17-22, M >> 4 at bits 24-28
@@ -89,7 +90,7 @@ __device__ __forceinline__ uint64_t sdesc(uint32_t addr) {
          ((uint64_t)(SBO >> 4) << 32) | (1ull << 46);
 }
 
-// byte offset of element (row, k) in an operand of the layout above
+// byte offset of element (row, k) in the B operand layout above
 __host__ __device__ __forceinline__ int op_off(int row, int k) {
   return (row >> 3) * SBO + (k >> 2) * LBO + (row & 7) * 16 + (k & 3) * 4;
 }
@@ -99,12 +100,14 @@ __host__ __device__ __forceinline__ uint32_t tf32_round_bits(uint32_t u) {
   return (u + 0x1000u) & 0xFFFFE000u;
 }
 
-__device__ __forceinline__ void mma_tf32(uint32_t d_tmem, uint64_t a, uint64_t b, uint32_t acc) {
+// D (tmem) (+)= A (tmem) . B (smem descriptor)^T
+__device__ __forceinline__ void mma_tf32_ts(uint32_t d_tmem, uint32_t a_tmem, uint64_t b,
+                                            uint32_t acc) {
   asm volatile(
       "{\n\t.reg .pred p;\n\t"
       "setp.ne.b32 p, %4, 0;\n\t"
-      "tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, p;\n\t}\n"
-      :: "r"(d_tmem), "l"(a), "l"(b), "r"(IDESC), "r"(acc) : "memory");
+      "tcgen05.mma.cta_group::1.kind::tf32 [%0], [%1], %2, %3, p;\n\t}\n"
+      :: "r"(d_tmem), "r"(a_tmem), "l"(b), "r"(IDESC), "r"(acc) : "memory");
 }
 
 __device__ __forceinline__ bool mbar_try(uint32_t bar, uint32_t parity) {
@@ -141,6 +144,26 @@ __device__ __forceinline__ void tmem_ld24(uint32_t taddr, float* v) {
       : "memory");
 #pragma unroll
   for (int i = 0; i < 24; i++) v[i] = __uint_as_float(r[i]);
+}
+
+// this thread's TMEM lane, 48 consecutive 32-bit columns from taddr; the wait for the stores
+// is part of the same asm statement
+__device__ __forceinline__ void tmem_st48(uint32_t taddr, const uint32_t* v) {
+  asm volatile(
+      "tcgen05.st.sync.aligned.32x32b.x32.b32 [%0], {%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,"
+      "%14,%15,%16,%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31,%32,%33};\n\t"
+      "tcgen05.st.sync.aligned.32x32b.x16.b32 [%1], {%34,%35,%36,%37,%38,%39,%40,%41,%42,%43,"
+      "%44,%45,%46,%47,%48,%49};\n\t"
+      "tcgen05.wait::st.sync.aligned;\n"
+      :: "r"(taddr), "r"(taddr + 32u), "r"(v[0]), "r"(v[1]), "r"(v[2]), "r"(v[3]), "r"(v[4]),
+         "r"(v[5]), "r"(v[6]), "r"(v[7]), "r"(v[8]), "r"(v[9]), "r"(v[10]), "r"(v[11]),
+         "r"(v[12]), "r"(v[13]), "r"(v[14]), "r"(v[15]), "r"(v[16]), "r"(v[17]), "r"(v[18]),
+         "r"(v[19]), "r"(v[20]), "r"(v[21]), "r"(v[22]), "r"(v[23]), "r"(v[24]), "r"(v[25]),
+         "r"(v[26]), "r"(v[27]), "r"(v[28]), "r"(v[29]), "r"(v[30]), "r"(v[31]), "r"(v[32]),
+         "r"(v[33]), "r"(v[34]), "r"(v[35]), "r"(v[36]), "r"(v[37]), "r"(v[38]), "r"(v[39]),
+         "r"(v[40]), "r"(v[41]), "r"(v[42]), "r"(v[43]), "r"(v[44]), "r"(v[45]), "r"(v[46]),
+         "r"(v[47])
+      : "memory");
 }
 
 // one node layer of the tile: displacements and mask bits of up to two nodes per thread.  The
@@ -215,55 +238,43 @@ __device__ __forceinline__ float e_fetch(int ke, int EX0, int EY0, int nx, int n
   return __ldg(E + ge + (int64_t)nx * (gf + (int64_t)ny * ke));
 }
 
-// element layer ke of the tile -> A operands (TF32 hi and lo rows) of buffer A, from the ring
-// slots of node layers ke (bottom, local nodes 0-3) and ke + 1 (top, local nodes 4-7)
-__device__ __forceinline__ void build_a(uint8_t* A, const float* s0, const float* s1, int ex,
-                                        int ey, int mt, int row) {
-  uint8_t* Ahi = A + mt * A_BYTES;
-  uint8_t* Alo = A + (2 + mt) * A_BYTES;
+// element (ex, ey) of layer ke: its 24 displacements from the ring slots of node layers ke
+// (bottom, local nodes 0-3) and ke + 1 (top, local nodes 4-7), split into TF32 hi (v[0..23])
+// and lo (v[24..47]) parts: the thread's row of the A operands
+__device__ __forceinline__ void a_row(uint32_t* v, const float* s0, const float* s1, int ex,
+                                      int ey) {
 #pragma unroll
-  for (int kc = 0; kc < 6; kc++) {
-    uint32_t hi[4], lo[4];
-#pragma unroll
-    for (int q = 0; q < 4; q++) {
-      const int k = 4 * kc + q, bn = k / 3, c = k % 3;
-      const float* sx = (bn & 4) ? s1 : s0;
-      const float v = sx[3 * ((ey + ((bn >> 1) & 1)) * TNX + ex + (bn & 1)) + c];
-      hi[q] = tf32_round_bits(__float_as_uint(v));
-      lo[q] = __float_as_uint(v - __uint_as_float(hi[q]));
-    }
-    const int off = op_off(row, 4 * kc);
-    *reinterpret_cast<uint4*>(Ahi + off) = make_uint4(hi[0], hi[1], hi[2], hi[3]);
-    *reinterpret_cast<uint4*>(Alo + off) = make_uint4(lo[0], lo[1], lo[2], lo[3]);
+  for (int k = 0; k < KD; k++) {
+    const int bn = k / 3, c = k % 3;
+    const float* sx = (bn & 4) ? s1 : s0;
+    const float xv = sx[3 * ((ey + ((bn >> 1) & 1)) * TNX + ex + (bn & 1)) + c];
+    const uint32_t hi = tf32_round_bits(__float_as_uint(xv));
+    v[k] = hi;
+    v[KD + k] = __float_as_uint(xv - __uint_as_float(hi));
   }
 }
 
 // 2 M-tiles x 3 split products x 3 K-steps into the accumulators at column d, then a commit
 // to the barrier (executed by one thread)
-__device__ __forceinline__ void issue_mmas(uint32_t d, uint32_t abase, uint32_t bbase,
-                                           uint32_t bar) {
+__device__ __forceinline__ void issue_mmas(uint32_t d, uint32_t a, uint32_t bbase, uint32_t bar) {
   asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
 #pragma unroll
   for (int m = 0; m < 2; m++) {
-    const uint32_t ahi = abase + m * A_BYTES, alo = abase + (2 + m) * A_BYTES;
+    const uint32_t ahi = a + (uint32_t)(48 * m), alo = ahi + (uint32_t)KD;
 #pragma unroll
     for (int p = 0; p < 3; p++) {
-      const uint32_t a = (p == 1) ? alo : ahi;
+      const uint32_t aa = (p == 1) ? alo : ahi;
       const uint32_t bb = (p == 2) ? bbase + B_BYTES : bbase;
 #pragma unroll
       for (int s = 0; s < 3; s++)
-        mma_tf32(d + (uint32_t)(m * NB), sdesc(a + 2 * LBO * s), sdesc(bb + 2 * LBO * s),
-                 (p | s) ? 1u : 0u);
+        mma_tf32_ts(d + (uint32_t)(m * NB), aa + (uint32_t)(8 * s), sdesc(bb + 2 * LBO * s),
+                    (p | s) ? 1u : 0u);
     }
   }
   asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];\n"
                :: "r"(bar) : "memory");
 }
 
-// Two-stage software pipeline over the element layers: while the tensor cores run the MMAs of
-// layer ke (A buffer and accumulators ke & 1), the threads finish layer ke - 1 (accumulators,
-// staging in the other A buffer, node sums, output).  The ring of node layers is refilled one
-// layer ahead from registers, so no global-memory latency sits between two layers' MMAs.
 template <int MODE>
 __global__ void __launch_bounds__(NT, 2)
 k_ebe3tc(int nx, int ny, int nz, int nz_tile, const uint4* __restrict__ Bimg,
@@ -274,12 +285,14 @@ k_ebe3tc(int nx, int ny, int nz, int nz_tile, const uint4* __restrict__ Bimg,
   pdl_prologue();
   if (solve_done(done)) return;
   uint8_t* sm = smem_raw + ((128 - (smem_u32(smem_raw) & 127u)) & 127u);
-  float* sxr = reinterpret_cast<float*>(sm + OFF_X);      // [2][LAYER_NODES][3]
+  float* sxr = reinterpret_cast<float*>(sm + OFF_X);          // [2][LAYER_NODES][3]
+  float* sP = reinterpret_cast<float*>(sm + OFF_P);           // [TEY][TEX][PS]
   uint64_t* bar = reinterpret_cast<uint64_t*>(sm + OFF_BAR);  // [2]
   uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(sm + OFF_BAR + 16);
   const uint32_t sbase = smem_u32(sm);
-  const uint32_t bar_a[2] = {smem_u32(bar), smem_u32(bar + 1)};
-  const int tid = threadIdx.x, warp = tid >> 5;
+  const uint32_t bar0 = smem_u32(bar);  // barrier j at bar0 + 8 j
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  const int ex = lane, ey = warp;  // element of this thread; node (ex, ey) if owned
 
   const int EX0 = blockIdx.x * ONX - 1, EY0 = blockIdx.y * ONY - 1;
   const int k0 = blockIdx.z * nz_tile;
@@ -292,20 +305,16 @@ k_ebe3tc(int nx, int ny, int nz, int nz_tile, const uint4* __restrict__ Bimg,
     asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;\n" ::: "memory");
   }
   if (tid == 0) {
-    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;\n" :: "r"(bar_a[0]), "r"(1) : "memory");
-    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;\n" :: "r"(bar_a[1]), "r"(1) : "memory");
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;\n" :: "r"(bar0), "r"(1) : "memory");
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;\n" :: "r"(bar0 + 8u), "r"(1) : "memory");
     asm volatile("fence.mbarrier_init.release.cluster;\n" ::: "memory");
   }
   for (int t = tid; t < 2 * B_BYTES / 16; t += NT)
     reinterpret_cast<uint4*>(sm + OFF_B)[t] = Bimg[t];
 
-  // owned node of this thread (threads >= OWNED only help with the element work)
-  const bool owner = tid < OWNED;
-  const int onx = tid % ONX + 1, ony = tid / ONX + 1;        // local node of the layer tile
-  const int gi = EX0 + onx, gj = EY0 + ony;
+  const bool owner = ex >= 1 && ey >= 1;
+  const int gi = EX0 + ex, gj = EY0 + ey;
   const bool in_plane = owner && gi <= nx && gj <= ny;
-  const int ex = tid % TEX, ey = tid / TEX;
-  const int mt = tid >> 7, row = tid & 127;
 
   XPre pre;
   x_fetch(pre, k0 - 1, EX0, EY0, nx, ny, nz, mask, x);
@@ -319,6 +328,8 @@ k_ebe3tc(int nx, int ny, int nz, int nz_tile, const uint4* __restrict__ Bimg,
   __syncthreads();
   asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
   const uint32_t tmem = *tmem_slot;
+  const uint32_t lane_base = (uint32_t)(32 * (warp & 3)) << 16;
+  const int mt = warp >> 2;  // M-tile of this thread's element row
 
   float acc[3] = {0.f, 0.f, 0.f};  // node layer ke - 1: contributions gathered so far
   FinData fd;                      // finishing data of node layer ke - 1
@@ -327,22 +338,33 @@ k_ebe3tc(int nx, int ny, int nz, int nz_tile, const uint4* __restrict__ Bimg,
 
   for (int ke = k0 - 1; ke <= k1; ke++) {
     const bool mma_now = ke < k1;  // the last step only finishes layer k1 - 1
-    const int j = ke & 1;
-    if (mma_now)
-      build_a(sm + OFF_A + j * A_SET, sxr + j * LAYER_NODES * 3,
-              sxr + (j ^ 1) * LAYER_NODES * 3, ex, ey, mt, row);
-    asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory");
+    const int j = ke & 1, jp = j ^ 1;
+    if (ke >= k0) {
+      // the MMAs of layer ke - 1: their accumulators are read below, their A operands are
+      // overwritten now
+      const bool ok = mbar_wait(bar0 + 8u * jp, (parity >> jp) & 1u);
+      parity ^= 1u << jp;
+      if (__syncthreads_or(!ok)) {
+        failed = true;
+        break;
+      }
+      asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
+    }
+    if (mma_now) {
+      uint32_t v[2 * KD];
+      a_row(v, sxr + j * LAYER_NODES * 3, sxr + jp * LAYER_NODES * 3, ex, ey);
+      tmem_st48(tmem + lane_base + (uint32_t)(A_COL + 48 * mt), v);
+    }
+    asm volatile("tcgen05.fence::before_thread_sync;\n" ::: "memory");
     __syncthreads();
     if (mma_now && tid == 0)
-      issue_mmas(tmem + (uint32_t)(j * 2 * NB), sbase + OFF_A + j * A_SET, sbase + OFF_B,
-                 bar_a[j]);
-    // refill the ring: node layer ke + 2 replaces layer ke (read by the build above)
+      issue_mmas(tmem + (uint32_t)(j * 2 * NB), tmem + (uint32_t)A_COL, sbase + OFF_B, bar0 + 8u * j);
+    // refill the ring: node layer ke + 2 replaces layer ke (read by the row build above)
     if (mma_now && ke + 2 <= k1) {
       x_store(pre, sxr + j * LAYER_NODES * 3);
       if (ke + 3 <= k1) x_fetch(pre, ke + 3, EX0, EY0, nx, ny, nz, mask, x);
     }
     const float e_next = (ke + 1 < k1) ? e_fetch(ke + 1, EX0, EY0, nx, ny, nz, E) : 0.f;
-
     // finishing data of node layer ke, used one step later
     FinData fd_next;
     const bool fin_next = in_plane && ke >= k0 && ke < k1;
@@ -350,41 +372,40 @@ k_ebe3tc(int nx, int ny, int nz, int nz_tile, const uint4* __restrict__ Bimg,
 
     if (ke >= k0) {
       // finish element layer ke - 1 and node layer ke - 1
-      const int jp = j ^ 1;
-      const int kn = ke - 1;  // node layer finished now
+      const int kn = ke - 1;
       const bool fin = in_plane && kn >= k0;
       const int64_t node = node_id(gi, gj, kn, nx, ny);
-      const bool ok = mbar_wait(bar_a[jp], (parity >> jp) & 1u);
-      parity ^= 1u << jp;
-      if (__syncthreads_or(!ok)) {
-        failed = true;
-        break;
-      }
-      asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
-      {
-        float v[24];
-        tmem_ld24(tmem + ((uint32_t)(32 * (warp & 3)) << 16) + (uint32_t)(jp * 2 * NB + mt * NB), v);
-        float* sY = reinterpret_cast<float*>(sm + OFF_A + jp * A_SET);  // A buffer of layer ke-1
+      float v[24];
+      tmem_ld24(tmem + lane_base + (uint32_t)(jp * 2 * NB + mt * NB), v);
+      // x-pairs: node column ex gets the dx = 1 corners of element ex - 1 (previous lane) and
+      // the dx = 0 corners of element ex; p[dy][dz][c]
 #pragma unroll
-        for (int n = 0; n < 24; n++) sY[tid * YS + n] = e_prev * v[n];
-      }
+      for (int n = 0; n < 24; n++) v[n] *= e_prev;
+      float pr[2][2][3];
+#pragma unroll
+      for (int dy = 0; dy < 2; dy++)
+#pragma unroll
+        for (int dz = 0; dz < 2; dz++)
+#pragma unroll
+          for (int c = 0; c < 3; c++) {
+            const float left = __shfl_up_sync(0xffffffffu, v[3 * (1 + 2 * dy + 4 * dz) + c], 1);
+            pr[dy][dz][c] = v[3 * (2 * dy + 4 * dz) + c] + left;  // lane 0: not an owned node
+          }
+      // y-pairs: node row ey gets the dy = 1 sums of element row ey - 1 through shared memory
+      float* myP = sP + (ey * TEX + ex) * PS;
+#pragma unroll
+      for (int dz = 0; dz < 2; dz++)
+#pragma unroll
+        for (int c = 0; c < 3; c++) myP[3 * dz + c] = pr[1][dz][c];
       asm volatile("tcgen05.fence::before_thread_sync;\n" ::: "memory");
       __syncthreads();
       if (owner) {
-        const float* sY = reinterpret_cast<const float*>(sm + OFF_A + jp * A_SET);
-        // elements (onx-1+dxe, ony-1+dye) of layer ke - 1; the node is their local node
-        // (1-dxe) + 2(1-dye) at the bottom (dz = 0) or + 4 at the top (dz = 1)
-        float top[3] = {0.f, 0.f, 0.f};
+        const float* upP = sP + ((ey - 1) * TEX + ex) * PS;
+        float top[3];
 #pragma unroll
-        for (int q = 0; q < 4; q++) {
-          const int dxe = q & 1, dye = q >> 1;
-          const float* Ye = sY + ((ony - 1 + dye) * TEX + onx - 1 + dxe) * YS;
-          const int bn = (1 - dxe) + 2 * (1 - dye);
-#pragma unroll
-          for (int c = 0; c < 3; c++) {
-            acc[c] += Ye[3 * bn + c];
-            top[c] += Ye[3 * (bn + 4) + c];
-          }
+        for (int c = 0; c < 3; c++) {
+          acc[c] += upP[c] + pr[0][0][c];
+          top[c] = upP[3 + c] + pr[0][1][c];
         }
         if (fin) {
           float Ax[3];
@@ -421,8 +442,8 @@ k_ebe3tc(int nx, int ny, int nz, int nz_tile, const uint4* __restrict__ Bimg,
   if (failed) {
     if (tid == 0) atomicExch(&g_tc_error, 1);
     // let MMAs still in flight finish (bounded) before the tensor memory is released
-    mbar_wait(bar_a[0], parity & 1u);
-    mbar_wait(bar_a[1], (parity >> 1) & 1u);
+    mbar_wait(bar0, parity & 1u);
+    mbar_wait(bar0 + 8u, (parity >> 1) & 1u);
   }
   asm volatile("tcgen05.fence::before_thread_sync;\n" ::: "memory");
   __syncthreads();
@@ -436,15 +457,22 @@ k_ebe3tc(int nx, int ny, int nz, int nz_tile, const uint4* __restrict__ Bimg,
 template <int MODE>
 void launch_mode(cudaStream_t s, const Ebe& op, const float* x, float* y, const float* b,
                  const float* Dinv, double omega, const int* done) {
-  static bool attr_set = false;  // per instantiation; the attribute is per device function
-  if (!attr_set) {
-    CK(cudaFuncSetAttribute(k_ebe3tc<MODE>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                            SMEM_ALLOC));
-    attr_set = true;
+  // dynamic shared memory per block, raised if needed so that at most two blocks share an SM:
+  // each holds 256 of the SM's 512 tensor-memory columns (a third would wait in tcgen05.alloc)
+  static int smem = 0;  // per instantiation
+  if (smem == 0) {
+    int bytes = SMEM_ALLOC, per_sm = 0;
+    CK(cudaFuncSetAttribute(k_ebe3tc<MODE>, cudaFuncAttributeMaxDynamicSharedMemorySize, 100 << 10));
+    for (;;) {
+      CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_ebe3tc<MODE>, NT, bytes));
+      if (per_sm <= 2 || bytes >= (100 << 10)) break;
+      bytes += 8 << 10;
+    }
+    smem = bytes;
   }
   const int nzt = op.tc_nz > 0 ? op.tc_nz : 8;
   dim3 grid(ceil_div(op.nx + 1, ONX), ceil_div(op.ny + 1, ONY), ceil_div(op.nz + 1, nzt));
-  LAUNCH(k_ebe3tc<MODE>, grid, NT, SMEM_ALLOC, s, op.nx, op.ny, op.nz, nzt,
+  LAUNCH(k_ebe3tc<MODE>, grid, NT, smem, s, op.nx, op.ny, op.nz, nzt,
          reinterpret_cast<const uint4*>(op.Ktc), (const float*)op.E, op.mask, x, y, b, Dinv,
          (float)omega, done);
 }
