@@ -468,6 +468,7 @@ void amg_extend(tomg_problem* P, int start) {
     pv.resize(A.n); pw.resize(A.n); parts.resize(std::max(ceil_div(nn, 256), 256));
     tr.mark("tentative", cur);
     const double rho = amg_spectral_radius(s, Ab, A.V64.p, A.D64.p, cur, 20, pv.p, pw.p, parts.p);
+    A.lam = rho;  // the same estimate bounds a Chebyshev smoother on this level
     const double omegaP = 4.0 / (3.0 * rho);
     tr.mark("spectral_radius", cur);
     // P = T - omega D^-1 A T
@@ -719,10 +720,11 @@ void setup(tomg_problem* P, const tomg_options& opt) {
       // iterations, interval [lower, upper] x lambda, three-term recurrence coefficients
       for (int l = 0; l + 1 < (int)P->L.size(); l++) {
         Level& Lv = *P->L[l];
-        Lv.lam = spectral_radius_op(s, Lv.nn, Lv.b, Lv.D64.p, l, 20,
-                                    [&](const double* xv, double* yv) {
-                                      level_op<double>(P, s, l, MODE_APPLY, xv, yv, nullptr, nullptr);
-                                    });
+        if (!(Lv.lam > 0.0))  // levels coarsened by aggregation have it already
+          Lv.lam = spectral_radius_op(s, Lv.nn, Lv.b, Lv.D64.p, l, 20,
+                                      [&](const double* xv, double* yv) {
+                                        level_op<double>(P, s, l, MODE_APPLY, xv, yv, nullptr, nullptr);
+                                      });
         const double a = opt.cheb_lower * Lv.lam, bnd = opt.cheb_upper * Lv.lam;
         const double theta = 0.5 * (bnd + a), delta = 0.5 * (bnd - a), sigma = theta / delta;
         double rho = 1.0 / sigma;
