@@ -42,11 +42,9 @@ namespace tomg {
 
 namespace {
 
-constexpr int TEX = 32, TEY = 8;              // elements of one layer of the tile
-constexpr int TNX = TEX + 1, TNY = TEY + 1;   // nodes of one layer of the tile (33 x 9)
-constexpr int ONX = TEX - 1, ONY = TEY - 1;   // owned nodes per layer (31 x 7)
-constexpr int NT = TEX * TEY;                 // 256 threads, one element each
-constexpr int LAYER_NODES = TNX * TNY;        // 297
+constexpr int TEX = 32;                       // elements of one layer of the tile in x
+constexpr int TNX = TEX + 1;                  // nodes of one layer of the tile in x (33)
+constexpr int ONX = TEX - 1;                  // owned nodes per layer in x (31)
 constexpr int KD = 24;                        // element DOFs (the K of the product)
 constexpr int NB = 32;                        // N: 24 outputs padded to a multiple of 16
 // B operand in shared memory, canonical K-major layout without swizzle: a core matrix is
@@ -56,19 +54,30 @@ constexpr int LBO = 128;
 constexpr int SBO = (KD / 4) * LBO;           // 768
 constexpr int B_BYTES = (NB / 8) * SBO;       // one N = 32 operand: 3072
 constexpr int PS = 7;                         // staged y-pair partial sums: row stride (floats)
-// tensor memory columns: accumulators of stage j, tile m at 64 j + 32 m; A of tile m at
-// 128 + 48 m (24 hi columns, then 24 lo columns; one TF32 element per 32-bit column)
-constexpr int TMEM_COLS = 256;
-constexpr int A_COL = 128;
 
-// dynamic shared memory map (bytes from a 128-aligned base)
-constexpr int OFF_B = 0;                                  // B_hi, B_lo
-constexpr int OFF_X = OFF_B + 2 * B_BYTES;                // x ring: 2 node layers
-constexpr int OFF_P = (OFF_X + 2 * LAYER_NODES * 3 * 4 + 15) / 16 * 16;  // [TEY][TEX][PS]
-constexpr int OFF_BAR = OFF_P + NT * PS * 4;              // 2 mbarriers + TMEM address
-constexpr int SMEM_BYTES = OFF_BAR + 24;
-constexpr int SMEM_ALLOC = SMEM_BYTES + 128;              // room to align the base
-static_assert(OFF_X % 16 == 0 && OFF_P % 16 == 0 && OFF_BAR % 8 == 0, "alignment");
+// Tile shapes: TY = 8 element rows (256 threads, two M = 128 tiles, 31 x 7 owned nodes per
+// layer) or TY = 4 (128 threads, one tile, 31 x 3 owned nodes).  Tensor memory columns:
+// accumulators of pipeline stage j, tile m at (j MT + m) 32; A of tile m at A_COL + 48 m
+// (24 hi columns, then 24 lo columns; one TF32 element per 32-bit column).
+template <int TY>
+struct Cfg {
+  static constexpr int TNY = TY + 1, ONY = TY - 1;
+  static constexpr int NT = TEX * TY;                     // one element per thread
+  static constexpr int MT = TY / 4;                       // M = 128 tiles per layer
+  static constexpr int LAYER_NODES = TNX * TNY;
+  static constexpr int A_COL = 2 * MT * NB;
+  static constexpr int TMEM_COLS = TY == 8 ? 256 : 128;   // >= A_COL + 48 MT, a power of 2
+  static constexpr int MAX_BLOCKS = 512 / TMEM_COLS;      // blocks per SM the TMEM can hold
+  // dynamic shared memory map (bytes from a 128-aligned base)
+  static constexpr int OFF_B = 0;                                               // B_hi, B_lo
+  static constexpr int OFF_X = OFF_B + 2 * B_BYTES;                             // x ring
+  static constexpr int OFF_P = (OFF_X + 2 * LAYER_NODES * 3 * 4 + 15) / 16 * 16;  // y pairs
+  static constexpr int OFF_BAR = OFF_P + NT * PS * 4;     // 2 mbarriers + TMEM address
+  static constexpr int SMEM_ALLOC = OFF_BAR + 24 + 128;   // + room to align the base
+  static_assert(A_COL + 48 * MT <= TMEM_COLS, "tensor memory map");
+  static_assert(OFF_X % 16 == 0 && OFF_P % 16 == 0 && OFF_BAR % 8 == 0, "alignment");
+  static_assert(LAYER_NODES <= 2 * NT, "two nodes per thread stage a layer");
+};
 
 // instruction descriptor, kind::tf32: D FP32 (bits 4-5 = 1), A and B TF32 (bits 7-9 and
 // 10-12 = 2), both K-major (bits 15, 16 = 0), N >> 3 at bits 17-22, M >> 4 at bits 24-28
@@ -174,15 +183,16 @@ struct XPre {
   unsigned m[2];
 };
 
+template <int TY>
 __device__ __forceinline__ void x_fetch(XPre& p, int kk, int EX0, int EY0, int nx, int ny, int nz,
                                         const uint8_t* __restrict__ mask,
                                         const float* __restrict__ x) {
 #pragma unroll
   for (int h = 0; h < 2; h++) {
-    const int q = threadIdx.x + h * NT;
+    const int q = threadIdx.x + h * Cfg<TY>::NT;
     p.v[h][0] = p.v[h][1] = p.v[h][2] = 0.f;
     p.m[h] = 7u;
-    if (q < LAYER_NODES) {
+    if (q < Cfg<TY>::LAYER_NODES) {
       const int gi = EX0 + q % TNX, gj = EY0 + q / TNX;
       if (gi >= 0 && gi <= nx && gj >= 0 && gj <= ny && kk >= 0 && kk <= nz) {
         const int64_t node = node_id(gi, gj, kk, nx, ny);
@@ -194,11 +204,12 @@ __device__ __forceinline__ void x_fetch(XPre& p, int kk, int EX0, int EY0, int n
   }
 }
 
+template <int TY>
 __device__ __forceinline__ void x_store(const XPre& p, float* sx) {
 #pragma unroll
   for (int h = 0; h < 2; h++) {
-    const int q = threadIdx.x + h * NT;
-    if (q < LAYER_NODES) {
+    const int q = threadIdx.x + h * Cfg<TY>::NT;
+    if (q < Cfg<TY>::LAYER_NODES) {
 #pragma unroll
       for (int c = 0; c < 3; c++) sx[3 * q + c] = ((p.m[h] >> c) & 1u) ? 0.f : p.v[h][c];
     }
@@ -254,12 +265,13 @@ __device__ __forceinline__ void a_row(uint32_t* v, const float* s0, const float*
   }
 }
 
-// 2 M-tiles x 3 split products x 3 K-steps into the accumulators at column d, then a commit
+// MT M-tiles x 3 split products x 3 K-steps into the accumulators at column d, then a commit
 // to the barrier (executed by one thread)
+template <int MT>
 __device__ __forceinline__ void issue_mmas(uint32_t d, uint32_t a, uint32_t bbase, uint32_t bar) {
   asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
 #pragma unroll
-  for (int m = 0; m < 2; m++) {
+  for (int m = 0; m < MT; m++) {
     const uint32_t ahi = a + (uint32_t)(48 * m), alo = ahi + (uint32_t)KD;
 #pragma unroll
     for (int p = 0; p < 3; p++) {
@@ -275,12 +287,16 @@ __device__ __forceinline__ void issue_mmas(uint32_t d, uint32_t a, uint32_t bbas
                :: "r"(bar) : "memory");
 }
 
-template <int MODE>
-__global__ void __launch_bounds__(NT, 2)
+template <int MODE, int TY>
+__global__ void __launch_bounds__(Cfg<TY>::NT, Cfg<TY>::MAX_BLOCKS)
 k_ebe3tc(int nx, int ny, int nz, int nz_tile, const uint4* __restrict__ Bimg,
          const float* __restrict__ E, const uint8_t* __restrict__ mask,
          const float* __restrict__ x, float* __restrict__ y, const float* __restrict__ b,
          const float* __restrict__ Dinv, float omega, const int* done) {
+  using C = Cfg<TY>;
+  constexpr int NT = C::NT, LAYER_NODES = C::LAYER_NODES, ONY = C::ONY, MT = C::MT;
+  constexpr int OFF_B = C::OFF_B, OFF_X = C::OFF_X, OFF_P = C::OFF_P, OFF_BAR = C::OFF_BAR;
+  constexpr int A_COL = C::A_COL, TMEM_COLS = C::TMEM_COLS;
   extern __shared__ uint8_t smem_raw[];
   pdl_prologue();
   if (solve_done(done)) return;
@@ -317,11 +333,11 @@ k_ebe3tc(int nx, int ny, int nz, int nz_tile, const uint4* __restrict__ Bimg,
   const bool in_plane = owner && gi <= nx && gj <= ny;
 
   XPre pre;
-  x_fetch(pre, k0 - 1, EX0, EY0, nx, ny, nz, mask, x);
-  x_store(pre, sxr + ((k0 - 1) & 1) * LAYER_NODES * 3);
-  x_fetch(pre, k0, EX0, EY0, nx, ny, nz, mask, x);
-  x_store(pre, sxr + (k0 & 1) * LAYER_NODES * 3);
-  x_fetch(pre, k0 + 1, EX0, EY0, nx, ny, nz, mask, x);  // stored after layer k0 - 1 is built
+  x_fetch<TY>(pre, k0 - 1, EX0, EY0, nx, ny, nz, mask, x);
+  x_store<TY>(pre, sxr + ((k0 - 1) & 1) * LAYER_NODES * 3);
+  x_fetch<TY>(pre, k0, EX0, EY0, nx, ny, nz, mask, x);
+  x_store<TY>(pre, sxr + (k0 & 1) * LAYER_NODES * 3);
+  x_fetch<TY>(pre, k0 + 1, EX0, EY0, nx, ny, nz, mask, x);  // stored after layer k0 - 1 is built
   float e_cur = e_fetch(k0 - 1, EX0, EY0, nx, ny, nz, E);  // modulus of element layer ke
   float e_prev = 0.f;                                      // ... of layer ke - 1
   asm volatile("tcgen05.fence::before_thread_sync;\n" ::: "memory");
@@ -329,7 +345,7 @@ k_ebe3tc(int nx, int ny, int nz, int nz_tile, const uint4* __restrict__ Bimg,
   asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
   const uint32_t tmem = *tmem_slot;
   const uint32_t lane_base = (uint32_t)(32 * (warp & 3)) << 16;
-  const int mt = warp >> 2;  // M-tile of this thread's element row
+  const int mt = warp >> 2;  // M-tile of this thread's element row (TY = 8: two tiles)
 
   float acc[3] = {0.f, 0.f, 0.f};  // node layer ke - 1: contributions gathered so far
   FinData fd;                      // finishing data of node layer ke - 1
@@ -358,11 +374,12 @@ k_ebe3tc(int nx, int ny, int nz, int nz_tile, const uint4* __restrict__ Bimg,
     asm volatile("tcgen05.fence::before_thread_sync;\n" ::: "memory");
     __syncthreads();
     if (mma_now && tid == 0)
-      issue_mmas(tmem + (uint32_t)(j * 2 * NB), tmem + (uint32_t)A_COL, sbase + OFF_B, bar0 + 8u * j);
+      issue_mmas<MT>(tmem + (uint32_t)(j * MT * NB), tmem + (uint32_t)A_COL, sbase + OFF_B,
+                     bar0 + 8u * j);
     // refill the ring: node layer ke + 2 replaces layer ke (read by the row build above)
     if (mma_now && ke + 2 <= k1) {
-      x_store(pre, sxr + j * LAYER_NODES * 3);
-      if (ke + 3 <= k1) x_fetch(pre, ke + 3, EX0, EY0, nx, ny, nz, mask, x);
+      x_store<TY>(pre, sxr + j * LAYER_NODES * 3);
+      if (ke + 3 <= k1) x_fetch<TY>(pre, ke + 3, EX0, EY0, nx, ny, nz, mask, x);
     }
     const float e_next = (ke + 1 < k1) ? e_fetch(ke + 1, EX0, EY0, nx, ny, nz, E) : 0.f;
     // finishing data of node layer ke, used one step later
@@ -376,7 +393,7 @@ k_ebe3tc(int nx, int ny, int nz, int nz_tile, const uint4* __restrict__ Bimg,
       const bool fin = in_plane && kn >= k0;
       const int64_t node = node_id(gi, gj, kn, nx, ny);
       float v[24];
-      tmem_ld24(tmem + lane_base + (uint32_t)(jp * 2 * NB + mt * NB), v);
+      tmem_ld24(tmem + lane_base + (uint32_t)((jp * MT + mt) * NB), v);
       // x-pairs: node column ex gets the dx = 1 corners of element ex - 1 (previous lane) and
       // the dx = 0 corners of element ex; p[dy][dz][c]
 #pragma unroll
@@ -454,27 +471,37 @@ k_ebe3tc(int nx, int ny, int nz, int nz_tile, const uint4* __restrict__ Bimg,
   }
 }
 
-template <int MODE>
-void launch_mode(cudaStream_t s, const Ebe& op, const float* x, float* y, const float* b,
+template <int MODE, int TY>
+void launch_tile(cudaStream_t s, const Ebe& op, const float* x, float* y, const float* b,
                  const float* Dinv, double omega, const int* done) {
-  // dynamic shared memory per block, raised if needed so that at most two blocks share an SM:
-  // each holds 256 of the SM's 512 tensor-memory columns (a third would wait in tcgen05.alloc)
+  using C = Cfg<TY>;
+  // dynamic shared memory per block, raised if needed so that the blocks sharing an SM never
+  // ask for more than its 512 tensor-memory columns (a further block would wait in
+  // tcgen05.alloc)
   static int smem = 0;  // per instantiation
   if (smem == 0) {
-    int bytes = SMEM_ALLOC, per_sm = 0;
-    CK(cudaFuncSetAttribute(k_ebe3tc<MODE>, cudaFuncAttributeMaxDynamicSharedMemorySize, 100 << 10));
+    int bytes = C::SMEM_ALLOC, per_sm = 0;
+    CK(cudaFuncSetAttribute(k_ebe3tc<MODE, TY>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                            100 << 10));
     for (;;) {
-      CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_ebe3tc<MODE>, NT, bytes));
-      if (per_sm <= 2 || bytes >= (100 << 10)) break;
-      bytes += 8 << 10;
+      CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_ebe3tc<MODE, TY>, C::NT, bytes));
+      if (per_sm <= C::MAX_BLOCKS || bytes >= (100 << 10)) break;
+      bytes += 4 << 10;
     }
     smem = bytes;
   }
   const int nzt = op.tc_nz > 0 ? op.tc_nz : 8;
-  dim3 grid(ceil_div(op.nx + 1, ONX), ceil_div(op.ny + 1, ONY), ceil_div(op.nz + 1, nzt));
-  LAUNCH(k_ebe3tc<MODE>, grid, NT, smem, s, op.nx, op.ny, op.nz, nzt,
+  dim3 grid(ceil_div(op.nx + 1, ONX), ceil_div(op.ny + 1, C::ONY), ceil_div(op.nz + 1, nzt));
+  LAUNCH((k_ebe3tc<MODE, TY>), grid, C::NT, smem, s, op.nx, op.ny, op.nz, nzt,
          reinterpret_cast<const uint4*>(op.Ktc), (const float*)op.E, op.mask, x, y, b, Dinv,
          (float)omega, done);
+}
+
+template <int MODE>
+void launch_mode(cudaStream_t s, const Ebe& op, const float* x, float* y, const float* b,
+                 const float* Dinv, double omega, const int* done) {
+  if (op.tc_ty == 4) launch_tile<MODE, 4>(s, op, x, y, b, Dinv, omega, done);
+  else launch_tile<MODE, 8>(s, op, x, y, b, Dinv, omega, done);
 }
 
 }  // namespace
@@ -509,8 +536,9 @@ void ebe3d_tc_launch(cudaStream_t s, int mode, const Ebe& op, const float* x, fl
   else launch_mode<MODE_JACOBI>(s, op, x, y, b, Dinv, omega, done);
 }
 
-// fastest node-layer count per block for this grid: each candidate timed on the stream with
-// scratch vectors the first time a grid shape is seen, cached per shape afterwards
+// fastest tile shape for this grid (element rows per block 8 or 4, node layers per block 4 to
+// 32): each candidate timed on the stream with scratch vectors the first time a grid shape is
+// seen, cached per shape afterwards.  Returns rows * 1000 + layers.
 int ebe3d_tc_autotune(cudaStream_t s, const Ebe& op, const float* Dinv) {
   static std::mutex mu;
   static std::map<std::tuple<int, int, int>, int> cache;
@@ -530,12 +558,16 @@ int ebe3d_tc_autotune(cudaStream_t s, const Ebe& op, const float* Dinv) {
   cudaEvent_t e0, e1;
   CK(cudaEventCreate(&e0));
   CK(cudaEventCreate(&e1));
-  int best = 8;
+  int best = 8, best_ty = 8;
   float best_ms = 1e30f;
-  for (int nzt : {8, 4, 16, 32}) {
-    if (nzt > 8 && nzt / 2 >= op.nz + 1) break;  // no more blocks to split off
+  for (int cand = 0; cand < 8; cand++) {
+    const int ty = cand < 4 ? 8 : 4;
+    static const int nz_options[4] = {8, 4, 16, 32};
+    const int nzt = nz_options[cand % 4];
+    if (nzt > 8 && nzt / 2 >= op.nz + 1) continue;  // no more blocks to split off
     Ebe o = op;
     o.tc_nz = nzt;
+    o.tc_ty = ty;
     launch_mode<MODE_JACOBI>(s, o, x.p, y.p, b.p, Dinv, 0.5, nullptr);
     CK(cudaEventRecord(e0, s));
     for (int r = 0; r < 5; r++) launch_mode<MODE_JACOBI>(s, o, x.p, y.p, b.p, Dinv, 0.5, nullptr);
@@ -546,13 +578,15 @@ int ebe3d_tc_autotune(cudaStream_t s, const Ebe& op, const float* Dinv) {
     if (ms < 0.97f * best_ms) {
       best_ms = ms;
       best = nzt;
+      best_ty = ty;
     }
   }
   cudaEventDestroy(e0);
   cudaEventDestroy(e1);
+  const int code = best_ty * 1000 + best;
   std::lock_guard<std::mutex> g(mu);
-  cache[key] = best;
-  return best;
+  cache[key] = code;
+  return code;
 }
 
 // reads and clears the error word of the tensor-core kernel (synchronises the stream)

@@ -29,6 +29,7 @@ struct Ebe {
   // split Ke operand images (ebe3d_tc_operand), tc_nz the node layers per block (0 = 8)
   int tc = 0;
   int tc_nz = 0;
+  int tc_ty = 0;   // element rows per block of the tensor-core kernel (8 or 4; 0 = 8)
   const void* Ktc = nullptr;
 };
 template <class T>
@@ -52,7 +53,8 @@ void ebe3d_tc_launch(cudaStream_t s, int mode, const Ebe& op, const float* x, fl
 // Ke (24 x 24, FP64) -> TF32 hi and lo B-operand images in the kernel's shared-memory layout
 void ebe3d_tc_operand(const double* Ke, uint32_t* img);
 int ebe3d_tc_operand_words();
-// fastest node layers per block (tc_nz) for this grid, timed once per grid shape and cached
+// fastest tile of the tensor-core kernel for this grid, rows * 1000 + node layers per block
+// (tc_ty, tc_nz), timed once per grid shape and cached
 int ebe3d_tc_autotune(cudaStream_t s, const Ebe& op, const float* Dinv);
 // true if a tensor-core kernel gave up waiting for its MMAs since the last call (syncs s)
 bool ebe3d_tc_error(cudaStream_t s);

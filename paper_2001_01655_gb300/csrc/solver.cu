@@ -117,6 +117,7 @@ template <> struct V<float> {
     const bool tc = P->tc_mode >= 0 ? P->tc_mode != 0 : P->opt.prec == TOMG_PREC_3XTF32_VCYCLE;
     op.tc = (P->dim == 3 && tc && P->Ketc.p) ? 1 : 0;
     op.tc_nz = P->tc_nz;
+    op.tc_ty = P->tc_ty;
     op.Ktc = P->Ketc.p;
     return op;
   }
@@ -660,7 +661,9 @@ void setup(tomg_problem* P, const tomg_options& opt) {
       P->ebe_tile = ebe2d_autotune(s, V<float>::ebe(P), L0->D32.p);
     if (P->dim == 3 && opt.prec == TOMG_PREC_3XTF32_VCYCLE && P->tc_nz == 0 && P->Ketc.p) {
       TcScope tcs(P, TOMG_PREC_3XTF32_VCYCLE);
-      P->tc_nz = ebe3d_tc_autotune(s, V<float>::ebe(P), L0->D32.p);
+      const int code = ebe3d_tc_autotune(s, V<float>::ebe(P), L0->D32.p);
+      P->tc_nz = code % 1000;
+      P->tc_ty = code / 1000;
     }
     P->L.push_back(std::move(L0));
   }
