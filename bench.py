@@ -66,7 +66,8 @@ def parse():
     ap.add_argument("--kernel-grid", default="2048x1024",
                     help="element counts of the cantilever used by --kernel (NXxNY or NXxNYxNZ)")
     ap.add_argument("--kernel-reps", type=int, default=20)
-    ap.add_argument("--no-fp64", action="store_true")
+    ap.add_argument("--no-fp64", action="store_true",
+                    help="skip the comparison variants (FP64 V-cycle, the paper's Jacobi sweep)")
     ap.add_argument("--no-cpu", action="store_true")
     return ap.parse_args()
 
@@ -235,7 +236,7 @@ def run_gpu(args, rank, world, local):
                        "iterations": statistics.median(i64),
                        "setup_ms": statistics.median(r["setup_ms"] for r in r64),
                        "solve_ms": statistics.median(r["solve_ms"] for r in r64)}
-    if args.smoother != "jacobi":
+    if args.smoother != "jacobi" and not args.no_fp64:
         # the paper's smoother (one weighted point-block Jacobi sweep), mixed and FP64
         oj = dict(opts, smoother="jacobi")
         jac = {}
@@ -292,11 +293,27 @@ def batched_run(tomg, ctx, slots, reps=3, prec="tf32x3", smoother="jacobi", cheb
         res[conc] = {"solves_per_s": p.nrhs / t, "ms_all_rhs": 1e3 * t,
                      "iterations_median": statistics.median(its), "rel_residual_max": worst,
                      "setup_ms": r[0]["setup_ms"]}
+    # the level-0 FP32 kernels of this case timed alone (cold L2, CUDA events), with the
+    # minimum-traffic bytes of one launch
+    peaks = load_peaks()
+    hbm = peaks.get("hbm_gbs", 6800.0)
+    kern = {}
+    for name in ("residual", "jacobi"):
+        for kp in ("tf32x3", "fp32"):
+            ms = P.time_fine_operator(name, kp, reps=20, cold_l2=True)
+            nb = kernel_bytes(name, kp, p)
+            kern["%s_%s" % (name, kp)] = {
+                "kernel": "k_ebe3tc (tcgen05 3xTF32)" if kp == "tf32x3" else "k_ebe3 (CUDA cores)",
+                "ms_per_launch": ms, "algorithmic_bytes": nb,
+                "achieved_gbs": nb / (ms * 1e-3) / 1e9, "frac_hbm": nb / (ms * 1e-3) / 1e9 / hbm,
+                "element_gflops": 1152.0 * p.nel / (ms * 1e-3) / 1e9}
+    res["kernels"] = kern
     return {"workload": "3D cantilever hex8 128x64x64 (1,635,075 DOFs), 8 point loads + 8 "
                         "adjoint-like right-hand sides, hybrid hierarchy, %s V-cycle" %
                         ("FP32 (3xTF32 tensor-core element contractions)" if prec == "tf32x3"
                          else "FP32"),
-            "rhs": p.nrhs, "concurrent": dict(res[slots], slots=slots), "one_at_a_time": res[1]}
+            "rhs": p.nrhs, "concurrent": dict(res[slots], slots=slots), "one_at_a_time": res[1],
+            "level0_kernels": res["kernels"]}
 
 
 def serving_run(tomg, ctx, n_requests, n_updates, slots):

@@ -72,7 +72,7 @@ struct Cfg {
   static constexpr int OFF_B = 0;                                               // B_hi, B_lo
   static constexpr int OFF_X = OFF_B + 2 * B_BYTES;                             // x ring
   static constexpr int OFF_P = (OFF_X + 2 * LAYER_NODES * 3 * 4 + 15) / 16 * 16;  // y pairs
-  static constexpr int OFF_BAR = OFF_P + NT * PS * 4;     // 2 mbarriers + TMEM address
+  static constexpr int OFF_BAR = OFF_P + 2 * NT * PS * 4; // 2 mbarriers + TMEM address
   static constexpr int SMEM_ALLOC = OFF_BAR + 24 + 128;   // + room to align the base
   static_assert(A_COL + 48 * MT <= TMEM_COLS, "tensor memory map");
   static_assert(OFF_X % 16 == 0 && OFF_P % 16 == 0 && OFF_BAR % 8 == 0, "alignment");
@@ -302,7 +302,7 @@ k_ebe3tc(int nx, int ny, int nz, int nz_tile, const uint4* __restrict__ Bimg,
   if (solve_done(done)) return;
   uint8_t* sm = smem_raw + ((128 - (smem_u32(smem_raw) & 127u)) & 127u);
   float* sxr = reinterpret_cast<float*>(sm + OFF_X);          // [2][LAYER_NODES][3]
-  float* sP = reinterpret_cast<float*>(sm + OFF_P);           // [TEY][TEX][PS]
+  float* sP = reinterpret_cast<float*>(sm + OFF_P);           // [2][TY][TEX][PS]
   uint64_t* bar = reinterpret_cast<uint64_t*>(sm + OFF_BAR);  // [2]
   uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(sm + OFF_BAR + 16);
   const uint32_t sbase = smem_u32(sm);
@@ -332,11 +332,11 @@ k_ebe3tc(int nx, int ny, int nz, int nz_tile, const uint4* __restrict__ Bimg,
   const int gi = EX0 + ex, gj = EY0 + ey;
   const bool in_plane = owner && gi <= nx && gj <= ny;
 
-  XPre pre;
+  XPre pre, pre2;
   x_fetch<TY>(pre, k0 - 1, EX0, EY0, nx, ny, nz, mask, x);
+  x_fetch<TY>(pre2, k0, EX0, EY0, nx, ny, nz, mask, x);
   x_store<TY>(pre, sxr + ((k0 - 1) & 1) * LAYER_NODES * 3);
-  x_fetch<TY>(pre, k0, EX0, EY0, nx, ny, nz, mask, x);
-  x_store<TY>(pre, sxr + (k0 & 1) * LAYER_NODES * 3);
+  x_store<TY>(pre2, sxr + (k0 & 1) * LAYER_NODES * 3);
   x_fetch<TY>(pre, k0 + 1, EX0, EY0, nx, ny, nz, mask, x);  // stored after layer k0 - 1 is built
   float e_cur = e_fetch(k0 - 1, EX0, EY0, nx, ny, nz, E);  // modulus of element layer ke
   float e_prev = 0.f;                                      // ... of layer ke - 1
@@ -355,24 +355,24 @@ k_ebe3tc(int nx, int ny, int nz, int nz_tile, const uint4* __restrict__ Bimg,
   for (int ke = k0 - 1; ke <= k1; ke++) {
     const bool mma_now = ke < k1;  // the last step only finishes layer k1 - 1
     const int j = ke & 1, jp = j ^ 1;
+    bool ok = true;
     if (ke >= k0) {
-      // the MMAs of layer ke - 1: their accumulators are read below, their A operands are
-      // overwritten now
-      const bool ok = mbar_wait(bar0 + 8u * jp, (parity >> jp) & 1u);
+      // the MMAs of layer ke - 1 (every thread waits itself): their accumulators are read
+      // below, their A operands are overwritten now
+      ok = mbar_wait(bar0 + 8u * jp, (parity >> jp) & 1u);
       parity ^= 1u << jp;
-      if (__syncthreads_or(!ok)) {
-        failed = true;
-        break;
-      }
       asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
     }
-    if (mma_now) {
+    if (ok && mma_now) {
       uint32_t v[2 * KD];
       a_row(v, sxr + j * LAYER_NODES * 3, sxr + jp * LAYER_NODES * 3, ex, ey);
       tmem_st48(tmem + lane_base + (uint32_t)(A_COL + 48 * mt), v);
     }
     asm volatile("tcgen05.fence::before_thread_sync;\n" ::: "memory");
-    __syncthreads();
+    if (__syncthreads_or(!ok)) {  // a wait that ran out anywhere stops the whole block
+      failed = true;
+      break;
+    }
     if (mma_now && tid == 0)
       issue_mmas<MT>(tmem + (uint32_t)(j * MT * NB), tmem + (uint32_t)A_COL, sbase + OFF_B,
                      bar0 + 8u * j);
@@ -387,18 +387,15 @@ k_ebe3tc(int nx, int ny, int nz, int nz_tile, const uint4* __restrict__ Bimg,
     const bool fin_next = in_plane && ke >= k0 && ke < k1;
     fin_fetch<MODE>(fd_next, fin_next, node_id(gi, gj, ke, nx, ny), mask, x, b, Dinv);
 
+    float pr[2][2][3];  // x-pair sums of element layer ke - 1 at node column ex: [dy][dz][c]
     if (ke >= k0) {
       // finish element layer ke - 1 and node layer ke - 1
-      const int kn = ke - 1;
-      const bool fin = in_plane && kn >= k0;
-      const int64_t node = node_id(gi, gj, kn, nx, ny);
       float v[24];
       tmem_ld24(tmem + lane_base + (uint32_t)((jp * MT + mt) * NB), v);
       // x-pairs: node column ex gets the dx = 1 corners of element ex - 1 (previous lane) and
       // the dx = 0 corners of element ex; p[dy][dz][c]
 #pragma unroll
       for (int n = 0; n < 24; n++) v[n] *= e_prev;
-      float pr[2][2][3];
 #pragma unroll
       for (int dy = 0; dy < 2; dy++)
 #pragma unroll
@@ -409,15 +406,21 @@ k_ebe3tc(int nx, int ny, int nz, int nz_tile, const uint4* __restrict__ Bimg,
             pr[dy][dz][c] = v[3 * (2 * dy + 4 * dz) + c] + left;  // lane 0: not an owned node
           }
       // y-pairs: node row ey gets the dy = 1 sums of element row ey - 1 through shared memory
-      float* myP = sP + (ey * TEX + ex) * PS;
+      float* myP = sP + (j * NT + ey * TEX + ex) * PS;
 #pragma unroll
       for (int dz = 0; dz < 2; dz++)
 #pragma unroll
         for (int c = 0; c < 3; c++) myP[3 * dz + c] = pr[1][dz][c];
       asm volatile("tcgen05.fence::before_thread_sync;\n" ::: "memory");
-      __syncthreads();
+    }
+    // makes the y-pair partials and the ring layer stored above visible to the block
+    __syncthreads();
+    if (ke >= k0) {
+      const int kn = ke - 1;
+      const bool fin = in_plane && kn >= k0;
+      const int64_t node = node_id(gi, gj, kn, nx, ny);
       if (owner) {
-        const float* upP = sP + ((ey - 1) * TEX + ex) * PS;
+        const float* upP = sP + (j * NT + (ey - 1) * TEX + ex) * PS;
         float top[3];
 #pragma unroll
         for (int c = 0; c < 3; c++) {
@@ -453,7 +456,6 @@ k_ebe3tc(int nx, int ny, int nz, int nz_tile, const uint4* __restrict__ Bimg,
     e_prev = e_cur;
     e_cur = e_next;
     fd = fd_next;
-    __syncthreads();
   }
 
   if (failed) {
