@@ -183,6 +183,25 @@ __device__ __forceinline__ void jacobi_first(const T* __restrict__ Dinv, const T
   }
 }
 
+// Chebyshev smoother step at one node (B components) from its residual r = b - A x:
+// dn = c1 d_prev + c2 Dinv r, y = x + dn, d = dn; d_prev = 0 (dmode 0), d (1) or x (2)
+template <class T, int B>
+__device__ __forceinline__ void cheb_node(int64_t node, const T* r, const T* xi,
+                                          const T* __restrict__ Dinv, T c1, T c2, int dmode,
+                                          T* __restrict__ d, T* __restrict__ y) {
+  const T* D = Dinv + (int64_t)B * B * node;
+#pragma unroll
+  for (int q = 0; q < B; q++) {
+    T v = T(0);
+#pragma unroll
+    for (int c = 0; c < B; c++) v += D[q * B + c] * r[c];
+    const T prev = dmode == 2 ? xi[q] : (dmode == 1 ? d[(int64_t)B * node + q] : T(0));
+    const T dn = c1 * prev + c2 * v;
+    y[(int64_t)B * node + q] = xi[q] + dn;
+    d[(int64_t)B * node + q] = dn;
+  }
+}
+
 }  // namespace tomg
 
 namespace tomg {

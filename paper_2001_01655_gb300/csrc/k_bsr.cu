@@ -30,7 +30,8 @@ __global__ void __launch_bounds__(256) k_bsr(int nbr, const int* __restrict__ rp
                                              const int* __restrict__ ci, const T* __restrict__ V,
                                              const T* __restrict__ x, T* __restrict__ y,
                                              const T* __restrict__ b, const T* __restrict__ Dinv,
-                                             T omega, const int* done, T* __restrict__ xo) {
+                                             T omega, const int* done, T* __restrict__ xo, T c1,
+                                             int dmode) {
   pdl_prologue();
   if (solve_done(done)) return;
   const int gtid = blockIdx.x * blockDim.x + threadIdx.x;
@@ -72,6 +73,14 @@ __global__ void __launch_bounds__(256) k_bsr(int nbr, const int* __restrict__ rp
   } else if (MODE == MODE_RESID) {
 #pragma unroll
     for (int r = 0; r < B; r++) y[(int64_t)B * i + r] = b[(int64_t)B * i + r] - acc[r];
+  } else if (MODE == MODE_CHEB) {
+    T res[B], xi[B];
+#pragma unroll
+    for (int r = 0; r < B; r++) {
+      res[r] = b[(int64_t)B * i + r] - acc[r];
+      xi[r] = x[(int64_t)B * i + r];
+    }
+    cheb_node<T, B>(i, res, xi, Dinv, c1, omega, dmode, xo, y);
   } else {
     T res[B];
 #pragma unroll
@@ -434,11 +443,14 @@ void scan_rec(cudaStream_t s, const int* in, int* out, int64_t n, int* total_dev
 
 template <class T>
 void bsr_op(cudaStream_t s, int mode, const Bsr& A, const T* V, const T* x, T* y, const T* b,
-            const T* Dinv, double omega, const int* done) {
+            const T* Dinv, double omega, const int* done, const ChebArg* ch) {
   const int G = lanes_for(A);
   const int grid = ceil_div((int64_t)A.nbr * G, 256);
-  T* xo = mode == MODE_RESID0 ? const_cast<T*>(x) : nullptr;
-#define BOP(B, M, GG) LAUNCH((k_bsr<T, B, M, GG>), grid, 256, 0, s, A.nbr, A.rp, A.ci, V, x, y, b, Dinv, (T)omega, done, xo)
+  if (mode == MODE_CHEB && !ch) TOMG_THROW(TOMG_E_INVALID, "Chebyshev step without its state");
+  T* xo = mode == MODE_RESID0 ? const_cast<T*>(x) : (mode == MODE_CHEB ? (T*)ch->d : nullptr);
+  const T c1 = mode == MODE_CHEB ? (T)ch->c1 : T(0);
+  const int dm = mode == MODE_CHEB ? ch->dmode : 0;
+#define BOP(B, M, GG) LAUNCH((k_bsr<T, B, M, GG>), grid, 256, 0, s, A.nbr, A.rp, A.ci, V, x, y, b, Dinv, (T)omega, done, xo, c1, dm)
 #define BG(B, M)                         \
   if (G == 4) BOP(B, M, 4);              \
   else if (G == 8) BOP(B, M, 8);         \
@@ -448,6 +460,7 @@ void bsr_op(cudaStream_t s, int mode, const Bsr& A, const T* V, const T* x, T* y
   if (mode == MODE_APPLY) { BG(B, MODE_APPLY) }     \
   else if (mode == MODE_RESID) { BG(B, MODE_RESID) } \
   else if (mode == MODE_RESID0) { BG(B, MODE_RESID0) } \
+  else if (mode == MODE_CHEB) { BG(B, MODE_CHEB) } \
   else { BG(B, MODE_JACOBI) }
   if (A.br == 2) { BMODES(2) }
   else if (A.br == 3) { BMODES(3) }
@@ -458,9 +471,9 @@ void bsr_op(cudaStream_t s, int mode, const Bsr& A, const T* V, const T* x, T* y
 #undef BOP
 }
 template void bsr_op<float>(cudaStream_t, int, const Bsr&, const float*, const float*, float*,
-                            const float*, const float*, double, const int*);
+                            const float*, const float*, double, const int*, const ChebArg*);
 template void bsr_op<double>(cudaStream_t, int, const Bsr&, const double*, const double*, double*,
-                             const double*, const double*, double, const int*);
+                             const double*, const double*, double, const int*, const ChebArg*);
 
 template <class T>
 void bsr_spmv_rect(cudaStream_t s, const Bsr& A, const T* V, const T* x, T* y, int accumulate,

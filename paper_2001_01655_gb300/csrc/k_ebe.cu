@@ -17,7 +17,8 @@ __global__ void __launch_bounds__(256) k_ebe(int nx, int ny, int nz, const T* __
                                              const uint8_t* __restrict__ mask,
                                              const T* __restrict__ x, T* __restrict__ y,
                                              const T* __restrict__ b, const T* __restrict__ Dinv,
-                                             T omega, const int* done, double* partials) {
+                                             T omega, const int* done, double* partials,
+                                             T* __restrict__ dch, T c1, int dmode) {
   constexpr int NN = 1 << DIM, ND = DIM * NN;
   __shared__ T sKe[ND * ND];
   __shared__ double sred[32];
@@ -76,6 +77,11 @@ __global__ void __launch_bounds__(256) k_ebe(int nx, int ny, int nz, const T* __
     } else if (MODE == MODE_RESID) {
 #pragma unroll
       for (int c = 0; c < DIM; c++) y[DIM * node + c] = b[DIM * node + c] - Ax[c];
+    } else if (MODE == MODE_CHEB) {
+      T r[DIM];
+#pragma unroll
+      for (int c = 0; c < DIM; c++) r[c] = b[DIM * node + c] - Ax[c];
+      cheb_node<T, DIM>(node, r, xi, Dinv, c1, omega, dmode, dch, y);
     } else {
       T r[DIM];
 #pragma unroll
@@ -195,28 +201,33 @@ inline int64_t nodes_of(const Ebe& op) {
 
 template <class T, int DIM, int MODE, bool DOT>
 void launch_ebe(cudaStream_t s, const Ebe& op, const T* x, T* y, const T* b, const T* Dinv,
-                double omega, const int* done, double* parts) {
+                double omega, const int* done, double* parts, const ChebArg* ch = nullptr) {
   // FP32 quad4: tiled kernel (memory/latency bound).  FP64: the node-per-thread kernel, whose
   // low register count keeps enough warps in flight to hide the long FP64 pipe latency.
   if (DIM == 3 && sizeof(T) == 4 && !DOT && op.tc) {
     ebe3d_tc_launch(s, MODE, op, reinterpret_cast<const float*>(x), reinterpret_cast<float*>(y),
                     reinterpret_cast<const float*>(b), reinterpret_cast<const float*>(Dinv),
-                    omega, done);
+                    omega, done, ch);
     return;
   }
   if (DIM == 3 && sizeof(T) == 4 && !DOT) {
     ebe3d_launch(s, MODE, op, reinterpret_cast<const float*>(x), reinterpret_cast<float*>(y),
                  reinterpret_cast<const float*>(b), reinterpret_cast<const float*>(Dinv), omega,
-                 done);
+                 done, ch);
     return;
   }
   if (DIM == 2 && sizeof(T) == 4) {
-    ebe2d_launch<T, MODE, DOT>(s, op, x, y, b, Dinv, omega, done, parts);
+    ebe2d_launch<T, MODE, DOT>(s, op, x, y, b, Dinv, omega, done, parts, ch);
     return;
   }
+  if (MODE == MODE_CHEB && !ch) TOMG_THROW(TOMG_E_INVALID, "Chebyshev step without its state");
+  T* dch = MODE == MODE_CHEB ? (T*)ch->d : nullptr;
+  const T c1 = MODE == MODE_CHEB ? (T)ch->c1 : T(0);
+  const int dm = MODE == MODE_CHEB ? ch->dmode : 0;
   const int64_t nn = nodes_of(op);
   LAUNCH((k_ebe<T, DIM, MODE, DOT>), ceil_div(nn, 256), 256, 0, s, op.nx, op.ny, op.nz,
-         (const T*)op.Ke, (const T*)op.E, op.mask, x, y, b, Dinv, (T)omega, done, parts);
+         (const T*)op.Ke, (const T*)op.E, op.mask, x, y, b, Dinv, (T)omega, done, parts, dch, c1,
+         dm);
 }
 
 }  // namespace
@@ -228,7 +239,12 @@ int ebe_blocks(const Ebe& op) {
 
 template <class T>
 void ebe_op(cudaStream_t s, int mode, const Ebe& op, const T* x, T* y, const T* b, const T* Dinv,
-            double omega, const int* done, double* parts) {
+            double omega, const int* done, double* parts, const ChebArg* ch) {
+  if (mode == MODE_CHEB) {
+    if (op.dim == 2) launch_ebe<T, 2, MODE_CHEB, false>(s, op, x, y, b, Dinv, omega, done, parts, ch);
+    else launch_ebe<T, 3, MODE_CHEB, false>(s, op, x, y, b, Dinv, omega, done, parts, ch);
+    return;
+  }
   if (op.dim == 2) {
     if (mode == MODE_APPLY) {
       if (parts) launch_ebe<T, 2, MODE_APPLY, true>(s, op, x, y, b, Dinv, omega, done, parts);
@@ -256,9 +272,9 @@ void ebe_op(cudaStream_t s, int mode, const Ebe& op, const T* x, T* y, const T* 
   }
 }
 template void ebe_op<float>(cudaStream_t, int, const Ebe&, const float*, float*, const float*,
-                            const float*, double, const int*, double*);
+                            const float*, double, const int*, double*, const ChebArg*);
 template void ebe_op<double>(cudaStream_t, int, const Ebe&, const double*, double*, const double*,
-                             const double*, double, const int*, double*);
+                             const double*, double, const int*, double*, const ChebArg*);
 
 void ebe_block_diag_inv(cudaStream_t s, const Ebe& op, double* Dinv64, float* Dinv32) {
   const int64_t nn = nodes_of(op);

@@ -38,7 +38,7 @@ __global__ void __launch_bounds__(BX * BY) k_ebe2(int nx, int ny, const KeP2<T> 
                                                   const T* __restrict__ b,
                                                   const T* __restrict__ Dinv, T omega,
                                                   const int* done, double* partials,
-                                                  T* __restrict__ xo) {
+                                                  T* __restrict__ xo, T c1, int dmode) {
   using V2 = typename V2t<T>::type;
   constexpr int TH = BY * NPT;
   __shared__ V2 sx[TH + 2][BX + 2];
@@ -176,6 +176,18 @@ __global__ void __launch_bounds__(BX * BY) k_ebe2(int nx, int ny, const KeP2<T> 
       if (MODE == MODE_RESID || MODE == MODE_RESID0) {
         out.x = r0v;
         out.y = r1v;
+      } else if (MODE == MODE_CHEB) {
+        const T* D = Dinv + 4 * (int64_t)node;
+        const T v0 = D[0] * r0v + D[1] * r1v, v1 = D[2] * r0v + D[3] * r1v;
+        V2 dp = {T(0), T(0)};
+        if (dmode == 2) dp = xi;
+        else if (dmode == 1) dp = reinterpret_cast<const V2*>(xo)[node];
+        V2 dn;
+        dn.x = c1 * dp.x + omega * v0;
+        dn.y = c1 * dp.y + omega * v1;
+        out.x = xi.x + dn.x;
+        out.y = xi.y + dn.y;
+        reinterpret_cast<V2*>(xo)[node] = dn;
       } else {
         const T* D = Dinv + 4 * (int64_t)node;
         out.x = xi.x + omega * (D[0] * r0v + D[1] * r1v);
@@ -207,15 +219,18 @@ int ebe2d_blocks(const Ebe& op) {
 
 template <class T, int MODE, bool DOT>
 void ebe2d_launch(cudaStream_t s, const Ebe& op, const T* x, T* y, const T* b, const T* Dinv,
-                  double omega, const int* done, double* parts) {
-  T* xo = MODE == MODE_RESID0 ? const_cast<T*>(x) : nullptr;
+                  double omega, const int* done, double* parts, const ChebArg* ch) {
+  if (MODE == MODE_CHEB && !ch) TOMG_THROW(TOMG_E_INVALID, "Chebyshev step without its state");
+  T* xo = MODE == MODE_RESID0 ? const_cast<T*>(x) : (MODE == MODE_CHEB ? (T*)ch->d : nullptr);
+  const T c1 = MODE == MODE_CHEB ? (T)ch->c1 : T(0);
+  const int dm = MODE == MODE_CHEB ? ch->dmode : 0;
   const int npt = DOT ? 4 : (op.tile == 1 || op.tile == 2 ? op.tile : 4);  // dots: fixed tile
   dim3 grid(ceil_div(op.nx + 1, BX), ceil_div(op.ny + 1, BY * npt));
   if (!op.Kh) TOMG_THROW(TOMG_E_INVALID, "tiled element kernel without a host copy of Ke");
   KeP2<T> K;
   memcpy(K.v, op.Kh, sizeof(K.v));
 #define EB(N) LAUNCH((k_ebe2<T, MODE, DOT, N>), grid, dim3(BX, BY), 0, s, op.nx, op.ny, K,     \
-                     (const T*)op.E, op.mask, x, y, b, Dinv, (T)omega, done, parts, xo)
+                     (const T*)op.E, op.mask, x, y, b, Dinv, (T)omega, done, parts, xo, c1, dm)
   if (npt == 1) EB(1);
   else if (npt == 2) EB(2);
   else EB(4);
@@ -268,11 +283,11 @@ int ebe2d_autotune(cudaStream_t s, const Ebe& op, const float* Dinv) {
 
 #define INST(T, M, D)                                                                      \
   template void ebe2d_launch<T, M, D>(cudaStream_t, const Ebe&, const T*, T*, const T*,     \
-                                      const T*, double, const int*, double*);
+                                      const T*, double, const int*, double*, const ChebArg*);
 INST(float, MODE_APPLY, true) INST(float, MODE_APPLY, false) INST(float, MODE_RESID, false)
 INST(float, MODE_JACOBI, false) INST(float, MODE_RESID0, false) INST(double, MODE_APPLY, true)
 INST(double, MODE_APPLY, false) INST(double, MODE_RESID, false) INST(double, MODE_JACOBI, false)
-INST(double, MODE_RESID0, false)
+INST(double, MODE_RESID0, false) INST(float, MODE_CHEB, false) INST(double, MODE_CHEB, false)
 #undef INST
 
 }  // namespace tomg

@@ -24,7 +24,8 @@ __global__ void __launch_bounds__(NTH) k_ebe3(int nx, int ny, int nz, const floa
                                               const float* __restrict__ x, float* __restrict__ y,
                                               const float* __restrict__ b,
                                               const float* __restrict__ Dinv, float omega,
-                                              const int* done) {
+                                              const int* done, float* __restrict__ dch, float c1,
+                                              int dmode) {
   __shared__ __align__(16) float sKe[576];
   __shared__ float sx[SXZ][SXY][SXX][3];
   __shared__ float sE[SEZ][SEY][SEX];
@@ -138,6 +139,8 @@ __global__ void __launch_bounds__(NTH) k_ebe3(int nx, int ny, int nz, const floa
       if (MODE == MODE_RESID) {
 #pragma unroll
         for (int c = 0; c < 3; c++) y[3 * node + c] = r[c];
+      } else if (MODE == MODE_CHEB) {
+        cheb_node<float, 3>(node, r, xi, Dinv, c1, omega, dmode, dch, y);
       } else {
         const float* D = Dinv + 9 * node;
 #pragma unroll
@@ -151,20 +154,23 @@ __global__ void __launch_bounds__(NTH) k_ebe3(int nx, int ny, int nz, const floa
 }  // namespace
 
 void ebe3d_launch(cudaStream_t s, int mode, const Ebe& op, const float* x, float* y,
-                  const float* b, const float* Dinv, double omega, const int* done) {
+                  const float* b, const float* Dinv, double omega, const int* done,
+                  const ChebArg* ch) {
   dim3 grid(ceil_div(op.nx + 1, BX), ceil_div(op.ny + 1, BY), ceil_div(op.nz + 1, TZ));
   dim3 block(BX, BY);
   const float* Ke = (const float*)op.Ke;
   const float* E = (const float*)op.E;
-  if (mode == MODE_APPLY)
-    LAUNCH(k_ebe3<MODE_APPLY>, grid, block, 0, s, op.nx, op.ny, op.nz, Ke, E, op.mask, x, y, b,
-           Dinv, (float)omega, done);
-  else if (mode == MODE_RESID)
-    LAUNCH(k_ebe3<MODE_RESID>, grid, block, 0, s, op.nx, op.ny, op.nz, Ke, E, op.mask, x, y, b,
-           Dinv, (float)omega, done);
-  else
-    LAUNCH(k_ebe3<MODE_JACOBI>, grid, block, 0, s, op.nx, op.ny, op.nz, Ke, E, op.mask, x, y, b,
-           Dinv, (float)omega, done);
+  if (mode == MODE_CHEB && !ch) TOMG_THROW(TOMG_E_INVALID, "Chebyshev step without its state");
+  float* dch = mode == MODE_CHEB ? (float*)ch->d : nullptr;
+  const float c1 = mode == MODE_CHEB ? (float)ch->c1 : 0.f;
+  const int dm = mode == MODE_CHEB ? ch->dmode : 0;
+#define E3(M) LAUNCH(k_ebe3<M>, grid, block, 0, s, op.nx, op.ny, op.nz, Ke, E, op.mask, x, y, b, \
+                     Dinv, (float)omega, done, dch, c1, dm)
+  if (mode == MODE_APPLY) E3(MODE_APPLY);
+  else if (mode == MODE_RESID) E3(MODE_RESID);
+  else if (mode == MODE_CHEB) E3(MODE_CHEB);
+  else E3(MODE_JACOBI);
+#undef E3
 }
 
 }  // namespace tomg

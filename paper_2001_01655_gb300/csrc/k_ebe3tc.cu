@@ -236,7 +236,7 @@ __device__ __forceinline__ void fin_fetch(FinData& f, bool valid, int64_t node,
 #pragma unroll
     for (int c = 0; c < 3; c++) f.b[c] = __ldg(b + 3 * node + c);
   }
-  if (MODE == MODE_JACOBI) {
+  if (MODE == MODE_JACOBI || MODE == MODE_CHEB) {
 #pragma unroll
     for (int c = 0; c < 9; c++) f.D[c] = __ldg(Dinv + 9 * node + c);
   }
@@ -292,7 +292,8 @@ __global__ void __launch_bounds__(Cfg<TY>::NT, Cfg<TY>::MAX_BLOCKS)
 k_ebe3tc(int nx, int ny, int nz, int nz_tile, const uint4* __restrict__ Bimg,
          const float* __restrict__ E, const uint8_t* __restrict__ mask,
          const float* __restrict__ x, float* __restrict__ y, const float* __restrict__ b,
-         const float* __restrict__ Dinv, float omega, const int* done) {
+         const float* __restrict__ Dinv, float omega, const int* done, float* __restrict__ dch,
+         float c1, int dmode) {
   using C = Cfg<TY>;
   constexpr int NT = C::NT, LAYER_NODES = C::LAYER_NODES, ONY = C::ONY, MT = C::MT;
   constexpr int OFF_B = C::OFF_B, OFF_X = C::OFF_X, OFF_P = C::OFF_P, OFF_BAR = C::OFF_BAR;
@@ -441,6 +442,15 @@ k_ebe3tc(int nx, int ny, int nz, int nz_tile, const uint4* __restrict__ Bimg,
             if (MODE == MODE_RESID) {
 #pragma unroll
               for (int c = 0; c < 3; c++) y[3 * node + c] = r[c];
+            } else if (MODE == MODE_CHEB) {
+#pragma unroll
+              for (int c = 0; c < 3; c++) {
+                const float v = fd.D[3 * c] * r[0] + fd.D[3 * c + 1] * r[1] + fd.D[3 * c + 2] * r[2];
+                const float prev = dmode == 2 ? fd.x[c] : (dmode == 1 ? dch[3 * node + c] : 0.f);
+                const float dn = c1 * prev + omega * v;
+                y[3 * node + c] = fd.x[c] + dn;
+                dch[3 * node + c] = dn;
+              }
             } else {
 #pragma unroll
               for (int c = 0; c < 3; c++)
@@ -475,7 +485,7 @@ k_ebe3tc(int nx, int ny, int nz, int nz_tile, const uint4* __restrict__ Bimg,
 
 template <int MODE, int TY>
 void launch_tile(cudaStream_t s, const Ebe& op, const float* x, float* y, const float* b,
-                 const float* Dinv, double omega, const int* done) {
+                 const float* Dinv, double omega, const int* done, const ChebArg* ch) {
   using C = Cfg<TY>;
   // dynamic shared memory per block, raised if needed so that the blocks sharing an SM never
   // ask for more than its 512 tensor-memory columns (a further block would wait in
@@ -494,16 +504,20 @@ void launch_tile(cudaStream_t s, const Ebe& op, const float* x, float* y, const 
   }
   const int nzt = op.tc_nz > 0 ? op.tc_nz : 8;
   dim3 grid(ceil_div(op.nx + 1, ONX), ceil_div(op.ny + 1, C::ONY), ceil_div(op.nz + 1, nzt));
+  if (MODE == MODE_CHEB && !ch) TOMG_THROW(TOMG_E_INVALID, "Chebyshev step without its state");
+  float* dch = MODE == MODE_CHEB ? (float*)ch->d : nullptr;
+  const float c1 = MODE == MODE_CHEB ? (float)ch->c1 : 0.f;
+  const int dm = MODE == MODE_CHEB ? ch->dmode : 0;
   LAUNCH((k_ebe3tc<MODE, TY>), grid, C::NT, smem, s, op.nx, op.ny, op.nz, nzt,
          reinterpret_cast<const uint4*>(op.Ktc), (const float*)op.E, op.mask, x, y, b, Dinv,
-         (float)omega, done);
+         (float)omega, done, dch, c1, dm);
 }
 
 template <int MODE>
 void launch_mode(cudaStream_t s, const Ebe& op, const float* x, float* y, const float* b,
-                 const float* Dinv, double omega, const int* done) {
-  if (op.tc_ty == 4) launch_tile<MODE, 4>(s, op, x, y, b, Dinv, omega, done);
-  else launch_tile<MODE, 8>(s, op, x, y, b, Dinv, omega, done);
+                 const float* Dinv, double omega, const int* done, const ChebArg* ch = nullptr) {
+  if (op.tc_ty == 4) launch_tile<MODE, 4>(s, op, x, y, b, Dinv, omega, done, ch);
+  else launch_tile<MODE, 8>(s, op, x, y, b, Dinv, omega, done, ch);
 }
 
 }  // namespace
@@ -532,9 +546,11 @@ void ebe3d_tc_operand(const double* Ke, uint32_t* img) {
 int ebe3d_tc_operand_words() { return 2 * B_BYTES / 4; }
 
 void ebe3d_tc_launch(cudaStream_t s, int mode, const Ebe& op, const float* x, float* y,
-                     const float* b, const float* Dinv, double omega, const int* done) {
+                     const float* b, const float* Dinv, double omega, const int* done,
+                     const ChebArg* ch) {
   if (mode == MODE_APPLY) launch_mode<MODE_APPLY>(s, op, x, y, b, Dinv, omega, done);
   else if (mode == MODE_RESID) launch_mode<MODE_RESID>(s, op, x, y, b, Dinv, omega, done);
+  else if (mode == MODE_CHEB) launch_mode<MODE_CHEB>(s, op, x, y, b, Dinv, omega, done, ch);
   else launch_mode<MODE_JACOBI>(s, op, x, y, b, Dinv, omega, done);
 }
 

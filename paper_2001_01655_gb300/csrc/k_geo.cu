@@ -31,7 +31,8 @@ __global__ void __launch_bounds__(256) k_stencil(int nx, int ny, int nz, const T
                                                  const T* __restrict__ x, T* __restrict__ y,
                                                  const T* __restrict__ b,
                                                  const T* __restrict__ Dinv, T omega,
-                                                 const int* done, T* __restrict__ xo) {
+                                                 const int* done, T* __restrict__ xo, T c1,
+                                                 int dmode) {
   constexpr int NO = (DIM == 3) ? 27 : 9, BB = DIM * DIM;
   pdl_prologue();
   if (solve_done(done)) return;
@@ -74,6 +75,14 @@ __global__ void __launch_bounds__(256) k_stencil(int nx, int ny, int nz, const T
   } else if (MODE == MODE_RESID) {
 #pragma unroll
     for (int c = 0; c < DIM; c++) y[DIM * node + c] = b[DIM * node + c] - acc[c];
+  } else if (MODE == MODE_CHEB) {
+    T r[DIM], xi[DIM];
+#pragma unroll
+    for (int c = 0; c < DIM; c++) {
+      r[c] = b[DIM * node + c] - acc[c];
+      xi[c] = x[DIM * node + c];
+    }
+    cheb_node<T, DIM>(node, r, xi, Dinv, c1, omega, dmode, xo, y);
   } else {
     T r[DIM];
 #pragma unroll
@@ -420,28 +429,34 @@ __global__ void k_geoP(int fnx, int fny, int fnz, int cnx, int cny, const int* r
 
 template <class T>
 void stencil_op(cudaStream_t s, int mode, const Geo& g, const T* S, const T* x, T* y, const T* b,
-                const T* Dinv, double omega, const int* done) {
+                const T* Dinv, double omega, const int* done, const ChebArg* ch) {
   const int64_t nn = g.nodes();
   const int grid = ceil_div(nn, 256);
-  T* xo = mode == MODE_RESID0 ? const_cast<T*>(x) : nullptr;
-#define STN(D, M) LAUNCH((k_stencil<T, D, M>), grid, 256, 0, s, g.nx, g.ny, g.nz, S, x, y, b, Dinv, (T)omega, done, xo)
+  if (mode == MODE_CHEB && !ch) TOMG_THROW(TOMG_E_INVALID, "Chebyshev step without its state");
+  T* xo = mode == MODE_RESID0 ? const_cast<T*>(x) : (mode == MODE_CHEB ? (T*)ch->d : nullptr);
+  const T c1 = mode == MODE_CHEB ? (T)ch->c1 : T(0);
+  const int dm = mode == MODE_CHEB ? ch->dmode : 0;
+#define STN(D, M) LAUNCH((k_stencil<T, D, M>), grid, 256, 0, s, g.nx, g.ny, g.nz, S, x, y, b, Dinv, (T)omega, done, xo, c1, dm)
   if (g.dim == 2) {
     if (mode == MODE_APPLY) STN(2, MODE_APPLY);
     else if (mode == MODE_RESID) STN(2, MODE_RESID);
     else if (mode == MODE_RESID0) STN(2, MODE_RESID0);
+    else if (mode == MODE_CHEB) STN(2, MODE_CHEB);
     else STN(2, MODE_JACOBI);
   } else {
     if (mode == MODE_APPLY) STN(3, MODE_APPLY);
     else if (mode == MODE_RESID) STN(3, MODE_RESID);
     else if (mode == MODE_RESID0) STN(3, MODE_RESID0);
+    else if (mode == MODE_CHEB) STN(3, MODE_CHEB);
     else STN(3, MODE_JACOBI);
   }
 #undef STN
 }
 template void stencil_op<float>(cudaStream_t, int, const Geo&, const float*, const float*, float*,
-                                const float*, const float*, double, const int*);
+                                const float*, const float*, double, const int*, const ChebArg*);
 template void stencil_op<double>(cudaStream_t, int, const Geo&, const double*, const double*,
-                                 double*, const double*, const double*, double, const int*);
+                                 double*, const double*, const double*, double, const int*,
+                                 const ChebArg*);
 
 int stencil_blocks(const Geo& g) { return ceil_div(g.nodes(), 256); }
 

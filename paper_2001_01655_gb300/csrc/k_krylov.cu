@@ -179,34 +179,6 @@ __global__ void k_jacobi0(int64_t nodes, const T* __restrict__ Dinv, const T* __
   }
 }
 
-// One step of point-block-Jacobi-preconditioned Chebyshev acceleration at every node:
-// d = c1 d_prev + c2 Dinv r, x += d, with d_prev = 0 (dmode 0), the stored d (1) or x itself
-// (2: the step after x_1 = d_0 from a zero guess)
-template <class T, int B>
-__global__ void k_cheb(int64_t nodes, const T* __restrict__ Dinv, const T* __restrict__ r,
-                       T* __restrict__ x, T* __restrict__ d, T c1, T c2, int dmode,
-                       const int* done) {
-  pdl_prologue();
-  if (solve_done(done)) return;
-  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (i >= nodes) return;
-  const T* D = Dinv + (int64_t)B * B * i;
-  T rv[B];
-#pragma unroll
-  for (int c = 0; c < B; c++) rv[c] = r[B * i + c];
-#pragma unroll
-  for (int q = 0; q < B; q++) {
-    T v = T(0);
-#pragma unroll
-    for (int c = 0; c < B; c++) v += D[q * B + c] * rv[c];
-    const T xq = x[B * i + q];
-    const T prev = dmode == 2 ? xq : (dmode == 1 ? d[B * i + q] : T(0));
-    const T dn = c1 * prev + c2 * v;
-    x[B * i + q] = xq + dn;
-    d[B * i + q] = dn;
-  }
-}
-
 template <class T>
 __global__ void k_gemv(int n, const T* __restrict__ A, const T* __restrict__ b, T* __restrict__ x,
                        const int* done) {
@@ -451,20 +423,6 @@ void jacobi0(cudaStream_t s, int bs, int64_t nodes, const T* Dinv, const T* b, T
   else if (bs == 6) LAUNCH((k_jacobi0<T, 6>), g, 256, 0, s, nodes, Dinv, b, x, (T)omega, done);
   else TOMG_THROW(TOMG_E_INVALID, "unsupported block size %d", bs);
 }
-template <class T>
-void cheb_step(cudaStream_t s, int bs, int64_t nodes, const T* Dinv, const T* r, T* x, T* d,
-               double c1, double c2, int dmode, const int* done) {
-  const int g = ceil_div(nodes, 256);
-  if (bs == 2) LAUNCH((k_cheb<T, 2>), g, 256, 0, s, nodes, Dinv, r, x, d, (T)c1, (T)c2, dmode, done);
-  else if (bs == 3) LAUNCH((k_cheb<T, 3>), g, 256, 0, s, nodes, Dinv, r, x, d, (T)c1, (T)c2, dmode, done);
-  else if (bs == 6) LAUNCH((k_cheb<T, 6>), g, 256, 0, s, nodes, Dinv, r, x, d, (T)c1, (T)c2, dmode, done);
-  else TOMG_THROW(TOMG_E_INVALID, "unsupported block size %d", bs);
-}
-template void cheb_step<float>(cudaStream_t, int, int64_t, const float*, const float*, float*,
-                               float*, double, double, int, const int*);
-template void cheb_step<double>(cudaStream_t, int, int64_t, const double*, const double*, double*,
-                                double*, double, double, int, const int*);
-
 template void jacobi0<float>(cudaStream_t, int, int64_t, const float*, const float*, float*,
                              double, const int*);
 template void jacobi0<double>(cudaStream_t, int, int64_t, const double*, const double*, double*,

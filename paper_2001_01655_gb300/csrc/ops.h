@@ -11,7 +11,16 @@ namespace tomg {
 
 // MODE_RESID0 fuses the first smoothing sweep from a zero guess with the residual that follows
 // it: x = w Dinv b is WRITTEN to the x argument, and y = b - A x.
-enum OpMode { MODE_APPLY = 0, MODE_RESID = 1, MODE_JACOBI = 2, MODE_RESID0 = 3 };
+// MODE_CHEB is one step of the Chebyshev smoother with its residual: r = b - A x,
+// d = c1 d_prev + c2 Dinv r (c2 passed as the omega argument), y = x + d (y must not alias
+// x), d written to ChebArg::d; d_prev = 0 (dmode 0), the stored d (1) or x itself (2).
+enum OpMode { MODE_APPLY = 0, MODE_RESID = 1, MODE_JACOBI = 2, MODE_RESID0 = 3, MODE_CHEB = 4 };
+struct ChebArg {
+  void* d = nullptr;  // T[n]
+  double c1 = 0.0;
+  double c2 = 0.0;    // the launchers take it through their omega argument
+  int dmode = 0;
+};
 struct Scalars;
 
 // ---------------- level 0: matrix-free SIMP element-by-element operator ----------------
@@ -34,22 +43,25 @@ struct Ebe {
 };
 template <class T>
 void ebe_op(cudaStream_t s, int mode, const Ebe& op, const T* x, T* y, const T* b,
-            const T* Dinv, double omega, const int* done, double* dot_partials);
+            const T* Dinv, double omega, const int* done, double* dot_partials,
+            const ChebArg* ch = nullptr);
 int ebe_blocks(const Ebe& op);  // number of blocks (= number of dot partials) of ebe_op
 // quad4 tiled implementation behind ebe_op (k_ebe2d.cu)
 template <class T, int MODE, bool DOT>
 void ebe2d_launch(cudaStream_t s, const Ebe& op, const T* x, T* y, const T* b, const T* Dinv,
-                  double omega, const int* done, double* parts);
+                  double omega, const int* done, double* parts, const ChebArg* ch = nullptr);
 int ebe2d_blocks(const Ebe& op);
 // fastest quad4 FP32 tile (nodes per thread) for this grid, timed on the stream with scratch
 // vectors the first time a grid shape is seen, cached per shape afterwards
 int ebe2d_autotune(cudaStream_t s, const Ebe& op, const float* Dinv);
 // hex8 FP32 tiled implementation behind ebe_op (k_ebe3d.cu; no fused dot)
 void ebe3d_launch(cudaStream_t s, int mode, const Ebe& op, const float* x, float* y,
-                  const float* b, const float* Dinv, double omega, const int* done);
+                  const float* b, const float* Dinv, double omega, const int* done,
+                  const ChebArg* ch = nullptr);
 // hex8 FP32 on the tensor cores (k_ebe3tc.cu): tcgen05 kind::tf32 split products, same modes
 void ebe3d_tc_launch(cudaStream_t s, int mode, const Ebe& op, const float* x, float* y,
-                     const float* b, const float* Dinv, double omega, const int* done);
+                     const float* b, const float* Dinv, double omega, const int* done,
+                     const ChebArg* ch = nullptr);
 // Ke (24 x 24, FP64) -> TF32 hi and lo B-operand images in the kernel's shared-memory layout
 void ebe3d_tc_operand(const double* Ke, uint32_t* img);
 int ebe3d_tc_operand_words();
@@ -75,7 +87,7 @@ struct Geo {
 inline int stencil_q(int dim) { return dim == 3 ? 27 * 9 : 9 * 4; }
 template <class T>
 void stencil_op(cudaStream_t s, int mode, const Geo& g, const T* S, const T* x, T* y, const T* b,
-                const T* Dinv, double omega, const int* done);
+                const T* Dinv, double omega, const int* done, const ChebArg* ch = nullptr);
 void stencil_block_diag_inv(cudaStream_t s, const Geo& g, const double* S, double* Dinv64,
                             float* Dinv32);
 // FP64 y = S x with per-block partials of x . y (stencil_blocks(g) partials); with sc set, the
@@ -110,7 +122,7 @@ struct Bsr {
 };
 template <class T>
 void bsr_op(cudaStream_t s, int mode, const Bsr& A, const T* V, const T* x, T* y, const T* b,
-            const T* Dinv, double omega, const int* done);
+            const T* Dinv, double omega, const int* done, const ChebArg* ch = nullptr);
 // y (+)= A x for rectangular blocks (transfers): accumulate = 1 adds into y
 template <class T>
 void bsr_spmv_rect(cudaStream_t s, const Bsr& A, const T* V, const T* x, T* y, int accumulate,
@@ -201,11 +213,6 @@ void mask_vec(cudaStream_t s, const double* f, double* b, const uint8_t* mask, i
 template <class T>
 void jacobi0(cudaStream_t s, int bs, int64_t nodes, const T* Dinv, const T* b, T* x, double omega,
              const int* done);
-// Chebyshev smoother step at every node: d = c1 d_prev + c2 Dinv r, x += d; d_prev = 0
-// (dmode 0), d (1) or x (2)
-template <class T>
-void cheb_step(cudaStream_t s, int bs, int64_t nodes, const T* Dinv, const T* r, T* x, T* d,
-               double c1, double c2, int dmode, const int* done);
 // coarse solve x = Ainv b (dense GEMV)
 template <class T>
 void dense_gemv(cudaStream_t s, int n, const T* Ainv, const T* b, T* x, const int* done);

@@ -137,22 +137,23 @@ struct TcScope {
 
 template <class T>
 void level_op(tomg_problem* P, cudaStream_t s, int l, int mode, const T* x, T* y, const T* b,
-              const int* done) {
+              const int* done, const ChebArg* ch = nullptr) {
   Level& Lv = *P->L[l];
-  const double w = P->opt.omega;
+  const double w = (mode == MODE_CHEB && ch) ? ch->c2 : P->opt.omega;
   switch (Lv.kind) {
     case KIND_EBE:
       // FP64: the assembled fine stencil kept by the setup halves the FP64 arithmetic
       if (sizeof(T) == 8 && Lv.S64.p)
-        stencil_op<T>(s, mode, Lv.g, reinterpret_cast<const T*>(Lv.S64.p), x, y, b, V<T>::D(Lv), w, done);
+        stencil_op<T>(s, mode, Lv.g, reinterpret_cast<const T*>(Lv.S64.p), x, y, b, V<T>::D(Lv), w,
+                      done, ch);
       else
-        ebe_op<T>(s, mode, V<T>::ebe(P), x, y, b, V<T>::D(Lv), w, done, nullptr);
+        ebe_op<T>(s, mode, V<T>::ebe(P), x, y, b, V<T>::D(Lv), w, done, nullptr, ch);
       break;
     case KIND_STENCIL:
-      stencil_op<T>(s, mode, Lv.g, V<T>::S(Lv), x, y, b, V<T>::D(Lv), w, done);
+      stencil_op<T>(s, mode, Lv.g, V<T>::S(Lv), x, y, b, V<T>::D(Lv), w, done, ch);
       break;
     default:
-      bsr_op<T>(s, mode, Lv.bsr(), V<T>::Vv(Lv), x, y, b, V<T>::D(Lv), w, done);
+      bsr_op<T>(s, mode, Lv.bsr(), V<T>::Vv(Lv), x, y, b, V<T>::D(Lv), w, done, ch);
   }
 }
 
@@ -192,24 +193,31 @@ void vcycle(tomg_problem* P, Work& W, int l, const T* b, T* out, const int* done
   T* r = V<T>::r(lw);
   if (P->opt.smoother == 1) {
     // Chebyshev smoothing (m steps of Chebyshev acceleration, the same polynomial before and
-    // after the coarse correction): the iterate lives in `out`, its last step in x
+    // after the coarse correction), each step one fused residual + update launch writing the
+    // new iterate to the other of two buffers.  Starting in x, the iterate ends in `out` for
+    // every m; r holds the step vector d, except while it carries the restricted residual.
     const int m = P->opt.cheb_degree;
-    const T* D = V<T>::D(Lv);
-    jacobi0<T>(s, Lv.b, Lv.nn, D, b, out, Lv.cheb_c2[0], done);  // x_1 = d_0 from x_0 = 0
+    T* cur = x;
+    T* nxt = out;
+    jacobi0<T>(s, Lv.b, Lv.nn, V<T>::D(Lv), b, cur, Lv.cheb_c2[0], done);  // x_1 = d_0
     for (int k = 1; k < m; k++) {
-      level_op<T>(P, s, l, MODE_RESID, out, r, b, done);
-      cheb_step<T>(s, Lv.b, Lv.nn, D, r, out, x, Lv.cheb_c1[k], Lv.cheb_c2[k], k == 1 ? 2 : 1, done);
+      ChebArg ch;
+      ch.d = r; ch.c1 = Lv.cheb_c1[k]; ch.c2 = Lv.cheb_c2[k]; ch.dmode = k == 1 ? 2 : 1;
+      level_op<T>(P, s, l, MODE_CHEB, cur, nxt, b, done, &ch);
+      std::swap(cur, nxt);
     }
-    level_op<T>(P, s, l, MODE_RESID, out, r, b, done);
+    level_op<T>(P, s, l, MODE_RESID, cur, r, b, done);
     LevelWork& cw = W.lw[l + 1];
     restrict_to<T>(P, s, l, r, V<T>::b(cw), done);
     vcycle<T>(P, W, l + 1, V<T>::b(cw), V<T>::y(cw), done);
-    prolong_add<T>(P, s, l, V<T>::y(cw), out, done);
+    prolong_add<T>(P, s, l, V<T>::y(cw), cur, done);
     for (int k = 0; k < m; k++) {
-      level_op<T>(P, s, l, MODE_RESID, out, r, b, done);
-      cheb_step<T>(s, Lv.b, Lv.nn, D, r, out, x, Lv.cheb_c1[k], Lv.cheb_c2[k], k == 0 ? 0 : 1, done);
+      ChebArg ch;
+      ch.d = r; ch.c1 = Lv.cheb_c1[k]; ch.c2 = Lv.cheb_c2[k]; ch.dmode = k == 0 ? 0 : 1;
+      level_op<T>(P, s, l, MODE_CHEB, cur, nxt, b, done, &ch);
+      std::swap(cur, nxt);
     }
-    return;
+    return;  // cur == out
   }
   // pre-smoothing; the first sweep from x = 0 needs no operator apply, and with a single
   // pre-sweep in FP32 it is fused into the residual pass (x = w Dinv b, r = b - A x in one
