@@ -84,6 +84,13 @@ typedef struct {
   double cheb_lower;   /* Chebyshev interval, fractions of the 20-step power-iteration
                           estimate of lambda_max(D^-1 A): lower                     0.1      */
   double cheb_upper;   /*                                   upper                     1.1      */
+  int adaptive_geo;    /* hybrid only: adaptive geometric level count across the design
+                          updates of a problem (Sec. 4.4): the first setup uses n_geo_levels
+                          (6 in the paper); every solve that needs more than adaptive_iters
+                          outer iterations makes the next setup use one geometric level
+                          fewer, down to adaptive_min_geo                          0 (off)  */
+  int adaptive_iters;  /*                                                          200      */
+  int adaptive_min_geo;/*                                                          2        */
 } tomg_options;
 
 typedef struct {
@@ -233,6 +240,9 @@ tomg_status tomg_time_fine_operator(tomg_problem* prob, int op, int prec, int re
  *             contexts on the same device) race and must be serialised by the caller.
  *             Every array entry a call reads is written earlier in the same call. */
 tomg_status tomg_fine_apply_f32_noalloc(tomg_problem* prob, const double* x, double* y);
+/* Adaptive hybrid hierarchy (Sec. 4.4): the geometric level count (including the fine grid)
+ * the next tomg_setup of this problem will use, 0 before the first setup with adaptive_geo. */
+tomg_status tomg_adaptive_geo_levels(const tomg_problem* prob, int* n_geo_levels);
 /* Number of kernels this library launched since the context was created. */
 tomg_status tomg_kernel_launches(const tomg_ctx* ctx, int64_t* count);
 

@@ -125,6 +125,9 @@ void tomg_options_default(tomg_options* o) {
   o->cheb_degree = 2;
   o->cheb_lower = 0.1;
   o->cheb_upper = 1.1;
+  o->adaptive_geo = 0;
+  o->adaptive_iters = 200;
+  o->adaptive_min_geo = 2;
   o->omega = 0.5;
   o->n_pre = 1;
   o->n_post = 1;
@@ -266,6 +269,12 @@ tomg_status tomg_solve(tomg_problem* P, int nrhs, const double* f, double* u, in
     StreamScope sc(P);
     return solve(P, nrhs, f, u, on_device, results);
   });
+}
+
+tomg_status tomg_adaptive_geo_levels(const tomg_problem* P, int* n) {
+  if (!P || !n) { set_error("null argument"); return TOMG_E_INVALID; }
+  *n = P->adapt_geo;
+  return TOMG_OK;
 }
 
 tomg_status tomg_num_levels(const tomg_problem* P, int* n) {

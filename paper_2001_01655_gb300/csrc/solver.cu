@@ -644,7 +644,8 @@ void setup(tomg_problem* P, const tomg_options& opt) {
       opt.max_coarse_dofs < 1 || opt.max_levels < 1 || opt.max_levels > 64 || opt.smoother < 0 ||
       opt.smoother > 1 || opt.concurrency < 0 || opt.concurrency > 64 ||
       (opt.smoother == 1 && (opt.cheb_degree < 1 || opt.cheb_degree > 8 ||
-                             !(opt.cheb_lower > 0.0) || !(opt.cheb_upper > opt.cheb_lower))))
+                             !(opt.cheb_lower > 0.0) || !(opt.cheb_upper > opt.cheb_lower))) ||
+      (opt.adaptive_geo != 0 && (opt.adaptive_iters < 1 || opt.adaptive_min_geo < 1)))
     TOMG_THROW(TOMG_E_INVALID, "invalid options");
   P->setup_valid = false;
   P->setup_gen++;
@@ -681,7 +682,11 @@ void setup(tomg_problem* P, const tomg_options& opt) {
     if (opt.pc == TOMG_PC_GMG)
       n_geo = opt.n_levels > 0 ? opt.n_levels
                                : levels_for_cap(P->dim, P->nx, P->ny, P->nz, opt.max_coarse_dofs, opt.max_levels);
-    else if (opt.pc == TOMG_PC_HYBRID)
+    else if (opt.pc == TOMG_PC_HYBRID && opt.adaptive_geo) {
+      // adaptive hybrid (Sec. 4.4): the count carried over from the previous solves
+      if (P->adapt_geo == 0) P->adapt_geo = std::max(opt.adaptive_min_geo, opt.n_geo_levels);
+      n_geo = P->adapt_geo;
+    } else if (opt.pc == TOMG_PC_HYBRID)
       n_geo = std::max(1, opt.n_geo_levels);
     n_geo = std::min(n_geo, opt.max_levels);
     // assembled level-0 stencil (FP64) for the Galerkin products / AMG / dense coarse solve
@@ -963,6 +968,13 @@ tomg_status solve(tomg_problem* P, int nrhs, const double* f, double* u, int on_
   CK(cudaStreamSynchronize(st(P)));
   if (P->dim == 3 && P->opt.prec == TOMG_PREC_3XTF32_VCYCLE && ebe3d_tc_error(st(P)))
     for (int j = 0; j < nrhs; j++) res[j].status = TOMG_E_TIMEOUT;
+  if (P->opt.pc == TOMG_PC_HYBRID && P->opt.adaptive_geo && P->adapt_geo > 0) {
+    // adaptive hybrid (Sec. 4.4): a solve over the iteration limit moves the next setup one
+    // geometric level towards aggregation
+    int worst_it = 0;
+    for (int j = 0; j < nrhs; j++) worst_it = std::max(worst_it, res[j].iterations);
+    if (worst_it > P->opt.adaptive_iters && P->adapt_geo > P->opt.adaptive_min_geo) P->adapt_geo--;
+  }
   tomg_status worst = TOMG_OK;
   for (int j = 0; j < nrhs; j++) {
     const int s = res[j].status;

@@ -124,6 +124,7 @@ struct tomg_problem {
   int tc_mode = -1;    // hex8 FP32 element kernel: -1 as opt.prec says, 0 CUDA cores, 1 tensor cores
   int tc_nz = 0;       // node layers per block of the tensor-core kernel (0 = default)
   int tc_ty = 0;       // element rows per block of the tensor-core kernel (0 = default)
+  int adapt_geo = 0;   // adaptive hybrid: geometric levels of the next setup (0 = not started)
   tomg::DBuf<uint32_t> Ketc;  // split Ke operand images of the tensor-core kernel (hex8)
   tomg::DBuf<double> Ke64;
   tomg::DBuf<float> Ke32;

@@ -32,7 +32,8 @@ class Options(C.Structure):
                 ("smoother", C.c_int), ("omega", C.c_double), ("n_pre", C.c_int),
                 ("n_post", C.c_int), ("soc_beta", C.c_double), ("check_every", C.c_int),
                 ("use_graph", C.c_int), ("max_levels", C.c_int), ("concurrency", C.c_int),
-                ("cheb_degree", C.c_int), ("cheb_lower", C.c_double), ("cheb_upper", C.c_double)]
+                ("cheb_degree", C.c_int), ("cheb_lower", C.c_double), ("cheb_upper", C.c_double),
+                ("adaptive_geo", C.c_int), ("adaptive_iters", C.c_int), ("adaptive_min_geo", C.c_int)]
 
 
 class Result(C.Structure):
@@ -81,6 +82,7 @@ _SIGS = {
     "tomg_element_stiffness": (C.c_int, [_P, _P]),
     "tomg_time_fine_operator": (C.c_int, [_P, C.c_int, C.c_int, C.c_int, C.c_int, _D]),
     "tomg_fine_apply_f32_noalloc": (C.c_int, [_P, _P, _P]),
+    "tomg_adaptive_geo_levels": (C.c_int, [_P, C.POINTER(C.c_int)]),
     "tomg_server_create": (C.c_int, [_P, C.c_size_t, C.c_int, C.POINTER(_P)]),
     "tomg_server_submit": (C.c_int, [_P, _P, _P, C.c_int, _P, _P, C.POINTER(Options),
                                      C.POINTER(C.c_uint64)]),
@@ -244,6 +246,12 @@ class Problem:
     def num_levels(self):
         v = C.c_int()
         _check(load().tomg_num_levels(self.h, C.byref(v)))
+        return v.value
+
+    def adaptive_geo_levels(self):
+        """Geometric levels the next setup of an adaptive hybrid hierarchy will use (0: none yet)."""
+        v = C.c_int()
+        _check(load().tomg_adaptive_geo_levels(self.h, C.byref(v)))
         return v.value
 
     def level_info(self, level):

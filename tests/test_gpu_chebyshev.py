@@ -100,3 +100,38 @@ def test_chebyshev_invalid_options(lib, ctx):
                 dict(cheb_lower=1.2, cheb_upper=1.1)):
         with pytest.raises(lib.TomgError):
             P.setup(pc="gmg", n_levels=2, **CHEB, **bad)
+
+
+def _geo_levels(P):
+    """Geometric levels of the current hierarchy (levels whose transfer is geometric, + 1)."""
+    n = P.num_levels()
+    return 1 + sum(1 for l in range(n - 1) if P.level_info(l)["geometric"])
+
+
+def test_adaptive_hybrid_drops_geometric_levels(lib, ctx):
+    """Sec. 4.4: start with 6 geometric levels; every solve above the iteration limit makes the
+    next setup use one fewer, down to the minimum of 2.  A limit of 3 iterations is exceeded by
+    every solve here, so the sequence is 6, 5, 4, 3, 2, 2; every solve stays exact."""
+    p = W.cantilever_3d(32, 16, 16, seed=0, sigma=2.0)
+    P = lib.Problem.from_workload(ctx, p)
+    ref = osolve.direct(p)
+    seen = []
+    for _ in range(6):
+        P.setup(pc="hybrid", prec="fp32", n_geo_levels=6, max_coarse_dofs=1000,
+                adaptive_geo=1, adaptive_iters=3, adaptive_min_geo=2)
+        seen.append(_geo_levels(P))
+        u, res = P.solve(p.f)
+        assert res[0]["status"] == 0 and res[0]["iterations"] > 3
+        assert relerr(u, ref["u"]) <= 1e-6
+    assert seen == [6, 5, 4, 3, 2, 2], seen
+    assert P.adaptive_geo_levels() == 2
+
+
+def test_adaptive_hybrid_keeps_levels_below_limit(lib, ctx):
+    p = W.cantilever_3d(16, 8, 8, seed=0, sigma=2.0)
+    P = lib.Problem.from_workload(ctx, p)
+    for _ in range(3):
+        P.setup(pc="hybrid", prec="fp32", n_geo_levels=3, max_coarse_dofs=200, adaptive_geo=1)
+        _, res = P.solve(p.f)
+        assert res[0]["iterations"] <= 200
+    assert P.adaptive_geo_levels() == 3
