@@ -13,8 +13,9 @@ Modules
   gmg      geometric bilinear/trilinear prolongation, Galerkin coarse operators, level counts
   amg      smoothed aggregation: block strength of connection, distance-2 MIS aggregation,
            tentative prolongator by Gram-Schmidt QR, Jacobi-smoothed prolongator
-  mg       V-cycle (Algorithm 1) with point-block Jacobi smoothing and a dense Cholesky
-           coarse solve; hierarchy builders for GMG / AMG / hybrid
+  mg       V-cycle (Algorithm 1) with point-block Jacobi or Chebyshev smoothing and a dense
+           Cholesky coarse solve; hierarchy builders for GMG / AMG / hybrid
+  design   linear density filter rho = S alpha and the compliance sensitivities (Eq. 3)
   krylov   textbook preconditioned CG and flexible CG
   solve    one call that mirrors the library's solve options
   hashing  splitmix64, the counter-based generator both sides implement from its published
