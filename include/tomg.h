@@ -240,6 +240,20 @@ tomg_status tomg_time_fine_operator(tomg_problem* prob, int op, int prec, int re
  *             contexts on the same device) race and must be serialised by the caller.
  *             Every array entry a call reads is written earlier in the same call. */
 tomg_status tomg_fine_apply_f32_noalloc(tomg_problem* prob, const double* x, double* y);
+/* ---- the steps either side of the solve in a design iteration (Sec. 2.1) ------------------
+ * Linear density filter (Eq. 1, rho = S alpha; radius 1.5 element sizes in Sec. 4):
+ *   rho_e = sum_j w_ej alpha_j / sum_j w_ej,  w_ej = max(0, radius - |c_e - c_j|)
+ * over the element centroids c of the problem's grid; transpose != 0 applies S^T instead (the
+ * chain rule dF/dalpha = S^T dF/drho of Eq. 3).  in, out: n_elems doubles, host or device
+ * (on_device), caller-owned, may not alias.  E_INVALID for radius outside (0, 3]. */
+tomg_status tomg_density_filter(tomg_problem* prob, double radius, int transpose,
+                                const double* in, double* out, int on_device);
+/* Compliance sensitivities (Eq. 3): dF/drho_e = -p rho_e^(p-1) (E0 - Emin) u_e^T Ke u_e for the
+ * problem's current density (tomg_set_density) and displacements u (n_dofs doubles, e.g. the
+ * output of tomg_solve); out: n_elems doubles.  Host or device arrays (on_device). */
+tomg_status tomg_compliance_sensitivity(tomg_problem* prob, const double* u, double* out,
+                                        int on_device);
+
 /* Adaptive hybrid hierarchy (Sec. 4.4): the geometric level count (including the fine grid)
  * the next tomg_setup of this problem will use, 0 before the first setup with adaptive_geo. */
 tomg_status tomg_adaptive_geo_levels(const tomg_problem* prob, int* n_geo_levels);

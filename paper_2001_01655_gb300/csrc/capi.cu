@@ -407,6 +407,58 @@ tomg_status tomg_moduli(tomg_problem* P, double* E, int on_device) {
   });
 }
 
+tomg_status tomg_density_filter(tomg_problem* P, double radius, int transpose, const double* in,
+                                double* out, int on_device) {
+  return guarded([&]() -> tomg_status {
+    if (!P || !in || !out || in == out) TOMG_THROW(TOMG_E_INVALID, "null or aliased argument");
+    set_device(P);
+    StreamScope sc(P);
+    cudaStream_t s = P->stream;
+    const size_t bytes = (size_t)P->nel * 8;
+    tomg::DBuf<double> W, din, dout;
+    W.resize(P->nel);
+    const double* a = in;
+    double* o = out;
+    if (!on_device) {
+      din.resize(P->nel);
+      dout.resize(P->nel);
+      CK(cudaMemcpyAsync(din.p, in, bytes, cudaMemcpyHostToDevice, s));
+      a = din.p;
+      o = dout.p;
+    }
+    tomg::density_filter(s, P->dim, P->nx, P->ny, P->nz, radius, transpose, a, o, W.p);
+    if (!on_device) CK(cudaMemcpyAsync(out, o, bytes, cudaMemcpyDeviceToHost, s));
+    CK(cudaStreamSynchronize(s));
+    return TOMG_OK;
+  });
+}
+
+tomg_status tomg_compliance_sensitivity(tomg_problem* P, const double* u, double* out,
+                                        int on_device) {
+  return guarded([&]() -> tomg_status {
+    if (!P || !u || !out) TOMG_THROW(TOMG_E_INVALID, "null argument");
+    if (!P->have_density) TOMG_THROW(TOMG_E_INVALID, "no density set");
+    set_device(P);
+    StreamScope sc(P);
+    cudaStream_t s = P->stream;
+    tomg::DBuf<double> du, dout;
+    const double* uu = u;
+    double* o = out;
+    if (!on_device) {
+      du.resize(P->n);
+      dout.resize(P->nel);
+      CK(cudaMemcpyAsync(du.p, u, (size_t)P->n * 8, cudaMemcpyHostToDevice, s));
+      uu = du.p;
+      o = dout.p;
+    }
+    tomg::compliance_sensitivity(s, P->dim, P->nx, P->ny, P->nz, P->Ke64.p, P->rho.p, uu, P->E0,
+                                 P->Emin, P->penal, o);
+    if (!on_device) CK(cudaMemcpyAsync(out, o, (size_t)P->nel * 8, cudaMemcpyDeviceToHost, s));
+    CK(cudaStreamSynchronize(s));
+    return TOMG_OK;
+  });
+}
+
 tomg_status tomg_element_stiffness(const tomg_problem* P, double* Ke) {
   if (!P || !Ke) { set_error("null argument"); return TOMG_E_INVALID; }
   memcpy(Ke, P->Ke_host.data(), P->Ke_host.size() * sizeof(double));

@@ -79,6 +79,16 @@ void ebe_assemble_stencil(cudaStream_t s, const Ebe& op64, double* S);
 void simp_moduli(cudaStream_t s, int64_t nel, const double* rho, double E0, double Emin,
                  double penal, double* E64, float* E32, int* bad);
 
+// ---------------- design iteration: density filter and sensitivities (k_design.cu) ------
+// rho = S alpha (transpose = 0) or S^T g (transpose = 1), linear filter of radius in (0, 3];
+// W: n_elems scratch (row sums)
+void density_filter(cudaStream_t s, int dim, int nx, int ny, int nz, double radius, int transpose,
+                    const double* in, double* out, double* W);
+// dF/drho_e = -p rho_e^(p-1) (E0 - Emin) u_e^T Ke u_e
+void compliance_sensitivity(cudaStream_t s, int dim, int nx, int ny, int nz, const double* Ke,
+                            const double* rho, const double* u, double E0, double Emin,
+                            double penal, double* dc);
+
 // ---------------- geometric levels: structured stencils and transfers -----------------
 struct Geo {
   int dim, nx, ny, nz;  // element counts of this level (nz = 1 in 2D)

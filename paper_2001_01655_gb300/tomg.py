@@ -83,6 +83,8 @@ _SIGS = {
     "tomg_time_fine_operator": (C.c_int, [_P, C.c_int, C.c_int, C.c_int, C.c_int, _D]),
     "tomg_fine_apply_f32_noalloc": (C.c_int, [_P, _P, _P]),
     "tomg_adaptive_geo_levels": (C.c_int, [_P, C.POINTER(C.c_int)]),
+    "tomg_density_filter": (C.c_int, [_P, C.c_double, C.c_int, _P, _P, C.c_int]),
+    "tomg_compliance_sensitivity": (C.c_int, [_P, _P, _P, C.c_int]),
     "tomg_server_create": (C.c_int, [_P, C.c_size_t, C.c_int, C.POINTER(_P)]),
     "tomg_server_submit": (C.c_int, [_P, _P, _P, C.c_int, _P, _P, C.POINTER(Options),
                                      C.POINTER(C.c_uint64)]),
@@ -323,6 +325,23 @@ class Problem:
         E = np.zeros(self.nel)
         _check(load().tomg_moduli(self.h, C.c_void_p(E.ctypes.data), 0))
         return E
+
+    def density_filter(self, a, radius=1.5, transpose=False):
+        """rho = S a (or S^T a): the linear density filter of the problem's grid."""
+        src = np.ascontiguousarray(a, dtype=np.float64)
+        out = np.zeros(self.nel)
+        _check(load().tomg_density_filter(self.h, float(radius), int(bool(transpose)),
+                                          C.c_void_p(src.ctypes.data),
+                                          C.c_void_p(out.ctypes.data), 0))
+        return out
+
+    def compliance_sensitivity(self, u):
+        """dF/drho for the current density and displacements u (n_dofs)."""
+        src = np.ascontiguousarray(u, dtype=np.float64).reshape(-1)
+        out = np.zeros(self.nel)
+        _check(load().tomg_compliance_sensitivity(self.h, C.c_void_p(src.ctypes.data),
+                                                  C.c_void_p(out.ctypes.data), 0))
+        return out
 
     def fine_apply_f32_noalloc(self, x, y):
         """y = A_0 x in FP32 arithmetic without any device allocation (x, y: contiguous float64
