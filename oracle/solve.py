@@ -33,8 +33,10 @@ def build(problem, pc="gmg", n_levels=None, cap=None, n_geo=None, beta=0.003, om
     raise ValueError(pc)
 
 
-def solve(problem, pc="gmg", rtol=1e-8, max_iter=1000, flexible=False, x0=None, H=None, **kw):
-    """Solve every right-hand side of ``problem``; returns a dict of stacked results."""
+def solve(problem, pc="gmg", rtol=1e-8, max_iter=1000, flexible=False, x0=None, H=None,
+          krylov_method="cg", restart=30, **kw):
+    """Solve every right-hand side of ``problem``; returns a dict of stacked results.
+    krylov_method: "cg" (PCG, or flexible CG with flexible=True) or "fgmres" (FGMRES(restart))."""
     A0 = mg.fine_operator(problem)
     if H is None:
         H = build(problem, pc=pc, A0=A0, **kw)
@@ -45,8 +47,12 @@ def solve(problem, pc="gmg", rtol=1e-8, max_iter=1000, flexible=False, x0=None, 
     for r in range(F.shape[0]):
         b = m * F[r]
         x0r = None if x0 is None else np.atleast_2d(x0)[r]
-        x, it, hist = krylov.pcg(A0, b, M=lambda v: mg.vcycle(H, v), x0=x0r, rtol=rtol,
-                                 max_iter=max_iter, flexible=flexible)
+        if krylov_method == "fgmres":
+            x, it, hist = krylov.fgmres(A0, b, M=lambda v: mg.vcycle(H, v), x0=x0r, rtol=rtol,
+                                        max_iter=max_iter, restart=restart)
+        else:
+            x, it, hist = krylov.pcg(A0, b, M=lambda v: mg.vcycle(H, v), x0=x0r, rtol=rtol,
+                                     max_iter=max_iter, flexible=flexible)
         U[r] = x
         its.append(it)
         nb = np.linalg.norm(b)

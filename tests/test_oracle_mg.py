@@ -185,3 +185,56 @@ def test_chebyshev_vcycle_cuts_iterations(case):
     rc = solve.solve(p, pc="gmg", n_levels=4, smoother="chebyshev", cheb_degree=2)
     assert rc["rel_residual"][0] <= 1e-8 and rj["rel_residual"][0] <= 1e-8
     assert rc["iterations"][0] < rj["iterations"][0]
+
+
+def _small_system(seed=19):
+    p = W.random_problem(2, 5, 3, seed=seed, contrast="minmax")
+    A = mg.fine_operator(p)
+    b = fem.free_mask(p.n, p.fixed) * np.random.default_rng(seed).standard_normal(p.n)
+    return p, A, b
+
+
+@pytest.mark.parametrize("k", [1, 3, 6, 10])
+def test_fgmres_minimal_residual_over_krylov_space(k):
+    """After k Arnoldi steps of one cycle, FGMRES with a fixed preconditioner M minimises
+    ||b - A x|| over x in span{M v_0, ..., M v_{k-1}} = M K_k(A M, b): brute force builds that
+    space from powers of A M applied to b and solves the least-squares problem with lstsq."""
+    p, A, b = _small_system()
+    Ad = A.toarray()
+    Dinv = np.diag(1.0 / np.diag(Ad))
+    Mfun = lambda v: Dinv @ v  # noqa: E731
+    x, it, hist = krylov.fgmres(A, b, M=Mfun, rtol=0.0, max_iter=k, restart=50)
+    assert it == k
+    Kb = [b / np.linalg.norm(b)]
+    for _ in range(k - 1):
+        v = Ad @ (Dinv @ Kb[-1])
+        Kb.append(v / np.linalg.norm(v))
+    Y = Dinv @ np.stack(Kb, axis=1)
+    c, *_ = np.linalg.lstsq(Ad @ Y, b, rcond=None)
+    best = np.linalg.norm(b - Ad @ (Y @ c))
+    assert np.linalg.norm(b - Ad @ x) == pytest.approx(best, rel=1e-7, abs=1e-12 * np.linalg.norm(b))
+    # the Givens estimate of the last step is the true residual of that cycle's iterate
+    assert hist[-1] * np.linalg.norm(b) == pytest.approx(np.linalg.norm(b - Ad @ x), rel=1e-6)
+
+
+def test_fgmres_finite_termination_and_monotone():
+    """Without restarts GMRES ends in at most n steps (exactly so in exact arithmetic; on a
+    well-conditioned operator -- uniform density -- also in FP64)."""
+    p = W.mbb_beam(6, 3)
+    A = mg.fine_operator(p)
+    b = fem.free_mask(p.n, p.fixed) * np.random.default_rng(20).standard_normal(p.n)
+    n = A.shape[0]
+    x, it, hist = krylov.fgmres(A, b, rtol=1e-12, max_iter=2 * n, restart=n + 1)
+    assert it <= n
+    assert np.linalg.norm(b - A @ x) <= 1e-10 * np.linalg.norm(b)
+    steps = hist[1:-1]  # the Givens estimates of the one cycle (the last entry: true residual)
+    assert all(steps[i + 1] <= steps[i] * (1 + 1e-12) for i in range(len(steps) - 1))
+
+
+@pytest.mark.parametrize("restart", [5, 30])
+def test_fgmres_vcycle_matches_direct(restart):
+    p = W.mbb_beam(48, 16)
+    r = solve.solve(p, pc="gmg", n_levels=3, krylov_method="fgmres", restart=restart)
+    ref = solve.direct(p)
+    assert r["rel_residual"][0] <= 1e-8
+    assert np.linalg.norm(r["u"] - ref["u"]) <= 1e-6 * np.linalg.norm(ref["u"])
