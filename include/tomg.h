@@ -91,6 +91,11 @@ typedef struct {
                           fewer, down to adaptive_min_geo                          0 (off)  */
   int adaptive_iters;  /*                                                          200      */
   int adaptive_min_geo;/*                                                          2        */
+  int krylov;          /* outer Krylov method: 0 = CG (PCG with the FP64 V-cycle, flexible CG
+                          with the FP32 one); 1 = flexible GMRES(gmres_restart), the paper's
+                          outer solver (Sec. 4), host-driven, one right-hand side at a time,
+                          iterations = preconditioner applications                    0        */
+  int gmres_restart;   /* FGMRES restart length m, 1..200                             30       */
 } tomg_options;
 
 typedef struct {

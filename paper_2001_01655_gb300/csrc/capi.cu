@@ -128,6 +128,8 @@ void tomg_options_default(tomg_options* o) {
   o->adaptive_geo = 0;
   o->adaptive_iters = 200;
   o->adaptive_min_geo = 2;
+  o->krylov = 0;
+  o->gmres_restart = 30;
   o->omega = 0.5;
   o->n_pre = 1;
   o->n_post = 1;

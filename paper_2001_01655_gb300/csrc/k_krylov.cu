@@ -179,6 +179,41 @@ __global__ void k_jacobi0(int64_t nodes, const T* __restrict__ Dinv, const T* __
   }
 }
 
+// Flexible GMRES building blocks.  parts[k * gridDim.x + block] = partial of V_k . w over the
+// block's grid-stride share (V_k = V + k * ldv); grid.y = number of vectors.
+__global__ void k_mdot(int64_t n, const double* __restrict__ V, int64_t ldv,
+                       const double* __restrict__ w, double* parts) {
+  __shared__ double sred[32];
+  const double* v = V + (int64_t)blockIdx.y * ldv;
+  double a = 0.0;
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n;
+       i += (int64_t)gridDim.x * blockDim.x)
+    a += v[i] * w[i];
+  a = block_sum(a, sred);
+  if (threadIdx.x == 0) parts[(int64_t)blockIdx.y * gridDim.x + blockIdx.x] = a;
+}
+// h[k] = sum over blocks of parts[k * nb + b], fixed order; one block per vector
+__global__ void k_mdot_finish(const double* __restrict__ parts, int nb, double* h) {
+  __shared__ double sred[32];
+  double a = 0.0;
+  for (int q = threadIdx.x; q < nb; q += blockDim.x) a += parts[(int64_t)blockIdx.x * nb + q];
+  a = block_sum(a, sred);
+  if (threadIdx.x == 0) h[blockIdx.x] = a;
+}
+// w += sign * sum_k c[k] V_k (k < J, fixed order)
+__global__ void k_mupdate(int64_t n, int J, const double* __restrict__ V, int64_t ldv,
+                          const double* __restrict__ c, double sign, double* __restrict__ w) {
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  double a = 0.0;
+  for (int k = 0; k < J; k++) a += c[k] * V[(int64_t)k * ldv + i];
+  w[i] += sign * a;
+}
+__global__ void k_scale_into(int64_t n, const double* __restrict__ w, double s, double* v) {
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < n) v[i] = s * w[i];
+}
+
 template <class T>
 __global__ void k_gemv(int n, const T* __restrict__ A, const T* __restrict__ b, T* __restrict__ x,
                        const int* done) {
@@ -368,6 +403,26 @@ inline int grid_for(int64_t n) {
 }  // namespace
 
 int red_blocks(int64_t n) { return grid_for(n); }
+
+constexpr int MDOT_BLOCKS = 120;  // partial sums per dot of the FGMRES kernels
+
+void multi_dot(cudaStream_t s, int64_t n, int J, const double* V, int64_t ldv, const double* w,
+               double* parts, double* h) {
+  if (J < 1) return;
+  LAUNCH(k_mdot, dim3(MDOT_BLOCKS, J), 256, 0, s, n, V, ldv, w, parts);
+  LAUNCH(k_mdot_finish, J, 256, 0, s, parts, MDOT_BLOCKS, h);
+}
+int multi_dot_parts(int J) { return MDOT_BLOCKS * J; }
+
+void multi_update(cudaStream_t s, int64_t n, int J, const double* V, int64_t ldv, const double* c,
+                  double sign, double* w) {
+  if (J < 1) return;
+  LAUNCH(k_mupdate, ceil_div(n, 256), 256, 0, s, n, J, V, ldv, c, sign, w);
+}
+
+void scale_into(cudaStream_t s, int64_t n, const double* w, double sc, double* v) {
+  LAUNCH(k_scale_into, ceil_div(n, 256), 256, 0, s, n, w, sc, v);
+}
 
 void dot_partials(cudaStream_t s, const double* x, const double* y, int64_t n, double* partials,
                   const int* done) {

@@ -223,6 +223,14 @@ void mask_vec(cudaStream_t s, const double* f, double* b, const uint8_t* mask, i
 template <class T>
 void jacobi0(cudaStream_t s, int bs, int64_t nodes, const T* Dinv, const T* b, T* x, double omega,
              const int* done);
+// flexible GMRES: h[k] = V_k . w for k < J (V_k = V + k ldv; parts: multi_dot_parts(J)
+// scratch), w += sign sum_k c[k] V_k, v = s w
+void multi_dot(cudaStream_t s, int64_t n, int J, const double* V, int64_t ldv, const double* w,
+               double* parts, double* h);
+int multi_dot_parts(int J);
+void multi_update(cudaStream_t s, int64_t n, int J, const double* V, int64_t ldv, const double* c,
+                  double sign, double* w);
+void scale_into(cudaStream_t s, int64_t n, const double* w, double sc, double* v);
 // coarse solve x = Ainv b (dense GEMV)
 template <class T>
 void dense_gemv(cudaStream_t s, int n, const T* Ainv, const T* b, T* x, const int* done);

@@ -645,7 +645,9 @@ void setup(tomg_problem* P, const tomg_options& opt) {
       opt.smoother > 1 || opt.concurrency < 0 || opt.concurrency > 64 ||
       (opt.smoother == 1 && (opt.cheb_degree < 1 || opt.cheb_degree > 8 ||
                              !(opt.cheb_lower > 0.0) || !(opt.cheb_upper > opt.cheb_lower))) ||
-      (opt.adaptive_geo != 0 && (opt.adaptive_iters < 1 || opt.adaptive_min_geo < 1)))
+      (opt.adaptive_geo != 0 && (opt.adaptive_iters < 1 || opt.adaptive_min_geo < 1)) ||
+      opt.krylov < 0 || opt.krylov > 1 ||
+      (opt.krylov == 1 && (opt.gmres_restart < 1 || opt.gmres_restart > 200)))
     TOMG_THROW(TOMG_E_INVALID, "invalid options");
   P->setup_valid = false;
   P->setup_gen++;
@@ -942,6 +944,141 @@ bool finish_rhs(tomg_problem* P, Work& W, double* u, int on_device, tomg_result*
   return true;
 }
 
+// z = M v: one V-cycle of the current setup in its precision (FP64 in and out)
+void precondition(tomg_problem* P, Work& W, const double* v, double* z) {
+  cudaStream_t s = W.stream;
+  const int64_t n = P->n;
+  if (P->opt.prec == TOMG_PREC_FP64) {
+    vcycle<double>(P, W, 0, v, z, nullptr);
+  } else {
+    LevelWork& l0 = W.lw[0];
+    cast_in<float>(s, v, l0.b32.p, n, nullptr);
+    vcycle<float>(P, W, 0, l0.b32.p, l0.y32.p, nullptr);
+    cast_f32_f64(s, l0.y32.p, z, n);
+  }
+}
+
+// h[0..J) = V_k . w, read back to the host (synchronises the stream)
+void host_dots(cudaStream_t s, int64_t n, int J, const double* V, int64_t ldv, const double* w,
+               double* parts, double* hd, double* hh) {
+  multi_dot(s, n, J, V, ldv, w, parts, hd);
+  CK(cudaMemcpyAsync(hh, hd, sizeof(double) * J, cudaMemcpyDeviceToHost, s));
+  CK(cudaStreamSynchronize(s));
+}
+
+// Flexible GMRES(m) (Saad, Alg. 9.6), right preconditioned by the V-cycle: Arnoldi with
+// classical Gram-Schmidt applied twice (two multi-dot / multi-update launches each) on the
+// device, Givens rotations and the small triangular solve on the host.  Every cycle starts
+// from the true FP64 residual b - K x; the solve stops when it is within rtol ||b||.
+void solve_fgmres(tomg_problem* P, int nrhs, const double* f, double* u, int on_device,
+                  tomg_result* res) {
+  Work& W = ensure_work(P, 0);
+  fork_to(P, W);
+  cudaStream_t s = W.stream;
+  const int64_t n = P->n;
+  const int m = P->opt.gmres_restart;
+  const cudaMemcpyKind h2d = on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice;
+  DBuf<double> V, Z, w, hd, parts, cd;
+  V.resize((int64_t)(m + 1) * n);
+  Z.resize((int64_t)m * n);
+  w.resize(n);
+  hd.resize(m + 2);
+  parts.resize(multi_dot_parts(m + 1));
+  cd.resize(m + 1);
+  std::vector<double> H((size_t)(m + 1) * m), cs(m), sn(m), g(m + 1), h1(m + 2), h2(m + 2), y(m);
+  auto Hc = [&](int i, int j) -> double& { return H[(size_t)i * m + j]; };
+  const double rtol2 = P->opt.rtol * P->opt.rtol;
+  for (int rj = 0; rj < nrhs; rj++) {
+    CK(cudaEventRecord(W.ev0, s));
+    CK(cudaMemcpyAsync(W.f.p, f + (int64_t)rj * n, n * 8, h2d, s));
+    CK(cudaMemcpyAsync(W.t.p, u + (int64_t)rj * n, n * 8, h2d, s));
+    mask_vec(s, W.f.p, W.bvec.p, P->mask.p, P->dim, P->nn);
+    mask_vec(s, W.t.p, W.x.p, P->mask.p, P->dim, P->nn);
+    double bb = 0.0;
+    host_dots(s, n, 1, W.bvec.p, n, W.bvec.p, parts.p, hd.p, &bb);
+    int it = 0, status = TOMG_NOT_CONVERGED;
+    double rr = 0.0;
+    if (bb == 0.0) {
+      CK(cudaMemsetAsync(W.x.p, 0, n * 8, s));
+      status = TOMG_OK;
+    }
+    while (status != TOMG_OK) {
+      fine64_resid(P, s, W.x.p, W.r.p, W.bvec.p);
+      host_dots(s, n, 1, W.r.p, n, W.r.p, parts.p, hd.p, &rr);
+      if (!std::isfinite(rr)) { status = TOMG_E_BREAKDOWN; break; }
+      if (rr <= rtol2 * bb) { status = TOMG_OK; break; }
+      if (it >= P->opt.max_iter) break;
+      const double beta = std::sqrt(rr);
+      scale_into(s, n, W.r.p, 1.0 / beta, V.p);
+      std::fill(g.begin(), g.end(), 0.0);
+      g[0] = beta;
+      int k = 0;
+      for (int j = 0; j < m; j++) {
+        double* vj = V.p + (int64_t)j * n;
+        double* zj = Z.p + (int64_t)j * n;
+        precondition(P, W, vj, zj);
+        fine64_apply_dot(P, s, zj, w.p, nullptr, nullptr, nullptr);
+        host_dots(s, n, j + 1, V.p, n, w.p, parts.p, hd.p, h1.data());
+        multi_update(s, n, j + 1, V.p, n, hd.p, -1.0, w.p);
+        host_dots(s, n, j + 1, V.p, n, w.p, parts.p, hd.p, h2.data());
+        multi_update(s, n, j + 1, V.p, n, hd.p, -1.0, w.p);
+        double hn2 = 0.0;
+        host_dots(s, n, 1, w.p, n, w.p, parts.p, hd.p, &hn2);
+        const double hn = std::sqrt(hn2);
+        for (int i = 0; i <= j; i++) Hc(i, j) = h1[i] + h2[i];
+        if (hn > 0.0) scale_into(s, n, w.p, 1.0 / hn, V.p + (int64_t)(j + 1) * n);
+        double hj1 = hn;
+        for (int i = 0; i < j; i++) {
+          const double t = cs[i] * Hc(i, j) + sn[i] * Hc(i + 1, j);
+          Hc(i + 1, j) = -sn[i] * Hc(i, j) + cs[i] * Hc(i + 1, j);
+          Hc(i, j) = t;
+        }
+        const double den = std::hypot(Hc(j, j), hj1);
+        if (!(den > 0.0) || !std::isfinite(den)) { status = TOMG_E_BREAKDOWN; break; }
+        cs[j] = Hc(j, j) / den;
+        sn[j] = hj1 / den;
+        Hc(j, j) = den;
+        g[j + 1] = -sn[j] * g[j];
+        g[j] = cs[j] * g[j];
+        it++;
+        k = j + 1;
+        if (g[j + 1] * g[j + 1] <= rtol2 * bb || it >= P->opt.max_iter || hn == 0.0) break;
+      }
+      if (status == TOMG_E_BREAKDOWN) break;
+      for (int i = k - 1; i >= 0; i--) {
+        double a = g[i];
+        for (int q = i + 1; q < k; q++) a -= Hc(i, q) * y[q];
+        y[i] = a / Hc(i, i);
+      }
+      CK(cudaMemcpyAsync(cd.p, y.data(), sizeof(double) * k, cudaMemcpyHostToDevice, s));
+      multi_update(s, n, k, Z.p, n, cd.p, 1.0, W.x.p);
+      CK(cudaStreamSynchronize(s));  // y is a host vector reused by the next cycle
+    }
+    // fixed DOFs exactly zero, compliance f^T u
+    mask_vec(s, W.x.p, W.t.p, P->mask.p, P->dim, P->nn);
+    double comp = 0.0;
+    host_dots(s, n, 1, W.f.p, n, W.t.p, parts.p, hd.p, &comp);
+    CK(cudaMemcpyAsync(u + (int64_t)rj * n, W.t.p, n * 8,
+                       on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost, s));
+    CK(cudaEventRecord(W.ev1, s));
+    CK(cudaEventSynchronize(W.ev1));
+    float ms = 0.f;
+    CK(cudaEventElapsedTime(&ms, W.ev0, W.ev1));
+    res[rj].iterations = it;
+    res[rj].rel_residual = bb > 0.0 ? std::sqrt(rr / bb) : 0.0;
+    res[rj].compliance = comp;
+    res[rj].setup_ms = P->setup_ms;
+    res[rj].solve_ms = ms;
+    res[rj].status = status;
+    if (status == TOMG_NOT_CONVERGED)
+      set_error("FGMRES not converged after %d iterations (rel residual %.3e, rhs %d)", it,
+                res[rj].rel_residual, rj);
+    else if (status == TOMG_E_BREAKDOWN)
+      set_error("FGMRES breakdown at iteration %d (rhs %d)", it, rj);
+  }
+  join_from(P, W);
+}
+
 }  // namespace
 
 tomg_status solve(tomg_problem* P, int nrhs, const double* f, double* u, int on_device,
@@ -949,22 +1086,26 @@ tomg_status solve(tomg_problem* P, int nrhs, const double* f, double* u, int on_
   if (!P->setup_valid) TOMG_THROW(TOMG_E_INVALID, "tomg_solve: call tomg_setup after changing density or fixed DOFs");
   if (nrhs < 0 || (nrhs > 0 && (!f || !u || !res))) TOMG_THROW(TOMG_E_INVALID, "bad solve arguments");
   if (nrhs == 0) return TOMG_OK;
-  const int slots = std::max(1, std::min(nrhs, P->opt.concurrency > 0 ? P->opt.concurrency : 1));
-  for (int k = 0; k < slots; k++) ensure_work(P, k);
-  for (int k = 0; k < slots; k++) fork_to(P, *P->works[k]);
-  int next = 0;
-  for (int k = 0; k < slots; k++) start_rhs(P, *P->works[k], next++, f, u, on_device);
-  int active = slots;
-  while (active > 0) {
-    for (int k = 0; k < slots; k++) {
-      Work& W = *P->works[k];
-      if (W.rhs < 0) continue;
-      if (!finish_rhs(P, W, u, on_device, res)) continue;
-      if (next < nrhs) start_rhs(P, W, next++, f, u, on_device);
-      else active--;
+  if (P->opt.krylov == 1) {
+    solve_fgmres(P, nrhs, f, u, on_device, res);
+  } else {
+    const int slots = std::max(1, std::min(nrhs, P->opt.concurrency > 0 ? P->opt.concurrency : 1));
+    for (int k = 0; k < slots; k++) ensure_work(P, k);
+    for (int k = 0; k < slots; k++) fork_to(P, *P->works[k]);
+    int next = 0;
+    for (int k = 0; k < slots; k++) start_rhs(P, *P->works[k], next++, f, u, on_device);
+    int active = slots;
+    while (active > 0) {
+      for (int k = 0; k < slots; k++) {
+        Work& W = *P->works[k];
+        if (W.rhs < 0) continue;
+        if (!finish_rhs(P, W, u, on_device, res)) continue;
+        if (next < nrhs) start_rhs(P, W, next++, f, u, on_device);
+        else active--;
+      }
     }
+    for (int k = 0; k < slots; k++) join_from(P, *P->works[k]);
   }
-  for (int k = 0; k < slots; k++) join_from(P, *P->works[k]);
   CK(cudaStreamSynchronize(st(P)));
   if (P->dim == 3 && P->opt.prec == TOMG_PREC_3XTF32_VCYCLE && ebe3d_tc_error(st(P)))
     for (int j = 0; j < nrhs; j++) res[j].status = TOMG_E_TIMEOUT;

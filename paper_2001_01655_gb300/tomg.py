@@ -18,6 +18,7 @@ OK, NOT_CONVERGED, E_INVALID, E_OOM, E_CUDA, E_BREAKDOWN, E_TIMEOUT, E_BUDGET = 
 PC = {"gmg": 0, "amg": 1, "hybrid": 2, "jacobi": 3}
 PREC = {"fp64": 0, "fp32": 1, "tf32x3": 2}
 SMOOTHER = {"jacobi": 0, "chebyshev": 1}
+KRYLOV = {"cg": 0, "fgmres": 1}
 
 
 class TomgError(RuntimeError):
@@ -33,7 +34,8 @@ class Options(C.Structure):
                 ("n_post", C.c_int), ("soc_beta", C.c_double), ("check_every", C.c_int),
                 ("use_graph", C.c_int), ("max_levels", C.c_int), ("concurrency", C.c_int),
                 ("cheb_degree", C.c_int), ("cheb_lower", C.c_double), ("cheb_upper", C.c_double),
-                ("adaptive_geo", C.c_int), ("adaptive_iters", C.c_int), ("adaptive_min_geo", C.c_int)]
+                ("adaptive_geo", C.c_int), ("adaptive_iters", C.c_int), ("adaptive_min_geo", C.c_int),
+                ("krylov", C.c_int), ("gmres_restart", C.c_int)]
 
 
 class Result(C.Structure):
@@ -127,6 +129,8 @@ def default_options(**kw) -> Options:
             v = PREC[v]
         if k == "smoother" and isinstance(v, str):
             v = SMOOTHER[v]
+        if k == "krylov" and isinstance(v, str):
+            v = KRYLOV[v]
         setattr(o, k, v)
     return o
 
