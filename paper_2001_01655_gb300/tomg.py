@@ -330,21 +330,35 @@ class Problem:
         _check(load().tomg_moduli(self.h, C.c_void_p(E.ctypes.data), 0))
         return E
 
-    def density_filter(self, a, radius=1.5, transpose=False):
-        """rho = S a (or S^T a): the linear density filter of the problem's grid."""
-        src = np.ascontiguousarray(a, dtype=np.float64)
-        out = np.zeros(self.nel)
-        _check(load().tomg_density_filter(self.h, float(radius), int(bool(transpose)),
-                                          C.c_void_p(src.ctypes.data),
-                                          C.c_void_p(out.ctypes.data), 0))
+    def density_filter(self, a, radius=1.5, transpose=False, out=None):
+        """rho = S a (or S^T a): the linear density filter of the problem's grid.  numpy in,
+        numpy out; or CUDA tensors (device path; `out` a tensor of n_elems doubles)."""
+        src, dev, keep = _ptr(a, np.float64)
+        if dev:
+            import torch
+            out = torch.empty_like(a) if out is None else out
+            dst, _, _ = _ptr(out, np.float64)
+        else:
+            out = np.zeros(self.nel)
+            dst = C.c_void_p(out.ctypes.data)
+        _check(load().tomg_density_filter(self.h, float(radius), int(bool(transpose)), src, dst,
+                                          dev))
         return out
 
-    def compliance_sensitivity(self, u):
-        """dF/drho for the current density and displacements u (n_dofs)."""
-        src = np.ascontiguousarray(u, dtype=np.float64).reshape(-1)
-        out = np.zeros(self.nel)
-        _check(load().tomg_compliance_sensitivity(self.h, C.c_void_p(src.ctypes.data),
-                                                  C.c_void_p(out.ctypes.data), 0))
+    def compliance_sensitivity(self, u, out=None):
+        """dF/drho for the current density and displacements u (n_dofs): numpy, or CUDA
+        tensors (device path)."""
+        if not _is_torch(u):
+            u = np.ascontiguousarray(u, dtype=np.float64).reshape(-1)
+        src, dev, keep = _ptr(u, np.float64)
+        if dev:
+            import torch
+            out = torch.empty(self.nel, dtype=torch.float64, device=u.device) if out is None else out
+            dst, _, _ = _ptr(out, np.float64)
+        else:
+            out = np.zeros(self.nel)
+            dst = C.c_void_p(out.ctypes.data)
+        _check(load().tomg_compliance_sensitivity(self.h, src, dst, dev))
         return out
 
     def fine_apply_f32_noalloc(self, x, y):
