@@ -1,0 +1,160 @@
+"""Linear buckling (stability) eigenproblem K_sigma Phi = lambda K Phi and the generalized
+Davidson eigensolver (oracle, FP64, test infrastructure only).
+
+Stress stiffness (Sec. 2.2, Eq. 4-5).  The pre-buckling stress of element e is evaluated at the
+element centre from the displacements u of K u = f:
+    sigma_e = E_sigma(rho_e) D_0 B(centre) u_e,   E_sigma(rho) = E0 rho^p if rho >= 0.1 else 0,
+with D_0 the unit-modulus constitutive matrix.  With S_e the d x d stress tensor and
+L_ij[a, b] = integral over the unit element of dN_a/dx_i dN_b/dx_j, the element geometric
+stiffness is K_G,e = (sum_ij S_e,ij L_ij) (x) I_d (one copy per displacement component).  The
+paper writes the eigenproblem as K_sigma Phi = lambda K Phi with lambda_max = 1 / P_critical;
+the reading adopted is K_sigma = -K_G, so that compression gives positive lambda = 1 / mu for
+the load factors mu of (K + mu K_G) Phi = 0.  Fixed DOFs: K_sigma is masked (M K_sigma M),
+K is the masked operator M K M + (I - M) of the solve.
+
+Generalized Davidson (Sec. 3.3, Algorithm 2): a K-orthonormal search space V of j_min..j_max
+vectors; Rayleigh-Ritz on V (the projected matrix V^T K_sigma V, V^T K V = I); the largest
+Ritz pairs are the targets; the search space grows by the preconditioned residual
+z = M(K_sigma q - theta K q) of the largest unconverged pair, orthonormalised against V, and
+is reset to the j_min best Ritz vectors when it reaches j_max.  The paper's settings:
+j_min = 10, j_max = 25, six modes.  Start vectors: splitmix64 uniform vectors.
+
+Parity: pinned (tests/test_oracle_stability.py: L_ij against exact rational integration,
+symmetry and the translation null space of K_sigma, the 1D-like stress of a uniformly
+compressed bar, Davidson eigenvalues against dense scipy.linalg.eigh on small grids).
+"""
+from __future__ import annotations
+
+import numpy as np
+import scipy.sparse as sp
+
+from . import fem
+from .hashing import SALT_POWER, unit_uniform
+
+SALT_GD = SALT_POWER + 1000  # start vector k of the Davidson search space uses salt SALT_GD + k
+
+
+def stress_interp(rho, E0, penal, cutoff=0.1):
+    """E_sigma(rho) = E0 rho^p for rho >= cutoff, else 0 (Eq. 5)."""
+    rho = np.asarray(rho, dtype=np.float64)
+    return np.where(rho >= cutoff, E0 * rho ** penal, 0.0)
+
+
+def gradient_products(dim):
+    """L[i][j] = integral of dN_a/dx_i dN_b/dx_j over the unit element (2^dim x 2^dim), by the
+    2x2(x2) Gauss rule (exact: the integrands are at most quadratic per direction)."""
+    g = [0.5 - 0.5 / np.sqrt(3.0), 0.5 + 0.5 / np.sqrt(3.0)]
+    nn = 1 << dim
+    L = np.zeros((dim, dim, nn, nn))
+    w = 0.5 ** dim
+    for p in range(1 << dim):
+        xi = [g[(p >> k) & 1] for k in range(dim)]
+        G = fem.shape_grad(dim, xi)
+        for i in range(dim):
+            for j in range(dim):
+                L[i, j] += w * np.outer(G[:, i], G[:, j])
+    return L
+
+
+def element_stresses(problem, u):
+    """(Nel, d, d) stress tensors at the element centres."""
+    p = problem
+    dim = p.dim
+    B = fem.strain_matrix(dim, fem.shape_grad(dim, [0.5] * dim))
+    D0 = fem.constitutive(dim, 1.0, p.nu)
+    ed = fem.element_dofs(dim, p.nx, p.ny, p.nz)
+    sv = (np.asarray(u)[ed] @ B.T) @ D0.T  # Voigt stresses per unit modulus
+    sv = sv * stress_interp(p.rho, p.E0, p.penal)[:, None]
+    S = np.zeros((sv.shape[0], dim, dim))
+    if dim == 2:
+        S[:, 0, 0], S[:, 1, 1] = sv[:, 0], sv[:, 1]
+        S[:, 0, 1] = S[:, 1, 0] = sv[:, 2]
+    else:
+        S[:, 0, 0], S[:, 1, 1], S[:, 2, 2] = sv[:, 0], sv[:, 1], sv[:, 2]
+        S[:, 1, 2] = S[:, 2, 1] = sv[:, 3]
+        S[:, 0, 2] = S[:, 2, 0] = sv[:, 4]
+        S[:, 0, 1] = S[:, 1, 0] = sv[:, 5]
+    return S
+
+
+def stress_stiffness(problem, u):
+    """K_sigma = -sum_e (sum_ij S_e,ij L_ij) (x) I_d, masked at fixed DOFs, as CSR."""
+    p = problem
+    dim = p.dim
+    L = gradient_products(dim)
+    S = element_stresses(p, u)
+    H = np.einsum("eij,ijab->eab", S, L)  # (Nel, nn, nn)
+    nn = 1 << dim
+    nd = dim * nn
+    Ke = np.zeros((H.shape[0], nd, nd))
+    for c in range(dim):
+        Ke[:, c::dim, c::dim] = -H
+    ed = fem.element_dofs(dim, p.nx, p.ny, p.nz)
+    n = p.n
+    rows = np.repeat(ed, nd, axis=1).ravel()
+    cols = np.tile(ed, (1, nd)).ravel()
+    Ks = sp.csr_matrix((Ke.ravel(), (rows, cols)), shape=(n, n))
+    Ks.sum_duplicates()
+    m = fem.free_mask(n, p.fixed)
+    Md = sp.diags(m)
+    return (Md @ Ks @ Md).tocsr()
+
+
+def _k_orthonormalize(z, V, KV, K, passes=2):
+    """z minus its K-projections on the K-orthonormal columns of V (twice), K-normalised.
+    Returns (z, Kz) or (None, None) if z is (numerically) inside span V."""
+    z = np.array(z, dtype=np.float64)
+    n0 = np.sqrt(max(z @ (K @ z), 0.0))
+    for _ in range(passes):
+        if V.shape[1]:
+            z = z - V @ (KV.T @ z)
+    Kz = K @ z
+    nz = np.sqrt(max(z @ Kz, 0.0))
+    if not (nz > 1e-10 * n0) or nz == 0.0:
+        return None, None
+    return z / nz, Kz / nz
+
+
+def davidson(Ks, K, M=None, n_eig=6, jmin=10, jmax=25, tol=1e-6, max_iter=1000):
+    """Largest eigenpairs of Ks Phi = lambda K Phi by generalized Davidson (Algorithm 2).
+    Returns (lambdas descending, Phi (n, n_eig) K-orthonormal, iterations, residuals), the
+    iteration count being the number of preconditioner applications.  Convergence of a pair:
+    ||Ks q - theta K q|| <= tol ||K q|| |theta| for each of the n_eig largest Ritz pairs."""
+    M = (lambda r: r.copy()) if M is None else M
+    n = K.shape[0]
+    V = np.zeros((n, 0))
+    KV = np.zeros((n, 0))
+    for k in range(jmin):
+        z, Kz = _k_orthonormalize(unit_uniform(n, SALT_GD + k), V, KV, K)
+        if z is not None:
+            V, KV = np.column_stack([V, z]), np.column_stack([KV, Kz])
+    SV = Ks @ V
+    it = 0
+    while True:
+        Hp = V.T @ SV
+        Hp = 0.5 * (Hp + Hp.T)
+        th, Sv = np.linalg.eigh(Hp)
+        order = np.argsort(th)[::-1]
+        th, Sv = th[order], Sv[:, order]
+        k = min(n_eig, len(th))
+        res, conv = [], []
+        for i in range(k):
+            r = SV @ Sv[:, i] - th[i] * (KV @ Sv[:, i])
+            nr = np.linalg.norm(r)
+            res.append(nr)
+            conv.append(nr <= tol * abs(th[i]) * np.linalg.norm(KV @ Sv[:, i]))
+        if all(conv) or it >= max_iter:
+            Phi = V @ Sv[:, :k]
+            return th[:k], Phi, it, np.array(res)
+        t = conv.index(False)
+        r = SV @ Sv[:, t] - th[t] * (KV @ Sv[:, t])
+        if V.shape[1] >= jmax:
+            keep = Sv[:, :jmin]
+            V, KV, SV = V @ keep, KV @ keep, SV @ keep
+        z, Kz = _k_orthonormalize(M(r), V, KV, K)
+        it += 1
+        if z is None:
+            continue
+        V = np.column_stack([V, z])
+        KV = np.column_stack([KV, Kz])
+        SV = np.column_stack([SV, Ks @ z])

@@ -154,6 +154,25 @@ def cantilever_2d(nx=768, ny=384, seed=0, sigma=8.0, volfrac=0.4, **mat) -> Prob
                    meta={"seed": seed, "sigma": sigma, "volfrac": volfrac}, **mat)
 
 
+def column_2d(nx=256, ny=1024, seed=None, sigma=8.0, rho_lo=0.1, **mat) -> Problem:
+    """2D column (the stability example's geometry): bottom edge clamped, a total downward load
+    of 1 spread over the top edge with consistent weights (end nodes half).  Density uniform 1,
+    or with ``seed`` a smoothed random field min-max mapped to [rho_lo, 1]."""
+    dim = 2
+    bottom = node_id(nx, ny, np.arange(nx + 1), 0)
+    fixed = _dofs_of_nodes(dim, bottom)
+    f = np.zeros((1, n_dofs(dim, nx, ny)))
+    w = np.full(nx + 1, 1.0 / nx)
+    w[0] = w[-1] = 0.5 / nx
+    f[0, dim * node_id(nx, ny, np.arange(nx + 1), ny) + 1] = -w
+    if seed is None:
+        rho = np.ones(nx * ny)
+    else:
+        rho = _minmax(smoothed_field((ny, nx), sigma, seed), rho_lo).ravel()
+    return Problem("column2d_%dx%d" % (nx, ny), dim, nx, ny, 1, rho, fixed, f,
+                   meta={"seed": seed}, **mat)
+
+
 def _clamp_x0_3d(nx, ny, nz):
     jj, kk = np.meshgrid(np.arange(ny + 1), np.arange(nz + 1), indexing="ij")
     return _dofs_of_nodes(3, node_id(nx, ny, 0, jj, kk))
