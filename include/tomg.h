@@ -259,6 +259,25 @@ tomg_status tomg_density_filter(tomg_problem* prob, double radius, int transpose
 tomg_status tomg_compliance_sensitivity(tomg_problem* prob, const double* u, double* out,
                                         int on_device);
 
+/* ---- linear buckling, the stability problem (Sec. 2.2 Eq. 4-5; Sec. 3.3 Algorithm 2) --------
+ * Stress stiffness for the displacements u of the current density: element stresses at the
+ * element centres sigma_e = E_sigma(rho_e) D_0 B u_e with E_sigma = E0 rho^p for rho >= 0.1 and 0
+ * below (Eq. 5); K_sigma = -sum_e (sum_ij sigma_e,ij L_ij) (x) I, L_ij the integrals of products of
+ * shape-function derivatives, masked at fixed DOFs (the sign makes compression give positive
+ * eigenvalues).  y = K_sigma x: u, x, y n_dofs doubles, host or device (on_device). */
+tomg_status tomg_stress_stiffness_apply(tomg_problem* prob, const double* u, const double* x,
+                                        double* y, int on_device);
+/* The n_eig largest eigenpairs of K_sigma Phi = lambda K Phi (lambda_max = 1 / P_critical) by
+ * generalized Davidson (Algorithm 2) with the current setup's V-cycle as preconditioner (its
+ * precision): search space j_min..j_max (10..25 in the paper), converged when every pair has
+ * ||K_sigma q - theta K q|| <= tol |theta| ||K q||.  lambdas: n_eig doubles, descending (host);
+ * modes: NULL or n_dofs x n_eig column-major, K-orthonormal (host or device per on_device);
+ * iterations: preconditioner applications (nullable).  Needs a setup; 1 <= n_eig <= 16,
+ * n_eig < j_min < j_max <= 64.  NOT_CONVERGED after max_iter with the current Ritz pairs. */
+tomg_status tomg_buckling(tomg_problem* prob, const double* u, int n_eig, int j_min, int j_max,
+                          double tol, int max_iter, double* lambdas, double* modes, int on_device,
+                          int* iterations);
+
 /* Adaptive hybrid hierarchy (Sec. 4.4): the geometric level count (including the fine grid)
  * the next tomg_setup of this problem will use, 0 before the first setup with adaptive_geo. */
 tomg_status tomg_adaptive_geo_levels(const tomg_problem* prob, int* n_geo_levels);

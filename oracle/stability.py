@@ -102,15 +102,18 @@ def stress_stiffness(problem, u):
 
 def _k_orthonormalize(z, V, KV, K, passes=2):
     """z minus its K-projections on the K-orthonormal columns of V (twice), K-normalised.
-    Returns (z, Kz) or (None, None) if z is (numerically) inside span V."""
+    Returns (z, Kz) or (None, None) if z is (numerically) inside span V: its 2-norm dropped
+    below 1e-10 of the 2-norm it had."""
     z = np.array(z, dtype=np.float64)
-    n0 = np.sqrt(max(z @ (K @ z), 0.0))
+    n0 = np.linalg.norm(z)
     for _ in range(passes):
         if V.shape[1]:
             z = z - V @ (KV.T @ z)
+    if not (np.linalg.norm(z) > 1e-10 * n0):
+        return None, None
     Kz = K @ z
     nz = np.sqrt(max(z @ Kz, 0.0))
-    if not (nz > 1e-10 * n0) or nz == 0.0:
+    if not (nz > 0.0):
         return None, None
     return z / nz, Kz / nz
 

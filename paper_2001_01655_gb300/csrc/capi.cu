@@ -461,6 +461,42 @@ tomg_status tomg_compliance_sensitivity(tomg_problem* P, const double* u, double
   });
 }
 
+tomg_status tomg_stress_stiffness_apply(tomg_problem* P, const double* u, const double* x,
+                                        double* y, int on_device) {
+  return guarded([&]() -> tomg_status {
+    if (!P || !u || !x || !y) TOMG_THROW(TOMG_E_INVALID, "null argument");
+    if (!P->have_density) TOMG_THROW(TOMG_E_INVALID, "no density set");
+    set_device(P);
+    StreamScope sc(P);
+    cudaStream_t s = P->stream;
+    const size_t bytes = (size_t)P->n * 8;
+    if (on_device) {
+      tomg::stress_stiffness_op(P, u, x, y);
+      return TOMG_OK;
+    }
+    tomg::DBuf<double> du, dx, dy;
+    du.resize(P->n); dx.resize(P->n); dy.resize(P->n);
+    CK(cudaMemcpyAsync(du.p, u, bytes, cudaMemcpyHostToDevice, s));
+    CK(cudaMemcpyAsync(dx.p, x, bytes, cudaMemcpyHostToDevice, s));
+    tomg::stress_stiffness_op(P, du.p, dx.p, dy.p);
+    CK(cudaMemcpyAsync(y, dy.p, bytes, cudaMemcpyDeviceToHost, s));
+    CK(cudaStreamSynchronize(s));
+    return TOMG_OK;
+  });
+}
+
+tomg_status tomg_buckling(tomg_problem* P, const double* u, int n_eig, int j_min, int j_max,
+                          double tol, int max_iter, double* lambdas, double* modes, int on_device,
+                          int* iterations) {
+  return guarded([&]() -> tomg_status {
+    if (!P || !u || !lambdas) TOMG_THROW(TOMG_E_INVALID, "null argument");
+    set_device(P);
+    StreamScope sc(P);
+    return tomg::buckling(P, u, n_eig, j_min, j_max, tol, max_iter, lambdas, modes, on_device,
+                          iterations);
+  });
+}
+
 tomg_status tomg_element_stiffness(const tomg_problem* P, double* Ke) {
   if (!P || !Ke) { set_error("null argument"); return TOMG_E_INVALID; }
   memcpy(Ke, P->Ke_host.data(), P->Ke_host.size() * sizeof(double));

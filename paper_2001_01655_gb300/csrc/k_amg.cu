@@ -514,6 +514,10 @@ __global__ void k_dinv_scale(int64_t nodes, const double* __restrict__ Dinv,
   }
 }
 
+void splitmix_uniform(cudaStream_t s, int64_t n, int level, double* v) {
+  LAUNCH(k_power_init, ceil_div(n, 256), 256, 0, s, n, level, v);
+}
+
 double spectral_radius_op(cudaStream_t s, int64_t nodes, int bs, const double* Dinv, int level,
                           int iters, const std::function<void(const double*, double*)>& apply) {
   // the same iteration as amg_spectral_radius, with the operator applied by the caller:

@@ -89,6 +89,15 @@ void compliance_sensitivity(cudaStream_t s, int dim, int nx, int ny, int nz, con
                             const double* rho, const double* u, double E0, double Emin,
                             double penal, double* dc);
 
+// ---------------- linear buckling (k_stability.cu) -----------------------------------
+int stress_components(int dim);  // 3 (2D) or 6 (3D) Voigt components per element
+// centre stresses sigma_e = E_sigma(rho_e) D_0 B(centre) u_e, n_elems x stress_components
+void element_stresses(cudaStream_t s, int dim, int nx, int ny, int nz, double nu, double E0,
+                      double penal, const double* rho, const double* u, double* sig);
+// y = M K_sigma M x from the element stresses (FP64)
+void stress_stiffness_apply(cudaStream_t s, int dim, int nx, int ny, int nz, double nu,
+                            const double* sig, const uint8_t* mask, const double* x, double* y);
+
 // ---------------- geometric levels: structured stencils and transfers -----------------
 struct Geo {
   int dim, nx, ny, nz;  // element counts of this level (nz = 1 in 2D)
@@ -176,6 +185,8 @@ void amg_tentative(cudaStream_t s, int n_nodes, int b, int k, int n_agg, const i
 // spectral radius of D^-1 A by power iteration (FP64), returns rho (syncs)
 double amg_spectral_radius(cudaStream_t s, const Bsr& A, const double* V, const double* Dinv,
                            int level, int iters, double* v, double* w, double* partials);
+// v[i] = (splitmix64(i + SALT_POWER + level) >> 11) 2^-53 - 0.5 (the power-iteration start vector)
+void splitmix_uniform(cudaStream_t s, int64_t n, int level, double* v);
 // spectral radius of D^-1 A for an operator applied by `apply(x, y)` (y = A x, FP64, n = nodes *
 // bs), same start vector and iteration as amg_spectral_radius; returns rho (syncs)
 double spectral_radius_op(cudaStream_t s, int64_t nodes, int bs, const double* Dinv, int level,

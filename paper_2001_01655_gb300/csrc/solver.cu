@@ -1125,6 +1125,187 @@ tomg_status solve(tomg_problem* P, int nrhs, const double* f, double* u, int on_
 }
 
 // ----------------------------------------------------------------------------------------
+// Linear buckling: K_sigma from the centre stresses of u, generalized Davidson (Algorithm 2)
+namespace {
+// eigenvalues (descending) and orthonormal eigenvectors (columns of Q, n x n row-major) of the
+// symmetric n x n matrix A (row-major, destroyed) by cyclic Jacobi rotations
+void sym_eig(int n, std::vector<double>& A, std::vector<double>& w, std::vector<double>& Q) {
+  Q.assign((size_t)n * n, 0.0);
+  for (int i = 0; i < n; i++) Q[(size_t)i * n + i] = 1.0;
+  auto a = [&](int i, int j) -> double& { return A[(size_t)i * n + j]; };
+  for (int sweep = 0; sweep < 100; sweep++) {
+    double off = 0.0, tot = 0.0;
+    for (int i = 0; i < n; i++)
+      for (int j = 0; j < n; j++) {
+        tot += a(i, j) * a(i, j);
+        if (i != j) off += a(i, j) * a(i, j);
+      }
+    if (off <= 1e-30 * tot || off == 0.0) break;
+    for (int p = 0; p < n - 1; p++)
+      for (int q = p + 1; q < n; q++) {
+        if (a(p, q) == 0.0) continue;
+        const double th = 0.5 * (a(q, q) - a(p, p)) / a(p, q);
+        const double t = (th >= 0 ? 1.0 : -1.0) / (std::fabs(th) + std::sqrt(th * th + 1.0));
+        const double c = 1.0 / std::sqrt(t * t + 1.0), sn = t * c;
+        for (int k = 0; k < n; k++) {  // columns p, q
+          const double akp = a(k, p), akq = a(k, q);
+          a(k, p) = c * akp - sn * akq;
+          a(k, q) = sn * akp + c * akq;
+        }
+        for (int k = 0; k < n; k++) {  // rows p, q
+          const double apk = a(p, k), aqk = a(q, k);
+          a(p, k) = c * apk - sn * aqk;
+          a(q, k) = sn * apk + c * aqk;
+        }
+        for (int k = 0; k < n; k++) {
+          const double qkp = Q[(size_t)k * n + p], qkq = Q[(size_t)k * n + q];
+          Q[(size_t)k * n + p] = c * qkp - sn * qkq;
+          Q[(size_t)k * n + q] = sn * qkp + c * qkq;
+        }
+      }
+  }
+  std::vector<int> idx(n);
+  for (int i = 0; i < n; i++) idx[i] = i;
+  std::sort(idx.begin(), idx.end(), [&](int x, int y) { return a(x, x) > a(y, y); });
+  w.resize(n);
+  std::vector<double> Qs((size_t)n * n);
+  for (int c = 0; c < n; c++) {
+    w[c] = a(idx[c], idx[c]);
+    for (int k = 0; k < n; k++) Qs[(size_t)k * n + c] = Q[(size_t)k * n + idx[c]];
+  }
+  Q.swap(Qs);
+}
+}  // namespace
+
+void stress_stiffness_op(tomg_problem* P, const double* u, const double* x, double* y) {
+  cudaStream_t s = st(P);
+  DBuf<double> sig;
+  sig.resize(P->nel * stress_components(P->dim));
+  element_stresses(s, P->dim, P->nx, P->ny, P->nz, P->nu, P->E0, P->penal, P->rho.p, u, sig.p);
+  stress_stiffness_apply(s, P->dim, P->nx, P->ny, P->nz, P->nu, sig.p, P->mask.p, x, y);
+  CK(cudaStreamSynchronize(s));
+}
+
+tomg_status buckling(tomg_problem* P, const double* u, int n_eig, int jmin, int jmax, double tol,
+                     int max_iter, double* lambdas, double* modes, int on_device, int* iterations) {
+  if (!P->setup_valid) TOMG_THROW(TOMG_E_INVALID, "tomg_buckling: needs a setup");
+  if (n_eig < 1 || n_eig > 16 || jmin <= n_eig || jmax <= jmin || jmax > 64 || !(tol > 0.0) ||
+      max_iter < 0 || !lambdas)
+    TOMG_THROW(TOMG_E_INVALID, "bad buckling arguments");
+  Work& W = ensure_work(P, 0);
+  fork_to(P, W);
+  cudaStream_t s = W.stream;
+  const int64_t n = P->n;
+  DBuf<double> du, sig, V, KV, SV, z, Kz, r, q, tmp, parts, hd, cd, dm;
+  const double* uu = u;
+  if (!on_device) {
+    du.resize(n);
+    CK(cudaMemcpyAsync(du.p, u, n * 8, cudaMemcpyHostToDevice, s));
+    uu = du.p;
+  }
+  sig.resize(P->nel * stress_components(P->dim));
+  element_stresses(s, P->dim, P->nx, P->ny, P->nz, P->nu, P->E0, P->penal, P->rho.p, uu, sig.p);
+  V.resize((int64_t)jmax * n); KV.resize((int64_t)jmax * n); SV.resize((int64_t)jmax * n);
+  z.resize(n); Kz.resize(n); r.resize(n); q.resize(n); tmp.resize((int64_t)jmin * n);
+  parts.resize(multi_dot_parts(jmax + 1)); hd.resize(jmax + 1); cd.resize(jmax + 1);
+  auto Kapply = [&](const double* x, double* y) { fine64_apply_dot(P, s, x, y, nullptr, nullptr, nullptr); };
+  auto Sapply = [&](const double* x, double* y) {
+    stress_stiffness_apply(s, P->dim, P->nx, P->ny, P->nz, P->nu, sig.p, P->mask.p, x, y);
+  };
+  auto dot = [&](const double* a, const double* b) {
+    double v = 0.0;
+    host_dots(s, n, 1, a, n, b, parts.p, hd.p, &v);
+    return v;
+  };
+  std::vector<double> Hp((size_t)jmax * jmax, 0.0), h(jmax + 1), c(jmax + 1);
+  int j = 0;
+  // K-orthonormalise z against V (classical Gram-Schmidt twice) and append it
+  auto add_vector = [&]() -> bool {
+    const double n0 = std::sqrt(dot(z.p, z.p));
+    for (int pass = 0; pass < 2 && j > 0; pass++) {
+      multi_dot(s, n, j, KV.p, n, z.p, parts.p, hd.p);
+      multi_update(s, n, j, V.p, n, hd.p, -1.0, z.p);
+    }
+    if (!(std::sqrt(dot(z.p, z.p)) > 1e-10 * n0)) return false;
+    Kapply(z.p, Kz.p);
+    const double nz = std::sqrt(std::max(dot(z.p, Kz.p), 0.0));
+    if (!(nz > 0.0)) return false;
+    scale_into(s, n, z.p, 1.0 / nz, V.p + (int64_t)j * n);
+    scale_into(s, n, Kz.p, 1.0 / nz, KV.p + (int64_t)j * n);
+    Sapply(V.p + (int64_t)j * n, SV.p + (int64_t)j * n);
+    host_dots(s, n, j + 1, V.p, n, SV.p + (int64_t)j * n, parts.p, hd.p, h.data());
+    for (int i = 0; i <= j; i++) Hp[(size_t)i * jmax + j] = Hp[(size_t)j * jmax + i] = h[i];
+    j++;
+    return true;
+  };
+  // out = sum_k coef[k] M_k over the first j columns of M (device coefficients through cd)
+  auto combine = [&](const double* M, const double* coef, double sign, double* out, bool zero) {
+    CK(cudaMemcpyAsync(cd.p, coef, sizeof(double) * j, cudaMemcpyHostToDevice, s));
+    if (zero) CK(cudaMemsetAsync(out, 0, n * 8, s));
+    multi_update(s, n, j, M, n, cd.p, sign, out);
+    CK(cudaStreamSynchronize(s));  // coef is a host vector the caller may reuse
+  };
+  for (int k = 0; k < jmin; k++) {
+    splitmix_uniform(s, n, 1000 + k, z.p);
+    add_vector();
+  }
+  int it = 0, status = TOMG_NOT_CONVERGED;
+  std::vector<double> th, Q, Hw;
+  int k = 0;
+  while (true) {
+    Hw.assign((size_t)j * j, 0.0);
+    for (int a = 0; a < j; a++)
+      for (int b = 0; b < j; b++) Hw[(size_t)a * j + b] = Hp[(size_t)a * jmax + b];
+    sym_eig(j, Hw, th, Q);
+    k = std::min(n_eig, j);
+    int t = -1;
+    for (int i = 0; i < k && t < 0; i++) {
+      for (int a = 0; a < j; a++) c[a] = Q[(size_t)a * j + i];
+      combine(SV.p, c.data(), 1.0, r.p, true);
+      combine(KV.p, c.data(), -th[i], r.p, false);
+      combine(KV.p, c.data(), 1.0, q.p, true);
+      const double nr = std::sqrt(dot(r.p, r.p)), nq = std::sqrt(dot(q.p, q.p));
+      if (!std::isfinite(nr)) { status = TOMG_E_BREAKDOWN; break; }
+      if (!(nr <= tol * std::fabs(th[i]) * nq)) t = i;
+    }
+    if (status == TOMG_E_BREAKDOWN) break;
+    if (t < 0) { status = TOMG_OK; break; }
+    if (it >= max_iter) break;
+    if (j >= jmax) {
+      // restart from the j_min best Ritz vectors (V^T K_sigma V becomes diagonal)
+      for (DBuf<double>* M : {&V, &KV, &SV}) {
+        for (int cc = 0; cc < jmin; cc++) {
+          for (int a = 0; a < j; a++) c[a] = Q[(size_t)a * j + cc];
+          combine(M->p, c.data(), 1.0, tmp.p + (int64_t)cc * n, true);
+        }
+        CK(cudaMemcpyAsync(M->p, tmp.p, (size_t)jmin * n * 8, cudaMemcpyDeviceToDevice, s));
+      }
+      std::fill(Hp.begin(), Hp.end(), 0.0);
+      for (int a = 0; a < jmin; a++) Hp[(size_t)a * jmax + a] = th[a];
+      j = jmin;
+    }
+    precondition(P, W, r.p, z.p);
+    it++;
+    add_vector();
+  }
+  for (int i = 0; i < k; i++) lambdas[i] = th[i];
+  if (modes) {
+    for (int i = 0; i < k; i++) {
+      for (int a = 0; a < j; a++) c[a] = Q[(size_t)a * j + i];
+      combine(V.p, c.data(), 1.0, q.p, true);
+      CK(cudaMemcpyAsync(modes + (int64_t)i * n, q.p, n * 8,
+                         on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost, s));
+    }
+  }
+  CK(cudaStreamSynchronize(s));
+  join_from(P, W);
+  if (iterations) *iterations = it;
+  if (status == TOMG_NOT_CONVERGED) set_error("Davidson not converged after %d iterations", it);
+  if (status == TOMG_E_BREAKDOWN) set_error("Davidson breakdown (non-finite residual)");
+  return (tomg_status)status;
+}
+
+// ----------------------------------------------------------------------------------------
 void level_apply(tomg_problem* P, int level, int prec, const double* x, double* y) {
   if (!P->setup_valid) TOMG_THROW(TOMG_E_INVALID, "no valid setup");
   if (level < 0 || level >= (int)P->L.size()) TOMG_THROW(TOMG_E_INVALID, "bad level %d", level);

@@ -87,6 +87,9 @@ _SIGS = {
     "tomg_adaptive_geo_levels": (C.c_int, [_P, C.POINTER(C.c_int)]),
     "tomg_density_filter": (C.c_int, [_P, C.c_double, C.c_int, _P, _P, C.c_int]),
     "tomg_compliance_sensitivity": (C.c_int, [_P, _P, _P, C.c_int]),
+    "tomg_stress_stiffness_apply": (C.c_int, [_P, _P, _P, _P, C.c_int]),
+    "tomg_buckling": (C.c_int, [_P, _P, C.c_int, C.c_int, C.c_int, C.c_double, C.c_int, _P, _P,
+                                C.c_int, C.POINTER(C.c_int)]),
     "tomg_server_create": (C.c_int, [_P, C.c_size_t, C.c_int, C.POINTER(_P)]),
     "tomg_server_submit": (C.c_int, [_P, _P, _P, C.c_int, _P, _P, C.POINTER(Options),
                                      C.POINTER(C.c_uint64)]),
@@ -360,6 +363,31 @@ class Problem:
             dst = C.c_void_p(out.ctypes.data)
         _check(load().tomg_compliance_sensitivity(self.h, src, dst, dev))
         return out
+
+    def stress_stiffness_apply(self, u, x):
+        """y = K_sigma(u) x (host arrays)."""
+        uu = np.ascontiguousarray(u, dtype=np.float64).reshape(-1)
+        xx = np.ascontiguousarray(x, dtype=np.float64).reshape(-1)
+        y = np.zeros(self.n)
+        _check(load().tomg_stress_stiffness_apply(self.h, C.c_void_p(uu.ctypes.data),
+                                                  C.c_void_p(xx.ctypes.data),
+                                                  C.c_void_p(y.ctypes.data), 0))
+        return y
+
+    def buckling(self, u, n_eig=6, j_min=10, j_max=25, tol=1e-6, max_iter=1000, modes=False):
+        """The n_eig largest eigenvalues of K_sigma Phi = lambda K Phi (and the K-orthonormal
+        modes, n_eig x n_dofs, if requested) by generalized Davidson.  Returns
+        (lambdas, modes or None, iterations, status)."""
+        uu = np.ascontiguousarray(u, dtype=np.float64).reshape(-1)
+        lam = np.zeros(n_eig)
+        Phi = np.zeros((n_eig, self.n)) if modes else None
+        it = C.c_int()
+        st = load().tomg_buckling(self.h, C.c_void_p(uu.ctypes.data), n_eig, j_min, j_max,
+                                  float(tol), max_iter, C.c_void_p(lam.ctypes.data),
+                                  C.c_void_p(Phi.ctypes.data) if modes else None, 0,
+                                  C.byref(it))
+        _check(st)
+        return lam, Phi, it.value, st
 
     def fine_apply_f32_noalloc(self, x, y):
         """y = A_0 x in FP32 arithmetic without any device allocation (x, y: contiguous float64

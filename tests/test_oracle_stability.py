@@ -104,3 +104,19 @@ def test_davidson_matches_dense(precond):
     assert np.allclose(Phi.T @ (A0 @ Phi), np.eye(6), atol=1e-8)
     if precond == "direct":
         assert it < 200
+
+
+def test_column_buckling_load_matches_euler():
+    """A slender solid fixed-free column under an end load buckles at Euler's
+    P_cr = pi^2 E I / (4 L^2) (I = width^3 / 12 per unit thickness, E = 1): 1 / lambda_max must
+    come within a few per cent (the FE column is not perfectly slender; shear and the discrete
+    bending stiffness of one element row account for the rest)."""
+    nx, ny = 8, 64
+    p = W.column_2d(nx, ny)
+    A0 = mg.fine_operator(p)
+    u = solve.direct(p)["u"][0]
+    Ks = stability.stress_stiffness(p, u)
+    H = solve.build(p, pc="gmg", n_levels=3)
+    th, _, _, _ = stability.davidson(Ks, A0, M=lambda v: mg.vcycle(H, v), n_eig=2, tol=1e-8)
+    pcr = np.pi ** 2 * nx ** 3 / 12.0 / (4.0 * ny ** 2)
+    assert 1.0 / th[0] == pytest.approx(pcr, rel=0.05)
