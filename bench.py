@@ -265,6 +265,7 @@ def run_gpu(args, rank, world, local):
     if not args.no_fp64:
         out["fgmres"] = fgmres_run(P, opts, rho_d, f_d, u_d, stream)
         out["design_iteration"] = design_run(P, opts, p, rho_d, f_d, stream)
+        out["stability"] = stability_run(tomg, ctx, opts)
     if args.serving > 0:
         out["serving"] = serving_run(tomg, ctx, args.serving, args.serving_updates, args.slots)
     if args.batched:
@@ -332,6 +333,47 @@ def design_run(P, opts, p, rho_d, f_d, stream, iters=5):
             "sensitivity_sum": float(da.sum().item())}
 
 
+def stability_run(tomg, ctx, opts, nx=256, ny=1024):
+    """The stability problem's linear solves on the paper's 2D column (256 x 1024 quad4, about
+    526k DOFs; seeded smoothed density in [0.1, 1]): setup, the displacement solve, the six
+    largest buckling eigenpairs by generalized Davidson (j_min 10, j_max 25, tol 1e-6, the
+    V-cycle as preconditioner) and six adjoint-like solves with seeded right-hand sides on
+    concurrent slots (the adjoint load formula itself is not built)."""
+    import torch
+    import workloads as W
+    p = W.column_2d(nx, ny, seed=0)
+    P = tomg.Problem.from_workload(ctx, p)
+    o = dict(opts, concurrency=6)
+    rng = np.random.default_rng(9)
+    free = np.ones(p.n)
+    free[p.fixed] = 0.0
+    adj = rng.standard_normal((6, p.n)) * free
+    adj /= np.linalg.norm(adj, axis=1, keepdims=True)
+    phases = {"setup": [], "solve": [], "davidson": [], "adjoint_solves": []}
+    for k in range(3):
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        P.setup(prec="fp32", **o)
+        t1 = time.perf_counter()
+        u, res = P.solve(p.f)
+        t2 = time.perf_counter()
+        lam, _, it, st = P.buckling(u[0], n_eig=6, tol=1e-6)
+        t3 = time.perf_counter()
+        _, ra = P.solve(adj)
+        t4 = time.perf_counter()
+        if k:
+            for name, a, b in (("setup", t0, t1), ("solve", t1, t2), ("davidson", t2, t3),
+                               ("adjoint_solves", t3, t4)):
+                phases[name].append(1e3 * (b - a))
+    return {"workload": "2D column quad4 %dx%d (%d DOFs), bottom clamped, unit load on top" %
+                        (nx, ny, p.n),
+            "ms": {k: statistics.median(v) for k, v in phases.items()},
+            "lambdas": [float(x) for x in lam], "davidson_iterations": it, "davidson_status": st,
+            "solve_iterations": res[0]["iterations"],
+            "adjoint_iterations": [r["iterations"] for r in ra],
+            "timing": "host clock per phase (each call synchronises)"}
+
+
 def batched_run(tomg, ctx, slots, reps=3, prec="tf32x3", smoother="jacobi", cheb_degree=2):
     """The 16 right-hand sides (8 point loads, 8 adjoint-like vectors) of the 3D hex8 128x64x64
     case (1,635,075 DOFs) on one shared hierarchy: all 16 on `slots` concurrent solve slots,
@@ -384,7 +426,7 @@ def serving_run(tomg, ctx, n_requests, n_updates, slots):
     request's arrival time and warm-starts from the previous one on the device."""
     import workloads as W
     stream = W.serving_stream(n_requests=n_requests, n_updates=n_updates)
-    opt = dict(pc="hybrid", prec="fp32", n_geo_levels=3, max_coarse_dofs=1000, concurrency=1,
+    opt = dict(pc="hybrid", prec="tf32x3", n_geo_levels=3, max_coarse_dofs=1000, concurrency=1,
                max_iter=2000)
     probs = []
     for r in stream:

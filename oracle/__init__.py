@@ -16,6 +16,8 @@ Modules
   mg       V-cycle (Algorithm 1) with point-block Jacobi or Chebyshev smoothing and a dense
            Cholesky coarse solve; hierarchy builders for GMG / AMG / hybrid
   design   linear density filter rho = S alpha and the compliance sensitivities (Eq. 3)
+  stability  stress stiffness matrix (Eq. 4-5) and the generalized Davidson eigensolver
+           (Algorithm 2)
   krylov   textbook preconditioned CG and flexible CG
   solve    one call that mirrors the library's solve options
   hashing  splitmix64, the counter-based generator both sides implement from its published

@@ -20,8 +20,9 @@ is reset to the j_min best Ritz vectors when it reaches j_max.  The paper's sett
 j_min = 10, j_max = 25, six modes.  Start vectors: splitmix64 uniform vectors.
 
 Parity: pinned (tests/test_oracle_stability.py: L_ij against exact rational integration,
-symmetry and the translation null space of K_sigma, the 1D-like stress of a uniformly
-compressed bar, Davidson eigenvalues against dense scipy.linalg.eigh on small grids).
+symmetry and the translation null space of K_sigma, the stresses of constant-strain fields,
+Davidson eigenvalues against dense scipy.linalg.eigh on small grids, the critical load of a
+slender fixed-free column against Euler's formula).
 """
 from __future__ import annotations
 
