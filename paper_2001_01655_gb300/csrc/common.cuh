@@ -59,6 +59,14 @@ __device__ __forceinline__ void pdl_prologue() {
   asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
   asm volatile("griddepcontrol.wait;" ::: "memory");
 }
+// The two halves of pdl_prologue, for kernels that first fetch data no kernel of the solve
+// loop writes (operator values, structure, smoother blocks: fixed between setups), so those
+// loads overlap the predecessor's tail; everything produced by the loop is read after
+// pdl_wait().  Without programmatic serialisation the wait returns at once.
+__device__ __forceinline__ void pdl_launch() {
+  asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
+}
+__device__ __forceinline__ void pdl_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
 
 #define LAUNCH(kernel, grid, block, smem, strm_, ...)                                   \
   do {                                                                                 \

@@ -32,16 +32,54 @@ __global__ void __launch_bounds__(256) k_bsr(int nbr, const int* __restrict__ rp
                                              const T* __restrict__ b, const T* __restrict__ Dinv,
                                              T omega, const int* done, T* __restrict__ xo, T c1,
                                              int dmode) {
-  pdl_prologue();
-  if (solve_done(done)) return;
+  // operator data is fixed during a solve: the row bounds, this lane's first block and (small
+  // blocks) the diagonal inverse are fetched before waiting for the producer of x and b
+  constexpr bool PRE = B <= 3;
+  constexpr bool NEED_D = MODE == MODE_JACOBI || MODE == MODE_CHEB;
+  pdl_launch();
   const int gtid = blockIdx.x * blockDim.x + threadIdx.x;
   const int i = gtid / G, sub = gtid % G;
   const bool live = i < nbr;
+  int p = 0, pend = 0, j0 = 0;
+  T blk0[PRE ? B * B : 1];
+  T Dl[PRE && NEED_D ? B * B : 1];
+  if (PRE && live) {
+    p = rp[i] + sub;
+    pend = rp[i + 1];
+    if (p < pend) {
+      j0 = ci[p];
+#pragma unroll
+      for (int t = 0; t < B * B; t++) blk0[t] = V[(int64_t)p * B * B + t];
+    }
+    if (NEED_D && sub == 0) {
+#pragma unroll
+      for (int t = 0; t < B * B; t++) Dl[t] = Dinv[(int64_t)B * B * i + t];
+    }
+  }
+  pdl_wait();
+  if (solve_done(done)) return;
   T acc[B];
 #pragma unroll
   for (int r = 0; r < B; r++) acc[r] = T(0);
   if (live) {
-    for (int p = rp[i] + sub; p < rp[i + 1]; p += G) {
+    if (!PRE) {
+      p = rp[i] + sub;
+      pend = rp[i + 1];
+    } else if (p < pend) {
+      T xv[B];
+      if (MODE == MODE_RESID0) {
+        jacobi_first<T, B>(Dinv, b, j0, omega, xv);
+      } else {
+#pragma unroll
+        for (int c = 0; c < B; c++) xv[c] = x[(int64_t)B * j0 + c];
+      }
+#pragma unroll
+      for (int r = 0; r < B; r++)
+#pragma unroll
+        for (int c = 0; c < B; c++) acc[r] += blk0[r * B + c] * xv[c];
+      p += G;
+    }
+    for (; p < pend; p += G) {
       const int j = ci[p];
       const T* blk = V + (int64_t)p * B * B;
       T xv[B];
@@ -73,25 +111,28 @@ __global__ void __launch_bounds__(256) k_bsr(int nbr, const int* __restrict__ rp
   } else if (MODE == MODE_RESID) {
 #pragma unroll
     for (int r = 0; r < B; r++) y[(int64_t)B * i + r] = b[(int64_t)B * i + r] - acc[r];
-  } else if (MODE == MODE_CHEB) {
-    T res[B], xi[B];
+  } else {
+    T res[B], xi[B], D[B * B];
 #pragma unroll
     for (int r = 0; r < B; r++) {
       res[r] = b[(int64_t)B * i + r] - acc[r];
       xi[r] = x[(int64_t)B * i + r];
     }
-    cheb_node<T, B>(i, res, xi, Dinv, c1, omega, dmode, xo, y);
-  } else {
-    T res[B];
 #pragma unroll
-    for (int r = 0; r < B; r++) res[r] = b[(int64_t)B * i + r] - acc[r];
-    const T* D = Dinv + (int64_t)B * B * i;
+    for (int t = 0; t < B * B; t++) D[t] = PRE ? Dl[PRE && NEED_D ? t : 0] : Dinv[(int64_t)B * B * i + t];
 #pragma unroll
     for (int r = 0; r < B; r++) {
       T v = T(0);
 #pragma unroll
       for (int c = 0; c < B; c++) v += D[r * B + c] * res[c];
-      y[(int64_t)B * i + r] = x[(int64_t)B * i + r] + omega * v;
+      if (MODE == MODE_CHEB) {
+        const T prev = dmode == 2 ? xi[r] : (dmode == 1 ? xo[(int64_t)B * i + r] : T(0));
+        const T dn = c1 * prev + omega * v;
+        y[(int64_t)B * i + r] = xi[r] + dn;
+        xo[(int64_t)B * i + r] = dn;
+      } else {
+        y[(int64_t)B * i + r] = xi[r] + omega * v;
+      }
     }
   }
 }
@@ -102,16 +143,36 @@ __global__ void __launch_bounds__(256) k_bsr_rect(int nbr, const int* __restrict
                                                   const T* __restrict__ V, const T* __restrict__ x,
                                                   T* __restrict__ y, int accumulate,
                                                   const int* done) {
-  pdl_prologue();
-  if (solve_done(done)) return;
+  // the transfer operator is fixed during a solve: row bounds and this lane's first block are
+  // fetched before waiting for the producer of x
+  pdl_launch();
   const int gtid = blockIdx.x * blockDim.x + threadIdx.x;
   const int i = gtid / G, sub = gtid % G;
   const bool live = i < nbr;
+  int p = 0, pend = 0, j0 = 0;
+  T blk0[BR * BC];
+  if (live) {
+    p = rp[i] + sub;
+    pend = rp[i + 1];
+    if (p < pend) {
+      j0 = ci[p];
+#pragma unroll
+      for (int t = 0; t < BR * BC; t++) blk0[t] = V[(int64_t)p * BR * BC + t];
+    }
+  }
+  pdl_wait();
+  if (solve_done(done)) return;
   T acc[BR];
 #pragma unroll
   for (int r = 0; r < BR; r++) acc[r] = T(0);
-  if (live) {
-    for (int p = rp[i] + sub; p < rp[i + 1]; p += G) {
+  if (live && p < pend) {
+#pragma unroll
+    for (int c = 0; c < BC; c++) {
+      const T xv = x[(int64_t)BC * j0 + c];
+#pragma unroll
+      for (int r = 0; r < BR; r++) acc[r] += blk0[r * BC + c] * xv;
+    }
+    for (p += G; p < pend; p += G) {
       const int j = ci[p];
       const T* blk = V + (int64_t)p * BR * BC;
 #pragma unroll

@@ -162,11 +162,14 @@ __global__ void k_mask_vec(const double* __restrict__ f, double* __restrict__ b,
 template <class T, int B>
 __global__ void k_jacobi0(int64_t nodes, const T* __restrict__ Dinv, const T* __restrict__ b,
                           T* __restrict__ x, T omega, const int* done) {
-  pdl_prologue();
-  if (solve_done(done)) return;
+  pdl_launch();
   const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= nodes) return;
-  const T* D = Dinv + (int64_t)B * B * i;
+  T D[B * B];  // the smoother block is fixed during a solve: fetched before the wait
+#pragma unroll
+  for (int t = 0; t < B * B; t++) D[t] = Dinv[(int64_t)B * B * i + t];
+  pdl_wait();
+  if (solve_done(done)) return;
   T bv[B];
 #pragma unroll
   for (int c = 0; c < B; c++) bv[c] = b[B * i + c];
@@ -217,13 +220,28 @@ __global__ void k_scale_into(int64_t n, const double* __restrict__ w, double s, 
 template <class T>
 __global__ void k_gemv(int n, const T* __restrict__ A, const T* __restrict__ b, T* __restrict__ x,
                        const int* done) {
-  pdl_prologue();
-  if (solve_done(done)) return;
+  // the coarse inverse is fixed during a solve: each lane fetches its first PF entries of the
+  // row before waiting for the producer of b
+  constexpr int PF = 24;
+  pdl_launch();
   const int row = (blockIdx.x * blockDim.x + threadIdx.x) >> 5, lane = threadIdx.x & 31;
   if (row >= n) return;
-  T s = T(0);
   const T* a = A + (int64_t)row * n;
-  for (int c = lane; c < n; c += 32) s += a[c] * b[c];
+  T ap[PF];
+#pragma unroll
+  for (int k = 0; k < PF; k++) {
+    const int c = lane + 32 * k;
+    ap[k] = c < n ? a[c] : T(0);
+  }
+  pdl_wait();
+  if (solve_done(done)) return;
+  T s = T(0);
+#pragma unroll
+  for (int k = 0; k < PF; k++) {
+    const int c = lane + 32 * k;
+    if (c < n) s += ap[k] * b[c];
+  }
+  for (int c = lane + 32 * PF; c < n; c += 32) s += a[c] * b[c];
   for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
   if (lane == 0) x[row] = s;
 }
