@@ -44,13 +44,14 @@ __global__ void __launch_bounds__(BX * BY) k_ebe2(int nx, int ny, const KeP2<T> 
   __shared__ V2 sx[TH + 2][BX + 2];
   __shared__ T sE[TH + 1][BX + 1];
   __shared__ double red[BX * BY / 32];
-  pdl_prologue();
-  if (solve_done(done)) return;
+  pdl_launch();
   const int tid = threadIdx.y * BX + threadIdx.x;
   const int i0 = blockIdx.x * BX, j0 = blockIdx.y * TH;
   const int W = nx + 1;
   // staging: issue every global load of this thread first (independent, all in flight at
-  // once), then write shared memory, so the tile costs one memory latency, not several
+  // once), then write shared memory, so the tile costs one memory latency, not several.  The
+  // mask and the moduli are fixed during a solve and are fetched before the wait for the
+  // producer of x (b and the smoother blocks for the fused first sweep).
   constexpr int NXL = ((TH + 2) * (BX + 2) + BX * BY - 1) / (BX * BY);
   constexpr int NEL = ((TH + 1) * (BX + 1) + BX * BY - 1) / (BX * BY);
   V2 xv[NXL];
@@ -61,23 +62,9 @@ __global__ void __launch_bounds__(BX * BY) k_ebe2(int nx, int ny, const KeP2<T> 
     const int t = tid + k * BX * BY;
     const int ly = t / (BX + 2), lx = t - ly * (BX + 2);
     const int gi = i0 - 1 + lx, gj = j0 - 1 + ly;
-    xv[k].x = T(0);
-    xv[k].y = T(0);
-    mv[k] = 3u;
-    if (t < (TH + 2) * (BX + 2) && gi >= 0 && gi <= nx && gj >= 0 && gj <= ny) {
-      const int node = gj * W + gi;
-      mv[k] = __ldg(mask + node);
-      if (MODE == MODE_RESID0) {
-        // x = w Dinv b of the first sweep, formed where it is needed
-        const V2 bv = __ldg(reinterpret_cast<const V2*>(b) + node);
-        const V2 d01 = __ldg(reinterpret_cast<const V2*>(Dinv) + 2 * node);
-        const V2 d23 = __ldg(reinterpret_cast<const V2*>(Dinv) + 2 * node + 1);
-        xv[k].x = omega * (d01.x * bv.x + d01.y * bv.y);
-        xv[k].y = omega * (d23.x * bv.x + d23.y * bv.y);
-      } else {
-        xv[k] = __ldg(reinterpret_cast<const V2*>(x) + node);
-      }
-    }
+    mv[k] = 3u | 4u;  // bit 2: outside the tile or the grid
+    if (t < (TH + 2) * (BX + 2) && gi >= 0 && gi <= nx && gj >= 0 && gj <= ny)
+      mv[k] = __ldg(mask + gj * W + gi);
   }
 #pragma unroll
   for (int k = 0; k < NEL; k++) {
@@ -86,6 +73,28 @@ __global__ void __launch_bounds__(BX * BY) k_ebe2(int nx, int ny, const KeP2<T> 
     const int ge = i0 - 1 + lx, gf = j0 - 1 + ly;
     evv[k] = (t < (TH + 1) * (BX + 1) && ge >= 0 && ge < nx && gf >= 0 && gf < ny)
                  ? __ldg(E + gf * nx + ge) : T(0);
+  }
+  pdl_wait();
+  if (solve_done(done)) return;
+#pragma unroll
+  for (int k = 0; k < NXL; k++) {
+    const int t = tid + k * BX * BY;
+    const int ly = t / (BX + 2), lx = t - ly * (BX + 2);
+    const int node = (j0 - 1 + ly) * W + i0 - 1 + lx;
+    xv[k].x = T(0);
+    xv[k].y = T(0);
+    if (!(mv[k] & 4u)) {
+      if (MODE == MODE_RESID0) {
+        // x = w Dinv b of the first sweep, formed where it is needed
+        const V2 bv = reinterpret_cast<const V2*>(b)[node];
+        const V2 d01 = __ldg(reinterpret_cast<const V2*>(Dinv) + 2 * node);
+        const V2 d23 = __ldg(reinterpret_cast<const V2*>(Dinv) + 2 * node + 1);
+        xv[k].x = omega * (d01.x * bv.x + d01.y * bv.y);
+        xv[k].y = omega * (d23.x * bv.x + d23.y * bv.y);
+      } else {
+        xv[k] = reinterpret_cast<const V2*>(x)[node];
+      }
+    }
   }
 #pragma unroll
   for (int k = 0; k < NXL; k++) {

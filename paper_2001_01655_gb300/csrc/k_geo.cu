@@ -34,11 +34,20 @@ __global__ void __launch_bounds__(256) k_stencil(int nx, int ny, int nz, const T
                                                  const int* done, T* __restrict__ xo, T c1,
                                                  int dmode) {
   constexpr int NO = (DIM == 3) ? 27 : 9, BB = DIM * DIM;
-  pdl_prologue();
-  if (solve_done(done)) return;
+  // 2D: the node's stencil row (fixed during a solve) is fetched before the wait for the
+  // producer of x and b; 3D rows (243 values) are read as they are used
+  constexpr bool PRE = DIM == 2;
+  pdl_launch();
   const int64_t nn = (int64_t)(nx + 1) * (ny + 1) * (DIM == 3 ? nz + 1 : 1);
   const int64_t node = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (node >= nn) return;
+  T Sr[PRE ? NO * BB : 1];
+  if (PRE) {
+#pragma unroll
+    for (int t = 0; t < NO * BB; t++) Sr[t] = S[(int64_t)t * nn + node];
+  }
+  pdl_wait();
+  if (solve_done(done)) return;
   int i, j, k;
   node_ijk(node, nx, ny, DIM, i, j, k);
   T acc[DIM];
@@ -59,7 +68,9 @@ __global__ void __launch_bounds__(256) k_stencil(int nx, int ny, int nz, const T
 #pragma unroll
     for (int r = 0; r < DIM; r++)
 #pragma unroll
-      for (int c = 0; c < DIM; c++) acc[r] += S[((int64_t)o * BB + r * DIM + c) * nn + node] * xv[c];
+      for (int c = 0; c < DIM; c++)
+        acc[r] += (PRE ? Sr[PRE ? o * BB + r * DIM + c : 0]
+                       : S[((int64_t)o * BB + r * DIM + c) * nn + node]) * xv[c];
   }
   if (MODE == MODE_RESID0) {
     T xi[DIM];
