@@ -31,11 +31,11 @@ __global__ void __launch_bounds__(256) k_bsr(int nbr, const int* __restrict__ rp
                                              const T* __restrict__ x, T* __restrict__ y,
                                              const T* __restrict__ b, const T* __restrict__ Dinv,
                                              T omega, const int* done, T* __restrict__ xo, T c1,
-                                             int dmode) {
+                                             int dmode, T w0) {
   // operator data is fixed during a solve: the row bounds, this lane's first block and (small
   // blocks) the diagonal inverse are fetched before waiting for the producer of x and b
   constexpr bool PRE = B <= 3;
-  constexpr bool NEED_D = MODE == MODE_JACOBI || MODE == MODE_CHEB;
+  constexpr bool NEED_D = MODE == MODE_JACOBI || MODE == MODE_CHEB || MODE == MODE_CHEB0;
   pdl_launch();
   const int gtid = blockIdx.x * blockDim.x + threadIdx.x;
   const int i = gtid / G, sub = gtid % G;
@@ -69,6 +69,8 @@ __global__ void __launch_bounds__(256) k_bsr(int nbr, const int* __restrict__ rp
       T xv[B];
       if (MODE == MODE_RESID0) {
         jacobi_first<T, B>(Dinv, b, j0, omega, xv);
+      } else if (MODE == MODE_CHEB0) {
+        jacobi_first<T, B>(Dinv, b, j0, w0, xv);
       } else {
 #pragma unroll
         for (int c = 0; c < B; c++) xv[c] = x[(int64_t)B * j0 + c];
@@ -85,6 +87,8 @@ __global__ void __launch_bounds__(256) k_bsr(int nbr, const int* __restrict__ rp
       T xv[B];
       if (MODE == MODE_RESID0) {
         jacobi_first<T, B>(Dinv, b, j, omega, xv);
+      } else if (MODE == MODE_CHEB0) {
+        jacobi_first<T, B>(Dinv, b, j, w0, xv);
       } else {
 #pragma unroll
         for (int c = 0; c < B; c++) xv[c] = x[(int64_t)B * j + c];
@@ -113,10 +117,11 @@ __global__ void __launch_bounds__(256) k_bsr(int nbr, const int* __restrict__ rp
     for (int r = 0; r < B; r++) y[(int64_t)B * i + r] = b[(int64_t)B * i + r] - acc[r];
   } else {
     T res[B], xi[B], D[B * B];
+    if (MODE == MODE_CHEB0) jacobi_first<T, B>(Dinv, b, i, w0, xi);
 #pragma unroll
     for (int r = 0; r < B; r++) {
       res[r] = b[(int64_t)B * i + r] - acc[r];
-      xi[r] = x[(int64_t)B * i + r];
+      if (MODE != MODE_CHEB0) xi[r] = x[(int64_t)B * i + r];
     }
 #pragma unroll
     for (int t = 0; t < B * B; t++) D[t] = PRE ? Dl[PRE && NEED_D ? t : 0] : Dinv[(int64_t)B * B * i + t];
@@ -125,8 +130,9 @@ __global__ void __launch_bounds__(256) k_bsr(int nbr, const int* __restrict__ rp
       T v = T(0);
 #pragma unroll
       for (int c = 0; c < B; c++) v += D[r * B + c] * res[c];
-      if (MODE == MODE_CHEB) {
-        const T prev = dmode == 2 ? xi[r] : (dmode == 1 ? xo[(int64_t)B * i + r] : T(0));
+      if (MODE == MODE_CHEB || MODE == MODE_CHEB0) {
+        const int dmo = MODE == MODE_CHEB0 ? 2 : dmode;
+        const T prev = dmo == 2 ? xi[r] : (dmo == 1 ? xo[(int64_t)B * i + r] : T(0));
         const T dn = c1 * prev + omega * v;
         y[(int64_t)B * i + r] = xi[r] + dn;
         xo[(int64_t)B * i + r] = dn;
@@ -507,11 +513,13 @@ void bsr_op(cudaStream_t s, int mode, const Bsr& A, const T* V, const T* x, T* y
             const T* Dinv, double omega, const int* done, const ChebArg* ch) {
   const int G = lanes_for(A);
   const int grid = ceil_div((int64_t)A.nbr * G, 256);
-  if (mode == MODE_CHEB && !ch) TOMG_THROW(TOMG_E_INVALID, "Chebyshev step without its state");
-  T* xo = mode == MODE_RESID0 ? const_cast<T*>(x) : (mode == MODE_CHEB ? (T*)ch->d : nullptr);
-  const T c1 = mode == MODE_CHEB ? (T)ch->c1 : T(0);
-  const int dm = mode == MODE_CHEB ? ch->dmode : 0;
-#define BOP(B, M, GG) LAUNCH((k_bsr<T, B, M, GG>), grid, 256, 0, s, A.nbr, A.rp, A.ci, V, x, y, b, Dinv, (T)omega, done, xo, c1, dm)
+  const bool cheb = mode == MODE_CHEB || mode == MODE_CHEB0;
+  if (cheb && !ch) TOMG_THROW(TOMG_E_INVALID, "Chebyshev step without its state");
+  T* xo = mode == MODE_RESID0 ? const_cast<T*>(x) : (cheb ? (T*)ch->d : nullptr);
+  const T c1 = cheb ? (T)ch->c1 : T(0);
+  const int dm = cheb ? ch->dmode : 0;
+  const T w0 = cheb ? (T)ch->w0 : T(0);
+#define BOP(B, M, GG) LAUNCH((k_bsr<T, B, M, GG>), grid, 256, 0, s, A.nbr, A.rp, A.ci, V, x, y, b, Dinv, (T)omega, done, xo, c1, dm, w0)
 #define BG(B, M)                         \
   if (G == 4) BOP(B, M, 4);              \
   else if (G == 8) BOP(B, M, 8);         \
@@ -522,6 +530,7 @@ void bsr_op(cudaStream_t s, int mode, const Bsr& A, const T* V, const T* x, T* y
   else if (mode == MODE_RESID) { BG(B, MODE_RESID) } \
   else if (mode == MODE_RESID0) { BG(B, MODE_RESID0) } \
   else if (mode == MODE_CHEB) { BG(B, MODE_CHEB) } \
+  else if (mode == MODE_CHEB0) { BG(B, MODE_CHEB0) } \
   else { BG(B, MODE_JACOBI) }
   if (A.br == 2) { BMODES(2) }
   else if (A.br == 3) { BMODES(3) }

@@ -245,6 +245,11 @@ void ebe_op(cudaStream_t s, int mode, const Ebe& op, const T* x, T* y, const T* 
     else launch_ebe<T, 3, MODE_CHEB, false>(s, op, x, y, b, Dinv, omega, done, parts, ch);
     return;
   }
+  if (mode == MODE_CHEB0) {
+    if (op.dim != 2) TOMG_THROW(TOMG_E_INVALID, "fused first Chebyshev steps on quad4 only");
+    ebe2d_launch<T, MODE_CHEB0, false>(s, op, x, y, b, Dinv, omega, done, parts, ch);
+    return;
+  }
   if (op.dim == 2) {
     if (mode == MODE_APPLY) {
       if (parts) launch_ebe<T, 2, MODE_APPLY, true>(s, op, x, y, b, Dinv, omega, done, parts);

@@ -38,7 +38,7 @@ __global__ void __launch_bounds__(BX * BY) k_ebe2(int nx, int ny, const KeP2<T> 
                                                   const T* __restrict__ b,
                                                   const T* __restrict__ Dinv, T omega,
                                                   const int* done, double* partials,
-                                                  T* __restrict__ xo, T c1, int dmode) {
+                                                  T* __restrict__ xo, T c1, int dmode, T w0) {
   using V2 = typename V2t<T>::type;
   constexpr int TH = BY * NPT;
   __shared__ V2 sx[TH + 2][BX + 2];
@@ -84,13 +84,14 @@ __global__ void __launch_bounds__(BX * BY) k_ebe2(int nx, int ny, const KeP2<T> 
     xv[k].x = T(0);
     xv[k].y = T(0);
     if (!(mv[k] & 4u)) {
-      if (MODE == MODE_RESID0) {
+      if (MODE == MODE_RESID0 || MODE == MODE_CHEB0) {
         // x = w Dinv b of the first sweep, formed where it is needed
+        const T wf = MODE == MODE_CHEB0 ? w0 : omega;
         const V2 bv = reinterpret_cast<const V2*>(b)[node];
         const V2 d01 = __ldg(reinterpret_cast<const V2*>(Dinv) + 2 * node);
         const V2 d23 = __ldg(reinterpret_cast<const V2*>(Dinv) + 2 * node + 1);
-        xv[k].x = omega * (d01.x * bv.x + d01.y * bv.y);
-        xv[k].y = omega * (d23.x * bv.x + d23.y * bv.y);
+        xv[k].x = wf * (d01.x * bv.x + d01.y * bv.y);
+        xv[k].y = wf * (d23.x * bv.x + d23.y * bv.y);
       } else {
         xv[k] = reinterpret_cast<const V2*>(x)[node];
       }
@@ -163,13 +164,14 @@ __global__ void __launch_bounds__(BX * BY) k_ebe2(int nx, int ny, const KeP2<T> 
     const int node = j * W + i;
     const unsigned m = mask[node];
     V2 xi;
-    if (MODE == MODE_RESID0) {
+    if (MODE == MODE_RESID0 || MODE == MODE_CHEB0) {
+      const T wf = MODE == MODE_CHEB0 ? w0 : omega;
       const V2 bv = reinterpret_cast<const V2*>(b)[node];
       const V2 d01 = reinterpret_cast<const V2*>(Dinv)[2 * node];
       const V2 d23 = reinterpret_cast<const V2*>(Dinv)[2 * node + 1];
-      xi.x = omega * (d01.x * bv.x + d01.y * bv.y);
-      xi.y = omega * (d23.x * bv.x + d23.y * bv.y);
-      reinterpret_cast<V2*>(xo)[node] = xi;
+      xi.x = wf * (d01.x * bv.x + d01.y * bv.y);
+      xi.y = wf * (d23.x * bv.x + d23.y * bv.y);
+      if (MODE == MODE_RESID0) reinterpret_cast<V2*>(xo)[node] = xi;
     } else {
       xi = reinterpret_cast<const V2*>(x)[node];
     }
@@ -185,11 +187,11 @@ __global__ void __launch_bounds__(BX * BY) k_ebe2(int nx, int ny, const KeP2<T> 
       if (MODE == MODE_RESID || MODE == MODE_RESID0) {
         out.x = r0v;
         out.y = r1v;
-      } else if (MODE == MODE_CHEB) {
+      } else if (MODE == MODE_CHEB || MODE == MODE_CHEB0) {
         const T* D = Dinv + 4 * (int64_t)node;
         const T v0 = D[0] * r0v + D[1] * r1v, v1 = D[2] * r0v + D[3] * r1v;
         V2 dp = {T(0), T(0)};
-        if (dmode == 2) dp = xi;
+        if (MODE == MODE_CHEB0 || dmode == 2) dp = xi;
         else if (dmode == 1) dp = reinterpret_cast<const V2*>(xo)[node];
         V2 dn;
         dn.x = c1 * dp.x + omega * v0;
@@ -229,17 +231,19 @@ int ebe2d_blocks(const Ebe& op) {
 template <class T, int MODE, bool DOT>
 void ebe2d_launch(cudaStream_t s, const Ebe& op, const T* x, T* y, const T* b, const T* Dinv,
                   double omega, const int* done, double* parts, const ChebArg* ch) {
-  if (MODE == MODE_CHEB && !ch) TOMG_THROW(TOMG_E_INVALID, "Chebyshev step without its state");
-  T* xo = MODE == MODE_RESID0 ? const_cast<T*>(x) : (MODE == MODE_CHEB ? (T*)ch->d : nullptr);
-  const T c1 = MODE == MODE_CHEB ? (T)ch->c1 : T(0);
-  const int dm = MODE == MODE_CHEB ? ch->dmode : 0;
+  constexpr bool CHEB = MODE == MODE_CHEB || MODE == MODE_CHEB0;
+  if (CHEB && !ch) TOMG_THROW(TOMG_E_INVALID, "Chebyshev step without its state");
+  T* xo = MODE == MODE_RESID0 ? const_cast<T*>(x) : (CHEB ? (T*)ch->d : nullptr);
+  const T c1 = CHEB ? (T)ch->c1 : T(0);
+  const int dm = CHEB ? ch->dmode : 0;
+  const T w0 = CHEB ? (T)ch->w0 : T(0);
   const int npt = DOT ? 4 : (op.tile == 1 || op.tile == 2 ? op.tile : 4);  // dots: fixed tile
   dim3 grid(ceil_div(op.nx + 1, BX), ceil_div(op.ny + 1, BY * npt));
   if (!op.Kh) TOMG_THROW(TOMG_E_INVALID, "tiled element kernel without a host copy of Ke");
   KeP2<T> K;
   memcpy(K.v, op.Kh, sizeof(K.v));
 #define EB(N) LAUNCH((k_ebe2<T, MODE, DOT, N>), grid, dim3(BX, BY), 0, s, op.nx, op.ny, K,     \
-                     (const T*)op.E, op.mask, x, y, b, Dinv, (T)omega, done, parts, xo, c1, dm)
+                     (const T*)op.E, op.mask, x, y, b, Dinv, (T)omega, done, parts, xo, c1, dm, w0)
   if (npt == 1) EB(1);
   else if (npt == 2) EB(2);
   else EB(4);
@@ -297,6 +301,7 @@ INST(float, MODE_APPLY, true) INST(float, MODE_APPLY, false) INST(float, MODE_RE
 INST(float, MODE_JACOBI, false) INST(float, MODE_RESID0, false) INST(double, MODE_APPLY, true)
 INST(double, MODE_APPLY, false) INST(double, MODE_RESID, false) INST(double, MODE_JACOBI, false)
 INST(double, MODE_RESID0, false) INST(float, MODE_CHEB, false) INST(double, MODE_CHEB, false)
+INST(float, MODE_CHEB0, false) INST(double, MODE_CHEB0, false)
 #undef INST
 
 }  // namespace tomg

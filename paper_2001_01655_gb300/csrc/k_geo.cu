@@ -32,7 +32,7 @@ __global__ void __launch_bounds__(256) k_stencil(int nx, int ny, int nz, const T
                                                  const T* __restrict__ b,
                                                  const T* __restrict__ Dinv, T omega,
                                                  const int* done, T* __restrict__ xo, T c1,
-                                                 int dmode) {
+                                                 int dmode, T w0) {
   constexpr int NO = (DIM == 3) ? 27 : 9, BB = DIM * DIM;
   // 2D: the node's stencil row (fixed during a solve) is fetched before the wait for the
   // producer of x and b; 3D rows (243 values) are read as they are used
@@ -61,6 +61,8 @@ __global__ void __launch_bounds__(256) k_stencil(int nx, int ny, int nz, const T
     T xv[DIM];
     if (MODE == MODE_RESID0) {
       jacobi_first<T, DIM>(Dinv, b, nb, omega, xv);
+    } else if (MODE == MODE_CHEB0) {
+      jacobi_first<T, DIM>(Dinv, b, nb, w0, xv);
     } else {
 #pragma unroll
       for (int c = 0; c < DIM; c++) xv[c] = x[DIM * nb + c];
@@ -86,14 +88,15 @@ __global__ void __launch_bounds__(256) k_stencil(int nx, int ny, int nz, const T
   } else if (MODE == MODE_RESID) {
 #pragma unroll
     for (int c = 0; c < DIM; c++) y[DIM * node + c] = b[DIM * node + c] - acc[c];
-  } else if (MODE == MODE_CHEB) {
+  } else if (MODE == MODE_CHEB || MODE == MODE_CHEB0) {
     T r[DIM], xi[DIM];
+    if (MODE == MODE_CHEB0) jacobi_first<T, DIM>(Dinv, b, node, w0, xi);
 #pragma unroll
     for (int c = 0; c < DIM; c++) {
       r[c] = b[DIM * node + c] - acc[c];
-      xi[c] = x[DIM * node + c];
+      if (MODE == MODE_CHEB) xi[c] = x[DIM * node + c];
     }
-    cheb_node<T, DIM>(node, r, xi, Dinv, c1, omega, dmode, xo, y);
+    cheb_node<T, DIM>(node, r, xi, Dinv, c1, omega, MODE == MODE_CHEB0 ? 2 : dmode, xo, y);
   } else {
     T r[DIM];
 #pragma unroll
@@ -443,22 +446,26 @@ void stencil_op(cudaStream_t s, int mode, const Geo& g, const T* S, const T* x, 
                 const T* Dinv, double omega, const int* done, const ChebArg* ch) {
   const int64_t nn = g.nodes();
   const int grid = ceil_div(nn, 256);
-  if (mode == MODE_CHEB && !ch) TOMG_THROW(TOMG_E_INVALID, "Chebyshev step without its state");
-  T* xo = mode == MODE_RESID0 ? const_cast<T*>(x) : (mode == MODE_CHEB ? (T*)ch->d : nullptr);
-  const T c1 = mode == MODE_CHEB ? (T)ch->c1 : T(0);
-  const int dm = mode == MODE_CHEB ? ch->dmode : 0;
-#define STN(D, M) LAUNCH((k_stencil<T, D, M>), grid, 256, 0, s, g.nx, g.ny, g.nz, S, x, y, b, Dinv, (T)omega, done, xo, c1, dm)
+  const bool cheb = mode == MODE_CHEB || mode == MODE_CHEB0;
+  if (cheb && !ch) TOMG_THROW(TOMG_E_INVALID, "Chebyshev step without its state");
+  T* xo = mode == MODE_RESID0 ? const_cast<T*>(x) : (cheb ? (T*)ch->d : nullptr);
+  const T c1 = cheb ? (T)ch->c1 : T(0);
+  const int dm = cheb ? ch->dmode : 0;
+  const T w0 = cheb ? (T)ch->w0 : T(0);
+#define STN(D, M) LAUNCH((k_stencil<T, D, M>), grid, 256, 0, s, g.nx, g.ny, g.nz, S, x, y, b, Dinv, (T)omega, done, xo, c1, dm, w0)
   if (g.dim == 2) {
     if (mode == MODE_APPLY) STN(2, MODE_APPLY);
     else if (mode == MODE_RESID) STN(2, MODE_RESID);
     else if (mode == MODE_RESID0) STN(2, MODE_RESID0);
     else if (mode == MODE_CHEB) STN(2, MODE_CHEB);
+    else if (mode == MODE_CHEB0) STN(2, MODE_CHEB0);
     else STN(2, MODE_JACOBI);
   } else {
     if (mode == MODE_APPLY) STN(3, MODE_APPLY);
     else if (mode == MODE_RESID) STN(3, MODE_RESID);
     else if (mode == MODE_RESID0) STN(3, MODE_RESID0);
     else if (mode == MODE_CHEB) STN(3, MODE_CHEB);
+    else if (mode == MODE_CHEB0) STN(3, MODE_CHEB0);
     else STN(3, MODE_JACOBI);
   }
 #undef STN

@@ -14,13 +14,18 @@ namespace tomg {
 // MODE_CHEB is one step of the Chebyshev smoother with its residual: r = b - A x,
 // d = c1 d_prev + c2 Dinv r (c2 passed as the omega argument), y = x + d (y must not alias
 // x), d written to ChebArg::d; d_prev = 0 (dmode 0), the stored d (1) or x itself (2).
-enum OpMode { MODE_APPLY = 0, MODE_RESID = 1, MODE_JACOBI = 2, MODE_RESID0 = 3, MODE_CHEB = 4 };
+// MODE_CHEB0 fuses the first Chebyshev step from a zero guess with the second: x_1 = w0 Dinv b
+// is formed where it is needed (never stored), then as MODE_CHEB with d_prev = x_1.
+enum OpMode { MODE_APPLY = 0, MODE_RESID = 1, MODE_JACOBI = 2, MODE_RESID0 = 3, MODE_CHEB = 4,
+              MODE_CHEB0 = 5 };
 struct ChebArg {
   void* d = nullptr;  // T[n]
   double c1 = 0.0;
   double c2 = 0.0;    // the launchers take it through their omega argument
   int dmode = 0;
+  double w0 = 0.0;    // MODE_CHEB0: weight of the first step
 };
+// operator families whose kernels implement MODE_CHEB0 (quad4 level 0, stencils, BSR levels)
 struct Scalars;
 
 // ---------------- level 0: matrix-free SIMP element-by-element operator ----------------

@@ -139,7 +139,7 @@ template <class T>
 void level_op(tomg_problem* P, cudaStream_t s, int l, int mode, const T* x, T* y, const T* b,
               const int* done, const ChebArg* ch = nullptr) {
   Level& Lv = *P->L[l];
-  const double w = (mode == MODE_CHEB && ch) ? ch->c2 : P->opt.omega;
+  const double w = ((mode == MODE_CHEB || mode == MODE_CHEB0) && ch) ? ch->c2 : P->opt.omega;
   switch (Lv.kind) {
     case KIND_EBE:
       // FP64: the assembled fine stencil kept by the setup halves the FP64 arithmetic
@@ -199,8 +199,19 @@ void vcycle(tomg_problem* P, Work& W, int l, const T* b, T* out, const int* done
     const int m = P->opt.cheb_degree;
     T* cur = x;
     T* nxt = out;
-    jacobi0<T>(s, Lv.b, Lv.nn, V<T>::D(Lv), b, cur, Lv.cheb_c2[0], done);  // x_1 = d_0
-    for (int k = 1; k < m; k++) {
+    int k = 1;
+    // quad4 level 0, stencil and BSR levels fuse x_1 = d_0 with the second step
+    const bool fuse = m >= 2 && (Lv.kind != KIND_EBE || P->dim == 2);
+    if (fuse) {
+      ChebArg ch;
+      ch.d = r; ch.c1 = Lv.cheb_c1[1]; ch.c2 = Lv.cheb_c2[1]; ch.dmode = 2; ch.w0 = Lv.cheb_c2[0];
+      level_op<T>(P, s, l, MODE_CHEB0, cur, nxt, b, done, &ch);
+      std::swap(cur, nxt);
+      k = 2;
+    } else {
+      jacobi0<T>(s, Lv.b, Lv.nn, V<T>::D(Lv), b, cur, Lv.cheb_c2[0], done);  // x_1 = d_0
+    }
+    for (; k < m; k++) {
       ChebArg ch;
       ch.d = r; ch.c1 = Lv.cheb_c1[k]; ch.c2 = Lv.cheb_c2[k]; ch.dmode = k == 1 ? 2 : 1;
       level_op<T>(P, s, l, MODE_CHEB, cur, nxt, b, done, &ch);
