@@ -19,10 +19,27 @@ z = M(K_sigma q - theta K q) of the largest unconverged pair, orthonormalised ag
 is reset to the j_min best Ritz vectors when it reaches j_max.  The paper's settings:
 j_min = 10, j_max = 25, six modes.  Start vectors: splitmix64 uniform vectors.
 
+Sensitivities (Sec. 2.2, Eq. 6-9).  For a K-normalised mode (Phi^T K Phi = 1):
+    dlambda/drho_e = E_sigma'(rho_e) Phi_e^T K_sigma,e^1 Phi_e - lambda E'(rho_e) Phi_e^T Ke Phi_e
+                     - E'(rho_e) v_e^T Ke u_e,          K v = g = d(Phi^T K_sigma(u) Phi)/du,
+with K_sigma,e^1 the element stress stiffness for a unit stress modulus, E' the derivative of
+the SIMP modulus of K (Eq. 2) and E_sigma' that of Eq. 5 (0 below the cutoff).  The adjoint
+term follows from u = u(rho): d(Phi^T K_sigma Phi) picks up g^T du/drho_e and
+du/drho_e = -K^-1 (dK/drho_e) u.  The paper prints that term as +v^T E_sigma' (dK/dE) u; the
+reading adopted is the derivation's -v^T E' (dK/dE) u (the modulus of K is E, not E_sigma; the
+sign is that of v solving K v = g as printed), which central finite differences of the dense
+eigenvalues confirm.  K_sigma is linear in u, so g does not depend on u:
+    g = -sum_e E_sigma(rho_e) B^T D_0 w_e(Phi),   w_e,v = sum_ab L_ij[a, b] Phi_a . Phi_b
+summed over the index pairs (i, j) of Voigt component v (both orders for a shear component),
+masked at fixed DOFs.  The objective aggregates the n largest eigenvalues by a p-norm
+(p = 8, n = 6): F = (sum_i lambda_i^p)^(1/p), dF/drho = F^(1-p) sum_i lambda_i^(p-1) dlambda_i/drho.
+
 Parity: pinned (tests/test_oracle_stability.py: L_ij against exact rational integration,
 symmetry and the translation null space of K_sigma, the stresses of constant-strain fields,
 Davidson eigenvalues against dense scipy.linalg.eigh on small grids, the critical load of a
-slender fixed-free column against Euler's formula).
+slender fixed-free column against Euler's formula, the adjoint right-hand side against
+Phi^T K_sigma(e_i) Phi for every unit displacement e_i, the eigenvalue and p-norm
+sensitivities against central finite differences of dense generalized eigenvalues).
 """
 from __future__ import annotations
 
@@ -76,6 +93,74 @@ def element_stresses(problem, u):
         S[:, 0, 2] = S[:, 2, 0] = sv[:, 4]
         S[:, 0, 1] = S[:, 1, 0] = sv[:, 5]
     return S
+
+
+def voigt_pairs(dim):
+    """Voigt component v -> the index pairs (i, j) of the stress tensor it fills."""
+    if dim == 2:
+        return [[(0, 0)], [(1, 1)], [(0, 1), (1, 0)]]
+    return [[(0, 0)], [(1, 1)], [(2, 2)], [(1, 2), (2, 1)], [(0, 2), (2, 0)], [(0, 1), (1, 0)]]
+
+
+def mode_weights(problem, phi):
+    """w_e,v = sum over the pairs (i, j) of component v of sum_ab L_ij[a, b] Phi_a . Phi_b,
+    (Nel, n_voigt), with Phi masked at fixed DOFs: Phi_e^T K_G,e Phi_e = sum_v sigma_e,v w_e,v."""
+    p = problem
+    dim = p.dim
+    L = gradient_products(dim)
+    ed = fem.element_dofs(dim, p.nx, p.ny, p.nz)
+    ph = (np.asarray(phi, dtype=np.float64) * fem.free_mask(p.n, p.fixed))[ed]
+    ph = ph.reshape(ph.shape[0], 1 << dim, dim)  # (Nel, node a, component)
+    G = np.einsum("ijab,eac,ebc->eij", L, ph, ph)
+    return np.stack([sum(G[:, i, j] for i, j in pairs) for pairs in voigt_pairs(dim)], axis=1)
+
+
+def adjoint_rhs(problem, phi):
+    """g = d(Phi^T K_sigma(u) Phi)/du = -sum_e E_sigma(rho_e) B^T D_0 w_e (Eq. 7), masked."""
+    p = problem
+    dim = p.dim
+    B = fem.strain_matrix(dim, fem.shape_grad(dim, [0.5] * dim))
+    D0 = fem.constitutive(dim, 1.0, p.nu)
+    Es = stress_interp(p.rho, p.E0, p.penal)
+    ge = -Es[:, None] * (mode_weights(p, phi) @ D0 @ B)  # (Nel, element DOFs)
+    g = np.zeros(p.n)
+    np.add.at(g, fem.element_dofs(dim, p.nx, p.ny, p.nz), ge)
+    return g * fem.free_mask(p.n, p.fixed)
+
+
+def eigenvalue_sensitivity(problem, u, lam, phi, v):
+    """dlambda/drho_e (Eq. 6) for the K-normalised mode phi of eigenvalue lam, the
+    displacements u and the adjoint solution v of K v = adjoint_rhs(phi)."""
+    p = problem
+    dim = p.dim
+    m = fem.free_mask(p.n, p.fixed)
+    ed = fem.element_dofs(dim, p.nx, p.ny, p.nz)
+    rho = np.asarray(p.rho, dtype=np.float64)
+    dE = p.penal * rho ** (p.penal - 1.0) * (p.E0 - p.Emin)
+    dEs = np.where(rho >= 0.1, p.penal * p.E0 * rho ** (p.penal - 1.0), 0.0)
+    B = fem.strain_matrix(dim, fem.shape_grad(dim, [0.5] * dim))
+    D0 = fem.constitutive(dim, 1.0, p.nu)
+    ue = (np.asarray(u) * m)[ed]
+    pe = (np.asarray(phi) * m)[ed]
+    ve = (np.asarray(v) * m)[ed]
+    Ke = fem.element_stiffness(dim, p.nu)
+    s1 = ue @ B.T @ D0.T  # unit-modulus Voigt stresses
+    geo = -np.einsum("ev,ev->e", s1, mode_weights(p, phi))  # Phi_e^T K_sigma,e^1 Phi_e
+    return (dEs * geo - lam * dE * np.einsum("ea,ab,eb->e", pe, Ke, pe)
+            - dE * np.einsum("ea,ab,eb->e", ve, Ke, ue))
+
+
+def pnorm(lams, p=8):
+    """F = (sum_i lambda_i^p)^(1/p) (Eq. 8)."""
+    lams = np.asarray(lams, dtype=np.float64)
+    return float(np.sum(lams ** p) ** (1.0 / p))
+
+
+def pnorm_sensitivity(lams, dlams, p=8):
+    """dF/drho = F^(1-p) sum_i lambda_i^(p-1) dlambda_i/drho (Eq. 9); dlams (n, Nel)."""
+    lams = np.asarray(lams, dtype=np.float64)
+    F = pnorm(lams, p)
+    return F ** (1.0 - p) * (lams ** (p - 1.0)) @ np.asarray(dlams)
 
 
 def stress_stiffness(problem, u):

@@ -120,3 +120,96 @@ def test_column_buckling_load_matches_euler():
     th, _, _, _ = stability.davidson(Ks, A0, M=lambda v: mg.vcycle(H, v), n_eig=2, tol=1e-8)
     pcr = np.pi ** 2 * nx ** 3 / 12.0 / (4.0 * ny ** 2)
     assert 1.0 / th[0] == pytest.approx(pcr, rel=0.05)
+
+
+def _with_rho(p, rho):
+    return W.Problem(p.name, p.dim, p.nx, p.ny, p.nz, np.asarray(rho, dtype=np.float64), p.fixed,
+                     p.f, E0=p.E0, Emin=p.Emin, penal=p.penal, nu=p.nu)
+
+
+@pytest.mark.parametrize("dim", [2, 3])
+def test_adjoint_rhs_brute_force(dim):
+    """g_i = Phi^T K_sigma(e_i) Phi for every free DOF i (K_sigma is linear in u), 0 at fixed
+    DOFs; the density spans the E_sigma cutoff so elements with E_sigma = 0 are included."""
+    p = W.random_problem(dim, 4, 3, 2, seed=8, contrast="minmax")
+    assert np.any(p.rho < 0.1) and np.any(p.rho >= 0.1)
+    free = fem.free_mask(p.n, p.fixed).astype(bool)
+    phi = np.random.default_rng(3).standard_normal(p.n) * free
+    g = stability.adjoint_rhs(p, phi)
+    ref = np.zeros(p.n)
+    for i in np.flatnonzero(free):
+        e = np.zeros(p.n)
+        e[i] = 1.0
+        ref[i] = phi @ (stability.stress_stiffness(p, e) @ phi)
+    assert np.all(g[~free] == 0.0)
+    assert np.allclose(g, ref, rtol=1e-12, atol=1e-14 * np.abs(ref).max())
+
+
+def _dense_buckling(p):
+    u = solve.direct(p)["u"][0]
+    Ks = stability.stress_stiffness(p, u).toarray()
+    K = mg.fine_operator(p).toarray()
+    lam, Z = sla.eigh(Ks, K)
+    return lam[::-1], Z[:, ::-1], u, K
+
+
+def _sensitivity_case(dim):
+    if dim == 2:
+        p = W.column_2d(3, 8)
+    else:
+        p = W.random_problem(3, 2, 2, 3, seed=4, contrast="minmax")
+    rho = np.random.default_rng(11).uniform(0.3, 1.0, p.nel)  # clear of the 0.1 cutoff
+    return _with_rho(p, rho)
+
+
+@pytest.mark.parametrize("dim", [2, 3])
+def test_eigenvalue_sensitivity_finite_differences(dim):
+    """dlambda/drho_e of the three largest (simple) eigenvalues against central differences of
+    dense generalized eigenvalues, u re-solved at every perturbed density.  The adjoint term is
+    large here: flipping its sign (the paper's printed +) misses by far more than the bound."""
+    p = _sensitivity_case(dim)
+    lam, Z, u, K = _dense_buckling(p)
+    assert np.all(np.diff(lam[:4]) < -1e-3 * abs(lam[0]))  # simple eigenvalues
+    h = 1e-5
+    for k in range(3):
+        phi = Z[:, k]
+        v = np.linalg.solve(K, stability.adjoint_rhs(p, phi))
+        d = stability.eigenvalue_sensitivity(p, u, lam[k], phi, v)
+        fd = np.zeros(p.nel)
+        for e in range(p.nel):
+            r1, r2 = p.rho.copy(), p.rho.copy()
+            r1[e] += h
+            r2[e] -= h
+            fd[e] = (_dense_buckling(_with_rho(p, r1))[0][k] -
+                     _dense_buckling(_with_rho(p, r2))[0][k]) / (2 * h)
+        scale = np.abs(fd).max()
+        assert np.abs(d - fd).max() <= 1e-6 * scale
+        flipped = stability.eigenvalue_sensitivity(p, u, lam[k], phi, -v)
+        assert np.abs(flipped - fd).max() > 1e-2 * scale
+
+
+def test_pnorm_closed_forms():
+    assert stability.pnorm([3.0]) == pytest.approx(3.0, rel=1e-15)
+    assert stability.pnorm([2.0] * 6) == pytest.approx(2.0 * 6 ** 0.125, rel=1e-15)
+    assert stability.pnorm([3.0, 4.0], p=2) == pytest.approx(5.0, rel=1e-15)
+
+
+def test_pnorm_sensitivity_finite_differences():
+    """dF/drho of the p = 8 norm of the three largest eigenvalues against central differences."""
+    p = _sensitivity_case(2)
+    lam, Z, u, K = _dense_buckling(p)
+    n = 3
+    dl = []
+    for k in range(n):
+        v = np.linalg.solve(K, stability.adjoint_rhs(p, Z[:, k]))
+        dl.append(stability.eigenvalue_sensitivity(p, u, lam[k], Z[:, k], v))
+    dF = stability.pnorm_sensitivity(lam[:n], np.array(dl))
+    h = 1e-5
+    fd = np.zeros(p.nel)
+    for e in range(p.nel):
+        r1, r2 = p.rho.copy(), p.rho.copy()
+        r1[e] += h
+        r2[e] -= h
+        fd[e] = (stability.pnorm(_dense_buckling(_with_rho(p, r1))[0][:n]) -
+                 stability.pnorm(_dense_buckling(_with_rho(p, r2))[0][:n])) / (2 * h)
+    assert np.abs(dF - fd).max() <= 1e-6 * np.abs(fd).max()
