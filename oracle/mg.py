@@ -24,11 +24,21 @@ Smoothers
              the three-term recurrence of Chebyshev acceleration (Saad, Iterative Methods for
              Sparse Linear Systems, 2nd ed., Alg. 12.1).  Pre- and post-smoothing use the same
              polynomial, so the cycle stays symmetric.
+  gmres      m steps of right-preconditioned GMRES (Saad, Alg. 9.5) with the point-block
+             diagonal in place of the paper's SOR preconditioning (Sec. 4.1 studies an
+             SOR-preconditioned GMRES smoother under flexible GMRES): Arnoldi by modified
+             Gram-Schmidt from r_0 = b - A x_0, the least-squares problem
+             min ||beta e_1 - Hbar y|| solved by a library routine, x = x_0 + D^-1 V y.  An exact
+             breakdown (a zero new Arnoldi vector, r_0 = 0 included) ends the steps early.  The
+             smoother depends nonlinearly on its right-hand side, so the cycle is a variable
+             preconditioner and needs a flexible outer method (FCG or FGMRES).
 
 Parity: pinned (tests/test_oracle_mg.py: symmetric preconditioner, contraction < 1,
 exactness of a one-level cycle, iteration counts bounded under refinement; the Chebyshev
 smoother's error propagation equals the scaled Chebyshev polynomial evaluated by
-numpy.polynomial.chebyshev on every eigenvector of D^-1 A).
+numpy.polynomial.chebyshev on every eigenvector of D^-1 A; the GMRES smoother's result
+against the minimiser of ||b - A x|| over the explicit power basis of the preconditioned
+Krylov space, finite termination at m = n, exact breakdowns).
 """
 from __future__ import annotations
 
@@ -50,8 +60,9 @@ class Hierarchy:
     n_pre: int = 1
     n_post: int = 1
     block: bool = True
-    smoother: str = "jacobi"      # or "chebyshev"
+    smoother: str = "jacobi"      # or "chebyshev", "gmres"
     cheb_degree: int = 2
+    gmres_steps: int = 2          # GMRES smoother: Arnoldi steps per smoothing
     cheb_lower: float = 0.1       # interval [lower, upper] * lambda(D^-1 A)
     cheb_upper: float = 1.1
     Dinv: list = field(default_factory=list)
@@ -111,7 +122,41 @@ def chebyshev_smooth(A, Dinv, x, b, lam_lo, lam_hi, m):
     return x
 
 
+def gmres_smooth(A, Dinv, x, b, m):
+    """m steps of GMRES for A x = b from x, right-preconditioned by the point-block diagonal
+    (Saad, Alg. 9.5): Arnoldi on A D^-1 by modified Gram-Schmidt, then the small
+    least-squares problem; stops early at an exact breakdown."""
+    r = b - A @ x
+    beta = np.linalg.norm(r)
+    if beta == 0.0:
+        return x
+    Vb = [r / beta]
+    Z = []
+    Hb = np.zeros((m + 1, m))
+    k = 0
+    for j in range(m):
+        z = amg.apply_block_diag(Dinv, Vb[j])
+        Z.append(z)
+        w = A @ z
+        for i in range(j + 1):
+            Hb[i, j] = w @ Vb[i]
+            w = w - Hb[i, j] * Vb[i]
+        Hb[j + 1, j] = np.linalg.norm(w)
+        k = j + 1
+        if Hb[j + 1, j] == 0.0:
+            break
+        Vb.append(w / Hb[j + 1, j])
+    e1 = np.zeros(k + 1)
+    e1[0] = beta
+    y = np.linalg.lstsq(Hb[:k + 1, :k], e1, rcond=None)[0]
+    for i in range(k):
+        x = x + y[i] * Z[i]
+    return x
+
+
 def presmooth(H, l, b):
+    if H.smoother == "gmres":
+        return gmres_smooth(H.A[l], H.Dinv[l], np.zeros_like(b), b, H.gmres_steps)
     if H.smoother == "chebyshev":
         lam = H.lam[l]
         return chebyshev_smooth(H.A[l], H.Dinv[l], np.zeros_like(b), b, H.cheb_lower * lam,
@@ -123,6 +168,8 @@ def presmooth(H, l, b):
 
 
 def postsmooth(H, l, x, b):
+    if H.smoother == "gmres":
+        return gmres_smooth(H.A[l], H.Dinv[l], x, b, H.gmres_steps)
     if H.smoother == "chebyshev":
         lam = H.lam[l]
         return chebyshev_smooth(H.A[l], H.Dinv[l], x, b, H.cheb_lower * lam, H.cheb_upper * lam,

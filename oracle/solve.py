@@ -21,9 +21,10 @@ def direct(problem):
 
 
 def build(problem, pc="gmg", n_levels=None, cap=None, n_geo=None, beta=0.003, omega=0.5,
-          A0=None, smoother="jacobi", cheb_degree=2, cheb_lower=0.1, cheb_upper=1.1):
+          A0=None, smoother="jacobi", cheb_degree=2, cheb_lower=0.1, cheb_upper=1.1,
+          gmres_steps=2):
     kw = dict(omega=omega, smoother=smoother, cheb_degree=cheb_degree, cheb_lower=cheb_lower,
-              cheb_upper=cheb_upper)
+              cheb_upper=cheb_upper, gmres_steps=gmres_steps)
     if pc == "gmg":
         return mg.build_gmg(problem, n_levels=n_levels, cap=cap, A0=A0, **kw)
     if pc == "amg":
@@ -36,10 +37,13 @@ def build(problem, pc="gmg", n_levels=None, cap=None, n_geo=None, beta=0.003, om
 def solve(problem, pc="gmg", rtol=1e-8, max_iter=1000, flexible=False, x0=None, H=None,
           krylov_method="cg", restart=30, **kw):
     """Solve every right-hand side of ``problem``; returns a dict of stacked results.
-    krylov_method: "cg" (PCG, or flexible CG with flexible=True) or "fgmres" (FGMRES(restart))."""
+    krylov_method: "cg" (PCG, or flexible CG with flexible=True; always flexible with the GMRES
+    smoother, a variable preconditioner) or "fgmres" (FGMRES(restart))."""
     A0 = mg.fine_operator(problem)
     if H is None:
         H = build(problem, pc=pc, A0=A0, **kw)
+    if H.smoother == "gmres":
+        flexible = True
     m = fem.free_mask(problem.n, problem.fixed)
     F = np.atleast_2d(problem.f)
     U = np.zeros_like(F)
