@@ -71,7 +71,12 @@ typedef struct {
   int smoother;        /* 0 = weighted point-block Jacobi (Sec. 4.1); 1 = point-block
                           Jacobi-preconditioned Chebyshev polynomial (the paper's Chebyshev
                           smoother study, Sec. 4.1), degree cheb_degree on
-                          [cheb_lower, cheb_upper] x lambda_max(D^-1 A) of each level  0        */
+                          [cheb_lower, cheb_upper] x lambda_max(D^-1 A) of each level;
+                          2 = gmres_steps steps of point-block-Jacobi right-preconditioned
+                          GMRES (the paper's GMRES smoother, Sec. 4.1), before the coarse
+                          correction from x = 0, after it from the corrected iterate; the
+                          cycle then depends on its input, so the CG loop is flexible CG in
+                          every precision                                             0        */
   double omega;        /* Jacobi weight (Sec. 4.1)                                 0.5      */
   int n_pre, n_post;   /* smoothing sweeps (one each)                              1, 1     */
   double soc_beta;     /* strength-of-connection threshold (Eq. 10)                0.003    */
@@ -96,6 +101,8 @@ typedef struct {
                           outer solver (Sec. 4), host-driven, one right-hand side at a time,
                           iterations = preconditioner applications                    0        */
   int gmres_restart;   /* FGMRES restart length m, 1..200                             30       */
+  int gmres_steps;     /* GMRES smoother: Arnoldi steps (operator applies) per smoothing,
+                          1..8                                                        2        */
 } tomg_options;
 
 typedef struct {
@@ -277,6 +284,36 @@ tomg_status tomg_stress_stiffness_apply(tomg_problem* prob, const double* u, con
 tomg_status tomg_buckling(tomg_problem* prob, const double* u, int n_eig, int j_min, int j_max,
                           double tol, int max_iter, double* lambdas, double* modes, int on_device,
                           int* iterations);
+
+/* Right-hand sides of the stability adjoint equations K v_k = g_k (Sec. 2.2, Eq. 7):
+ *   g_k = Phi_k^T (dK_sigma/du) Phi_k = -sum_e E_sigma(rho_e) (D_0 B)^T w_e(Phi_k),
+ *   w_e,v = sum_ab L_ij[a, b] Phi_a . Phi_b summed over the index pairs (i, j) of Voigt
+ *           component v (both orders for a shear component),
+ * masked at fixed DOFs, for the problem's current density.  K_sigma is linear in u, so g does
+ * not depend on u.  modes: n_dofs x n_modes column-major (e.g. from tomg_buckling); g: n_dofs
+ * x n_modes column-major, ready for tomg_solve.  Host or device arrays (on_device),
+ * caller-owned, may not alias.  E_INVALID for n_modes outside 1..16. */
+tomg_status tomg_buckling_adjoint_rhs(tomg_problem* prob, int n_modes, const double* modes,
+                                      double* g, int on_device);
+/* Sensitivities of the buckling eigenvalues (Sec. 2.2, Eq. 6) and of their p-norm aggregate
+ * F = (sum_k lambda_k^p)^(1/p) (Eq. 8-9) with respect to the densities rho:
+ *   dlambda_k/drho_e = E_sigma'(rho_e) Phi_k,e^T K_sigma,e^1 Phi_k,e
+ *                      - lambda_k E'(rho_e) Phi_k,e^T Ke Phi_k,e - E'(rho_e) v_k,e^T Ke u_e,
+ *   dF/drho_e = F^(1-p) sum_k lambda_k^(p-1) dlambda_k/drho_e,
+ * for K-normalised modes Phi_k (as tomg_buckling returns them), the displacements u and the
+ * adjoint solutions v_k of K v_k = g_k (tomg_buckling_adjoint_rhs, then tomg_solve).
+ * K_sigma,e^1 is the element stress stiffness at unit stress modulus, E' the derivative of the
+ * SIMP modulus of K (Eq. 2), E_sigma' that of Eq. 5 (0 below rho = 0.1).  The paper prints the
+ * adjoint term as +v^T E_sigma' (dK/dE) u; this is the derivation's -v^T E' (dK/dE) u.
+ * lambdas: host, n_modes; u: n_dofs; modes, adjoints: n_dofs x n_modes column-major;
+ * dlambda: NULL or n_elems x n_modes column-major; dF: NULL or n_elems; F: NULL or a host
+ * scalar.  Arrays other than lambdas and F on host or device (on_device).  E_INVALID for
+ * n_modes outside 1..16, pnorm < 1 or a p-norm that is not positive and finite.  dF/drho is
+ * the chain rule's first factor: tomg_density_filter with transpose gives dF/dalpha. */
+tomg_status tomg_buckling_sensitivity(tomg_problem* prob, const double* u, int n_modes,
+                                      const double* lambdas, const double* modes,
+                                      const double* adjoints, double pnorm, double* dlambda,
+                                      double* dF, double* F, int on_device);
 
 /* Adaptive hybrid hierarchy (Sec. 4.4): the geometric level count (including the fine grid)
  * the next tomg_setup of this problem will use, 0 before the first setup with adaptive_geo. */

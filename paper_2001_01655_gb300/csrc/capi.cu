@@ -1,7 +1,9 @@
 // C ABI of the tomg library (declared in include/tomg.h): argument checks, error capture and
 // host/device marshalling around the runtime in solver.cu.  No exception crosses the ABI.
+#include <cmath>
 #include <cstdarg>
 #include <cstring>
+#include <vector>
 
 #include "solver.h"
 
@@ -130,6 +132,7 @@ void tomg_options_default(tomg_options* o) {
   o->adaptive_min_geo = 2;
   o->krylov = 0;
   o->gmres_restart = 30;
+  o->gmres_steps = 2;
   o->omega = 0.5;
   o->n_pre = 1;
   o->n_post = 1;
@@ -494,6 +497,83 @@ tomg_status tomg_buckling(tomg_problem* P, const double* u, int n_eig, int j_min
     StreamScope sc(P);
     return tomg::buckling(P, u, n_eig, j_min, j_max, tol, max_iter, lambdas, modes, on_device,
                           iterations);
+  });
+}
+
+tomg_status tomg_buckling_adjoint_rhs(tomg_problem* P, int n_modes, const double* modes,
+                                      double* g, int on_device) {
+  return guarded([&]() -> tomg_status {
+    if (!P || !modes || !g) TOMG_THROW(TOMG_E_INVALID, "null argument");
+    if (!P->have_density) TOMG_THROW(TOMG_E_INVALID, "no density set");
+    if (n_modes < 1 || n_modes > 16) TOMG_THROW(TOMG_E_INVALID, "1 <= n_modes <= 16");
+    set_device(P);
+    StreamScope sc(P);
+    cudaStream_t s = P->stream;
+    const size_t bytes = (size_t)P->n * n_modes * 8;
+    tomg::DBuf<double> dphi, dg, sw;
+    const double* ph = modes;
+    double* gg = g;
+    if (!on_device) {
+      dphi.resize((int64_t)P->n * n_modes);
+      dg.resize((int64_t)P->n * n_modes);
+      CK(cudaMemcpyAsync(dphi.p, modes, bytes, cudaMemcpyHostToDevice, s));
+      ph = dphi.p;
+      gg = dg.p;
+    }
+    sw.resize(P->nel * n_modes * tomg::stress_components(P->dim));
+    tomg::buckling_adjoint_rhs(s, P->dim, P->nx, P->ny, P->nz, P->nu, P->E0, P->penal, P->rho.p,
+                               P->mask.p, n_modes, ph, P->n, sw.p, gg, P->n);
+    if (!on_device) CK(cudaMemcpyAsync(g, gg, bytes, cudaMemcpyDeviceToHost, s));
+    CK(cudaStreamSynchronize(s));
+    return TOMG_OK;
+  });
+}
+
+tomg_status tomg_buckling_sensitivity(tomg_problem* P, const double* u, int n_modes,
+                                      const double* lambdas, const double* modes,
+                                      const double* adjoints, double pnorm, double* dlambda,
+                                      double* dF, double* F, int on_device) {
+  return guarded([&]() -> tomg_status {
+    if (!P || !u || !lambdas || !modes || !adjoints) TOMG_THROW(TOMG_E_INVALID, "null argument");
+    if (!P->have_density) TOMG_THROW(TOMG_E_INVALID, "no density set");
+    if (n_modes < 1 || n_modes > 16) TOMG_THROW(TOMG_E_INVALID, "1 <= n_modes <= 16");
+    if (!(pnorm >= 1.0)) TOMG_THROW(TOMG_E_INVALID, "pnorm %g < 1", pnorm);
+    double sum = 0.0;
+    for (int k = 0; k < n_modes; k++) sum += std::pow(lambdas[k], pnorm);
+    const double Fv = std::pow(sum, 1.0 / pnorm);
+    if (!(sum > 0.0) || !std::isfinite(Fv))
+      TOMG_THROW(TOMG_E_INVALID, "p-norm of the eigenvalues is not positive and finite");
+    std::vector<double> coef(n_modes);
+    for (int k = 0; k < n_modes; k++)
+      coef[k] = std::pow(Fv, 1.0 - pnorm) * std::pow(lambdas[k], pnorm - 1.0);
+    if (F) *F = Fv;
+    if (!dlambda && !dF) return TOMG_OK;
+    set_device(P);
+    StreamScope sc(P);
+    cudaStream_t s = P->stream;
+    const int64_t n = P->n, nel = P->nel;
+    tomg::DBuf<double> du, dphi, dv, ddl, ddf;
+    const double *uu = u, *ph = modes, *vv = adjoints;
+    double *dl = dlambda, *df = dF;
+    if (!on_device) {
+      du.resize(n); dphi.resize(n * n_modes); dv.resize(n * n_modes);
+      CK(cudaMemcpyAsync(du.p, u, (size_t)n * 8, cudaMemcpyHostToDevice, s));
+      CK(cudaMemcpyAsync(dphi.p, modes, (size_t)n * n_modes * 8, cudaMemcpyHostToDevice, s));
+      CK(cudaMemcpyAsync(dv.p, adjoints, (size_t)n * n_modes * 8, cudaMemcpyHostToDevice, s));
+      uu = du.p; ph = dphi.p; vv = dv.p;
+      if (dlambda) { ddl.resize(nel * n_modes); dl = ddl.p; }
+      if (dF) { ddf.resize(nel); df = ddf.p; }
+    }
+    tomg::buckling_sensitivity(s, P->dim, P->nx, P->ny, P->nz, P->nu, P->E0, P->Emin, P->penal,
+                               P->Ke64.p, P->rho.p, P->mask.p, uu, n_modes, lambdas, coef.data(),
+                               ph, vv, n, dl, df);
+    if (!on_device) {
+      if (dlambda)
+        CK(cudaMemcpyAsync(dlambda, dl, (size_t)nel * n_modes * 8, cudaMemcpyDeviceToHost, s));
+      if (dF) CK(cudaMemcpyAsync(dF, df, (size_t)nel * 8, cudaMemcpyDeviceToHost, s));
+    }
+    CK(cudaStreamSynchronize(s));
+    return TOMG_OK;
   });
 }
 

@@ -102,6 +102,18 @@ void element_stresses(cudaStream_t s, int dim, int nx, int ny, int nz, double nu
 // y = M K_sigma M x from the element stresses (FP64)
 void stress_stiffness_apply(cudaStream_t s, int dim, int nx, int ny, int nz, double nu,
                             const double* sig, const uint8_t* mask, const double* x, double* y);
+// adjoint right-hand sides g_m = d(Phi_m^T K_sigma Phi_m)/du for nm modes (columns of Phi,
+// leading dimension ldp); sw: scratch, nm x n_elems x stress_components doubles
+void buckling_adjoint_rhs(cudaStream_t s, int dim, int nx, int ny, int nz, double nu, double E0,
+                          double penal, const double* rho, const uint8_t* mask, int nm,
+                          const double* Phi, int64_t ldp, double* sw, double* g, int64_t ldg);
+// dlambda_m/drho (n_elems x nm, nullable) and sum_m coef_m dlambda_m/drho (n_elems, nullable);
+// lam, coef: host arrays of nm <= 16 values
+void buckling_sensitivity(cudaStream_t s, int dim, int nx, int ny, int nz, double nu, double E0,
+                          double Emin, double penal, const double* Ke, const double* rho,
+                          const uint8_t* mask, const double* u, int nm, const double* lam,
+                          const double* coef, const double* Phi, const double* Vadj, int64_t ld,
+                          double* dlam, double* dF);
 
 // ---------------- geometric levels: structured stencils and transfers -----------------
 struct Geo {
@@ -239,6 +251,35 @@ void mask_vec(cudaStream_t s, const double* f, double* b, const uint8_t* mask, i
 template <class T>
 void jacobi0(cudaStream_t s, int bs, int64_t nodes, const T* Dinv, const T* b, T* x, double omega,
              const int* done);
+// GMRES smoother (k_gmres_smooth.cu): state of one smoothing in device memory; the ticket
+// must be zero when the state is first used
+constexpr int GM_MAX = 8;  // most Arnoldi steps per smoothing
+struct GmState {
+  double H[(GM_MAX + 1) * GM_MAX];  // Hbar, column-major, leading dimension GM_MAX + 1
+  double h1[GM_MAX], h2[GM_MAX];    // the two Gram-Schmidt passes' projections of a step
+  double beta, inv;                 // ||r_0||; 1 / norm of the vector being normalised
+  double y[GM_MAX];                 // least-squares solution
+  int meff;                         // steps before an exact breakdown
+  unsigned tk;                      // last-block ticket
+};
+int gmres_smooth_parts(int64_t n);  // FP64 scratch partials for vectors of n entries
+// beta = ||r0||, first scale
+template <class T>
+void gmres_smooth_begin(cudaStream_t s, int64_t n, const T* r0, double* parts, GmState* st, int m,
+                        const int* done);
+// v_j (from src: r0 for j = 0, slot j of V otherwise), z_j = D^-1 v_j (bs x bs blocks)
+template <class T>
+void gmres_smooth_next(cudaStream_t s, int bs, int64_t nodes, int j, const T* src, T* V,
+                       int64_t ldv, T* Z, const T* Dinv, const GmState* st, const int* done);
+// after w = A z_j is in slot j + 1 of V: both Gram-Schmidt passes, column j of Hbar, and the
+// least-squares solve after the last step (j = m - 1)
+template <class T>
+void gmres_smooth_orth(cudaStream_t s, int64_t n, int j, int m, T* V, int64_t ldv, double* parts,
+                       GmState* st, const int* done);
+// out = x0 + Z y (x0 nullable: zero)
+template <class T>
+void gmres_smooth_finish(cudaStream_t s, int64_t n, int m, const T* Z, int64_t ldv,
+                         const GmState* st, const T* x0, T* out, const int* done);
 // flexible GMRES: h[k] = V_k . w for k < J (V_k = V + k ldv; parts: multi_dot_parts(J)
 // scratch), w += sign sum_k c[k] V_k, v = s w
 void multi_dot(cudaStream_t s, int64_t n, int J, const double* V, int64_t ldv, const double* w,

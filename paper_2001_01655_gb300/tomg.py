@@ -17,7 +17,7 @@ LIB_PATH = os.path.join(HERE, "_build", "libtomg.so")
 OK, NOT_CONVERGED, E_INVALID, E_OOM, E_CUDA, E_BREAKDOWN, E_TIMEOUT, E_BUDGET = 0, 1, -1, -2, -3, -4, -5, -6
 PC = {"gmg": 0, "amg": 1, "hybrid": 2, "jacobi": 3}
 PREC = {"fp64": 0, "fp32": 1, "tf32x3": 2}
-SMOOTHER = {"jacobi": 0, "chebyshev": 1}
+SMOOTHER = {"jacobi": 0, "chebyshev": 1, "gmres": 2}
 KRYLOV = {"cg": 0, "fgmres": 1}
 
 
@@ -35,7 +35,8 @@ class Options(C.Structure):
                 ("use_graph", C.c_int), ("max_levels", C.c_int), ("concurrency", C.c_int),
                 ("cheb_degree", C.c_int), ("cheb_lower", C.c_double), ("cheb_upper", C.c_double),
                 ("adaptive_geo", C.c_int), ("adaptive_iters", C.c_int), ("adaptive_min_geo", C.c_int),
-                ("krylov", C.c_int), ("gmres_restart", C.c_int)]
+                ("krylov", C.c_int), ("gmres_restart", C.c_int),
+                ("gmres_steps", C.c_int)]
 
 
 class Result(C.Structure):
@@ -88,6 +89,9 @@ _SIGS = {
     "tomg_density_filter": (C.c_int, [_P, C.c_double, C.c_int, _P, _P, C.c_int]),
     "tomg_compliance_sensitivity": (C.c_int, [_P, _P, _P, C.c_int]),
     "tomg_stress_stiffness_apply": (C.c_int, [_P, _P, _P, _P, C.c_int]),
+    "tomg_buckling_adjoint_rhs": (C.c_int, [_P, C.c_int, _P, _P, C.c_int]),
+    "tomg_buckling_sensitivity": (C.c_int, [_P, _P, C.c_int, _P, _P, _P, C.c_double, _P, _P, _P,
+                                            C.c_int]),
     "tomg_buckling": (C.c_int, [_P, _P, C.c_int, C.c_int, C.c_int, C.c_double, C.c_int, _P, _P,
                                 C.c_int, C.POINTER(C.c_int)]),
     "tomg_server_create": (C.c_int, [_P, C.c_size_t, C.c_int, C.POINTER(_P)]),
@@ -376,18 +380,78 @@ class Problem:
 
     def buckling(self, u, n_eig=6, j_min=10, j_max=25, tol=1e-6, max_iter=1000, modes=False):
         """The n_eig largest eigenvalues of K_sigma Phi = lambda K Phi (and the K-orthonormal
-        modes, n_eig x n_dofs, if requested) by generalized Davidson.  Returns
+        modes, n_eig x n_dofs, if requested) by generalized Davidson.  u: numpy, or a CUDA
+        tensor (device path: the modes come back as a CUDA tensor).  Returns
         (lambdas, modes or None, iterations, status)."""
-        uu = np.ascontiguousarray(u, dtype=np.float64).reshape(-1)
+        if not _is_torch(u):
+            u = np.ascontiguousarray(u, dtype=np.float64).reshape(-1)
+        pu, dev, _ = _ptr(u, np.float64)
         lam = np.zeros(n_eig)
-        Phi = np.zeros((n_eig, self.n)) if modes else None
+        Phi, pm = None, None
+        if modes:
+            if dev:
+                import torch
+                Phi = torch.empty((n_eig, self.n), dtype=torch.float64, device=u.device)
+                pm = _ptr(Phi, np.float64)[0]
+            else:
+                Phi = np.zeros((n_eig, self.n))
+                pm = C.c_void_p(Phi.ctypes.data)
         it = C.c_int()
-        st = load().tomg_buckling(self.h, C.c_void_p(uu.ctypes.data), n_eig, j_min, j_max,
-                                  float(tol), max_iter, C.c_void_p(lam.ctypes.data),
-                                  C.c_void_p(Phi.ctypes.data) if modes else None, 0,
-                                  C.byref(it))
+        st = load().tomg_buckling(self.h, pu, n_eig, j_min, j_max, float(tol), max_iter,
+                                  C.c_void_p(lam.ctypes.data), pm, dev, C.byref(it))
         _check(st)
         return lam, Phi, it.value, st
+
+    def buckling_adjoint_rhs(self, modes):
+        """g_k = Phi_k^T (dK_sigma/du) Phi_k for the modes (n_modes x n_dofs, numpy or a CUDA
+        tensor): the right-hand sides of the stability adjoint equations, same shape and kind."""
+        if not _is_torch(modes):
+            modes = np.ascontiguousarray(np.atleast_2d(modes), dtype=np.float64)
+        src, dev, keep = _ptr(modes, np.float64)
+        if dev:
+            import torch
+            g = torch.empty_like(modes)
+            dst, _, _ = _ptr(g, np.float64)
+        else:
+            g = np.zeros_like(modes)
+            dst = C.c_void_p(g.ctypes.data)
+        _check(load().tomg_buckling_adjoint_rhs(self.h, int(modes.shape[0]), src, dst, dev))
+        return g
+
+    def buckling_sensitivity(self, u, lambdas, modes, adjoints, pnorm=8.0, per_mode=True):
+        """dlambda_k/drho (n_modes x n_elems, if per_mode), dF/drho (n_elems) and F for the
+        p-norm aggregate F = (sum lambda_k^p)^(1/p) of the buckling eigenvalues, from the
+        displacements u, the K-normalised modes and the adjoint solutions (n_modes x n_dofs).
+        numpy arrays, or CUDA tensors for u, modes and adjoints (device path).  Returns
+        (dlambda or None, dF, F)."""
+        lam = np.ascontiguousarray(lambdas, dtype=np.float64).reshape(-1)
+        nm = lam.size
+        if not _is_torch(u):
+            u = np.ascontiguousarray(u, dtype=np.float64).reshape(-1)
+            modes = np.ascontiguousarray(np.atleast_2d(modes), dtype=np.float64)
+            adjoints = np.ascontiguousarray(np.atleast_2d(adjoints), dtype=np.float64)
+        pu, dev, _ = _ptr(u, np.float64)
+        pm, dm, _ = _ptr(modes, np.float64)
+        pa, da, _ = _ptr(adjoints, np.float64)
+        if not (dev == dm == da):
+            raise TypeError("u, modes and adjoints must all be numpy arrays or all CUDA tensors")
+        if tuple(modes.shape) != (nm, self.n) or tuple(adjoints.shape) != (nm, self.n):
+            raise ValueError("modes and adjoints must be n_modes x n_dofs")
+        if dev:
+            import torch
+            dl = torch.empty((nm, self.nel), dtype=torch.float64, device=u.device) if per_mode else None
+            dF = torch.empty(self.nel, dtype=torch.float64, device=u.device)
+            pdl = _ptr(dl, np.float64)[0] if per_mode else None
+            pdf = _ptr(dF, np.float64)[0]
+        else:
+            dl = np.zeros((nm, self.nel)) if per_mode else None
+            dF = np.zeros(self.nel)
+            pdl = C.c_void_p(dl.ctypes.data) if per_mode else None
+            pdf = C.c_void_p(dF.ctypes.data)
+        F = C.c_double()
+        _check(load().tomg_buckling_sensitivity(self.h, pu, nm, C.c_void_p(lam.ctypes.data), pm, pa,
+                                                float(pnorm), pdl, pdf, C.byref(F), dev))
+        return dl, dF, F.value
 
     def fine_apply_f32_noalloc(self, x, y):
         """y = A_0 x in FP32 arithmetic without any device allocation (x, y: contiguous float64
