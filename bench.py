@@ -248,6 +248,16 @@ def run_gpu(args, rank, world, local):
                 "solve_ms": statistics.median(r["solve_ms"] for r in rj),
                 "rel_residual_max": max(r["rel_residual"] for r in rj)}
         out["jacobi"] = jac
+        # the paper's third smoother (Sec. 4.1): GMRES steps per smoothing, flexible CG outside
+        gm = {}
+        for steps_ in (2, 4):
+            og = dict(opts, smoother="gmres", gmres_steps=steps_)
+            tg, ig, rg, _ = timed("fp32", max(3, args.steps // 2), 1, og)
+            gm["steps_%d" % steps_] = {
+                "solves_per_s": len(tg) / (sum(tg) / 1e3), "iterations": statistics.median(ig),
+                "solve_ms": statistics.median(r["solve_ms"] for r in rg),
+                "rel_residual_max": max(r["rel_residual"] for r in rg)}
+        out["gmres_smoother"] = gm
     # end to end through the C ABI with host buffers (copies inside the timed region)
     rho_h, f_h = p.rho.copy(), p.f[0].copy()
     e2e = []

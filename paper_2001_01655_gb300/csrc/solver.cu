@@ -95,6 +95,8 @@ template <> struct V<double> {
   static double* x(LevelWork& l) { return l.x64.p; }
   static double* r(LevelWork& l) { return l.r64.p; }
   static double* y(LevelWork& l) { return l.y64.p; }
+  static double* gV(LevelWork& l) { return l.gV64.p; }
+  static double* gZ(LevelWork& l) { return l.gZ64.p; }
   static const double* Ainv(const tomg_problem* P) { return P->Ainv64.p; }
   static Ebe ebe(const tomg_problem* P) {
     return Ebe{P->dim, P->nx, P->ny, P->nz, P->Ke64.p, P->E64.p, P->mask.p, 0, P->Ke_host.data()};
@@ -110,6 +112,8 @@ template <> struct V<float> {
   static float* x(LevelWork& l) { return l.x32.p; }
   static float* r(LevelWork& l) { return l.r32.p; }
   static float* y(LevelWork& l) { return l.y32.p; }
+  static float* gV(LevelWork& l) { return l.gV32.p; }
+  static float* gZ(LevelWork& l) { return l.gZ32.p; }
   static const float* Ainv(const tomg_problem* P) { return P->Ainv32.p; }
   static Ebe ebe(const tomg_problem* P) {
     Ebe op{P->dim, P->nx, P->ny, P->nz, P->Ke32.p, P->E32.p, P->mask.p, P->ebe_tile,
@@ -173,6 +177,29 @@ void prolong_add(tomg_problem* P, cudaStream_t s, int l, const T* xc, T* x, cons
   else bsr_spmv_rect<T>(s, Lv.Pmat(C.nn), V<T>::Pv(Lv), xc, x, 1, done);
 }
 
+// out = x0 + (m steps of point-block-Jacobi right-preconditioned GMRES on A_l from x0, whose
+// initial residual r0 is given); x0 = nullptr means x0 = 0 (r0 = b)
+template <class T>
+void gmres_smooth(tomg_problem* P, Work& W, int l, const T* r0, const T* x0, T* out,
+                  const int* done) {
+  Level& Lv = *P->L[l];
+  LevelWork& lw = W.lw[l];
+  cudaStream_t s = W.stream;
+  const int m = P->opt.gmres_steps;
+  const int64_t n = Lv.n;
+  T* Vb = V<T>::gV(lw);
+  T* Zb = V<T>::gZ(lw);
+  GmState* st = lw.gst.p;
+  gmres_smooth_begin<T>(s, n, r0, lw.gparts.p, st, m, done);
+  for (int j = 0; j < m; j++) {
+    gmres_smooth_next<T>(s, Lv.b, Lv.nn, j, j == 0 ? r0 : Vb + (int64_t)j * n, Vb, n, Zb,
+                         V<T>::D(Lv), st, done);
+    level_op<T>(P, s, l, MODE_APPLY, Zb + (int64_t)j * n, Vb + (int64_t)(j + 1) * n, nullptr, done);
+    gmres_smooth_orth<T>(s, n, j, m, Vb, n, lw.gparts.p, st, done);
+  }
+  gmres_smooth_finish<T>(s, n, m, Zb, n, st, x0, out, done);
+}
+
 // V-cycle of Algorithm 1: out = MG(b) on level l (x = 0 initial guess), work vectors of slot W
 template <class T>
 void vcycle(tomg_problem* P, Work& W, int l, const T* b, T* out, const int* done) {
@@ -191,6 +218,19 @@ void vcycle(tomg_problem* P, Work& W, int l, const T* b, T* out, const int* done
   }
   T* x = V<T>::x(lw);
   T* r = V<T>::r(lw);
+  if (P->opt.smoother == 2) {
+    // GMRES smoothing: from x = 0 before the coarse correction (r_0 = b), from the corrected
+    // iterate after it (r_0 = b - A x)
+    gmres_smooth<T>(P, W, l, b, nullptr, x, done);
+    level_op<T>(P, s, l, MODE_RESID, x, r, b, done);
+    LevelWork& cw = W.lw[l + 1];
+    restrict_to<T>(P, s, l, r, V<T>::b(cw), done);
+    vcycle<T>(P, W, l + 1, V<T>::b(cw), V<T>::y(cw), done);
+    prolong_add<T>(P, s, l, V<T>::y(cw), x, done);
+    level_op<T>(P, s, l, MODE_RESID, x, r, b, done);
+    gmres_smooth<T>(P, W, l, r, x, out, done);
+    return;
+  }
   if (P->opt.smoother == 1) {
     // Chebyshev smoothing (m steps of Chebyshev acceleration, the same polynomial before and
     // after the coarse correction), each step one fused residual + update launch writing the
@@ -653,7 +693,8 @@ void setup(tomg_problem* P, const tomg_options& opt) {
   if (!(opt.rtol > 0.0) || opt.max_iter < 1 || opt.max_iter > 1000000 || !(opt.omega > 0.0) ||
       !(opt.omega < 2.0) || opt.n_pre < 1 || opt.n_pre > 8 || opt.n_post < 1 || opt.n_post > 8 ||
       opt.max_coarse_dofs < 1 || opt.max_levels < 1 || opt.max_levels > 64 || opt.smoother < 0 ||
-      opt.smoother > 1 || opt.concurrency < 0 || opt.concurrency > 64 ||
+      opt.smoother > 2 || opt.concurrency < 0 || opt.concurrency > 64 ||
+      (opt.smoother == 2 && (opt.gmres_steps < 1 || opt.gmres_steps > GM_MAX)) ||
       (opt.smoother == 1 && (opt.cheb_degree < 1 || opt.cheb_degree > 8 ||
                              !(opt.cheb_lower > 0.0) || !(opt.cheb_upper > opt.cheb_lower))) ||
       (opt.adaptive_geo != 0 && (opt.adaptive_iters < 1 || opt.adaptive_min_geo < 1)) ||
@@ -812,6 +853,19 @@ Work& ensure_work(tomg_problem* P, int k) {
       const int64_t n = P->L[l]->n;
       for (auto* v : {&lw.b64, &lw.x64, &lw.r64, &lw.y64}) v->resize(n);
       for (auto* v : {&lw.b32, &lw.x32, &lw.r32, &lw.y32}) v->resize(n);
+      if (P->opt.smoother == 2 && !P->jacobi_only && l + 1 < P->L.size()) {
+        const int m = P->opt.gmres_steps;
+        if (P->opt.prec == TOMG_PREC_FP64) {
+          lw.gV64.resize((m + 1) * n);
+          lw.gZ64.resize(m * n);
+        } else {
+          lw.gV32.resize((m + 1) * n);
+          lw.gZ32.resize(m * n);
+        }
+        lw.gparts.resize(gmres_smooth_parts(n));
+        lw.gst.resize(1);
+        CK(cudaMemsetAsync(lw.gst.p, 0, sizeof(GmState), W.stream));
+      }
     }
     destroy_graph(W);
     W.built_for = P->setup_gen;
@@ -840,7 +894,9 @@ void init_solve(tomg_problem* P, Work& W, int max_iter) {
   memset(&h, 0, sizeof(h));
   h.rtol2 = P->opt.rtol * P->opt.rtol;
   h.max_iter = max_iter;
-  h.flexible = P->opt.prec == TOMG_PREC_FP64 ? 0 : 1;
+  // the FP64 V-cycle is a fixed symmetric operator (PCG) unless the GMRES smoother makes it
+  // depend on its input
+  h.flexible = (P->opt.prec == TOMG_PREC_FP64 && P->opt.smoother != 2) ? 0 : 1;
   *W.sc_host = h;
   CK(cudaMemcpyAsync(W.sc.p, W.sc_host, sizeof(Scalars), cudaMemcpyHostToDevice, s));
   finish(s, FIN_INIT, W.partA.p, red_blocks(n), W.partB.p, red_blocks(n), W.sc.p);

@@ -80,6 +80,10 @@ struct Level {
 struct LevelWork {
   DBuf<double> b64, x64, r64, y64;
   DBuf<float> b32, x32, r32, y32;
+  // GMRES smoother: Arnoldi basis (m + 1 vectors), preconditioned basis (m), scratch, state
+  DBuf<double> gV64, gZ64, gparts;
+  DBuf<float> gV32, gZ32;
+  DBuf<GmState> gst;
 };
 
 // One solve slot: stream, outer Krylov vectors, V-cycle work, scalars and captured iteration

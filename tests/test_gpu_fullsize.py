@@ -1,8 +1,9 @@
 """GPU parity at the full workload sizes, in the launch configuration the bench times.
 
 * 2D cantilever 768x384 (592,130 DOFs), hybrid hierarchy (one geometric coarsening, SA-AMG to
-  < 1500 DOFs), FP32 V-cycle in FP64 flexible CG and the FP64 PCG: against the oracle's sparse
-  direct solve (u and compliance to 1e-6) and its assembled CSR residual (1e-8).
+  < 1500 DOFs), FP32 V-cycle in FP64 flexible CG and the FP64 PCG, with the degree-2 Chebyshev
+  smoother the bench times and the paper's Jacobi sweep: against the oracle's sparse direct
+  solve (u and compliance to 1e-6) and its assembled CSR residual (1e-8).
 * 3D cantilever 192x96x96 (5,447,811 DOFs) and the 16 right-hand sides of the batched 128x64x64
   case (1,635,075 DOFs each): K is too large to assemble on the host, so the oracle evaluates
   sampled rows of b - K u element by element (oracle.fem.masked_apply_rows, pinned against
@@ -36,11 +37,12 @@ def relerr(a, b):
     return np.linalg.norm(np.asarray(a) - np.asarray(b)) / np.linalg.norm(b)
 
 
+@pytest.mark.parametrize("smoother", ["chebyshev", "jacobi"])
 @pytest.mark.parametrize("prec", ["fp32", "fp64"])
-def test_cantilever2d_full_vs_direct(lib, ctx, cant2d, prec):
+def test_cantilever2d_full_vs_direct(lib, ctx, cant2d, prec, smoother):
     p, ref = cant2d
     P = lib.Problem.from_workload(ctx, p)
-    P.setup(prec=prec, **HEADLINE)
+    P.setup(prec=prec, smoother=smoother, cheb_degree=2, **HEADLINE)
     u, res = P.solve(p.f)
     r = res[0]
     assert r["status"] == 0 and r["rel_residual"] <= 1e-8, r
@@ -73,10 +75,11 @@ def check_sampled(lib, P, p, u, f, nodes):
     assert np.all(np.abs(Ku - rows) <= 1e-13 * scale + 1e-300)
 
 
-def test_cantilever3d_full_sampled(lib, ctx):
+@pytest.mark.parametrize("prec", ["fp32", "tf32x3"])
+def test_cantilever3d_full_sampled(lib, ctx, prec):
     p = W.cantilever_3d(192, 96, 96, seed=0)
     P = lib.Problem.from_workload(ctx, p)
-    P.setup(pc="hybrid", prec="fp32", n_geo_levels=3, max_coarse_dofs=1000, rtol=1e-8)
+    P.setup(pc="hybrid", prec=prec, n_geo_levels=3, max_coarse_dofs=1000, rtol=1e-8)
     u, res = P.solve(p.f)
     r = res[0]
     assert r["status"] == 0 and r["rel_residual"] <= 1e-8, r
@@ -84,11 +87,14 @@ def test_cantilever3d_full_sampled(lib, ctx):
     assert abs(r["compliance"] - p.f[0] @ u[0]) <= 1e-12 * abs(p.f[0] @ u[0])
 
 
-def test_batched_full_sampled(lib, ctx):
+@pytest.mark.parametrize("prec,smoother", [("fp32", "jacobi"), ("tf32x3", "chebyshev")])
+def test_batched_full_sampled(lib, ctx, prec, smoother):
+    """Both the paper's configuration and the one the bench times (3xTF32 tensor-core operator,
+    degree-2 Chebyshev, 4 concurrent slots)."""
     p = W.batched_3d()
     P = lib.Problem.from_workload(ctx, p)
-    P.setup(pc="hybrid", prec="fp32", n_geo_levels=3, max_coarse_dofs=1000, rtol=1e-8,
-            concurrency=4)
+    P.setup(pc="hybrid", prec=prec, n_geo_levels=3, max_coarse_dofs=1000, rtol=1e-8,
+            concurrency=4, smoother=smoother)
     u, res = P.solve(p.f)
     assert len(res) == 16
     for j in range(16):
@@ -96,8 +102,8 @@ def test_batched_full_sampled(lib, ctx):
         check_sampled(lib, P, p, u[j], p.f[j], sampled_nodes(p, p.f[j], 300, 100 + j))
     # the slots share the hierarchy and each runs its own graph: the result of a right-hand
     # side does not depend on how many run at once
-    P.setup(pc="hybrid", prec="fp32", n_geo_levels=3, max_coarse_dofs=1000, rtol=1e-8,
-            concurrency=1)
+    P.setup(pc="hybrid", prec=prec, n_geo_levels=3, max_coarse_dofs=1000, rtol=1e-8,
+            concurrency=1, smoother=smoother)
     u1, res1 = P.solve(p.f[:3])
     for j in range(3):
         assert res1[j]["iterations"] == res[j]["iterations"]
