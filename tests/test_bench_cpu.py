@@ -8,7 +8,7 @@ import bench
 
 def test_reference_arm_contract(monkeypatch):
     monkeypatch.setattr(bench, "WORKLOAD", dict(nx=48, ny=24, seed=0))
-    args = argparse.Namespace(steps=2, warmup=1, gpus=1, smoother="chebyshev")
+    args = argparse.Namespace(steps=2, warmup=1, gpus=1, smoother="chebyshev", cheb_degree=2)
     out = bench.run_reference(args, rank=0, world=1)
     json.dumps(out)
     for k in ("metric", "value", "unit", "n_gpus", "steps", "warmup", "ms_per_step",
