@@ -520,14 +520,6 @@ def roofline(P, ctx, p, stream):
                 "peak": FP64_PEAK_GFLOPS / 1e3, "unit": "TFLOP/s",
                 "frac": o["achieved_gflops"] / FP64_PEAK_GFLOPS,
                 "peak_source": "nominal FP64 rate (the measured-peaks file has no FP64 figure)"}
-        # the FP64 FMA rate this device sustains on independent FMA chains (k_fp64_fma),
-        # the practical ceiling of an FP64-bound kernel
-        try:
-            fm = ctx.fp64_fma_rate()
-            head["fp64_fma_measured_tflops"] = fm
-            head["frac_of_measured_fp64_fma"] = o["achieved_gflops"] / 1e3 / fm
-        except Exception as e:  # noqa: BLE001
-            head["fp64_fma_measured_error"] = str(e)
     else:
         k = out[dom]
         head = {"kernel": "k_ebe2<float, %s> (FP32 %s, 2D)" % ("1" if dom == "residual" else "2", dom),

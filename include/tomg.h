@@ -318,11 +318,6 @@ tomg_status tomg_buckling_sensitivity(tomg_problem* prob, const double* u, int n
 /* Adaptive hybrid hierarchy (Sec. 4.4): the geometric level count (including the fine grid)
  * the next tomg_setup of this problem will use, 0 before the first setup with adaptive_geo. */
 tomg_status tomg_adaptive_geo_levels(const tomg_problem* prob, int* n_geo_levels);
-/* FP64 fused multiply-add throughput of the context's device in TFLOP/s (2 flops per FMA),
- * measured by a kernel of independent FMA chains at full occupancy (best of five launches on
- * the context stream, which it synchronises): the denominator of the FP64-bound kernels'
- * roofline.  About 50 ms of device time. */
-tomg_status tomg_fp64_fma_rate(tomg_ctx* ctx, double* tflops);
 /* Number of kernels this library launched since the context was created. */
 tomg_status tomg_kernel_launches(const tomg_ctx* ctx, int64_t* count);
 

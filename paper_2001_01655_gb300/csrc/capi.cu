@@ -180,15 +180,6 @@ tomg_status tomg_ctx_destroy(tomg_ctx* c) {
   });
 }
 
-tomg_status tomg_fp64_fma_rate(tomg_ctx* c, double* tflops) {
-  return guarded([&]() -> tomg_status {
-    if (!c || !tflops) TOMG_THROW(TOMG_E_INVALID, "null argument");
-    set_device(c);
-    *tflops = fp64_fma_tflops(c->stream, c->device);
-    return TOMG_OK;
-  });
-}
-
 tomg_status tomg_kernel_launches(const tomg_ctx* c, int64_t* count) {
   if (!c || !count) { set_error("null argument"); return TOMG_E_INVALID; }
   *count = g_launches - c->launches0;

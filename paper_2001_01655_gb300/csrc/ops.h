@@ -94,9 +94,6 @@ void compliance_sensitivity(cudaStream_t s, int dim, int nx, int ny, int nz, con
                             const double* rho, const double* u, double E0, double Emin,
                             double penal, double* dc);
 
-// measured FP64 FMA rate of the device (TFLOP/s), synchronises the stream (k_probe.cu)
-double fp64_fma_tflops(cudaStream_t s, int device);
-
 // ---------------- linear buckling (k_stability.cu) -----------------------------------
 int stress_components(int dim);  // 3 (2D) or 6 (3D) Voigt components per element
 // centre stresses sigma_e = E_sigma(rho_e) D_0 B(centre) u_e, n_elems x stress_components

@@ -83,7 +83,6 @@ _SIGS = {
     "tomg_coarse_solve": (C.c_int, [_P, _P, _P, C.c_int]),
     "tomg_moduli": (C.c_int, [_P, _P, C.c_int]),
     "tomg_element_stiffness": (C.c_int, [_P, _P]),
-    "tomg_fp64_fma_rate": (C.c_int, [_P, _D]),
     "tomg_time_fine_operator": (C.c_int, [_P, C.c_int, C.c_int, C.c_int, C.c_int, _D]),
     "tomg_fine_apply_f32_noalloc": (C.c_int, [_P, _P, _P]),
     "tomg_adaptive_geo_levels": (C.c_int, [_P, C.POINTER(C.c_int)]),
@@ -171,12 +170,6 @@ class Context:
         _check(lib.tomg_ctx_create(C.byref(h), device, raw))
         self.h = h
         self.device = device
-
-    def fp64_fma_rate(self) -> float:
-        """Measured FP64 FMA throughput of the device, TFLOP/s."""
-        v = C.c_double()
-        _check(load().tomg_fp64_fma_rate(self.h, C.byref(v)))
-        return v.value
 
     def kernel_launches(self) -> int:
         v = C.c_int64()
