@@ -463,34 +463,44 @@ void amg_tentative(cudaStream_t s, int n, int b, int k, int n_agg, const int* ag
   CK(cudaStreamSynchronize(s));
 }
 
-double amg_spectral_radius(cudaStream_t s, const Bsr& A, const double* V, const double* Dinv,
-                           int level, int iters, double* v, double* w, double* partials) {
+void amg_power_alloc(cudaStream_t s, AmgPower& ps, const Bsr& A, int iters) {
+  const int64_t n = (int64_t)A.nbr * A.br;
+  const int gb = ceil_div((int64_t)A.nbr * 8, 256);
+  ps.iters = iters;
+  ps.v.resize(n);
+  ps.w.resize(n);
+  ps.parts.resize(std::max(gb, 256));
+  ps.nrm.resize(2 * (iters + 1));
+  ps.ticket.resize(1);
+  ps.ticket.zero(s);
+}
+
+void amg_power_enqueue(cudaStream_t s, AmgPower& ps, const Bsr& A, const double* V,
+                       const double* Dinv, int level) {
   // u_0 = splitmix64 vector; step: w = (1/||u_it||) D^-1 A u_it, rho_it = ||w||, u_{it+1} = w.
   // Norms and their reciprocals stay on the device; the host reads the last rho only.
-  (void)partials;
   const int64_t n = (int64_t)A.nbr * A.br;
   const int gb = ceil_div((int64_t)A.nbr * 8, 256);
   const int gp = 256;
-  DBuf<double> parts, nrm;
-  DBuf<unsigned> ticket;
-  parts.resize(std::max(gb, gp));
-  nrm.resize(2 * (iters + 1));
-  ticket.resize(1);
-  ticket.zero(s);
+  double* v = ps.v.p;
+  double* w = ps.w.p;
   LAUNCH(k_power_init, ceil_div(n, 256), 256, 0, s, n, level, v);
-  LAUNCH(k_sumsq_partials, gp, 256, 0, s, n, v, parts.p);
-  LAUNCH(k_norm_finish, 1, 256, 0, s, parts.p, gp, nrm.p);
-  for (int it = 0; it < iters; it++) {
-    const double* sc = nrm.p + 2 * it + 1;
-    double* o = nrm.p + 2 * (it + 1);
-    if (A.br == 2) LAUNCH(k_power_step<2>, gb, 256, 0, s, A.nbr, A.rp, A.ci, V, Dinv, v, sc, w, parts.p, o, ticket.p);
-    else if (A.br == 3) LAUNCH(k_power_step<3>, gb, 256, 0, s, A.nbr, A.rp, A.ci, V, Dinv, v, sc, w, parts.p, o, ticket.p);
-    else if (A.br == 6) LAUNCH(k_power_step<6>, gb, 256, 0, s, A.nbr, A.rp, A.ci, V, Dinv, v, sc, w, parts.p, o, ticket.p);
+  LAUNCH(k_sumsq_partials, gp, 256, 0, s, n, v, ps.parts.p);
+  LAUNCH(k_norm_finish, 1, 256, 0, s, ps.parts.p, gp, ps.nrm.p);
+  for (int it = 0; it < ps.iters; it++) {
+    const double* sc = ps.nrm.p + 2 * it + 1;
+    double* o = ps.nrm.p + 2 * (it + 1);
+    if (A.br == 2) LAUNCH(k_power_step<2>, gb, 256, 0, s, A.nbr, A.rp, A.ci, V, Dinv, v, sc, w, ps.parts.p, o, ps.ticket.p);
+    else if (A.br == 3) LAUNCH(k_power_step<3>, gb, 256, 0, s, A.nbr, A.rp, A.ci, V, Dinv, v, sc, w, ps.parts.p, o, ps.ticket.p);
+    else if (A.br == 6) LAUNCH(k_power_step<6>, gb, 256, 0, s, A.nbr, A.rp, A.ci, V, Dinv, v, sc, w, ps.parts.p, o, ps.ticket.p);
     else TOMG_THROW(TOMG_E_INVALID, "unsupported block %d", A.br);
     std::swap(v, w);
   }
+}
+
+double amg_power_result(cudaStream_t s, const AmgPower& ps) {
   double rho = 0.0;
-  CK(cudaMemcpyAsync(&rho, nrm.p + 2 * iters, sizeof(double), cudaMemcpyDeviceToHost, s));
+  CK(cudaMemcpyAsync(&rho, ps.nrm.p + 2 * ps.iters, sizeof(double), cudaMemcpyDeviceToHost, s));
   CK(cudaStreamSynchronize(s));
   if (!(rho > 0.0)) TOMG_THROW(TOMG_E_BREAKDOWN, "power iteration collapsed");
   return rho;
@@ -518,40 +528,57 @@ void splitmix_uniform(cudaStream_t s, int64_t n, int level, double* v) {
   LAUNCH(k_power_init, ceil_div(n, 256), 256, 0, s, n, level, v);
 }
 
-double spectral_radius_op(cudaStream_t s, int64_t nodes, int bs, const double* Dinv, int level,
-                          int iters, const std::function<void(const double*, double*)>& apply) {
+void power_alloc(PowerState& ps, int64_t nodes, int bs, int iters) {
+  const int64_t n = nodes * bs;
+  ps.nodes = nodes;
+  ps.bs = bs;
+  ps.iters = iters;
+  ps.v.resize(n);
+  ps.w.resize(n);
+  ps.t.resize(n);
+  ps.parts.resize(256);
+  ps.nrm.resize(2 * (iters + 1));
+}
+
+void power_enqueue(cudaStream_t s, PowerState& ps, const double* Dinv, int level,
+                   const std::function<void(const double*, double*)>& apply) {
   // the same iteration as amg_spectral_radius, with the operator applied by the caller:
   // u_0 = splitmix64 vector; w = (1/||u_it||) D^-1 A u_it, rho_it = ||w||, u_{it+1} = w
-  const int64_t n = nodes * bs;
+  const int64_t nodes = ps.nodes, n = nodes * ps.bs;
   const int gp = 256;
-  DBuf<double> v, w, t, parts, nrm;
-  v.resize(n);
-  w.resize(n);
-  t.resize(n);
-  parts.resize(gp);
-  nrm.resize(2 * (iters + 1));
-  LAUNCH(k_power_init, ceil_div(n, 256), 256, 0, s, n, level, v.p);
-  LAUNCH(k_sumsq_partials, gp, 256, 0, s, n, v.p, parts.p);
-  LAUNCH(k_norm_finish, 1, 256, 0, s, parts.p, gp, nrm.p);
-  double* a = v.p;
-  double* c = w.p;
-  for (int it = 0; it < iters; it++) {
-    apply(a, t.p);
-    const double* sc = nrm.p + 2 * it + 1;
+  LAUNCH(k_power_init, ceil_div(n, 256), 256, 0, s, n, level, ps.v.p);
+  LAUNCH(k_sumsq_partials, gp, 256, 0, s, n, ps.v.p, ps.parts.p);
+  LAUNCH(k_norm_finish, 1, 256, 0, s, ps.parts.p, gp, ps.nrm.p);
+  double* a = ps.v.p;
+  double* c = ps.w.p;
+  for (int it = 0; it < ps.iters; it++) {
+    apply(a, ps.t.p);
+    const double* sc = ps.nrm.p + 2 * it + 1;
     const int g = ceil_div(nodes, 256);
-    if (bs == 2) LAUNCH(k_dinv_scale<2>, g, 256, 0, s, nodes, Dinv, t.p, sc, c);
-    else if (bs == 3) LAUNCH(k_dinv_scale<3>, g, 256, 0, s, nodes, Dinv, t.p, sc, c);
-    else if (bs == 6) LAUNCH(k_dinv_scale<6>, g, 256, 0, s, nodes, Dinv, t.p, sc, c);
-    else TOMG_THROW(TOMG_E_INVALID, "unsupported block %d", bs);
-    LAUNCH(k_sumsq_partials, gp, 256, 0, s, n, c, parts.p);
-    LAUNCH(k_norm_finish, 1, 256, 0, s, parts.p, gp, nrm.p + 2 * (it + 1));
+    if (ps.bs == 2) LAUNCH(k_dinv_scale<2>, g, 256, 0, s, nodes, Dinv, ps.t.p, sc, c);
+    else if (ps.bs == 3) LAUNCH(k_dinv_scale<3>, g, 256, 0, s, nodes, Dinv, ps.t.p, sc, c);
+    else if (ps.bs == 6) LAUNCH(k_dinv_scale<6>, g, 256, 0, s, nodes, Dinv, ps.t.p, sc, c);
+    else TOMG_THROW(TOMG_E_INVALID, "unsupported block %d", ps.bs);
+    LAUNCH(k_sumsq_partials, gp, 256, 0, s, n, c, ps.parts.p);
+    LAUNCH(k_norm_finish, 1, 256, 0, s, ps.parts.p, gp, ps.nrm.p + 2 * (it + 1));
     std::swap(a, c);
   }
+}
+
+double power_result(cudaStream_t s, const PowerState& ps) {
   double rho = 0.0;
-  CK(cudaMemcpyAsync(&rho, nrm.p + 2 * iters, sizeof(double), cudaMemcpyDeviceToHost, s));
+  CK(cudaMemcpyAsync(&rho, ps.nrm.p + 2 * ps.iters, sizeof(double), cudaMemcpyDeviceToHost, s));
   CK(cudaStreamSynchronize(s));
   if (!(rho > 0.0)) TOMG_THROW(TOMG_E_BREAKDOWN, "power iteration collapsed");
   return rho;
+}
+
+double spectral_radius_op(cudaStream_t s, int64_t nodes, int bs, const double* Dinv, int level,
+                          int iters, const std::function<void(const double*, double*)>& apply) {
+  PowerState ps;
+  power_alloc(ps, nodes, bs, iters);
+  power_enqueue(s, ps, Dinv, level, apply);
+  return power_result(s, ps);
 }
 
 void amg_smooth_prolongator(cudaStream_t s, const Bsr& AT, const double* ATV, const int* agg,

@@ -199,15 +199,37 @@ int amg_aggregate(cudaStream_t s, int n, const int* srp, const int* sci, int lev
 // tentative prolongator: T as BSR (one block per aggregated node), Bc (n_agg*k x k)
 void amg_tentative(cudaStream_t s, int n_nodes, int b, int k, int n_agg, const int* agg,
                    const double* B, int* Trp, int* Tci, double* TV, double* Bc);
-// spectral radius of D^-1 A by power iteration (FP64), returns rho (syncs)
-double amg_spectral_radius(cudaStream_t s, const Bsr& A, const double* V, const double* Dinv,
-                           int level, int iters, double* v, double* w, double* partials);
+// spectral radius of D^-1 A by power iteration (FP64) on an assembled BSR level, in three
+// steps so that the launches can run on another stream than the allocation: amg_power_alloc
+// (buffers and the zeroed ticket, in the order of stream s), amg_power_enqueue (launches on s),
+// amg_power_result (copies rho back on s and synchronises s)
+struct AmgPower {
+  DBuf<double> v, w, parts, nrm;
+  DBuf<unsigned> ticket;
+  int iters = 0;
+};
+void amg_power_alloc(cudaStream_t s, AmgPower& ps, const Bsr& A, int iters);
+void amg_power_enqueue(cudaStream_t s, AmgPower& ps, const Bsr& A, const double* V,
+                       const double* Dinv, int level);
+double amg_power_result(cudaStream_t s, const AmgPower& ps);
 // v[i] = (splitmix64(i + SALT_POWER + level) >> 11) 2^-53 - 0.5 (the power-iteration start vector)
 void splitmix_uniform(cudaStream_t s, int64_t n, int level, double* v);
 // spectral radius of D^-1 A for an operator applied by `apply(x, y)` (y = A x, FP64, n = nodes *
 // bs), same start vector and iteration as amg_spectral_radius; returns rho (syncs)
 double spectral_radius_op(cudaStream_t s, int64_t nodes, int bs, const double* Dinv, int level,
                           int iters, const std::function<void(const double*, double*)>& apply);
+// the same iteration in two halves, so that it can run on another stream than the one that
+// allocates its buffers: power_alloc (allocation-stream order), power_enqueue (launches only, on
+// s), power_result (copies rho back on s and synchronises s)
+struct PowerState {
+  DBuf<double> v, w, t, parts, nrm;
+  int64_t nodes = 0;
+  int bs = 0, iters = 0;
+};
+void power_alloc(PowerState& ps, int64_t nodes, int bs, int iters);
+void power_enqueue(cudaStream_t s, PowerState& ps, const double* Dinv, int level,
+                   const std::function<void(const double*, double*)>& apply);
+double power_result(cudaStream_t s, const PowerState& ps);
 // P = T - omega Dinv (A T) on the pattern of AT
 void amg_smooth_prolongator(cudaStream_t s, const Bsr& AT, const double* ATV, const int* agg,
                             const double* TV, const int* Trp, const double* Dinv, double omega,

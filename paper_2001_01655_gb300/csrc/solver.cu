@@ -139,6 +139,30 @@ struct TcScope {
   ~TcScope() { P->tc_mode = saved; }
 };
 
+// the setup's side streams and their events, created on first use
+void ensure_side_streams(tomg_problem* P) {
+  if (P->side) return;
+  CK(cudaStreamCreateWithFlags(&P->side, cudaStreamNonBlocking));
+  CK(cudaStreamCreateWithFlags(&P->side2, cudaStreamNonBlocking));
+  for (cudaEvent_t* e : {&P->ev_fork, &P->ev_side, &P->ev_fork2, &P->ev_side2})
+    CK(cudaEventCreateWithFlags(e, cudaEventDisableTiming));
+}
+
+// Makes stream `s` wait for event `ev` (recorded on another stream) once: at join(), or when
+// the guard goes out of scope, including on an exception.
+struct StreamJoin {
+  cudaStream_t s = nullptr;
+  cudaEvent_t ev = nullptr;
+  void arm(cudaStream_t s_, cudaEvent_t ev_) { s = s_; ev = ev_; }
+  void join() {
+    if (ev) CK(cudaStreamWaitEvent(s, ev, 0));
+    ev = nullptr;
+  }
+  ~StreamJoin() {
+    if (ev) cudaStreamWaitEvent(s, ev, 0);
+  }
+};
+
 template <class T>
 void level_op(tomg_problem* P, cudaStream_t s, int l, int mode, const T* x, T* y, const T* b,
               const int* done, const ChebArg* ch = nullptr) {
@@ -495,6 +519,19 @@ void amg_extend(tomg_problem* P, int start) {
     Level& A = *P->L[cur];
     const Bsr Ab = A.bsr();
     const int nn = (int)A.nn, b = A.b;
+    // rho(D^-1 A) for the prolongator smoothing (and a Chebyshev smoother on this level) reads
+    // only this level's operator: it runs on the second side stream during the strength,
+    // aggregation, tentative prolongator and A T phases and is joined before the smoothing
+    // (the guard joins on every exit from this step, before the buffers are released)
+    AmgPower rho_pw;
+    StreamJoin rho_join;
+    ensure_side_streams(P);
+    amg_power_alloc(s, rho_pw, Ab, 20);
+    CK(cudaEventRecord(P->ev_fork2, s));
+    CK(cudaStreamWaitEvent(P->side2, P->ev_fork2, 0));
+    amg_power_enqueue(P->side2, rho_pw, Ab, A.V64.p, A.D64.p, cur);
+    CK(cudaEventRecord(P->ev_side2, P->side2));
+    rho_join.arm(s, P->ev_side2);
     // strength of connection (Eq. 10)
     DBuf<int> scnt, srp, sci;
     scnt.resize(nn);
@@ -523,18 +560,17 @@ void amg_extend(tomg_problem* P, int start) {
     CK(cudaStreamSynchronize(s));
     Bsr Tm;
     Tm.nbr = nn; Tm.nbc = n_agg; Tm.br = b; Tm.bc = k; Tm.nnzb = nT; Tm.rp = Trp.p; Tm.ci = Tci.p;
-    // prolongator smoothing weight from rho(D^-1 A)
-    DBuf<double> pv, pw, parts;
-    pv.resize(A.n); pw.resize(A.n); parts.resize(std::max(ceil_div(nn, 256), 256));
     tr.mark("tentative", cur);
-    const double rho = amg_spectral_radius(s, Ab, A.V64.p, A.D64.p, cur, 20, pv.p, pw.p, parts.p);
-    A.lam = rho;  // the same estimate bounds a Chebyshev smoother on this level
-    const double omegaP = 4.0 / (3.0 * rho);
-    tr.mark("spectral_radius", cur);
     // P = T - omega D^-1 A T
     OwnedBsr AT;
     spgemm_full(s, Ab, A.V64.p, Tm, TV.p, AT);
     tr.mark("A*T", cur);
+    // prolongator smoothing weight from rho(D^-1 A)
+    rho_join.join();
+    const double rho = amg_power_result(s, rho_pw);
+    A.lam = rho;  // the same estimate bounds a Chebyshev smoother on this level
+    const double omegaP = 4.0 / (3.0 * rho);
+    tr.mark("spectral_radius", cur);
     A.Pnnzb = AT.m.nnzb;
     A.Prp = std::move(AT.rp);
     A.Pci = std::move(AT.ci);
@@ -706,6 +742,9 @@ void setup(tomg_problem* P, const tomg_options& opt) {
   P->opt = opt;
   CK(cudaEventRecord(P->ev0, s));
   SetupTrace tr(s);
+  // side-stream power iterations (declared before the join guard, released after it)
+  std::vector<PowerState> cheb_pw;
+  StreamJoin side_join;
   P->L.clear();
   P->jacobi_only = (opt.pc == TOMG_PC_JACOBI);
   // level 0: matrix-free SIMP operator
@@ -768,6 +807,28 @@ void setup(tomg_problem* P, const tomg_options& opt) {
       P->L.push_back(std::move(C));
       tr.mark("geometric RAP", l);
     }
+    // Chebyshev bounds of the geometric levels above the last one: they read only those
+    // levels, so their power iterations run on the side stream while the algebraic levels and
+    // the coarse inverse are built (phases with many host synchronisations and small kernels;
+    // the last geometric level gets its estimate from the prolongator smoothing, or is the
+    // coarsest).  The guard makes the problem stream wait for the side stream on every exit,
+    // before any of the buffers involved is released.
+    if (opt.smoother == 1 && n_geo >= 2) {
+      ensure_side_streams(P);
+      cheb_pw.resize(n_geo - 1);
+      for (int l = 0; l + 1 < n_geo; l++)
+        power_alloc(cheb_pw[l], P->L[l]->nn, P->L[l]->b, 20);
+      CK(cudaEventRecord(P->ev_fork, s));
+      CK(cudaStreamWaitEvent(P->side, P->ev_fork, 0));
+      for (int l = 0; l + 1 < n_geo; l++) {
+        Level& Lv = *P->L[l];
+        power_enqueue(P->side, cheb_pw[l], Lv.D64.p, l, [&](const double* xv, double* yv) {
+          level_op<double>(P, P->side, l, MODE_APPLY, xv, yv, nullptr, nullptr);
+        });
+      }
+      CK(cudaEventRecord(P->ev_side, P->side));
+      side_join.arm(s, P->ev_side);
+    }
     if (opt.pc == TOMG_PC_AMG || opt.pc == TOMG_PC_HYBRID) amg_extend(P, (int)P->L.size() - 1);
     tr.mark("amg total");
     // coarsest level: dense FP64 Cholesky -> explicit inverse
@@ -788,9 +849,12 @@ void setup(tomg_problem* P, const tomg_options& opt) {
     if (opt.smoother == 1) {
       // Chebyshev smoother on every level above the coarsest: lambda_max(D^-1 A_l) by 20 power
       // iterations, interval [lower, upper] x lambda, three-term recurrence coefficients
+      side_join.join();
       for (int l = 0; l + 1 < (int)P->L.size(); l++) {
         Level& Lv = *P->L[l];
-        if (!(Lv.lam > 0.0))  // levels coarsened by aggregation have it already
+        if (l < (int)cheb_pw.size())  // estimated on the side stream, now joined
+          Lv.lam = power_result(s, cheb_pw[l]);
+        else if (!(Lv.lam > 0.0))  // levels coarsened by aggregation have it already
           Lv.lam = spectral_radius_op(s, Lv.nn, Lv.b, Lv.D64.p, l, 20,
                                       [&](const double* xv, double* yv) {
                                         level_op<double>(P, s, l, MODE_APPLY, xv, yv, nullptr, nullptr);
@@ -1522,7 +1586,7 @@ tomg_problem::~tomg_problem() {
   works.clear();
   L.clear();
   if (flag_host) cudaFreeHost(flag_host);
-  for (cudaEvent_t e : {ev0, ev1, ev_in, ev_out})
+  for (cudaEvent_t e : {ev0, ev1, ev_in, ev_out, ev_fork, ev_side, ev_fork2, ev_side2})
     if (e) cudaEventDestroy(e);
   // device buffers are released by their destructors on this stream before it is destroyed
   Ke64.release(); Ke32.release(); mask.release(); rho.release(); E64.release(); E32.release();
@@ -1531,4 +1595,9 @@ tomg_problem::~tomg_problem() {
     cudaStreamSynchronize(stream);
     cudaStreamDestroy(stream);
   }
+  for (cudaStream_t q : {side, side2})
+    if (q) {
+      cudaStreamSynchronize(q);
+      cudaStreamDestroy(q);
+    }
 }

@@ -119,6 +119,10 @@ struct tomg_problem {
   tomg_ctx* ctx = nullptr;
   cudaStream_t stream = nullptr;  // the problem's own stream
   cudaEvent_t ev_in = nullptr, ev_out = nullptr;
+  // setup work that overlaps the rest of the setup (created on first use): the Chebyshev
+  // bounds of the geometric levels on `side`, the AMG levels' spectral radii on `side2`
+  cudaStream_t side = nullptr, side2 = nullptr;
+  cudaEvent_t ev_fork = nullptr, ev_side = nullptr, ev_fork2 = nullptr, ev_side2 = nullptr;
   int dim = 2, nx = 0, ny = 0, nz = 1;
   double E0 = 1, Emin = 1e-9, penal = 3, nu = 0.3;
   int64_t nn = 0, n = 0, nel = 0;
