@@ -269,11 +269,15 @@ __device__ __forceinline__ double rsqrt_newton(double d) {
 __global__ void __launch_bounds__(NB * NB) k_potrf_diag(int n, int k0, double* A, double* Linv,
                                                         int* fail) {
   __shared__ double s[NB][NB + 1];
+  // L_kk^-1, built alongside the factorisation: row r holds e_r - sum_{t<k} L[r][t] X[t][.] until
+  // step r scales it into row r of X = L^-1 (forward substitution in right-looking order, so the
+  // dependent chain is one FMA per pivot instead of one per entry of a row)
   __shared__ double li[NB][NB + 1];
   __shared__ double rdiag[NB];
   const int tx = threadIdx.x, ty = threadIdx.y;
   const int kb = min(NB, n - k0);
   s[ty][tx] = (ty < kb && tx < kb) ? A[(int64_t)(k0 + ty) * n + k0 + tx] : (ty == tx ? 1.0 : 0.0);
+  li[ty][tx] = ty == tx ? 1.0 : 0.0;
   __syncthreads();
   // every pivot needs 1 / sqrt(d); everything else multiplies by it
   for (int k = 0; k < NB; k++) {
@@ -288,21 +292,13 @@ __global__ void __launch_bounds__(NB * NB) k_potrf_diag(int n, int k0, double* A
       rdiag[k] = y;
     }
     __syncthreads();
-    if (tx == k && ty > k) s[ty][k] *= rdiag[k];
+    if (tx == k && ty > k) s[ty][k] *= rdiag[k];    // column k of L
+    if (ty == k && tx <= k) li[k][tx] *= rdiag[k];  // row k of L^-1
     __syncthreads();
     if (ty > k && tx > k && tx <= ty) s[ty][tx] -= s[ty][k] * s[tx][k];
+    if (ty > k && tx <= k) li[ty][tx] -= s[ty][k] * li[k][tx];
     __syncthreads();
   }
-  if (ty == 0) {  // column tx of L_kk^-1
-    const int c = tx;
-    for (int r = 0; r < NB; r++) {
-      if (r < c) { li[r][c] = 0.0; continue; }
-      double v = (r == c) ? 1.0 : 0.0;
-      for (int t = c; t < r; t++) v -= s[r][t] * li[t][c];
-      li[r][c] = v * rdiag[r];
-    }
-  }
-  __syncthreads();
   if (ty < kb && tx < kb) A[(int64_t)(k0 + ty) * n + k0 + tx] = (tx <= ty) ? s[ty][tx] : 0.0;
   Linv[ty * NB + tx] = li[ty][tx];
 }
