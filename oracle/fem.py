@@ -126,15 +126,25 @@ def element_dofs(dim, nx, ny, nz):
     return np.stack(cols, axis=1).astype(np.int64)
 
 
-def assemble(dim, nx, ny, nz, E, Ke):
-    """K = sum_e E_e * Ke scattered to global DOFs, as a scipy CSR matrix (Sec. 2.1, 3.1)."""
-    _, _, n = grid_counts(dim, nx, ny, nz)
+def assemble(dim, nx, ny, nz, E, Ke, chunk=1 << 19):
+    """K = sum_e E_e * Ke scattered to global DOFs, as a scipy CSR matrix (Sec. 2.1, 3.1).
+    The sum runs over consecutive groups of at most ``chunk`` elements, each group scattered
+    and added to K (the same sum; it only bounds the host memory of the scatter on grids of
+    millions of elements)."""
+    _, nel, n = grid_counts(dim, nx, ny, nz)
     edofs = element_dofs(dim, nx, ny, nz)
     nd = edofs.shape[1]
-    rows = np.repeat(edofs, nd, axis=1).ravel()
-    cols = np.tile(edofs, (1, nd)).ravel()
-    vals = (np.asarray(E)[:, None] * Ke.ravel()[None, :]).ravel()
-    K = sp.coo_matrix((vals, (rows, cols)), shape=(n, n)).tocsr()
+    E = np.asarray(E, dtype=np.float64)
+    K = None
+    for e0 in range(0, nel, chunk):
+        ed = edofs[e0:e0 + chunk]
+        rows = np.repeat(ed, nd, axis=1).ravel()
+        cols = np.tile(ed, (1, nd)).ravel()
+        vals = (E[e0:e0 + chunk, None] * Ke.ravel()[None, :]).ravel()
+        part = sp.coo_matrix((vals, (rows, cols)), shape=(n, n)).tocsr()
+        part.sum_duplicates()
+        del rows, cols, vals
+        K = part if K is None else (K + part).tocsr()
     K.sum_duplicates()
     return K
 
@@ -176,10 +186,20 @@ def free_mask(n, fixed):
 
 
 def masked_operator(K, fixed):
-    """A = M K M + (I - M): identity rows/columns on fixed DOFs, K elsewhere."""
+    """A = M K M + (I - M): identity rows/columns on fixed DOFs, K elsewhere.  Entry (i, j) of
+    K is scaled by m_i m_j in place of the two diagonal products, and the diagonal entries of
+    fixed DOFs (present in K, every DOF belongs to an element) are set to 1."""
     m = free_mask(K.shape[0], fixed)
-    Mm = sp.diags(m)
-    return (Mm @ K @ Mm + sp.diags(1.0 - m)).tocsr()
+    A = K.tocsr(copy=True)
+    A.sum_duplicates()
+    rows = np.repeat(np.arange(A.shape[0]), np.diff(A.indptr))
+    A.data *= m[rows] * m[A.indices]
+    del rows
+    fx = np.flatnonzero(m == 0.0)
+    if fx.size:
+        A[fx, fx] = 1.0
+    A.eliminate_zeros()
+    return A
 
 
 def stiffness(problem):
