@@ -192,6 +192,14 @@ tomg_status tomg_server_wait(tomg_server* srv, uint64_t ticket, int timeout_ms,
 tomg_status tomg_server_stats(tomg_server* srv, double* p50_ms, double* p99_ms,
                               double* solves_per_s, int64_t* completed, int* peak_active,
                               size_t* peak_bytes);
+/* Waits (timeout_ms < 0: no limit) until `prob` has no queued or running request, then frees
+ * the warm start the server keeps for it and stops counting its device memory against the
+ * budget: the client is done with this problem (destroy it, or keep it outside the server).
+ * While a problem is resident, i.e. after its first update and until it is retired, its
+ * measured device bytes (hierarchy, solve slots, warm start) count against the budget; a
+ * request of a problem that is not resident yet is admitted only when its estimated footprint
+ * fits beside them.  E_TIMEOUT if requests remain after the limit. */
+tomg_status tomg_server_retire(tomg_server* srv, tomg_problem* prob, int timeout_ms);
 tomg_status tomg_server_destroy(tomg_server* srv);
 
 /* ---- hierarchy introspection and single steps (parity checking) ------------------------- */

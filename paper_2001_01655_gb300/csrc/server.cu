@@ -51,6 +51,12 @@ struct tomg_server {
   std::map<uint64_t, std::shared_ptr<tomg::Request>> tickets;
   std::map<tomg_problem*, bool> busy;
   std::map<tomg_problem*, tomg::DBuf<double>*> warm;  // device-resident previous solutions
+  // device bytes each problem holds between its updates (hierarchy, solve slots, warm start),
+  // measured after its latest update; requests of problems not yet resident count with their
+  // estimated footprint while in flight
+  std::map<tomg_problem*, size_t> resident;
+  std::map<tomg_problem*, int> pending;  // queued + running requests per problem
+  size_t resident_total = 0;
   size_t in_flight = 0, peak_in_flight = 0;
   int active = 0, peak_active = 0;
   uint64_t next_ticket = 1;
@@ -64,14 +70,23 @@ struct tomg_server {
 namespace tomg {
 namespace {
 
-// device bytes a request needs while in flight: moduli, density, hierarchy (about the fine
-// operator's 3^d stencil on the geometric levels plus the AMG levels) and one solve slot's
-// FP64 Krylov vectors and FP32/FP64 V-cycle work vectors
+// estimated device bytes of a problem that has not run yet: moduli and density, the FP64
+// fine stencil (3^d blocks of d x d per node: 648 B per DOF in 3D, 144 in 2D), the coarser
+// geometric and algebraic levels with their FP32 copies and block-diagonal inverses, and one
+// solve slot's FP64 Krylov vectors and FP32/FP64 V-cycle work vectors
 size_t footprint(const tomg_problem* P) {
   const size_t n = (size_t)P->n, nel = (size_t)P->nel;
-  const size_t hier = n * (P->dim == 3 ? 120 : 60);
-  const size_t slot = n * (8 * 12 + 2 * 4 * 12 + 2 * 8 * 4);
-  return nel * 20 + hier + slot + ((size_t)16 << 20);
+  const size_t hier = n * (P->dim == 3 ? 648 + 140 : 144 + 100);
+  const size_t slot = n * (8 * 8 + 4 * 4 + 4 * 8);
+  return nel * 20 + hier + slot + ((size_t)32 << 20);
+}
+
+// whether request R may start now; extra = bytes it adds to the device while it runs
+bool admissible(const tomg_server* S, const Request& R, size_t* extra) {
+  const bool res = S->resident.count(R.P) != 0;
+  *extra = res ? 0 : R.bytes;
+  if (S->active == 0 && S->resident_total == 0) return true;  // always make progress
+  return S->resident_total + S->in_flight + *extra <= S->budget;
 }
 
 void process(tomg_server* S, Request& R) {
@@ -108,12 +123,17 @@ void worker_loop(tomg_server* S) {
       std::unique_lock<std::mutex> lk(S->mu);
       while (true) {
         if (S->stop) return;
-        // first request in arrival order whose problem is idle and which fits the budget
+        // first request in arrival order whose problem is idle and which fits the budget;
+        // a problem already resident on the device adds nothing and is never held up by a
+        // new problem that does not fit yet (its client would otherwise never finish and
+        // retire, so the new one could never get in)
         for (auto it = S->queue.begin(); it != S->queue.end(); ++it) {
           Request& q = **it;
           if (S->busy[q.P]) continue;
-          if (S->active > 0 && S->in_flight + q.bytes > S->budget) break;  // keep FIFO fairness
+          size_t extra = 0;
+          if (!admissible(S, q, &extra)) continue;
           R = *it;
+          R->bytes = extra;
           S->queue.erase(it);
           break;
         }
@@ -123,7 +143,7 @@ void worker_loop(tomg_server* S) {
       S->busy[R->P] = true;
       S->in_flight += R->bytes;
       S->active++;
-      S->peak_in_flight = std::max(S->peak_in_flight, S->in_flight);
+      S->peak_in_flight = std::max(S->peak_in_flight, S->resident_total + S->in_flight);
       S->peak_active = std::max(S->peak_active, S->active);
       R->t_start = Clock::now();
     }
@@ -136,12 +156,26 @@ void worker_loop(tomg_server* S) {
       R->status = TOMG_E_CUDA;
       R->error = "unexpected internal error";
     }
+    size_t held = 0;
+    try {
+      held = problem_device_bytes(R->P);
+    } catch (...) {
+      held = footprint(R->P);
+    }
     {
       std::lock_guard<std::mutex> lk(S->mu);
       R->t_end = Clock::now();
       R->done = true;
       S->busy[R->P] = false;
       S->in_flight -= R->bytes;
+      auto w = S->warm.find(R->P);
+      held += (w != S->warm.end() && w->second) ? w->second->bytes() : 0;
+      auto rs = S->resident.find(R->P);
+      if (rs != S->resident.end()) S->resident_total -= rs->second;
+      S->resident[R->P] = held;
+      S->resident_total += held;
+      S->peak_in_flight = std::max(S->peak_in_flight, S->resident_total + S->in_flight);
+      if (--S->pending[R->P] == 0) S->pending.erase(R->P);
       S->active--;
       S->latencies_ms.push_back(
           std::chrono::duration<double, std::milli>(R->t_end - R->t_submit).count());
@@ -202,6 +236,7 @@ tomg_status tomg_server_submit(tomg_server* S, tomg_problem* P, const double* rh
     R->ticket = S->next_ticket++;
     S->tickets[R->ticket] = R;
     S->queue.push_back(R);
+    S->pending[P]++;
   }
   S->cv_work.notify_all();
   *ticket = R->ticket;
@@ -261,6 +296,45 @@ tomg_status tomg_server_stats(tomg_server* S, double* p50_ms, double* p99_ms,
   if (completed) *completed = S->completed;
   if (peak_active) *peak_active = S->peak_active;
   if (peak_bytes) *peak_bytes = S->peak_in_flight;
+  return TOMG_OK;
+}
+
+tomg_status tomg_server_retire(tomg_server* S, tomg_problem* P, int timeout_ms) {
+  if (!S || !P) {
+    set_error("tomg_server_retire: bad arguments");
+    return TOMG_E_INVALID;
+  }
+  DBuf<double>* w = nullptr;
+  {
+    std::unique_lock<std::mutex> lk(S->mu);
+    auto idle = [&] { return S->pending.count(P) == 0; };
+    if (timeout_ms < 0) S->cv_done.wait(lk, idle);
+    else if (!S->cv_done.wait_for(lk, std::chrono::milliseconds(timeout_ms), idle)) {
+      set_error("problem still has requests after %d ms", timeout_ms);
+      return TOMG_E_TIMEOUT;
+    }
+    auto it = S->warm.find(P);
+    if (it != S->warm.end()) {
+      w = it->second;
+      S->warm.erase(it);
+    }
+    auto rs = S->resident.find(P);
+    if (rs != S->resident.end()) {
+      S->resident_total -= rs->second;
+      S->resident.erase(rs);
+    }
+    S->busy.erase(P);
+  }
+  if (w) {
+    try {
+      CK(cudaSetDevice(S->ctx->device));
+      set_alloc_stream(P->stream);
+      CK(cudaStreamSynchronize(P->stream));
+    } catch (...) {
+    }
+    delete w;
+  }
+  S->cv_work.notify_all();
   return TOMG_OK;
 }
 

@@ -1581,6 +1581,32 @@ double time_fine_operator(tomg_problem* P, int op, int prec, int reps, int cold_
 
 }  // namespace tomg
 
+// device bytes the problem holds: its inputs, the hierarchy and every solve slot
+size_t tomg::problem_device_bytes(const tomg_problem* P) {
+  using namespace tomg;
+  size_t b = P->Ketc.bytes() + P->Ke64.bytes() + P->Ke32.bytes() + P->mask.bytes() +
+             P->rho.bytes() + P->E64.bytes() + P->E32.bytes() + P->flag_dev.bytes() +
+             P->Ainv64.bytes() + P->Ainv32.bytes();
+  for (const auto& lp : P->L) {
+    const Level& l = *lp;
+    b += l.S64.bytes() + l.S32.bytes() + l.rp.bytes() + l.ci.bytes() + l.V64.bytes() +
+         l.V32.bytes() + l.D64.bytes() + l.D32.bytes() + l.Prp.bytes() + l.Pci.bytes() +
+         l.Rrp.bytes() + l.Rci.bytes() + l.Pv64.bytes() + l.Rv64.bytes() + l.Pv32.bytes() +
+         l.Rv32.bytes() + l.agg.bytes();
+  }
+  for (const auto& wp : P->works) {
+    const Work& w = *wp;
+    b += w.f.bytes() + w.bvec.bytes() + w.x.bytes() + w.r.bytes() + w.p.bytes() + w.q.bytes() +
+         w.z.bytes() + w.t.bytes() + w.partA.bytes() + w.partB.bytes() + w.partE.bytes() +
+         w.partC.bytes() + w.sc.bytes();
+    for (const auto& lw : w.lw)
+      b += lw.b64.bytes() + lw.x64.bytes() + lw.r64.bytes() + lw.y64.bytes() + lw.b32.bytes() +
+           lw.x32.bytes() + lw.r32.bytes() + lw.y32.bytes() + lw.gV64.bytes() + lw.gZ64.bytes() +
+           lw.gparts.bytes() + lw.gV32.bytes() + lw.gZ32.bytes() + lw.gst.bytes();
+  }
+  return b;
+}
+
 tomg_problem::~tomg_problem() {
   if (stream) cudaStreamSynchronize(stream);
   works.clear();

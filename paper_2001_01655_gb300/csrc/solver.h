@@ -180,6 +180,7 @@ void coarse_apply(tomg_problem* P, const double* b, double* x);
 void level_export(tomg_problem* P, int level, int64_t* nnzb, int64_t* rp, int64_t* ci, double* v);
 void prolong_export(tomg_problem* P, int level, int64_t* nnzb, int64_t* rp, int64_t* ci, double* v);
 void element_stiffness_host(int dim, double nu, std::vector<double>& Ke);
+size_t problem_device_bytes(const tomg_problem* P);
 double time_fine_operator(tomg_problem* P, int op, int prec, int reps, int cold_l2);
 void stress_stiffness_op(tomg_problem* P, const double* u, const double* x, double* y);
 tomg_status buckling(tomg_problem* P, const double* u, int n_eig, int jmin, int jmax, double tol,

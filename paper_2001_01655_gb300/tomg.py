@@ -100,6 +100,7 @@ _SIGS = {
     "tomg_server_wait": (C.c_int, [_P, C.c_uint64, C.c_int, C.POINTER(Result)]),
     "tomg_server_stats": (C.c_int, [_P, _D, _D, _D, _I64, C.POINTER(C.c_int),
                                     C.POINTER(C.c_size_t)]),
+    "tomg_server_retire": (C.c_int, [_P, _P, C.c_int]),
     "tomg_server_destroy": (C.c_int, [_P]),
 }
 
@@ -517,6 +518,12 @@ class Server:
         self._keep.pop(ticket, None)
         _check(st)
         return [res[i].as_dict() for i in range(nrhs)]
+
+    def retire(self, problem: Problem, timeout_ms=-1):
+        """The client is done with ``problem``: wait for its requests, free its warm start and
+        stop counting its device memory (tomg_server_retire)."""
+        _check(load().tomg_server_retire(self.h, problem.h, timeout_ms))
+        self._problems.pop(id(problem), None)
 
     def stats(self):
         p50, p99, sps = C.c_double(), C.c_double(), C.c_double()

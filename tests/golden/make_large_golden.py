@@ -1,7 +1,9 @@
-"""Writes the oracle reference values of the large workloads (3D cantilever 192x96x96 and the
-16 right-hand sides of the batched 128x64x64 case) to text fixtures in this folder.
+"""Writes the oracle reference values of the benchmark workloads to text fixtures in this
+folder: the 3D cantilever 192x96x96 and the 16 right-hand sides of the batched 128x64x64 case
+(solved by PCG, see below), and the 2D cantilever 768x384 and the MBB beam 96x32 (solved by the
+oracle's refined sparse direct solve).
 
-Both are too large for a sparse direct solve on a host.  The method reaches the unique
+The 3D workloads are too large for a sparse direct solve on a host.  The method reaches the unique
 solution of K(rho) u = f with u = 0 on fixed DOFs (Sec. 3.1), so the oracle computes that
 solution by textbook PCG (oracle.krylov.pcg) on the assembled masked CSR operator, with the
 oracle's own hybrid multigrid V-cycle (FP64 throughout) as preconditioner, iterating to a
@@ -19,8 +21,9 @@ Each fixture holds, per right-hand side:
     |u| and at the (at most 16 most) loaded DOFs.
 
 Run from the repository root (about an hour and 20 GB of host memory):
-    python tests/golden/make_large_golden.py [cantilever3d] [batched3d]
-It imports only ``oracle`` and ``workloads``.
+    python tests/golden/make_large_golden.py [cantilever3d] [batched3d] [cantilever2d] [mbb]
+It imports only ``oracle``, ``workloads`` and the fixture reader ``refs`` beside it (for the
+seeded probe vectors).
 """
 from __future__ import annotations
 
@@ -33,15 +36,13 @@ import numpy as np
 HERE = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, os.path.dirname(os.path.dirname(HERE)))
 
+sys.path.insert(0, HERE)
+
 import workloads as W  # noqa: E402
 from oracle import fem, krylov, mg, solve as osolve  # noqa: E402
+from refs import projections  # noqa: E402
 
-N_PROJ = 8
 N_SAMPLE = 200
-
-
-def projections(n):
-    return [np.random.default_rng(1000 + i).standard_normal(n) for i in range(N_PROJ)]
 
 
 def sample_dofs(u, f, free, rhs):
@@ -109,8 +110,44 @@ def run(p, name, n_geo, cap, out_path):
     print("wrote", out_path, flush=True)
 
 
+def run_direct(p, name, out_path):
+    """Reference of a 2D workload: the oracle's sparse LU with iterative refinement."""
+    t0 = time.perf_counter()
+    ref = osolve.direct(p)
+    A0 = mg.fine_operator(p)
+    free = fem.free_mask(p.n, p.fixed)
+    G = projections(p.n)
+    print("%s: direct solve %.1f s" % (name, time.perf_counter() - t0), flush=True)
+    lines = ["# oracle reference of %s: %d DOFs, %d right-hand sides" % (name, p.n, p.nrhs),
+             "# sparse LU of the reduced system with iterative refinement (oracle.solve.direct)",
+             "# written by tests/golden/make_large_golden.py (oracle only)"]
+    U = np.atleast_2d(ref["u"])
+    for r in range(p.nrhs):
+        u = U[r]
+        b = free * p.f[r]
+        true = np.linalg.norm(b - A0 @ u) / np.linalg.norm(b)
+        lines.append("rhs %d n %d iterations 0 true_rel_residual %.6e" % (r, p.n, true))
+        lines.append("compliance %.17e" % float(p.f[r] @ u))
+        lines.append("norm2 %.17e" % np.linalg.norm(u))
+        lines.append("norminf %.17e" % np.abs(u).max())
+        lines.append("proj " + " ".join("%.17e" % (g @ u) for g in G))
+        uni, extra = sample_dofs(u, p.f[r], free.astype(bool), r)
+        lines.append("uniform %d" % len(uni))
+        lines += ["%d %.17e" % (i, u[i]) for i in uni]
+        lines.append("extra %d" % len(extra))
+        lines += ["%d %.17e" % (i, u[i]) for i in extra]
+    with open(out_path, "w") as fh:
+        fh.write("\n".join(lines) + "\n")
+    print("wrote", out_path, flush=True)
+
+
 def main():
-    which = sys.argv[1:] or ["cantilever3d", "batched3d"]
+    which = sys.argv[1:] or ["cantilever3d", "batched3d", "cantilever2d", "mbb"]
+    if "mbb" in which:
+        run_direct(W.mbb_beam(96, 32), "mbb_96x32", os.path.join(HERE, "mbb_96x32.txt"))
+    if "cantilever2d" in which:
+        run_direct(W.cantilever_2d(768, 384, seed=0), "cantilever2d_768x384",
+                   os.path.join(HERE, "cantilever2d_768x384.txt"))
     if "cantilever3d" in which:
         run(W.cantilever_3d(192, 96, 96, seed=0), "cantilever3d_192x96x96", 3, 1000,
             os.path.join(HERE, "cantilever3d_192x96x96.txt"))

@@ -9,13 +9,20 @@
   sampled rows of b - K u element by element (oracle.fem.masked_apply_rows, pinned against
   the assembled operator).  Every sampled residual entry must be below 1e-8 ||b|| (a necessary
   condition of ||b - K u|| <= 1e-8 ||b||), and the GPU's own FP64 K u must match the oracle's
-  rows to 1e-13 of the summed element-product magnitudes.
+  rows to 1e-13 of the summed element-product magnitudes.  The 3D compliance is compared with
+  the oracle's reference (tests/golden/cantilever3d_192x96x96.txt).
 """
+import os
+import sys
+
 import numpy as np
 import pytest
 
 import workloads as W
 from oracle import fem, mg, solve as osolve
+
+sys.path.insert(0, os.path.join(os.path.dirname(os.path.abspath(__file__)), "golden"))
+import refs  # noqa: E402
 
 pytestmark = pytest.mark.gpu
 
@@ -84,7 +91,10 @@ def test_cantilever3d_full_sampled(lib, ctx, prec):
     r = res[0]
     assert r["status"] == 0 and r["rel_residual"] <= 1e-8, r
     check_sampled(lib, P, p, u[0], p.f[0], sampled_nodes(p, p.f[0], 3000, 7))
-    assert abs(r["compliance"] - p.f[0] @ u[0]) <= 1e-12 * abs(p.f[0] @ u[0])
+    # the compliance against the oracle's reference solution (tests/golden, oracle PCG to a
+    # true residual of 2e-12); the whole-vector comparison is in test_gpu_reference.py
+    ref = refs.load("cantilever3d_192x96x96")[0]
+    assert abs(r["compliance"] - ref["compliance"]) <= 1e-6 * abs(ref["compliance"])
 
 
 @pytest.mark.parametrize("prec,smoother", [("fp32", "jacobi"), ("tf32x3", "chebyshev")])
