@@ -163,6 +163,15 @@ def throughput(units_per_rank: int, world: int, total_ms: float) -> float:
     return world * units_per_rank / (total_ms / 1e3)
 
 
+T_START = time.perf_counter()
+
+
+def progress(what):
+    """One line per phase on stderr (the JSON line alone goes to stdout)."""
+    print("[bench %7.1f s] %s" % (time.perf_counter() - T_START, what), file=sys.stderr,
+          flush=True)
+
+
 def load_peaks():
     try:
         return json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
@@ -193,13 +202,14 @@ class Stepper:
         self.rho_d = torch.tensor(p.rho, dtype=torch.float64, device=dev)
         self.f_d = torch.tensor(p.f[0], dtype=torch.float64, device=dev)
         self.u_d = torch.zeros_like(self.f_d)
+        self.u_last = self.u_d
         self.flush = torch.empty(256 << 20, dtype=torch.int8, device=dev)  # > 129 MB L2
 
     def step(self, prec, opts):
         self.u_d.zero_()
         self.P.set_density(self.rho_d)
         self.P.setup(prec=prec, **opts)
-        _, res = self.P.solve(self.f_d, u0=self.u_d)
+        self.u_last, res = self.P.solve(self.f_d, u0=self.u_d)
         return res[0]
 
     def timed(self, prec, opts, K, Wm, world=1):
@@ -259,6 +269,7 @@ def run_gpu(args, rank, world, local):
     ref = refs.load(REF_NAME)[0]
     G = refs.projections(p.n)
 
+    progress("headline")
     with Clocks(local) as clk:
         times, results, launches = S.timed(HEAD_PREC, opts, args.steps, args.warmup, world)
     total_ms = max_over_ranks(sum(times), world, device=dev)
@@ -284,14 +295,15 @@ def run_gpu(args, rank, world, local):
         "setup_ms": head["setup_ms"], "solve_ms": head["solve_ms"],
         "rel_residual_max": head["rel_residual_max"],
         "failed_steps": head["failed_steps"],
-        "accuracy": accuracy_of(S.u_d.cpu().numpy(), results[-1], ref, G),
+        "accuracy": accuracy_of(S.u_last.cpu().numpy(), results[-1], ref, G),
         "gpu_launches": launches,
         "clocks": clk.summary(),
     }
+    progress("fp64 + jacobi variants")
     if not args.no_fp64:
         t64, r64, _ = S.timed("fp64", opts, max(3, args.steps // 2), 1)
         out["fp64"] = dict(S.summary(t64, r64),
-                           accuracy=accuracy_of(S.u_d.cpu().numpy(), r64[-1], ref, G))
+                           accuracy=accuracy_of(S.u_last.cpu().numpy(), r64[-1], ref, G))
         out["mixed_over_fp64"] = out["value"] / out["fp64"]["solves_per_s"]
         if args.smoother != "jacobi":
             # the paper's smoother (one weighted point-block Jacobi sweep), mixed and FP64
@@ -300,8 +312,9 @@ def run_gpu(args, rank, world, local):
             for prec, key in ((HEAD_PREC, "mixed"), ("fp64", "fp64")):
                 tj, rj, _ = S.timed(prec, oj, max(3, args.steps // 4), 1)
                 jac[key] = dict(S.summary(tj, rj),
-                                accuracy=accuracy_of(S.u_d.cpu().numpy(), rj[-1], ref, G))
+                                accuracy=accuracy_of(S.u_last.cpu().numpy(), rj[-1], ref, G))
             out["jacobi"] = jac
+    progress("e2e")
     # end to end through the C ABI with host buffers (copies inside the timed region)
     rho_h, f_h = p.rho.copy(), p.f[0].copy()
     e2e = []
@@ -316,16 +329,21 @@ def run_gpu(args, rank, world, local):
     out["e2e"] = {"value": world / statistics.median(e2e), "unit": "solves/s",
                   "h2d_bytes_per_step": int(rho_h.nbytes + 2 * f_h.nbytes),
                   "d2h_bytes_per_step": int(f_h.nbytes),
-                  "accuracy": accuracy_of(u_h[0], res[0], ref, G)}
+                  "accuracy": accuracy_of(u_h, res[0], ref, G)}
+    progress("roofline")
     out["roofline"] = roofline(S.P, p, head)
+    progress("mbb + 2D cantilever")
     if args.others:
         out["mbb_96x32"] = mbb_run(tomg, ctx, stream, dev, args)
         out["cantilever2d_768x384"] = cantilever2d_run(tomg, ctx, stream, dev, args)
+    progress("batched")
     if args.batched:
         out["batched"] = batched_run(tomg, ctx, args.slots, smoother=args.smoother,
                                      cheb_degree=args.cheb_degree)
+    progress("serving")
     if args.serving > 0:
         out["serving"] = serving_run(tomg, ctx, args.serving, args.serving_updates, args.slots)
+    progress("variants")
     if args.variants and not args.no_fp64:
         out["variants_2d"] = variants_run(tomg, ctx, stream, dev, args)
     return out
@@ -343,7 +361,7 @@ def mbb_run(tomg, ctx, stream, dev, args):
     ref = refs.load("mbb_96x32")[0]
     return dict(S.summary(t, r), workload="MBB beam quad4 96x32 (6,402 DOFs), rho = 0.5",
                 preconditioner="GMG 4 levels, FP64 PCG, Jacobi",
-                accuracy=accuracy_of(S.u_d.cpu().numpy(), r[-1], ref,
+                accuracy=accuracy_of(S.u_last.cpu().numpy(), r[-1], ref,
                                      refs.projections(p.n)))
 
 
@@ -365,8 +383,9 @@ def cantilever2d_run(tomg, ctx, stream, dev, args):
                  use_graph=args.graph_mode, smoother=args.smoother, cheb_degree=args.cheb_degree)
         res = {"levels": None}
         for prec, key in (("fp32", "mixed"), ("fp64", "fp64")):
-            t, r, _ = S.timed(prec, o, 10, 2)
-            res[key] = dict(S.summary(t, r), accuracy=accuracy_of(S.u_d.cpu().numpy(), r[-1],
+            t, r, _ = S.timed(prec, o, 10 if pc != "gmg" else 2, 1 if pc != "gmg" else 0)
+            res[key] = dict(S.summary(t, r), converged=all(x["status"] == 0 for x in r),
+                            accuracy=accuracy_of(S.u_last.cpu().numpy(), r[-1],
                                                                    ref, G))
         res["levels"] = [S.P.level_info(l)["n_dofs"] for l in range(S.P.num_levels())]
         out[pc] = res
@@ -585,14 +604,14 @@ def serving_run(tomg, ctx, n_clients, n_updates, slots, budget_gb=160):
                 if k:
                     rho = np.clip(rho * (1.0 + r["noise"] * rng.standard_normal(rho.shape)),
                                   1e-3, 1.0)
-                res = srv.wait(srv.submit(P, rho, p.f[0], **opt))[0]
+                res = srv.wait(srv.submit(P, rho, p.f[0], **opt), timeout_ms=300000)[0]
                 with lock:
                     stats["solves"] += 1
                     if res["status"] == 0 and res["rel_residual"] <= 1e-8:
                         stats["converged"] += 1
                     else:
                         stats["not_converged_rel_residual"].append(res["rel_residual"])
-            srv.retire(P)
+            srv.retire(P, timeout_ms=300000)
             P.close()
         except Exception as e:  # noqa: BLE001
             with lock:
@@ -831,11 +850,13 @@ def main():
         dist.init_process_group("nccl")
     out = run_gpu(args, rank, world, local)
     if rank == 0 and world == 1 and not args.no_cpu:
+        progress("cpu baseline")
         cb = cpu_baseline(smoother=args.smoother)
         out["cpu_baseline"] = {k: cb[k] for k in ("value", "unit", "cores", "host_cores", "kind",
                                                   "sample", "sample_solves_per_s")}
         out["cpu_baseline"]["gpu_solves_per_s_on_sample"] = gpu_on_sample(args)
     if rank == 0 and out is not None:
+        progress("done")
         print(json.dumps(out))
     if world > 1:
         import torch.distributed as dist

@@ -81,10 +81,17 @@ size_t footprint(const tomg_problem* P) {
   return nel * 20 + hier + slot + ((size_t)32 << 20);
 }
 
-// whether request R may start now; extra = bytes it adds to the device while it runs
+// whether request R may start now; extra = bytes it adds to the device while it runs.  A
+// problem that is resident already holds its memory: its requests always start (the resident
+// total may exceed the budget when measured footprints exceed the estimates; holding them
+// back then would stop every client from finishing and retiring).  A new problem starts when
+// its estimated footprint fits beside the resident problems and the other new ones in flight.
 bool admissible(const tomg_server* S, const Request& R, size_t* extra) {
-  const bool res = S->resident.count(R.P) != 0;
-  *extra = res ? 0 : R.bytes;
+  if (S->resident.count(R.P) != 0) {
+    *extra = 0;
+    return true;
+  }
+  *extra = R.bytes;
   if (S->active == 0 && S->resident_total == 0) return true;  // always make progress
   return S->resident_total + S->in_flight + *extra <= S->budget;
 }
