@@ -5,7 +5,7 @@ One step = one whole pass of the hot path on the 3D cantilever (192 x 96 x 96 he
 on the far bottom edge): SIMP moduli from the density already resident in HBM, preconditioner
 setup (two geometric Galerkin coarsenings, smoothed aggregation below to < 1000 DOFs, smoother
 bounds, coarse Cholesky) and a solve to a true relative residual of 1e-8.  Headline: mixed
-precision (FP32 V-cycle with tensor-core 3xTF32 element contractions inside FP64 flexible CG);
+precision (FP32 V-cycle with tensor-core element contractions inside FP64 flexible CG);
 the FP64 V-cycle PCG is measured beside it.  Every result is compared with the oracle's
 reference solution (tests/golden).  The other workloads (MBB beam, 2D cantilever with GMG /
 AMG / hybrid, the 16 right-hand sides of the batched 3D case, the serving stream) are
@@ -38,7 +38,7 @@ METRIC = "MG-PCG solves/sec & DOF-iters/sec @1e-8 residual, mixed vs FP64; p50/p
 WORKLOAD = dict(nx=192, ny=96, nz=96, seed=0)
 REF_NAME = "cantilever3d_192x96x96"
 HEADLINE = dict(pc="hybrid", n_geo_levels=3, max_coarse_dofs=1000, rtol=1e-8, max_iter=2000)
-HEAD_PREC = "tf32x3"
+HEAD_PREC = "tc"
 # the oracle's complete solves run on the same cantilever with 1/27 of the elements
 SAMPLE_GRID = (64, 32, 32)
 
@@ -281,7 +281,7 @@ def run_gpu(args, rank, world, local):
         "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
         "ms_per_step": total_ms / args.steps,
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
-        "dtype": "f64 outer / f32 V-cycle (3xTF32 tensor-core element contractions)",
+        "dtype": "f64 outer / f32 V-cycle (tensor-core element contractions)",
         "data": "synthetic",
         "config": {"workload": workload_label(),
                    "preconditioner": "hybrid: 3 geometric levels, SA-AMG below to < 1000 DOFs",
@@ -526,7 +526,7 @@ def stability_run(tomg, ctx, opts, nx=256, ny=1024):
             "timing": "host clock per phase, device arrays throughout, synchronised per phase"}
 
 
-def batched_run(tomg, ctx, slots, reps=3, prec="tf32x3", smoother="chebyshev", cheb_degree=2):
+def batched_run(tomg, ctx, slots, reps=3, prec="tc", smoother="chebyshev", cheb_degree=2):
     """The 16 right-hand sides (8 point loads, 8 adjoint-like vectors) of the 3D hex8 128x64x64
     case (1,635,075 DOFs) on one shared hierarchy: all 16 on `slots` concurrent solve slots,
     against the same 16 one after another (one slot).  Median of `reps` runs, setup excluded;
@@ -561,18 +561,18 @@ def batched_run(tomg, ctx, slots, reps=3, prec="tf32x3", smoother="chebyshev", c
     hbm = peaks.get("hbm_gbs", 6800.0)
     kern = {}
     for name in ("residual", "jacobi"):
-        for kp in ("tf32x3", "fp32"):
+        for kp in ("tc", "fp32"):
             ms = P.time_fine_operator(name, kp, reps=20, cold_l2=True)
             nb = kernel_bytes(name, kp, p)
             kern["%s_%s" % (name, kp)] = {
-                "kernel": "k_ebe3tc (tcgen05 3xTF32)" if kp == "tf32x3" else "k_ebe3 (CUDA cores)",
+                "kernel": "k_ebe3tc (tcgen05 kind::f16, split x against integer Ke)" if kp == "tc" else "k_ebe3 (CUDA cores)",
                 "ms_per_launch": ms, "algorithmic_bytes": nb,
                 "achieved_gbs": nb / (ms * 1e-3) / 1e9, "frac_hbm": nb / (ms * 1e-3) / 1e9 / hbm,
                 "element_gflops": 1152.0 * p.nel / (ms * 1e-3) / 1e9}
     P.close()
     return {"workload": "3D cantilever hex8 128x64x64 (1,635,075 DOFs), 8 point loads + 8 "
                         "adjoint-like right-hand sides, hybrid hierarchy, FP32 V-cycle with "
-                        "3xTF32 tensor-core element contractions",
+                        "tensor-core element contractions",
             "rhs": p.nrhs, "concurrent": dict(res[slots], slots=slots), "one_at_a_time": res[1],
             "level0_kernels": kern}
 
@@ -587,7 +587,7 @@ def serving_run(tomg, ctx, n_clients, n_updates, slots, budget_gb=160):
     count against it) and overlaps up to `slots` of them on the GPU."""
     import workloads as W
     stream = W.serving_stream(n_requests=n_clients, n_updates=n_updates)
-    opt = dict(pc="hybrid", prec="tf32x3", n_geo_levels=3, max_coarse_dofs=1000, concurrency=1,
+    opt = dict(pc="hybrid", prec="tc", n_geo_levels=3, max_coarse_dofs=1000, concurrency=1,
                max_iter=2000)
     srv = tomg.Server(ctx, budget_gb << 30, slots)
     lock = threading.Lock()
@@ -695,7 +695,7 @@ def roofline(P, p, head):
                  "peak_source": "nominal FP64 rate (the measured-peaks file has no FP64 figure)"}
     else:
         k = out[dom]
-        headr = {"kernel": "k_ebe3tc (%s, 3xTF32 tensor cores)" % dom, "bound": "hbm",
+        headr = {"kernel": "k_ebe3tc (%s, tensor cores)" % dom, "bound": "hbm",
                  "achieved": k["achieved_gbs"], "peak": hbm, "unit": "GB/s",
                  "frac": k["frac_hbm"], "peak_source": src}
     share = {k: out[k]["ms_per_launch"] * out[k]["launches_per_iteration"] * head["iterations"]

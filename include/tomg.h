@@ -55,9 +55,13 @@ typedef enum {
 typedef enum {
   TOMG_PREC_FP64 = 0,         /* FP64 V-cycle inside FP64 PCG                                 */
   TOMG_PREC_FP32_VCYCLE = 1,  /* FP32 V-cycle inside FP64 flexible CG (Notay 2000)            */
-  TOMG_PREC_3XTF32_VCYCLE = 2 /* as FP32_VCYCLE, with the hex8 level-0 element contractions on
-                                 the tensor cores as 3xTF32 split products (FP32 accuracy);
-                                 quad4 problems run exactly as FP32_VCYCLE                     */
+  TOMG_PREC_TC_VCYCLE = 2,    /* as FP32_VCYCLE, with the hex8 level-0 element contractions on
+                                 the tensor cores: each element row scaled by a power of two
+                                 and split into two FP16 parts, against the exact integer
+                                 parts 72 K_l, 72 K_m of Ke = lambda K_l + mu K_m, FP32
+                                 accumulation (FP32 accuracy); quad4 problems run exactly as
+                                 FP32_VCYCLE                                                   */
+  TOMG_PREC_3XTF32_VCYCLE = 2 /* former name of TOMG_PREC_TC_VCYCLE                           */
 } tomg_prec;
 
 typedef struct {
@@ -243,6 +247,14 @@ tomg_status tomg_element_stiffness(const tomg_problem* prob, double* Ke);
  * setup; reps in [1, 10000]. */
 tomg_status tomg_time_fine_operator(tomg_problem* prob, int op, int prec, int reps, int cold_l2,
                                     double* ms_per_launch);
+/* Test hook of the failure path of the tensor-core element kernel (TOMG_PREC_TC_VCYCLE).  With
+ * polls > 0, launches made after this call wait for their MMAs on a barrier that nothing
+ * arrives on and give up after `polls` polls, exactly as after a real timeout: the kernel
+ * records the failure, waits with the default limit (2^22 polls) for the MMAs it has in flight
+ * on their own barrier, frees its tensor memory and returns; the next tomg_level_apply or
+ * tomg_solve of the problem reports TOMG_E_TIMEOUT and clears the record.  polls <= 0 restores
+ * normal launches.  No fault is involved.  Process-wide, not thread-safe; for tests only. */
+tomg_status tomg_debug_tc_wait_limit(int polls);
 /* Allocation-free y = A_0 x with FP32 arithmetic: the same computation as
  * tomg_level_apply(prob, 0, TOMG_PREC_FP32_VCYCLE, x, y, 1), for callers that must not
  * allocate device memory where they apply the operator (memory owned by another allocator,

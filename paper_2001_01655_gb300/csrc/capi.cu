@@ -599,3 +599,8 @@ extern "C" tomg_status tomg_time_fine_operator(tomg_problem* P, int op, int prec
     return TOMG_OK;
   });
 }
+
+extern "C" tomg_status tomg_debug_tc_wait_limit(int polls) {
+  tomg::ebe3d_tc_set_wait_limit(polls);
+  return TOMG_OK;
+}

@@ -1,40 +1,53 @@
 // Level-0 SIMP element operator on hex8 grids (Sec. 2.1 Eq. 2, Sec. 3.1) with the element
-// contractions on the fifth-generation tensor cores: tcgen05.mma kind::tf32, A operands and
-// accumulators in tensor memory, B operand (Ke) in shared memory.
+// contractions on the fifth-generation tensor cores: tcgen05.mma kind::f16, A operands and
+// accumulators in tensor memory, B operand in shared memory.
 //
 // The element products y_e = Ke x_e of a tile of elements form one dense product
 //   Y (elements x 24) = X (elements x 24) . Ke^T (24 x 24)
-// whose rows are the gathered element displacement vectors.  FP32 accuracy on TF32 units comes
-// from split products ("3xTF32"): x = x_hi + x_lo and Ke = K_hi + K_lo with every part a TF32
-// value, and Y = X_hi K_hi^T + X_lo K_hi^T + X_hi K_lo^T (the X_lo K_lo^T term is below FP32
-// rounding).  The three products accumulate in FP32 in the same tensor-memory tile.
+// whose rows are the gathered element displacement vectors.  Two facts make it cheap on FP16
+// tensor cores:
+//   * on the unit cube with the 2x2x2 Gauss rule, Ke = lambda K_l + mu K_m where 72 K_l and
+//     72 K_m are integer matrices (entries up to 8 and 32): exact in FP16, so B needs no split;
+//   * each element row is scaled by a power of two 2^-s (s from its largest |x|), t = x 2^-s,
+//     and split into two FP16 parts, h0 = fp16(t) and h1 = fp16(2^11 (t - h0)); the second part
+//     is scaled up so that it stays clear of the FP16 subnormal range, and its B half carries
+//     the factor 2^-11 (still exact).  t - h0 - 2^-11 h1 is below 2^-22 |t| per entry, plus
+//     2^-36 of the row's largest entry for entries under 2^-13 of it: the accuracy of the
+//     3xTF32 split products this replaces, with one B operand instead of two.
+// One MMA chain of K = 48 (h0 | h1 against K_int | 2^-11 K_int) and N = 48 (K_l rows | K_m
+// rows) accumulates both parts in FP32; the epilogue forms
+// y_e = E_e 2^s (lambda/72 Z_l + mu/72 Z_m).  That is 3 MMAs (K-steps of 16) per M = 128 tile.
 //
-// Tiling.  A block owns a column of output nodes: 31 x 7 nodes in x, y and `nz_tile` node
-// layers in z.  It walks the element layers under and inside that column.  One element layer
-// of the tile is 32 x 8 = 256 elements = two M = 128 tiles; thread (lane ex, warp ey) owns
-// element (ex, ey) and, for ex, ey >= 1, node (ex, ey) of the layer tile.  Per element layer:
-//   1. the masked displacements of the next node layer (33 x 9 nodes) are staged in shared
+// Tiling.  A block owns a column of output nodes: 31 x (TY-1) nodes in x and y and `nz_tile`
+// node layers in z.  It walks the element layers under and inside that column.  One element
+// layer of the tile is 32 x TY elements = TY / 4 tiles of M = 128; thread (lane ex, warp ey)
+// owns element (ex, ey) and, for ex, ey >= 1, node (ex, ey) of the layer tile.  Per layer:
+//   1. the masked displacements of the next node layer (33 x (TY+1) nodes) are staged in shared
 //      memory, and each thread keeps its element's modulus (both fetched one layer ahead);
-//   2. every thread splits its element's 24 displacements into TF32 hi and lo parts and writes
-//      them as its row of the A operands in tensor memory (tcgen05.st: lane = row);
-//   3. one thread issues 2 tiles x 3 products x 3 K-steps of M128 N32 K8 MMAs and commits them
-//      to an mbarrier (N = 32: the 24 outputs padded with zero rows of B);
+//   2. every thread scales and splits its element's 24 displacements and writes them as its row
+//      of the A operand in tensor memory (tcgen05.st: lane = row);
+//   3. one thread issues 3 MMAs per tile and commits them to an mbarrier;
 //   4. while they run, the threads finish the previous element layer: each reads its element's
-//      accumulator row (tcgen05.ld) and scales it by E_e; node sums over the four elements of
-//      the layer around a node take the x-neighbour through a warp shuffle and the
-//      y-neighbour through shared memory;
+//      accumulator row (tcgen05.ld) and scales it; node sums over the four elements of the layer
+//      around a node take the x-neighbour through a warp shuffle and the y-neighbour through
+//      shared memory;
 //   5. a node layer is complete after the element layers below and above it, and is then
-//      finished (mask, residual or Jacobi update) and written.
+//      finished (mask, residual or Jacobi / Chebyshev update) and written.
 // The accumulators are double-buffered (layer ke's MMAs overlap the finishing of layer ke - 1);
 // the A operands are single-buffered and rewritten once the previous layer's MMAs completed.
 // The outer ring of nodes of each tile is computed but not written: the neighbouring tile owns
 // it, so every node's sum comes from one block, in a fixed order, with no atomics.
-// All waits are bounded: an mbarrier that does not complete within the limit sets an error word
-// (read by the host after the solve) and the block releases its tensor memory and returns.
+// All waits are bounded: a block whose wait for its MMAs runs out sets an error word (read by
+// the host after the solve), waits with the full limit for the MMAs it still has in flight,
+// releases its tensor memory and returns.
+#include <cuda_fp16.h>
+
+#include <cmath>
 #include <cstring>
 #include <map>
 #include <mutex>
 #include <tuple>
+#include <vector>
 
 #include "ops.h"
 
@@ -45,48 +58,56 @@ namespace {
 constexpr int TEX = 32;                       // elements of one layer of the tile in x
 constexpr int TNX = TEX + 1;                  // nodes of one layer of the tile in x (33)
 constexpr int ONX = TEX - 1;                  // owned nodes per layer in x (31)
-constexpr int KD = 24;                        // element DOFs (the K of the product)
-constexpr int NB = 32;                        // N: 24 outputs padded to a multiple of 16
+constexpr int KD = 24;                        // element DOFs
+constexpr int KA = 2 * KD;                    // K of the product: two FP16 parts of x
+constexpr int AW = KA / 2;                    // A row in 32-bit tensor-memory columns (24)
+constexpr int NB = 2 * KD;                    // N: K_l rows, then K_m rows (48)
+constexpr int KDEN = 72;                      // 72 K_l and 72 K_m are integer matrices
 // B operand in shared memory, canonical K-major layout without swizzle: a core matrix is
-// 8 rows x 16 bytes (4 TF32); core matrices adjacent in K are LBO bytes apart, adjacent
-// 8-row groups SBO bytes apart
+// 8 rows x 16 bytes (8 FP16); core matrices adjacent in K are LBO bytes apart, adjacent 8-row
+// groups SBO bytes apart
 constexpr int LBO = 128;
-constexpr int SBO = (KD / 4) * LBO;           // 768
-constexpr int B_BYTES = (NB / 8) * SBO;       // one N = 32 operand: 3072
+constexpr int SBO = (KA / 8) * LBO;           // 768
+constexpr int B_BYTES = (NB / 8) * SBO;       // 4608
 constexpr int PS = 7;                         // staged y-pair partial sums: row stride (floats)
 
 // Tile shapes: TY = 8 element rows (256 threads, two M = 128 tiles, 31 x 7 owned nodes per
-// layer) or TY = 4 (128 threads, one tile, 31 x 3 owned nodes).  Tensor memory columns:
-// accumulators of pipeline stage j, tile m at (j MT + m) 32; A of tile m at A_COL + 48 m
-// (24 hi columns, then 24 lo columns; one TF32 element per 32-bit column).
+// layer) or TY = 4 (128 threads, one tile, 31 x 3 owned nodes).  Tensor memory columns: the A
+// operand of tile m (24 columns) at 32 m, accumulators of pipeline stage j, tile m at
+// ACC + (j MT + m) 48 with ACC = 32 MT (every operand starts on a multiple of 16 columns).
 template <int TY>
 struct Cfg {
   static constexpr int TNY = TY + 1, ONY = TY - 1;
   static constexpr int NT = TEX * TY;                     // one element per thread
   static constexpr int MT = TY / 4;                       // M = 128 tiles per layer
   static constexpr int LAYER_NODES = TNX * TNY;
-  static constexpr int A_COL = 2 * MT * NB;
-  static constexpr int TMEM_COLS = TY == 8 ? 256 : 128;   // >= A_COL + 48 MT, a power of 2
+  static constexpr int ACC = 32 * MT;                     // after the A operands
+  static constexpr int TMEM_COLS = TY == 8 ? 256 : 128;   // a power of 2
   static constexpr int MAX_BLOCKS = 512 / TMEM_COLS;      // blocks per SM the TMEM can hold
   // dynamic shared memory map (bytes from a 128-aligned base)
-  static constexpr int OFF_B = 0;                                               // B_hi, B_lo
-  static constexpr int OFF_X = OFF_B + 2 * B_BYTES;                             // x ring
+  static constexpr int OFF_B = 0;                                               // B operand
+  static constexpr int OFF_X = OFF_B + B_BYTES;                                 // x ring
   static constexpr int OFF_P = (OFF_X + 2 * LAYER_NODES * 3 * 4 + 15) / 16 * 16;  // y pairs
-  static constexpr int OFF_BAR = OFF_P + 2 * NT * PS * 4; // 2 mbarriers + TMEM address
-  static constexpr int SMEM_ALLOC = OFF_BAR + 24 + 128;   // + room to align the base
-  static_assert(A_COL + 48 * MT <= TMEM_COLS, "tensor memory map");
+  static constexpr int OFF_BAR = OFF_P + 2 * NT * PS * 4; // 3 mbarriers + TMEM address
+  static constexpr int SMEM_ALLOC = OFF_BAR + 32 + 128;   // + room to align the base
+  static_assert(AW * MT <= ACC && ACC + 2 * MT * NB <= TMEM_COLS, "tensor memory map");
   static_assert(OFF_X % 16 == 0 && OFF_P % 16 == 0 && OFF_BAR % 8 == 0, "alignment");
   static_assert(LAYER_NODES <= 2 * NT, "two nodes per thread stage a layer");
 };
 
-// instruction descriptor, kind::tf32: D FP32 (bits 4-5 = 1), A and B TF32 (bits 7-9 and
-// 10-12 = 2), both K-major (bits 15, 16 = 0), N >> 3 at bits 17-22, M >> 4 at bits 24-28
-constexpr uint32_t IDESC = (1u << 4) | (2u << 7) | (2u << 10) | ((uint32_t)(NB >> 3) << 17) |
-                           ((uint32_t)(128 >> 4) << 24);
+// instruction descriptor, kind::f16: D FP32 (bits 4-5 = 1), A and B FP16 (bits 7-9 and 10-12
+// = 0), both K-major (bits 15, 16 = 0), N >> 3 at bits 17-22, M >> 4 at bits 24-28
+constexpr uint32_t IDESC = (1u << 4) | ((uint32_t)(NB >> 3) << 17) | ((uint32_t)(128 >> 4) << 24);
 
 constexpr uint32_t WAIT_LIMIT = 1u << 22;  // mbarrier polls before a block gives up
 
 __device__ int g_tc_error;  // set to 1 by a block whose MMA completion wait ran out
+
+// test hook (tomg_debug_tc_wait_limit): polls > 0 makes the in-loop MMA waits of later launches
+// watch a third barrier that nothing arrives on and give up after that many polls, so that the
+// error path runs exactly as after a real timeout (the MMAs complete on their own barrier,
+// which the drain then waits for with the full limit)
+int g_first_wait_limit = 0;
 
 __device__ __forceinline__ uint32_t smem_u32(const void* p) {
   return (uint32_t)__cvta_generic_to_shared(p);
@@ -101,21 +122,16 @@ __device__ __forceinline__ uint64_t sdesc(uint32_t addr) {
 
 // byte offset of element (row, k) in the B operand layout above
 __host__ __device__ __forceinline__ int op_off(int row, int k) {
-  return (row >> 3) * SBO + (k >> 2) * LBO + (row & 7) * 16 + (k & 3) * 4;
-}
-
-// x rounded to the nearest TF32 value (10 explicit mantissa bits), ties away from zero
-__host__ __device__ __forceinline__ uint32_t tf32_round_bits(uint32_t u) {
-  return (u + 0x1000u) & 0xFFFFE000u;
+  return (row >> 3) * SBO + (k >> 3) * LBO + (row & 7) * 16 + (k & 7) * 2;
 }
 
 // D (tmem) (+)= A (tmem) . B (smem descriptor)^T
-__device__ __forceinline__ void mma_tf32_ts(uint32_t d_tmem, uint32_t a_tmem, uint64_t b,
-                                            uint32_t acc) {
+__device__ __forceinline__ void mma_f16_ts(uint32_t d_tmem, uint32_t a_tmem, uint64_t b,
+                                           uint32_t acc) {
   asm volatile(
       "{\n\t.reg .pred p;\n\t"
       "setp.ne.b32 p, %4, 0;\n\t"
-      "tcgen05.mma.cta_group::1.kind::tf32 [%0], [%1], %2, %3, p;\n\t}\n"
+      "tcgen05.mma.cta_group::1.kind::f16 [%0], [%1], %2, %3, p;\n\t}\n"
       :: "r"(d_tmem), "r"(a_tmem), "l"(b), "r"(IDESC), "r"(acc) : "memory");
 }
 
@@ -129,49 +145,52 @@ __device__ __forceinline__ bool mbar_try(uint32_t bar, uint32_t parity) {
   return ok != 0;
 }
 
-// bounded wait for phase `parity` of the barrier; true if it completed
-__device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity) {
-  for (uint32_t i = 0; i < WAIT_LIMIT; i++)
+// bounded wait for the phase of the barrier with parity `parity`; true if it completed
+__device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity, uint32_t limit) {
+  for (uint32_t i = 0; i < limit; i++)
     if (mbar_try(bar, parity)) return true;
   return false;
 }
 
-// this thread's TMEM lane, 24 consecutive FP32 columns from taddr; the wait for the loads is
-// part of the same asm statement, so no use of the registers can be scheduled before it
-__device__ __forceinline__ void tmem_ld24(uint32_t taddr, float* v) {
-  uint32_t r[24];
+// this thread's TMEM lane, 48 consecutive FP32 columns from taddr (16-column aligned); the wait
+// for the loads is part of the same asm statement, so no use of the registers can be
+// scheduled before it
+__device__ __forceinline__ void tmem_ld48(uint32_t taddr, float* v) {
+  uint32_t r[48];
   asm volatile(
       "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,"
-      "%14,%15}, [%24];\n\t"
-      "tcgen05.ld.sync.aligned.32x32b.x8.b32 {%16,%17,%18,%19,%20,%21,%22,%23}, [%25];\n\t"
+      "%14,%15}, [%48];\n\t"
+      "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%16,%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,"
+      "%28,%29,%30,%31}, [%49];\n\t"
+      "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%32,%33,%34,%35,%36,%37,%38,%39,%40,%41,%42,%43,"
+      "%44,%45,%46,%47}, [%50];\n\t"
       "tcgen05.wait::ld.sync.aligned;\n"
       : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]),
         "=r"(r[7]), "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]),
         "=r"(r[14]), "=r"(r[15]), "=r"(r[16]), "=r"(r[17]), "=r"(r[18]), "=r"(r[19]),
-        "=r"(r[20]), "=r"(r[21]), "=r"(r[22]), "=r"(r[23])
-      : "r"(taddr), "r"(taddr + 16u)
+        "=r"(r[20]), "=r"(r[21]), "=r"(r[22]), "=r"(r[23]), "=r"(r[24]), "=r"(r[25]),
+        "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]), "=r"(r[30]), "=r"(r[31]),
+        "=r"(r[32]), "=r"(r[33]), "=r"(r[34]), "=r"(r[35]), "=r"(r[36]), "=r"(r[37]),
+        "=r"(r[38]), "=r"(r[39]), "=r"(r[40]), "=r"(r[41]), "=r"(r[42]), "=r"(r[43]),
+        "=r"(r[44]), "=r"(r[45]), "=r"(r[46]), "=r"(r[47])
+      : "r"(taddr), "r"(taddr + 16u), "r"(taddr + 32u)
       : "memory");
 #pragma unroll
-  for (int i = 0; i < 24; i++) v[i] = __uint_as_float(r[i]);
+  for (int i = 0; i < 48; i++) v[i] = __uint_as_float(r[i]);
 }
 
-// this thread's TMEM lane, 48 consecutive 32-bit columns from taddr; the wait for the stores
-// is part of the same asm statement
-__device__ __forceinline__ void tmem_st48(uint32_t taddr, const uint32_t* v) {
+// this thread's TMEM lane, 24 consecutive 32-bit columns from taddr (8-column aligned); the
+// wait for the stores is part of the same asm statement
+__device__ __forceinline__ void tmem_st24(uint32_t taddr, const uint32_t* v) {
   asm volatile(
-      "tcgen05.st.sync.aligned.32x32b.x32.b32 [%0], {%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,"
-      "%14,%15,%16,%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31,%32,%33};\n\t"
-      "tcgen05.st.sync.aligned.32x32b.x16.b32 [%1], {%34,%35,%36,%37,%38,%39,%40,%41,%42,%43,"
-      "%44,%45,%46,%47,%48,%49};\n\t"
+      "tcgen05.st.sync.aligned.32x32b.x16.b32 [%0], {%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,"
+      "%14,%15,%16,%17};\n\t"
+      "tcgen05.st.sync.aligned.32x32b.x8.b32 [%1], {%18,%19,%20,%21,%22,%23,%24,%25};\n\t"
       "tcgen05.wait::st.sync.aligned;\n"
-      :: "r"(taddr), "r"(taddr + 32u), "r"(v[0]), "r"(v[1]), "r"(v[2]), "r"(v[3]), "r"(v[4]),
+      :: "r"(taddr), "r"(taddr + 16u), "r"(v[0]), "r"(v[1]), "r"(v[2]), "r"(v[3]), "r"(v[4]),
          "r"(v[5]), "r"(v[6]), "r"(v[7]), "r"(v[8]), "r"(v[9]), "r"(v[10]), "r"(v[11]),
          "r"(v[12]), "r"(v[13]), "r"(v[14]), "r"(v[15]), "r"(v[16]), "r"(v[17]), "r"(v[18]),
-         "r"(v[19]), "r"(v[20]), "r"(v[21]), "r"(v[22]), "r"(v[23]), "r"(v[24]), "r"(v[25]),
-         "r"(v[26]), "r"(v[27]), "r"(v[28]), "r"(v[29]), "r"(v[30]), "r"(v[31]), "r"(v[32]),
-         "r"(v[33]), "r"(v[34]), "r"(v[35]), "r"(v[36]), "r"(v[37]), "r"(v[38]), "r"(v[39]),
-         "r"(v[40]), "r"(v[41]), "r"(v[42]), "r"(v[43]), "r"(v[44]), "r"(v[45]), "r"(v[46]),
-         "r"(v[47])
+         "r"(v[19]), "r"(v[20]), "r"(v[21]), "r"(v[22]), "r"(v[23])
       : "memory");
 }
 
@@ -250,38 +269,57 @@ __device__ __forceinline__ float e_fetch(int ke, int EX0, int EY0, int nx, int n
 }
 
 // element (ex, ey) of layer ke: its 24 displacements from the ring slots of node layers ke
-// (bottom, local nodes 0-3) and ke + 1 (top, local nodes 4-7), split into TF32 hi (v[0..23])
-// and lo (v[24..47]) parts: the thread's row of the A operands
-__device__ __forceinline__ void a_row(uint32_t* v, const float* s0, const float* s1, int ex,
-                                      int ey) {
+// (bottom, local nodes 0-3) and ke + 1 (top, local nodes 4-7), scaled by 2^-s so that the
+// largest magnitude lies in [1/2, 1), t = x 2^-s, and split into FP16 parts h0 = fp16(t) and
+// h1 = fp16(2^11 (t - h0)): the thread's row of the A operand, K order (h0 of DOFs 0..23, h1
+// of DOFs 0..23), two FP16 per 32-bit word (lower K index in the low half).  Returns 2^s.
+__device__ __forceinline__ float a_row(uint32_t* w, const float* s0, const float* s1, int ex,
+                                       int ey) {
+  float xv[KD];
+  float amax = 0.f;
 #pragma unroll
   for (int k = 0; k < KD; k++) {
     const int bn = k / 3, c = k % 3;
     const float* sx = (bn & 4) ? s1 : s0;
-    const float xv = sx[3 * ((ey + ((bn >> 1) & 1)) * TNX + ex + (bn & 1)) + c];
-    const uint32_t hi = tf32_round_bits(__float_as_uint(xv));
-    v[k] = hi;
-    v[KD + k] = __float_as_uint(xv - __uint_as_float(hi));
+    xv[k] = sx[3 * ((ey + ((bn >> 1) & 1)) * TNX + ex + (bn & 1)) + c];
+    amax = fmaxf(amax, fabsf(xv[k]));
   }
+  // 2^s with amax 2^-s in [1/2, 1): s = biased exponent of amax - 126 (a zero or subnormal
+  // row keeps s = 0: its parts then flush below the FP16 range, far below the FP32 rounding of
+  // any row that matters)
+  const int be = (int)((__float_as_uint(amax) >> 23) & 0xffu);
+  const int s = be > 0 ? min(be - 126, 127) : 0;                  // in [-125, 127]
+  const float down = __uint_as_float((uint32_t)(127 - s) << 23);  // 2^-s
+  const float up = __uint_as_float((uint32_t)(127 + s) << 23);    // 2^s
+  float h0f[KD], h1f[KD];
+#pragma unroll
+  for (int k = 0; k < KD; k++) {
+    const float t = xv[k] * down;
+    const __half h0 = __float2half_rn(t);
+    h0f[k] = t;
+    h1f[k] = 2048.f * (t - __half2float(h0));  // exact: t - h0 is exact in FP32
+  }
+#pragma unroll
+  for (int c = 0; c < KD / 2; c++) {
+    const __half2 p0 = __floats2half2_rn(h0f[2 * c], h0f[2 * c + 1]);
+    const __half2 p1 = __floats2half2_rn(h1f[2 * c], h1f[2 * c + 1]);
+    w[c] = *reinterpret_cast<const uint32_t*>(&p0);
+    w[KD / 2 + c] = *reinterpret_cast<const uint32_t*>(&p1);
+  }
+  return up;
 }
 
-// MT M-tiles x 3 split products x 3 K-steps into the accumulators at column d, then a commit
-// to the barrier (executed by one thread)
+// MT M-tiles x 3 K-steps of M128 N48 K16 into the accumulators at column d, then a commit to the
+// barrier (executed by one thread)
 template <int MT>
 __device__ __forceinline__ void issue_mmas(uint32_t d, uint32_t a, uint32_t bbase, uint32_t bar) {
   asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
 #pragma unroll
   for (int m = 0; m < MT; m++) {
-    const uint32_t ahi = a + (uint32_t)(48 * m), alo = ahi + (uint32_t)KD;
 #pragma unroll
-    for (int p = 0; p < 3; p++) {
-      const uint32_t aa = (p == 1) ? alo : ahi;
-      const uint32_t bb = (p == 2) ? bbase + B_BYTES : bbase;
-#pragma unroll
-      for (int s = 0; s < 3; s++)
-        mma_tf32_ts(d + (uint32_t)(m * NB), aa + (uint32_t)(8 * s), sdesc(bb + 2 * LBO * s),
-                    (p | s) ? 1u : 0u);
-    }
+    for (int s = 0; s < KA / 16; s++)
+      mma_f16_ts(d + (uint32_t)(m * NB), a + (uint32_t)(32 * m + 8 * s),
+                 sdesc(bbase + 2 * LBO * s), s ? 1u : 0u);
   }
   asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];\n"
                :: "r"(bar) : "memory");
@@ -293,19 +331,19 @@ k_ebe3tc(int nx, int ny, int nz, int nz_tile, const uint4* __restrict__ Bimg,
          const float* __restrict__ E, const uint8_t* __restrict__ mask,
          const float* __restrict__ x, float* __restrict__ y, const float* __restrict__ b,
          const float* __restrict__ Dinv, float omega, const int* done, float* __restrict__ dch,
-         float c1, int dmode) {
+         float c1, int dmode, float cl, float cm, uint32_t wait_limit) {
   using C = Cfg<TY>;
   constexpr int NT = C::NT, LAYER_NODES = C::LAYER_NODES, ONY = C::ONY, MT = C::MT;
   constexpr int OFF_B = C::OFF_B, OFF_X = C::OFF_X, OFF_P = C::OFF_P, OFF_BAR = C::OFF_BAR;
-  constexpr int A_COL = C::A_COL, TMEM_COLS = C::TMEM_COLS;
+  constexpr int ACC = C::ACC, TMEM_COLS = C::TMEM_COLS;
   extern __shared__ uint8_t smem_raw[];
   pdl_prologue();
   if (solve_done(done)) return;
   uint8_t* sm = smem_raw + ((128 - (smem_u32(smem_raw) & 127u)) & 127u);
   float* sxr = reinterpret_cast<float*>(sm + OFF_X);          // [2][LAYER_NODES][3]
   float* sP = reinterpret_cast<float*>(sm + OFF_P);           // [2][TY][TEX][PS]
-  uint64_t* bar = reinterpret_cast<uint64_t*>(sm + OFF_BAR);  // [2]
-  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(sm + OFF_BAR + 16);
+  uint64_t* bar = reinterpret_cast<uint64_t*>(sm + OFF_BAR);  // [3]; [2] never arrives
+  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(sm + OFF_BAR + 24);
   const uint32_t sbase = smem_u32(sm);
   const uint32_t bar0 = smem_u32(bar);  // barrier j at bar0 + 8 j
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
@@ -315,7 +353,7 @@ k_ebe3tc(int nx, int ny, int nz, int nz_tile, const uint4* __restrict__ Bimg,
   const int k0 = blockIdx.z * nz_tile;
   const int k1 = min(k0 + nz_tile, nz + 1);  // owned node layers [k0, k1)
 
-  // tensor memory (one warp), the MMA barriers, the B operands
+  // tensor memory (one warp), the MMA barriers, the B operand
   if (warp == 0) {
     asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;\n"
                  :: "r"(smem_u32(tmem_slot)), "r"(TMEM_COLS) : "memory");
@@ -324,9 +362,10 @@ k_ebe3tc(int nx, int ny, int nz, int nz_tile, const uint4* __restrict__ Bimg,
   if (tid == 0) {
     asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;\n" :: "r"(bar0), "r"(1) : "memory");
     asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;\n" :: "r"(bar0 + 8u), "r"(1) : "memory");
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;\n" :: "r"(bar0 + 16u), "r"(1) : "memory");
     asm volatile("fence.mbarrier_init.release.cluster;\n" ::: "memory");
   }
-  for (int t = tid; t < 2 * B_BYTES / 16; t += NT)
+  for (int t = tid; t < B_BYTES / 16; t += NT)
     reinterpret_cast<uint4*>(sm + OFF_B)[t] = Bimg[t];
 
   const bool owner = ex >= 1 && ey >= 1;
@@ -341,6 +380,7 @@ k_ebe3tc(int nx, int ny, int nz, int nz_tile, const uint4* __restrict__ Bimg,
   x_fetch<TY>(pre, k0 + 1, EX0, EY0, nx, ny, nz, mask, x);  // stored after layer k0 - 1 is built
   float e_cur = e_fetch(k0 - 1, EX0, EY0, nx, ny, nz, E);  // modulus of element layer ke
   float e_prev = 0.f;                                      // ... of layer ke - 1
+  float sc_prev = 1.f;                                     // 2^s of the row of layer ke - 1
   asm volatile("tcgen05.fence::before_thread_sync;\n" ::: "memory");
   __syncthreads();
   asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
@@ -351,6 +391,7 @@ k_ebe3tc(int nx, int ny, int nz, int nz_tile, const uint4* __restrict__ Bimg,
   float acc[3] = {0.f, 0.f, 0.f};  // node layer ke - 1: contributions gathered so far
   FinData fd;                      // finishing data of node layer ke - 1
   uint32_t parity = 0;             // bit j: phase of barrier j to wait for next
+  uint32_t pending = 0;            // bit j: MMAs committed to barrier j not yet seen complete
   bool failed = false;
 
   for (int ke = k0 - 1; ke <= k1; ke++) {
@@ -359,24 +400,33 @@ k_ebe3tc(int nx, int ny, int nz, int nz_tile, const uint4* __restrict__ Bimg,
     bool ok = true;
     if (ke >= k0) {
       // the MMAs of layer ke - 1 (every thread waits itself): their accumulators are read
-      // below, their A operands are overwritten now
-      ok = mbar_wait(bar0 + 8u * jp, (parity >> jp) & 1u);
-      parity ^= 1u << jp;
+      // below, their A operands are overwritten now.  The phase bit advances only on success,
+      // so that a block that gives up still knows which phase its MMAs in flight complete.
+      const bool probe = wait_limit < WAIT_LIMIT;  // test hook: a barrier nothing completes
+      ok = mbar_wait(probe ? bar0 + 16u : bar0 + 8u * jp, probe ? 0u : (parity >> jp) & 1u,
+                     wait_limit);
+      if (ok) {
+        parity ^= 1u << jp;
+        pending &= ~(1u << jp);
+      }
       asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
     }
+    float sc_now = 1.f;
     if (ok && mma_now) {
-      uint32_t v[2 * KD];
-      a_row(v, sxr + j * LAYER_NODES * 3, sxr + jp * LAYER_NODES * 3, ex, ey);
-      tmem_st48(tmem + lane_base + (uint32_t)(A_COL + 48 * mt), v);
+      uint32_t w[AW];
+      sc_now = a_row(w, sxr + j * LAYER_NODES * 3, sxr + jp * LAYER_NODES * 3, ex, ey);
+      tmem_st24(tmem + lane_base + (uint32_t)(32 * mt), w);
     }
     asm volatile("tcgen05.fence::before_thread_sync;\n" ::: "memory");
     if (__syncthreads_or(!ok)) {  // a wait that ran out anywhere stops the whole block
       failed = true;
       break;
     }
-    if (mma_now && tid == 0)
-      issue_mmas<MT>(tmem + (uint32_t)(j * MT * NB), tmem + (uint32_t)A_COL, sbase + OFF_B,
-                     bar0 + 8u * j);
+    if (mma_now) {
+      if (tid == 0)
+        issue_mmas<MT>(tmem + (uint32_t)(ACC + j * MT * NB), tmem, sbase + OFF_B, bar0 + 8u * j);
+      pending |= 1u << j;
+    }
     // refill the ring: node layer ke + 2 replaces layer ke (read by the row build above)
     if (mma_now && ke + 2 <= k1) {
       x_store<TY>(pre, sxr + j * LAYER_NODES * 3);
@@ -391,12 +441,13 @@ k_ebe3tc(int nx, int ny, int nz, int nz_tile, const uint4* __restrict__ Bimg,
     float pr[2][2][3];  // x-pair sums of element layer ke - 1 at node column ex: [dy][dz][c]
     if (ke >= k0) {
       // finish element layer ke - 1 and node layer ke - 1
-      float v[24];
-      tmem_ld24(tmem + lane_base + (uint32_t)((jp * MT + mt) * NB), v);
+      float v[NB];
+      tmem_ld48(tmem + lane_base + (uint32_t)(ACC + (jp * MT + mt) * NB), v);
+      const float sl = e_prev * sc_prev * cl, sm_ = e_prev * sc_prev * cm;
+#pragma unroll
+      for (int n = 0; n < KD; n++) v[n] = sl * v[n] + sm_ * v[KD + n];
       // x-pairs: node column ex gets the dx = 1 corners of element ex - 1 (previous lane) and
       // the dx = 0 corners of element ex; p[dy][dz][c]
-#pragma unroll
-      for (int n = 0; n < 24; n++) v[n] *= e_prev;
 #pragma unroll
       for (int dy = 0; dy < 2; dy++)
 #pragma unroll
@@ -465,14 +516,17 @@ k_ebe3tc(int nx, int ny, int nz, int nz_tile, const uint4* __restrict__ Bimg,
     }
     e_prev = e_cur;
     e_cur = e_next;
+    sc_prev = sc_now;
     fd = fd_next;
   }
 
   if (failed) {
     if (tid == 0) atomicExch(&g_tc_error, 1);
-    // let MMAs still in flight finish (bounded) before the tensor memory is released
-    mbar_wait(bar0, parity & 1u);
-    mbar_wait(bar0 + 8u, (parity >> 1) & 1u);
+    // MMAs still in flight write their accumulators until they complete: wait for them with
+    // the full limit before the tensor memory is released
+#pragma unroll
+    for (int q = 0; q < 2; q++)
+      if ((pending >> q) & 1u) mbar_wait(bar0 + 8u * q, (parity >> q) & 1u, WAIT_LIMIT);
   }
   asm volatile("tcgen05.fence::before_thread_sync;\n" ::: "memory");
   __syncthreads();
@@ -508,9 +562,10 @@ void launch_tile(cudaStream_t s, const Ebe& op, const float* x, float* y, const 
   float* dch = MODE == MODE_CHEB ? (float*)ch->d : nullptr;
   const float c1 = MODE == MODE_CHEB ? (float)ch->c1 : 0.f;
   const int dm = MODE == MODE_CHEB ? ch->dmode : 0;
+  const uint32_t wl = g_first_wait_limit > 0 ? (uint32_t)g_first_wait_limit : WAIT_LIMIT;
   LAUNCH((k_ebe3tc<MODE, TY>), grid, C::NT, smem, s, op.nx, op.ny, op.nz, nzt,
          reinterpret_cast<const uint4*>(op.Ktc), (const float*)op.E, op.mask, x, y, b, Dinv,
-         (float)omega, done, dch, c1, dm);
+         (float)omega, done, dch, c1, dm, op.tc_cl, op.tc_cm, wl);
 }
 
 template <int MODE>
@@ -522,28 +577,40 @@ void launch_mode(cudaStream_t s, const Ebe& op, const float* x, float* y, const 
 
 }  // namespace
 
-void ebe3d_tc_operand(const double* Ke, uint32_t* img) {
-  // B_hi then B_lo: row n < 24 is Ke row n (Ke is symmetric), rows 24..31 are zero
-  for (int i = 0; i < 2 * B_BYTES / 4; i++) img[i] = 0u;
-  for (int n = 0; n < KD; n++)
+void ebe3d_tc_operand(double nu, uint32_t* img, float* cl, float* cm) {
+  // K_l, K_m: the hex8 element stiffness of D = m m^T and of D = diag(2, 2, 2, 1, 1, 1); Ke =
+  // lambda K_l + mu K_m for E = 1.  Rows 0..23 of B are 72 K_l, rows 24..47 are 72 K_m (both
+  // symmetric, so row n is also column n): K columns 0..23 (against h0) hold the integers,
+  // K columns 24..47 (against h1 = 2^11 (t - h0)) hold them times 2^-11.
+  std::vector<double> Kl, Km;
+  std::vector<double> Dl(36, 0.0), Dm(36, 0.0);
+  for (int i = 0; i < 3; i++)
+    for (int j = 0; j < 3; j++) Dl[i * 6 + j] = 1.0;
+  for (int i = 0; i < 6; i++) Dm[i * 6 + i] = i < 3 ? 2.0 : 1.0;
+  element_stiffness_D(3, Dl.data(), Kl);
+  element_stiffness_D(3, Dm.data(), Km);
+  uint16_t* h = reinterpret_cast<uint16_t*>(img);
+  for (int i = 0; i < B_BYTES / 2; i++) h[i] = 0;
+  for (int n = 0; n < NB; n++)
     for (int k = 0; k < KD; k++) {
-      const float v = (float)Ke[n * KD + k];
-      uint32_t u;
-      memcpy(&u, &v, 4);
-      const uint32_t hi = tf32_round_bits(u);
-      float fh;
-      memcpy(&fh, &hi, 4);
-      const double rest = Ke[n * KD + k] - (double)fh;
-      const float fl = (float)rest;
-      uint32_t ul;
-      memcpy(&ul, &fl, 4);
-      const uint32_t lo = tf32_round_bits(ul);
-      img[op_off(n, k) / 4] = hi;
-      img[(B_BYTES + op_off(n, k)) / 4] = lo;
+      const double v = KDEN * (n < KD ? Kl[n * KD + k] : Km[(n - KD) * KD + k]);
+      const double r = std::nearbyint(v);
+      if (std::fabs(v - r) > 1e-9 || std::fabs(r) > 2048.0)
+        TOMG_THROW(TOMG_E_INVALID, "element stiffness part is not a small integer / 72");
+      const __half hv = __double2half(r);             // exact: |r| <= 2048
+      const __half hs = __double2half(r / 2048.0);    // exact: a power-of-two scaling, normal
+      uint16_t bits, bits_s;
+      std::memcpy(&bits, &hv, 2);
+      std::memcpy(&bits_s, &hs, 2);
+      h[op_off(n, k) / 2] = bits;
+      h[op_off(n, KD + k) / 2] = bits_s;
     }
+  const double lam = nu / ((1.0 + nu) * (1.0 - 2.0 * nu)), mu = 1.0 / (2.0 * (1.0 + nu));
+  *cl = (float)(lam / KDEN);
+  *cm = (float)(mu / KDEN);
 }
 
-int ebe3d_tc_operand_words() { return 2 * B_BYTES / 4; }
+int ebe3d_tc_operand_words() { return B_BYTES / 4; }
 
 void ebe3d_tc_launch(cudaStream_t s, int mode, const Ebe& op, const float* x, float* y,
                      const float* b, const float* Dinv, double omega, const int* done,
@@ -619,5 +686,8 @@ bool ebe3d_tc_error(cudaStream_t s) {
   }
   return v != 0;
 }
+
+// polls of the in-loop MMA completion waits of later launches (0 restores the default)
+void ebe3d_tc_set_wait_limit(int polls) { g_first_wait_limit = polls > 0 ? polls : 0; }
 
 }  // namespace tomg

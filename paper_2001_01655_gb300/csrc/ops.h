@@ -3,6 +3,8 @@
 // device flag: once it is set the solve-loop kernels return immediately.
 #pragma once
 
+#include <vector>
+
 #include <functional>
 
 #include "common.cuh"
@@ -39,12 +41,14 @@ struct Ebe {
   const uint8_t* mask;
   int tile = 0;    // quad4 FP32: nodes per thread of the tiled kernel (1, 2, 4; 0 = 4)
   const void* Kh = nullptr;  // host copy of Ke (T); the tiled kernels take Ke by value
-  // hex8 FP32: element contractions on the tensor cores (3xTF32) when tc != 0; Ktc holds the
-  // split Ke operand images (ebe3d_tc_operand), tc_nz the node layers per block (0 = 8)
+  // hex8 FP32: element contractions on the tensor cores when tc != 0; Ktc holds the integer
+  // FP16 B operand (ebe3d_tc_operand), tc_cl / tc_cm its scales lambda / 72, mu / 72, tc_nz the
+  // node layers per block (0 = 8)
   int tc = 0;
   int tc_nz = 0;
   int tc_ty = 0;   // element rows per block of the tensor-core kernel (8 or 4; 0 = 8)
   const void* Ktc = nullptr;
+  float tc_cl = 0.f, tc_cm = 0.f;
 };
 template <class T>
 void ebe_op(cudaStream_t s, int mode, const Ebe& op, const T* x, T* y, const T* b,
@@ -63,12 +67,20 @@ int ebe2d_autotune(cudaStream_t s, const Ebe& op, const float* Dinv);
 void ebe3d_launch(cudaStream_t s, int mode, const Ebe& op, const float* x, float* y,
                   const float* b, const float* Dinv, double omega, const int* done,
                   const ChebArg* ch = nullptr);
-// hex8 FP32 on the tensor cores (k_ebe3tc.cu): tcgen05 kind::tf32 split products, same modes
+// hex8 FP32 on the tensor cores (k_ebe3tc.cu): tcgen05 kind::f16, x split in two FP16 parts
+// against the integer parts of Ke, same modes
 void ebe3d_tc_launch(cudaStream_t s, int mode, const Ebe& op, const float* x, float* y,
                      const float* b, const float* Dinv, double omega, const int* done,
                      const ChebArg* ch = nullptr);
-// Ke (24 x 24, FP64) -> TF32 hi and lo B-operand images in the kernel's shared-memory layout
-void ebe3d_tc_operand(const double* Ke, uint32_t* img);
+// B operand of the tensor-core kernel for Poisson ratio nu: 72 K_l and 72 K_m (Ke = lambda K_l
+// + mu K_m) as FP16 in the kernel's shared-memory layout; cl = lambda / 72, cm = mu / 72
+void ebe3d_tc_operand(double nu, uint32_t* img, float* cl, float* cm);
+// polls of the tensor-core kernel's in-loop MMA waits in later launches (0 = the default);
+// a test shortens it to make the waits run out and exercise the error path
+void ebe3d_tc_set_wait_limit(int polls);
+// element stiffness of the unit quad4 / hex8 element for a constitutive matrix D (3x3 / 6x6,
+// row-major), 2x2(x2) Gauss rule
+void element_stiffness_D(int dim, const double* D, std::vector<double>& Ke);
 int ebe3d_tc_operand_words();
 // fastest tile of the tensor-core kernel for this grid, rows * 1000 + node layers per block
 // (tc_ty, tc_nz), timed once per grid shape and cached

@@ -20,7 +20,7 @@ namespace tomg {
 // element stiffness by 2x2(x2) Gauss quadrature on the unit element (bilinear quad4 plane
 // stress, trilinear hex8 isotropic); local node a = (a&1, a>>1&1, a>>2&1), DOF = dim*a + c
 void element_stiffness_host(int dim, double nu, std::vector<double>& Ke) {
-  const int nn = 1 << dim, nd = dim * nn, ns = dim == 2 ? 3 : 6;
+  const int ns = dim == 2 ? 3 : 6;
   std::vector<double> D(ns * ns, 0.0);
   if (dim == 2) {
     const double c = 1.0 / (1.0 - nu * nu);
@@ -31,6 +31,11 @@ void element_stiffness_host(int dim, double nu, std::vector<double>& Ke) {
       for (int j = 0; j < 3; j++) D[i * 6 + j] = lam + (i == j ? 2.0 * mu : 0.0);
     for (int i = 3; i < 6; i++) D[i * 6 + i] = mu;
   }
+  element_stiffness_D(dim, D.data(), Ke);
+}
+
+void element_stiffness_D(int dim, const double* D, std::vector<double>& Ke) {
+  const int nn = 1 << dim, nd = dim * nn, ns = dim == 2 ? 3 : 6;
   Ke.assign(nd * nd, 0.0);
   const double g[2] = {0.5 - 0.5 / std::sqrt(3.0), 0.5 + 0.5 / std::sqrt(3.0)};
   const double w = std::pow(0.5, dim);
@@ -118,11 +123,13 @@ template <> struct V<float> {
   static Ebe ebe(const tomg_problem* P) {
     Ebe op{P->dim, P->nx, P->ny, P->nz, P->Ke32.p, P->E32.p, P->mask.p, P->ebe_tile,
            P->Ke32_host.data()};
-    const bool tc = P->tc_mode >= 0 ? P->tc_mode != 0 : P->opt.prec == TOMG_PREC_3XTF32_VCYCLE;
+    const bool tc = P->tc_mode >= 0 ? P->tc_mode != 0 : P->opt.prec == TOMG_PREC_TC_VCYCLE;
     op.tc = (P->dim == 3 && tc && P->Ketc.p) ? 1 : 0;
     op.tc_nz = P->tc_nz;
     op.tc_ty = P->tc_ty;
     op.Ktc = P->Ketc.p;
+    op.tc_cl = P->tc_cl;
+    op.tc_cm = P->tc_cm;
     return op;
   }
 };
@@ -134,7 +141,7 @@ struct TcScope {
   tomg_problem* P;
   int saved;
   TcScope(tomg_problem* p, int prec) : P(p), saved(p->tc_mode) {
-    P->tc_mode = prec == TOMG_PREC_3XTF32_VCYCLE ? 1 : 0;
+    P->tc_mode = prec == TOMG_PREC_TC_VCYCLE ? 1 : 0;
   }
   ~TcScope() { P->tc_mode = saved; }
 };
@@ -677,7 +684,7 @@ void problem_init(tomg_problem* P) {
   CK(cudaMemcpyAsync(P->Ke32.p, P->Ke32_host.data(), nk * 4, cudaMemcpyHostToDevice, s));
   if (P->dim == 3) {
     std::vector<uint32_t> img(ebe3d_tc_operand_words());
-    ebe3d_tc_operand(P->Ke_host.data(), img.data());
+    ebe3d_tc_operand(P->nu, img.data(), &P->tc_cl, &P->tc_cm);
     P->Ketc.resize(img.size());
     CK(cudaMemcpyAsync(P->Ketc.p, img.data(), img.size() * 4, cudaMemcpyHostToDevice, s));
     CK(cudaStreamSynchronize(s));  // img is a host temporary
@@ -761,8 +768,8 @@ void setup(tomg_problem* P, const tomg_options& opt) {
     ebe_block_diag_inv(s, V<double>::ebe(P), L0->D64.p, L0->D32.p);
     if (P->dim == 2 && opt.prec != TOMG_PREC_FP64 && P->ebe_tile == 0)
       P->ebe_tile = ebe2d_autotune(s, V<float>::ebe(P), L0->D32.p);
-    if (P->dim == 3 && opt.prec == TOMG_PREC_3XTF32_VCYCLE && P->tc_nz == 0 && P->Ketc.p) {
-      TcScope tcs(P, TOMG_PREC_3XTF32_VCYCLE);
+    if (P->dim == 3 && opt.prec == TOMG_PREC_TC_VCYCLE && P->tc_nz == 0 && P->Ketc.p) {
+      TcScope tcs(P, TOMG_PREC_TC_VCYCLE);
       const int code = ebe3d_tc_autotune(s, V<float>::ebe(P), L0->D32.p);
       P->tc_nz = code % 1000;
       P->tc_ty = code / 1000;
@@ -1238,7 +1245,7 @@ tomg_status solve(tomg_problem* P, int nrhs, const double* f, double* u, int on_
     for (int k = 0; k < slots; k++) join_from(P, *P->works[k]);
   }
   CK(cudaStreamSynchronize(st(P)));
-  if (P->dim == 3 && P->opt.prec == TOMG_PREC_3XTF32_VCYCLE && ebe3d_tc_error(st(P)))
+  if (P->dim == 3 && P->opt.prec == TOMG_PREC_TC_VCYCLE && ebe3d_tc_error(st(P)))
     for (int j = 0; j < nrhs; j++) res[j].status = TOMG_E_TIMEOUT;
   if (P->opt.pc == TOMG_PC_HYBRID && P->opt.adaptive_geo && P->adapt_geo > 0) {
     // adaptive hybrid (Sec. 4.4): a solve over the iteration limit moves the next setup one
@@ -1455,7 +1462,7 @@ void level_apply(tomg_problem* P, int level, int prec, const double* x, double* 
     cast_f32_f64(s, lw.y32.p, y, n);
   }
   CK(cudaStreamSynchronize(s));
-  if (P->dim == 3 && prec == TOMG_PREC_3XTF32_VCYCLE && ebe3d_tc_error(s))
+  if (P->dim == 3 && prec == TOMG_PREC_TC_VCYCLE && ebe3d_tc_error(s))
     TOMG_THROW(TOMG_E_TIMEOUT, "tensor-core element kernel: MMA completion wait expired");
 }
 

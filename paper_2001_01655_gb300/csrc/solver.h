@@ -133,7 +133,8 @@ struct tomg_problem {
   int tc_nz = 0;       // node layers per block of the tensor-core kernel (0 = default)
   int tc_ty = 0;       // element rows per block of the tensor-core kernel (0 = default)
   int adapt_geo = 0;   // adaptive hybrid: geometric levels of the next setup (0 = not started)
-  tomg::DBuf<uint32_t> Ketc;  // split Ke operand images of the tensor-core kernel (hex8)
+  tomg::DBuf<uint32_t> Ketc;  // FP16 integer B operand of the tensor-core kernel (hex8)
+  float tc_cl = 0.f, tc_cm = 0.f;  // its scales lambda / 72 and mu / 72
   tomg::DBuf<double> Ke64;
   tomg::DBuf<float> Ke32;
   tomg::DBuf<uint8_t> mask;

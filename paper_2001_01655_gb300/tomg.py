@@ -16,7 +16,7 @@ LIB_PATH = os.path.join(HERE, "_build", "libtomg.so")
 
 OK, NOT_CONVERGED, E_INVALID, E_OOM, E_CUDA, E_BREAKDOWN, E_TIMEOUT, E_BUDGET = 0, 1, -1, -2, -3, -4, -5, -6
 PC = {"gmg": 0, "amg": 1, "hybrid": 2, "jacobi": 3}
-PREC = {"fp64": 0, "fp32": 1, "tf32x3": 2}
+PREC = {"fp64": 0, "fp32": 1, "tc": 2, "tf32x3": 2}
 SMOOTHER = {"jacobi": 0, "chebyshev": 1, "gmres": 2}
 KRYLOV = {"cg": 0, "fgmres": 1}
 
@@ -101,6 +101,7 @@ _SIGS = {
     "tomg_server_stats": (C.c_int, [_P, _D, _D, _D, _I64, C.POINTER(C.c_int),
                                     C.POINTER(C.c_size_t)]),
     "tomg_server_retire": (C.c_int, [_P, _P, C.c_int]),
+    "tomg_debug_tc_wait_limit": (C.c_int, [C.c_int]),
     "tomg_server_destroy": (C.c_int, [_P]),
 }
 
@@ -477,6 +478,11 @@ class Problem:
         Ke = np.zeros((nd, nd))
         _check(load().tomg_element_stiffness(self.h, C.c_void_p(Ke.ctypes.data)))
         return Ke
+
+
+def debug_tc_wait_limit(polls: int):
+    """Shorten the tensor-core kernel's MMA waits (tomg_debug_tc_wait_limit; 0 = default)."""
+    _check(load().tomg_debug_tc_wait_limit(int(polls)))
 
 
 class Server:

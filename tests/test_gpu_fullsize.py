@@ -82,7 +82,7 @@ def check_sampled(lib, P, p, u, f, nodes):
     assert np.all(np.abs(Ku - rows) <= 1e-13 * scale + 1e-300)
 
 
-@pytest.mark.parametrize("prec", ["fp32", "tf32x3"])
+@pytest.mark.parametrize("prec", ["fp32", "tc"])
 def test_cantilever3d_full_sampled(lib, ctx, prec):
     p = W.cantilever_3d(192, 96, 96, seed=0)
     P = lib.Problem.from_workload(ctx, p)
@@ -97,7 +97,7 @@ def test_cantilever3d_full_sampled(lib, ctx, prec):
     assert abs(r["compliance"] - ref["compliance"]) <= 1e-6 * abs(ref["compliance"])
 
 
-@pytest.mark.parametrize("prec,smoother", [("fp32", "jacobi"), ("tf32x3", "chebyshev")])
+@pytest.mark.parametrize("prec,smoother", [("fp32", "jacobi"), ("tc", "chebyshev")])
 def test_batched_full_sampled(lib, ctx, prec, smoother):
     """Both the paper's configuration and the one the bench times (3xTF32 tensor-core operator,
     degree-2 Chebyshev, 4 concurrent slots)."""

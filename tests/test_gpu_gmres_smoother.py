@@ -44,14 +44,14 @@ def test_vcycle_gmres(lib, ctx, pc, kw, okw, dim, grid, m):
     P.setup(pc=pc, prec="fp32", smoother="gmres", gmres_steps=m, **kw)
     assert relerr(P.vcycle(r), zr) < 1e-3
     if dim == 3:
-        P.setup(pc=pc, prec="tf32x3", smoother="gmres", gmres_steps=m, **kw)
+        P.setup(pc=pc, prec="tc", smoother="gmres", gmres_steps=m, **kw)
         assert relerr(P.vcycle(r), zr) < 1e-3
 
 
 @pytest.mark.parametrize("pc,kw,okw", [
     ("gmg", dict(n_levels=4), dict(n_levels=4)),
     ("hybrid", dict(n_geo_levels=2, max_coarse_dofs=200), dict(n_geo=2, cap=200))])
-@pytest.mark.parametrize("prec", ["fp64", "fp32", "tf32x3"])
+@pytest.mark.parametrize("prec", ["fp64", "fp32", "tc"])
 @pytest.mark.parametrize("case", ["mbb", "cant2d", "cant3d"])
 @pytest.mark.parametrize("krylov", ["cg", "fgmres"])
 def test_solve_gmres_smoother_vs_direct(lib, ctx, pc, kw, okw, prec, case, krylov):
@@ -63,7 +63,7 @@ def test_solve_gmres_smoother_vs_direct(lib, ctx, pc, kw, okw, prec, case, krylo
         p = W.cantilever_3d(16, 8, 8, seed=0, sigma=2.0)
         if pc == "gmg":
             kw, okw = dict(n_levels=3), dict(n_levels=3)
-    if prec == "tf32x3" and case != "cant3d":
+    if prec == "tc" and case != "cant3d":
         pytest.skip("the tensor-core operator is the hex8 one")
     P = lib.Problem.from_workload(ctx, p)
     if case == "cant2d" and pc == "gmg":

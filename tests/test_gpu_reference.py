@@ -53,8 +53,8 @@ def cant3d():
     return p, refs.load("cantilever3d_192x96x96")[0], refs.projections(p.n)
 
 
-@pytest.mark.parametrize("prec,smoother", [("tf32x3", "chebyshev"), ("fp32", "chebyshev"),
-                                           ("fp64", "chebyshev"), ("tf32x3", "jacobi")])
+@pytest.mark.parametrize("prec,smoother", [("tc", "chebyshev"), ("fp32", "chebyshev"),
+                                           ("fp64", "chebyshev"), ("tc", "jacobi")])
 def test_cantilever3d_full_vs_oracle(lib, ctx, cant3d, prec, smoother):
     p, ref, G = cant3d
     P = lib.Problem.from_workload(ctx, p)
@@ -69,7 +69,7 @@ def batched():
     return p, refs.load("batched3d_128x64x64"), refs.projections(p.n)
 
 
-@pytest.mark.parametrize("prec,smoother,conc", [("tf32x3", "chebyshev", 4), ("fp32", "jacobi", 1)])
+@pytest.mark.parametrize("prec,smoother,conc", [("tc", "chebyshev", 4), ("fp32", "jacobi", 1)])
 def test_batched_full_vs_oracle(lib, ctx, batched, prec, smoother, conc):
     p, ref, G = batched
     P = lib.Problem.from_workload(ctx, p)
@@ -107,7 +107,7 @@ def test_mbb_gmg4_fp64_jacobi_vs_oracle(lib, ctx):
     check(u[0], res[0], ref, refs.projections(p.n))
 
 
-@pytest.mark.parametrize("prec", ["tf32x3", "fp32", "fp64"])
+@pytest.mark.parametrize("prec", ["tc", "fp32", "fp64"])
 def test_cantilever3d_32x16x16_vs_direct(lib, ctx, prec):
     p = W.cantilever_3d(32, 16, 16, seed=0)
     ref = osolve.direct(p)

@@ -1,12 +1,14 @@
 """GPU parity of the hex8 level-0 operator whose element contractions run on the tensor cores
-(tcgen05, TF32 split products: prec "tf32x3"), called through the C ABI, against the CPU
-oracle on the same seeded inputs.
+(tcgen05 kind::f16: each element row scaled by a power of two and split into two FP16 parts,
+against the exact integer parts of Ke; prec "tc", formerly "tc"), called through the C ABI,
+against the CPU oracle on the same seeded inputs.
 
 Tolerance of one apply: 2e-6 per entry of the summed element-product magnitudes
 sum_e E_e |Ke| |x_e| (the rounding scale of an element-by-element sum; the assembled |A| |x| is
-smaller where element contributions cancel).  3xTF32 drops only the lo x lo product, about
-2^-22 of each element product; the tensor cores' FP32 accumulation adds a few 2^-24 per term.
-Measured maxima on these grids: 8.6e-7 (tensor cores) and 2.6e-7 (CUDA-core FP32).  Solves: the 1e-8 true relative residual and 1e-6 displacement /
+smaller where element contributions cancel).  The split loses below 2^-22 of each entry (and
+2^-36 of the row's largest entry); a CPU emulation of the split on rows spanning eight orders
+of magnitude stays within 1.2e-7 of the element scale; the tensor cores' FP32 accumulation adds
+a few 2^-24 per term.  Solves: the 1e-8 true relative residual and 1e-6 displacement /
 compliance bounds of every other solve test."""
 import numpy as np
 import pytest
@@ -38,14 +40,14 @@ GRIDS = [(1, 1, 1), (3, 2, 1), (9, 8, 7), (13, 7, 5), (30, 6, 7), (31, 7, 8), (4
 def test_tc_operator_apply(lib, ctx, grid, contrast):
     p = W.random_problem(3, *grid, seed=31, contrast=contrast)
     P = lib.Problem.from_workload(ctx, p)
-    P.setup(pc="jacobi", prec="tf32x3")
+    P.setup(pc="jacobi", prec="tc")
     A0 = mg.fine_operator(p)
     E = fem.simp(p.rho, p.E0, p.Emin, p.penal)
     Kabs = fem.masked_operator(abs(fem.assemble(3, p.nx, p.ny, p.nz, E,
                                                 np.abs(fem.element_stiffness(3, p.nu)))), p.fixed)
     rng = np.random.default_rng(7)
     for x in (rng.standard_normal(p.n), rng.standard_normal(p.n) * 10.0 ** rng.uniform(-4, 4, p.n)):
-        y = P.level_apply(0, x, "tf32x3")
+        y = P.level_apply(0, x, "tc")
         scale = Kabs @ np.abs(x)
         assert np.all(np.abs(y - A0 @ x) <= 2e-6 * scale + 1e-300)
 
@@ -58,7 +60,7 @@ def test_tc_matches_cuda_core_fp32(lib, ctx, grid):
     P.setup(pc="jacobi", prec="fp32")
     x = np.random.default_rng(3).standard_normal(p.n)
     y32 = P.level_apply(0, x, "fp32")
-    ytc = P.level_apply(0, x, "tf32x3")
+    ytc = P.level_apply(0, x, "tc")
     y64 = P.level_apply(0, x, "fp64")
     assert relerr(ytc, y64) < 1e-6
     assert relerr(y32, y64) < 1e-6
@@ -73,7 +75,7 @@ def test_tc_vcycle_close_to_fp32(lib, ctx):
     r = np.random.default_rng(4).standard_normal(p.n) * fem.free_mask(p.n, p.fixed)
     P.setup(pc="gmg", n_levels=3, prec="fp64")
     z64 = P.vcycle(r)
-    P.setup(pc="gmg", n_levels=3, prec="tf32x3")
+    P.setup(pc="gmg", n_levels=3, prec="tc")
     ztc = P.vcycle(r)
     P.setup(pc="gmg", n_levels=3, prec="fp32")
     z32 = P.vcycle(r)
@@ -86,7 +88,7 @@ def test_tc_vcycle_close_to_fp32(lib, ctx):
 def test_tc_solve_vs_direct(lib, ctx, pc, kw):
     p = W.cantilever_3d(16, 8, 8, seed=0, sigma=2.0)
     P = lib.Problem.from_workload(ctx, p)
-    P.setup(pc=pc, prec="tf32x3", rtol=1e-8, **kw)
+    P.setup(pc=pc, prec="tc", rtol=1e-8, **kw)
     u, res = P.solve(p.f)
     r = res[0]
     assert r["status"] == 0, r
@@ -107,9 +109,41 @@ def test_tc_multi_rhs_concurrent_slots(lib, ctx):
     equals its solve alone (fixed-order sums in the kernel: bit-identical)."""
     p = W.random_problem(3, 20, 10, 10, seed=34, contrast="minmax", nrhs=3)
     P = lib.Problem.from_workload(ctx, p)
-    P.setup(pc="gmg", n_levels=3, prec="tf32x3", concurrency=3)
+    P.setup(pc="gmg", n_levels=3, prec="tc", concurrency=3)
     U, res = P.solve(p.f)
     for j in range(3):
         assert res[j]["status"] == 0
         u1, _ = P.solve(p.f[j])
         assert np.array_equal(U[j], np.asarray(u1).reshape(-1))
+
+
+def test_tc_wait_timeout_path(lib, ctx):
+    """The bounded-wait path of the tensor-core kernel, exercised without a fault: with the test
+    hook set (tomg_debug_tc_wait_limit) the blocks' waits watch a barrier that nothing arrives
+    on and give up after one poll, so every block records the failure, waits with the full limit
+    for the MMAs it has in flight, frees its tensor memory and returns; the apply reports
+    TOMG_E_TIMEOUT.  With the hook cleared the record is clear and the operator and a solve give
+    the results of before."""
+    p = W.random_problem(3, 40, 20, 18, seed=35, contrast="minmax")
+    P = lib.Problem.from_workload(ctx, p)
+    P.setup(pc="gmg", n_levels=3, prec="tc", rtol=1e-8)
+    x = np.random.default_rng(8).standard_normal(p.n)
+    y_ref = P.level_apply(0, x, "tc")
+    u_ref, r_ref = P.solve(p.f)
+    timeouts = 0
+    lib.debug_tc_wait_limit(1)
+    try:
+        for _ in range(3):
+            try:
+                P.level_apply(0, x, "tc")
+            except lib.TomgError as e:
+                assert e.status == lib.E_TIMEOUT, e
+                timeouts += 1
+    finally:
+        lib.debug_tc_wait_limit(0)
+    assert timeouts == 3
+    assert np.array_equal(P.level_apply(0, x, "tc"), y_ref)
+    P.setup(pc="gmg", n_levels=3, prec="tc", rtol=1e-8)
+    u, r = P.solve(p.f)
+    assert r[0]["status"] == 0 and r[0]["iterations"] == r_ref[0]["iterations"]
+    assert np.array_equal(u, u_ref)
