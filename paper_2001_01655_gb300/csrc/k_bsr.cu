@@ -405,50 +405,66 @@ __global__ void __launch_bounds__(128) k_spgemm_num_w(int nrows, int64_t nnzC,
     if (lane == (t & 31)) Cb[t] = acc[t];
 }
 
+// Numeric phase, one warp per row of C: for each output block of the row the lanes first
+// search B's rows for the block column j in parallel (lane q takes A block q of the row), then
+// every hit, in ascending order of A's blocks, is applied by all lanes at once, lane q owning
+// scalars q and q + 32 of the BR x BC output block.  Each scalar sums A[r][t] B[t][c] over the
+// hits in A's order and t ascending (the order of a one-thread-per-block loop), and no FP64
+// instruction runs for a block that only some lanes would use.
 template <int BR, int BK, int BC>
-__global__ void __launch_bounds__(128) k_spgemm_num(int nrows, const int* __restrict__ Arp,
-                                                    const int* __restrict__ Aci,
-                                                    const double* __restrict__ VA,
-                                                    const int* __restrict__ Brp,
-                                                    const int* __restrict__ Bci,
-                                                    const double* __restrict__ VB,
-                                                    const int* __restrict__ Crp,
-                                                    const int* __restrict__ Cci, double* VC) {
-  const int w = (blockIdx.x * blockDim.x + threadIdx.x) >> 5, lane = threadIdx.x & 31;
-  if (w >= nrows) return;
-  const int row = w;
-  for (int pc = Crp[row] + lane; pc < Crp[row + 1]; pc += 32) {
+__global__ void __launch_bounds__(128) k_spgemm_num_s(int nrows, const int* __restrict__ Arp,
+                                                      const int* __restrict__ Aci,
+                                                      const double* __restrict__ VA,
+                                                      const int* __restrict__ Brp,
+                                                      const int* __restrict__ Bci,
+                                                      const double* __restrict__ VB,
+                                                      const int* __restrict__ Crp,
+                                                      const int* __restrict__ Cci, double* VC) {
+  constexpr int NS = BR * BC;
+  static_assert(NS <= 64, "two output scalars per lane at most");
+  const int row = (int)(((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5);
+  const int lane = threadIdx.x & 31;
+  if (row >= nrows) return;  // warp-uniform
+  const int q0 = lane, q1 = lane + 32;
+  const int r0 = q0 / BC, c0 = q0 % BC, r1 = q1 / BC, c1 = q1 % BC;
+  const int a_lo = Arp[row], a_hi = Arp[row + 1];
+  for (int pc = Crp[row]; pc < Crp[row + 1]; pc++) {
     const int j = Cci[pc];
-    double acc[BR * BC];
-#pragma unroll
-    for (int t = 0; t < BR * BC; t++) acc[t] = 0.0;
-    for (int a = Arp[row]; a < Arp[row + 1]; a++) {
-      const int k = Aci[a];
-      const int hi = Brp[k + 1];
-      int l = Brp[k], h = hi;
-      while (l < h) {
-        const int mid = (l + h) >> 1;
-        if (Bci[mid] < j) l = mid + 1;
-        else h = mid;
-      }
-      if (l >= hi || Bci[l] != j) continue;
-      const double* Ab = VA + (int64_t)a * BR * BK;
-      const double* Bb = VB + (int64_t)l * BK * BC;
-      double bv[BK * BC];
-#pragma unroll
-      for (int t = 0; t < BK * BC; t++) bv[t] = Bb[t];
-#pragma unroll
-      for (int r = 0; r < BR; r++)
-#pragma unroll
-        for (int t = 0; t < BK; t++) {
-          const double av = Ab[r * BK + t];
-#pragma unroll
-          for (int c = 0; c < BC; c++) acc[r * BC + c] += av * bv[t * BC + c];
+    double acc0 = 0.0, acc1 = 0.0;
+    for (int base = a_lo; base < a_hi; base += 32) {
+      const int a = base + lane;
+      int l = -1;
+      if (a < a_hi) {
+        const int k = Aci[a];
+        const int bh = Brp[k + 1];
+        int lo = Brp[k], hi = bh;
+        while (lo < hi) {
+          const int mid = (lo + hi) >> 1;
+          if (Bci[mid] < j) lo = mid + 1;
+          else hi = mid;
         }
-    }
-    double* Cb = VC + (int64_t)pc * BR * BC;
+        if (lo < bh && Bci[lo] == j) l = lo;
+      }
+      unsigned hits = __ballot_sync(0xffffffffu, l >= 0);
+      while (hits) {
+        const int src = __ffs(hits) - 1;
+        hits &= hits - 1u;
+        const int lh = __shfl_sync(0xffffffffu, l, src);
+        const double* Ab = VA + (int64_t)(base + src) * BR * BK;
+        const double* Bb = VB + (int64_t)lh * BK * BC;
+        if (q0 < NS) {
 #pragma unroll
-    for (int t = 0; t < BR * BC; t++) Cb[t] = acc[t];
+          for (int t = 0; t < BK; t++) acc0 += Ab[r0 * BK + t] * Bb[t * BC + c0];
+        }
+        if (NS > 32 && q1 < NS) {
+#pragma unroll
+          for (int t = 0; t < BK; t++) acc1 += Ab[r1 * BK + t] * Bb[t * BC + c1];
+        }
+      }
+    }
+    double* Cb = VC + (int64_t)pc * NS;
+    if (q0 < NS) Cb[q0] = acc0;
+    if (NS > 32 && q1 < NS) Cb[q1] = acc1;
   }
 }
 
@@ -631,7 +647,7 @@ void spgemm_numeric(cudaStream_t s, const Bsr& A, const double* VA, const Bsr& B
                B.rp, B.ci, VB, C.rp, C.ci, VC);                                                \
       return;                                                                                  \
     }                                                                                          \
-    LAUNCH((k_spgemm_num<R, K, CC>), grid, 128, 0, s, A.nbr, A.rp, A.ci, VA, B.rp, B.ci, VB,   \
+    LAUNCH((k_spgemm_num_s<R, K, CC>), grid, 128, 0, s, A.nbr, A.rp, A.ci, VA, B.rp, B.ci, VB, \
            C.rp, C.ci, VC);                                                                    \
     return;                                                                                    \
   }

@@ -291,18 +291,13 @@ __device__ __forceinline__ float a_row(uint32_t* w, const float* s0, const float
   const int s = be > 0 ? min(be - 126, 127) : 0;                  // in [-125, 127]
   const float down = __uint_as_float((uint32_t)(127 - s) << 23);  // 2^-s
   const float up = __uint_as_float((uint32_t)(127 + s) << 23);    // 2^s
-  float h0f[KD], h1f[KD];
-#pragma unroll
-  for (int k = 0; k < KD; k++) {
-    const float t = xv[k] * down;
-    const __half h0 = __float2half_rn(t);
-    h0f[k] = t;
-    h1f[k] = 2048.f * (t - __half2float(h0));  // exact: t - h0 is exact in FP32
-  }
+  // h0 pairs packed by one conversion each; h1 from the exact remainder t - h0
 #pragma unroll
   for (int c = 0; c < KD / 2; c++) {
-    const __half2 p0 = __floats2half2_rn(h0f[2 * c], h0f[2 * c + 1]);
-    const __half2 p1 = __floats2half2_rn(h1f[2 * c], h1f[2 * c + 1]);
+    const float ta = xv[2 * c] * down, tb = xv[2 * c + 1] * down;
+    const __half2 p0 = __floats2half2_rn(ta, tb);
+    const float2 h0 = __half22float2(p0);
+    const __half2 p1 = __floats2half2_rn(2048.f * (ta - h0.x), 2048.f * (tb - h0.y));
     w[c] = *reinterpret_cast<const uint32_t*>(&p0);
     w[KD / 2 + c] = *reinterpret_cast<const uint32_t*>(&p1);
   }
