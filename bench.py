@@ -528,9 +528,10 @@ def stability_run(tomg, ctx, opts, nx=256, ny=1024):
 
 def batched_run(tomg, ctx, slots, reps=3, prec="tc", smoother="chebyshev", cheb_degree=2):
     """The 16 right-hand sides (8 point loads, 8 adjoint-like vectors) of the 3D hex8 128x64x64
-    case (1,635,075 DOFs) on one shared hierarchy: all 16 on `slots` concurrent solve slots,
-    against the same 16 one after another (one slot).  Median of `reps` runs, setup excluded;
-    every right-hand side compared with the oracle's reference."""
+    case (1,635,075 DOFs) on one shared hierarchy: as one block solve (every kernel launch
+    covers all 16), on `slots` concurrent solve slots, and one after another (one slot).
+    Median of `reps` runs, setup excluded; every right-hand side compared with the oracle's
+    reference."""
     import refs
     import workloads as W
     p = W.batched_3d()
@@ -538,9 +539,11 @@ def batched_run(tomg, ctx, slots, reps=3, prec="tc", smoother="chebyshev", cheb_
     ref = refs.load("batched3d_128x64x64")
     G = refs.projections(p.n)
     res = {}
-    for conc in (slots, 1):
+    for conc in ("block", slots, 1):
+        block = p.nrhs if conc == "block" else 0
         P.setup(pc="hybrid", prec=prec, n_geo_levels=3, max_coarse_dofs=1000, rtol=1e-8,
-                concurrency=conc, smoother=smoother, cheb_degree=cheb_degree)
+                concurrency=1 if conc == "block" else conc, block_rhs=block, smoother=smoother,
+                cheb_degree=cheb_degree)
         P.solve(p.f[:2])  # warm-up: graphs and vectors of the slots
         times, worst_rr = [], 0.0
         for _ in range(reps):
@@ -573,7 +576,10 @@ def batched_run(tomg, ctx, slots, reps=3, prec="tc", smoother="chebyshev", cheb_
     return {"workload": "3D cantilever hex8 128x64x64 (1,635,075 DOFs), 8 point loads + 8 "
                         "adjoint-like right-hand sides, hybrid hierarchy, FP32 V-cycle with "
                         "tensor-core element contractions",
-            "rhs": p.nrhs, "concurrent": dict(res[slots], slots=slots), "one_at_a_time": res[1],
+            "rhs": p.nrhs,
+            "block": dict(res["block"], mode="one block solve: every launch covers all %d "
+                                              "right-hand sides" % p.nrhs),
+            "concurrent": dict(res[slots], slots=slots), "one_at_a_time": res[1],
             "level0_kernels": kern}
 
 

@@ -107,6 +107,16 @@ typedef struct {
   int gmres_restart;   /* FGMRES restart length m, 1..200                             30       */
   int gmres_steps;     /* GMRES smoother: Arnoldi steps (operator applies) per smoothing,
                           1..8                                                        2        */
+  int block_rhs;       /* block solve of several right-hand sides (Sec. 2.2, 4.2: load cases
+                          and adjoint right-hand sides on one hierarchy): with R = block_rhs
+                          >= 2, tomg_solve advances up to R right-hand sides together in one
+                          flexible-CG loop, one captured graph whose every kernel launch
+                          covers all of them (per-right-hand-side scalars, reductions and
+                          convergence: a converged right-hand side stops updating while the
+                          others go on); each result is bit-identical to its solve alone
+                          (the same sums in the same order per right-hand side).  Needs hex8, prec
+                          TOMG_PREC_TC_VCYCLE, the Jacobi or Chebyshev smoother and krylov 0;
+                          R <= 64.  0 or 1: solve slots (concurrency)                  0        */
 } tomg_options;
 
 typedef struct {

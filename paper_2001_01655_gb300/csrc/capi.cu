@@ -24,6 +24,13 @@ static thread_local bool g_pdl = false;
 bool pdl_enabled() { return g_pdl; }
 void set_pdl(bool on) { g_pdl = on; }
 
+static thread_local int g_batch = 1;
+int batch_rhs() { return g_batch; }
+void set_batch_rhs(int r) { g_batch = r > 1 ? r : 1; }
+void no_batch(const char* what) {
+  if (g_batch > 1) TOMG_THROW(TOMG_E_INVALID, "%s has no block (several right-hand sides) form", what);
+}
+
 static thread_local cudaStream_t g_alloc_stream = nullptr;
 cudaStream_t alloc_stream() { return g_alloc_stream; }
 void set_alloc_stream(cudaStream_t s) { g_alloc_stream = s; }

@@ -54,6 +54,24 @@ extern std::atomic<int64_t> g_launches;
 // completed and its writes are visible, before touching any data.
 bool pdl_enabled();
 void set_pdl(bool on);
+// Right-hand sides of a block solve (Sec. 2.2, 4.2: several loads and adjoint right-hand sides
+// on one hierarchy): while a BatchScope of R > 1 is active on this thread, the wrappers of the
+// solve's kernels launch R copies of their grid (blockIdx.y, or a factor of blockIdx.z for the
+// 3D-tiled element kernel) and the kernels offset every vector by the copy index times the
+// vector's length; matrices, moduli, masks and smoother blocks are shared.  Wrappers without a
+// block form throw while a scope is active.
+int batch_rhs();
+void set_batch_rhs(int r);
+// distance between consecutive right-hand sides of a block vector whose vectors have n
+// entries: n rounded up to a multiple of 4, so that every right-hand side starts on a 16-byte
+// boundary (FP64 and FP32) and the paired 8 / 16-byte vector loads stay aligned
+__host__ __device__ __forceinline__ int64_t rhs_stride(int64_t n) { return (n + 3) & ~(int64_t)3; }
+struct BatchScope {
+  int saved;
+  explicit BatchScope(int r) : saved(batch_rhs()) { set_batch_rhs(r); }
+  ~BatchScope() { set_batch_rhs(saved); }
+};
+void no_batch(const char* what);  // throws E_INVALID inside a BatchScope of R > 1
 
 __device__ __forceinline__ void pdl_prologue() {
   asm volatile("griddepcontrol.launch_dependents;" ::: "memory");

@@ -11,15 +11,15 @@
 
 namespace tomg {
 
-// True in exactly one block of the grid: the last one to arrive, after every block has made
-// its partials visible.  All threads of every block must call it (no early exit before it).
-// The ticket is left at zero for the next launch.
-__device__ __forceinline__ bool last_block(unsigned* ticket) {
+// True in exactly one of the nblk blocks that share `ticket`: the last one to arrive, after
+// every one of them has made its partials visible (nblk = the whole grid, or the blocks of one
+// right-hand side of a block solve, which each have their own ticket).  All threads of every
+// block must call it (no early exit before it).  The ticket is left at zero for the next launch.
+__device__ __forceinline__ bool last_block(unsigned* ticket, unsigned nblk) {
   __shared__ unsigned s_last;
   __syncthreads();
   if (threadIdx.x == 0 && threadIdx.y == 0 && threadIdx.z == 0) {
     __threadfence();
-    const unsigned nblk = gridDim.x * gridDim.y * gridDim.z;
     const unsigned t = atomicAdd(ticket, 1u);
     s_last = (t == nblk - 1) ? 1u : 0u;
     if (s_last) *ticket = 0u;

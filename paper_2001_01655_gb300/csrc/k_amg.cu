@@ -278,7 +278,7 @@ __global__ void __launch_bounds__(256) k_power_step(int nbr, const int* __restri
   const double tot = block_sum(ss, sred);
   if (threadIdx.x == 0) partials[blockIdx.x] = tot;
   // the last block forms ||w|| and 1 / ||w|| for the next step (fixed summation order)
-  if (last_block(ticket)) {
+  if (last_block(ticket, gridDim.x * gridDim.y * gridDim.z)) {
     double a = 0.0;
     for (int q = threadIdx.x; q < (int)gridDim.x; q += blockDim.x) a += __ldcg(partials + q);
     a = block_sum(a, sred);

@@ -37,6 +37,13 @@ __global__ void __launch_bounds__(256) k_bsr(int nbr, const int* __restrict__ rp
   constexpr bool PRE = B <= 3;
   constexpr bool NEED_D = MODE == MODE_JACOBI || MODE == MODE_CHEB || MODE == MODE_CHEB0;
   pdl_launch();
+  {  // right-hand side blockIdx.y of a block solve
+    const int64_t vo = (int64_t)blockIdx.y * rhs_stride((int64_t)B * nbr);
+    if (x) x += vo;
+    y += vo;
+    if (b) b += vo;
+    if (xo) xo += vo;
+  }
   const int gtid = blockIdx.x * blockDim.x + threadIdx.x;
   const int i = gtid / G, sub = gtid % G;
   const bool live = i < nbr;
@@ -144,7 +151,7 @@ __global__ void __launch_bounds__(256) k_bsr(int nbr, const int* __restrict__ rp
 }
 
 template <class T, int BR, int BC, int G>
-__global__ void __launch_bounds__(256) k_bsr_rect(int nbr, const int* __restrict__ rp,
+__global__ void __launch_bounds__(256) k_bsr_rect(int nbr, int nbc, const int* __restrict__ rp,
                                                   const int* __restrict__ ci,
                                                   const T* __restrict__ V, const T* __restrict__ x,
                                                   T* __restrict__ y, int accumulate,
@@ -152,6 +159,8 @@ __global__ void __launch_bounds__(256) k_bsr_rect(int nbr, const int* __restrict
   // the transfer operator is fixed during a solve: row bounds and this lane's first block are
   // fetched before waiting for the producer of x
   pdl_launch();
+  x += (int64_t)blockIdx.y * rhs_stride((int64_t)BC * nbc);  // right-hand side blockIdx.y
+  y += (int64_t)blockIdx.y * rhs_stride((int64_t)BR * nbr);
   const int gtid = blockIdx.x * blockDim.x + threadIdx.x;
   const int i = gtid / G, sub = gtid % G;
   const bool live = i < nbr;
@@ -528,7 +537,7 @@ template <class T>
 void bsr_op(cudaStream_t s, int mode, const Bsr& A, const T* V, const T* x, T* y, const T* b,
             const T* Dinv, double omega, const int* done, const ChebArg* ch) {
   const int G = lanes_for(A);
-  const int grid = ceil_div((int64_t)A.nbr * G, 256);
+  const dim3 grid(ceil_div((int64_t)A.nbr * G, 256), batch_rhs());
   const bool cheb = mode == MODE_CHEB || mode == MODE_CHEB0;
   if (cheb && !ch) TOMG_THROW(TOMG_E_INVALID, "Chebyshev step without its state");
   T* xo = mode == MODE_RESID0 ? const_cast<T*>(x) : (cheb ? (T*)ch->d : nullptr);
@@ -565,8 +574,8 @@ template <class T>
 void bsr_spmv_rect(cudaStream_t s, const Bsr& A, const T* V, const T* x, T* y, int accumulate,
                    const int* done) {
   const int G = lanes_for(A);
-  const int grid = ceil_div((int64_t)A.nbr * G, 256);
-#define RL(R, C, GG) LAUNCH((k_bsr_rect<T, R, C, GG>), grid, 256, 0, s, A.nbr, A.rp, A.ci, V, x, y, accumulate, done)
+  const dim3 grid(ceil_div((int64_t)A.nbr * G, 256), batch_rhs());
+#define RL(R, C, GG) LAUNCH((k_bsr_rect<T, R, C, GG>), grid, 256, 0, s, A.nbr, A.nbc, A.rp, A.ci, V, x, y, accumulate, done)
 #define RECT(R, C)                     \
   if (A.br == R && A.bc == C) {        \
     if (G == 4) RL(R, C, 4);           \

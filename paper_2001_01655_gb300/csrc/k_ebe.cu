@@ -210,6 +210,7 @@ void launch_ebe(cudaStream_t s, const Ebe& op, const T* x, T* y, const T* b, con
                     omega, done, ch);
     return;
   }
+  no_batch("the element operator other than the tensor-core hex8 kernel");
   if (DIM == 3 && sizeof(T) == 4 && !DOT) {
     ebe3d_launch(s, MODE, op, reinterpret_cast<const float*>(x), reinterpret_cast<float*>(y),
                  reinterpret_cast<const float*>(b), reinterpret_cast<const float*>(Dinv), omega,

@@ -326,7 +326,7 @@ k_ebe3tc(int nx, int ny, int nz, int nz_tile, const uint4* __restrict__ Bimg,
          const float* __restrict__ E, const uint8_t* __restrict__ mask,
          const float* __restrict__ x, float* __restrict__ y, const float* __restrict__ b,
          const float* __restrict__ Dinv, float omega, const int* done, float* __restrict__ dch,
-         float c1, int dmode, float cl, float cm, uint32_t wait_limit) {
+         float c1, int dmode, float cl, float cm, uint32_t wait_limit, int nzc) {
   using C = Cfg<TY>;
   constexpr int NT = C::NT, LAYER_NODES = C::LAYER_NODES, ONY = C::ONY, MT = C::MT;
   constexpr int OFF_B = C::OFF_B, OFF_X = C::OFF_X, OFF_P = C::OFF_P, OFF_BAR = C::OFF_BAR;
@@ -345,7 +345,16 @@ k_ebe3tc(int nx, int ny, int nz, int nz_tile, const uint4* __restrict__ Bimg,
   const int ex = lane, ey = warp;  // element of this thread; node (ex, ey) if owned
 
   const int EX0 = blockIdx.x * ONX - 1, EY0 = blockIdx.y * ONY - 1;
-  const int k0 = blockIdx.z * nz_tile;
+  // blockIdx.z = chunk of node layers + nzc x right-hand side of a block solve
+  const int zc = blockIdx.z % nzc, rhs = blockIdx.z / nzc;
+  {
+    const int64_t vo = (int64_t)rhs * rhs_stride((int64_t)3 * (nx + 1) * (ny + 1) * (nz + 1));
+    x += vo;
+    y += vo;
+    if (b) b += vo;
+    if (dch) dch += vo;
+  }
+  const int k0 = zc * nz_tile;
   const int k1 = min(k0 + nz_tile, nz + 1);  // owned node layers [k0, k1)
 
   // tensor memory (one warp), the MMA barriers, the B operand
@@ -552,7 +561,8 @@ void launch_tile(cudaStream_t s, const Ebe& op, const float* x, float* y, const 
     smem = bytes;
   }
   const int nzt = op.tc_nz > 0 ? op.tc_nz : 8;
-  dim3 grid(ceil_div(op.nx + 1, ONX), ceil_div(op.ny + 1, C::ONY), ceil_div(op.nz + 1, nzt));
+  const int nzc = ceil_div(op.nz + 1, nzt);
+  dim3 grid(ceil_div(op.nx + 1, ONX), ceil_div(op.ny + 1, C::ONY), nzc * batch_rhs());
   if (MODE == MODE_CHEB && !ch) TOMG_THROW(TOMG_E_INVALID, "Chebyshev step without its state");
   float* dch = MODE == MODE_CHEB ? (float*)ch->d : nullptr;
   const float c1 = MODE == MODE_CHEB ? (float)ch->c1 : 0.f;
@@ -560,7 +570,7 @@ void launch_tile(cudaStream_t s, const Ebe& op, const float* x, float* y, const 
   const uint32_t wl = g_first_wait_limit > 0 ? (uint32_t)g_first_wait_limit : WAIT_LIMIT;
   LAUNCH((k_ebe3tc<MODE, TY>), grid, C::NT, smem, s, op.nx, op.ny, op.nz, nzt,
          reinterpret_cast<const uint4*>(op.Ktc), (const float*)op.E, op.mask, x, y, b, Dinv,
-         (float)omega, done, dch, c1, dm, op.tc_cl, op.tc_cm, wl);
+         (float)omega, done, dch, c1, dm, op.tc_cl, op.tc_cm, wl, nzc);
 }
 
 template <int MODE>

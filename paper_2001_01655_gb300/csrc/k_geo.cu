@@ -41,6 +41,13 @@ __global__ void __launch_bounds__(256) k_stencil(int nx, int ny, int nz, const T
   const int64_t nn = (int64_t)(nx + 1) * (ny + 1) * (DIM == 3 ? nz + 1 : 1);
   const int64_t node = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (node >= nn) return;
+  {  // right-hand side blockIdx.y of a block solve
+    const int64_t vo = (int64_t)blockIdx.y * rhs_stride(DIM * nn);
+    if (x) x += vo;
+    y += vo;
+    if (b) b += vo;
+    if (xo) xo += vo;
+  }
   T Sr[PRE ? NO * BB : 1];
   if (PRE) {
 #pragma unroll
@@ -124,8 +131,18 @@ __global__ void __launch_bounds__(256) k_stencil_apply_dot(int nx, int ny, int n
   constexpr int NO = (DIM == 3) ? 27 : 9, BB = DIM * DIM;
   __shared__ double sred[32];
   pdl_prologue();
-  if (solve_done(done)) return;
   const int64_t nn = (int64_t)(nx + 1) * (ny + 1) * (DIM == 3 ? nz + 1 : 1);
+  {  // right-hand side blockIdx.y of a block solve: its vectors, partials and scalar state
+    const int64_t vo = (int64_t)blockIdx.y * rhs_stride(DIM * nn);
+    x += vo;
+    y += vo;
+    if (partials) partials += (int64_t)blockIdx.y * gridDim.x;
+    if (sc) {
+      sc += blockIdx.y;
+      if (done) done = &sc->done;
+    }
+  }
+  if (solve_done(done)) return;
   const int64_t node = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   double dotv = 0.0;
   if (node < nn) {
@@ -156,7 +173,8 @@ __global__ void __launch_bounds__(256) k_stencil_apply_dot(int nx, int ny, int n
   if (!partials) return;  // plain y = S x (uniform over the grid)
   const double tot = block_sum(dotv, sred);
   if (threadIdx.x == 0) partials[blockIdx.x] = tot;
-  if (sc && last_block(&sc->tk[TK_ALPHA])) finish_body(FIN_ALPHA, partials, gridDim.x, nullptr, 0, sc, sred);
+  if (sc && last_block(&sc->tk[TK_ALPHA], gridDim.x))
+    finish_body(FIN_ALPHA, partials, gridDim.x, nullptr, 0, sc, sred);
 }
 
 template <int DIM>
@@ -289,6 +307,11 @@ __global__ void k_restrict(int fnx, int fny, int fnz, int cnx, int cny, int cnz,
   const int64_t nnc = (int64_t)(cnx + 1) * (cny + 1) * (DIM == 3 ? cnz + 1 : 1);
   const int64_t I = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (I >= nnc) return;
+  {  // right-hand side blockIdx.y of a block solve
+    const int64_t nnf = (int64_t)(fnx + 1) * (fny + 1) * (DIM == 3 ? fnz + 1 : 1);
+    rf += (int64_t)blockIdx.y * rhs_stride(DIM * nnf);
+    bc += (int64_t)blockIdx.y * rhs_stride(DIM * nnc);
+  }
   int Ix, Iy, Iz;
   node_ijk(I, cnx, cny, DIM, Ix, Iy, Iz);
   T acc[DIM];
@@ -339,6 +362,11 @@ __global__ void k_prolong_add(int fnx, int fny, int fnz, int cnx, int cny, int c
   const int64_t nnf = (int64_t)(fnx + 1) * (fny + 1) * (DIM == 3 ? fnz + 1 : 1);
   const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= nnf) return;
+  {  // right-hand side blockIdx.y of a block solve
+    const int64_t nnc = (int64_t)(cnx + 1) * (cny + 1) * (DIM == 3 ? cnz + 1 : 1);
+    xc += (int64_t)blockIdx.y * rhs_stride(DIM * nnc);
+    xf += (int64_t)blockIdx.y * rhs_stride(DIM * nnf);
+  }
   int x, y, z;
   node_ijk(i, fnx, fny, DIM, x, y, z);
   int Ix[2], Iy[2], Iz[2] = {0, 0};
@@ -445,7 +473,7 @@ template <class T>
 void stencil_op(cudaStream_t s, int mode, const Geo& g, const T* S, const T* x, T* y, const T* b,
                 const T* Dinv, double omega, const int* done, const ChebArg* ch) {
   const int64_t nn = g.nodes();
-  const int grid = ceil_div(nn, 256);
+  const dim3 grid(ceil_div(nn, 256), batch_rhs());
   const bool cheb = mode == MODE_CHEB || mode == MODE_CHEB0;
   if (cheb && !ch) TOMG_THROW(TOMG_E_INVALID, "Chebyshev step without its state");
   T* xo = mode == MODE_RESID0 ? const_cast<T*>(x) : (cheb ? (T*)ch->d : nullptr);
@@ -480,7 +508,7 @@ int stencil_blocks(const Geo& g) { return ceil_div(g.nodes(), 256); }
 
 void stencil_apply_dot(cudaStream_t s, const Geo& g, const double* S, const double* x, double* y,
                        const int* done, double* partials, Scalars* sc) {
-  const int grid = stencil_blocks(g);
+  const dim3 grid(stencil_blocks(g), batch_rhs());
   if (g.dim == 2)
     LAUNCH(k_stencil_apply_dot<2>, grid, 256, 0, s, g.nx, g.ny, g.nz, S, x, y, done, partials, sc);
   else
@@ -513,7 +541,7 @@ void stencil_rap(cudaStream_t s, const Geo& f, const Geo& c, const double* Sf, d
 
 template <class T>
 void geo_restrict(cudaStream_t s, const Geo& f, const Geo& c, const T* rf, T* bc, const int* done) {
-  const int grid = ceil_div(c.nodes(), 256);
+  const dim3 grid(ceil_div(c.nodes(), 256), batch_rhs());
   if (f.dim == 2)
     LAUNCH((k_restrict<T, 2>), grid, 256, 0, s, f.nx, f.ny, f.nz, c.nx, c.ny, c.nz, rf, bc, done);
   else
@@ -527,7 +555,7 @@ template void geo_restrict<double>(cudaStream_t, const Geo&, const Geo&, const d
 template <class T>
 void geo_prolong_add(cudaStream_t s, const Geo& f, const Geo& c, const T* xc, T* xf,
                      const int* done) {
-  const int grid = ceil_div(f.nodes(), 256);
+  const dim3 grid(ceil_div(f.nodes(), 256), batch_rhs());
   if (f.dim == 2)
     LAUNCH((k_prolong_add<T, 2>), grid, 256, 0, s, f.nx, f.ny, f.nz, c.nx, c.ny, c.nz, xc, xf, done);
   else

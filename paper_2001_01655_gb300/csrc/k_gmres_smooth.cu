@@ -39,7 +39,7 @@ __global__ void __launch_bounds__(GM_THREADS) k_gm_start(int64_t n, const T* __r
   }
   a = block_sum(a, sred);
   if (threadIdx.x == 0) parts[blockIdx.x] = a;
-  if (last_block(&st->tk)) {
+  if (last_block(&st->tk, gridDim.x * gridDim.y * gridDim.z)) {
     double t = 0.0;
     for (int q = threadIdx.x; q < (int)gridDim.x; q += blockDim.x) t += __ldcg(parts + q);
     t = block_sum(t, sred);
@@ -113,7 +113,7 @@ __global__ void __launch_bounds__(GM_THREADS) k_gm_dots(int64_t n, int j, const 
     const double a = block_sum(acc[k], sred);
     if (threadIdx.x == 0) parts[(int64_t)k * nb + blockIdx.x] = a;
   }
-  if (last_block(&st->tk)) {
+  if (last_block(&st->tk, gridDim.x * gridDim.y * gridDim.z)) {
     for (int k = 0; k <= j; k++) {
       double t = 0.0;
       for (int q = threadIdx.x; q < nb; q += blockDim.x) t += __ldcg(parts + (int64_t)k * nb + q);
@@ -201,7 +201,7 @@ __global__ void __launch_bounds__(GM_THREADS) k_gm_orth(int64_t n, int j, int m,
     const double a = block_sum(acc[GM_MAX], sred);
     if (threadIdx.x == 0) parts[(int64_t)GM_MAX * nb + blockIdx.x] = a;
   }
-  if (last_block(&st->tk)) {
+  if (last_block(&st->tk, gridDim.x * gridDim.y * gridDim.z)) {
     __shared__ double tot[GM_MAX + 1];
     for (int k = 0; k <= GM_MAX; k++) {
       if (k > j && k < GM_MAX) continue;

@@ -37,6 +37,9 @@ __global__ void __launch_bounds__(RED_THREADS) k_dot(const double* __restrict__ 
   __shared__ double sred[32];
   pdl_prologue();
   if (solve_done(done)) return;
+  x += (int64_t)blockIdx.y * rhs_stride(n);  // right-hand side blockIdx.y of a block solve
+  y += (int64_t)blockIdx.y * rhs_stride(n);
+  partials += (int64_t)blockIdx.y * gridDim.x;
   double s = 0.0;
   const int64_t np = (n + 1) / 2;
   for (int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; k < np; k += (int64_t)gridDim.x * blockDim.x) {
@@ -52,6 +55,9 @@ __global__ void __launch_bounds__(256) k_finish(int kind, const double* __restri
                                                  Scalars* sc) {
   __shared__ double sred[32];
   pdl_prologue();
+  sc += blockIdx.x;  // right-hand side blockIdx.x of a block solve
+  pa += (int64_t)blockIdx.x * na;
+  if (pb) pb += (int64_t)blockIdx.x * nb;
   if (kind != FIN_INIT && sc->done) return;
   finish_body(kind, pa, na, pb, nb, sc, sred);
 }
@@ -63,6 +69,16 @@ __global__ void __launch_bounds__(RED_THREADS) k_xr(double* __restrict__ x, doub
                                                     float* __restrict__ r32) {
   __shared__ double sred[32];
   pdl_prologue();
+  {  // right-hand side blockIdx.y of a block solve: its vectors, partials and scalar state
+    const int64_t vo = (int64_t)blockIdx.y * rhs_stride(n);
+    x += vo;
+    r += vo;
+    p += vo;
+    q += vo;
+    if (r32) r32 += vo;
+    partials += (int64_t)blockIdx.y * gridDim.x;
+    sc += blockIdx.y;
+  }
   if (sc->done) return;
   const double alpha = sc->alpha;
   double s = 0.0;
@@ -85,7 +101,8 @@ __global__ void __launch_bounds__(RED_THREADS) k_xr(double* __restrict__ x, doub
   }
   s = block_sum(s, sred);
   if (threadIdx.x == 0) partials[blockIdx.x] = s;
-  if (last_block(&sc->tk[TK_RR])) finish_body(FIN_RR, partials, gridDim.x, nullptr, 0, sc, sred);
+  if (last_block(&sc->tk[TK_RR], gridDim.x))
+    finish_body(FIN_RR, partials, gridDim.x, nullptr, 0, sc, sred);
 }
 
 // p = z + beta p.  The last kernel of an iteration: with has_cond it also sets the while
@@ -94,6 +111,9 @@ __global__ void __launch_bounds__(RED_THREADS) k_xr(double* __restrict__ x, doub
 __global__ void k_p(double* __restrict__ p, const double* __restrict__ z, int64_t n,
                     const Scalars* sc, cudaGraphConditionalHandle cond, int has_cond) {
   pdl_prologue();
+  p += (int64_t)blockIdx.y * rhs_stride(n);  // right-hand side blockIdx.y of a block solve
+  z += (int64_t)blockIdx.y * rhs_stride(n);
+  sc += blockIdx.y;
   const int done = *(volatile const int*)&sc->done;
   if (has_cond && blockIdx.x == 0 && threadIdx.x == 0) cudaGraphSetConditional(cond, done ? 0u : 1u);
   if (done) return;
@@ -114,9 +134,19 @@ __global__ void __launch_bounds__(RED_THREADS) k_zdots(const T* __restrict__ z, 
                                                        int kind) {
   __shared__ double sred[32];
   pdl_prologue();
+  const bool copy = (const void*)z != (const void*)z64;
+  {  // right-hand side blockIdx.y of a block solve
+    const int64_t vo = (int64_t)blockIdx.y * rhs_stride(n);
+    z += vo;
+    z64 += vo;
+    r += vo;
+    if (q) q += vo;
+    pa += (int64_t)blockIdx.y * gridDim.x;
+    if (q) pb += (int64_t)blockIdx.y * gridDim.x;
+    sc += blockIdx.y;
+  }
   if (sc->done) return;
   double a = 0.0, b = 0.0;
-  const bool copy = (const void*)z != (const void*)z64;
   const int64_t np = (n + 1) / 2;
   for (int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; k < np; k += (int64_t)gridDim.x * blockDim.x) {
     const auto zv = ld2(z, k, n);
@@ -138,8 +168,17 @@ __global__ void __launch_bounds__(RED_THREADS) k_zdots(const T* __restrict__ z, 
     pa[blockIdx.x] = a;
     if (q) pb[blockIdx.x] = b;
   }
-  if (last_block(&sc->tk[TK_DOTS]))
+  if (last_block(&sc->tk[TK_DOTS], gridDim.x))
     finish_body(kind, pa, gridDim.x, pb, q ? gridDim.x : 0, sc, sred);
+}
+
+// while condition of a captured block solve: go on while some right-hand side is not done
+__global__ void k_block_cond(const Scalars* sc, int nrhs, cudaGraphConditionalHandle cond) {
+  pdl_prologue();
+  if (threadIdx.x != 0) return;
+  int any = 0;
+  for (int r = 0; r < nrhs; r++) any |= (*(volatile const int*)&sc[r].done) ? 0 : 1;
+  cudaGraphSetConditional(cond, any ? 1u : 0u);
 }
 
 template <class T>
@@ -165,6 +204,8 @@ __global__ void k_jacobi0(int64_t nodes, const T* __restrict__ Dinv, const T* __
   pdl_launch();
   const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= nodes) return;
+  b += (int64_t)blockIdx.y * rhs_stride(B * nodes);  // right-hand side blockIdx.y
+  x += (int64_t)blockIdx.y * rhs_stride(B * nodes);
   T D[B * B];  // the smoother block is fixed during a solve: fetched before the wait
 #pragma unroll
   for (int t = 0; t < B * B; t++) D[t] = Dinv[(int64_t)B * B * i + t];
@@ -226,6 +267,8 @@ __global__ void k_gemv(int n, const T* __restrict__ A, const T* __restrict__ b, 
   pdl_launch();
   const int row = (blockIdx.x * blockDim.x + threadIdx.x) >> 5, lane = threadIdx.x & 31;
   if (row >= n) return;
+  b += (int64_t)blockIdx.y * rhs_stride(n);  // right-hand side blockIdx.y of a block solve
+  x += (int64_t)blockIdx.y * rhs_stride(n);
   const T* a = A + (int64_t)row * n;
   T ap[PF];
 #pragma unroll
@@ -440,28 +483,34 @@ void scale_into(cudaStream_t s, int64_t n, const double* w, double sc, double* v
 
 void dot_partials(cudaStream_t s, const double* x, const double* y, int64_t n, double* partials,
                   const int* done) {
-  LAUNCH(k_dot, grid_for(n), RED_THREADS, 0, s, x, y, n, partials, done);
+  LAUNCH(k_dot, dim3(grid_for(n), batch_rhs()), RED_THREADS, 0, s, x, y, n, partials, done);
 }
 
 void finish(cudaStream_t s, int kind, const double* pa, int na, const double* pb, int nb,
             Scalars* sc) {
-  LAUNCH(k_finish, 1, 256, 0, s, kind, pa, na, pb, nb, sc);
+  LAUNCH(k_finish, batch_rhs(), 256, 0, s, kind, pa, na, pb, nb, sc);
 }
 
 void xr_update(cudaStream_t s, double* x, double* r, const double* p, const double* q, int64_t n,
                Scalars* sc, double* partials, float* r32) {
-  LAUNCH(k_xr, grid_for(n), RED_THREADS, 0, s, x, r, p, q, n, sc, partials, r32);
+  LAUNCH(k_xr, dim3(grid_for(n), batch_rhs()), RED_THREADS, 0, s, x, r, p, q, n, sc, partials, r32);
 }
 
 void p_update(cudaStream_t s, double* p, const double* z, int64_t n, const Scalars* sc,
               cudaGraphConditionalHandle cond, int has_cond) {
-  LAUNCH(k_p, grid_for(n), RED_THREADS, 0, s, p, z, n, sc, cond, has_cond);
+  if (batch_rhs() > 1 && has_cond) TOMG_THROW(TOMG_E_INVALID, "block p update sets no condition");
+  LAUNCH(k_p, dim3(grid_for(n), batch_rhs()), RED_THREADS, 0, s, p, z, n, sc, cond, has_cond);
+}
+
+void block_cond(cudaStream_t s, const Scalars* sc, int nrhs, cudaGraphConditionalHandle cond) {
+  LAUNCH(k_block_cond, 1, 32, 0, s, sc, nrhs, cond);
 }
 
 template <class T>
 void z_dots(cudaStream_t s, const T* z, double* z64, const double* r, const double* q, int64_t n,
             double* pa, double* pb, Scalars* sc, int kind) {
-  LAUNCH((k_zdots<T>), grid_for(n), RED_THREADS, 0, s, z, z64, r, q, n, pa, pb, sc, kind);
+  LAUNCH((k_zdots<T>), dim3(grid_for(n), batch_rhs()), RED_THREADS, 0, s, z, z64, r, q, n, pa, pb,
+         sc, kind);
 }
 template void z_dots<float>(cudaStream_t, const float*, double*, const double*, const double*,
                             int64_t, double*, double*, Scalars*, int);
@@ -470,6 +519,9 @@ template void z_dots<double>(cudaStream_t, const double*, double*, const double*
 
 template <class T>
 void cast_in(cudaStream_t s, const double* a, T* b, int64_t n, const int* done) {
+  // elementwise: the right-hand sides of a block solve are one contiguous vector
+  if (batch_rhs() > 1 && done) TOMG_THROW(TOMG_E_INVALID, "block cast with a done flag");
+  if (batch_rhs() > 1) n = batch_rhs() * rhs_stride(n);  // padding entries included
   LAUNCH((k_cast_in<T>), grid_for(n), RED_THREADS, 0, s, a, b, n, done);
 }
 template void cast_in<float>(cudaStream_t, const double*, float*, int64_t, const int*);
@@ -480,13 +532,14 @@ void copy_f64(cudaStream_t s, const double* a, double* b, int64_t n, const int* 
 }
 
 void mask_vec(cudaStream_t s, const double* f, double* b, const uint8_t* mask, int dim, int64_t nn) {
+  no_batch("mask_vec");
   LAUNCH(k_mask_vec, ceil_div(nn, 256), 256, 0, s, f, b, mask, dim, nn);
 }
 
 template <class T>
 void jacobi0(cudaStream_t s, int bs, int64_t nodes, const T* Dinv, const T* b, T* x, double omega,
              const int* done) {
-  const int g = ceil_div(nodes, 256);
+  const dim3 g(ceil_div(nodes, 256), batch_rhs());
   if (bs == 2) LAUNCH((k_jacobi0<T, 2>), g, 256, 0, s, nodes, Dinv, b, x, (T)omega, done);
   else if (bs == 3) LAUNCH((k_jacobi0<T, 3>), g, 256, 0, s, nodes, Dinv, b, x, (T)omega, done);
   else if (bs == 6) LAUNCH((k_jacobi0<T, 6>), g, 256, 0, s, nodes, Dinv, b, x, (T)omega, done);
@@ -499,7 +552,8 @@ template void jacobi0<double>(cudaStream_t, int, int64_t, const double*, const d
 
 template <class T>
 void dense_gemv(cudaStream_t s, int n, const T* Ainv, const T* b, T* x, const int* done) {
-  LAUNCH((k_gemv<T>), ceil_div((int64_t)n * 32, 256), 256, 0, s, n, Ainv, b, x, done);
+  LAUNCH((k_gemv<T>), dim3(ceil_div((int64_t)n * 32, 256), batch_rhs()), 256, 0, s, n, Ainv, b, x,
+         done);
 }
 template void dense_gemv<float>(cudaStream_t, int, const float*, const float*, float*, const int*);
 template void dense_gemv<double>(cudaStream_t, int, const double*, const double*, double*,

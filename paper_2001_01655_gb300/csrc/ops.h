@@ -269,6 +269,8 @@ void finish(cudaStream_t s, int kind, const double* partA, int nA, const double*
 // x += alpha p, r -= alpha q, r32 = (float) r (nullable), then FIN_RR in the last block
 void xr_update(cudaStream_t s, double* x, double* r, const double* p, const double* q, int64_t n,
                Scalars* sc, double* partials, float* r32);
+// while condition of a captured block solve of nrhs right-hand sides: some one not done
+void block_cond(cudaStream_t s, const Scalars* sc, int nrhs, cudaGraphConditionalHandle cond);
 // p = z + beta p; with has_cond, also sets the graph's while condition to !done
 void p_update(cudaStream_t s, double* p, const double* z, int64_t n, const Scalars* sc,
               cudaGraphConditionalHandle cond, int has_cond);

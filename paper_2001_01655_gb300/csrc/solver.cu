@@ -374,6 +374,25 @@ void iteration_body(tomg_problem* P, Work& W) {
   p_update(s, W.p.p, W.z.p, n, sc, W.cond, W.has_cond);
 }
 
+// One outer iteration of a block solve: the iteration_body sequence with every launch covering
+// the W.block right-hand sides (BatchScope).  The Krylov kernels read each right-hand side's own
+// scalar state and leave a converged one untouched; the V-cycle between them runs for all of
+// them (its result is not used for a converged one).  The last kernel sets the captured loop's
+// condition from all done flags.
+void block_iteration_body(tomg_problem* P, Work& W) {
+  const int64_t n = P->n;
+  const int R = W.block;
+  Scalars* sc = W.sc.p;
+  cudaStream_t s = W.stream;
+  BatchScope bs(R);
+  fine64_apply_dot(P, s, W.p.p, W.q.p, &sc->done, W.partA.p, sc);  // + FIN_ALPHA per rhs
+  xr_update(s, W.x.p, W.r.p, W.p.p, W.q.p, n, sc, W.partA.p, W.lw[0].b32.p);  // + FIN_RR
+  vcycle<float>(P, W, 0, W.lw[0].b32.p, W.lw[0].y32.p, nullptr);
+  z_dots<float>(s, W.lw[0].y32.p, W.z.p, W.r.p, W.q.p, n, W.partA.p, W.partB.p, sc, FIN_BETA);
+  p_update(s, W.p.p, W.z.p, n, sc, 0, 0);
+  if (W.has_cond) block_cond(s, sc, R, W.cond);
+}
+
 void destroy_graph(Work& W) {
   if (W.gexec) cudaGraphExecDestroy(W.gexec);
   if (W.graph) cudaGraphDestroy(W.graph);
@@ -384,7 +403,11 @@ void destroy_graph(Work& W) {
 
 void build_graph(tomg_problem* P, Work& W) {
   destroy_graph(W);
-  const int mode = P->opt.use_graph;
+  const int mode = W.block > 1 ? 2 : P->opt.use_graph;
+  auto run_body = [&]() {
+    if (W.block > 1) block_iteration_body(P, W);
+    else iteration_body(P, W);
+  };
   if (mode <= 0) return;
   cudaStream_t s = W.stream;
   const int64_t saved = g_launches;
@@ -409,7 +432,7 @@ void build_graph(tomg_problem* P, Work& W) {
     W.cond = h;
     W.has_cond = 1;
     try {
-      iteration_body(P, W);
+      run_body();
     } catch (...) {
       W.has_cond = 0;
       cudaGraph_t dummy;
@@ -422,7 +445,7 @@ void build_graph(tomg_problem* P, Work& W) {
   } else {
     CK(cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal));
     try {
-      iteration_body(P, W);
+      run_body();
     } catch (...) {
       cudaGraph_t dummy;
       cudaStreamEndCapture(s, &dummy);
@@ -741,7 +764,9 @@ void setup(tomg_problem* P, const tomg_options& opt) {
       (opt.smoother == 1 && (opt.cheb_degree < 1 || opt.cheb_degree > 8 ||
                              !(opt.cheb_lower > 0.0) || !(opt.cheb_upper > opt.cheb_lower))) ||
       (opt.adaptive_geo != 0 && (opt.adaptive_iters < 1 || opt.adaptive_min_geo < 1)) ||
-      opt.krylov < 0 || opt.krylov > 1 ||
+      opt.krylov < 0 || opt.krylov > 1 || opt.block_rhs < 0 || opt.block_rhs > 64 ||
+      (opt.block_rhs > 1 && (P->dim != 3 || opt.prec != TOMG_PREC_TC_VCYCLE || opt.smoother == 2 ||
+                             opt.krylov != 0)) ||
       (opt.krylov == 1 && (opt.gmres_restart < 1 || opt.gmres_restart > 200)))
     TOMG_THROW(TOMG_E_INVALID, "invalid options");
   P->setup_valid = false;
@@ -1233,6 +1258,144 @@ void solve_fgmres(tomg_problem* P, int nrhs, const double* f, double* u, int on_
   join_from(P, W);
 }
 
+// Work of a block solve of R right-hand sides: every outer vector and the FP32 V-cycle vectors
+// of every level hold R vectors back to back (right-hand side r at r x length), R scalar
+// states, R x (blocks) reduction partials
+Work& ensure_block_work(tomg_problem* P, int R) {
+  if (P->bwork && P->bwork->block != R) P->bwork.reset();
+  if (!P->bwork) {
+    auto W = std::make_unique<Work>();
+    CK(cudaStreamCreateWithFlags(&W->stream, cudaStreamNonBlocking));
+    CK(cudaEventCreate(&W->ev0));
+    CK(cudaEventCreate(&W->ev1));
+    CK(cudaEventCreateWithFlags(&W->evdone, cudaEventDisableTiming));
+    CK(cudaEventCreateWithFlags(&W->evsync, cudaEventDisableTiming));
+    W->block = R;
+    W->np = std::max(stencil_blocks(Geo{P->dim, P->nx, P->ny, P->dim == 3 ? P->nz : 1}),
+                     red_blocks(P->n));
+    CK(cudaMallocHost((void**)&W->sc_host, sizeof(Scalars) * R));
+    CK(cudaMallocHost((void**)&W->partE_host, sizeof(double) * W->np * R));
+    CK(cudaMallocHost((void**)&W->partC_host, sizeof(double) * W->np * R));
+    P->bwork = std::move(W);
+  }
+  Work& W = *P->bwork;
+  if (W.built_for != P->setup_gen) {
+    for (auto* v : {&W.f, &W.bvec, &W.x, &W.r, &W.p, &W.q, &W.z, &W.t}) v->resize(rhs_stride(P->n) * R);
+    for (auto* v : {&W.partA, &W.partB, &W.partE, &W.partC}) v->resize((size_t)W.np * R);
+    W.sc.resize(R);
+    W.lw.resize(P->L.size());
+    for (size_t l = 0; l < P->L.size(); l++) {
+      LevelWork& lw = W.lw[l];
+      for (auto* v : {&lw.b32, &lw.x32, &lw.r32, &lw.y32}) v->resize(rhs_stride(P->L[l]->n) * R);
+    }
+    destroy_graph(W);
+    W.built_for = P->setup_gen;
+  }
+  return W;
+}
+
+// Block solve of right-hand sides [j0, j0 + R): one flexible-CG loop over all of them in one
+// captured graph (block_iteration_body), then the true residuals and compliances.  A right-hand
+// side whose recursive residual converged while its true one did not is finished by the
+// single-right-hand-side path from the block's iterate.
+void solve_block(tomg_problem* P, int j0, int R, const double* f, double* u, int on_device,
+                 tomg_result* res) {
+  Work& W = ensure_block_work(P, R);
+  cudaStream_t s = W.stream;
+  const int64_t n = P->n, ld = rhs_stride(n);  // right-hand side r at r x ld
+  const cudaMemcpyKind h2d = on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice;
+  fork_to(P, W);
+  CK(cudaEventRecord(W.ev0, s));
+  for (int r = 0; r < R; r++) {
+    CK(cudaMemcpyAsync(W.f.p + r * ld, f + (int64_t)(j0 + r) * n, n * 8, h2d, s));
+    CK(cudaMemcpyAsync(W.t.p + r * ld, u + (int64_t)(j0 + r) * n, n * 8, h2d, s));
+    mask_vec(s, W.f.p + r * ld, W.bvec.p + r * ld, P->mask.p, P->dim, P->nn);
+    mask_vec(s, W.t.p + r * ld, W.x.p + r * ld, P->mask.p, P->dim, P->nn);
+  }
+  if (!W.gexec) {
+    SetupTrace tr(s);
+    build_graph(P, W);
+    tr.mark("block graph build");
+  }
+  const int nr = red_blocks(n);
+  {
+    BatchScope bs(R);
+    fine64_resid(P, s, W.x.p, W.r.p, W.bvec.p);
+    dot_partials(s, W.r.p, W.r.p, n, W.partA.p, nullptr);
+    dot_partials(s, W.bvec.p, W.bvec.p, n, W.partB.p, nullptr);
+    for (int r = 0; r < R; r++) {
+      Scalars h;
+      memset(&h, 0, sizeof(h));
+      h.rtol2 = P->opt.rtol * P->opt.rtol;
+      h.max_iter = P->opt.max_iter;
+      h.flexible = 1;  // FP32 V-cycle
+      W.sc_host[r] = h;
+    }
+    CK(cudaMemcpyAsync(W.sc.p, W.sc_host, sizeof(Scalars) * R, cudaMemcpyHostToDevice, s));
+    finish(s, FIN_INIT, W.partA.p, nr, W.partB.p, nr, W.sc.p);
+    cast_in<float>(s, W.r.p, W.lw[0].b32.p, n, nullptr);
+    vcycle<float>(P, W, 0, W.lw[0].b32.p, W.lw[0].y32.p, nullptr);
+    z_dots<float>(s, W.lw[0].y32.p, W.z.p, W.r.p, nullptr, n, W.partA.p, W.partB.p, W.sc.p,
+                  FIN_RZ0);
+    copy_f64(s, W.z.p, W.p.p, n, nullptr);
+  }
+  CK(cudaGraphLaunch(W.gexec, s));
+  {
+    BatchScope bs(R);
+    fine64_resid(P, s, W.x.p, W.t.p, W.bvec.p);
+    dot_partials(s, W.t.p, W.t.p, n, W.partE.p, nullptr);
+    dot_partials(s, W.f.p, W.x.p, n, W.partC.p, nullptr);
+  }
+  CK(cudaMemcpyAsync(W.sc_host, W.sc.p, sizeof(Scalars) * R, cudaMemcpyDeviceToHost, s));
+  CK(cudaMemcpyAsync(W.partE_host, W.partE.p, sizeof(double) * nr * R, cudaMemcpyDeviceToHost, s));
+  CK(cudaMemcpyAsync(W.partC_host, W.partC.p, sizeof(double) * nr * R, cudaMemcpyDeviceToHost, s));
+  for (int r = 0; r < R; r++)
+    CK(cudaMemcpyAsync(u + (int64_t)(j0 + r) * n, W.x.p + r * ld, n * 8,
+                       on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost, s));
+  CK(cudaEventRecord(W.ev1, s));
+  CK(cudaEventSynchronize(W.ev1));
+  join_from(P, W);
+  float ms = 0.f;
+  CK(cudaEventElapsedTime(&ms, W.ev0, W.ev1));
+  int max_it = 0;
+  for (int r = 0; r < R; r++) max_it = std::max(max_it, W.sc_host[r].it);
+  g_launches += W.kernels_per_iter * std::max(1, max_it);
+  std::vector<int> again;
+  for (int r = 0; r < R; r++) {
+    const Scalars& sc = W.sc_host[r];
+    double rr_true = 0.0, comp = 0.0;
+    for (int q = 0; q < nr; q++) rr_true += W.partE_host[(size_t)r * nr + q];
+    for (int q = 0; q < nr; q++) comp += W.partC_host[(size_t)r * nr + q];
+    tomg_result& o = res[j0 + r];
+    o.iterations = sc.it;
+    o.rel_residual = sc.bb > 0.0 ? std::sqrt(rr_true / sc.bb) : 0.0;
+    o.compliance = comp;
+    o.setup_ms = P->setup_ms;
+    o.solve_ms = ms;
+    o.status = sc.status;
+    if (sc.status == TOMG_OK && sc.bb > 0.0 &&
+        !(rr_true <= P->opt.rtol * P->opt.rtol * sc.bb) && sc.it < P->opt.max_iter)
+      again.push_back(j0 + r);
+  }
+  // the single path restarts from the block's iterate (u now holds it)
+  for (int j : again) {
+    const int it0 = res[j].iterations;
+    const float ms0 = (float)res[j].solve_ms;
+    tomg_options o = P->opt;
+    P->opt.block_rhs = 0;
+    P->opt.max_iter = std::max(1, o.max_iter - it0);
+    try {
+      solve(P, 1, f + (int64_t)j * n, u + (int64_t)j * n, on_device, &res[j]);
+    } catch (...) {
+      P->opt = o;
+      throw;
+    }
+    P->opt = o;
+    res[j].iterations += it0;
+    res[j].solve_ms += ms0;
+  }
+}
+
 }  // namespace
 
 tomg_status solve(tomg_problem* P, int nrhs, const double* f, double* u, int on_device,
@@ -1242,6 +1405,25 @@ tomg_status solve(tomg_problem* P, int nrhs, const double* f, double* u, int on_
   if (nrhs == 0) return TOMG_OK;
   if (P->opt.krylov == 1) {
     solve_fgmres(P, nrhs, f, u, on_device, res);
+  } else if (P->opt.block_rhs > 1 && nrhs > 1) {
+    const int64_t n = P->n;
+    for (int j0 = 0; j0 < nrhs; j0 += P->opt.block_rhs) {
+      const int R = std::min(P->opt.block_rhs, nrhs - j0);
+      if (R > 1) {
+        solve_block(P, j0, R, f, u, on_device, res);
+        continue;
+      }
+      // a last single right-hand side: the slot path
+      const tomg_options o = P->opt;
+      P->opt.block_rhs = 0;
+      try {
+        solve(P, 1, f + j0 * n, u + j0 * n, on_device, res + j0);
+      } catch (...) {
+        P->opt = o;
+        throw;
+      }
+      P->opt = o;
+    }
   } else {
     const int slots = std::max(1, std::min(nrhs, P->opt.concurrency > 0 ? P->opt.concurrency : 1));
     for (int k = 0; k < slots; k++) ensure_work(P, k);
@@ -1617,7 +1799,10 @@ size_t tomg::problem_device_bytes(const tomg_problem* P) {
          l.Rrp.bytes() + l.Rci.bytes() + l.Pv64.bytes() + l.Rv64.bytes() + l.Pv32.bytes() +
          l.Rv32.bytes() + l.agg.bytes();
   }
-  for (const auto& wp : P->works) {
+  std::vector<const Work*> all;
+  for (const auto& wp : P->works) all.push_back(wp.get());
+  if (P->bwork) all.push_back(P->bwork.get());
+  for (const Work* wp : all) {
     const Work& w = *wp;
     b += w.f.bytes() + w.bvec.bytes() + w.x.bytes() + w.r.bytes() + w.p.bytes() + w.q.bytes() +
          w.z.bytes() + w.t.bytes() + w.partA.bytes() + w.partB.bytes() + w.partE.bytes() +
@@ -1633,6 +1818,7 @@ size_t tomg::problem_device_bytes(const tomg_problem* P) {
 tomg_problem::~tomg_problem() {
   if (stream) cudaStreamSynchronize(stream);
   works.clear();
+  bwork.reset();
   L.clear();
   if (flag_host) cudaFreeHost(flag_host);
   for (cudaEvent_t e : {ev0, ev1, ev_in, ev_out, ev_fork, ev_side, ev_fork2, ev_side2})

@@ -105,6 +105,7 @@ struct Work {
   int has_cond = 0;
   int64_t kernels_per_iter = 0;
   cudaEvent_t ev0 = nullptr, ev1 = nullptr, evdone = nullptr, evsync = nullptr;
+  int block = 0;  // right-hand sides of a block solve work (vectors and scalars x block); 0: slot
   // per right-hand side bookkeeping while a solve is in flight
   int rhs = -1;
   int attempts = 0;
@@ -151,8 +152,9 @@ struct tomg_problem {
   int nc = 0;  // coarsest DOFs
   tomg::DBuf<double> Ainv64;
   tomg::DBuf<float> Ainv32;
-  // solve slots
+  // solve slots, and the work of a block solve of several right-hand sides
   std::vector<std::unique_ptr<tomg::Work>> works;
+  std::unique_ptr<tomg::Work> bwork;
   int* flag_host = nullptr;  // pinned
   tomg::DBuf<int> flag_dev;
   cudaEvent_t ev0 = nullptr, ev1 = nullptr;

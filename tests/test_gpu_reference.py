@@ -69,11 +69,15 @@ def batched():
     return p, refs.load("batched3d_128x64x64"), refs.projections(p.n)
 
 
-@pytest.mark.parametrize("prec,smoother,conc", [("tc", "chebyshev", 4), ("fp32", "jacobi", 1)])
-def test_batched_full_vs_oracle(lib, ctx, batched, prec, smoother, conc):
+@pytest.mark.parametrize("prec,smoother,conc,block", [("tc", "chebyshev", 4, 0),
+                                                      ("fp32", "jacobi", 1, 0),
+                                                      ("tc", "chebyshev", 1, 16)])
+def test_batched_full_vs_oracle(lib, ctx, batched, prec, smoother, conc, block):
+    """The 16 right-hand sides on concurrent solve slots, one at a time, and as one block solve
+    (block_rhs = 16: every launch of the loop covers all 16)."""
     p, ref, G = batched
     P = lib.Problem.from_workload(ctx, p)
-    P.setup(prec=prec, smoother=smoother, cheb_degree=2, concurrency=conc, **HYB3)
+    P.setup(prec=prec, smoother=smoother, cheb_degree=2, concurrency=conc, block_rhs=block, **HYB3)
     u, res = P.solve(p.f)
     assert len(res) == 16
     for j in range(16):
