@@ -117,6 +117,12 @@ typedef struct {
                           (the same sums in the same order per right-hand side).  Needs hex8, prec
                           TOMG_PREC_TC_VCYCLE, the Jacobi or Chebyshev smoother and krylov 0;
                           R <= 64.  0 or 1: solve slots (concurrency)                  0        */
+  int fp64_tc;         /* hex8: the outer loop's FP64 K p and residuals with the element
+                          contractions on the tensor cores, exact integer products of 11-bit
+                          digits of each element's fixed-point displacements against the
+                          integer matrix C of Ke = c C (nu with a rational lambda / mu, e.g.
+                          0.3), FP64 scaling and node sums; 0: the assembled FP64 stencil on
+                          the FP64 pipe.  Ignored where nu admits no such C           1        */
 } tomg_options;
 
 typedef struct {

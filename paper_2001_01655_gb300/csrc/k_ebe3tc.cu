@@ -413,6 +413,9 @@ k_ebe3tc(int nx, int ny, int nz, int nz_tile, const uint4* __restrict__ Bimg,
         parity ^= 1u << jp;
         pending &= ~(1u << jp);
       }
+      // the tensor-memory stores and loads below are warp-collective: a warp takes part only
+      // if every lane saw the MMAs complete (otherwise the whole block gives up below)
+      ok = __all_sync(0xffffffffu, ok);
       asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
     }
     float sc_now = 1.f;

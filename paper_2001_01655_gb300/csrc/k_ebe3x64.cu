@@ -1,0 +1,559 @@
+// FP64 level-0 SIMP element operator on hex8 grids (Sec. 2.1 Eq. 2, Sec. 3.1: the outer Krylov
+// loop's K p and residuals) with the element contractions on the FP16 tensor cores, exact to
+// the FP64 rounding of the result.
+//
+// GB300 issues FP64 at about 2 FMAs per clock and SM, so the assembled 243-entry stencil the
+// FP64 apply used to run on is bound by that pipe.  Here every product of the element
+// contraction is computed exactly in integers on the tensor cores (the splitting idea of Ozaki
+// et al., 2012), and FP64 is left with the scaling and the node sums:
+//   * for nu with a rational ratio lambda / mu = p / q (nu = 0.3: 3 / 2), Ke = c C with C =
+//     p K_l + q K_m an integer matrix (K_l, K_m the 72-scaled parts; entries of C up to 88,
+//     absolute row sums up to 472) and c = mu / (72 q);
+//   * each element row x_e (24 values) is written in fixed point on its largest exponent:
+//     X_j = round(x_j 2^(52 - e)) with |X_j| <= 2^53, and cut into five digits of 11 bits, four
+//     unsigned (0..2047) and a signed top one; every digit is an exact FP16 value;
+//   * one MMA chain per digit (K = 24 padded to 32, N = 24 outputs padded to 32) accumulates
+//     sum_j C_oj d_j in FP32 exactly (|sum| < 2^20);
+//   * the digit sums are turned back into integers and combined in int64: Z_o = sum_j C_oj X_j
+//     exactly; y_o = (E_e c 2^(e - 52)) Z_o, one FP64 conversion and one FP64 product per
+//     output.
+// The result differs from the exact element product only by the rounding of X (2^-53 of the
+// row's largest entry) and the FP64 roundings of the conversion, the product and the node sums.
+// The FP64 pipe is left with these, the node sums and the dot product.
+//
+// Tiling as in the FP32 tensor-core kernel (k_ebe3tc.cu), with one M = 128 tile per element
+// layer (32 x 4 elements, 128 threads, 31 x 3 owned nodes): the block walks the element layers
+// of its column of nodes; per layer it builds the 5 digit rows of its elements in tensor
+// memory, issues 10 MMAs, waits, and folds the accumulators into node sums (x-neighbour by warp
+// shuffle, y-neighbour through shared memory, z in registers), all in a fixed order.  Tensor
+// memory: digit k of A at column 16 k, its accumulator at 80 + 32 k (256 columns, two blocks
+// per SM).  Modes: y = A x with the partials of x . y and FIN_ALPHA in the last block (the
+// outer apply), and r = b - A x.  All waits are bounded as in the FP32 kernel.
+#include <cuda_fp16.h>
+
+#include <cmath>
+#include <cstring>
+#include <vector>
+
+#include "finish.cuh"
+
+namespace tomg {
+
+namespace {
+
+constexpr int TEX = 32, TY = 4;              // elements of a layer tile in x and y
+constexpr int TNX = TEX + 1, TNY = TY + 1;   // nodes of a layer tile
+constexpr int ONX = TEX - 1, ONY = TY - 1;   // owned nodes per layer
+constexpr int NT = TEX * TY;                 // 128 threads, one element each
+constexpr int LAYER_NODES = TNX * TNY;       // 165
+constexpr int KD = 24;                       // element DOFs
+constexpr int ND = 5;                        // digits of 11 bits
+constexpr int NB = 32;                       // N: 24 outputs padded
+constexpr int KP = 32;                       // K per digit: 24 padded
+constexpr int LBO = 128;                     // core matrices adjacent in K
+constexpr int SBO = (KP / 8) * LBO;          // 8-row groups: 512
+constexpr int B_BYTES = (NB / 8) * SBO;      // 2048
+constexpr int A_COL = 0, ACC_COL = 80, TMEM_COLS = 256;
+constexpr int PS = 7;                        // staged y-pair partials: row stride (doubles)
+constexpr int OFF_B = 0;
+constexpr int OFF_X = OFF_B + B_BYTES;                         // x ring, FP64
+constexpr int OFF_P = OFF_X + 2 * LAYER_NODES * 3 * 8;         // y pairs, FP64
+constexpr int OFF_R = OFF_P + 2 * NT * PS * 8;                 // reduction scratch
+constexpr int OFF_BAR = OFF_R + 32 * 8;                        // mbarrier, TMEM address
+constexpr int SMEM_ALLOC = OFF_BAR + 16 + 128;
+static_assert(ACC_COL >= ND * KP / 2 && ACC_COL + ND * NB <= TMEM_COLS, "tensor memory map");
+static_assert(OFF_X % 16 == 0 && OFF_P % 16 == 0 && OFF_BAR % 8 == 0, "alignment");
+static_assert(LAYER_NODES <= 2 * NT, "two nodes per thread stage a layer");
+
+// kind::f16, D FP32, A and B FP16, K-major, N = 32, M = 128
+constexpr uint32_t IDESC = (1u << 4) | ((uint32_t)(NB >> 3) << 17) | ((uint32_t)(128 >> 4) << 24);
+constexpr uint32_t WAIT_LIMIT = 1u << 22;
+
+__device__ int g_x64_error;  // set by a block whose MMA completion wait ran out
+
+__device__ __forceinline__ uint32_t smem_u32(const void* p) {
+  return (uint32_t)__cvta_generic_to_shared(p);
+}
+__device__ __forceinline__ uint64_t sdesc(uint32_t addr) {
+  return (uint64_t)((addr & 0x3FFFFu) >> 4) | ((uint64_t)(LBO >> 4) << 16) |
+         ((uint64_t)(SBO >> 4) << 32) | (1ull << 46);
+}
+__host__ __device__ __forceinline__ int op_off(int row, int k) {
+  return (row >> 3) * SBO + (k >> 3) * LBO + (row & 7) * 16 + (k & 7) * 2;
+}
+__device__ __forceinline__ void mma_ts(uint32_t d, uint32_t a, uint64_t b, uint32_t acc) {
+  asm volatile(
+      "{\n\t.reg .pred p;\n\t"
+      "setp.ne.b32 p, %4, 0;\n\t"
+      "tcgen05.mma.cta_group::1.kind::f16 [%0], [%1], %2, %3, p;\n\t}\n"
+      :: "r"(d), "r"(a), "l"(b), "r"(IDESC), "r"(acc) : "memory");
+}
+__device__ __forceinline__ bool mbar_try(uint32_t bar, uint32_t parity) {
+  uint32_t ok;
+  asm volatile(
+      "{\n\t.reg .pred p;\n\t"
+      "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+      "selp.u32 %0, 1, 0, p;\n\t}\n"
+      : "=r"(ok) : "r"(bar), "r"(parity) : "memory");
+  return ok != 0;
+}
+__device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity) {
+  for (uint32_t i = 0; i < WAIT_LIMIT; i++)
+    if (mbar_try(bar, parity)) return true;
+  return false;
+}
+// 24 FP32 columns of this thread's lane
+__device__ __forceinline__ void tmem_ld24(uint32_t taddr, float* v) {
+  uint32_t r[24];
+  asm volatile(
+      "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,"
+      "%14,%15}, [%24];\n\t"
+      "tcgen05.ld.sync.aligned.32x32b.x8.b32 {%16,%17,%18,%19,%20,%21,%22,%23}, [%25];\n\t"
+      "tcgen05.wait::ld.sync.aligned;\n"
+      : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]),
+        "=r"(r[7]), "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]),
+        "=r"(r[14]), "=r"(r[15]), "=r"(r[16]), "=r"(r[17]), "=r"(r[18]), "=r"(r[19]),
+        "=r"(r[20]), "=r"(r[21]), "=r"(r[22]), "=r"(r[23])
+      : "r"(taddr), "r"(taddr + 16u)
+      : "memory");
+#pragma unroll
+  for (int i = 0; i < 24; i++) v[i] = __uint_as_float(r[i]);
+}
+// 16 32-bit columns of this thread's lane (no wait: the caller waits once for all stores)
+__device__ __forceinline__ void tmem_st16(uint32_t taddr, const uint32_t* v) {
+  asm volatile(
+      "tcgen05.st.sync.aligned.32x32b.x16.b32 [%0], {%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,"
+      "%13,%14,%15,%16};\n"
+      :: "r"(taddr), "r"(v[0]), "r"(v[1]), "r"(v[2]), "r"(v[3]), "r"(v[4]), "r"(v[5]),
+         "r"(v[6]), "r"(v[7]), "r"(v[8]), "r"(v[9]), "r"(v[10]), "r"(v[11]), "r"(v[12]),
+         "r"(v[13]), "r"(v[14]), "r"(v[15])
+      : "memory");
+}
+
+// an integer |v| < 2^22 as an exact FP32 value, and back (rounding-free: the magic constant
+// 1.5 x 2^23 puts v in the last place of the significand)
+__device__ __forceinline__ float int_to_f32(int v) {
+  return __int_as_float(0x4B400000 + v) - 12582912.0f;
+}
+__device__ __forceinline__ int f32_to_int(float f) {
+  return __float_as_int(f + 12582912.0f) - 0x4B400000;
+}
+
+// node layer kk of the tile (FP64): values and mask bits of up to two nodes per thread
+struct XPre {
+  double v[2][3];
+  unsigned m[2];
+};
+__device__ __forceinline__ void x_fetch(XPre& p, int kk, int EX0, int EY0, int nx, int ny, int nz,
+                                        const uint8_t* __restrict__ mask,
+                                        const double* __restrict__ x) {
+#pragma unroll
+  for (int h = 0; h < 2; h++) {
+    const int q = threadIdx.x + h * NT;
+    p.v[h][0] = p.v[h][1] = p.v[h][2] = 0.0;
+    p.m[h] = 7u;
+    if (q < LAYER_NODES) {
+      const int gi = EX0 + q % TNX, gj = EY0 + q / TNX;
+      if (gi >= 0 && gi <= nx && gj >= 0 && gj <= ny && kk >= 0 && kk <= nz) {
+        const int64_t node = node_id(gi, gj, kk, nx, ny);
+        p.m[h] = __ldg(mask + node);
+#pragma unroll
+        for (int c = 0; c < 3; c++) p.v[h][c] = __ldg(x + 3 * node + c);
+      }
+    }
+  }
+}
+__device__ __forceinline__ void x_store(const XPre& p, double* sx) {
+#pragma unroll
+  for (int h = 0; h < 2; h++) {
+    const int q = threadIdx.x + h * NT;
+    if (q < LAYER_NODES) {
+#pragma unroll
+      for (int c = 0; c < 3; c++) sx[3 * q + c] = ((p.m[h] >> c) & 1u) ? 0.0 : p.v[h][c];
+    }
+  }
+}
+__device__ __forceinline__ double e_fetch(int ke, int EX0, int EY0, int nx, int ny, int nz,
+                                          const double* __restrict__ E) {
+  const int ge = EX0 + (int)(threadIdx.x % TEX), gf = EY0 + (int)(threadIdx.x / TEX);
+  if (ge < 0 || ge >= nx || gf < 0 || gf >= ny || ke < 0 || ke >= nz) return 0.0;
+  return __ldg(E + ge + (int64_t)nx * (gf + (int64_t)ny * ke));
+}
+
+// Element (ex, ey) of layer ke from the ring slots of node layers ke (s0) and ke + 1 (s1): the
+// five FP16 digit rows of its fixed-point values, written to tensor memory from column
+// taddr (digit q at taddr + 16 q: 12 words of digit pairs, lower K index in the low half, and 4
+// zero words of K padding).  Returns the biased FP64 exponent e of the row's largest entry
+// (the fixed point is X_j = round(x_j 2^(1075 - e)), |X_j| <= 2^53), or 0 for a row whose
+// entries are all below 2^-970 (written as zero digits).
+__device__ __forceinline__ int a_digits(uint32_t taddr, const double* s0, const double* s1,
+                                        int ex, int ey) {
+  uint64_t bits[KD];
+  int emax = 0;
+#pragma unroll
+  for (int k = 0; k < KD; k++) {
+    const int bn = k / 3, c = k % 3;
+    const double* sx = (bn & 4) ? s1 : s0;
+    bits[k] = __double_as_longlong(sx[3 * ((ey + ((bn >> 1) & 1)) * TNX + ex + (bn & 1)) + c]);
+    emax = max(emax, (int)((bits[k] >> 52) & 0x7FFu));
+  }
+  if (emax < 53) emax = 0;
+  int64_t X[KD];
+#pragma unroll
+  for (int k = 0; k < KD; k++) {
+    const int e = (int)((bits[k] >> 52) & 0x7FFu);
+    const uint64_t m = (bits[k] & 0xFFFFFFFFFFFFFull) | (e ? (1ull << 52) : 0ull);
+    const int sh = emax - e;
+    uint64_t a = 0;
+    if (emax && sh <= 54) a = (m + ((1ull << sh) >> 1)) >> sh;  // round half up
+    X[k] = (bits[k] >> 63) ? -(int64_t)a : (int64_t)a;
+  }
+#pragma unroll
+  for (int q = 0; q < ND; q++) {
+    uint32_t w[16];
+#pragma unroll
+    for (int c = 0; c < KD / 2; c++) {
+      int d0, d1;
+      if (q < ND - 1) {
+        d0 = (int)((X[2 * c] >> (11 * q)) & 2047);
+        d1 = (int)((X[2 * c + 1] >> (11 * q)) & 2047);
+      } else {
+        d0 = (int)(X[2 * c] >> 44);  // signed top digit
+        d1 = (int)(X[2 * c + 1] >> 44);
+      }
+      const __half2 h = __floats2half2_rn(int_to_f32(d0), int_to_f32(d1));  // exact
+      w[c] = *reinterpret_cast<const uint32_t*>(&h);
+    }
+#pragma unroll
+    for (int c = KD / 2; c < 16; c++) w[c] = 0u;
+    tmem_st16(taddr + (uint32_t)(16 * q), w);
+  }
+  asm volatile("tcgen05.wait::st.sync.aligned;\n" ::: "memory");
+  return emax;
+}
+
+// the digit MMAs of one layer: digit q's rows against B (K steps of 16) into accumulator q
+__device__ __forceinline__ void issue_mmas(uint32_t tmem, uint32_t bbase, uint32_t bar) {
+  asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
+#pragma unroll
+  for (int q = 0; q < ND; q++)
+#pragma unroll
+    for (int s = 0; s < KP / 16; s++)
+      mma_ts(tmem + (uint32_t)(ACC_COL + NB * q), tmem + (uint32_t)(A_COL + 16 * q + 8 * s),
+             sdesc(bbase + 2 * LBO * s), s ? 1u : 0u);
+  asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];\n"
+               :: "r"(bar) : "memory");
+}
+
+// this thread's element row of the previous layer: Z_o = sum_q D_q,o 2^(11 q) in int64 (exact),
+// then v_o = scale Z_o in FP64, scale = E_e c 2^(p - 1075) (0 for a zero row or no element).
+// Measured against forming ec Z 2^(p - 1075) entirely with integer operations (a 64 x 64-bit
+// product and an assembled double, no FP64 instruction), this is faster: the kernel is bound by
+// instruction latency at its two blocks per SM, not by the FP64 pipe.
+__device__ __forceinline__ void fold_digits(uint32_t taddr, double scale, double* v) {
+  int64_t Z[KD];
+#pragma unroll
+  for (int o = 0; o < KD; o++) Z[o] = 0;
+#pragma unroll
+  for (int q = ND - 1; q >= 0; q--) {
+    float d[KD];
+    tmem_ld24(taddr + (uint32_t)(ACC_COL + NB * q), d);
+#pragma unroll
+    for (int o = 0; o < KD; o++) Z[o] = Z[o] * 2048 + f32_to_int(d[o]);
+  }
+#pragma unroll
+  for (int o = 0; o < KD; o++) v[o] = scale * __ll2double_rn(Z[o]);
+}
+
+struct Fin {
+  double x[3], b[3];
+  unsigned m;
+};
+
+template <int MODE>
+__global__ void __launch_bounds__(NT, 2)
+k_ebe3x64(int nx, int ny, int nz, int nz_tile, int nzc, const uint4* __restrict__ Bimg,
+          const double* __restrict__ E, double c, const uint8_t* __restrict__ mask,
+          const double* __restrict__ x, double* __restrict__ y, const double* __restrict__ b,
+          const int* done, double* partials, Scalars* sc) {
+  extern __shared__ uint8_t smem_raw[];
+  pdl_prologue();
+  // blockIdx.z = chunk of node layers + nzc x right-hand side of a block solve
+  const int zc = blockIdx.z % nzc, rhs = blockIdx.z / nzc;
+  const int nblk = gridDim.x * gridDim.y * nzc;  // blocks of one right-hand side
+  {
+    const int64_t vo = (int64_t)rhs * rhs_stride((int64_t)3 * (nx + 1) * (ny + 1) * (nz + 1));
+    x += vo;
+    y += vo;
+    if (b) b += vo;
+    if (partials) partials += (int64_t)rhs * nblk;
+    if (sc) {
+      sc += rhs;
+      if (done) done = &sc->done;
+    }
+  }
+  if (solve_done(done)) return;
+  uint8_t* sm = smem_raw + ((128 - (smem_u32(smem_raw) & 127u)) & 127u);
+  double* sxr = reinterpret_cast<double*>(sm + OFF_X);  // [2][LAYER_NODES][3]
+  double* sP = reinterpret_cast<double*>(sm + OFF_P);   // [2][TY][TEX][PS]
+  double* sred = reinterpret_cast<double*>(sm + OFF_R);
+  uint64_t* bar = reinterpret_cast<uint64_t*>(sm + OFF_BAR);
+  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(sm + OFF_BAR + 8);
+  const uint32_t sbase = smem_u32(sm), bar0 = smem_u32(bar);
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  const int ex = lane, ey = warp;
+  const int EX0 = blockIdx.x * ONX - 1, EY0 = blockIdx.y * ONY - 1;
+  const int k0 = zc * nz_tile;
+  const int k1 = min(k0 + nz_tile, nz + 1);  // owned node layers [k0, k1)
+
+  if (warp == 0) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;\n"
+                 :: "r"(smem_u32(tmem_slot)), "r"(TMEM_COLS) : "memory");
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;\n" ::: "memory");
+  }
+  if (tid == 0) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;\n" :: "r"(bar0), "r"(1) : "memory");
+    asm volatile("fence.mbarrier_init.release.cluster;\n" ::: "memory");
+  }
+  for (int t = tid; t < B_BYTES / 16; t += NT) reinterpret_cast<uint4*>(sm + OFF_B)[t] = Bimg[t];
+
+  const bool owner = ex >= 1 && ey >= 1;
+  const int gi = EX0 + ex, gj = EY0 + ey;
+  const bool in_plane = owner && gi <= nx && gj <= ny;
+
+  XPre pre, pre2;
+  x_fetch(pre, k0 - 1, EX0, EY0, nx, ny, nz, mask, x);
+  x_fetch(pre2, k0, EX0, EY0, nx, ny, nz, mask, x);
+  x_store(pre, sxr + ((k0 - 1) & 1) * LAYER_NODES * 3);
+  x_store(pre2, sxr + (k0 & 1) * LAYER_NODES * 3);
+  x_fetch(pre, k0 + 1, EX0, EY0, nx, ny, nz, mask, x);
+  double ec_cur = c * e_fetch(k0 - 1, EX0, EY0, nx, ny, nz, E);  // E c of element layer ke
+  double sc_prev = 0.0;  // E c 2^(p - 1075) of this thread's row of layer ke - 1
+  asm volatile("tcgen05.fence::before_thread_sync;\n" ::: "memory");
+  __syncthreads();
+  asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
+  const uint32_t tmem = *tmem_slot;
+  const uint32_t lane_base = (uint32_t)(32 * warp) << 16;
+
+  double acc[3] = {0.0, 0.0, 0.0};  // node layer ke - 1: contributions gathered so far
+  Fin fd;
+  fd.m = 7u;
+  uint32_t parity = 0, pending = 0;
+  bool failed = false;
+  double dotv = 0.0;
+
+  for (int ke = k0 - 1; ke <= k1; ke++) {
+    const bool mma_now = ke < k1;
+    const int j = ke & 1, jp = j ^ 1;
+    bool ok = true;
+    double v[KD];
+    if (ke >= k0) {
+      // the MMAs of layer ke - 1; the phase advances only on success (see the drain below)
+      ok = mbar_wait(bar0, parity);
+      if (ok) {
+        parity ^= 1u;
+        pending = 0u;
+      }
+      // the tensor-memory loads and stores below are warp-collective: a warp takes part only
+      // if every lane saw the MMAs complete (otherwise the whole block gives up below)
+      ok = __all_sync(0xffffffffu, ok);
+      asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
+      // the accumulators are single-buffered: read before this layer's MMAs are issued
+      if (ok) fold_digits(tmem + lane_base, sc_prev, v);
+    }
+    double sc_now = 0.0;
+    if (ok && mma_now) {
+      const int p = a_digits(tmem + lane_base + A_COL, sxr + j * LAYER_NODES * 3,
+                             sxr + jp * LAYER_NODES * 3, ex, ey);
+      if (p) sc_now = ec_cur * __longlong_as_double((long long)(p - 52) << 52);
+    }
+    asm volatile("tcgen05.fence::before_thread_sync;\n" ::: "memory");
+    if (__syncthreads_or(!ok)) {  // a wait that ran out anywhere stops the whole block
+      failed = true;
+      break;
+    }
+    if (mma_now) {
+      if (tid == 0) issue_mmas(tmem, sbase + OFF_B, bar0);
+      pending = 1u;
+    }
+    if (mma_now && ke + 2 <= k1) {
+      x_store(pre, sxr + j * LAYER_NODES * 3);
+      if (ke + 3 <= k1) x_fetch(pre, ke + 3, EX0, EY0, nx, ny, nz, mask, x);
+    }
+    const double ec_next = (ke + 1 < k1) ? c * e_fetch(ke + 1, EX0, EY0, nx, ny, nz, E) : 0.0;
+    Fin fd_next;
+    fd_next.m = 7u;
+    if (in_plane && ke >= k0 && ke < k1) {
+      const int64_t node = node_id(gi, gj, ke, nx, ny);
+      fd_next.m = __ldg(mask + node);
+#pragma unroll
+      for (int q = 0; q < 3; q++) fd_next.x[q] = __ldg(x + 3 * node + q);
+      if (MODE == MODE_RESID) {
+#pragma unroll
+        for (int q = 0; q < 3; q++) fd_next.b[q] = __ldg(b + 3 * node + q);
+      }
+    }
+    double pr[2][2][3];
+    if (ke >= k0) {
+#pragma unroll
+      for (int dy = 0; dy < 2; dy++)
+#pragma unroll
+        for (int dz = 0; dz < 2; dz++)
+#pragma unroll
+          for (int q = 0; q < 3; q++) {
+            const double left = __shfl_up_sync(0xffffffffu, v[3 * (1 + 2 * dy + 4 * dz) + q], 1);
+            pr[dy][dz][q] = v[3 * (2 * dy + 4 * dz) + q] + left;
+          }
+      double* myP = sP + (j * NT + ey * TEX + ex) * PS;
+#pragma unroll
+      for (int dz = 0; dz < 2; dz++)
+#pragma unroll
+        for (int q = 0; q < 3; q++) myP[3 * dz + q] = pr[1][dz][q];
+    }
+    __syncthreads();
+    if (ke >= k0 && owner) {
+      const int kn = ke - 1;
+      const double* upP = sP + (j * NT + (ey - 1) * TEX + ex) * PS;
+      double top[3];
+#pragma unroll
+      for (int q = 0; q < 3; q++) {
+        acc[q] += upP[q] + pr[0][0][q];
+        top[q] = upP[3 + q] + pr[0][1][q];
+      }
+      if (in_plane && kn >= k0) {
+        const int64_t node = node_id(gi, gj, kn, nx, ny);
+        double Ax[3];
+#pragma unroll
+        for (int q = 0; q < 3; q++) Ax[q] = ((fd.m >> q) & 1u) ? fd.x[q] : acc[q];
+        if (MODE == MODE_APPLY) {
+#pragma unroll
+          for (int q = 0; q < 3; q++) {
+            y[3 * node + q] = Ax[q];
+            dotv += fd.x[q] * Ax[q];
+          }
+        } else {
+#pragma unroll
+          for (int q = 0; q < 3; q++) y[3 * node + q] = fd.b[q] - Ax[q];
+        }
+      }
+#pragma unroll
+      for (int q = 0; q < 3; q++) acc[q] = top[q];
+    }
+    sc_prev = sc_now;
+    ec_cur = ec_next;
+    fd = fd_next;
+  }
+
+  if (failed) {
+    if (tid == 0) atomicExch(&g_x64_error, 1);
+    // MMAs still in flight write the accumulators until they complete
+    if (pending) mbar_wait(bar0, parity);
+  }
+  asm volatile("tcgen05.fence::before_thread_sync;\n" ::: "memory");
+  __syncthreads();
+  if (warp == 0) {
+    asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;\n"
+                 :: "r"(tmem), "r"(TMEM_COLS) : "memory");
+  }
+  if (MODE != MODE_APPLY || !partials) return;  // uniform over the grid
+  const double tot = block_sum(dotv, sred);
+  if (tid == 0) partials[blockIdx.x + gridDim.x * (blockIdx.y + gridDim.y * zc)] = tot;
+  if (sc && last_block(&sc->tk[TK_ALPHA], nblk))
+    finish_body(FIN_ALPHA, partials, nblk, nullptr, 0, sc, sred);
+}
+
+template <int MODE>
+void launch(cudaStream_t s, const Ebe& op, const void* Bimg, double c, const double* x, double* y,
+            const double* b, const int* done, double* partials, Scalars* sc) {
+  // two blocks per SM at most: their 256 tensor-memory columns each fill the SM's 512 (a third
+  // block would wait in tcgen05.alloc), so the dynamic shared memory is raised until no more fit
+  static int smem = 0;
+  if (smem == 0) {
+    int bytes = SMEM_ALLOC, per_sm = 0;
+    CK(cudaFuncSetAttribute(k_ebe3x64<MODE>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                            110 << 10));
+    for (;;) {
+      CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_ebe3x64<MODE>, NT, bytes));
+      if (per_sm <= 2 || bytes >= (110 << 10)) break;
+      bytes += 4 << 10;
+    }
+    smem = bytes;
+  }
+  const int nzt = 8;
+  const int nzc = ceil_div(op.nz + 1, nzt);
+  const dim3 grid(ceil_div(op.nx + 1, ONX), ceil_div(op.ny + 1, ONY), nzc * batch_rhs());
+  LAUNCH((k_ebe3x64<MODE>), grid, NT, smem, s, op.nx, op.ny, op.nz, nzt, nzc,
+         reinterpret_cast<const uint4*>(Bimg), (const double*)op.E, c, op.mask, x, y, b, done,
+         partials, sc);
+}
+
+}  // namespace
+
+bool ebe3x_operand(double nu, uint32_t* img, double* c) {
+  // lambda / mu = 2 nu / (1 - 2 nu) = p / q with a small q, so that C = p K_l + q K_m (the
+  // 72-scaled integer parts) is an integer matrix whose digit products stay exact in FP32
+  const double lam = nu / ((1.0 + nu) * (1.0 - 2.0 * nu)), mu = 1.0 / (2.0 * (1.0 + nu));
+  const double ratio = lam / mu;
+  int q = 0;
+  for (int t = 1; t <= 8 && !q; t++)
+    if (std::fabs(ratio * t - std::nearbyint(ratio * t)) < 1e-12 * std::max(1.0, ratio * t)) q = t;
+  if (!q) return false;
+  const double p = std::nearbyint(ratio * q);
+  std::vector<double> Kl, Km, Dl(36, 0.0), Dm(36, 0.0);
+  for (int i = 0; i < 3; i++)
+    for (int j = 0; j < 3; j++) Dl[i * 6 + j] = 1.0;
+  for (int i = 0; i < 6; i++) Dm[i * 6 + i] = i < 3 ? 2.0 : 1.0;
+  element_stiffness_D(3, Dl.data(), Kl);
+  element_stiffness_D(3, Dm.data(), Km);
+  uint16_t* h = reinterpret_cast<uint16_t*>(img);
+  for (int i = 0; i < B_BYTES / 2; i++) h[i] = 0;
+  double rowmax = 0.0;
+  for (int n = 0; n < KD; n++) {
+    double rs = 0.0;
+    for (int k = 0; k < KD; k++) {
+      const double v = p * 72.0 * Kl[n * KD + k] + q * 72.0 * Km[n * KD + k];
+      const double r = std::nearbyint(v);
+      if (std::fabs(v - r) > 1e-8 || std::fabs(r) > 2048.0) return false;
+      rs += std::fabs(r);
+      const __half hv = __double2half(r);
+      uint16_t bits;
+      std::memcpy(&bits, &hv, 2);
+      h[op_off(n, k) / 2] = bits;
+    }
+    rowmax = std::max(rowmax, rs);
+  }
+  // digit sums: |sum_k C_nk d_k| <= rowmax x 2047 must stay below 2^22 (exact in FP32 and in
+  // the integer conversion)
+  if (rowmax * 2047.0 >= 4194304.0) return false;
+  *c = mu / (72.0 * q);
+  return true;
+}
+
+int ebe3x_operand_words() { return B_BYTES / 4; }
+
+int ebe3x_blocks(const Ebe& op) {
+  return ceil_div(op.nx + 1, ONX) * ceil_div(op.ny + 1, ONY) * ceil_div(op.nz + 1, 8);
+}
+
+void ebe3x_apply(cudaStream_t s, int mode, const Ebe& op, const void* Bimg, double c,
+                 const double* x, double* y, const double* b, const int* done, double* partials,
+                 Scalars* sc) {
+  if (mode == MODE_APPLY) launch<MODE_APPLY>(s, op, Bimg, c, x, y, b, done, partials, sc);
+  else if (mode == MODE_RESID) launch<MODE_RESID>(s, op, Bimg, c, x, y, b, done, nullptr, nullptr);
+  else TOMG_THROW(TOMG_E_INVALID, "FP64 tensor-core element operator: apply and residual only");
+}
+
+bool ebe3x_error(cudaStream_t s) {
+  int v = 0;
+  CK(cudaMemcpyFromSymbolAsync(&v, g_x64_error, sizeof(int), 0, cudaMemcpyDeviceToHost, s));
+  CK(cudaStreamSynchronize(s));
+  if (v) {
+    const int zero = 0;
+    CK(cudaMemcpyToSymbolAsync(g_x64_error, &zero, sizeof(int), 0, cudaMemcpyHostToDevice, s));
+    CK(cudaStreamSynchronize(s));
+  }
+  return v != 0;
+}
+
+}  // namespace tomg

@@ -75,6 +75,17 @@ void ebe3d_tc_launch(cudaStream_t s, int mode, const Ebe& op, const float* x, fl
 // B operand of the tensor-core kernel for Poisson ratio nu: 72 K_l and 72 K_m (Ke = lambda K_l
 // + mu K_m) as FP16 in the kernel's shared-memory layout; cl = lambda / 72, cm = mu / 72
 void ebe3d_tc_operand(double nu, uint32_t* img, float* cl, float* cm);
+// FP64 hex8 operator on the tensor cores (k_ebe3x64.cu): exact integer digit products of the
+// element contractions, FP64 scaling and node sums.  ebe3x_operand builds its B operand (the
+// integer matrix C with Ke = c C) and returns false when nu gives no small integer C.
+bool ebe3x_operand(double nu, uint32_t* img, double* c);
+int ebe3x_operand_words();
+int ebe3x_blocks(const Ebe& op);  // blocks (= dot partials) of one launch
+// MODE_APPLY: y = A x, partials of x . y (nullable), FIN_ALPHA with sc; MODE_RESID: y = b - A x
+void ebe3x_apply(cudaStream_t s, int mode, const Ebe& op, const void* Bimg, double c,
+                 const double* x, double* y, const double* b, const int* done, double* partials,
+                 Scalars* sc);
+bool ebe3x_error(cudaStream_t s);  // a wait of the FP64 tensor-core kernel ran out (syncs s)
 // polls of the tensor-core kernel's in-loop MMA waits in later launches (0 = the default);
 // a test shortens it to make the waits run out and exercise the error path
 void ebe3d_tc_set_wait_limit(int polls);

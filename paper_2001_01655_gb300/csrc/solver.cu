@@ -344,13 +344,21 @@ void apply_M_and_dots(tomg_problem* P, Work& W, const double* q, const int* done
 
 // FP64 outer operator K (masked): the assembled fine stencil when the setup kept it (36 / 243
 // FMAs per node instead of 72 / 600 for the element products), else the matrix-free kernel
-// Outer-loop K in FP64: the assembled fine stencil when the setup kept it (36 / 243 FMAs per
-// node instead of 64 / 576 for the element products), else the FP64 element kernel.  Partials
-// of x . y (nullable); with sc set, FIN_ALPHA is applied to the scalar state on the device.
+// whether the outer FP64 applies of hex8 run on the tensor cores (k_ebe3x64.cu)
+bool x64_active(const tomg_problem* P) { return P->dim == 3 && P->Kx64.p && P->opt.fp64_tc; }
+
+// Outer-loop K in FP64: on hex8 the element products on the tensor cores (exact integer digit
+// products, FP64 scaling and node sums) when nu allows them; else the assembled fine stencil
+// when the setup kept it (36 / 243 FMAs per node instead of 64 / 576 for the element products),
+// else the FP64 element kernel.  Partials of x . y (nullable); with sc set, FIN_ALPHA is
+// applied to the scalar state on the device.
 void fine64_apply_dot(tomg_problem* P, cudaStream_t s, const double* x, double* y, const int* done,
                       double* partials, Scalars* sc) {
   Level& L0 = *P->L[0];
-  if (L0.S64.p) {
+  if (x64_active(P)) {
+    ebe3x_apply(s, MODE_APPLY, V<double>::ebe(P), P->Kx64.p, P->x64_c, x, y, nullptr, done,
+                partials, sc);
+  } else if (L0.S64.p) {
     stencil_apply_dot(s, L0.g, L0.S64.p, x, y, done, partials, sc);
   } else {
     ebe_op<double>(s, MODE_APPLY, V<double>::ebe(P), x, y, nullptr, nullptr, 0.0, done, partials);
@@ -358,7 +366,11 @@ void fine64_apply_dot(tomg_problem* P, cudaStream_t s, const double* x, double* 
   }
 }
 void fine64_resid(tomg_problem* P, cudaStream_t s, const double* x, double* y, const double* b) {
-  level_op<double>(P, s, 0, MODE_RESID, x, y, b, nullptr);
+  if (x64_active(P))
+    ebe3x_apply(s, MODE_RESID, V<double>::ebe(P), P->Kx64.p, P->x64_c, x, y, b, nullptr, nullptr,
+                nullptr);
+  else
+    level_op<double>(P, s, 0, MODE_RESID, x, y, b, nullptr);
 }
 
 void iteration_body(tomg_problem* P, Work& W) {
@@ -710,7 +722,12 @@ void problem_init(tomg_problem* P) {
     ebe3d_tc_operand(P->nu, img.data(), &P->tc_cl, &P->tc_cm);
     P->Ketc.resize(img.size());
     CK(cudaMemcpyAsync(P->Ketc.p, img.data(), img.size() * 4, cudaMemcpyHostToDevice, s));
-    CK(cudaStreamSynchronize(s));  // img is a host temporary
+    std::vector<uint32_t> imgx(ebe3x_operand_words());
+    if (ebe3x_operand(P->nu, imgx.data(), &P->x64_c)) {
+      P->Kx64.resize(imgx.size());
+      CK(cudaMemcpyAsync(P->Kx64.p, imgx.data(), imgx.size() * 4, cudaMemcpyHostToDevice, s));
+    }
+    CK(cudaStreamSynchronize(s));  // img, imgx are host temporaries
   }
   P->mask.resize(P->nn);
   P->mask.zero(s);
@@ -948,7 +965,7 @@ Work& ensure_work(tomg_problem* P, int k) {
     CK(cudaEventCreateWithFlags(&W->evdone, cudaEventDisableTiming));
     CK(cudaEventCreateWithFlags(&W->evsync, cudaEventDisableTiming));
     const Ebe op{P->dim, P->nx, P->ny, P->nz, nullptr, nullptr, nullptr};
-    W->np = std::max(ebe_blocks(op), red_blocks(P->n));
+    W->np = std::max(std::max(ebe_blocks(op), red_blocks(P->n)), P->dim == 3 ? ebe3x_blocks(op) : 0);
     CK(cudaMallocHost((void**)&W->sc_host, sizeof(Scalars)));
     CK(cudaMallocHost((void**)&W->partE_host, sizeof(double) * W->np));
     CK(cudaMallocHost((void**)&W->partC_host, sizeof(double) * W->np));
@@ -1271,8 +1288,10 @@ Work& ensure_block_work(tomg_problem* P, int R) {
     CK(cudaEventCreateWithFlags(&W->evdone, cudaEventDisableTiming));
     CK(cudaEventCreateWithFlags(&W->evsync, cudaEventDisableTiming));
     W->block = R;
-    W->np = std::max(stencil_blocks(Geo{P->dim, P->nx, P->ny, P->dim == 3 ? P->nz : 1}),
-                     red_blocks(P->n));
+    const Ebe op{P->dim, P->nx, P->ny, P->nz, nullptr, nullptr, nullptr};
+    W->np = std::max(std::max(stencil_blocks(Geo{P->dim, P->nx, P->ny, P->dim == 3 ? P->nz : 1}),
+                              red_blocks(P->n)),
+                     P->dim == 3 ? ebe3x_blocks(op) : 0);
     CK(cudaMallocHost((void**)&W->sc_host, sizeof(Scalars) * R));
     CK(cudaMallocHost((void**)&W->partE_host, sizeof(double) * W->np * R));
     CK(cudaMallocHost((void**)&W->partC_host, sizeof(double) * W->np * R));
@@ -1443,7 +1462,8 @@ tomg_status solve(tomg_problem* P, int nrhs, const double* f, double* u, int on_
     for (int k = 0; k < slots; k++) join_from(P, *P->works[k]);
   }
   CK(cudaStreamSynchronize(st(P)));
-  if (P->dim == 3 && P->opt.prec == TOMG_PREC_TC_VCYCLE && ebe3d_tc_error(st(P)))
+  if (P->dim == 3 && ((P->opt.prec == TOMG_PREC_TC_VCYCLE && ebe3d_tc_error(st(P))) ||
+                      (x64_active(P) && ebe3x_error(st(P)))))
     for (int j = 0; j < nrhs; j++) res[j].status = TOMG_E_TIMEOUT;
   if (P->opt.pc == TOMG_PC_HYBRID && P->opt.adaptive_geo && P->adapt_geo > 0) {
     // adaptive hybrid (Sec. 4.4): a solve over the iteration limit moves the next setup one
@@ -1789,7 +1809,7 @@ double time_fine_operator(tomg_problem* P, int op, int prec, int reps, int cold_
 // device bytes the problem holds: its inputs, the hierarchy and every solve slot
 size_t tomg::problem_device_bytes(const tomg_problem* P) {
   using namespace tomg;
-  size_t b = P->Ketc.bytes() + P->Ke64.bytes() + P->Ke32.bytes() + P->mask.bytes() +
+  size_t b = P->Ketc.bytes() + P->Kx64.bytes() + P->Ke64.bytes() + P->Ke32.bytes() + P->mask.bytes() +
              P->rho.bytes() + P->E64.bytes() + P->E32.bytes() + P->flag_dev.bytes() +
              P->Ainv64.bytes() + P->Ainv32.bytes();
   for (const auto& lp : P->L) {
@@ -1824,7 +1844,7 @@ tomg_problem::~tomg_problem() {
   for (cudaEvent_t e : {ev0, ev1, ev_in, ev_out, ev_fork, ev_side, ev_fork2, ev_side2})
     if (e) cudaEventDestroy(e);
   // device buffers are released by their destructors on this stream before it is destroyed
-  Ke64.release(); Ke32.release(); mask.release(); rho.release(); E64.release(); E32.release();
+  Ke64.release(); Ke32.release(); Ketc.release(); Kx64.release(); mask.release(); rho.release(); E64.release(); E32.release();
   flag_dev.release(); Ainv64.release(); Ainv32.release();
   if (stream) {
     cudaStreamSynchronize(stream);

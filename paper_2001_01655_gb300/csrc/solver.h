@@ -136,6 +136,8 @@ struct tomg_problem {
   int adapt_geo = 0;   // adaptive hybrid: geometric levels of the next setup (0 = not started)
   tomg::DBuf<uint32_t> Ketc;  // FP16 integer B operand of the tensor-core kernel (hex8)
   float tc_cl = 0.f, tc_cm = 0.f;  // its scales lambda / 72 and mu / 72
+  tomg::DBuf<uint32_t> Kx64;  // integer B operand of the FP64 tensor-core kernel (hex8; empty if
+  double x64_c = 0.0;         // nu admits none) and its scale: Ke = x64_c C
   tomg::DBuf<double> Ke64;
   tomg::DBuf<float> Ke32;
   tomg::DBuf<uint8_t> mask;

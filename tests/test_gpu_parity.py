@@ -61,10 +61,13 @@ def test_fine_operator_apply(lib, ctx, dim, grid, prec):
 @pytest.mark.parametrize("dim,grid", GRIDS + [(2, (95, 40, 1)), (3, (40, 9, 6))])
 @pytest.mark.parametrize("prec", ["fp32", "fp64"])
 def test_outer_operator_apply(lib, ctx, dim, grid, prec):
-    """The outer loop's FP64 K (the assembled fine stencil, in both precisions' setups).  Bound:
-    1e-13 of the summed element-product magnitudes sum_e E_e |Ke| |x| (FP64 rounding of the
-    assembly and of the 9 / 27 block products), on a 1e9-contrast density and x spanning 12
-    decades."""
+    """The outer loop's FP64 K (quad4: the assembled fine stencil; hex8: the element products on
+    the tensor cores, exact integer digit products of each element's fixed-point displacements),
+    in both precisions' setups.  Bound: 1e-13 of the summed element-product magnitudes
+    sum_e E_e |Ke| |x| (FP64 rounding of the assembly and of the 9 / 27 block products; for the
+    digit products the rounding of each element's fixed point, 2^-53 of its largest entry, times
+    at most sum |Ke_ij| / min |Ke_ij| = 280, about 3e-14), on a 1e9-contrast density and x
+    spanning 12 decades."""
     p = W.random_problem(dim, *grid, seed=21, contrast="threshold")
     P = make(lib, ctx, p)
     P.setup(pc="gmg", prec=prec)
@@ -77,6 +80,30 @@ def test_outer_operator_apply(lib, ctx, dim, grid, prec):
         y = P.outer_apply(x)
         scale = Kabs @ np.abs(x)
         assert np.all(np.abs(y - A0 @ x) <= 1e-13 * scale + 1e-300)
+
+
+@pytest.mark.parametrize("grid", [(13, 7, 5), (40, 9, 6), (64, 20, 17)])
+def test_outer_apply_tensor_cores_vs_stencil(lib, ctx, grid):
+    """The hex8 outer K on the tensor cores against the assembled FP64 stencil it replaces: both
+    within FP64 rounding of the element scale of each other, and the same dot-product finish
+    (one solve with each gives the same iterations and a solution within 1e-10)."""
+    p = W.random_problem(3, *grid, seed=23, contrast="minmax")
+    P = make(lib, ctx, p)
+    E = fem.simp(p.rho, p.E0, p.Emin, p.penal)
+    Kabs = fem.masked_operator(abs(fem.assemble(3, p.nx, p.ny, p.nz, E,
+                                                np.abs(fem.element_stiffness(3, p.nu)))), p.fixed)
+    x = np.random.default_rng(6).standard_normal(p.n) * 10.0 ** np.random.default_rng(7).uniform(-3, 3, p.n)
+    opts = dict(pc="hybrid", n_geo_levels=2, max_coarse_dofs=300, prec="tc", smoother="chebyshev")
+    P.setup(fp64_tc=1, **opts)
+    y_tc = P.outer_apply(x)
+    u_tc, r_tc = P.solve(p.f)
+    P.setup(fp64_tc=0, **opts)
+    y_st = P.outer_apply(x)
+    u_st, r_st = P.solve(p.f)
+    assert np.all(np.abs(y_tc - y_st) <= 2e-13 * (Kabs @ np.abs(x)) + 1e-300)
+    assert r_tc[0]["status"] == 0 and r_st[0]["status"] == 0
+    assert abs(r_tc[0]["iterations"] - r_st[0]["iterations"]) <= 1
+    assert relerr(u_tc, u_st) <= 1e-10
 
 
 @pytest.mark.parametrize("dim,grid,L", [(2, (37, 23, 1), 4), (2, (20, 10, 1), 3),
