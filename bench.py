@@ -331,7 +331,7 @@ def run_gpu(args, rank, world, local):
                   "d2h_bytes_per_step": int(f_h.nbytes),
                   "accuracy": accuracy_of(u_h, res[0], ref, G)}
     progress("roofline")
-    out["roofline"] = roofline(S.P, p, head)
+    out["roofline"] = roofline(S.P, p, head, opts)
     progress("mbb + 2D cantilever")
     if args.others:
         out["mbb_96x32"] = mbb_run(tomg, ctx, stream, dev, args)
@@ -656,14 +656,17 @@ FP64_PEAK_TFLOPS = 1.25  # GB300 FP64 rate (nominal; the measured-peaks file has
 MODEL_FLOPS_PER_DOF = {2: 64.0, 3: 384.0}
 
 
-def roofline(P, p, head):
+def roofline(P, p, head, opts):
     """The level-0 kernels of one FCG iteration of the headline, each timed live on the context
     stream with CUDA events (cold L2 before each launch): the FP64 outer q = K p (+ dot) on the
-    assembled fine stencil, and the V-cycle's FP32 residual and Jacobi sweeps on the tensor-core
-    element operator.  The dominant kernel is the one with the largest share of the solve
-    (time per launch x launches per iteration); its roofline is the bound that binds it."""
+    tensor cores (exact digit products, k_ebe3x64), and the V-cycle's FP32 residual and
+    Chebyshev / Jacobi steps on the FP32 tensor-core element operator (k_ebe3tc).  The dominant
+    kernel is the one with the largest share of the solve (time per launch x launches per
+    iteration).  The FP64 outer apply it replaces, on the assembled 3^d stencil, is timed beside
+    it (a setup with fp64_tc = 0)."""
     peaks = load_peaks()
     hbm = peaks.get("hbm_gbs", 6800.0)
+    bf16 = peaks.get("bf16_tflops", 1900.0)
     src = "measured" if "fallback" not in peaks else "fallback"
     nn = p.n // p.dim
     out = {}
@@ -677,43 +680,54 @@ def roofline(P, p, head):
                      per_it[name], "achieved_gbs": b / (ms * 1e-3) / 1e9,
                      "frac_hbm": b / (ms * 1e-3) / 1e9 / hbm}
     o = out["outer"]
-    # assembled 3^d stencil: d^2 FMAs per neighbour block, 3^d blocks per node, + the dot
-    executed = 2 * nn * (3 ** p.dim) * p.dim * p.dim + 2 * p.n
+    o["kernel"] = "k_ebe3x64 (FP64 outer q = K p + p.q; exact 11-bit digit products on the " \
+                  "FP16 tensor cores)"
     model = MODEL_FLOPS_PER_DOF[p.dim] * p.n
-    o["executed_flops"] = executed
     o["model_flops"] = model
-    o["executed_tflops"] = executed / (o["ms_per_launch"] * 1e-3) / 1e12
-    o["model_tflops"] = model / (o["ms_per_launch"] * 1e-3) / 1e12
-    # stencil bytes actually streamed: 3^d d^2 doubles per node, x and y, one mask byte
-    o["stencil_bytes"] = nn * (3 ** p.dim) * p.dim * p.dim * 8 + 2 * 8 * p.n + nn
-    o["stencil_frac_hbm"] = o["stencil_bytes"] / (o["ms_per_launch"] * 1e-3) / 1e9 / hbm
-    dom = max(out, key=lambda k: out[k]["ms_per_launch"] * out[k]["launches_per_iteration"])
+    o["fp64_equivalent_tflops"] = model / (o["ms_per_launch"] * 1e-3) / 1e12
+    # MMA work as issued: per element row 5 digits x (K 32 x N 32) multiply-adds; rows of a
+    # 32 x 4 tile own 31 x 3 node columns
+    rows = p.nel * (32 * 4) / (31 * 3)
+    o["tensor_tflops_issued"] = rows * 5 * 32 * 32 * 2 / (o["ms_per_launch"] * 1e-3) / 1e12
+    o["tensor_frac_of_bf16_peak"] = o["tensor_tflops_issued"] / bf16
+    # the assembled FP64 stencil it replaces
+    P.setup(prec=HEAD_PREC, **dict(opts, fp64_tc=0))
+    ms_st = P.time_fine_operator("outer", "fp64", reps=20, cold_l2=True)
+    executed = 2 * nn * (3 ** p.dim) * p.dim * p.dim + 2 * p.n
+    out["outer_fp64_stencil"] = {
+        "kernel": "k_stencil_apply_dot<%d> (assembled 3^d FP64 stencil)" % p.dim,
+        "ms_per_launch": ms_st, "executed_flops": executed,
+        "executed_tflops": executed / (ms_st * 1e-3) / 1e12,
+        "frac_fp64_peak": executed / (ms_st * 1e-3) / 1e12 / FP64_PEAK_TFLOPS,
+        "stencil_bytes": nn * (3 ** p.dim) * p.dim * p.dim * 8 + 2 * 8 * p.n + nn,
+        "stencil_frac_hbm": (nn * (3 ** p.dim) * p.dim * p.dim * 8 + 2 * 8 * p.n + nn)
+                            / (ms_st * 1e-3) / 1e9 / hbm,
+        "launches_per_iteration": 0}
+    P.setup(prec=HEAD_PREC, **opts)
+    dom = max((k for k in out if out[k]["launches_per_iteration"]),
+              key=lambda k: out[k]["ms_per_launch"] * out[k]["launches_per_iteration"])
+    k = out[dom]
+    headr = {"kernel": k.get("kernel", "k_ebe3tc (%s, FP32 on the tensor cores)" % dom),
+             "bound": "hbm", "achieved": k["achieved_gbs"], "peak": hbm, "unit": "GB/s",
+             "frac": k["frac_hbm"], "peak_source": src,
+             "bytes_counted": "minimum traffic of the work model: x and y (and b, the block "
+                              "inverse) once, one modulus per element, one mask byte per node"}
     if dom == "outer":
-        headr = {"kernel": "k_stencil_apply_dot<%d> (FP64 outer q = K p + p.q, assembled "
-                           "3^d stencil)" % p.dim,
-                 "bound": "alu", "achieved": o["executed_tflops"], "peak": FP64_PEAK_TFLOPS,
-                 "unit": "TFLOP/s", "frac": o["executed_tflops"] / FP64_PEAK_TFLOPS,
-                 "flops_counted": "executed: 2 x 3^d x d^2 per node + the dot (%d per DOF); the "
-                                  "matrix-free element products the work model counts would be "
-                                  "%d per DOF (frac %.2f)" % (round(executed / p.n),
-                                                             MODEL_FLOPS_PER_DOF[p.dim],
-                                                             o["model_tflops"] / FP64_PEAK_TFLOPS),
-                 "peak_source": "nominal FP64 rate (the measured-peaks file has no FP64 figure)"}
-    else:
-        k = out[dom]
-        headr = {"kernel": "k_ebe3tc (%s, tensor cores)" % dom, "bound": "hbm",
-                 "achieved": k["achieved_gbs"], "peak": hbm, "unit": "GB/s",
-                 "frac": k["frac_hbm"], "peak_source": src}
-    share = {k: out[k]["ms_per_launch"] * out[k]["launches_per_iteration"] * head["iterations"]
-             / head["solve_ms"] for k in out}
-    headr.update({"traffic": OUTER_TRAFFIC.get((dom, p.dim, p.n)),
-                  "ms_per_launch": out[dom]["ms_per_launch"], "share_of_solve": share,
-                  "kernels": out})
+        headr["note"] = ("latency-bound at two 128-thread blocks per SM (tensor memory and "
+                         "registers); FP64-equivalent rate %.2f TFLOP/s, %.2f x GB300's FP64 "
+                         "peak; the assembled FP64 stencil it replaces runs at %.2f of that peak "
+                         "and takes %.3f ms" % (o["fp64_equivalent_tflops"],
+                                               o["fp64_equivalent_tflops"] / FP64_PEAK_TFLOPS,
+                                               out["outer_fp64_stencil"]["frac_fp64_peak"], ms_st))
+    share = {kk: out[kk]["ms_per_launch"] * out[kk]["launches_per_iteration"] * head["iterations"]
+             / head["solve_ms"] for kk in out if out[kk]["launches_per_iteration"]}
+    headr.update({"traffic": TRAFFIC.get((dom, p.dim, p.n)),
+                  "ms_per_launch": k["ms_per_launch"], "share_of_solve": share, "kernels": out})
     return headr
 
 
-# DRAM read + write of one launch, from the ncu captures summarised under profiles/
-OUTER_TRAFFIC = {}
+# DRAM read + write bytes of one launch, from the ncu captures summarised under profiles/
+TRAFFIC = {}
 
 
 def kernel_only(args):

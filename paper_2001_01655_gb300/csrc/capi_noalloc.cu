@@ -12,6 +12,7 @@
 // the device address is looked up with cudaGetSymbolAddress once per device (on the first call
 // on that device, with that device current) and passed to the kernels.
 #include <mutex>
+#include <new>
 
 #include "solver.h"
 
@@ -46,6 +47,9 @@ float* scratch_for_current_device(int device) {
 }  // namespace tomg
 
 extern "C" tomg_status tomg_fine_apply_f32_noalloc(tomg_problem* P, const double* x, double* y) {
+  // as at every entry point: a non-sticky error left behind by another library's runtime call
+  // in this thread would otherwise surface at the first launch check of this call
+  (void)cudaGetLastError();
   try {
     if (!P || !x || !y) TOMG_THROW(TOMG_E_INVALID, "null argument");
     if (!P->have_density) TOMG_THROW(TOMG_E_INVALID, "no density set");
@@ -67,6 +71,9 @@ extern "C" tomg_status tomg_fine_apply_f32_noalloc(tomg_problem* P, const double
     return TOMG_OK;
   } catch (const tomg::Error& e) {
     return e.st;
+  } catch (const std::bad_alloc&) {
+    tomg::set_error("host allocation failed");
+    return TOMG_E_OOM;
   } catch (...) {
     tomg::set_error("unexpected internal error");
     return TOMG_E_CUDA;

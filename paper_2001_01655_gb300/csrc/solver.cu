@@ -938,9 +938,11 @@ void setup(tomg_problem* P, const tomg_options& opt) {
       }
       tr.mark("chebyshev bounds");
     }
-    // setup-only storage of the fine level (its FP64 stencil stays: it carries every FP64
-    // application of K, see fine64_apply_dot)
+    // setup-only storage of the fine level.  Its FP64 stencil stays where it carries the FP64
+    // applications of K (see fine64_apply_dot); with an FP32 V-cycle on hex8 with the FP64
+    // tensor-core operator nothing reads it after the setup (3.5 GB at 5.4 M DOFs)
     L0.rp.release(); L0.ci.release(); L0.V64.release();
+    if (P->dim == 3 && x64_active(P) && opt.prec != TOMG_PREC_FP64) L0.S64.release();
     for (auto& lv : P->L)
       if (lv->kind == KIND_STENCIL) { lv->rp.release(); lv->ci.release(); lv->V64.release(); }
   }

@@ -46,7 +46,8 @@ def test_noalloc_matches_regular_apply_twice(lib, case):
 
 def test_noalloc_rejects_oversized_problem(lib):
     ctx = lib.Context(0)
-    P = lib.Problem(ctx, 2, 800, 700)  # 1,123,202 DOFs > 1,048,576
+    P = lib.Problem(ctx, 2, 800, 700)  # 2 x 801 x 701 = 1,123,002 DOFs > 1,048,576
+    assert P.n == 2 * 801 * 701 and P.n > 1 << 20
     P.set_density(np.ones(800 * 700))
     import torch
     x = torch.zeros(P.n, dtype=torch.float64, device="cuda:0")
