@@ -727,7 +727,11 @@ def roofline(P, p, head, opts):
 
 
 # DRAM read + write bytes of one launch, from the ncu captures summarised under profiles/
-TRAFFIC = {}
+# (key: kernel role, dimension, DOFs); valid while the kernel is unchanged since its capture
+TRAFFIC = {
+    # k_ebe3x64 apply, 3D cantilever 192x96x96: 59.7 MB read + 10.7 MB write
+    ("outer", 3, 5447811): 70.4e6,
+}
 
 
 def kernel_only(args):
