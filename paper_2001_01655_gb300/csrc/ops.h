@@ -156,6 +156,11 @@ void stencil_apply_dot(cudaStream_t s, const Geo& g, const double* S, const doub
 int stencil_blocks(const Geo& g);
 // Galerkin product with bilinear / trilinear P (coarse node I at fine position min(2I, n))
 void stencil_rap(cudaStream_t s, const Geo& fine, const Geo& coarse, const double* Sf, double* Sc);
+// hex8: the first coarse stencil P^T A_0 P straight from the level-0 elements (FP64 operator
+// op64, coarse grid c = the coarsening of op64's grid).  Returns false, writing nothing, when
+// more than one element in eight touches a fixed DOF (the caller then takes the product on the
+// assembled fine stencil).  Synchronises s once (the count of those elements).
+bool ebe_galerkin_stencil(cudaStream_t s, const Ebe& op64, const Geo& c, double* Sc);
 template <class T>
 void geo_restrict(cudaStream_t s, const Geo& fine, const Geo& coarse, const T* rf, T* bc,
                   const int* done);

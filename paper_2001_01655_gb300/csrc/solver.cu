@@ -832,22 +832,38 @@ void setup(tomg_problem* P, const tomg_options& opt) {
     } else if (opt.pc == TOMG_PC_HYBRID)
       n_geo = std::max(1, opt.n_geo_levels);
     n_geo = std::min(n_geo, opt.max_levels);
-    // assembled level-0 stencil (FP64) for the Galerkin products / AMG / dense coarse solve
     Level& L0 = *P->L[0];
-    L0.S64.resize((int64_t)stencil_q(P->dim) * P->nn);
-    ebe_assemble_stencil(s, V<double>::ebe(P), L0.S64.p);
-    tr.mark("level0 stencil", 0);
+    // hex8: the first coarse stencil straight from the elements (k_galerkin.cu).  The assembled
+    // FP64 level-0 stencil is built only where something reads it: the product on stencils
+    // when the direct one declines, AMG or the dense solve on level 0, and the FP64
+    // applications of K on level 0 unless the tensor-core FP64 operator carries them
+    std::unique_ptr<Level> C1;
+    if (P->dim == 3 && n_geo >= 2) {
+      C1 = std::make_unique<Level>();
+      C1->g = coarse_geo(L0.g);
+      C1->S64.resize((int64_t)stencil_q(P->dim) * C1->g.nodes());
+      if (!ebe_galerkin_stencil(s, V<double>::ebe(P), C1->g, C1->S64.p)) C1.reset();
+      tr.mark("level1 from elements", 1);
+    }
+    const bool keep_S0 = !C1 || opt.prec == TOMG_PREC_FP64 || !x64_active(P);
+    if (keep_S0) {
+      L0.S64.resize((int64_t)stencil_q(P->dim) * P->nn);
+      ebe_assemble_stencil(s, V<double>::ebe(P), L0.S64.p);
+      tr.mark("level0 stencil", 0);
+    }
     for (int l = 1; l < n_geo; l++) {
       Level& F = *P->L[l - 1];
-      auto C = std::make_unique<Level>();
+      auto C = (l == 1 && C1) ? std::move(C1) : std::make_unique<Level>();
       C->kind = KIND_STENCIL;
       C->b = P->dim;
       C->g = coarse_geo(F.g);
       C->nn = C->g.nodes();
       C->n = C->nn * P->dim;
       C->geometric = true;
-      C->S64.resize((int64_t)stencil_q(P->dim) * C->nn);
-      stencil_rap(s, F.g, C->g, F.S64.p, C->S64.p);
+      if (!C->S64.p) {
+        C->S64.resize((int64_t)stencil_q(P->dim) * C->nn);
+        stencil_rap(s, F.g, C->g, F.S64.p, C->S64.p);
+      }
       C->S32.resize(C->S64.n);
       cast_f64_f32(s, C->S64.p, C->S32.p, C->S64.n);
       C->D64.resize(C->nn * P->dim * P->dim);

@@ -127,6 +127,35 @@ def test_gmg_hierarchy(lib, ctx, dim, grid, L):
         assert relerr(P.level_apply(l, x, "fp32"), Ar @ x) < 1e-5
 
 
+@pytest.mark.parametrize("grid,n_extra,prec", [
+    ((16, 6, 6), 3, "fp64"),   # clamped face + 3 scattered nodes: elements -> coarse stencil
+    ((16, 6, 6), 3, "tc"),     # the same without the assembled fine stencil
+    ((13, 5, 7), 2, "fp32"),   # odd axes: the single child of the last coarse element
+    ((10, 6, 6), 60, "tc"),    # most elements touch a fixed DOF: product on the fine stencil
+])
+def test_galerkin_from_elements(lib, ctx, grid, n_extra, prec):
+    """The first hex8 coarse operator P^T A_0 P (Eq. 9), formed straight from the elements with
+    fixed DOFs scattered through the grid (single components of a few nodes), against the
+    oracle's sparse triple product."""
+    import dataclasses
+    p = W.random_problem(3, *grid, seed=31, contrast="minmax")
+    rng = np.random.default_rng(32)
+    nodes = rng.choice(p.n // 3, size=n_extra, replace=False)
+    comps = rng.integers(0, 3, size=n_extra)
+    p = dataclasses.replace(p, fixed=np.unique(np.concatenate([p.fixed, 3 * nodes + comps])))
+    P = make(lib, ctx, p)
+    P.setup(pc="gmg", n_levels=3, prec=prec)
+    H = osolve.build(p, pc="gmg", n_levels=3)
+    for l in (1, 2):
+        Ag = P.level_matrix(l)
+        Ar = H.A[l]
+        assert abs(Ag - Ar).max() <= 1e-13 * abs(Ar).max(), l
+        assert abs(Ag - Ag.T).max() <= 1e-13 * abs(Ar).max(), l
+    r = np.random.default_rng(1).standard_normal(p.n)
+    P.setup(pc="gmg", n_levels=3, prec="fp64")
+    assert relerr(P.vcycle(r), mg.vcycle(H, r)) < 1e-9
+
+
 @pytest.mark.parametrize("pc,kw", [("gmg", dict(n_levels=3)), ("amg", dict(max_coarse_dofs=80)),
                                    ("hybrid", dict(n_geo_levels=2, max_coarse_dofs=80))])
 @pytest.mark.parametrize("dim,grid", [(2, (30, 14, 1)), (3, (8, 6, 5))])
