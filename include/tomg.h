@@ -123,6 +123,15 @@ typedef struct {
                           integer matrix C of Ke = c C (nu with a rational lambda / mu, e.g.
                           0.3), FP64 scaling and node sums; 0: the assembled FP64 stencil on
                           the FP64 pipe.  Ignored where nu admits no such C           1        */
+  int fuse_transfers;  /* V-cycle with the Chebyshev smoother (Algorithm 1, Sec. 3.2): 1 =
+                          the prolongation of the coarse correction computed inside the first
+                          post-smoothing step of the geometric levels that support it (3^d
+                          stencils, the FP32 tensor-core hex8 operator), and the first step
+                          from x = 0 inside the second on hex8 level 0; bit-identical results
+                          to the separate kernels.  Off by default: forming x + P xc at every
+                          node a smoothing kernel reads costs those kernels more than the
+                          separate streaming passes (3D cantilever 192x96x96: 25.9 against
+                          24.0 ms per solve).  0: separate transfer launches           0        */
 } tomg_options;
 
 typedef struct {

@@ -149,6 +149,7 @@ void tomg_options_default(tomg_options* o) {
   o->max_levels = 25;
   o->concurrency = 4;
   o->fp64_tc = 1;
+  o->fuse_transfers = 0;
 }
 
 tomg_status tomg_ctx_create(tomg_ctx** out, int device, void* cuda_stream) {

@@ -192,14 +192,11 @@ struct SetupTrace {
 
 __device__ __forceinline__ bool solve_done(const int* done) { return done && *(volatile const int*)done; }
 
-// First point-block Jacobi sweep from x = 0 at one node: x = w Dinv_node b_node (B x B blocks)
+// First point-block Jacobi sweep from x = 0 at one node: x = w Dinv_node b_node (B x B blocks).
+// Every kernel that forms this value (the sweep itself and the smoothing steps that fuse it)
+// goes through jacobi_block, so they agree bit for bit.
 template <class T, int B>
-__device__ __forceinline__ void jacobi_first(const T* __restrict__ Dinv, const T* __restrict__ b,
-                                             int64_t node, T omega, T* xv) {
-  const T* D = Dinv + (int64_t)B * B * node;
-  T bv[B];
-#pragma unroll
-  for (int c = 0; c < B; c++) bv[c] = b[(int64_t)B * node + c];
+__device__ __forceinline__ void jacobi_block(const T* D, const T* bv, T omega, T* xv) {
 #pragma unroll
   for (int r = 0; r < B; r++) {
     T v = T(0);
@@ -207,6 +204,16 @@ __device__ __forceinline__ void jacobi_first(const T* __restrict__ Dinv, const T
     for (int c = 0; c < B; c++) v += D[r * B + c] * bv[c];
     xv[r] = omega * v;
   }
+}
+template <class T, int B>
+__device__ __forceinline__ void jacobi_first(const T* __restrict__ Dinv, const T* __restrict__ b,
+                                             int64_t node, T omega, T* xv) {
+  T D[B * B], bv[B];
+#pragma unroll
+  for (int t = 0; t < B * B; t++) D[t] = Dinv[(int64_t)B * B * node + t];
+#pragma unroll
+  for (int c = 0; c < B; c++) bv[c] = b[(int64_t)B * node + c];
+  jacobi_block<T, B>(D, bv, omega, xv);
 }
 
 // Chebyshev smoother step at one node (B components) from its residual r = b - A x:
@@ -284,6 +291,19 @@ __device__ __forceinline__ bool spd_inverse(const double* A, double* Ainv) {
 // linear node index <-> grid coordinates
 __device__ __forceinline__ void node_ijk(int64_t node, int nx, int ny, int dim, int& i, int& j,
                                          int& k) {
+  if (node >= 0 && node < 0x7fffffffLL) {  // 32-bit division (a 64-bit one is a long sequence)
+    const unsigned n = (unsigned)node, a = (unsigned)(nx + 1);
+    i = (int)(n % a);
+    const unsigned r = n / a;
+    if (dim == 3) {
+      j = (int)(r % (unsigned)(ny + 1));
+      k = (int)(r / (unsigned)(ny + 1));
+    } else {
+      j = (int)r;
+      k = 0;
+    }
+    return;
+  }
   i = (int)(node % (nx + 1));
   int64_t r = node / (nx + 1);
   if (dim == 3) {
@@ -296,5 +316,55 @@ __device__ __forceinline__ void node_ijk(int64_t node, int nx, int ny, int dim, 
 }
 __device__ __forceinline__ int64_t node_id(int i, int j, int k, int nx, int ny) {
   return (int64_t)i + (int64_t)(nx + 1) * ((int64_t)j + (int64_t)(ny + 1) * k);
+}
+
+// Geometric transfers (Sec. 3.2): coarse node I sits at fine position min(2I, nf) per axis; a
+// fine node at a coarse position takes weight 1 from it, one midway between two coarse nodes
+// 1/2 from each.  coarse_of lists the coarse partners of fine position p and their weights.
+__host__ __device__ __forceinline__ int coarse_of(int p, int nf, int* I, double* w) {
+  const int nc = (nf + 1) / 2;
+  if (p == nf) { I[0] = nc; w[0] = 1.0; return 1; }
+  if ((p & 1) == 0) { I[0] = p / 2; w[0] = 1.0; return 1; }
+  I[0] = (p - 1) / 2; w[0] = 0.5;
+  I[1] = (p + 1) / 2; w[1] = 0.5;
+  return 2;
+}
+// the same partners along one axis with FP32 weights (1 or 1/2: products of three are exact
+// in any precision, so no FP64 instruction is needed to form them)
+struct AxisP {
+  int n;
+  int I[2];
+  float w[2];
+};
+__device__ __forceinline__ AxisP axis_partners(int p, int nf) {
+  AxisP a;
+  const int nc = (nf + 1) / 2;
+  if (p == nf) { a.n = 1; a.I[0] = nc; a.w[0] = 1.f; a.I[1] = nc; a.w[1] = 0.f; return a; }
+  if ((p & 1) == 0) { a.n = 1; a.I[0] = p >> 1; a.w[0] = 1.f; a.I[1] = a.I[0]; a.w[1] = 0.f; return a; }
+  a.n = 2; a.I[0] = (p - 1) >> 1; a.w[0] = 0.5f; a.I[1] = (p + 1) >> 1; a.w[1] = 0.5f;
+  return a;
+}
+// acc += (P xc) at the fine node with axis partners (px, py, pz), coarse vector xc on the grid
+// cnx x cny (x cnz), in a fixed order (z, y, x partners).  The prolongation kernel and the
+// smoothing steps that fuse it all go through here, so they agree bit for bit.
+template <class T, int DIM>
+__device__ __forceinline__ void prolong_acc(const AxisP& px, const AxisP& py, const AxisP& pz,
+                                            int cnx, int cny, const T* __restrict__ xc, T* acc) {
+  const int nzs = DIM == 3 ? pz.n : 1;
+  for (int c3 = 0; c3 < nzs; c3++)
+    for (int b = 0; b < py.n; b++)
+      for (int a = 0; a < px.n; a++) {
+        const T w = (T)(px.w[a] * py.w[b] * (DIM == 3 ? pz.w[c3] : 1.f));
+        const int64_t I = node_id(px.I[a], py.I[b], DIM == 3 ? pz.I[c3] : 0, cnx, cny);
+#pragma unroll
+        for (int c = 0; c < DIM; c++) acc[c] += w * xc[DIM * I + c];
+      }
+}
+template <class T, int DIM>
+__device__ __forceinline__ void prolong_node(int x, int y, int z, int fnx, int fny, int fnz,
+                                             int cnx, int cny, const T* __restrict__ xc, T* acc) {
+  const AxisP px = axis_partners(x, fnx), py = axis_partners(y, fny);
+  const AxisP pz = DIM == 3 ? axis_partners(z, fnz) : AxisP{1, {0, 0}, {1.f, 0.f}};
+  prolong_acc<T, DIM>(px, py, pz, cnx, cny, xc, acc);
 }
 }  // namespace tomg

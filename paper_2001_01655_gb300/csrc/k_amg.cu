@@ -71,38 +71,95 @@ __global__ void k_strength(int nbr, int b, const int* __restrict__ rp, const int
   if (counts && lane == 0) counts[i] = cnt;
 }
 
-__global__ void k_mis_init(int n, const int* __restrict__ srp, int* state) {
-  const int i = blockIdx.x * blockDim.x + threadIdx.x;
-  if (i >= n) return;
-  state[i] = (srp[i + 1] == srp[i]) ? OUT : UND;
+// All MIS-2 rounds in one cooperative launch (every block resident): the three phases of a
+// round (values, neighbour maxima, update) are separated by a grid barrier, and the blocks stop
+// together after the first round that leaves no node undecided.  Per round: v = TOP for a node
+// in the set, its key for an undecided node, 0 otherwise; m1 = the largest v within distance 1;
+// an undecided node whose largest m1 within distance 1 is TOP leaves, one whose own key is that
+// maximum joins (distance-2 independence).  Values written by other blocks
+// are read past L1 (ld.global.cg).  Barrier waits are bounded: a block that gives up sets
+// sync[4] and leaves, and so do the others when their own waits run out.
+//   sync[0] arrivals, sync[1] generation, sync[2..3] undecided counts of even / odd rounds,
+//   sync[4] error, sync[5] rounds run
+constexpr unsigned MIS_WAIT_LIMIT = 1u << 24;
+
+__device__ __forceinline__ bool grid_barrier(unsigned* sync, unsigned nblocks) {
+  __syncthreads();
+  unsigned ok = 1;
+  if (threadIdx.x == 0) {
+    volatile unsigned* gen = sync + 1;
+    const unsigned g = *gen;
+    __threadfence();
+    if (atomicAdd(sync, 1u) == nblocks - 1) {
+      sync[0] = 0;
+      __threadfence();
+      atomicAdd(sync + 1, 1u);
+    } else {
+      unsigned it = 0;
+      while (*gen == g) {
+        if (++it > MIS_WAIT_LIMIT || *(volatile unsigned*)(sync + 4)) {
+          ok = 0;
+          break;
+        }
+        __nanosleep(64);
+      }
+    }
+    __threadfence();
+    if (!ok) atomicExch(sync + 4, 1u);
+  }
+  return __syncthreads_and(ok) != 0;
 }
-__global__ void k_mis_values(int n, int level, const int* __restrict__ state, uint64_t* v) {
-  const int i = blockIdx.x * blockDim.x + threadIdx.x;
-  if (i >= n) return;
-  const int st = state[i];
-  v[i] = (st == IN) ? TOP : (st == UND ? mis_key(i, level) : 0ull);
-}
-__global__ void k_neigh_max(int n, const int* __restrict__ srp, const int* __restrict__ sci,
-                            const uint64_t* __restrict__ v, uint64_t* m) {
-  const int i = blockIdx.x * blockDim.x + threadIdx.x;
-  if (i >= n) return;
-  uint64_t best = v[i];
-  for (int p = srp[i]; p < srp[i + 1]; p++) best = max(best, v[sci[p]]);
-  m[i] = best;
-}
-__global__ void k_mis_update(int n, int level, const int* __restrict__ srp,
-                             const int* __restrict__ sci, const uint64_t* __restrict__ m1,
-                             int* state, int* undecided) {
-  const int i = blockIdx.x * blockDim.x + threadIdx.x;
-  if (i >= n) return;
-  if (state[i] != UND) return;
-  uint64_t m2 = m1[i];
-  for (int p = srp[i]; p < srp[i + 1]; p++) m2 = max(m2, m1[sci[p]]);
-  int st = UND;
-  if (m2 == TOP) st = OUT;
-  else if (m2 == mis_key(i, level)) st = IN;
-  state[i] = st;
-  if (st == UND) atomicAdd(undecided, 1);
+
+__global__ void __launch_bounds__(256) k_mis2_loop(int n, int level, const int* __restrict__ srp,
+                                                   const int* __restrict__ sci, int* state,
+                                                   uint64_t* v, uint64_t* m1, unsigned* sync,
+                                                   int max_rounds) {
+  __shared__ unsigned red[8];
+  const int stride = gridDim.x * blockDim.x;
+  const int t0 = blockIdx.x * blockDim.x + threadIdx.x;
+  const unsigned nb = gridDim.x;
+  for (int i = t0; i < n; i += stride) state[i] = (srp[i + 1] == srp[i]) ? OUT : UND;
+  if (!grid_barrier(sync, nb)) return;
+  for (int r = 0; r < max_rounds; r++) {
+    for (int i = t0; i < n; i += stride) {
+      const int st = state[i];
+      v[i] = (st == IN) ? TOP : (st == UND ? mis_key(i, level) : 0ull);
+    }
+    if (!grid_barrier(sync, nb)) return;
+    // the other round's count: every block has read it before the barrier above
+    if (t0 == 0) sync[2 + ((r + 1) & 1)] = 0;
+    for (int i = t0; i < n; i += stride) {
+      uint64_t best = __ldcg(v + i);
+      for (int p = srp[i]; p < srp[i + 1]; p++) best = max(best, __ldcg(v + sci[p]));
+      m1[i] = best;
+    }
+    if (!grid_barrier(sync, nb)) return;
+    unsigned und = 0;
+    for (int i = t0; i < n; i += stride) {
+      if (state[i] != UND) continue;
+      uint64_t m2 = __ldcg(m1 + i);
+      for (int p = srp[i]; p < srp[i + 1]; p++) m2 = max(m2, __ldcg(m1 + sci[p]));
+      int st = UND;
+      if (m2 == TOP) st = OUT;
+      else if (m2 == mis_key(i, level)) st = IN;
+      state[i] = st;
+      und += st == UND ? 1u : 0u;
+    }
+    for (int o = 16; o > 0; o >>= 1) und += __shfl_xor_sync(0xffffffffu, und, o);
+    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = und;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      unsigned tot = 0;
+      for (int w = 0; w < (int)(blockDim.x >> 5); w++) tot += red[w];
+      if (tot) atomicAdd(sync + 2 + (r & 1), tot);
+    }
+    if (!grid_barrier(sync, nb)) return;
+    if (*(volatile unsigned*)(sync + 2 + (r & 1)) == 0) {
+      if (t0 == 0) sync[5] = (unsigned)(r + 1);
+      return;
+    }
+  }
+  if (t0 == 0) sync[5] = (unsigned)max_rounds;
 }
 
 __global__ void k_root_flags(int n, const int* __restrict__ state, int* flags) {
@@ -314,25 +371,27 @@ __global__ void k_scale(int64_t n, double* v, double s) {
   if (i < n) v[i] *= s;
 }
 
+// P = T - omega D^-1 (A T), row block i of P by one warp: the lanes take the scalars of the
+// row's blocks in turn (block p, row r, column c), each the same b-term sum as a serial loop
 __global__ void k_smooth_P(int nbr, int b, int k, const int* __restrict__ rp,
                            const int* __restrict__ ci, const double* __restrict__ ATV,
                            const int* __restrict__ agg, const int* __restrict__ Trp,
                            const double* __restrict__ TV, const double* __restrict__ Dinv,
                            double omega, double* PV) {
-  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  const int i = (int)(((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5);
+  const int lane = threadIdx.x & 31;
   if (i >= nbr) return;
   const double* D = Dinv + (int64_t)b * b * i;
-  for (int p = rp[i]; p < rp[i + 1]; p++) {
-    const double* X = ATV + (int64_t)p * b * k;
-    double* Y = PV + (int64_t)p * b * k;
-    const bool own = (agg[i] >= 0 && ci[p] == agg[i]);
-    const double* Tb = own ? TV + (int64_t)Trp[i] * b * k : nullptr;
-    for (int r = 0; r < b; r++)
-      for (int c = 0; c < k; c++) {
-        double t = 0.0;
-        for (int q = 0; q < b; q++) t += D[r * b + q] * X[q * k + c];
-        Y[r * k + c] = (own ? Tb[r * k + c] : 0.0) - omega * t;
-      }
+  const int p0 = rp[i], bk = b * k;
+  const int items = (rp[i + 1] - p0) * bk;
+  const int ai = agg[i];
+  for (int it = lane; it < items; it += 32) {
+    const int p = p0 + it / bk, rc = it % bk, r = rc / k, c = rc % k;
+    const double* X = ATV + (int64_t)p * bk;
+    double t = 0.0;
+    for (int q = 0; q < b; q++) t += D[r * b + q] * X[q * k + c];
+    const bool own = ai >= 0 && ci[p] == ai;
+    PV[(int64_t)p * bk + rc] = (own ? TV[(int64_t)Trp[i] * bk + rc] : 0.0) - omega * t;
   }
 }
 
@@ -399,26 +458,36 @@ void amg_strength_fill(cudaStream_t s, const Bsr& A, const double* V, double bet
 
 int amg_mis2(cudaStream_t s, int n, const int* srp, const int* sci, int level, int* state,
              uint64_t* v, uint64_t* m1, int* flag_host, int* flag_dev) {
-  const int g = ceil_div(n, 256);
-  LAUNCH(k_mis_init, g, 256, 0, s, n, srp, state);
-  // rounds run in batches between host checks: once every node is decided a round changes
-  // nothing, so the rounds after convergence inside a batch are no-ops
-  constexpr int BATCH = 4;
-  int rounds = 0;
-  while (true) {
-    for (int k = 0; k < BATCH; k++) {
-      CK(cudaMemsetAsync(flag_dev, 0, sizeof(int), s));
-      LAUNCH(k_mis_values, g, 256, 0, s, n, level, state, v);
-      LAUNCH(k_neigh_max, g, 256, 0, s, n, srp, sci, v, m1);
-      LAUNCH(k_mis_update, g, 256, 0, s, n, level, srp, sci, m1, state, flag_dev);
-    }
-    CK(cudaMemcpyAsync(flag_host, flag_dev, sizeof(int), cudaMemcpyDeviceToHost, s));
-    CK(cudaStreamSynchronize(s));
-    rounds += BATCH;
-    if (*flag_host == 0) break;
-    if (rounds > 100000) TOMG_THROW(TOMG_E_BREAKDOWN, "MIS-2 did not terminate");
-  }
-  return rounds;
+  (void)flag_dev;
+  if (n == 0) return 0;
+  // one cooperative launch, every block resident (grid-stride loops over the nodes)
+  static int per_sm = 0;
+  if (per_sm == 0)
+    CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_mis2_loop, 256, 0));
+  const int grid = std::max(1, std::min(ceil_div(n, 256), per_sm * num_sms()));
+  constexpr int MAX_ROUNDS = 100000;
+  DBuf<unsigned> sync;
+  sync.resize(6);
+  sync.zero(s);
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3(grid);
+  cfg.blockDim = dim3(256);
+  cfg.stream = s;
+  cudaLaunchAttribute at[1];
+  at[0].id = cudaLaunchAttributeCooperative;
+  at[0].val.cooperative = 1;
+  cfg.attrs = at;
+  cfg.numAttrs = 1;
+  CK(cudaLaunchKernelEx(&cfg, k_mis2_loop, n, level, srp, sci, state, v, m1, sync.p,
+                        MAX_ROUNDS));
+  g_launches++;
+  unsigned h[6];
+  CK(cudaMemcpyAsync(h, sync.p, sizeof(h), cudaMemcpyDeviceToHost, s));
+  CK(cudaStreamSynchronize(s));
+  (void)flag_host;
+  if (h[4]) TOMG_THROW(TOMG_E_TIMEOUT, "MIS-2 grid barrier wait ran out");
+  if ((int)h[5] >= MAX_ROUNDS) TOMG_THROW(TOMG_E_BREAKDOWN, "MIS-2 did not terminate");
+  return (int)h[5];
 }
 
 int amg_aggregate(cudaStream_t s, int n, const int* srp, const int* sci, int level,
@@ -440,8 +509,8 @@ int amg_aggregate(cudaStream_t s, int n, const int* srp, const int* sci, int lev
   return n_agg;
 }
 
-void amg_tentative(cudaStream_t s, int n, int b, int k, int n_agg, const int* agg,
-                   const double* B, int* Trp, int* Tci, double* TV, double* Bc) {
+int64_t amg_tentative(cudaStream_t s, int n, int b, int k, int n_agg, const int* agg,
+                      const double* B, int* Trp, int* Tci, double* TV, double* Bc) {
   const int g = ceil_div(n, 256);
   DBuf<int> flags, cnt, start, cursor, members;
   flags.resize(n);
@@ -455,12 +524,12 @@ void amg_tentative(cudaStream_t s, int n, int b, int k, int n_agg, const int* ag
   cnt.zero(s);
   cursor.zero(s);
   LAUNCH(k_agg_count, g, 256, 0, s, n, agg, cnt.p);
-  exclusive_scan(s, cnt.p, start.p, n_agg);
+  exclusive_scan_nosync(s, cnt.p, start.p, n_agg);
   LAUNCH(k_agg_scatter, g, 256, 0, s, n, agg, start.p, cursor.p, members.p);
   LAUNCH(k_agg_sort, ceil_div(n_agg, 128), 128, 0, s, n_agg, start.p, members.p);
   LAUNCH(k_tentative, ceil_div((int64_t)n_agg * 32, 128), 128, 0, s, n_agg, b, k, start.p,
          members.p, Trp, B, TV, Bc);
-  CK(cudaStreamSynchronize(s));
+  return nT;
 }
 
 void amg_power_alloc(cudaStream_t s, AmgPower& ps, const Bsr& A, int iters) {
@@ -584,8 +653,8 @@ double spectral_radius_op(cudaStream_t s, int64_t nodes, int bs, const double* D
 void amg_smooth_prolongator(cudaStream_t s, const Bsr& AT, const double* ATV, const int* agg,
                             const double* TV, const int* Trp, const double* Dinv, double omega,
                             int b, double* PV) {
-  LAUNCH(k_smooth_P, ceil_div(AT.nbr, 128), 128, 0, s, AT.nbr, b, AT.bc, AT.rp, AT.ci, ATV, agg,
-         Trp, TV, Dinv, omega, PV);
+  LAUNCH(k_smooth_P, ceil_div((int64_t)AT.nbr * 32, 128), 128, 0, s, AT.nbr, b, AT.bc, AT.rp,
+         AT.ci, ATV, agg, Trp, TV, Dinv, omega, PV);
 }
 
 void amg_fix_zero_rows(cudaStream_t s, const Bsr& A, double* V) {

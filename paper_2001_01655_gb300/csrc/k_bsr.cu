@@ -357,9 +357,25 @@ __global__ void __launch_bounds__(32 * SPG_WARPS)
   }
 }
 
+// position of column c in row r of a CSR pattern (sorted columns), or -1
+__device__ __forceinline__ int64_t csr_find(const int* __restrict__ rp, const int* __restrict__ ci,
+                                            int r, int c) {
+  int l = rp[r], h = rp[r + 1];
+  const int end = h;
+  while (l < h) {
+    const int mid = (l + h) >> 1;
+    if (ci[mid] < c) l = mid + 1;
+    else h = mid;
+  }
+  return (l < end && ci[l] == c) ? l : -1;
+}
+
 // Numeric phase for long rows of A (the coarse Galerkin products): one warp per output block,
 // the lanes split A's row and their partial blocks are combined by a fixed butterfly, so the
-// work of one output block is spread over 32 lanes instead of one (still deterministic).
+// work of one output block is spread over 32 lanes instead of one (still deterministic).  With
+// sym set (C = P^T A P, symmetric, square blocks) the warp of an upper block (j > row) also
+// writes its transpose into the mirror block, and the warp of a lower block with a mirror does
+// nothing: half the FP64 work, and C symmetric to the last bit.
 template <int BR, int BK, int BC>
 __global__ void __launch_bounds__(128) k_spgemm_num_w(int nrows, int64_t nnzC,
                                                       const int* __restrict__ Arp,
@@ -369,7 +385,8 @@ __global__ void __launch_bounds__(128) k_spgemm_num_w(int nrows, int64_t nnzC,
                                                       const int* __restrict__ Bci,
                                                       const double* __restrict__ VB,
                                                       const int* __restrict__ Crp,
-                                                      const int* __restrict__ Cci, double* VC) {
+                                                      const int* __restrict__ Cci, double* VC,
+                                                      int sym) {
   const int64_t pc = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
   const int lane = threadIdx.x & 31;
   if (pc >= nnzC) return;  // warp-uniform
@@ -380,6 +397,12 @@ __global__ void __launch_bounds__(128) k_spgemm_num_w(int nrows, int64_t nnzC,
     else hi = mid;
   }
   const int row = lo, j = Cci[pc];
+  int64_t mirror = -1;
+  if (BR == BC && sym && j != row) {
+    mirror = csr_find(Crp, Cci, j, row);  // warp-uniform
+    if (j < row && mirror >= 0) return;   // written by the warp of block (j, row)
+    if (j < row) mirror = -1;
+  }
   double acc[BR * BC];
 #pragma unroll
   for (int t = 0; t < BR * BC; t++) acc[t] = 0.0;
@@ -412,6 +435,12 @@ __global__ void __launch_bounds__(128) k_spgemm_num_w(int nrows, int64_t nnzC,
 #pragma unroll
   for (int t = 0; t < BR * BC; t++)
     if (lane == (t & 31)) Cb[t] = acc[t];
+  if (BR == BC && mirror >= 0) {
+    double* Ct = VC + mirror * BR * BC;
+#pragma unroll
+    for (int t = 0; t < BR * BC; t++)
+      if (lane == (t & 31)) Ct[(t % BC) * BR + t / BC] = acc[t];
+  }
 }
 
 // Numeric phase, one warp per row of C: for each output block of the row the lanes first
@@ -643,17 +672,19 @@ void spgemm_fill(cudaStream_t s, const Bsr& A, const Bsr& B, const int* rpC, int
 }
 
 void spgemm_numeric(cudaStream_t s, const Bsr& A, const double* VA, const Bsr& B, const double* VB,
-                    const Bsr& C, double* VC) {
+                    const Bsr& C, double* VC, bool sym) {
   const int grid = ceil_div((int64_t)A.nbr * 32, 128);
-  // few long rows (the coarsest Galerkin products): one warp per output block
-  const bool long_rows = A.nbr > 0 && A.nbr < 4096 && A.nnzb >= 12LL * A.nbr;
+  // few long rows (the restrictions of the coarse Galerkin products, a hundred blocks and more
+  // per row): one warp per output block.  Shorter rows keep the row-per-warp kernel, whose
+  // lanes own the output scalars (no butterfly of every output block over 32 lanes)
+  const bool long_rows = A.nbr > 0 && A.nbr < 4096 && A.nnzb >= 48LL * A.nbr;
   const int gridw = (int)std::max<int64_t>(1, ceil_div(C.nnzb * 32, 128));
 #define NUM(R, K, CC)                                                                          \
   if (A.br == R && A.bc == K && B.bc == CC) {                                                  \
     if (long_rows) {                                                                           \
       if (C.nnzb > 0)                                                                          \
         LAUNCH((k_spgemm_num_w<R, K, CC>), gridw, 128, 0, s, A.nbr, C.nnzb, A.rp, A.ci, VA,     \
-               B.rp, B.ci, VB, C.rp, C.ci, VC);                                                \
+               B.rp, B.ci, VB, C.rp, C.ci, VC, sym ? 1 : 0);                                   \
       return;                                                                                  \
     }                                                                                          \
     LAUNCH((k_spgemm_num_s<R, K, CC>), grid, 128, 0, s, A.nbr, A.rp, A.ci, VA, B.rp, B.ci, VB, \
@@ -670,6 +701,14 @@ void cast_f64_f32(cudaStream_t s, const double* a, float* b, int64_t n) {
 }
 void cast_f32_f64(cudaStream_t s, const float* a, double* b, int64_t n) {
   if (n > 0) LAUNCH((k_cast<float, double>), ceil_div(n, 256), 256, 0, s, a, b, n);
+}
+
+void exclusive_scan_nosync(cudaStream_t s, const int* in, int* out, int64_t n) {
+  if (n == 0) {
+    CK(cudaMemsetAsync(out, 0, sizeof(int), s));
+    return;
+  }
+  scan_rec(s, in, out, n, out + n);
 }
 
 int64_t exclusive_scan(cudaStream_t s, const int* in, int* out, int64_t n) {

@@ -247,10 +247,18 @@ void ebe_op(cudaStream_t s, int mode, const Ebe& op, const T* x, T* y, const T* 
     return;
   }
   if (mode == MODE_CHEB0) {
+    if (op.dim == 3 && ebe_fuses_transfers<T>(op)) {
+      ebe3d_tc_launch(s, MODE_CHEB0, op, reinterpret_cast<const float*>(x),
+                      reinterpret_cast<float*>(y), reinterpret_cast<const float*>(b),
+                      reinterpret_cast<const float*>(Dinv), omega, done, ch);
+      return;
+    }
     if (op.dim != 2) TOMG_THROW(TOMG_E_INVALID, "fused first Chebyshev steps on quad4 only");
     ebe2d_launch<T, MODE_CHEB0, false>(s, op, x, y, b, Dinv, omega, done, parts, ch);
     return;
   }
+  if (ch && ch->xc && !(op.dim == 3 && ebe_fuses_transfers<T>(op)))
+    TOMG_THROW(TOMG_E_INVALID, "fused prolongation on the hex8 tensor-core operator only");
   if (op.dim == 2) {
     if (mode == MODE_APPLY) {
       if (parts) launch_ebe<T, 2, MODE_APPLY, true>(s, op, x, y, b, Dinv, omega, done, parts);

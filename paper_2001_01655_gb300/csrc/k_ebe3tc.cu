@@ -194,18 +194,34 @@ __device__ __forceinline__ void tmem_st24(uint32_t taddr, const uint32_t* v) {
       : "memory");
 }
 
-// one node layer of the tile: displacements and mask bits of up to two nodes per thread.  The
-// loads are independent (the mask is applied when the layer is stored), so a prefetch issued
-// at the top of a layer step never stalls the thread before the values are needed.
+// Input transforms of a Chebyshev step that fuses the kernel before it: the iterate of the step
+// is formed where it is read (in the layer ring and for the owned nodes), with the same device
+// functions as the kernels it replaces, so the results are bit-identical to the unfused pair.
+//   XF_NONE  x as stored
+//   XF_JAC0  x = w0 Dinv b       (the first step from x = 0: the k_jacobi0 sweep)
+//   XF_PROL  x = x + P xc        (the coarse correction: the k_prolong_add pass)
+enum { XF_NONE = 0, XF_JAC0 = 1, XF_PROL = 2 };
+struct XfArg {
+  const float* Dinv;
+  const float* xc;  // coarse correction (XF_PROL), grid cnx x cny x cnz
+  int cnx, cny, cnz;
+  float w0;         // weight of the first step (XF_JAC0)
+};
+
+// one node layer of the tile: displacements (XF_JAC0: right-hand sides) and mask bits of up to
+// two nodes per thread.  The loads are independent (the mask and the transform are applied when
+// the layer is stored), so a prefetch issued at the top of a layer step never stalls the thread
+// before the values are needed.
 struct XPre {
   float v[2][3];
   unsigned m[2];
 };
 
-template <int TY>
+template <int TY, int XF>
 __device__ __forceinline__ void x_fetch(XPre& p, int kk, int EX0, int EY0, int nx, int ny, int nz,
                                         const uint8_t* __restrict__ mask,
-                                        const float* __restrict__ x) {
+                                        const float* __restrict__ x, const float* __restrict__ b) {
+  const float* src = XF == XF_JAC0 ? b : x;
 #pragma unroll
   for (int h = 0; h < 2; h++) {
     const int q = threadIdx.x + h * Cfg<TY>::NT;
@@ -217,18 +233,41 @@ __device__ __forceinline__ void x_fetch(XPre& p, int kk, int EX0, int EY0, int n
         const int64_t node = node_id(gi, gj, kk, nx, ny);
         p.m[h] = __ldg(mask + node);
 #pragma unroll
-        for (int c = 0; c < 3; c++) p.v[h][c] = __ldg(x + 3 * node + c);
+        for (int c = 0; c < 3; c++) p.v[h][c] = __ldg(src + 3 * node + c);
       }
     }
   }
 }
 
-template <int TY>
-__device__ __forceinline__ void x_store(const XPre& p, float* sx) {
+// the fused input transform at one node (v: x, or b for XF_JAC0)
+template <int XF>
+__device__ __forceinline__ void x_transform(float* v, int gi, int gj, int kk, int64_t node,
+                                            int nx, int ny, int nz, const XfArg& xa) {
+  if (XF == XF_JAC0) {
+    float D[9], bv[3];
+#pragma unroll
+    for (int t = 0; t < 9; t++) D[t] = __ldg(xa.Dinv + 9 * node + t);
+#pragma unroll
+    for (int c = 0; c < 3; c++) bv[c] = v[c];
+    jacobi_block<float, 3>(D, bv, xa.w0, v);
+  } else if (XF == XF_PROL) {
+    prolong_node<float, 3>(gi, gj, kk, nx, ny, nz, xa.cnx, xa.cny, xa.xc, v);
+  }
+}
+
+template <int TY, int XF>
+__device__ __forceinline__ void x_store(XPre& p, float* sx, int kk, int EX0, int EY0, int nx,
+                                        int ny, int nz, const XfArg& xa) {
 #pragma unroll
   for (int h = 0; h < 2; h++) {
     const int q = threadIdx.x + h * Cfg<TY>::NT;
     if (q < Cfg<TY>::LAYER_NODES) {
+      // a node outside the grid has all three bits set, as has one fixed in every direction:
+      // neither needs the transform (its values are stored as zero)
+      if (XF != XF_NONE && p.m[h] != 7u) {
+        const int gi = EX0 + q % TNX, gj = EY0 + q / TNX;
+        x_transform<XF>(p.v[h], gi, gj, kk, node_id(gi, gj, kk, nx, ny), nx, ny, nz, xa);
+      }
 #pragma unroll
       for (int c = 0; c < 3; c++) sx[3 * q + c] = ((p.m[h] >> c) & 1u) ? 0.f : p.v[h][c];
     }
@@ -241,16 +280,15 @@ struct FinData {
   unsigned m;
 };
 
-template <int MODE>
-__device__ __forceinline__ void fin_fetch(FinData& f, bool valid, int64_t node,
-                                          const uint8_t* __restrict__ mask,
+template <int MODE, int XF>
+__device__ __forceinline__ void fin_fetch(FinData& f, bool valid, int gi, int gj, int kk, int nx,
+                                          int ny, int nz, const uint8_t* __restrict__ mask,
                                           const float* __restrict__ x,
                                           const float* __restrict__ b,
-                                          const float* __restrict__ Dinv) {
+                                          const float* __restrict__ Dinv, const XfArg& xa) {
   if (!valid) return;
+  const int64_t node = node_id(gi, gj, kk, nx, ny);
   f.m = __ldg(mask + node);
-#pragma unroll
-  for (int c = 0; c < 3; c++) f.x[c] = __ldg(x + 3 * node + c);
   if (MODE != MODE_APPLY) {
 #pragma unroll
     for (int c = 0; c < 3; c++) f.b[c] = __ldg(b + 3 * node + c);
@@ -258,6 +296,13 @@ __device__ __forceinline__ void fin_fetch(FinData& f, bool valid, int64_t node,
   if (MODE == MODE_JACOBI || MODE == MODE_CHEB) {
 #pragma unroll
     for (int c = 0; c < 9; c++) f.D[c] = __ldg(Dinv + 9 * node + c);
+  }
+  if (XF == XF_JAC0) {
+    jacobi_block<float, 3>(f.D, f.b, xa.w0, f.x);
+  } else {
+#pragma unroll
+    for (int c = 0; c < 3; c++) f.x[c] = __ldg(x + 3 * node + c);
+    if (XF == XF_PROL) x_transform<XF_PROL>(f.x, gi, gj, kk, node, nx, ny, nz, xa);
   }
 }
 
@@ -320,13 +365,13 @@ __device__ __forceinline__ void issue_mmas(uint32_t d, uint32_t a, uint32_t bbas
                :: "r"(bar) : "memory");
 }
 
-template <int MODE, int TY>
+template <int MODE, int TY, int XF>
 __global__ void __launch_bounds__(Cfg<TY>::NT, Cfg<TY>::MAX_BLOCKS)
 k_ebe3tc(int nx, int ny, int nz, int nz_tile, const uint4* __restrict__ Bimg,
          const float* __restrict__ E, const uint8_t* __restrict__ mask,
          const float* __restrict__ x, float* __restrict__ y, const float* __restrict__ b,
          const float* __restrict__ Dinv, float omega, const int* done, float* __restrict__ dch,
-         float c1, int dmode, float cl, float cm, uint32_t wait_limit, int nzc) {
+         float c1, int dmode, float cl, float cm, uint32_t wait_limit, int nzc, XfArg xa) {
   using C = Cfg<TY>;
   constexpr int NT = C::NT, LAYER_NODES = C::LAYER_NODES, ONY = C::ONY, MT = C::MT;
   constexpr int OFF_B = C::OFF_B, OFF_X = C::OFF_X, OFF_P = C::OFF_P, OFF_BAR = C::OFF_BAR;
@@ -349,10 +394,12 @@ k_ebe3tc(int nx, int ny, int nz, int nz_tile, const uint4* __restrict__ Bimg,
   const int zc = blockIdx.z % nzc, rhs = blockIdx.z / nzc;
   {
     const int64_t vo = (int64_t)rhs * rhs_stride((int64_t)3 * (nx + 1) * (ny + 1) * (nz + 1));
-    x += vo;
+    if (x) x += vo;
     y += vo;
     if (b) b += vo;
     if (dch) dch += vo;
+    if (XF == XF_PROL)
+      xa.xc += (int64_t)rhs * rhs_stride((int64_t)3 * (xa.cnx + 1) * (xa.cny + 1) * (xa.cnz + 1));
   }
   const int k0 = zc * nz_tile;
   const int k1 = min(k0 + nz_tile, nz + 1);  // owned node layers [k0, k1)
@@ -377,11 +424,11 @@ k_ebe3tc(int nx, int ny, int nz, int nz_tile, const uint4* __restrict__ Bimg,
   const bool in_plane = owner && gi <= nx && gj <= ny;
 
   XPre pre, pre2;
-  x_fetch<TY>(pre, k0 - 1, EX0, EY0, nx, ny, nz, mask, x);
-  x_fetch<TY>(pre2, k0, EX0, EY0, nx, ny, nz, mask, x);
-  x_store<TY>(pre, sxr + ((k0 - 1) & 1) * LAYER_NODES * 3);
-  x_store<TY>(pre2, sxr + (k0 & 1) * LAYER_NODES * 3);
-  x_fetch<TY>(pre, k0 + 1, EX0, EY0, nx, ny, nz, mask, x);  // stored after layer k0 - 1 is built
+  x_fetch<TY, XF>(pre, k0 - 1, EX0, EY0, nx, ny, nz, mask, x, b);
+  x_fetch<TY, XF>(pre2, k0, EX0, EY0, nx, ny, nz, mask, x, b);
+  x_store<TY, XF>(pre, sxr + ((k0 - 1) & 1) * LAYER_NODES * 3, k0 - 1, EX0, EY0, nx, ny, nz, xa);
+  x_store<TY, XF>(pre2, sxr + (k0 & 1) * LAYER_NODES * 3, k0, EX0, EY0, nx, ny, nz, xa);
+  x_fetch<TY, XF>(pre, k0 + 1, EX0, EY0, nx, ny, nz, mask, x, b);  // stored after layer k0 - 1
   float e_cur = e_fetch(k0 - 1, EX0, EY0, nx, ny, nz, E);  // modulus of element layer ke
   float e_prev = 0.f;                                      // ... of layer ke - 1
   float sc_prev = 1.f;                                     // 2^s of the row of layer ke - 1
@@ -436,14 +483,14 @@ k_ebe3tc(int nx, int ny, int nz, int nz_tile, const uint4* __restrict__ Bimg,
     }
     // refill the ring: node layer ke + 2 replaces layer ke (read by the row build above)
     if (mma_now && ke + 2 <= k1) {
-      x_store<TY>(pre, sxr + j * LAYER_NODES * 3);
-      if (ke + 3 <= k1) x_fetch<TY>(pre, ke + 3, EX0, EY0, nx, ny, nz, mask, x);
+      x_store<TY, XF>(pre, sxr + j * LAYER_NODES * 3, ke + 2, EX0, EY0, nx, ny, nz, xa);
+      if (ke + 3 <= k1) x_fetch<TY, XF>(pre, ke + 3, EX0, EY0, nx, ny, nz, mask, x, b);
     }
     const float e_next = (ke + 1 < k1) ? e_fetch(ke + 1, EX0, EY0, nx, ny, nz, E) : 0.f;
     // finishing data of node layer ke, used one step later
     FinData fd_next;
     const bool fin_next = in_plane && ke >= k0 && ke < k1;
-    fin_fetch<MODE>(fd_next, fin_next, node_id(gi, gj, ke, nx, ny), mask, x, b, Dinv);
+    fin_fetch<MODE, XF>(fd_next, fin_next, gi, gj, ke, nx, ny, nz, mask, x, b, Dinv, xa);
 
     float pr[2][2][3];  // x-pair sums of element layer ke - 1 at node column ex: [dy][dz][c]
     if (ke >= k0) {
@@ -544,7 +591,7 @@ k_ebe3tc(int nx, int ny, int nz, int nz_tile, const uint4* __restrict__ Bimg,
   }
 }
 
-template <int MODE, int TY>
+template <int MODE, int TY, int XF>
 void launch_tile(cudaStream_t s, const Ebe& op, const float* x, float* y, const float* b,
                  const float* Dinv, double omega, const int* done, const ChebArg* ch) {
   using C = Cfg<TY>;
@@ -554,10 +601,11 @@ void launch_tile(cudaStream_t s, const Ebe& op, const float* x, float* y, const 
   static int smem = 0;  // per instantiation
   if (smem == 0) {
     int bytes = C::SMEM_ALLOC, per_sm = 0;
-    CK(cudaFuncSetAttribute(k_ebe3tc<MODE, TY>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+    CK(cudaFuncSetAttribute(k_ebe3tc<MODE, TY, XF>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                             100 << 10));
     for (;;) {
-      CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_ebe3tc<MODE, TY>, C::NT, bytes));
+      CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_ebe3tc<MODE, TY, XF>, C::NT,
+                                                       bytes));
       if (per_sm <= C::MAX_BLOCKS || bytes >= (100 << 10)) break;
       bytes += 4 << 10;
     }
@@ -569,18 +617,27 @@ void launch_tile(cudaStream_t s, const Ebe& op, const float* x, float* y, const 
   if (MODE == MODE_CHEB && !ch) TOMG_THROW(TOMG_E_INVALID, "Chebyshev step without its state");
   float* dch = MODE == MODE_CHEB ? (float*)ch->d : nullptr;
   const float c1 = MODE == MODE_CHEB ? (float)ch->c1 : 0.f;
-  const int dm = MODE == MODE_CHEB ? ch->dmode : 0;
+  const int dm = XF == XF_JAC0 ? 2 : (MODE == MODE_CHEB ? ch->dmode : 0);
+  XfArg xa{Dinv, nullptr, 0, 0, 0, 0.f};
+  if (XF == XF_JAC0) xa.w0 = (float)ch->w0;
+  if (XF == XF_PROL) {
+    if (ch->dmode != 0) TOMG_THROW(TOMG_E_INVALID, "fused prolongation on a later step");
+    xa.xc = static_cast<const float*>(ch->xc);
+    xa.cnx = ch->cnx;
+    xa.cny = ch->cny;
+    xa.cnz = ch->cnz;
+  }
   const uint32_t wl = g_first_wait_limit > 0 ? (uint32_t)g_first_wait_limit : WAIT_LIMIT;
-  LAUNCH((k_ebe3tc<MODE, TY>), grid, C::NT, smem, s, op.nx, op.ny, op.nz, nzt,
+  LAUNCH((k_ebe3tc<MODE, TY, XF>), grid, C::NT, smem, s, op.nx, op.ny, op.nz, nzt,
          reinterpret_cast<const uint4*>(op.Ktc), (const float*)op.E, op.mask, x, y, b, Dinv,
-         (float)omega, done, dch, c1, dm, op.tc_cl, op.tc_cm, wl, nzc);
+         (float)omega, done, dch, c1, dm, op.tc_cl, op.tc_cm, wl, nzc, xa);
 }
 
-template <int MODE>
+template <int MODE, int XF = XF_NONE>
 void launch_mode(cudaStream_t s, const Ebe& op, const float* x, float* y, const float* b,
                  const float* Dinv, double omega, const int* done, const ChebArg* ch = nullptr) {
-  if (op.tc_ty == 4) launch_tile<MODE, 4>(s, op, x, y, b, Dinv, omega, done, ch);
-  else launch_tile<MODE, 8>(s, op, x, y, b, Dinv, omega, done, ch);
+  if (op.tc_ty == 4) launch_tile<MODE, 4, XF>(s, op, x, y, b, Dinv, omega, done, ch);
+  else launch_tile<MODE, 8, XF>(s, op, x, y, b, Dinv, omega, done, ch);
 }
 
 }  // namespace
@@ -625,6 +682,10 @@ void ebe3d_tc_launch(cudaStream_t s, int mode, const Ebe& op, const float* x, fl
                      const ChebArg* ch) {
   if (mode == MODE_APPLY) launch_mode<MODE_APPLY>(s, op, x, y, b, Dinv, omega, done);
   else if (mode == MODE_RESID) launch_mode<MODE_RESID>(s, op, x, y, b, Dinv, omega, done);
+  else if (mode == MODE_CHEB0)  // the first sweep from x = 0 fused into the second step
+    launch_mode<MODE_CHEB, XF_JAC0>(s, op, nullptr, y, b, Dinv, omega, done, ch);
+  else if (mode == MODE_CHEB && ch && ch->xc)  // the prolongation fused into the first step
+    launch_mode<MODE_CHEB, XF_PROL>(s, op, x, y, b, Dinv, omega, done, ch);
   else if (mode == MODE_CHEB) launch_mode<MODE_CHEB>(s, op, x, y, b, Dinv, omega, done, ch);
   else launch_mode<MODE_JACOBI>(s, op, x, y, b, Dinv, omega, done);
 }

@@ -21,18 +21,32 @@ __device__ __forceinline__ double w1(int p, int I, int nf) {
   return 0.5;
 }
 
+// the same weight in FP32 (1, 1/2 or 0: products of three are exact in FP32, so the transfer
+// kernels form their weights without FP64 instructions, with the same values)
+__device__ __forceinline__ float w1f(int p, int I, int nf) {
+  const int pI = min(2 * I, nf);
+  if (p == pI) return 1.f;
+  const int d = p - pI;
+  if (d != 1 && d != -1) return 0.f;
+  if ((p & 1) == 0 || p == nf) return 0.f;
+  return 0.5f;
+}
+
 template <int DIM>
 __device__ __forceinline__ bool in_grid(int i, int j, int k, int nx, int ny, int nz) {
   return i >= 0 && i <= nx && j >= 0 && j <= ny && (DIM == 2 || (k >= 0 && k <= nz));
 }
 
-template <class T, int DIM, int MODE>
+// PROL (MODE_CHEB, dmode 0): the step's iterate is x + P xc, the coarse correction xc (grid
+// cnx x cny x cnz) prolonged at every node read, with the prolongation kernel's own arithmetic
+template <class T, int DIM, int MODE, bool PROL = false>
 __global__ void __launch_bounds__(256) k_stencil(int nx, int ny, int nz, const T* __restrict__ S,
                                                  const T* __restrict__ x, T* __restrict__ y,
                                                  const T* __restrict__ b,
                                                  const T* __restrict__ Dinv, T omega,
                                                  const int* done, T* __restrict__ xo, T c1,
-                                                 int dmode, T w0) {
+                                                 int dmode, T w0, const T* __restrict__ xc,
+                                                 int cnx, int cny, int cnz) {
   constexpr int NO = (DIM == 3) ? 27 : 9, BB = DIM * DIM;
   // 2D: the node's stencil row (fixed during a solve) is fetched before the wait for the
   // producer of x and b; 3D rows (243 values) are read as they are used
@@ -47,6 +61,9 @@ __global__ void __launch_bounds__(256) k_stencil(int nx, int ny, int nz, const T
     y += vo;
     if (b) b += vo;
     if (xo) xo += vo;
+    if (PROL)
+      xc += (int64_t)blockIdx.y *
+            rhs_stride((int64_t)DIM * (cnx + 1) * (cny + 1) * (DIM == 3 ? cnz + 1 : 1));
   }
   T Sr[PRE ? NO * BB : 1];
   if (PRE) {
@@ -57,6 +74,15 @@ __global__ void __launch_bounds__(256) k_stencil(int nx, int ny, int nz, const T
   if (solve_done(done)) return;
   int i, j, k;
   node_ijk(node, nx, ny, DIM, i, j, k);
+  AxisP pa[3][3];  // PROL: coarse partners of fine positions i-1..i+1 (and j, k) per axis
+  if (PROL) {
+#pragma unroll
+    for (int d = 0; d < 3; d++) {
+      pa[0][d] = axis_partners(i - 1 + d, nx);
+      pa[1][d] = axis_partners(j - 1 + d, ny);
+      pa[2][d] = DIM == 3 ? axis_partners(k - 1 + d, nz) : AxisP{1, {0, 0}, {1.f, 0.f}};
+    }
+  }
   T acc[DIM];
 #pragma unroll
   for (int c = 0; c < DIM; c++) acc[c] = T(0);
@@ -73,6 +99,8 @@ __global__ void __launch_bounds__(256) k_stencil(int nx, int ny, int nz, const T
     } else {
 #pragma unroll
       for (int c = 0; c < DIM; c++) xv[c] = x[DIM * nb + c];
+      if (PROL)
+        prolong_acc<T, DIM>(pa[0][ox + 1], pa[1][oy + 1], pa[2][oz + 1], cnx, cny, xc, xv);
     }
 #pragma unroll
     for (int r = 0; r < DIM; r++)
@@ -103,6 +131,7 @@ __global__ void __launch_bounds__(256) k_stencil(int nx, int ny, int nz, const T
       r[c] = b[DIM * node + c] - acc[c];
       if (MODE == MODE_CHEB) xi[c] = x[DIM * node + c];
     }
+    if (MODE == MODE_CHEB && PROL) prolong_acc<T, DIM>(pa[0][1], pa[1][1], pa[2][1], cnx, cny, xc, xi);
     cheb_node<T, DIM>(node, r, xi, Dinv, c1, omega, MODE == MODE_CHEB0 ? 2 : dmode, xo, y);
   } else {
     T r[DIM];
@@ -321,18 +350,18 @@ __global__ void k_restrict(int fnx, int fny, int fnz, int cnx, int cny, int cnz,
   for (int dz = (DIM == 3 ? -1 : 0); dz <= (DIM == 3 ? 1 : 0); dz++) {
     const int z = pz + dz;
     if (DIM == 3 && (z < 0 || z > fnz)) continue;
-    const double wz = (DIM == 3) ? w1(z, Iz, fnz) : 1.0;
-    if (wz == 0.0) continue;
+    const float wz = (DIM == 3) ? w1f(z, Iz, fnz) : 1.f;
+    if (wz == 0.f) continue;
     for (int dy = -1; dy <= 1; dy++) {
       const int yy = py + dy;
       if (yy < 0 || yy > fny) continue;
-      const double wy = w1(yy, Iy, fny);
-      if (wy == 0.0) continue;
+      const float wy = w1f(yy, Iy, fny);
+      if (wy == 0.f) continue;
       for (int dx = -1; dx <= 1; dx++) {
         const int xx = px + dx;
         if (xx < 0 || xx > fnx) continue;
-        const double wx = w1(xx, Ix, fnx);
-        if (wx == 0.0) continue;
+        const float wx = w1f(xx, Ix, fnx);
+        if (wx == 0.f) continue;
         const T w = (T)(wx * wy * wz);
         const int64_t fi = node_id(xx, yy, z, fnx, fny);
 #pragma unroll
@@ -344,15 +373,6 @@ __global__ void k_restrict(int fnx, int fny, int fnz, int cnx, int cny, int cnz,
   for (int c = 0; c < DIM; c++) bc[DIM * I + c] = acc[c];
 }
 
-// coarse nodes interpolating fine position p along an axis: returns count (1 or 2)
-__device__ __forceinline__ int coarse_of(int p, int nf, int* I, double* w) {
-  const int nc = (nf + 1) / 2;
-  if (p == nf) { I[0] = nc; w[0] = 1.0; return 1; }
-  if ((p & 1) == 0) { I[0] = p / 2; w[0] = 1.0; return 1; }
-  I[0] = (p - 1) / 2; w[0] = 0.5;
-  I[1] = (p + 1) / 2; w[1] = 0.5;
-  return 2;
-}
 
 template <class T, int DIM>
 __global__ void k_prolong_add(int fnx, int fny, int fnz, int cnx, int cny, int cnz,
@@ -369,21 +389,10 @@ __global__ void k_prolong_add(int fnx, int fny, int fnz, int cnx, int cny, int c
   }
   int x, y, z;
   node_ijk(i, fnx, fny, DIM, x, y, z);
-  int Ix[2], Iy[2], Iz[2] = {0, 0};
-  double wx[2], wy[2], wz[2] = {1.0, 0.0};
-  const int nxs = coarse_of(x, fnx, Ix, wx), nys = coarse_of(y, fny, Iy, wy);
-  const int nzs = (DIM == 3) ? coarse_of(z, fnz, Iz, wz) : 1;
   T acc[DIM];
 #pragma unroll
   for (int c = 0; c < DIM; c++) acc[c] = xf[DIM * i + c];
-  for (int c3 = 0; c3 < nzs; c3++)
-    for (int b = 0; b < nys; b++)
-      for (int a = 0; a < nxs; a++) {
-        const T w = (T)(wx[a] * wy[b] * wz[c3]);
-        const int64_t I = node_id(Ix[a], Iy[b], Iz[c3], cnx, cny);
-#pragma unroll
-        for (int c = 0; c < DIM; c++) acc[c] += w * xc[DIM * I + c];
-      }
+  prolong_node<T, DIM>(x, y, z, fnx, fny, fnz, cnx, cny, xc, acc);
 #pragma unroll
   for (int c = 0; c < DIM; c++) xf[DIM * i + c] = acc[c];
 }
@@ -480,7 +489,18 @@ void stencil_op(cudaStream_t s, int mode, const Geo& g, const T* S, const T* x, 
   const T c1 = cheb ? (T)ch->c1 : T(0);
   const int dm = cheb ? ch->dmode : 0;
   const T w0 = cheb ? (T)ch->w0 : T(0);
-#define STN(D, M) LAUNCH((k_stencil<T, D, M>), grid, 256, 0, s, g.nx, g.ny, g.nz, S, x, y, b, Dinv, (T)omega, done, xo, c1, dm, w0)
+#define STN(D, M) LAUNCH((k_stencil<T, D, M>), grid, 256, 0, s, g.nx, g.ny, g.nz, S, x, y, b, Dinv, (T)omega, done, xo, c1, dm, w0, (const T*)nullptr, 0, 0, 0)
+  if (mode == MODE_CHEB && ch->xc) {  // the prolongation fused into the first post-smoothing step
+    if (ch->dmode != 0) TOMG_THROW(TOMG_E_INVALID, "fused prolongation on a later step");
+    const T* xc = static_cast<const T*>(ch->xc);
+    if (g.dim == 2)
+      LAUNCH((k_stencil<T, 2, MODE_CHEB, true>), grid, 256, 0, s, g.nx, g.ny, g.nz, S, x, y, b, Dinv,
+             (T)omega, done, xo, c1, dm, w0, xc, ch->cnx, ch->cny, ch->cnz);
+    else
+      LAUNCH((k_stencil<T, 3, MODE_CHEB, true>), grid, 256, 0, s, g.nx, g.ny, g.nz, S, x, y, b, Dinv,
+             (T)omega, done, xo, c1, dm, w0, xc, ch->cnx, ch->cny, ch->cnz);
+    return;
+  }
   if (g.dim == 2) {
     if (mode == MODE_APPLY) STN(2, MODE_APPLY);
     else if (mode == MODE_RESID) STN(2, MODE_RESID);

@@ -211,16 +211,12 @@ __global__ void k_jacobi0(int64_t nodes, const T* __restrict__ Dinv, const T* __
   for (int t = 0; t < B * B; t++) D[t] = Dinv[(int64_t)B * B * i + t];
   pdl_wait();
   if (solve_done(done)) return;
-  T bv[B];
+  T bv[B], xv[B];
 #pragma unroll
   for (int c = 0; c < B; c++) bv[c] = b[B * i + c];
+  jacobi_block<T, B>(D, bv, omega, xv);
 #pragma unroll
-  for (int r = 0; r < B; r++) {
-    T v = T(0);
-#pragma unroll
-    for (int c = 0; c < B; c++) v += D[r * B + c] * bv[c];
-    x[B * i + r] = omega * v;
-  }
+  for (int r = 0; r < B; r++) x[B * i + r] = xv[r];
 }
 
 // Flexible GMRES building blocks.  parts[k * gridDim.x + block] = partial of V_k . w over the
@@ -309,41 +305,69 @@ __device__ __forceinline__ double rsqrt_newton(double d) {
   return y;
 }
 
-__global__ void __launch_bounds__(NB * NB) k_potrf_diag(int n, int k0, double* A, double* Linv,
-                                                        int* fail) {
+// The diagonal block in shared memory, right-looking: at pivot k, column k of L and row k of
+// L_kk^-1 are scaled by 1 / sqrt(d_k), then the trailing lower triangle (s_ij -= l_ik l_jk) and
+// the rows of L_kk^-1 below k (x_ic -= l_ik x_kc) are updated.  The entries of each update are
+// packed onto consecutive threads (a table of the triangle's (row, column) offsets), so only
+// as many warps issue FP64 work as the step has entries, and the next pivot's 1 / sqrt is
+// taken by the thread that has just updated that diagonal entry: two block barriers per pivot.
+constexpr int TRI = NB * (NB - 1) / 2;  // entries of the largest trailing triangle (k = 0)
+__global__ void __launch_bounds__(512) k_potrf_diag(int n, int k0, double* A, double* Linv,
+                                                    int* fail) {
   __shared__ double s[NB][NB + 1];
-  // L_kk^-1, built alongside the factorisation: row r holds e_r - sum_{t<k} L[r][t] X[t][.] until
-  // step r scales it into row r of X = L^-1 (forward substitution in right-looking order, so the
-  // dependent chain is one FMA per pivot instead of one per entry of a row)
   __shared__ double li[NB][NB + 1];
   __shared__ double rdiag[NB];
-  const int tx = threadIdx.x, ty = threadIdx.y;
+  __shared__ unsigned char tri_r[TRI], tri_c[TRI];
+  const int t = threadIdx.x;
   const int kb = min(NB, n - k0);
-  s[ty][tx] = (ty < kb && tx < kb) ? A[(int64_t)(k0 + ty) * n + k0 + tx] : (ty == tx ? 1.0 : 0.0);
-  li[ty][tx] = ty == tx ? 1.0 : 0.0;
+  for (int e = t; e < NB * NB; e += blockDim.x) {
+    const int r = e / NB, c = e % NB;
+    s[r][c] = (r < kb && c < kb) ? A[(int64_t)(k0 + r) * n + k0 + c] : (r == c ? 1.0 : 0.0);
+    li[r][c] = r == c ? 1.0 : 0.0;
+  }
+  for (int u = t; u < TRI; u += blockDim.x) {  // u = r (r + 1) / 2 + c, 0 <= c <= r
+    int r = 0;
+    while ((r + 1) * (r + 2) / 2 <= u) r++;
+    tri_r[u] = (unsigned char)r;
+    tri_c[u] = (unsigned char)(u - r * (r + 1) / 2);
+  }
   __syncthreads();
-  // every pivot needs 1 / sqrt(d); everything else multiplies by it
-  for (int k = 0; k < NB; k++) {
-    if (tx == 0 && ty == 0) {
-      double d = s[k][k];
-      if (!(d > 0.0)) {
-        if (k < kb) atomicCAS(fail, 0, k0 + k + 1);
-        d = 1.0;
-      }
-      const double y = rsqrt_newton(d);
-      s[k][k] = d * y;  // sqrt(d)
-      rdiag[k] = y;
+  auto pivot = [&](int k) {
+    double d = s[k][k];
+    if (!(d > 0.0)) {
+      if (k < kb) atomicCAS(fail, 0, k0 + k + 1);
+      d = 1.0;
     }
+    const double y = rsqrt_newton(d);
+    s[k][k] = d * y;  // sqrt(d)
+    rdiag[k] = y;
+  };
+  if (t == 0) pivot(0);
+  __syncthreads();
+  for (int k = 0; k < NB; k++) {
+    const double y = rdiag[k];
+    if (t > k && t < NB) s[t][k] *= y;                     // column k of L
+    if (t >= NB && t - NB <= k && t < 2 * NB) li[k][t - NB] *= y;  // row k of L^-1
     __syncthreads();
-    if (tx == k && ty > k) s[ty][k] *= rdiag[k];    // column k of L
-    if (ty == k && tx <= k) li[k][tx] *= rdiag[k];  // row k of L^-1
-    __syncthreads();
-    if (ty > k && tx > k && tx <= ty) s[ty][tx] -= s[ty][k] * s[tx][k];
-    if (ty > k && tx <= k) li[ty][tx] -= s[ty][k] * li[k][tx];
+    const int m = (NB - 1 - k) * (NB - k) / 2;
+    if (t < m) {
+      const int i = k + 1 + tri_r[t], j = k + 1 + tri_c[t];
+      s[i][j] -= s[i][k] * s[j][k];
+    }
+    const int lc = (NB - 1 - k) * (k + 1);
+    for (int u = t; u < lc; u += blockDim.x) {
+      const int i = k + 1 + u / (k + 1), c = u % (k + 1);
+      li[i][c] -= s[i][k] * li[k][c];
+    }
+    // entry 0 of the trailing triangle is the next diagonal entry, just updated by thread 0
+    if (t == 0 && k + 1 < NB) pivot(k + 1);
     __syncthreads();
   }
-  if (ty < kb && tx < kb) A[(int64_t)(k0 + ty) * n + k0 + tx] = (tx <= ty) ? s[ty][tx] : 0.0;
-  Linv[ty * NB + tx] = li[ty][tx];
+  for (int e = t; e < NB * NB; e += blockDim.x) {
+    const int r = e / NB, c = e % NB;
+    if (r < kb && c < kb) A[(int64_t)(k0 + r) * n + k0 + c] = (c <= r) ? s[r][c] : 0.0;
+    Linv[e] = li[r][c];
+  }
 }
 
 // rows below the diagonal block: L_ik = A_ik L_kk^-T  (one row per threadIdx.y, NB columns)
@@ -571,7 +595,7 @@ int dense_spd_inverse(cudaStream_t s, int n, double* A, double* work) {
   for (int b = 0; b < nblk; b++) {
     const int k0 = b * NB;
     double* Lb = linv.p + (size_t)b * NB * NB;
-    LAUNCH(k_potrf_diag, 1, dim3(NB, NB), 0, s, n, k0, A, Lb, fail.p);
+    LAUNCH(k_potrf_diag, 1, 512, 0, s, n, k0, A, Lb, fail.p);
     const int rest = n - k0 - std::min(NB, n - k0);
     if (rest > 0) {
       LAUNCH(k_panel, ceil_div(rest, 8), dim3(NB, 8), 0, s, n, k0, A, Lb);

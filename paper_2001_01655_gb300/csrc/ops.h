@@ -26,6 +26,11 @@ struct ChebArg {
   double c2 = 0.0;    // the launchers take it through their omega argument
   int dmode = 0;
   double w0 = 0.0;    // MODE_CHEB0: weight of the first step
+  // MODE_CHEB, dmode 0, with xc set: the step's iterate is x + P xc, the coarse correction xc of
+  // the level below (grid cnx x cny x cnz) prolonged on the fly (the prolongation fused into the
+  // first post-smoothing step; x itself is not written back)
+  const void* xc = nullptr;
+  int cnx = 0, cny = 0, cnz = 0;
 };
 // operator families whose kernels implement MODE_CHEB0 (quad4 level 0, stencils, BSR levels)
 struct Scalars;
@@ -55,6 +60,12 @@ void ebe_op(cudaStream_t s, int mode, const Ebe& op, const T* x, T* y, const T* 
             const T* Dinv, double omega, const int* done, double* dot_partials,
             const ChebArg* ch = nullptr);
 int ebe_blocks(const Ebe& op);  // number of blocks (= number of dot partials) of ebe_op
+// whether ebe_op in precision T takes MODE_CHEB0 on hex8 and a fused prolongation (ChebArg::xc):
+// the FP32 tensor-core hex8 operator does
+template <class T>
+inline bool ebe_fuses_transfers(const Ebe& op) {
+  return op.dim == 3 && sizeof(T) == 4 && op.tc != 0;
+}
 // quad4 tiled implementation behind ebe_op (k_ebe2d.cu)
 template <class T, int MODE, bool DOT>
 void ebe2d_launch(cudaStream_t s, const Ebe& op, const T* x, T* y, const T* b, const T* Dinv,
@@ -205,14 +216,18 @@ struct SpgemmWork {
 void spgemm_counts(cudaStream_t s, const Bsr& A, const Bsr& B, int* counts, SpgemmWork& w);
 void spgemm_fill(cudaStream_t s, const Bsr& A, const Bsr& B, const int* rpC, int* ciC,
                  SpgemmWork& w);
+// sym: C is known to be symmetric with square blocks (a Galerkin product P^T (A P)): the few
+// long rows of the coarse products then compute each off-diagonal block pair once
 void spgemm_numeric(cudaStream_t s, const Bsr& A, const double* VA, const Bsr& B,
-                    const double* VB, const Bsr& C, double* VC);
+                    const double* VB, const Bsr& C, double* VC, bool sym = false);
 void cast_f64_f32(cudaStream_t s, const double* a, float* b, int64_t n);
 void cast_f32_f64(cudaStream_t s, const float* a, double* b, int64_t n);
 
 // ---------------- prefix sums --------------------------------------------------------
 // exclusive scan of n ints into out (n+1 entries; out[n] = total); returns total (syncs)
 int64_t exclusive_scan(cudaStream_t s, const int* in, int* out, int64_t n);
+// the same scan without reading the total back (no host synchronisation)
+void exclusive_scan_nosync(cudaStream_t s, const int* in, int* out, int64_t n);
 
 // ---------------- smoothed aggregation ------------------------------------------------
 void amg_strength_counts(cudaStream_t s, const Bsr& A, const double* V, double beta, int* counts);
@@ -225,7 +240,7 @@ int amg_mis2(cudaStream_t s, int n, const int* srp, const int* sci, int level, i
 int amg_aggregate(cudaStream_t s, int n, const int* srp, const int* sci, int level,
                   const int* state, int* agg, int* root_scan);
 // tentative prolongator: T as BSR (one block per aggregated node), Bc (n_agg*k x k)
-void amg_tentative(cudaStream_t s, int n_nodes, int b, int k, int n_agg, const int* agg,
+int64_t amg_tentative(cudaStream_t s, int n_nodes, int b, int k, int n_agg, const int* agg,
                    const double* B, int* Trp, int* Tci, double* TV, double* Bc);
 // spectral radius of D^-1 A by power iteration (FP64) on an assembled BSR level, in three
 // steps so that the launches can run on another stream than the allocation: amg_power_alloc

@@ -271,8 +271,11 @@ void vcycle(tomg_problem* P, Work& W, int l, const T* b, T* out, const int* done
     T* cur = x;
     T* nxt = out;
     int k = 1;
-    // quad4 level 0, stencil and BSR levels fuse x_1 = d_0 with the second step
-    const bool fuse = m >= 2 && (Lv.kind != KIND_EBE || P->dim == 2);
+    // quad4 level 0, stencil and BSR levels and the FP32 tensor-core hex8 operator fuse
+    // x_1 = d_0 with the second step
+    const bool ebe_fuses = Lv.kind == KIND_EBE && ebe_fuses_transfers<T>(V<T>::ebe(P));
+    const bool fuse = m >= 2 && (Lv.kind != KIND_EBE || P->dim == 2 ||
+                                 (ebe_fuses && P->opt.fuse_transfers));
     if (fuse) {
       ChebArg ch;
       ch.d = r; ch.c1 = Lv.cheb_c1[1]; ch.c2 = Lv.cheb_c2[1]; ch.dmode = 2; ch.w0 = Lv.cheb_c2[0];
@@ -292,10 +295,21 @@ void vcycle(tomg_problem* P, Work& W, int l, const T* b, T* out, const int* done
     LevelWork& cw = W.lw[l + 1];
     restrict_to<T>(P, s, l, r, V<T>::b(cw), done);
     vcycle<T>(P, W, l + 1, V<T>::b(cw), V<T>::y(cw), done);
-    prolong_add<T>(P, s, l, V<T>::y(cw), cur, done);
+    // the coarse correction: its own pass, or (geometric transfer into a 3^d stencil level or
+    // the FP32 tensor-core hex8 operator) prolonged inside the first post-smoothing step
+    const bool fuse_prol = P->opt.fuse_transfers && Lv.geo_next &&
+                           (Lv.kind == KIND_STENCIL || ebe_fuses);
+    if (!fuse_prol) prolong_add<T>(P, s, l, V<T>::y(cw), cur, done);
     for (int k = 0; k < m; k++) {
       ChebArg ch;
       ch.d = r; ch.c1 = Lv.cheb_c1[k]; ch.c2 = Lv.cheb_c2[k]; ch.dmode = k == 0 ? 0 : 1;
+      if (k == 0 && fuse_prol) {
+        const Level& C = *P->L[l + 1];
+        ch.xc = V<T>::y(cw);
+        ch.cnx = C.g.nx;
+        ch.cny = C.g.ny;
+        ch.cnz = C.g.nz;
+      }
       level_op<T>(P, s, l, MODE_CHEB, cur, nxt, b, done, &ch);
       std::swap(cur, nxt);
     }
@@ -498,7 +512,7 @@ struct OwnedBsr {
 };
 
 void spgemm_full(cudaStream_t s, const Bsr& A, const double* VA, const Bsr& B, const double* VB,
-                 OwnedBsr& C) {
+                 OwnedBsr& C, bool sym = false) {
   DBuf<int> counts;
   counts.resize(A.nbr > 0 ? A.nbr : 1);
   C.rp.resize(A.nbr + 1);
@@ -513,8 +527,7 @@ void spgemm_full(cudaStream_t s, const Bsr& A, const double* VA, const Bsr& B, c
   C.m.nbr = A.nbr; C.m.nbc = B.nbc; C.m.br = A.br; C.m.bc = B.bc; C.m.nnzb = nnz;
   C.m.rp = C.rp.p; C.m.ci = C.ci.p;
   C.V.resize(std::max<int64_t>(1, nnz * A.br * B.bc));
-  spgemm_numeric(s, A, VA, B, VB, C.m, C.V.p);
-  CK(cudaStreamSynchronize(s));
+  spgemm_numeric(s, A, VA, B, VB, C.m, C.V.p, sym);
   tr.mark("  spgemm numeric");
 }
 
@@ -553,7 +566,7 @@ void amg_extend(tomg_problem* P, int start) {
     CK(cudaMemcpyAsync(dz.p, zs.data(), zs.size() * 8, cudaMemcpyHostToDevice, s));
     B.resize(S0.n * k);
     rigid_body_modes(s, S0.g, dx.p, dy.p, dz.p, B.p);
-    CK(cudaStreamSynchronize(s));
+    // (xs, ys, zs are pageable: each copy has read them before cudaMemcpyAsync returned)
   }
   tr.mark("bsr+rbm", start);
   int cur = start;
@@ -596,10 +609,7 @@ void amg_extend(tomg_problem* P, int start) {
     DBuf<int> Trp, Tci;
     DBuf<double> TV, Bc;
     Trp.resize(nn + 1); Tci.resize(nn); TV.resize((int64_t)nn * b * k); Bc.resize((int64_t)n_agg * k * k);
-    amg_tentative(s, nn, b, k, n_agg, agg.p, B.p, Trp.p, Tci.p, TV.p, Bc.p);
-    int nT = 0;
-    CK(cudaMemcpyAsync(&nT, Trp.p + nn, sizeof(int), cudaMemcpyDeviceToHost, s));
-    CK(cudaStreamSynchronize(s));
+    const int nT = (int)amg_tentative(s, nn, b, k, n_agg, agg.p, B.p, Trp.p, Tci.p, TV.p, Bc.p);
     Bsr Tm;
     Tm.nbr = nn; Tm.nbc = n_agg; Tm.br = b; Tm.bc = k; Tm.nnzb = nT; Tm.rp = Trp.p; Tm.ci = Tci.p;
     tr.mark("tentative", cur);
@@ -626,7 +636,7 @@ void amg_extend(tomg_problem* P, int start) {
       cnt.resize(n_agg); cursor.resize(n_agg);
       bsr_col_counts(s, Pm, cnt.p);
       A.Rrp.resize(n_agg + 1);
-      exclusive_scan(s, cnt.p, A.Rrp.p, n_agg);
+      exclusive_scan_nosync(s, cnt.p, A.Rrp.p, n_agg);
       A.Rci.resize(std::max<int64_t>(1, A.Pnnzb));
       A.Rv64.resize(std::max<int64_t>(1, A.Pnnzb * b * k));
       bsr_transpose_fill(s, Pm, A.Pv64.p, A.Rrp.p, A.Rci.p, A.Rv64.p, cursor.p);
@@ -636,7 +646,7 @@ void amg_extend(tomg_problem* P, int start) {
     OwnedBsr AP, Ac;
     spgemm_full(s, Ab, A.V64.p, Pm, A.Pv64.p, AP);
     tr.mark("A*P", cur);
-    spgemm_full(s, A.Rmat(n_agg), A.Rv64.p, AP.m, AP.V.p, Ac);
+    spgemm_full(s, A.Rmat(n_agg), A.Rv64.p, AP.m, AP.V.p, Ac, true);
     tr.mark("R*(AP)", cur);
     amg_fix_zero_rows(s, Ac.m, Ac.V.p);
     A.Pv32.resize(A.Pv64.n); cast_f64_f32(s, A.Pv64.p, A.Pv32.p, A.Pv64.n);
@@ -662,7 +672,6 @@ void amg_extend(tomg_problem* P, int start) {
     P->L.push_back(std::move(C));
     B = std::move(Bc);
     cur++;
-    CK(cudaStreamSynchronize(s));
     tr.mark("coarse level", cur);
   }
 }

@@ -37,7 +37,7 @@ class Options(C.Structure):
                 ("adaptive_geo", C.c_int), ("adaptive_iters", C.c_int), ("adaptive_min_geo", C.c_int),
                 ("krylov", C.c_int), ("gmres_restart", C.c_int),
                 ("gmres_steps", C.c_int), ("block_rhs", C.c_int),
-                ("fp64_tc", C.c_int)]
+                ("fp64_tc", C.c_int), ("fuse_transfers", C.c_int)]
 
 
 class Result(C.Structure):

@@ -135,3 +135,29 @@ def test_adaptive_hybrid_keeps_levels_below_limit(lib, ctx):
         _, res = P.solve(p.f)
         assert res[0]["iterations"] <= 200
     assert P.adaptive_geo_levels() == 3
+
+
+@pytest.mark.parametrize("dim,grid,prec,pc,kw", [
+    (3, (16, 8, 8), "tc", "hybrid", dict(n_geo_levels=3, max_coarse_dofs=200)),
+    (3, (13, 7, 9), "tc", "gmg", dict(n_levels=3)),     # odd axes: last coarse partners
+    (3, (12, 6, 6), "fp64", "gmg", dict(n_levels=3)),
+    (2, (64, 33, 1), "fp32", "gmg", dict(n_levels=4)),
+])
+@pytest.mark.parametrize("m", [1, 2, 3])
+def test_fused_transfers_bit_identical(lib, ctx, dim, grid, prec, pc, kw, m):
+    """Algorithm 1 with the prolongation computed inside the first post-smoothing step (and, on
+    the hex8 tensor-core level 0, the first step from x = 0 inside the second): the V-cycle and
+    the whole solve are bit-identical to the cycle with separate transfer launches."""
+    p = W.random_problem(dim, *grid, seed=41, contrast="minmax")
+    P = lib.Problem.from_workload(ctx, p)
+    r = np.random.default_rng(42).standard_normal(p.n)
+    out = []
+    for fuse in (0, 1):
+        P.setup(pc=pc, prec=prec, smoother="chebyshev", cheb_degree=m, fuse_transfers=fuse, **kw)
+        z = P.vcycle(r)
+        u, res = P.solve(p.f)
+        out.append((z, u, res[0]["iterations"], res[0]["status"]))
+    (z0, u0, i0, s0), (z1, u1, i1, s1) = out
+    assert s0 == 0 and s1 == 0
+    assert np.array_equal(z0, z1)
+    assert i0 == i1 and np.array_equal(u0, u1)
