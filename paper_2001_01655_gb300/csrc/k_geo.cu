@@ -47,10 +47,14 @@ __global__ void __launch_bounds__(256) k_stencil(int nx, int ny, int nz, const T
                                                  const int* done, T* __restrict__ xo, T c1,
                                                  int dmode, T w0, const T* __restrict__ xc,
                                                  int cnx, int cny, int cnz) {
-  constexpr int NO = (DIM == 3) ? 27 : 9, BB = DIM * DIM;
+  constexpr int NO = (DIM == 3) ? 27 : 9, BB = DIM * DIM, C0 = NO / 2;
   // 2D: the node's stencil row (fixed during a solve) is fetched before the wait for the
   // producer of x and b; 3D rows (243 values) are read as they are used
   constexpr bool PRE = DIM == 2;
+  // FP32 stencils are stored as their upper half (the centre and the offsets after it): the
+  // block of offset o < centre is the transpose of the neighbour's block of offset NO - 1 - o
+  // (the Galerkin operators are symmetric), read at the neighbour.  Half the bytes per apply.
+  constexpr bool HALF = sizeof(T) == 4;
   pdl_launch();
   const int64_t nn = (int64_t)(nx + 1) * (ny + 1) * (DIM == 3 ? nz + 1 : 1);
   const int64_t node = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
@@ -65,15 +69,27 @@ __global__ void __launch_bounds__(256) k_stencil(int nx, int ny, int nz, const T
       xc += (int64_t)blockIdx.y *
             rhs_stride((int64_t)DIM * (cnx + 1) * (cny + 1) * (DIM == 3 ? cnz + 1 : 1));
   }
+  int i, j, k;
+  node_ijk(node, nx, ny, DIM, i, j, k);
+  // entry (r, c) of the block of offset o (neighbour nb)
+  auto sval = [&](int o, int r, int c, int64_t nb) -> T {
+    if (!HALF) return S[((int64_t)o * BB + r * DIM + c) * nn + node];
+    if (o >= C0) return S[((int64_t)(o - C0) * BB + r * DIM + c) * nn + node];
+    return S[((int64_t)(NO - 1 - o - C0) * BB + c * DIM + r) * nn + nb];
+  };
   T Sr[PRE ? NO * BB : 1];
   if (PRE) {
 #pragma unroll
-    for (int t = 0; t < NO * BB; t++) Sr[t] = S[(int64_t)t * nn + node];
+    for (int o = 0; o < NO; o++) {
+      const int ox = o % 3 - 1, oy = (o / 3) % 3 - 1, oz = (DIM == 3) ? o / 9 - 1 : 0;
+      const bool in = in_grid<DIM>(i + ox, j + oy, k + oz, nx, ny, nz);
+      const int64_t nb = in ? node_id(i + ox, j + oy, k + oz, nx, ny) : node;
+#pragma unroll
+      for (int t = 0; t < BB; t++) Sr[o * BB + t] = in ? sval(o, t / DIM, t % DIM, nb) : T(0);
+    }
   }
   pdl_wait();
   if (solve_done(done)) return;
-  int i, j, k;
-  node_ijk(node, nx, ny, DIM, i, j, k);
   AxisP pa[3][3];  // PROL: coarse partners of fine positions i-1..i+1 (and j, k) per axis
   if (PROL) {
 #pragma unroll
@@ -106,8 +122,7 @@ __global__ void __launch_bounds__(256) k_stencil(int nx, int ny, int nz, const T
     for (int r = 0; r < DIM; r++)
 #pragma unroll
       for (int c = 0; c < DIM; c++)
-        acc[r] += (PRE ? Sr[PRE ? o * BB + r * DIM + c : 0]
-                       : S[((int64_t)o * BB + r * DIM + c) * nn + node]) * xv[c];
+        acc[r] += (PRE ? Sr[PRE ? o * BB + r * DIM + c : 0] : sval(o, r, c, nb)) * xv[c];
   }
   if (MODE == MODE_RESID0) {
     T xi[DIM];

@@ -873,8 +873,12 @@ void setup(tomg_problem* P, const tomg_options& opt) {
         C->S64.resize((int64_t)stencil_q(P->dim) * C->nn);
         stencil_rap(s, F.g, C->g, F.S64.p, C->S64.p);
       }
-      C->S32.resize(C->S64.n);
-      cast_f64_f32(s, C->S64.p, C->S32.p, C->S64.n);
+      {  // FP32 copy of the upper half for the V-cycle (the centre and the offsets after it)
+        const int no = P->dim == 3 ? 27 : 9, bb = P->dim * P->dim;
+        const int64_t off = (int64_t)(no / 2) * bb * C->nn, len = C->S64.n - off;
+        C->S32.resize(len);
+        cast_f64_f32(s, C->S64.p + off, C->S32.p, len);
+      }
       C->D64.resize(C->nn * P->dim * P->dim);
       C->D32.resize(C->nn * P->dim * P->dim);
       stencil_block_diag_inv(s, C->g, C->S64.p, C->D64.p, C->D32.p);

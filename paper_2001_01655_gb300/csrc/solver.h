@@ -33,7 +33,7 @@ struct Level {
   bool geo_next = false;  // transfer to the next level is geometric
   // structured stencil (geometric levels >= 1; level 0 during setup)
   DBuf<double> S64;
-  DBuf<float> S32;
+  DBuf<float> S32;  // the upper half of S64 (centre and later offsets), for the FP32 V-cycle
   // block CSR (AMG levels; the level an AMG part starts from, during setup)
   DBuf<int> rp, ci;
   DBuf<double> V64;

@@ -239,10 +239,16 @@ class Problem:
         _check(load().tomg_setup(self.h, C.byref(o)))
         self.opt = o
 
-    def solve(self, f, u0=None):
-        """Solve for right-hand sides f: numpy (nrhs, n) / (n,) on the host, or a CUDA tensor of
-        the same shape (device path).  Returns (u, [result dicts]); u has f's shape and kind."""
-        if _is_torch(f):
+    def solve(self, f, u0=None, out=None):
+        """Solve for right-hand sides f: numpy (nrhs, n) / (n,) on the host, or a torch tensor of
+        the same shape (on the device, or on the host, e.g. in pinned memory).  Returns
+        (u, [result dicts]); u has f's shape and kind.  With out (a contiguous float64 tensor or
+        array of f's shape and kind) the solve starts from out and writes u into it, with no
+        copy on the Python side (pinned host buffers stay pinned)."""
+        if out is not None:
+            nrhs = 1 if len(tuple(out.shape)) == 1 else out.shape[0]
+            u = out
+        elif _is_torch(f):
             import torch
             nrhs = 1 if f.dim() == 1 else f.shape[0]
             u = torch.zeros_like(f) if u0 is None else u0.clone().contiguous()
@@ -251,7 +257,9 @@ class Problem:
             nrhs = 1 if f.ndim == 1 else f.shape[0]
             u = np.zeros_like(f) if u0 is None else np.array(u0, dtype=np.float64, copy=True)
         fp, dev, keepf = _ptr(f, np.float64)
-        up, _, keepu = _ptr(u, np.float64)
+        up, udev, keepu = _ptr(u, np.float64)
+        if out is not None and (udev != dev or keepu is not u):
+            raise TypeError("out must be a contiguous float64 buffer on the same side as f")
         res = (Result * max(nrhs, 1))()
         st = load().tomg_solve(self.h, nrhs, fp, up, dev, res)
         _check(st)

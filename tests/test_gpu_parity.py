@@ -294,3 +294,21 @@ def test_graph_modes_identical(lib, ctx, use_graph):
     assert r0[0]["iterations"] == r1[0]["iterations"]
     assert np.array_equal(u0, u1)  # deterministic reductions: bit-identical
 
+
+
+def test_solve_into_pinned_host_buffer(lib, ctx):
+    """The host path with pinned buffers (f and an out buffer that is the initial guess and
+    receives u in place) gives the same solve as numpy arrays."""
+    torch = pytest.importorskip("torch")
+    p = W.cantilever_3d(16, 8, 8, seed=0, sigma=2.0)
+    P = make(lib, ctx, p)
+    P.setup(pc="hybrid", n_geo_levels=2, max_coarse_dofs=300, prec="tc", smoother="chebyshev")
+    u_np, r_np = P.solve(p.f[0])
+    f_h = torch.tensor(p.f[0], dtype=torch.float64).pin_memory()
+    u_h = torch.zeros_like(f_h).pin_memory()
+    ret, r_h = P.solve(f_h, out=u_h)
+    assert ret is u_h and u_h.is_pinned()
+    assert r_h[0]["iterations"] == r_np[0]["iterations"]
+    assert np.array_equal(u_h.numpy(), u_np)
+    with pytest.raises(TypeError):
+        P.solve(f_h, out=torch.zeros(p.n, dtype=torch.float32))
