@@ -10,8 +10,9 @@
 //     p K_l + q K_m an integer matrix (K_l, K_m the 72-scaled parts; entries of C up to 88,
 //     absolute row sums up to 472) and c = mu / (72 q);
 //   * each element row x_e (24 values) is written in fixed point on its largest exponent:
-//     X_j = round(x_j 2^(52 - e)) with |X_j| <= 2^53, and cut into five digits of 11 bits, four
-//     unsigned (0..2047) and a signed top one; every digit is an exact FP16 value;
+//     X_j = round(x_j 2^(52 - e)) with |X_j| <= 2^53, and |X_j| is cut into five digits of 11
+//     bits that carry the sign of X_j (sign-magnitude, in [-2047, 2047]); every digit is an
+//     exact FP16 value;
 //   * one MMA chain per digit (K = 24 padded to 32, N = 24 outputs padded to 32) accumulates
 //     sum_j C_oj d_j in FP32 exactly (|sum| < 2^20);
 //   * the digit sums are turned back into integers and combined in int64: Z_o = sum_j C_oj X_j
@@ -44,9 +45,11 @@ namespace {
 constexpr int TEX = 32, TY = 4;              // elements of a layer tile in x and y
 constexpr int TNX = TEX + 1, TNY = TY + 1;   // nodes of a layer tile
 constexpr int ONX = TEX - 1, ONY = TY - 1;   // owned nodes per layer
-constexpr int NT = TEX * TY;                 // 128 threads, one element each
+constexpr int ROWS = TEX * TY;               // 128 element rows: the tensor-memory lanes
+constexpr int NT = 2 * ROWS;                 // two threads per element row (bottom, top half)
 constexpr int LAYER_NODES = TNX * TNY;       // 165
 constexpr int KD = 24;                       // element DOFs
+constexpr int KH = KD / 2;                   // DOFs (inputs and outputs) of one half
 constexpr int ND = 5;                        // digits of 11 bits
 constexpr int NB = 32;                       // N: 24 outputs padded
 constexpr int KP = 32;                       // K per digit: 24 padded
@@ -58,12 +61,14 @@ constexpr int PS = 7;                        // staged y-pair partials: row stri
 constexpr int OFF_B = 0;
 constexpr int OFF_X = OFF_B + B_BYTES;                         // x ring, FP64
 constexpr int OFF_P = OFF_X + 2 * LAYER_NODES * 3 * 8;         // y pairs, FP64
-constexpr int OFF_R = OFF_P + 2 * NT * PS * 8;                 // reduction scratch
+constexpr int OFF_T = OFF_P + 2 * ROWS * PS * 8;               // top-half node sums, FP64
+constexpr int OFF_R = OFF_T + 2 * ROWS * 3 * 8;                // reduction scratch
 constexpr int OFF_BAR = OFF_R + 32 * 8;                        // mbarrier, TMEM address
 constexpr int SMEM_ALLOC = OFF_BAR + 16 + 128;
 static_assert(ACC_COL >= ND * KP / 2 && ACC_COL + ND * NB <= TMEM_COLS, "tensor memory map");
-static_assert(OFF_X % 16 == 0 && OFF_P % 16 == 0 && OFF_BAR % 8 == 0, "alignment");
-static_assert(LAYER_NODES <= 2 * NT, "two nodes per thread stage a layer");
+static_assert(OFF_X % 16 == 0 && OFF_P % 16 == 0 && OFF_T % 16 == 0 && OFF_BAR % 8 == 0,
+              "alignment");
+static_assert(LAYER_NODES <= NT, "one node per thread stages a layer");
 
 // kind::f16, D FP32, A and B FP16, K-major, N = 32, M = 128
 constexpr uint32_t IDESC = (1u << 4) | ((uint32_t)(NB >> 3) << 17) | ((uint32_t)(128 >> 4) << 24);
@@ -102,31 +107,52 @@ __device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity) {
     if (mbar_try(bar, parity)) return true;
   return false;
 }
-// 24 FP32 columns of this thread's lane
-__device__ __forceinline__ void tmem_ld24(uint32_t taddr, float* v) {
-  uint32_t r[24];
+// n FP32 columns of this thread's lane from column taddr (n = 8 or 4; no wait)
+__device__ __forceinline__ void tmem_ld8(uint32_t taddr, float* v) {
+  uint32_t r[8];
   asm volatile(
-      "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,"
-      "%14,%15}, [%24];\n\t"
-      "tcgen05.ld.sync.aligned.32x32b.x8.b32 {%16,%17,%18,%19,%20,%21,%22,%23}, [%25];\n\t"
-      "tcgen05.wait::ld.sync.aligned;\n"
+      "tcgen05.ld.sync.aligned.32x32b.x8.b32 {%0,%1,%2,%3,%4,%5,%6,%7}, [%8];\n"
       : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]),
-        "=r"(r[7]), "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]),
-        "=r"(r[14]), "=r"(r[15]), "=r"(r[16]), "=r"(r[17]), "=r"(r[18]), "=r"(r[19]),
-        "=r"(r[20]), "=r"(r[21]), "=r"(r[22]), "=r"(r[23])
-      : "r"(taddr), "r"(taddr + 16u)
+        "=r"(r[7])
+      : "r"(taddr)
       : "memory");
 #pragma unroll
-  for (int i = 0; i < 24; i++) v[i] = __uint_as_float(r[i]);
+  for (int i = 0; i < 8; i++) v[i] = __uint_as_float(r[i]);
 }
-// 16 32-bit columns of this thread's lane (no wait: the caller waits once for all stores)
-__device__ __forceinline__ void tmem_st16(uint32_t taddr, const uint32_t* v) {
+__device__ __forceinline__ void tmem_ld4(uint32_t taddr, float* v) {
+  uint32_t r[4];
+  asm volatile("tcgen05.ld.sync.aligned.32x32b.x4.b32 {%0,%1,%2,%3}, [%4];\n"
+               : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3])
+               : "r"(taddr)
+               : "memory");
+#pragma unroll
+  for (int i = 0; i < 4; i++) v[i] = __uint_as_float(r[i]);
+}
+// 12 FP32 columns of one half of the 24 outputs: half 0 columns 0-11 (x8 at 0, x4 at 8),
+// half 1 columns 12-23 (x4 at 12, x8 at 16); every access aligned to its width
+__device__ __forceinline__ void tmem_ld12(uint32_t taddr, int h, float* v) {
+  if (h == 0) {
+    tmem_ld8(taddr, v);
+    tmem_ld4(taddr + 8u, v + 8);
+  } else {
+    tmem_ld4(taddr + 12u, v);
+    tmem_ld8(taddr + 16u, v + 4);
+  }
+  asm volatile("tcgen05.wait::ld.sync.aligned;\n" ::: "memory");
+}
+__device__ __forceinline__ void tmem_st2(uint32_t taddr, const uint32_t* v) {
+  asm volatile("tcgen05.st.sync.aligned.32x32b.x2.b32 [%0], {%1,%2};\n"
+               :: "r"(taddr), "r"(v[0]), "r"(v[1]) : "memory");
+}
+__device__ __forceinline__ void tmem_st4(uint32_t taddr, const uint32_t* v) {
+  asm volatile("tcgen05.st.sync.aligned.32x32b.x4.b32 [%0], {%1,%2,%3,%4};\n"
+               :: "r"(taddr), "r"(v[0]), "r"(v[1]), "r"(v[2]), "r"(v[3]) : "memory");
+}
+__device__ __forceinline__ void tmem_st8(uint32_t taddr, const uint32_t* v) {
   asm volatile(
-      "tcgen05.st.sync.aligned.32x32b.x16.b32 [%0], {%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,"
-      "%13,%14,%15,%16};\n"
+      "tcgen05.st.sync.aligned.32x32b.x8.b32 [%0], {%1,%2,%3,%4,%5,%6,%7,%8};\n"
       :: "r"(taddr), "r"(v[0]), "r"(v[1]), "r"(v[2]), "r"(v[3]), "r"(v[4]), "r"(v[5]),
-         "r"(v[6]), "r"(v[7]), "r"(v[8]), "r"(v[9]), "r"(v[10]), "r"(v[11]), "r"(v[12]),
-         "r"(v[13]), "r"(v[14]), "r"(v[15])
+         "r"(v[6]), "r"(v[7])
       : "memory");
 }
 
@@ -139,94 +165,99 @@ __device__ __forceinline__ int f32_to_int(float f) {
   return __float_as_int(f + 12582912.0f) - 0x4B400000;
 }
 
-// node layer kk of the tile (FP64): values and mask bits of up to two nodes per thread
+// node layer kk of the tile (FP64): values and mask bits of one node per thread
 struct XPre {
-  double v[2][3];
-  unsigned m[2];
+  double v[3];
+  unsigned m;
 };
 __device__ __forceinline__ void x_fetch(XPre& p, int kk, int EX0, int EY0, int nx, int ny, int nz,
                                         const uint8_t* __restrict__ mask,
                                         const double* __restrict__ x) {
+  const int q = threadIdx.x;
+  p.v[0] = p.v[1] = p.v[2] = 0.0;
+  p.m = 7u;
+  if (q < LAYER_NODES) {
+    const int gi = EX0 + q % TNX, gj = EY0 + q / TNX;
+    if (gi >= 0 && gi <= nx && gj >= 0 && gj <= ny && kk >= 0 && kk <= nz) {
+      const int64_t node = node_id(gi, gj, kk, nx, ny);
+      p.m = __ldg(mask + node);
 #pragma unroll
-  for (int h = 0; h < 2; h++) {
-    const int q = threadIdx.x + h * NT;
-    p.v[h][0] = p.v[h][1] = p.v[h][2] = 0.0;
-    p.m[h] = 7u;
-    if (q < LAYER_NODES) {
-      const int gi = EX0 + q % TNX, gj = EY0 + q / TNX;
-      if (gi >= 0 && gi <= nx && gj >= 0 && gj <= ny && kk >= 0 && kk <= nz) {
-        const int64_t node = node_id(gi, gj, kk, nx, ny);
-        p.m[h] = __ldg(mask + node);
-#pragma unroll
-        for (int c = 0; c < 3; c++) p.v[h][c] = __ldg(x + 3 * node + c);
-      }
+      for (int c = 0; c < 3; c++) p.v[c] = __ldg(x + 3 * node + c);
     }
   }
 }
 __device__ __forceinline__ void x_store(const XPre& p, double* sx) {
+  const int q = threadIdx.x;
+  if (q < LAYER_NODES) {
 #pragma unroll
-  for (int h = 0; h < 2; h++) {
-    const int q = threadIdx.x + h * NT;
-    if (q < LAYER_NODES) {
-#pragma unroll
-      for (int c = 0; c < 3; c++) sx[3 * q + c] = ((p.m[h] >> c) & 1u) ? 0.0 : p.v[h][c];
-    }
+    for (int c = 0; c < 3; c++) sx[3 * q + c] = ((p.m >> c) & 1u) ? 0.0 : p.v[c];
   }
 }
-__device__ __forceinline__ double e_fetch(int ke, int EX0, int EY0, int nx, int ny, int nz,
-                                          const double* __restrict__ E) {
-  const int ge = EX0 + (int)(threadIdx.x % TEX), gf = EY0 + (int)(threadIdx.x / TEX);
+__device__ __forceinline__ double e_fetch(int ke, int ex, int ey, int EX0, int EY0, int nx, int ny,
+                                          int nz, const double* __restrict__ E) {
+  const int ge = EX0 + ex, gf = EY0 + ey;
   if (ge < 0 || ge >= nx || gf < 0 || gf >= ny || ke < 0 || ke >= nz) return 0.0;
   return __ldg(E + ge + (int64_t)nx * (gf + (int64_t)ny * ke));
 }
 
-// Element (ex, ey) of layer ke from the ring slots of node layers ke (s0) and ke + 1 (s1): the
-// five FP16 digit rows of its fixed-point values, written to tensor memory from column
-// taddr (digit q at taddr + 16 q: 12 words of digit pairs, lower K index in the low half, and 4
-// zero words of K padding).  Returns the biased FP64 exponent e of the row's largest entry
-// (the fixed point is X_j = round(x_j 2^(1075 - e)), |X_j| <= 2^53), or 0 for a row whose
-// entries are all below 2^-970 (written as zero digits).
+// input k (0..23) of element (ex, ey): DOF k % 3 of local node k / 3, from the ring slots of
+// node layers ke (s0: local nodes 0-3) and ke + 1 (s1: local nodes 4-7)
+__device__ __forceinline__ double elem_in(const double* s0, const double* s1, int ex, int ey, int k) {
+  const int bn = k / 3, c = k % 3;
+  const double* sx = (bn & 4) ? s1 : s0;
+  return sx[3 * ((ey + ((bn >> 1) & 1)) * TNX + ex + (bn & 1)) + c];
+}
+
+// Element (ex, ey) of layer ke, half h: the largest biased FP64 exponent e of the row's 24
+// entries (both halves find the same), then this half's 12 entries in fixed point on it,
+// X_j = round(x_j 2^(1075 - e)), |X_j| <= 2^53, cut into five FP16 digits of 11 bits and written
+// to tensor memory: digit q at taddr + 16 q holds 12 words of digit pairs (lower K index in the
+// low half) and 4 zero words of K padding; half 0 writes words 0-5, half 1 words 6-11 and the
+// padding.  Returns e, or 0 for a row whose entries are all below 2^-970 (zero digits).
 __device__ __forceinline__ int a_digits(uint32_t taddr, const double* s0, const double* s1,
-                                        int ex, int ey) {
-  uint64_t bits[KD];
+                                        int ex, int ey, int h) {
   int emax = 0;
 #pragma unroll
-  for (int k = 0; k < KD; k++) {
-    const int bn = k / 3, c = k % 3;
-    const double* sx = (bn & 4) ? s1 : s0;
-    bits[k] = __double_as_longlong(sx[3 * ((ey + ((bn >> 1) & 1)) * TNX + ex + (bn & 1)) + c]);
-    emax = max(emax, (int)((bits[k] >> 52) & 0x7FFu));
-  }
+  for (int k = 0; k < KD; k++)
+    emax = max(emax, (int)((__double_as_longlong(elem_in(s0, s1, ex, ey, k)) >> 52) & 0x7FF));
   if (emax < 53) emax = 0;
-  int64_t X[KD];
+  // |X_j| and its sign: every digit of |X_j| carries the sign of X_j (sign-magnitude digits in
+  // [-2047, 2047], each exact in FP16), so that sum_q 2^(11 q) d_q,j = X_j
+  uint64_t A[KH];
+  uint32_t sg[KH / 2];
 #pragma unroll
-  for (int k = 0; k < KD; k++) {
-    const int e = (int)((bits[k] >> 52) & 0x7FFu);
-    const uint64_t m = (bits[k] & 0xFFFFFFFFFFFFFull) | (e ? (1ull << 52) : 0ull);
+  for (int t = 0; t < KH; t++) {
+    const uint64_t bits = __double_as_longlong(elem_in(s0, s1, ex, ey, KH * h + t));
+    const int e = (int)((bits >> 52) & 0x7FFu);
+    const uint64_t m = (bits & 0xFFFFFFFFFFFFFull) | (e ? (1ull << 52) : 0ull);
     const int sh = emax - e;
     uint64_t a = 0;
     if (emax && sh <= 54) a = (m + ((1ull << sh) >> 1)) >> sh;  // round half up
-    X[k] = (bits[k] >> 63) ? -(int64_t)a : (int64_t)a;
+    A[t] = a;
+    const uint32_t neg = (uint32_t)(bits >> 63);
+    if (t & 1) sg[t / 2] |= neg << 31;
+    else sg[t / 2] = neg << 15;
   }
 #pragma unroll
   for (int q = 0; q < ND; q++) {
-    uint32_t w[16];
+    uint32_t w[8];
 #pragma unroll
-    for (int c = 0; c < KD / 2; c++) {
-      int d0, d1;
-      if (q < ND - 1) {
-        d0 = (int)((X[2 * c] >> (11 * q)) & 2047);
-        d1 = (int)((X[2 * c + 1] >> (11 * q)) & 2047);
-      } else {
-        d0 = (int)(X[2 * c] >> 44);  // signed top digit
-        d1 = (int)(X[2 * c + 1] >> 44);
-      }
-      const __half2 h = __floats2half2_rn(int_to_f32(d0), int_to_f32(d1));  // exact
-      w[c] = *reinterpret_cast<const uint32_t*>(&h);
+    for (int c = 0; c < KH / 2; c++) {
+      const int d0 = (int)((A[2 * c] >> (11 * q)) & 2047);
+      const int d1 = (int)((A[2 * c + 1] >> (11 * q)) & 2047);
+      const __half2 hv = __floats2half2_rn(int_to_f32(d0), int_to_f32(d1));  // exact
+      w[c] = *reinterpret_cast<const uint32_t*>(&hv) ^ sg[c];
     }
-#pragma unroll
-    for (int c = KD / 2; c < 16; c++) w[c] = 0u;
-    tmem_st16(taddr + (uint32_t)(16 * q), w);
+    const uint32_t col = taddr + (uint32_t)(16 * q);
+    if (h == 0) {  // words 0-5
+      tmem_st4(col, w);
+      tmem_st2(col + 4u, w + 4);
+    } else {  // words 6-11, then the padding words 12-15
+      tmem_st2(col + 6u, w);
+      w[0] = w[2]; w[1] = w[3]; w[2] = w[4]; w[3] = w[5];
+      w[4] = w[5] = w[6] = w[7] = 0u;
+      tmem_st8(col + 8u, w);
+    }
   }
   asm volatile("tcgen05.wait::st.sync.aligned;\n" ::: "memory");
   return emax;
@@ -245,24 +276,37 @@ __device__ __forceinline__ void issue_mmas(uint32_t tmem, uint32_t bbase, uint32
                :: "r"(bar) : "memory");
 }
 
-// this thread's element row of the previous layer: Z_o = sum_q D_q,o 2^(11 q) in int64 (exact),
-// then v_o = scale Z_o in FP64, scale = E_e c 2^(p - 1075) (0 for a zero row or no element).
-// Measured against forming ec Z 2^(p - 1075) entirely with integer operations (a 64 x 64-bit
-// product and an assembled double, no FP64 instruction), this is faster: the kernel is bound by
-// instruction latency at its two blocks per SM, not by the FP64 pipe.
-__device__ __forceinline__ void fold_digits(uint32_t taddr, double scale, double* v) {
-  int64_t Z[KD];
+// this thread's half of its element row of the previous layer: Z_o = sum_q D_q,o 2^(11 q)
+// exactly, then v_o = scale Z_o in FP64, scale = E_e c 2^(p - 1075) (0 for a zero row or no
+// element).  Each digit sum D (an integer, |D| < 2^20, exact in FP32) is read as the bit
+// pattern of D + 1.5 x 2^23 (one FP32 add), and the five patterns are combined with 32 x 32-bit
+// wide multiply-adds modulo 2^64; the offsets they carry, 0x4B400000 (1 + 2^11 + ... + 2^44), are
+// removed by one subtraction.  The wrap-around cancels: Z itself fits in 64 bits.
+// Measured against converting Z with integer operations instead of the FP64 conversion, and
+// against forming ec Z 2^(p - 1075) entirely with integer operations: both slower.
+__device__ __forceinline__ void fold_digits(uint32_t taddr, int h, double scale, double* v) {
+  constexpr uint64_t MAGIC = 0x4B400000ull;
+  constexpr uint64_t OFFSET = MAGIC * (1ull + (1ull << 11) + (1ull << 22) + (1ull << 33) +
+                                       (1ull << 44));
+  uint64_t lo[KH], hi[KH];  // digits 0-2 and 3-4
 #pragma unroll
-  for (int o = 0; o < KD; o++) Z[o] = 0;
+  for (int q = 0; q < ND; q++) {
+    float d[KH];
+    tmem_ld12(taddr + (uint32_t)(ACC_COL + NB * q), h, d);
 #pragma unroll
-  for (int q = ND - 1; q >= 0; q--) {
-    float d[KD];
-    tmem_ld24(taddr + (uint32_t)(ACC_COL + NB * q), d);
-#pragma unroll
-    for (int o = 0; o < KD; o++) Z[o] = Z[o] * 2048 + f32_to_int(d[o]);
+    for (int o = 0; o < KH; o++) {
+      const uint64_t bq = __float_as_uint(d[o] + 12582912.0f);
+      if (q == 0) lo[o] = bq;
+      else if (q < 3) lo[o] += bq * (1ull << (11 * q));
+      else if (q == 3) hi[o] = bq;
+      else hi[o] += bq * (1ull << 11);
+    }
   }
 #pragma unroll
-  for (int o = 0; o < KD; o++) v[o] = scale * __ll2double_rn(Z[o]);
+  for (int o = 0; o < KH; o++) {
+    const int64_t Z = (int64_t)(lo[o] + (hi[o] << 33) - OFFSET);
+    v[o] = scale * __ll2double_rn(Z);
+  }
 }
 
 struct Fin {
@@ -270,6 +314,12 @@ struct Fin {
   unsigned m;
 };
 
+// One block: a 32 x 4 element column of the grid, node layers [k0, k1); two threads per element
+// row (its tensor-memory lane): half 0 (warps 0-3) builds the digits of the row's bottom inputs
+// and folds its bottom outputs, half 1 (warps 4-7) the top ones, so that twice as many warps
+// hide the latency of the digit arithmetic.  A node layer's sum is the top sums of the element
+// layer below it (half 1, staged in shared memory) plus the bottom sums of the element layer
+// above it (half 0), which finishes the node.
 template <int MODE>
 __global__ void __launch_bounds__(NT, 2)
 k_ebe3x64(int nx, int ny, int nz, int nz_tile, int nzc, const uint4* __restrict__ Bimg,
@@ -296,12 +346,14 @@ k_ebe3x64(int nx, int ny, int nz, int nz_tile, int nzc, const uint4* __restrict_
   uint8_t* sm = smem_raw + ((128 - (smem_u32(smem_raw) & 127u)) & 127u);
   double* sxr = reinterpret_cast<double*>(sm + OFF_X);  // [2][LAYER_NODES][3]
   double* sP = reinterpret_cast<double*>(sm + OFF_P);   // [2][TY][TEX][PS]
+  double* sT = reinterpret_cast<double*>(sm + OFF_T);   // [2][ROWS][3]
   double* sred = reinterpret_cast<double*>(sm + OFF_R);
   uint64_t* bar = reinterpret_cast<uint64_t*>(sm + OFF_BAR);
   uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(sm + OFF_BAR + 8);
   const uint32_t sbase = smem_u32(sm), bar0 = smem_u32(bar);
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-  const int ex = lane, ey = warp;
+  const int h = tid / ROWS, r = tid % ROWS;  // half, element row
+  const int ex = lane, ey = (warp & 3);
   const int EX0 = blockIdx.x * ONX - 1, EY0 = blockIdx.y * ONY - 1;
   const int k0 = zc * nz_tile;
   const int k1 = min(k0 + nz_tile, nz + 1);  // owned node layers [k0, k1)
@@ -316,6 +368,7 @@ k_ebe3x64(int nx, int ny, int nz, int nz_tile, int nzc, const uint4* __restrict_
     asm volatile("fence.mbarrier_init.release.cluster;\n" ::: "memory");
   }
   for (int t = tid; t < B_BYTES / 16; t += NT) reinterpret_cast<uint4*>(sm + OFF_B)[t] = Bimg[t];
+  for (int t = tid; t < 2 * ROWS * 3; t += NT) sT[t] = 0.0;
 
   const bool owner = ex >= 1 && ey >= 1;
   const int gi = EX0 + ex, gj = EY0 + ey;
@@ -327,15 +380,14 @@ k_ebe3x64(int nx, int ny, int nz, int nz_tile, int nzc, const uint4* __restrict_
   x_store(pre, sxr + ((k0 - 1) & 1) * LAYER_NODES * 3);
   x_store(pre2, sxr + (k0 & 1) * LAYER_NODES * 3);
   x_fetch(pre, k0 + 1, EX0, EY0, nx, ny, nz, mask, x);
-  double ec_cur = c * e_fetch(k0 - 1, EX0, EY0, nx, ny, nz, E);  // E c of element layer ke
+  double ec_cur = c * e_fetch(k0 - 1, ex, ey, EX0, EY0, nx, ny, nz, E);  // E c of layer ke
   double sc_prev = 0.0;  // E c 2^(p - 1075) of this thread's row of layer ke - 1
   asm volatile("tcgen05.fence::before_thread_sync;\n" ::: "memory");
   __syncthreads();
   asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
   const uint32_t tmem = *tmem_slot;
-  const uint32_t lane_base = (uint32_t)(32 * warp) << 16;
+  const uint32_t lane_base = (uint32_t)(32 * (warp & 3)) << 16;
 
-  double acc[3] = {0.0, 0.0, 0.0};  // node layer ke - 1: contributions gathered so far
   Fin fd;
   fd.m = 7u;
   uint32_t parity = 0, pending = 0;
@@ -346,7 +398,7 @@ k_ebe3x64(int nx, int ny, int nz, int nz_tile, int nzc, const uint4* __restrict_
     const bool mma_now = ke < k1;
     const int j = ke & 1, jp = j ^ 1;
     bool ok = true;
-    double v[KD];
+    double v[KH];
     if (ke >= k0) {
       // the MMAs of layer ke - 1; the phase advances only on success (see the drain below)
       ok = mbar_wait(bar0, parity);
@@ -359,12 +411,12 @@ k_ebe3x64(int nx, int ny, int nz, int nz_tile, int nzc, const uint4* __restrict_
       ok = __all_sync(0xffffffffu, ok);
       asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
       // the accumulators are single-buffered: read before this layer's MMAs are issued
-      if (ok) fold_digits(tmem + lane_base, sc_prev, v);
+      if (ok) fold_digits(tmem + lane_base, h, sc_prev, v);
     }
     double sc_now = 0.0;
     if (ok && mma_now) {
       const int p = a_digits(tmem + lane_base + A_COL, sxr + j * LAYER_NODES * 3,
-                             sxr + jp * LAYER_NODES * 3, ex, ey);
+                             sxr + jp * LAYER_NODES * 3, ex, ey, h);
       if (p) sc_now = ec_cur * __longlong_as_double((long long)(p - 52) << 52);
     }
     asm volatile("tcgen05.fence::before_thread_sync;\n" ::: "memory");
@@ -380,10 +432,11 @@ k_ebe3x64(int nx, int ny, int nz, int nz_tile, int nzc, const uint4* __restrict_
       x_store(pre, sxr + j * LAYER_NODES * 3);
       if (ke + 3 <= k1) x_fetch(pre, ke + 3, EX0, EY0, nx, ny, nz, mask, x);
     }
-    const double ec_next = (ke + 1 < k1) ? c * e_fetch(ke + 1, EX0, EY0, nx, ny, nz, E) : 0.0;
+    const double ec_next =
+        (ke + 1 < k1) ? c * e_fetch(ke + 1, ex, ey, EX0, EY0, nx, ny, nz, E) : 0.0;
     Fin fd_next;
     fd_next.m = 7u;
-    if (in_plane && ke >= k0 && ke < k1) {
+    if (h == 0 && in_plane && ke >= k0 && ke < k1) {
       const int64_t node = node_id(gi, gj, ke, nx, ny);
       fd_next.m = __ldg(mask + node);
 #pragma unroll
@@ -393,51 +446,47 @@ k_ebe3x64(int nx, int ny, int nz, int nz_tile, int nzc, const uint4* __restrict_
         for (int q = 0; q < 3; q++) fd_next.b[q] = __ldg(b + 3 * node + q);
       }
     }
-    double pr[2][2][3];
+    double pr[2][3];  // x-pair sums of this half's node layer at node column ex: [dy][c]
     if (ke >= k0) {
 #pragma unroll
       for (int dy = 0; dy < 2; dy++)
 #pragma unroll
-        for (int dz = 0; dz < 2; dz++)
+        for (int q = 0; q < 3; q++) {
+          const double left = __shfl_up_sync(0xffffffffu, v[3 * (1 + 2 * dy) + q], 1);
+          pr[dy][q] = v[3 * (2 * dy) + q] + left;
+        }
+      double* myP = sP + (j * ROWS + ey * TEX + ex) * PS;
 #pragma unroll
-          for (int q = 0; q < 3; q++) {
-            const double left = __shfl_up_sync(0xffffffffu, v[3 * (1 + 2 * dy + 4 * dz) + q], 1);
-            pr[dy][dz][q] = v[3 * (2 * dy + 4 * dz) + q] + left;
-          }
-      double* myP = sP + (j * NT + ey * TEX + ex) * PS;
-#pragma unroll
-      for (int dz = 0; dz < 2; dz++)
-#pragma unroll
-        for (int q = 0; q < 3; q++) myP[3 * dz + q] = pr[1][dz][q];
+      for (int q = 0; q < 3; q++) myP[3 * h + q] = pr[1][q];
     }
     __syncthreads();
     if (ke >= k0 && owner) {
-      const int kn = ke - 1;
-      const double* upP = sP + (j * NT + (ey - 1) * TEX + ex) * PS;
-      double top[3];
+      const double* upP = sP + (j * ROWS + (ey - 1) * TEX + ex) * PS;
+      if (h == 1) {  // top sums of element layer ke - 1: node layer ke, finished next step
 #pragma unroll
-      for (int q = 0; q < 3; q++) {
-        acc[q] += upP[q] + pr[0][0][q];
-        top[q] = upP[3 + q] + pr[0][1][q];
-      }
-      if (in_plane && kn >= k0) {
-        const int64_t node = node_id(gi, gj, kn, nx, ny);
-        double Ax[3];
+        for (int q = 0; q < 3; q++) sT[(j * ROWS + r) * 3 + q] = upP[3 + q] + pr[0][q];
+      } else {  // node layer ke - 1: top sums of element layer ke - 2 plus bottom sums of ke - 1
+        const int kn = ke - 1;
+        double acc[3];
 #pragma unroll
-        for (int q = 0; q < 3; q++) Ax[q] = ((fd.m >> q) & 1u) ? fd.x[q] : acc[q];
-        if (MODE == MODE_APPLY) {
+        for (int q = 0; q < 3; q++) acc[q] = sT[(jp * ROWS + r) * 3 + q] + (upP[q] + pr[0][q]);
+        if (in_plane && kn >= k0) {
+          const int64_t node = node_id(gi, gj, kn, nx, ny);
+          double Ax[3];
 #pragma unroll
-          for (int q = 0; q < 3; q++) {
-            y[3 * node + q] = Ax[q];
-            dotv += fd.x[q] * Ax[q];
+          for (int q = 0; q < 3; q++) Ax[q] = ((fd.m >> q) & 1u) ? fd.x[q] : acc[q];
+          if (MODE == MODE_APPLY) {
+#pragma unroll
+            for (int q = 0; q < 3; q++) {
+              y[3 * node + q] = Ax[q];
+              dotv += fd.x[q] * Ax[q];
+            }
+          } else {
+#pragma unroll
+            for (int q = 0; q < 3; q++) y[3 * node + q] = fd.b[q] - Ax[q];
           }
-        } else {
-#pragma unroll
-          for (int q = 0; q < 3; q++) y[3 * node + q] = fd.b[q] - Ax[q];
         }
       }
-#pragma unroll
-      for (int q = 0; q < 3; q++) acc[q] = top[q];
     }
     sc_prev = sc_now;
     ec_cur = ec_next;
