@@ -734,8 +734,8 @@ def roofline(P, p, head, opts):
 # DRAM read + write bytes of one launch, from the ncu captures summarised under profiles/
 # (key: kernel role, dimension, DOFs); valid while the kernel is unchanged since its capture
 TRAFFIC = {
-    # k_ebe3x64 apply, 3D cantilever 192x96x96: 59.7 MB read + 10.7 MB write
-    ("outer", 3, 5447811): 70.4e6,
+    # k_ebe3x64 apply, 3D cantilever 192x96x96: 59.6 MB read + 11.5 MB write
+    ("outer", 3, 5447811): 71.1e6,
 }
 
 

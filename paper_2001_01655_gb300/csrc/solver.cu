@@ -822,9 +822,17 @@ void setup(tomg_problem* P, const tomg_options& opt) {
       P->ebe_tile = ebe2d_autotune(s, V<float>::ebe(P), L0->D32.p);
     if (P->dim == 3 && opt.prec == TOMG_PREC_TC_VCYCLE && P->tc_nz == 0 && P->Ketc.p) {
       TcScope tcs(P, TOMG_PREC_TC_VCYCLE);
-      const int code = ebe3d_tc_autotune(s, V<float>::ebe(P), L0->D32.p);
-      P->tc_nz = code % 1000;
+      // TOMG_TC_TILE = rows * 1000 + layers fixes the tile instead of timing the candidates
+      // (for profiler runs, under which the timed choice is not the one of a plain run)
+      const char* forced = getenv("TOMG_TC_TILE");
+      const int code = forced ? atoi(forced) : ebe3d_tc_autotune(s, V<float>::ebe(P), L0->D32.p);
+      if (code / 1000 != 8 && code / 1000 != 4)
+        TOMG_THROW(TOMG_E_INVALID, "TOMG_TC_TILE: rows 8 or 4 (rows * 1000 + layers)");
+      P->tc_nz = std::max(1, code % 1000);
       P->tc_ty = code / 1000;
+      if (getenv("TOMG_TRACE_SETUP"))
+        fprintf(stderr, "[setup] tensor-core tile: %d element rows, %d node layers\n", P->tc_ty,
+                P->tc_nz);
     }
     P->L.push_back(std::move(L0));
   }
