@@ -32,6 +32,21 @@ __device__ __forceinline__ float w1f(int p, int I, int nf) {
   return 0.5f;
 }
 
+// position of stored entry t (of he per node) of node i in an FP32 half stencil
+__host__ __device__ __forceinline__ int64_t half_index(int64_t i, int t, int he) {
+  return ((i >> 5) * he + t) * 32 + (i & 31);
+}
+
+// FP32 half stencil from the FP64 stencil: entries of the centre and the offsets after it
+__global__ void k_stencil_half(int64_t nn, int he, int64_t first, const double* __restrict__ S64,
+                               float* __restrict__ S32) {
+  const int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (e >= nn * he) return;
+  const int t = (int)(e / nn);
+  const int64_t i = e % nn;
+  S32[half_index(i, t, he)] = (float)S64[first + e];
+}
+
 template <int DIM>
 __device__ __forceinline__ bool in_grid(int i, int j, int k, int nx, int ny, int nz) {
   return i >= 0 && i <= nx && j >= 0 && j <= ny && (DIM == 2 || (k >= 0 && k <= nz));
@@ -54,7 +69,10 @@ __global__ void __launch_bounds__(256) k_stencil(int nx, int ny, int nz, const T
   // FP32 stencils are stored as their upper half (the centre and the offsets after it): the
   // block of offset o < centre is the transpose of the neighbour's block of offset NO - 1 - o
   // (the Galerkin operators are symmetric), read at the neighbour.  Half the bytes per apply.
+  // Layout: tiles of 32 nodes, entry-major inside a tile (half_index), so that the values of
+  // the 32 nodes of a warp are one contiguous run per entry and per tile.
   constexpr bool HALF = sizeof(T) == 4;
+  constexpr int HE = (NO - C0) * BB;  // stored entries per node
   pdl_launch();
   const int64_t nn = (int64_t)(nx + 1) * (ny + 1) * (DIM == 3 ? nz + 1 : 1);
   const int64_t node = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
@@ -74,8 +92,8 @@ __global__ void __launch_bounds__(256) k_stencil(int nx, int ny, int nz, const T
   // entry (r, c) of the block of offset o (neighbour nb)
   auto sval = [&](int o, int r, int c, int64_t nb) -> T {
     if (!HALF) return S[((int64_t)o * BB + r * DIM + c) * nn + node];
-    if (o >= C0) return S[((int64_t)(o - C0) * BB + r * DIM + c) * nn + node];
-    return S[((int64_t)(NO - 1 - o - C0) * BB + c * DIM + r) * nn + nb];
+    if (o >= C0) return S[half_index(node, (o - C0) * BB + r * DIM + c, HE)];
+    return S[half_index(nb, (NO - 1 - o - C0) * BB + c * DIM + r, HE)];
   };
   T Sr[PRE ? NO * BB : 1];
   if (PRE) {
@@ -540,6 +558,19 @@ template void stencil_op<double>(cudaStream_t, int, const Geo&, const double*, c
                                  const ChebArg*);
 
 int stencil_blocks(const Geo& g) { return ceil_div(g.nodes(), 256); }
+
+int64_t stencil_half_size(const Geo& g) {
+  const int no = g.dim == 3 ? 27 : 9, bb = g.dim * g.dim;
+  return (g.nodes() + 31) / 32 * 32 * (int64_t)(no - no / 2) * bb;
+}
+
+void stencil_half_f32(cudaStream_t s, const Geo& g, const double* S64, float* S32) {
+  const int no = g.dim == 3 ? 27 : 9, bb = g.dim * g.dim, he = (no - no / 2) * bb;
+  const int64_t nn = g.nodes();
+  CK(cudaMemsetAsync(S32, 0, sizeof(float) * stencil_half_size(g), s));  // tile padding
+  LAUNCH(k_stencil_half, ceil_div(nn * he, 256), 256, 0, s, nn, he, (int64_t)(no / 2) * bb * nn,
+         S64, S32);
+}
 
 void stencil_apply_dot(cudaStream_t s, const Geo& g, const double* S, const double* x, double* y,
                        const int* done, double* partials, Scalars* sc) {

@@ -167,6 +167,10 @@ void stencil_apply_dot(cudaStream_t s, const Geo& g, const double* S, const doub
 int stencil_blocks(const Geo& g);
 // Galerkin product with bilinear / trilinear P (coarse node I at fine position min(2I, n))
 void stencil_rap(cudaStream_t s, const Geo& fine, const Geo& coarse, const double* Sf, double* Sc);
+// the FP32 copy the V-cycle's stencil kernels read: the upper half of the FP64 stencil (the
+// centre and the offsets after it), in tiles of 32 nodes with the entries of a tile contiguous
+int64_t stencil_half_size(const Geo& g);
+void stencil_half_f32(cudaStream_t s, const Geo& g, const double* S64, float* S32);
 // hex8: the first coarse stencil P^T A_0 P straight from the level-0 elements (FP64 operator
 // op64, coarse grid c = the coarsening of op64's grid).  Returns false, writing nothing, when
 // more than one element in eight touches a fixed DOF (the caller then takes the product on the

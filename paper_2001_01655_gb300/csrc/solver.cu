@@ -271,11 +271,15 @@ void vcycle(tomg_problem* P, Work& W, int l, const T* b, T* out, const int* done
     T* cur = x;
     T* nxt = out;
     int k = 1;
-    // quad4 level 0, stencil and BSR levels and the FP32 tensor-core hex8 operator fuse
-    // x_1 = d_0 with the second step
+    // x_1 = d_0 fused with the second step on quad4 level 0 (its tiled kernel forms w0 Dinv b
+    // once per staged node), on 2D stencil levels (9 neighbours) and, with fuse_transfers, on
+    // the FP32 tensor-core hex8 operator.  3D stencil and BSR kernels would form it at every
+    // neighbour they read (27 and 30-60 per row): a separate sweep is cheaper there (measured
+    // on the 3D cantilever 192x96x96 and the 2D cantilever 768x384)
     const bool ebe_fuses = Lv.kind == KIND_EBE && ebe_fuses_transfers<T>(V<T>::ebe(P));
-    const bool fuse = m >= 2 && (Lv.kind != KIND_EBE || P->dim == 2 ||
-                                 (ebe_fuses && P->opt.fuse_transfers));
+    const bool fuse =
+        m >= 2 && (Lv.kind == KIND_EBE ? (P->dim == 2 || (ebe_fuses && P->opt.fuse_transfers))
+                                       : (Lv.kind == KIND_STENCIL && P->dim == 2));
     if (fuse) {
       ChebArg ch;
       ch.d = r; ch.c1 = Lv.cheb_c1[1]; ch.c2 = Lv.cheb_c2[1]; ch.dmode = 2; ch.w0 = Lv.cheb_c2[0];
@@ -881,12 +885,8 @@ void setup(tomg_problem* P, const tomg_options& opt) {
         C->S64.resize((int64_t)stencil_q(P->dim) * C->nn);
         stencil_rap(s, F.g, C->g, F.S64.p, C->S64.p);
       }
-      {  // FP32 copy of the upper half for the V-cycle (the centre and the offsets after it)
-        const int no = P->dim == 3 ? 27 : 9, bb = P->dim * P->dim;
-        const int64_t off = (int64_t)(no / 2) * bb * C->nn, len = C->S64.n - off;
-        C->S32.resize(len);
-        cast_f64_f32(s, C->S64.p + off, C->S32.p, len);
-      }
+      C->S32.resize(stencil_half_size(C->g));  // FP32 upper half for the V-cycle
+      stencil_half_f32(s, C->g, C->S64.p, C->S32.p);
       C->D64.resize(C->nn * P->dim * P->dim);
       C->D32.resize(C->nn * P->dim * P->dim);
       stencil_block_diag_inv(s, C->g, C->S64.p, C->D64.p, C->D32.p);
