@@ -279,7 +279,7 @@ __global__ void k_transpose_finish(int nbc, int br, int bc, const int* __restric
 }
 
 // ------------------------------- SpGEMM ------------------------------------------------
-constexpr int SPG_WARPS = 4;
+constexpr int SPG_WARPS = 2;
 constexpr int SPG_SMEM_T = 2048;
 
 __device__ __forceinline__ int next_pow2(int x) { return x <= 1 ? 1 : 1 << (32 - __clz(x - 1)); }
@@ -288,32 +288,42 @@ __device__ __forceinline__ int warp_sum_int(int v) {
   return v;
 }
 __device__ __forceinline__ unsigned hash_col(int key) { return (unsigned)key * 2654435761u; }
+// hash table size of a row of C: twice the bound on its distinct columns (products summed over
+// A's row, at most B's column count), a power of two; a row whose distinct columns cannot
+// exceed the shared-memory table uses that table even when the sum of products is larger
+// (linear probing ends: there are never more keys than slots)
+__device__ __forceinline__ int spg_table(int ub, int nbcB) {
+  const int lim = min(ub, nbcB);
+  int T = max(64, next_pow2(2 * lim));
+  if (T > SPG_SMEM_T && lim <= SPG_SMEM_T) T = SPG_SMEM_T;
+  return T;
+}
 
 // per-row hash table size when it does not fit in shared memory (0 otherwise)
 __global__ void k_spgemm_big(int nrows, const int* __restrict__ Arp, const int* __restrict__ Aci,
-                             const int* __restrict__ Brp, int* big) {
+                             const int* __restrict__ Brp, int nbcB, int* big) {
   const int row = blockIdx.x * blockDim.x + threadIdx.x;
   if (row >= nrows) return;
   int ub = 0;
   for (int a = Arp[row]; a < Arp[row + 1]; a++) ub += Brp[Aci[a] + 1] - Brp[Aci[a]];
-  const int T = max(64, next_pow2(2 * ub));
+  const int T = spg_table(ub, nbcB);
   big[row] = (T > SPG_SMEM_T) ? 2 * T : 0;  // table + compaction area
 }
 
 __global__ void __launch_bounds__(32 * SPG_WARPS)
     k_spgemm_sym(int nrows, const int* __restrict__ Arp, const int* __restrict__ Aci,
-                 const int* __restrict__ Brp, const int* __restrict__ Bci,
+                 const int* __restrict__ Brp, const int* __restrict__ Bci, int nbcB,
                  const int* __restrict__ goff, int* gtable, int* countsC,
                  const int* __restrict__ rpC, int* ciC) {
   __shared__ int tab[SPG_WARPS][SPG_SMEM_T];
-  __shared__ int cmp[SPG_WARPS][SPG_SMEM_T / 2];
+  __shared__ int cmp[SPG_WARPS][SPG_SMEM_T];
   const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int row = blockIdx.x * SPG_WARPS + w;
   if (row >= nrows) return;  // warp-uniform
   int ub = 0;
   for (int a = Arp[row] + lane; a < Arp[row + 1]; a += 32) ub += Brp[Aci[a] + 1] - Brp[Aci[a]];
   ub = warp_sum_int(ub);
-  const int T = max(64, next_pow2(2 * ub));
+  const int T = spg_table(ub, nbcB);
   int* table = (T <= SPG_SMEM_T) ? tab[w] : gtable + goff[row];
   for (int s = lane; s < T; s += 32) table[s] = -1;
   __syncwarp();
@@ -657,18 +667,18 @@ void bsr_transpose_fill(cudaStream_t s, const Bsr& A, const double* V, const int
 void spgemm_counts(cudaStream_t s, const Bsr& A, const Bsr& B, int* counts, SpgemmWork& w) {
   w.big.resize(A.nbr + 1);
   w.goff.resize(A.nbr + 1);
-  LAUNCH(k_spgemm_big, ceil_div(A.nbr, 256), 256, 0, s, A.nbr, A.rp, A.ci, B.rp, w.big.p);
+  LAUNCH(k_spgemm_big, ceil_div(A.nbr, 256), 256, 0, s, A.nbr, A.rp, A.ci, B.rp, B.nbc, w.big.p);
   const int64_t tot = exclusive_scan(s, w.big.p, w.goff.p, A.nbr);
   if (tot > 0x7fffffffLL) TOMG_THROW(TOMG_E_OOM, "SpGEMM hash tables too large (%lld)", (long long)tot);
   w.gtable.resize(tot > 0 ? tot : 1);
   LAUNCH(k_spgemm_sym, ceil_div(A.nbr, SPG_WARPS), 32 * SPG_WARPS, 0, s, A.nbr, A.rp, A.ci, B.rp,
-         B.ci, w.goff.p, w.gtable.p, counts, (const int*)nullptr, (int*)nullptr);
+         B.ci, B.nbc, w.goff.p, w.gtable.p, counts, (const int*)nullptr, (int*)nullptr);
 }
 
 void spgemm_fill(cudaStream_t s, const Bsr& A, const Bsr& B, const int* rpC, int* ciC,
                  SpgemmWork& w) {
   LAUNCH(k_spgemm_sym, ceil_div(A.nbr, SPG_WARPS), 32 * SPG_WARPS, 0, s, A.nbr, A.rp, A.ci, B.rp,
-         B.ci, w.goff.p, w.gtable.p, (int*)nullptr, rpC, ciC);
+         B.ci, B.nbc, w.goff.p, w.gtable.p, (int*)nullptr, rpC, ciC);
 }
 
 void spgemm_numeric(cudaStream_t s, const Bsr& A, const double* VA, const Bsr& B, const double* VB,
