@@ -213,15 +213,19 @@ __global__ void k_agg_scatter(int n, const int* __restrict__ agg, const int* __r
   const int a = agg[i];
   members[start[a] + atomicAdd(&cursor[a], 1)] = i;
 }
-__global__ void k_agg_sort(int n_agg, const int* __restrict__ start, int* members) {
-  const int a = blockIdx.x * blockDim.x + threadIdx.x;
+// the members of each aggregate in ascending node order: one warp per aggregate, each member
+// placed at its rank (the count of smaller members; node ids are distinct)
+__global__ void k_agg_sort(int n_agg, const int* __restrict__ start,
+                           const int* __restrict__ unsorted, int* members) {
+  const int a = (int)(((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5);
+  const int lane = threadIdx.x & 31;
   if (a >= n_agg) return;
   const int s = start[a], e = start[a + 1];
-  for (int p = s + 1; p < e; p++) {
-    const int v = members[p];
-    int q = p - 1;
-    while (q >= s && members[q] > v) { members[q + 1] = members[q]; q--; }
-    members[q + 1] = v;
+  for (int p = s + lane; p < e; p += 32) {
+    const int v = unsorted[p];
+    int rank = 0;
+    for (int q = s; q < e; q++) rank += unsorted[q] < v ? 1 : 0;
+    members[s + rank] = v;
   }
 }
 
@@ -234,6 +238,65 @@ __global__ void k_T_cols(int n, const int* __restrict__ agg, int* Tci, const int
   if (i < n && agg[i] >= 0) Tci[Trp[i]] = agg[i];
 }
 
+// the aggregate's rows of B (m <= 32 RPL) held in registers, row t on lane t % 32: the same
+// modified Gram-Schmidt as the general path below, operation for operation (padding rows are
+// zero and add nothing)
+constexpr int TENT_RPL = 8;
+template <int K>
+__device__ __forceinline__ void tentative_regs(int m, int b, const int* __restrict__ mem,
+                                               const int* __restrict__ Trp,
+                                               const double* __restrict__ B, double* TV,
+                                               double* R, int lane) {
+  double v[TENT_RPL][K];
+#pragma unroll
+  for (int j = 0; j < TENT_RPL; j++) {
+    const int t = lane + 32 * j;
+#pragma unroll
+    for (int c = 0; c < K; c++) v[j][c] = 0.0;
+    if (t < m) {
+      const int node = mem[t / b];
+#pragma unroll
+      for (int c = 0; c < K; c++) v[j][c] = B[((int64_t)node * b + (t % b)) * K + c];
+    }
+  }
+#pragma unroll
+  for (int c = 0; c < K; c++) {
+    double n0 = 0.0;
+#pragma unroll
+    for (int j = 0; j < TENT_RPL; j++) n0 += v[j][c] * v[j][c];
+    for (int o = 16; o > 0; o >>= 1) n0 += __shfl_xor_sync(0xffffffffu, n0, o);
+    n0 = sqrt(n0);
+#pragma unroll
+    for (int i = 0; i < c; i++) {
+      double d = 0.0;
+#pragma unroll
+      for (int j = 0; j < TENT_RPL; j++) d += v[j][i] * v[j][c];
+      for (int o = 16; o > 0; o >>= 1) d += __shfl_xor_sync(0xffffffffu, d, o);
+      if (lane == 0) R[i * K + c] = d;
+#pragma unroll
+      for (int j = 0; j < TENT_RPL; j++) v[j][c] -= d * v[j][i];
+    }
+    double nr = 0.0;
+#pragma unroll
+    for (int j = 0; j < TENT_RPL; j++) nr += v[j][c] * v[j][c];
+    for (int o = 16; o > 0; o >>= 1) nr += __shfl_xor_sync(0xffffffffu, nr, o);
+    nr = sqrt(nr);
+    const bool live = n0 > 0.0 && nr > 1e-8 * n0;
+#pragma unroll
+    for (int j = 0; j < TENT_RPL; j++) v[j][c] = live ? v[j][c] / nr : 0.0;
+    if (lane == 0) R[c * K + c] = live ? nr : 0.0;
+  }
+#pragma unroll
+  for (int j = 0; j < TENT_RPL; j++) {
+    const int t = lane + 32 * j;
+    if (t < m) {
+      const int node = mem[t / b];
+#pragma unroll
+      for (int c = 0; c < K; c++) TV[((int64_t)Trp[node] * b + (t % b)) * K + c] = v[j][c];
+    }
+  }
+}
+
 // one warp per aggregate: modified Gram-Schmidt on the aggregate's rows of B (m x k), written
 // in place into the T blocks (b x k per member node); R goes to Bc (k x k per aggregate)
 __global__ void k_tentative(int n_agg, int b, int k, const int* __restrict__ start,
@@ -243,6 +306,14 @@ __global__ void k_tentative(int n_agg, int b, int k, const int* __restrict__ sta
   if (a >= n_agg) return;
   const int s = start[a], e = start[a + 1];
   const int m = (e - s) * b;
+  if (m <= 32 * TENT_RPL && (k == 3 || k == 6)) {  // warp-uniform
+    double* Rr = Bc + (int64_t)a * k * k;
+    for (int t = lane; t < k * k; t += 32) Rr[t] = 0.0;
+    __syncwarp();
+    if (k == 3) tentative_regs<3>(m, b, members + s, Trp, B, TV, Rr, lane);
+    else tentative_regs<6>(m, b, members + s, Trp, B, TV, Rr, lane);
+    return;
+  }
   // row t of the aggregate = member (t / b), component (t % b)
   auto tv = [&](int t, int c) -> double& {
     const int node = members[s + t / b];
@@ -525,8 +596,11 @@ int64_t amg_tentative(cudaStream_t s, int n, int b, int k, int n_agg, const int*
   cursor.zero(s);
   LAUNCH(k_agg_count, g, 256, 0, s, n, agg, cnt.p);
   exclusive_scan_nosync(s, cnt.p, start.p, n_agg);
-  LAUNCH(k_agg_scatter, g, 256, 0, s, n, agg, start.p, cursor.p, members.p);
-  LAUNCH(k_agg_sort, ceil_div(n_agg, 128), 128, 0, s, n_agg, start.p, members.p);
+  DBuf<int> unsorted;
+  unsorted.resize(nT > 0 ? nT : 1);
+  LAUNCH(k_agg_scatter, g, 256, 0, s, n, agg, start.p, cursor.p, unsorted.p);
+  LAUNCH(k_agg_sort, ceil_div((int64_t)n_agg * 32, 128), 128, 0, s, n_agg, start.p, unsorted.p,
+         members.p);
   LAUNCH(k_tentative, ceil_div((int64_t)n_agg * 32, 128), 128, 0, s, n_agg, b, k, start.p,
          members.p, Trp, B, TV, Bc);
   return nT;

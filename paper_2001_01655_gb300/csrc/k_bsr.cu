@@ -684,10 +684,13 @@ void spgemm_fill(cudaStream_t s, const Bsr& A, const Bsr& B, const int* rpC, int
 void spgemm_numeric(cudaStream_t s, const Bsr& A, const double* VA, const Bsr& B, const double* VB,
                     const Bsr& C, double* VC, bool sym) {
   const int grid = ceil_div((int64_t)A.nbr * 32, 128);
-  // few long rows (the restrictions of the coarse Galerkin products, a hundred blocks and more
-  // per row): one warp per output block.  Shorter rows keep the row-per-warp kernel, whose
-  // lanes own the output scalars (no butterfly of every output block over 32 lanes)
-  const bool long_rows = A.nbr > 0 && A.nbr < 4096 && A.nnzb >= 48LL * A.nbr;
+  // few rows with many products per output block (the coarse Galerkin products: about 4 per
+  // block for A P on the first AMG level, a hundred and more for R (A P)): one warp per output
+  // block, the lanes over A's row.  Fewer products per block (A T: about one) keep the
+  // row-per-warp kernel, whose lanes own the output scalars (no butterfly per output block)
+  const double per_block = (double)A.nnzb * ((double)B.nnzb / std::max(1, B.nbr)) /
+                           (double)std::max<int64_t>(1, C.nnzb);
+  const bool long_rows = A.nbr > 0 && A.nbr < 4096 && per_block >= 3.0;
   const int gridw = (int)std::max<int64_t>(1, ceil_div(C.nnzb * 32, 128));
 #define NUM(R, K, CC)                                                                          \
   if (A.br == R && A.bc == K && B.bc == CC) {                                                  \
