@@ -238,11 +238,24 @@ __device__ __forceinline__ void cheb_node(int64_t node, const T* r, const T* xi,
 }  // namespace tomg
 
 namespace tomg {
-// Inverse of a small SPD block (row-major B x B, FP64) through its Cholesky factor.
+// 1 / sqrt(d) in FP64 from the FP32 hardware estimate and two Newton steps for the reciprocal
+// square root, y <- y (3 - d y^2) / 2, each of which doubles the number of correct bits
+// (about 22 -> 44 -> 88).  A few FP64 FMAs instead of an FP64 square root and division, which
+// are long sequences on GB300's narrow FP64 pipe.  Outside the FP32 range: the plain formula.
+__device__ __forceinline__ double rsqrt_newton(double d) {
+  if (!(d > 1e-30 && d < 1e30)) return 1.0 / sqrt(d);
+  double y = (double)rsqrtf((float)d);
+  y = y * (1.5 - 0.5 * d * y * y);
+  y = y * (1.5 - 0.5 * d * y * y);
+  return y;
+}
+
+// Inverse of a small SPD block (row-major B x B, FP64) through its Cholesky factor; the B
+// reciprocal square roots of the pivots replace every square root and division.
 // Returns false if a pivot is not positive (the block is then left unchanged in Ainv = 0).
 template <int B>
 __device__ __forceinline__ bool spd_inverse(const double* A, double* Ainv) {
-  double L[B][B];
+  double L[B][B], rL[B];
 #pragma unroll
   for (int i = 0; i < B; i++)
 #pragma unroll
@@ -254,14 +267,15 @@ __device__ __forceinline__ bool spd_inverse(const double* A, double* Ainv) {
 #pragma unroll
     for (int k = 0; k < j; k++) d -= L[j][k] * L[j][k];
     if (!(d > 0.0)) ok = false;
-    double ljj = ok ? sqrt(d) : 1.0;
-    L[j][j] = ljj;
+    const double rl = ok ? rsqrt_newton(d) : 1.0;  // 1 / L_jj
+    rL[j] = rl;
+    L[j][j] = ok ? d * rl : 1.0;
 #pragma unroll
     for (int i = j + 1; i < B; i++) {
       double v = A[i * B + j];
 #pragma unroll
       for (int k = 0; k < j; k++) v -= L[i][k] * L[j][k];
-      L[i][j] = v / ljj;
+      L[i][j] = v * rl;
     }
   }
   // columns of L^-1, then Ainv = L^-T L^-1
@@ -273,7 +287,7 @@ __device__ __forceinline__ bool spd_inverse(const double* A, double* Ainv) {
       double v = (i == c) ? 1.0 : 0.0;
 #pragma unroll
       for (int k = 0; k < i; k++) v -= L[i][k] * Li[k][c];
-      Li[i][c] = v / L[i][i];
+      Li[i][c] = v * rL[i];
     }
   }
 #pragma unroll

@@ -293,18 +293,6 @@ __global__ void k_gemv(int n, const T* __restrict__ A, const T* __restrict__ b, 
 // A^-1 = Y^T Y (k_ltl).
 constexpr int NB = 32;
 
-// 1 / sqrt(d) in FP64 from the FP32 hardware estimate and two Newton steps for the reciprocal
-// square root, y <- y (3 - d y^2) / 2, each of which doubles the number of correct bits
-// (about 22 -> 44 -> 88).  A few FP64 FMAs instead of an FP64 square root and division, which
-// are long sequences on GB300's narrow FP64 pipe.  Outside the FP32 range: the plain formula.
-__device__ __forceinline__ double rsqrt_newton(double d) {
-  if (!(d > 1e-30 && d < 1e30)) return 1.0 / sqrt(d);
-  double y = (double)rsqrtf((float)d);
-  y = y * (1.5 - 0.5 * d * y * y);
-  y = y * (1.5 - 0.5 * d * y * y);
-  return y;
-}
-
 // The diagonal block in shared memory, right-looking: at pivot k, column k of L and row k of
 // L_kk^-1 are scaled by 1 / sqrt(d_k), then the trailing lower triangle (s_ij -= l_ik l_jk) and
 // the rows of L_kk^-1 below k (x_ic -= l_ik x_kc) are updated.  The entries of each update are
