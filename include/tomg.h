@@ -246,6 +246,9 @@ tomg_status tomg_prolongation_export(tomg_problem* prob, int level, int64_t* nnz
                                      int64_t* row_ptr, int64_t* col, double* val);
 /* AMG levels: aggregate id of every node of `level` (-1 = unaggregated), host array. */
 tomg_status tomg_aggregates_export(tomg_problem* prob, int level, int64_t* agg);
+/* The point-block smoother's inverse diagonal blocks D_b^-1 of `level` (Alg. 1, Sec. 3.2):
+ * n_nodes blocks of block x block, row-major, FP64, host array (levels below the coarsest). */
+tomg_status tomg_block_diag_inv_export(tomg_problem* prob, int level, double* dinv);
 /* y = A_level x in the given tomg_prec (FP32 math for FP32_VCYCLE), double in/out. */
 tomg_status tomg_level_apply(tomg_problem* prob, int level, int prec, const double* x, double* y,
                              int on_device);

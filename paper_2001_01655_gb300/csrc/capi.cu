@@ -352,6 +352,20 @@ tomg_status tomg_aggregates_export(tomg_problem* P, int level, int64_t* agg) {
   });
 }
 
+tomg_status tomg_block_diag_inv_export(tomg_problem* P, int level, double* dinv) {
+  return guarded([&]() -> tomg_status {
+    if (!P || !dinv) TOMG_THROW(TOMG_E_INVALID, "null argument");
+    if (!P->setup_valid || level < 0 || level + 1 >= (int)P->L.size() || !P->L[level]->D64.p)
+      TOMG_THROW(TOMG_E_INVALID, "level %d has no smoother blocks", level);
+    set_device(P);
+    StreamScope sc(P);
+    const Level& L = *P->L[level];
+    CK(cudaMemcpyAsync(dinv, L.D64.p, L.D64.bytes(), cudaMemcpyDeviceToHost, P->stream));
+    CK(cudaStreamSynchronize(P->stream));
+    return TOMG_OK;
+  });
+}
+
 tomg_status tomg_level_apply(tomg_problem* P, int level, int prec, const double* x, double* y,
                              int on_device) {
   return guarded([&]() -> tomg_status {

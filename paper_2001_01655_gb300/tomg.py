@@ -78,6 +78,7 @@ _SIGS = {
     "tomg_level_export": (C.c_int, [_P, C.c_int, _I64, _P, _P, _P]),
     "tomg_prolongation_export": (C.c_int, [_P, C.c_int, _I64, _P, _P, _P]),
     "tomg_aggregates_export": (C.c_int, [_P, C.c_int, _P]),
+    "tomg_block_diag_inv_export": (C.c_int, [_P, C.c_int, _P]),
     "tomg_level_apply": (C.c_int, [_P, C.c_int, C.c_int, _P, _P, C.c_int]),
     "tomg_vcycle": (C.c_int, [_P, _P, _P, C.c_int]),
     "tomg_outer_apply": (C.c_int, [_P, _P, _P, C.c_int]),
@@ -309,6 +310,14 @@ class Problem:
         b, bc, nn = li["block"], lc["block"], li["n_nodes"]
         rp, ci, val = self._bsr_export(load().tomg_prolongation_export, level, nn, b, bc)
         return sp.bsr_matrix((val, ci, rp), shape=(nn * b, lc["n_nodes"] * bc)).tocsr()
+
+    def block_diag_inv(self, level):
+        """The smoother's inverse diagonal blocks of `level`: (n_nodes, block, block), FP64."""
+        li = self.level_info(level)
+        b, nn = li["block"], li["n_nodes"]
+        d = np.zeros((nn, b, b))
+        _check(load().tomg_block_diag_inv_export(self.h, level, C.c_void_p(d.ctypes.data)))
+        return d
 
     def aggregates(self, level):
         li = self.level_info(level)

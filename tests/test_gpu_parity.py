@@ -312,3 +312,28 @@ def test_solve_into_pinned_host_buffer(lib, ctx):
     assert np.array_equal(u_h.numpy(), u_np)
     with pytest.raises(TypeError):
         P.solve(f_h, out=torch.zeros(p.n, dtype=torch.float32))
+
+
+@pytest.mark.parametrize("dim,grid,pc,kw", [
+    (3, (12, 8, 6), "hybrid", dict(n_geo_levels=2, max_coarse_dofs=200)),  # hex8, stencil, 6x6 BSR
+    (2, (40, 20, 1), "amg", dict(max_coarse_dofs=100)),                    # quad4, 3x3 BSR
+])
+def test_smoother_block_inverses(lib, ctx, dim, grid, pc, kw):
+    """The smoother's inverse diagonal blocks (Alg. 1), formed with reciprocal square roots of
+    the Cholesky pivots by Newton steps from the FP32 estimate instead of FP64 square roots and
+    divisions, against numpy's inverse of the same diagonal blocks of the level operator: the
+    error bound of an FP64 block inverse, a few units of roundoff times the block's condition."""
+    p = W.random_problem(dim, *grid, seed=51, contrast="minmax")
+    P = make(lib, ctx, p)
+    P.setup(pc=pc, prec="fp64", **kw)
+    for l in range(P.num_levels() - 1):
+        A = P.level_matrix(l).tocsr()
+        Dg = P.block_diag_inv(l)
+        b = Dg.shape[1]
+        worst = 0.0
+        for i in range(Dg.shape[0]):
+            D = A[i * b:(i + 1) * b, i * b:(i + 1) * b].toarray()
+            Di = np.linalg.inv(D)
+            err = np.abs(Dg[i] - Di).max() / np.abs(Di).max()
+            worst = max(worst, err / np.linalg.cond(D))
+        assert worst <= 1e-14, (l, worst)
