@@ -61,8 +61,8 @@ constexpr int PS = 7;                        // staged y-pair partials: row stri
 constexpr int OFF_B = 0;
 constexpr int OFF_X = OFF_B + B_BYTES;                         // x ring, FP64
 constexpr int OFF_P = OFF_X + 2 * LAYER_NODES * 3 * 8;         // y pairs, FP64
-constexpr int OFF_T = OFF_P + 2 * ROWS * PS * 8;               // top-half node sums, FP64
-constexpr int OFF_R = OFF_T + 2 * ROWS * 3 * 8;                // reduction scratch
+constexpr int OFF_T = OFF_P + 2 * TY * TNX * PS * 8;           // top-half node sums, FP64
+constexpr int OFF_R = OFF_T + 2 * LAYER_NODES * 3 * 8;         // reduction scratch
 constexpr int OFF_BAR = OFF_R + 32 * 8;                        // mbarrier, TMEM address
 constexpr int SMEM_ALLOC = OFF_BAR + 16 + 128;
 static_assert(ACC_COL >= ND * KP / 2 && ACC_COL + ND * NB <= TMEM_COLS, "tensor memory map");
@@ -314,29 +314,31 @@ struct Fin {
   unsigned m;
 };
 
-// One block: a 32 x 4 element column of the grid, node layers [k0, k1); two threads per element
+// Kernel 1 of an apply: the element products of one tile of the grid's element partition (32 x 4
+// elements x nz_tile layers; every element belongs to exactly one tile) summed into the nodes of
+// the tile's node box (33 x 5 x (nz_tile + 1)), written as partial sums; nodes on the box faces
+// also receive sums from the neighbouring tiles, which kernel 2 adds.  Two threads per element
 // row (its tensor-memory lane): half 0 (warps 0-3) builds the digits of the row's bottom inputs
-// and folds its bottom outputs, half 1 (warps 4-7) the top ones, so that twice as many warps
-// hide the latency of the digit arithmetic.  A node layer's sum is the top sums of the element
-// layer below it (half 1, staged in shared memory) plus the bottom sums of the element layer
-// above it (half 0), which finishes the node.
-template <int MODE>
+// and folds its bottom outputs, half 1 (warps 4-7) the top ones.  Node layer L of the box is
+// the top sums of element layer L - 1 (half 1, staged in shared memory) plus the bottom sums of
+// element layer L (half 0); within a layer, x-neighbour sums by warp shuffle (lane 31 also
+// carries the box's last column), y-neighbour sums through shared memory.
 __global__ void __launch_bounds__(NT, 2)
-k_ebe3x64(int nx, int ny, int nz, int nz_tile, int nzc, const uint4* __restrict__ Bimg,
-          const double* __restrict__ E, double c, const uint8_t* __restrict__ mask,
-          const double* __restrict__ x, double* __restrict__ y, const double* __restrict__ b,
-          const int* done, double* partials, Scalars* sc) {
+k_ebe3x64_tiles(int nx, int ny, int nz, int nz_tile, int nzc, const uint4* __restrict__ Bimg,
+                const double* __restrict__ E, double c, const uint8_t* __restrict__ mask,
+                const double* __restrict__ x, double* __restrict__ pbuf, const int* done,
+                Scalars* sc) {
   extern __shared__ uint8_t smem_raw[];
   pdl_prologue();
-  // blockIdx.z = chunk of node layers + nzc x right-hand side of a block solve
+  // blockIdx.z = chunk of element layers + nzc x right-hand side of a block solve
   const int zc = blockIdx.z % nzc, rhs = blockIdx.z / nzc;
-  const int nblk = gridDim.x * gridDim.y * nzc;  // blocks of one right-hand side
+  const int64_t tile = blockIdx.x + (int64_t)gridDim.x * (blockIdx.y + (int64_t)gridDim.y * zc);
+  const int64_t ntile = (int64_t)gridDim.x * gridDim.y * nzc;
+  const int slots = LAYER_NODES * (nz_tile + 1);
   {
     const int64_t vo = (int64_t)rhs * rhs_stride((int64_t)3 * (nx + 1) * (ny + 1) * (nz + 1));
     x += vo;
-    y += vo;
-    if (b) b += vo;
-    if (partials) partials += (int64_t)rhs * nblk;
+    pbuf += ((int64_t)rhs * ntile + tile) * slots * 3;
     if (sc) {
       sc += rhs;
       if (done) done = &sc->done;
@@ -345,18 +347,17 @@ k_ebe3x64(int nx, int ny, int nz, int nz_tile, int nzc, const uint4* __restrict_
   if (solve_done(done)) return;
   uint8_t* sm = smem_raw + ((128 - (smem_u32(smem_raw) & 127u)) & 127u);
   double* sxr = reinterpret_cast<double*>(sm + OFF_X);  // [2][LAYER_NODES][3]
-  double* sP = reinterpret_cast<double*>(sm + OFF_P);   // [2][TY][TEX][PS]
-  double* sT = reinterpret_cast<double*>(sm + OFF_T);   // [2][ROWS][3]
-  double* sred = reinterpret_cast<double*>(sm + OFF_R);
+  double* sP = reinterpret_cast<double*>(sm + OFF_P);   // [2][TY][TNX][PS]
+  double* sT = reinterpret_cast<double*>(sm + OFF_T);   // [2][LAYER_NODES][3]
   uint64_t* bar = reinterpret_cast<uint64_t*>(sm + OFF_BAR);
   uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(sm + OFF_BAR + 8);
   const uint32_t sbase = smem_u32(sm), bar0 = smem_u32(bar);
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-  const int h = tid / ROWS, r = tid % ROWS;  // half, element row
+  const int h = tid / ROWS;  // half
   const int ex = lane, ey = (warp & 3);
-  const int EX0 = blockIdx.x * ONX - 1, EY0 = blockIdx.y * ONY - 1;
+  const int EX0 = blockIdx.x * TEX, EY0 = blockIdx.y * TY;
   const int k0 = zc * nz_tile;
-  const int k1 = min(k0 + nz_tile, nz + 1);  // owned node layers [k0, k1)
+  const int k1 = min(k0 + nz_tile, nz);  // element layers [k0, k1), node layers [k0, k1]
 
   if (warp == 0) {
     asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;\n"
@@ -368,19 +369,15 @@ k_ebe3x64(int nx, int ny, int nz, int nz_tile, int nzc, const uint4* __restrict_
     asm volatile("fence.mbarrier_init.release.cluster;\n" ::: "memory");
   }
   for (int t = tid; t < B_BYTES / 16; t += NT) reinterpret_cast<uint4*>(sm + OFF_B)[t] = Bimg[t];
-  for (int t = tid; t < 2 * ROWS * 3; t += NT) sT[t] = 0.0;
-
-  const bool owner = ex >= 1 && ey >= 1;
-  const int gi = EX0 + ex, gj = EY0 + ey;
-  const bool in_plane = owner && gi <= nx && gj <= ny;
+  for (int t = tid; t < 2 * LAYER_NODES * 3; t += NT) sT[t] = 0.0;
 
   XPre pre, pre2;
-  x_fetch(pre, k0 - 1, EX0, EY0, nx, ny, nz, mask, x);
-  x_fetch(pre2, k0, EX0, EY0, nx, ny, nz, mask, x);
-  x_store(pre, sxr + ((k0 - 1) & 1) * LAYER_NODES * 3);
-  x_store(pre2, sxr + (k0 & 1) * LAYER_NODES * 3);
-  x_fetch(pre, k0 + 1, EX0, EY0, nx, ny, nz, mask, x);
-  double ec_cur = c * e_fetch(k0 - 1, ex, ey, EX0, EY0, nx, ny, nz, E);  // E c of layer ke
+  x_fetch(pre, k0, EX0, EY0, nx, ny, nz, mask, x);
+  x_fetch(pre2, k0 + 1, EX0, EY0, nx, ny, nz, mask, x);
+  x_store(pre, sxr + (k0 & 1) * LAYER_NODES * 3);
+  x_store(pre2, sxr + ((k0 + 1) & 1) * LAYER_NODES * 3);
+  x_fetch(pre, k0 + 2, EX0, EY0, nx, ny, nz, mask, x);
+  double ec_cur = c * e_fetch(k0, ex, ey, EX0, EY0, nx, ny, nz, E);  // E c of layer ke
   double sc_prev = 0.0;  // E c 2^(p - 1075) of this thread's row of layer ke - 1
   asm volatile("tcgen05.fence::before_thread_sync;\n" ::: "memory");
   __syncthreads();
@@ -388,18 +385,15 @@ k_ebe3x64(int nx, int ny, int nz, int nz_tile, int nzc, const uint4* __restrict_
   const uint32_t tmem = *tmem_slot;
   const uint32_t lane_base = (uint32_t)(32 * (warp & 3)) << 16;
 
-  Fin fd;
-  fd.m = 7u;
   uint32_t parity = 0, pending = 0;
   bool failed = false;
-  double dotv = 0.0;
 
-  for (int ke = k0 - 1; ke <= k1; ke++) {
+  for (int ke = k0; ke <= k1; ke++) {
     const bool mma_now = ke < k1;
     const int j = ke & 1, jp = j ^ 1;
     bool ok = true;
     double v[KH];
-    if (ke >= k0) {
+    if (ke > k0) {
       // the MMAs of layer ke - 1; the phase advances only on success (see the drain below)
       ok = mbar_wait(bar0, parity);
       if (ok) {
@@ -428,69 +422,72 @@ k_ebe3x64(int nx, int ny, int nz, int nz_tile, int nzc, const uint4* __restrict_
       if (tid == 0) issue_mmas(tmem, sbase + OFF_B, bar0);
       pending = 1u;
     }
+    // refill the ring: node layer ke + 2 replaces layer ke (read by the digits above)
     if (mma_now && ke + 2 <= k1) {
       x_store(pre, sxr + j * LAYER_NODES * 3);
       if (ke + 3 <= k1) x_fetch(pre, ke + 3, EX0, EY0, nx, ny, nz, mask, x);
     }
     const double ec_next =
         (ke + 1 < k1) ? c * e_fetch(ke + 1, ex, ey, EX0, EY0, nx, ny, nz, E) : 0.0;
-    Fin fd_next;
-    fd_next.m = 7u;
-    if (h == 0 && in_plane && ke >= k0 && ke < k1) {
-      const int64_t node = node_id(gi, gj, ke, nx, ny);
-      fd_next.m = __ldg(mask + node);
-#pragma unroll
-      for (int q = 0; q < 3; q++) fd_next.x[q] = __ldg(x + 3 * node + q);
-      if (MODE == MODE_RESID) {
-#pragma unroll
-        for (int q = 0; q < 3; q++) fd_next.b[q] = __ldg(b + 3 * node + q);
-      }
-    }
-    double pr[2][3];  // x-pair sums of this half's node layer at node column ex: [dy][c]
-    if (ke >= k0) {
+    // x-pair sums of this half's node layer of element layer ke - 1: node column ex gets the
+    // dx = 0 corner of element ex and the dx = 1 corner of element ex - 1 (none for column 0);
+    // lane 31 also holds column 32 (the dx = 1 corner of element 31 alone)
+    double pr[2][3], p32[2][3];
+    if (ke > k0) {
 #pragma unroll
       for (int dy = 0; dy < 2; dy++)
 #pragma unroll
         for (int q = 0; q < 3; q++) {
-          const double left = __shfl_up_sync(0xffffffffu, v[3 * (1 + 2 * dy) + q], 1);
-          pr[dy][q] = v[3 * (2 * dy) + q] + left;
+          const double r1 = v[3 * (1 + 2 * dy) + q];
+          const double left = __shfl_up_sync(0xffffffffu, r1, 1);
+          pr[dy][q] = v[3 * (2 * dy) + q] + (lane ? left : 0.0);
+          p32[dy][q] = r1;
         }
-      double* myP = sP + (j * ROWS + ey * TEX + ex) * PS;
+      double* myP = sP + ((j * TY + ey) * TNX + ex) * PS;
 #pragma unroll
       for (int q = 0; q < 3; q++) myP[3 * h + q] = pr[1][q];
+      if (lane == 31) {
+        double* myP32 = sP + ((j * TY + ey) * TNX + TEX) * PS;
+#pragma unroll
+        for (int q = 0; q < 3; q++) myP32[3 * h + q] = p32[1][q];
+      }
     }
     __syncthreads();
-    if (ke >= k0 && owner) {
-      const double* upP = sP + (j * ROWS + (ey - 1) * TEX + ex) * PS;
-      if (h == 1) {  // top sums of element layer ke - 1: node layer ke, finished next step
+    if (ke > k0) {
+      // the box positions of this thread: (ex, ey), with lane 31 also column 32 and element
+      // row 3 also node row 4; node (lx, ly) sums the dy = 0 pairs of element row ly and the
+      // dy = 1 pairs of element row ly - 1
+      const int L = h ? ke : ke - 1;  // the node layer of this half's corners
+      for (int cx = 0; cx < (lane == 31 ? 2 : 1); cx++) {
+        const int lx = ex + cx;
+        for (int cy = 0; cy < (ey == TY - 1 ? 2 : 1); cy++) {
+          const int ly = ey + cy;
+          double sum[3];
 #pragma unroll
-        for (int q = 0; q < 3; q++) sT[(j * ROWS + r) * 3 + q] = upP[3 + q] + pr[0][q];
-      } else {  // node layer ke - 1: top sums of element layer ke - 2 plus bottom sums of ke - 1
-        const int kn = ke - 1;
-        double acc[3];
-#pragma unroll
-        for (int q = 0; q < 3; q++) acc[q] = sT[(jp * ROWS + r) * 3 + q] + (upP[q] + pr[0][q]);
-        if (in_plane && kn >= k0) {
-          const int64_t node = node_id(gi, gj, kn, nx, ny);
-          double Ax[3];
-#pragma unroll
-          for (int q = 0; q < 3; q++) Ax[q] = ((fd.m >> q) & 1u) ? fd.x[q] : acc[q];
-          if (MODE == MODE_APPLY) {
-#pragma unroll
-            for (int q = 0; q < 3; q++) {
-              y[3 * node + q] = Ax[q];
-              dotv += fd.x[q] * Ax[q];
+          for (int q = 0; q < 3; q++) {
+            const double own = (cy == 0) ? (cx ? p32[0][q] : pr[0][q]) : 0.0;
+            double up = 0.0;
+            if (ly >= 1) {
+              const double* upP = sP + ((j * TY + (ly - 1)) * TNX + lx) * PS;
+              up = upP[3 * h + q];
             }
-          } else {
+            sum[q] = up + own;
+          }
+          const int pos = ly * TNX + lx;
+          if (h == 1 && L < k1) {  // staged for node layer L, finished next step by half 0
 #pragma unroll
-            for (int q = 0; q < 3; q++) y[3 * node + q] = fd.b[q] - Ax[q];
+            for (int q = 0; q < 3; q++) sT[(j * LAYER_NODES + pos) * 3 + q] = sum[q];
+          } else {  // node layer L complete within the tile: top of L - 1 plus bottom of L
+            double* out = pbuf + ((int64_t)(L - k0) * LAYER_NODES + pos) * 3;
+#pragma unroll
+            for (int q = 0; q < 3; q++)
+              out[q] = (h == 0 ? sT[(jp * LAYER_NODES + pos) * 3 + q] : 0.0) + sum[q];
           }
         }
       }
     }
     sc_prev = sc_now;
     ec_cur = ec_next;
-    fd = fd_next;
   }
 
   if (failed) {
@@ -505,36 +502,126 @@ k_ebe3x64(int nx, int ny, int nz, int nz_tile, int nzc, const uint4* __restrict_
     asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;\n"
                  :: "r"(tmem), "r"(TMEM_COLS) : "memory");
   }
+}
+
+// Kernel 2: every node's sum of the partial sums of the (one to eight) tiles whose boxes hold it,
+// in ascending tile order, then the outer operator's finishing: A x = x on fixed DOFs, y = A x
+// with the partials of x . y and FIN_ALPHA in the last block (MODE_APPLY), or y = b - A x.
+constexpr int FIN_THREADS = 256;
+
+__device__ __forceinline__ int tiles_of(int i, int n_t, int w, int* t0) {
+  // tiles t (0 <= t < n_t) with t w <= i <= t w + w; returns their count (1 or 2), first in *t0
+  const int hi = min(i / w, n_t - 1);
+  const int lo = (i % w == 0 && i > 0) ? i / w - 1 : hi;
+  *t0 = lo;
+  return hi - lo + 1;
+}
+
+template <int MODE>
+__global__ void __launch_bounds__(FIN_THREADS)
+k_ebe3x64_nodes(int nx, int ny, int nz, int nz_tile, int gx, int gy, int nzc,
+                const double* __restrict__ pbuf, const uint8_t* __restrict__ mask,
+                const double* __restrict__ x, double* __restrict__ y,
+                const double* __restrict__ b, const int* done, double* partials, Scalars* sc) {
+  __shared__ double sred[32];
+  pdl_prologue();
+  const int rhs = blockIdx.y;
+  const int64_t nn = (int64_t)(nx + 1) * (ny + 1) * (nz + 1);
+  const int slots = LAYER_NODES * (nz_tile + 1);
+  const int64_t ntile = (int64_t)gx * gy * nzc;
+  {
+    const int64_t vo = (int64_t)rhs * rhs_stride(3 * nn);
+    x += vo;
+    y += vo;
+    if (b) b += vo;
+    pbuf += (int64_t)rhs * ntile * slots * 3;
+    if (partials) partials += (int64_t)rhs * gridDim.x;
+    if (sc) {
+      sc += rhs;
+      if (done) done = &sc->done;
+    }
+  }
+  if (solve_done(done)) return;
+  double dotv = 0.0;
+  const int64_t node = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (node < nn) {
+    int i, j, k;
+    node_ijk(node, nx, ny, 3, i, j, k);
+    int tx, ty, tz;
+    const int cx = tiles_of(i, gx, TEX, &tx), cy = tiles_of(j, gy, TY, &ty);
+    const int cz = tiles_of(k, nzc, nz_tile, &tz);
+    double acc[3] = {0.0, 0.0, 0.0};
+    for (int a = 0; a < cz; a++)
+      for (int bb = 0; bb < cy; bb++)
+        for (int d = 0; d < cx; d++) {
+          const int bx = tx + d, by = ty + bb, bz = tz + a;
+          const int64_t t = bx + (int64_t)gx * (by + (int64_t)gy * bz);
+          const int slot = ((k - bz * nz_tile) * TNY + (j - by * TY)) * TNX + (i - bx * TEX);
+          const double* pp = pbuf + (t * slots + slot) * 3;
+#pragma unroll
+          for (int q = 0; q < 3; q++) acc[q] += pp[q];
+        }
+    const unsigned m = mask[node];
+    double xv[3], Ax[3];
+#pragma unroll
+    for (int q = 0; q < 3; q++) {
+      xv[q] = x[3 * node + q];
+      Ax[q] = ((m >> q) & 1u) ? xv[q] : acc[q];
+    }
+    if (MODE == MODE_APPLY) {
+#pragma unroll
+      for (int q = 0; q < 3; q++) {
+        y[3 * node + q] = Ax[q];
+        dotv += xv[q] * Ax[q];
+      }
+    } else {
+#pragma unroll
+      for (int q = 0; q < 3; q++) y[3 * node + q] = b[3 * node + q] - Ax[q];
+    }
+  }
   if (MODE != MODE_APPLY || !partials) return;  // uniform over the grid
   const double tot = block_sum(dotv, sred);
-  if (tid == 0) partials[blockIdx.x + gridDim.x * (blockIdx.y + gridDim.y * zc)] = tot;
-  if (sc && last_block(&sc->tk[TK_ALPHA], nblk))
-    finish_body(FIN_ALPHA, partials, nblk, nullptr, 0, sc, sred);
+  if (threadIdx.x == 0) partials[blockIdx.x] = tot;
+  if (sc && last_block(&sc->tk[TK_ALPHA], gridDim.x))
+    finish_body(FIN_ALPHA, partials, gridDim.x, nullptr, 0, sc, sred);
+}
+
+constexpr int X64_NZ_TILE = 8;
+
+struct X64Grid {
+  int gx, gy, nzc;
+};
+inline X64Grid x64_grid(const Ebe& op) {
+  return X64Grid{ceil_div(op.nx, TEX), ceil_div(op.ny, TY), ceil_div(op.nz, X64_NZ_TILE)};
 }
 
 template <int MODE>
 void launch(cudaStream_t s, const Ebe& op, const void* Bimg, double c, const double* x, double* y,
-            const double* b, const int* done, double* partials, Scalars* sc) {
+            const double* b, const int* done, double* partials, Scalars* sc, double* pbuf) {
   // two blocks per SM at most: their 256 tensor-memory columns each fill the SM's 512 (a third
   // block would wait in tcgen05.alloc), so the dynamic shared memory is raised until no more fit
   static int smem = 0;
   if (smem == 0) {
     int bytes = SMEM_ALLOC, per_sm = 0;
-    CK(cudaFuncSetAttribute(k_ebe3x64<MODE>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+    CK(cudaFuncSetAttribute(k_ebe3x64_tiles, cudaFuncAttributeMaxDynamicSharedMemorySize,
                             110 << 10));
     for (;;) {
-      CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_ebe3x64<MODE>, NT, bytes));
+      CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_ebe3x64_tiles, NT, bytes));
       if (per_sm <= 2 || bytes >= (110 << 10)) break;
       bytes += 4 << 10;
     }
     smem = bytes;
   }
-  const int nzt = 8;
-  const int nzc = ceil_div(op.nz + 1, nzt);
-  const dim3 grid(ceil_div(op.nx + 1, ONX), ceil_div(op.ny + 1, ONY), nzc * batch_rhs());
-  LAUNCH((k_ebe3x64<MODE>), grid, NT, smem, s, op.nx, op.ny, op.nz, nzt, nzc,
-         reinterpret_cast<const uint4*>(Bimg), (const double*)op.E, c, op.mask, x, y, b, done,
-         partials, sc);
+  if (!pbuf) TOMG_THROW(TOMG_E_INVALID, "FP64 tensor-core element operator without its buffer");
+  const X64Grid g = x64_grid(op);
+  const dim3 grid(g.gx, g.gy, g.nzc * batch_rhs());
+  LAUNCH(k_ebe3x64_tiles, grid, NT, smem, s, op.nx, op.ny, op.nz, X64_NZ_TILE, g.nzc,
+         reinterpret_cast<const uint4*>(Bimg), (const double*)op.E, c, op.mask, x, pbuf, done,
+         sc);
+  const int64_t nn = (int64_t)(op.nx + 1) * (op.ny + 1) * (op.nz + 1);
+  LAUNCH((k_ebe3x64_nodes<MODE>), dim3(ceil_div(nn, FIN_THREADS), batch_rhs()), FIN_THREADS, 0, s,
+         op.nx, op.ny, op.nz, X64_NZ_TILE, g.gx, g.gy, g.nzc, (const double*)pbuf, op.mask, x, y,
+         b, done, partials, sc);
 }
 
 }  // namespace
@@ -582,14 +669,20 @@ bool ebe3x_operand(double nu, uint32_t* img, double* c) {
 int ebe3x_operand_words() { return B_BYTES / 4; }
 
 int ebe3x_blocks(const Ebe& op) {
-  return ceil_div(op.nx + 1, ONX) * ceil_div(op.ny + 1, ONY) * ceil_div(op.nz + 1, 8);
+  return ceil_div((int64_t)(op.nx + 1) * (op.ny + 1) * (op.nz + 1), FIN_THREADS);
+}
+
+int64_t ebe3x_buffer_doubles(const Ebe& op) {
+  const X64Grid g = x64_grid(op);
+  return (int64_t)g.gx * g.gy * g.nzc * LAYER_NODES * (X64_NZ_TILE + 1) * 3;
 }
 
 void ebe3x_apply(cudaStream_t s, int mode, const Ebe& op, const void* Bimg, double c,
                  const double* x, double* y, const double* b, const int* done, double* partials,
-                 Scalars* sc) {
-  if (mode == MODE_APPLY) launch<MODE_APPLY>(s, op, Bimg, c, x, y, b, done, partials, sc);
-  else if (mode == MODE_RESID) launch<MODE_RESID>(s, op, Bimg, c, x, y, b, done, nullptr, nullptr);
+                 Scalars* sc, double* pbuf) {
+  if (mode == MODE_APPLY) launch<MODE_APPLY>(s, op, Bimg, c, x, y, b, done, partials, sc, pbuf);
+  else if (mode == MODE_RESID)
+    launch<MODE_RESID>(s, op, Bimg, c, x, y, b, done, nullptr, nullptr, pbuf);
   else TOMG_THROW(TOMG_E_INVALID, "FP64 tensor-core element operator: apply and residual only");
 }
 

@@ -91,11 +91,14 @@ void ebe3d_tc_operand(double nu, uint32_t* img, float* cl, float* cm);
 // integer matrix C with Ke = c C) and returns false when nu gives no small integer C.
 bool ebe3x_operand(double nu, uint32_t* img, double* c);
 int ebe3x_operand_words();
-int ebe3x_blocks(const Ebe& op);  // blocks (= dot partials) of one launch
-// MODE_APPLY: y = A x, partials of x . y (nullable), FIN_ALPHA with sc; MODE_RESID: y = b - A x
+int ebe3x_blocks(const Ebe& op);  // blocks (= dot partials) of one apply, per right-hand side
+// doubles of the work buffer of one apply per right-hand side (the tiles' node partial sums)
+int64_t ebe3x_buffer_doubles(const Ebe& op);
+// MODE_APPLY: y = A x, partials of x . y (nullable), FIN_ALPHA with sc; MODE_RESID: y = b - A x.
+// pbuf: ebe3x_buffer_doubles x batch_rhs() doubles, owned by the caller (one per stream)
 void ebe3x_apply(cudaStream_t s, int mode, const Ebe& op, const void* Bimg, double c,
                  const double* x, double* y, const double* b, const int* done, double* partials,
-                 Scalars* sc);
+                 Scalars* sc, double* pbuf);
 bool ebe3x_error(cudaStream_t s);  // a wait of the FP64 tensor-core kernel ran out (syncs s)
 // polls of the tensor-core kernel's in-loop MMA waits in later launches (0 = the default);
 // a test shortens it to make the waits run out and exercise the error path

@@ -365,6 +365,16 @@ void apply_M_and_dots(tomg_problem* P, Work& W, const double* q, const int* done
 // whether the outer FP64 applies of hex8 run on the tensor cores (k_ebe3x64.cu)
 bool x64_active(const tomg_problem* P) { return P->dim == 3 && P->Kx64.p && P->opt.fp64_tc; }
 
+// the FP64 tensor-core operator's work buffer for launches on stream s (one per stream: solve
+// slots apply concurrently), sized for the current block of right-hand sides.  Allocated
+// outside graph captures (build_graph asks for it before capturing).
+double* x64_buffer(tomg_problem* P, cudaStream_t s) {
+  const int64_t need = ebe3x_buffer_doubles(V<double>::ebe(P)) * batch_rhs();
+  DBuf<double>& b = P->x64buf[s];
+  if ((int64_t)b.n < need) b.resize(need);
+  return b.p;
+}
+
 // Outer-loop K in FP64: on hex8 the element products on the tensor cores (exact integer digit
 // products, FP64 scaling and node sums) when nu allows them; else the assembled fine stencil
 // when the setup kept it (36 / 243 FMAs per node instead of 64 / 576 for the element products),
@@ -375,7 +385,7 @@ void fine64_apply_dot(tomg_problem* P, cudaStream_t s, const double* x, double* 
   Level& L0 = *P->L[0];
   if (x64_active(P)) {
     ebe3x_apply(s, MODE_APPLY, V<double>::ebe(P), P->Kx64.p, P->x64_c, x, y, nullptr, done,
-                partials, sc);
+                partials, sc, x64_buffer(P, s));
   } else if (L0.S64.p) {
     stencil_apply_dot(s, L0.g, L0.S64.p, x, y, done, partials, sc);
   } else {
@@ -386,7 +396,7 @@ void fine64_apply_dot(tomg_problem* P, cudaStream_t s, const double* x, double* 
 void fine64_resid(tomg_problem* P, cudaStream_t s, const double* x, double* y, const double* b) {
   if (x64_active(P))
     ebe3x_apply(s, MODE_RESID, V<double>::ebe(P), P->Kx64.p, P->x64_c, x, y, b, nullptr, nullptr,
-                nullptr);
+                nullptr, x64_buffer(P, s));
   else
     level_op<double>(P, s, 0, MODE_RESID, x, y, b, nullptr);
 }
@@ -434,6 +444,10 @@ void destroy_graph(Work& W) {
 void build_graph(tomg_problem* P, Work& W) {
   destroy_graph(W);
   const int mode = W.block > 1 ? 2 : P->opt.use_graph;
+  if (mode > 0 && x64_active(P)) {  // the outer operator's buffer, before any capture
+    BatchScope bs(W.block > 1 ? W.block : 1);
+    x64_buffer(P, W.stream);
+  }
   auto run_body = [&]() {
     if (W.block > 1) block_iteration_body(P, W);
     else iteration_body(P, W);

@@ -8,6 +8,7 @@
 #pragma once
 
 #include <atomic>
+#include <map>
 #include <memory>
 
 #include "ops.h"
@@ -138,6 +139,7 @@ struct tomg_problem {
   float tc_cl = 0.f, tc_cm = 0.f;  // its scales lambda / 72 and mu / 72
   tomg::DBuf<uint32_t> Kx64;  // integer B operand of the FP64 tensor-core kernel (hex8; empty if
   double x64_c = 0.0;         // nu admits none) and its scale: Ke = x64_c C
+  std::map<cudaStream_t, tomg::DBuf<double>> x64buf;  // its work buffers, one per stream
   tomg::DBuf<double> Ke64;
   tomg::DBuf<float> Ke32;
   tomg::DBuf<uint8_t> mask;
