@@ -44,6 +44,7 @@
 
 #include <cmath>
 #include <cstring>
+#include <algorithm>
 #include <map>
 #include <mutex>
 #include <tuple>
@@ -714,10 +715,18 @@ int ebe3d_tc_autotune(cudaStream_t s, const Ebe& op, const float* Dinv) {
   CK(cudaEventCreate(&e1));
   int best = 8, best_ty = 8;
   float best_ms = 1e30f;
-  for (int cand = 0; cand < 8; cand++) {
-    const int ty = cand < 4 ? 8 : 4;
-    static const int nz_options[4] = {8, 4, 16, 32};
-    const int nzt = nz_options[cand % 4];
+  // node layers per block: powers of two, and the sizes that split the node layers into 2-12
+  // near-equal chunks (each chunk computes one more element layer than it owns, so fewer,
+  // even chunks waste less)
+  std::vector<int> nzs = {8, 4, 16, 32};
+  for (int k = 2; k <= 12; k++) {
+    const int t = (op.nz + 1 + k - 1) / k;
+    if (t >= 4 && t <= 64 && std::find(nzs.begin(), nzs.end(), t) == nzs.end()) nzs.push_back(t);
+  }
+  const int nc = (int)nzs.size();
+  for (int cand = 0; cand < 2 * nc; cand++) {
+    const int ty = cand < nc ? 8 : 4;
+    const int nzt = nzs[cand % nc];
     if (nzt > 8 && nzt / 2 >= op.nz + 1) continue;  // no more blocks to split off
     Ebe o = op;
     o.tc_nz = nzt;
