@@ -508,6 +508,7 @@ k_ebe3x64_tiles(int nx, int ny, int nz, int nz_tile, int nzc, const uint4* __res
 // in ascending tile order, then the outer operator's finishing: A x = x on fixed DOFs, y = A x
 // with the partials of x . y and FIN_ALPHA in the last block (MODE_APPLY), or y = b - A x.
 constexpr int FIN_THREADS = 256;
+constexpr int X64_NZ_TILE = 8;  // element layers per tile
 
 __device__ __forceinline__ int tiles_of(int i, int n_t, int w, int* t0) {
   // tiles t (0 <= t < n_t) with t w <= i <= t w + w; returns their count (1 or 2), first in *t0
@@ -517,14 +518,15 @@ __device__ __forceinline__ int tiles_of(int i, int n_t, int w, int* t0) {
   return hi - lo + 1;
 }
 
-template <int MODE>
+template <int MODE, int NZT>
 __global__ void __launch_bounds__(FIN_THREADS)
-k_ebe3x64_nodes(int nx, int ny, int nz, int nz_tile, int gx, int gy, int nzc,
+k_ebe3x64_nodes(int nx, int ny, int nz, int gx, int gy, int nzc,
                 const double* __restrict__ pbuf, const uint8_t* __restrict__ mask,
                 const double* __restrict__ x, double* __restrict__ y,
                 const double* __restrict__ b, const int* done, double* partials, Scalars* sc) {
   __shared__ double sred[32];
   pdl_prologue();
+  constexpr int nz_tile = NZT;
   const int rhs = blockIdx.y;
   const int64_t nn = (int64_t)(nx + 1) * (ny + 1) * (nz + 1);
   const int slots = LAYER_NODES * (nz_tile + 1);
@@ -551,15 +553,20 @@ k_ebe3x64_nodes(int nx, int ny, int nz, int nz_tile, int gx, int gy, int nzc,
     const int cx = tiles_of(i, gx, TEX, &tx), cy = tiles_of(j, gy, TY, &ty);
     const int cz = tiles_of(k, nzc, nz_tile, &tz);
     double acc[3] = {0.0, 0.0, 0.0};
-    for (int a = 0; a < cz; a++)
-      for (int bb = 0; bb < cy; bb++)
-        for (int d = 0; d < cx; d++) {
+    // fixed trip counts (the absent second tiles of an axis are skipped by predicate)
+#pragma unroll
+    for (int a = 0; a < 2; a++)
+#pragma unroll
+      for (int bb = 0; bb < 2; bb++)
+#pragma unroll
+        for (int d = 0; d < 2; d++) {
+          if (a >= cz || bb >= cy || d >= cx) continue;
           const int bx = tx + d, by = ty + bb, bz = tz + a;
           const int64_t t = bx + (int64_t)gx * (by + (int64_t)gy * bz);
           const int slot = ((k - bz * nz_tile) * TNY + (j - by * TY)) * TNX + (i - bx * TEX);
           const double* pp = pbuf + (t * slots + slot) * 3;
 #pragma unroll
-          for (int q = 0; q < 3; q++) acc[q] += pp[q];
+          for (int q = 0; q < 3; q++) acc[q] += __ldg(pp + q);
         }
     const unsigned m = mask[node];
     double xv[3], Ax[3];
@@ -585,8 +592,6 @@ k_ebe3x64_nodes(int nx, int ny, int nz, int nz_tile, int gx, int gy, int nzc,
   if (sc && last_block(&sc->tk[TK_ALPHA], gridDim.x))
     finish_body(FIN_ALPHA, partials, gridDim.x, nullptr, 0, sc, sred);
 }
-
-constexpr int X64_NZ_TILE = 8;
 
 struct X64Grid {
   int gx, gy, nzc;
@@ -619,9 +624,9 @@ void launch(cudaStream_t s, const Ebe& op, const void* Bimg, double c, const dou
          reinterpret_cast<const uint4*>(Bimg), (const double*)op.E, c, op.mask, x, pbuf, done,
          sc);
   const int64_t nn = (int64_t)(op.nx + 1) * (op.ny + 1) * (op.nz + 1);
-  LAUNCH((k_ebe3x64_nodes<MODE>), dim3(ceil_div(nn, FIN_THREADS), batch_rhs()), FIN_THREADS, 0, s,
-         op.nx, op.ny, op.nz, X64_NZ_TILE, g.gx, g.gy, g.nzc, (const double*)pbuf, op.mask, x, y,
-         b, done, partials, sc);
+  LAUNCH((k_ebe3x64_nodes<MODE, X64_NZ_TILE>), dim3(ceil_div(nn, FIN_THREADS), batch_rhs()),
+         FIN_THREADS, 0, s, op.nx, op.ny, op.nz, g.gx, g.gy, g.nzc, (const double*)pbuf, op.mask,
+         x, y, b, done, partials, sc);
 }
 
 }  // namespace
