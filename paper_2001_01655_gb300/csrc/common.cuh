@@ -238,6 +238,38 @@ __device__ __forceinline__ void cheb_node(int64_t node, const T* r, const T* xi,
 }  // namespace tomg
 
 namespace tomg {
+// Barrier over every block of a cooperative launch (all blocks resident).  sync[0] counts the
+// arrivals, sync[1] is the generation the last arrival advances.  A wait is bounded: past
+// `limit` polls, or once *err is set by another block, the block sets *err and every thread
+// of it gets false, so that no kernel waits forever on a block that has gone.
+__device__ __forceinline__ bool grid_sync(unsigned* sync, unsigned* err, unsigned nblocks,
+                                          unsigned limit) {
+  __syncthreads();
+  unsigned ok = 1;
+  if (threadIdx.x == 0) {
+    volatile unsigned* gen = sync + 1;
+    const unsigned g = *gen;
+    __threadfence();
+    if (atomicAdd(sync, 1u) == nblocks - 1) {
+      sync[0] = 0;
+      __threadfence();
+      atomicAdd(sync + 1, 1u);
+    } else {
+      unsigned it = 0;
+      while (*gen == g) {
+        if (++it > limit || *(volatile unsigned*)err) {
+          ok = 0;
+          break;
+        }
+        __nanosleep(32);
+      }
+    }
+    __threadfence();
+    if (!ok) atomicExch(err, 1u);
+  }
+  return __syncthreads_and(ok) != 0;
+}
+
 // 1 / sqrt(d) in FP64 from the FP32 hardware estimate and two Newton steps for the reciprocal
 // square root, y <- y (3 - d y^2) / 2, each of which doubles the number of correct bits
 // (about 22 -> 44 -> 88).  A few FP64 FMAs instead of an FP64 square root and division, which

@@ -84,30 +84,7 @@ __global__ void k_strength(int nbr, int b, const int* __restrict__ rp, const int
 constexpr unsigned MIS_WAIT_LIMIT = 1u << 24;
 
 __device__ __forceinline__ bool grid_barrier(unsigned* sync, unsigned nblocks) {
-  __syncthreads();
-  unsigned ok = 1;
-  if (threadIdx.x == 0) {
-    volatile unsigned* gen = sync + 1;
-    const unsigned g = *gen;
-    __threadfence();
-    if (atomicAdd(sync, 1u) == nblocks - 1) {
-      sync[0] = 0;
-      __threadfence();
-      atomicAdd(sync + 1, 1u);
-    } else {
-      unsigned it = 0;
-      while (*gen == g) {
-        if (++it > MIS_WAIT_LIMIT || *(volatile unsigned*)(sync + 4)) {
-          ok = 0;
-          break;
-        }
-        __nanosleep(64);
-      }
-    }
-    __threadfence();
-    if (!ok) atomicExch(sync + 4, 1u);
-  }
-  return __syncthreads_and(ok) != 0;
+  return grid_sync(sync, sync + 4, nblocks, MIS_WAIT_LIMIT);
 }
 
 __global__ void __launch_bounds__(256) k_mis2_loop(int n, int level, const int* __restrict__ srp,

@@ -285,184 +285,213 @@ __global__ void k_gemv(int n, const T* __restrict__ A, const T* __restrict__ b, 
   if (lane == 0) x[row] = s;
 }
 
-// Blocked right-looking Cholesky A = L L^T (lower, in place, row-major), block NB:
-//   k_potrf_diag  factor the diagonal block in shared memory and invert it (L_kk^-1 saved)
-//   k_panel       L_ik = A_ik L_kk^-T for the rows below
-//   k_syrk        A_ij -= L_ik L_jk^T on the trailing lower triangle (32 x 32 tiles)
-// then Y = L^-1 by right-looking blocked forward substitution (k_inv_row, k_inv_update) and
-// A^-1 = Y^T Y (k_ltl).
+// Inverse of the SPD coarsest-level matrix (Sec. 3.2: dense Cholesky factorisation at setup)
+// in one cooperative launch, FP64, blocks of NB = 32: the blocked right-looking Cholesky
+// A = L L^T, the block forward substitution Y = L^-1 (L Y = I), and A^-1 = Y^T Y.  Step b of
+// the factorisation has two phases, each closed by a grid barrier:
+//   1. every CTA factors the diagonal block L_bb and inverts it in its own shared memory (the
+//      same arithmetic on every CTA, so no barrier is spent on broadcasting it); then the rows
+//      below, L_ib = A_ib L_bb^-T, and the forward-substitution update of the row blocks
+//      i >= b with the previous step's solved block row, B_i -= L_i,b-1 X_b-1 (tiles j < b);
+//   2. the trailing lower triangle, A_ij -= L_ib L_jb^T (32 x 32 tiles), and the solved block
+//      row X_b = L_bb^-1 B_b (tiles j <= b).
+// A final phase forms Y^T Y (lower triangle, mirrored, so exactly symmetric).  Every entry is
+// summed in a fixed order (increasing inner index), independent of the grid.  Values written by
+// other CTAs are read past L1 (ld.global.cg).
 constexpr int NB = 32;
-
-// The diagonal block in shared memory, right-looking: at pivot k, column k of L and row k of
-// L_kk^-1 are scaled by 1 / sqrt(d_k), then the trailing lower triangle (s_ij -= l_ik l_jk) and
-// the rows of L_kk^-1 below k (x_ic -= l_ik x_kc) are updated.  The entries of each update are
-// packed onto consecutive threads (a table of the triangle's (row, column) offsets), so only
-// as many warps issue FP64 work as the step has entries, and the next pivot's 1 / sqrt is
-// taken by the thread that has just updated that diagonal entry: two block barriers per pivot.
+constexpr int INV_THREADS = 512;  // 16 warps: 16 rows of 32 columns per pass over a tile
+constexpr unsigned INV_WAIT_LIMIT = 1u << 24;
 constexpr int TRI = NB * (NB - 1) / 2;  // entries of the largest trailing triangle (k = 0)
-__global__ void __launch_bounds__(512) k_potrf_diag(int n, int k0, double* A, double* Linv,
-                                                    int* fail) {
-  __shared__ double s[NB][NB + 1];
-  __shared__ double li[NB][NB + 1];
-  __shared__ double rdiag[NB];
-  __shared__ unsigned char tri_r[TRI], tri_c[TRI];
+
+struct InvSmem {
+  double s[NB][NB + 1];   // the diagonal block, factored in place
+  double li[NB][NB + 1];  // its inverse L_bb^-1
+  double ta[NB][NB + 1], tb[NB][NB + 1];  // operand tiles
+  double rdiag[NB];
+  unsigned char tri_r[TRI], tri_c[TRI];  // (row, column) offsets of the packed triangle
+};
+
+// Factor the diagonal block at k0 in shared memory and invert it, right-looking: at pivot k,
+// column k of L and row k of L_kk^-1 are scaled by 1 / sqrt(d_k), then the trailing lower
+// triangle (s_ij -= l_ik l_jk) and the rows of L_kk^-1 below k (x_ic -= l_ik x_kc) are updated.
+// The entries of each update are packed onto consecutive threads, so only as many warps issue
+// FP64 work as the step has entries, and the next pivot's 1 / sqrt is taken by the thread that
+// has just updated that diagonal entry: two block barriers per pivot.  Rows and columns past n
+// are padded with the identity.
+__device__ void potrf_tile(int n, int k0, const double* A, InvSmem& m, int* fail) {
   const int t = threadIdx.x;
   const int kb = min(NB, n - k0);
   for (int e = t; e < NB * NB; e += blockDim.x) {
     const int r = e / NB, c = e % NB;
-    s[r][c] = (r < kb && c < kb) ? A[(int64_t)(k0 + r) * n + k0 + c] : (r == c ? 1.0 : 0.0);
-    li[r][c] = r == c ? 1.0 : 0.0;
-  }
-  for (int u = t; u < TRI; u += blockDim.x) {  // u = r (r + 1) / 2 + c, 0 <= c <= r
-    int r = 0;
-    while ((r + 1) * (r + 2) / 2 <= u) r++;
-    tri_r[u] = (unsigned char)r;
-    tri_c[u] = (unsigned char)(u - r * (r + 1) / 2);
+    m.s[r][c] = (r < kb && c < kb) ? __ldcg(A + (int64_t)(k0 + r) * n + k0 + c)
+                                   : (r == c ? 1.0 : 0.0);
+    m.li[r][c] = r == c ? 1.0 : 0.0;
   }
   __syncthreads();
   auto pivot = [&](int k) {
-    double d = s[k][k];
+    double d = m.s[k][k];
     if (!(d > 0.0)) {
       if (k < kb) atomicCAS(fail, 0, k0 + k + 1);
       d = 1.0;
     }
     const double y = rsqrt_newton(d);
-    s[k][k] = d * y;  // sqrt(d)
-    rdiag[k] = y;
+    m.s[k][k] = d * y;  // sqrt(d)
+    m.rdiag[k] = y;
   };
   if (t == 0) pivot(0);
   __syncthreads();
   for (int k = 0; k < NB; k++) {
-    const double y = rdiag[k];
-    if (t > k && t < NB) s[t][k] *= y;                     // column k of L
-    if (t >= NB && t - NB <= k && t < 2 * NB) li[k][t - NB] *= y;  // row k of L^-1
+    const double y = m.rdiag[k];
+    if (t > k && t < NB) m.s[t][k] *= y;                          // column k of L
+    if (t >= NB && t - NB <= k && t < 2 * NB) m.li[k][t - NB] *= y;  // row k of L^-1
     __syncthreads();
-    const int m = (NB - 1 - k) * (NB - k) / 2;
-    if (t < m) {
-      const int i = k + 1 + tri_r[t], j = k + 1 + tri_c[t];
-      s[i][j] -= s[i][k] * s[j][k];
+    const int cnt = (NB - 1 - k) * (NB - k) / 2;
+    if (t < cnt) {
+      const int i = k + 1 + m.tri_r[t], j = k + 1 + m.tri_c[t];
+      m.s[i][j] -= m.s[i][k] * m.s[j][k];
     }
     const int lc = (NB - 1 - k) * (k + 1);
     for (int u = t; u < lc; u += blockDim.x) {
       const int i = k + 1 + u / (k + 1), c = u % (k + 1);
-      li[i][c] -= s[i][k] * li[k][c];
+      m.li[i][c] -= m.s[i][k] * m.li[k][c];
     }
     // entry 0 of the trailing triangle is the next diagonal entry, just updated by thread 0
     if (t == 0 && k + 1 < NB) pivot(k + 1);
     __syncthreads();
   }
-  for (int e = t; e < NB * NB; e += blockDim.x) {
-    const int r = e / NB, c = e % NB;
-    if (r < kb && c < kb) A[(int64_t)(k0 + r) * n + k0 + c] = (c <= r) ? s[r][c] : 0.0;
-    Linv[e] = li[r][c];
-  }
 }
 
-// rows below the diagonal block: L_ik = A_ik L_kk^-T  (one row per threadIdx.y, NB columns)
-__global__ void __launch_bounds__(NB * 8) k_panel(int n, int k0, double* A, const double* Linv) {
-  __shared__ double row[8][NB];
-  __shared__ double li[NB][NB + 1];
-  const int tx = threadIdx.x, ty = threadIdx.y;
-  const int kb = min(NB, n - k0);
-  for (int t = ty; t < NB; t += 8) li[t][tx] = Linv[t * NB + tx];
-  const int i = k0 + kb + blockIdx.x * 8 + ty;
-  row[ty][tx] = (i < n && tx < kb) ? A[(int64_t)i * n + k0 + tx] : 0.0;
+__global__ void __launch_bounds__(INV_THREADS) k_spd_inverse(int n, double* A, double* Y,
+                                                             int* fail, unsigned* sync) {
+  __shared__ InvSmem m;
+  const int t = threadIdx.x, tx = t & 31, ty = t >> 5;
+  const int G = gridDim.x, bid = blockIdx.x;
+  const int nblk = (n + NB - 1) / NB;
+  for (int u = t; u < TRI; u += blockDim.x) {  // u = r (r + 1) / 2 + c, 0 <= c <= r
+    int r = 0;
+    while ((r + 1) * (r + 2) / 2 <= u) r++;
+    m.tri_r[u] = (unsigned char)r;
+    m.tri_c[u] = (unsigned char)(u - r * (r + 1) / 2);
+  }
+  for (int64_t e = (int64_t)bid * blockDim.x + t; e < (int64_t)n * n; e += (int64_t)G * blockDim.x)
+    Y[e] = (e / n == e % n) ? 1.0 : 0.0;  // the right-hand side B = I
   __syncthreads();
-  if (i >= n || tx >= kb) return;
-  double v = 0.0;
-  for (int t = 0; t <= tx; t++) v += row[ty][t] * li[tx][t];
-  A[(int64_t)i * n + k0 + tx] = v;
-}
 
-// trailing update of the lower triangle: A_ij -= sum_t L_it L_jt, t over the panel columns
-__global__ void __launch_bounds__(32 * 8) k_syrk(int n, int k0, double* A) {
-  __shared__ double Li[32][NB + 1];
-  __shared__ double Lj[32][NB + 1];
-  const int kb = min(NB, n - k0);
-  const int base = k0 + kb;
-  const int ti = blockIdx.y, tj = blockIdx.x;
-  if (tj > ti) return;  // tile entirely above the diagonal
-  const int i0 = base + ti * 32, j0 = base + tj * 32;
-  const int tx = threadIdx.x, ty = threadIdx.y;
-  for (int r = ty; r < 32; r += 8) {
-    const int gi = i0 + r, gj = j0 + r;
-    Li[r][tx] = (gi < n && tx < kb) ? A[(int64_t)gi * n + k0 + tx] : 0.0;
-    Lj[r][tx] = (gj < n && tx < kb) ? A[(int64_t)gj * n + k0 + tx] : 0.0;
-  }
-  __syncthreads();
-  for (int r = ty; r < 32; r += 8) {
-    const int gi = i0 + r, gj = j0 + tx;
-    if (gi >= n || gj >= n || gj > gi) continue;
-    double v = 0.0;
-    for (int t = 0; t < kb; t++) v += Li[r][t] * Lj[tx][t];
-    A[(int64_t)gi * n + gj] -= v;
-  }
-}
-
-// Y = L^-1 by right-looking block forward substitution on L Y = I, with Y holding the
-// right-hand side B = I at the start.  Step k: block row k becomes X_k = L_kk^-1 B_k (tiles
-// j <= k, k_inv_row), then every later block row is updated, B_i -= L_ik X_k (tiles i > k,
-// j <= k, k_inv_update).  Every tile is a 32 x 32 x 32 product on its own block, so a step
-// spreads over up to (K - k - 1)(k + 1) SMs instead of walking the rows one block at a time.
-__global__ void __launch_bounds__(256) k_inv_row(int n, int K0, const double* __restrict__ LinvKK,
-                                                 double* Y) {
-  __shared__ double Li[NB][NB + 1];
-  __shared__ double Bt[NB][NB + 1];
-  const int tx = threadIdx.x, ty = threadIdx.y;  // 32 x 8
-  const int kb = min(NB, n - K0);
-  const int c0 = blockIdx.x * NB;
-  for (int r = ty; r < NB; r += 8) {
-    Li[r][tx] = LinvKK[r * NB + tx];
-    const int c = c0 + tx;
-    Bt[r][tx] = (r < kb && c < n) ? Y[(int64_t)(K0 + r) * n + c] : 0.0;
-  }
-  __syncthreads();
-  for (int r = ty; r < kb; r += 8) {
-    const int c = c0 + tx;
-    double v = 0.0;
-    for (int t = 0; t <= r; t++) v += Li[r][t] * Bt[t][tx];
-    if (c < n) Y[(int64_t)(K0 + r) * n + c] = v;
-  }
-}
-
-__global__ void __launch_bounds__(256) k_inv_update(int n, int K0, const double* __restrict__ L,
-                                                    double* Y) {
-  __shared__ double Lt[NB][NB + 1];
-  __shared__ double Xt[NB][NB + 1];
-  const int tx = threadIdx.x, ty = threadIdx.y;  // 32 x 8
-  const int kb = min(NB, n - K0);
-  const int c0 = blockIdx.x * NB;
-  const int r0 = K0 + kb + blockIdx.y * NB;
-  for (int r = ty; r < NB; r += 8) {
-    const int gi = r0 + r, c = c0 + tx;
-    Lt[r][tx] = (gi < n && tx < kb) ? L[(int64_t)gi * n + K0 + tx] : 0.0;
-    Xt[r][tx] = (r < kb && c < n) ? Y[(int64_t)(K0 + r) * n + c] : 0.0;
-  }
-  __syncthreads();
-  for (int r = ty; r < NB; r += 8) {
-    const int gi = r0 + r, c = c0 + tx;
-    if (gi >= n || c >= n) continue;
-    double v = 0.0;
+  for (int b = 0; b < nblk; b++) {
+    const int k0 = b * NB, kb = min(NB, n - k0);
+    const int rest = n - k0 - kb;
+    // ---- phase 1: L_bb and L_bb^-1 (every CTA), the panel, the update with X_b-1
+    potrf_tile(n, k0, A, m, fail);
+    const int n_panel = (rest + 15) / 16;
+    const int n_upd = b * (nblk - b);  // tiles (i, j), i in [b, nblk), j in [0, b)
+    for (int u = bid; u < n_panel + n_upd; u += G) {
+      if (u < n_panel) {  // 16 rows, one per warp: L_ib = A_ib L_bb^-T
+        const int i = k0 + kb + u * 16 + ty;
+        const bool ok = i < n && tx < kb;
+        m.ta[ty][tx] = ok ? __ldcg(A + (int64_t)i * n + k0 + tx) : 0.0;
+        __syncwarp();
+        if (ok) {
+          double v = 0.0;
+          for (int q = 0; q <= tx; q++) v += m.ta[ty][q] * m.li[tx][q];
+          A[(int64_t)i * n + k0 + tx] = v;
+        }
+        __syncwarp();
+      } else {  // B_i -= L_i,b-1 X_b-1 on tile (i, j)
+        const int w = u - n_panel;
+        const int K0 = (b - 1) * NB, kbp = min(NB, n - K0);
+        const int r0 = (b + w / b) * NB, c0 = (w % b) * NB;
+        __syncthreads();
+        for (int r = ty; r < NB; r += 16) {
+          const int gi = r0 + r, c = c0 + tx;
+          m.ta[r][tx] = (gi < n && tx < kbp) ? __ldcg(A + (int64_t)gi * n + K0 + tx) : 0.0;
+          m.tb[r][tx] = (r < kbp && c < n) ? __ldcg(Y + (int64_t)(K0 + r) * n + c) : 0.0;
+        }
+        __syncthreads();
+        for (int r = ty; r < NB; r += 16) {
+          const int gi = r0 + r, c = c0 + tx;
+          if (gi >= n || c >= n) continue;
+          double v = 0.0;
 #pragma unroll 8
-    for (int t = 0; t < NB; t++) v += Lt[r][t] * Xt[t][tx];
-    Y[(int64_t)gi * n + c] -= v;
+          for (int q = 0; q < NB; q++) v += m.ta[r][q] * m.tb[q][tx];
+          const int64_t o = (int64_t)gi * n + c;
+          Y[o] = __ldcg(Y + o) - v;
+        }
+      }
+    }
+    if (!grid_sync(sync, sync + 2, G, INV_WAIT_LIMIT)) return;
+    // ---- phase 2: X_b = L_bb^-1 B_b, the trailing update
+    const int n_x = b + 1;  // tiles j <= b of block row b
+    const int nt = (rest + 31) / 32;
+    const int n_syrk = nt * (nt + 1) / 2;
+    for (int u = bid; u < n_x + n_syrk; u += G) {
+      __syncthreads();
+      if (u < n_x) {
+        const int c0 = u * NB;
+        for (int r = ty; r < NB; r += 16) {
+          const int c = c0 + tx;
+          m.ta[r][tx] = (r < kb && c < n) ? __ldcg(Y + (int64_t)(k0 + r) * n + c) : 0.0;
+        }
+        __syncthreads();
+        for (int r = ty; r < kb; r += 16) {
+          const int c = c0 + tx;
+          double v = 0.0;
+          for (int q = 0; q <= r; q++) v += m.li[r][q] * m.ta[q][tx];
+          if (c < n) Y[(int64_t)(k0 + r) * n + c] = v;
+        }
+      } else {  // tile (ti, tj), tj <= ti, of the trailing lower triangle
+        const int w = u - n_x;
+        int ti = 0;
+        while ((ti + 1) * (ti + 2) / 2 <= w) ti++;
+        const int tj = w - ti * (ti + 1) / 2;
+        const int i0 = k0 + kb + ti * 32, j0 = k0 + kb + tj * 32;
+        for (int r = ty; r < 32; r += 16) {
+          const int gi = i0 + r, gj = j0 + r;
+          m.ta[r][tx] = (gi < n && tx < kb) ? __ldcg(A + (int64_t)gi * n + k0 + tx) : 0.0;
+          m.tb[r][tx] = (gj < n && tx < kb) ? __ldcg(A + (int64_t)gj * n + k0 + tx) : 0.0;
+        }
+        __syncthreads();
+        for (int r = ty; r < 32; r += 16) {
+          const int gi = i0 + r, gj = j0 + tx;
+          if (gi >= n || gj >= n || gj > gi) continue;
+          double v = 0.0;
+          for (int q = 0; q < kb; q++) v += m.ta[r][q] * m.tb[tx][q];
+          const int64_t o = (int64_t)gi * n + gj;
+          A[o] = __ldcg(A + o) - v;
+        }
+      }
+    }
+    if (!grid_sync(sync, sync + 2, G, INV_WAIT_LIMIT)) return;
   }
-}
 
-__global__ void k_eye(int n, double* Y) {
-  const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (t < (int64_t)n * n) Y[t] = (t / n == t % n) ? 1.0 : 0.0;
-}
-
-// Ainv = Linv^T Linv, computed for i >= j and mirrored (exactly symmetric)
-__global__ void k_ltl(int n, const double* __restrict__ Li, double* Ainv) {
-  const int i = blockIdx.y * blockDim.y + threadIdx.y;
-  const int j = blockIdx.x * blockDim.x + threadIdx.x;
-  if (i >= n || j > i) return;
-  double v = 0.0;
-  for (int t = i; t < n; t++) v += Li[(int64_t)t * n + i] * Li[(int64_t)t * n + j];
-  Ainv[(int64_t)i * n + j] = v;
-  Ainv[(int64_t)j * n + i] = v;
+  // ---- A^-1 = Y^T Y: entry (i, j), j <= i, sums Y_ti Y_tj over t = i .. n - 1 in order.
+  // Tiles of 16 rows i x 32 columns j; Y is staged 32 rows t at a time.
+  const int nti = (n + 15) / 16, ntj = (n + 31) / 32;
+  for (int u = bid; u < nti * ntj; u += G) {
+    const int i0 = (u / ntj) * 16, j0 = (u % ntj) * 32;
+    if (j0 > i0 + 15) continue;  // above the diagonal (uniform over the CTA)
+    const int i = i0 + ty, j = j0 + tx;
+    double v = 0.0;
+    for (int tc = i0; tc < n; tc += 32) {
+      __syncthreads();
+      {
+        const int q = t >> 4, c = t & 15;  // 32 rows x 16 columns i
+        m.ta[q][c] = (tc + q < n && i0 + c < n) ? __ldcg(Y + (int64_t)(tc + q) * n + i0 + c) : 0.0;
+      }
+      for (int e = t; e < 32 * 32; e += blockDim.x) {
+        const int q = e >> 5, c = e & 31;
+        m.tb[q][c] = (tc + q < n && j0 + c < n) ? __ldcg(Y + (int64_t)(tc + q) * n + j0 + c) : 0.0;
+      }
+      __syncthreads();
+      if (i < n && j <= i) {
+        const int q0 = max(0, i - tc), q1 = min(32, n - tc);
+        for (int q = q0; q < q1; q++) v += m.ta[q][ty] * m.tb[q][tx];
+      }
+    }
+    if (i < n && j <= i) {
+      A[(int64_t)i * n + j] = v;
+      A[(int64_t)j * n + i] = v;
+    }
+  }
 }
 
 inline int grid_for(int64_t n) {
@@ -573,42 +602,42 @@ template void dense_gemv<double>(cudaStream_t, int, const double*, const double*
 
 int dense_spd_inverse(cudaStream_t s, int n, double* A, double* work) {
   SetupTrace tr(s);
-  double* Y = work;  // n x n
+  if (n <= 0) return 0;
+  // one cooperative launch, every CTA resident
+  static int per_sm = 0;
+  if (per_sm == 0)
+    CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_spd_inverse, INV_THREADS, 0));
   const int nblk = ceil_div(n, NB);
+  const int work_items = std::max(nblk * (nblk + 1) / 2, ceil_div(n, 16) * ceil_div(n, 32) / 2);
+  // one CTA per SM at most: every CTA factors the diagonal block itself, and two on one SM
+  // would share its FP64 pipe on that critical path
+  if (per_sm < 1) TOMG_THROW(TOMG_E_CUDA, "coarse inverse kernel cannot be resident");
+  const int grid = std::max(1, std::min(num_sms(), work_items));
   DBuf<int> fail;
-  DBuf<double> linv;
+  DBuf<unsigned> sync;  // arrivals, generation, error
   fail.resize(1);
+  sync.resize(3);
   fail.zero(s);
-  linv.resize((size_t)nblk * NB * NB);
-  for (int b = 0; b < nblk; b++) {
-    const int k0 = b * NB;
-    double* Lb = linv.p + (size_t)b * NB * NB;
-    LAUNCH(k_potrf_diag, 1, 512, 0, s, n, k0, A, Lb, fail.p);
-    const int rest = n - k0 - std::min(NB, n - k0);
-    if (rest > 0) {
-      LAUNCH(k_panel, ceil_div(rest, 8), dim3(NB, 8), 0, s, n, k0, A, Lb);
-      const int nt = ceil_div(rest, 32);
-      LAUNCH(k_syrk, dim3(nt, nt), dim3(32, 8), 0, s, n, k0, A);
-    }
-  }
+  sync.zero(s);
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3(grid);
+  cfg.blockDim = dim3(INV_THREADS);
+  cfg.stream = s;
+  cudaLaunchAttribute at[1];
+  at[0].id = cudaLaunchAttributeCooperative;
+  at[0].val.cooperative = 1;
+  cfg.attrs = at;
+  cfg.numAttrs = 1;
+  CK(cudaLaunchKernelEx(&cfg, k_spd_inverse, n, A, work, fail.p, sync.p));
+  g_launches++;
   int f = 0;
+  unsigned err = 0;
   CK(cudaMemcpyAsync(&f, fail.p, sizeof(int), cudaMemcpyDeviceToHost, s));
+  CK(cudaMemcpyAsync(&err, sync.p + 2, sizeof(unsigned), cudaMemcpyDeviceToHost, s));
   CK(cudaStreamSynchronize(s));
-  tr.mark("  cholesky");
-  if (f) return f;
-  LAUNCH(k_eye, ceil_div((int64_t)n * n, 256), 256, 0, s, n, Y);
-  for (int b = 0; b < nblk; b++) {
-    const int K0 = b * NB, kb = std::min(NB, n - K0);
-    LAUNCH(k_inv_row, b + 1, dim3(32, 8), 0, s, n, K0, linv.p + (size_t)b * NB * NB, Y);
-    const int below = ceil_div(n - K0 - kb, NB);
-    if (below > 0) LAUNCH(k_inv_update, dim3(b + 1, below), dim3(32, 8), 0, s, n, K0, A, Y);
-  }
-  tr.mark("  triangular inverse");
-  dim3 blk(16, 16), grd(ceil_div(n, 16), ceil_div(n, 16));
-  LAUNCH(k_ltl, grd, blk, 0, s, n, Y, A);
-  CK(cudaStreamSynchronize(s));
-  tr.mark("  L^-T L^-1");
-  return 0;
+  tr.mark("  cholesky + inverse");
+  if (err) TOMG_THROW(TOMG_E_TIMEOUT, "coarse inverse: a grid barrier wait ran out");
+  return f;
 }
 
 

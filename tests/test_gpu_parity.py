@@ -182,6 +182,26 @@ def test_vcycle(lib, ctx, pc, kw, dim, grid):
     assert relerr(P.coarse_solve(bc), np.linalg.solve(H.A[-1].toarray(), bc)) < 1e-8
 
 
+@pytest.mark.gpu
+@pytest.mark.parametrize("dim,grid", [(2, (64, 32, 1)), (3, (12, 8, 10))])
+def test_coarse_inverse_many_blocks(lib, ctx, dim, grid):
+    """Coarsest-level direct solve (Sec. 3.2: dense Cholesky factorisation at setup) on a
+    coarse matrix of many 32-wide blocks with a ragged last block (1,122 and 630 DOFs): more
+    trailing tiles and more tiles of Y^T Y than the GPU has SMs, so every phase of the one
+    cooperative launch strides over its tiles."""
+    p = W.random_problem(dim, *grid, seed=21, contrast="minmax")
+    p.rho[:] = 0.5 + 0.5 * p.rho  # moduli within a factor of 8: the dense solve is well posed
+    P = make(lib, ctx, p)
+    P.setup(pc="gmg", prec="fp64", n_levels=2)
+    H = osolve.build(p, pc="gmg", n_levels=2)
+    Ac = H.A[-1].toarray()
+    nc = Ac.shape[0]
+    assert nc > 32 * 16 and nc % 32 != 0
+    B = np.random.default_rng(3).standard_normal((3, nc))
+    for bc in B:
+        assert relerr(P.coarse_solve(bc), np.linalg.solve(Ac, bc)) < 1e-9
+
+
 @pytest.mark.parametrize("dim,grid", [(2, (30, 14, 1)), (2, (45, 21, 1)), (3, (8, 6, 5))])
 def test_amg_setup_parity(lib, ctx, dim, grid):
     p = W.random_problem(dim, *grid, seed=14, contrast="threshold")
