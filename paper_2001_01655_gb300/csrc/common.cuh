@@ -270,6 +270,40 @@ __device__ __forceinline__ bool grid_sync(unsigned* sync, unsigned* err, unsigne
   return __syncthreads_and(ok) != 0;
 }
 
+// FP32 <-> FP64 conversions by integer operations on the bit patterns, for the vector kernels
+// of the outer loop: there the conversion instructions share GB300's narrow FP64 pipe with the
+// dot products.  Both are exact restatements of IEEE 754 binary32 / binary64 conversion (round
+// to nearest even on the way down) for zeros and normal numbers; subnormals, infinities and
+// NaNs take the hardware conversion, in a function of its own, so that the compiler cannot
+// replace the branch by computing both and selecting (which would put the conversion
+// instruction back on every element).
+static __device__ __noinline__ double f2d_hw(float f) { return (double)f; }
+static __device__ __noinline__ float d2f_hw(double x) { return (float)x; }
+__device__ __forceinline__ double f2d_bits(float f) {
+  const uint32_t u = __float_as_uint(f);
+  const uint32_t e = (u >> 23) & 0xffu;
+  const uint64_t sign = (uint64_t)(u & 0x80000000u) << 32;
+  if (e == 0u && (u & 0x7fffffu) == 0u) return __longlong_as_double((long long)sign);
+  if (e == 0u || e == 0xffu) return f2d_hw(f);
+  // exponent bias 127 -> 1023, the 23 fraction bits at the top of the 52
+  return __longlong_as_double(
+      (long long)(sign | ((uint64_t)(e + 896u) << 52) | ((uint64_t)(u & 0x7fffffu) << 29)));
+}
+__device__ __forceinline__ float d2f_bits(double x) {
+  const uint64_t b = (uint64_t)__double_as_longlong(x);
+  const uint32_t sign = (uint32_t)(b >> 32) & 0x80000000u;
+  if ((b << 1) == 0u) return __uint_as_float(sign);
+  const int e = (int)((b >> 52) & 0x7ffu) - 896;  // binary32 biased exponent
+  if (e < 1 || e > 254) return d2f_hw(x);          // subnormal or out of range, inf, NaN
+  const uint64_t m = b & 0xfffffffffffffull;
+  uint32_t u = sign | ((uint32_t)e << 23) | (uint32_t)(m >> 29);
+  const uint32_t rest = (uint32_t)(m & 0x1fffffffu);  // the 29 dropped fraction bits
+  // round to nearest, ties to even; a carry out of the fraction raises the exponent, which is
+  // the correctly rounded result (up to infinity from the largest exponent)
+  if (rest > 0x10000000u || (rest == 0x10000000u && (u & 1u))) u += 1u;
+  return __uint_as_float(u);
+}
+
 // 1 / sqrt(d) in FP64 from the FP32 hardware estimate and two Newton steps for the reciprocal
 // square root, y <- y (3 - d y^2) / 2, each of which doubles the number of correct bits
 // (about 22 -> 44 -> 88).  A few FP64 FMAs instead of an FP64 square root and division, which

@@ -414,10 +414,6 @@ __global__ void k_sumsq_partials(int64_t n, const double* __restrict__ v, double
   const double tot = block_sum(ss, sred);
   if (threadIdx.x == 0) partials[blockIdx.x] = tot;
 }
-__global__ void k_scale(int64_t n, double* v, double s) {
-  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (i < n) v[i] *= s;
-}
 
 // P = T - omega D^-1 (A T), row block i of P by one warp: the lanes take the scalars of the
 // row's blocks in turn (block p, row r, column c), each the same b-term sum as a serial loop

@@ -15,6 +15,27 @@ namespace tomg {
 
 namespace {
 
+// One stored block (NE values) into registers.  Neighbouring lanes read different blocks, so
+// each load instruction touches one cache line per lane: where a block is a whole number of
+// 16-byte words (6 x 6 in FP32 or FP64, 2 x 2) it is read in 16-byte words, four times fewer
+// instructions and L1 lookups than scalar loads.  Blocks are contiguous from a 256-byte
+// aligned base, so block p starts on a 16-byte boundary whenever its size is a multiple of 16.
+template <int NE, class T>
+__device__ __forceinline__ void load_block(const T* __restrict__ blk, T* v) {
+  if constexpr ((NE * sizeof(T)) % 16 == 0) {
+    constexpr int W = 16 / sizeof(T);
+    const float4* q = reinterpret_cast<const float4*>(blk);
+#pragma unroll
+    for (int k = 0; k < NE / W; k++) {
+      const float4 w = __ldg(q + k);
+      memcpy(v + W * k, &w, 16);
+    }
+  } else {
+#pragma unroll
+    for (int t = 0; t < NE; t++) v[t] = blk[t];
+  }
+}
+
 // G lanes cooperate on one block row (strided over its blocks), partial sums combined with a
 // fixed butterfly, so the result does not depend on scheduling.
 template <int G, class T, int B>
@@ -55,8 +76,7 @@ __global__ void __launch_bounds__(256) k_bsr(int nbr, const int* __restrict__ rp
     pend = rp[i + 1];
     if (p < pend) {
       j0 = ci[p];
-#pragma unroll
-      for (int t = 0; t < B * B; t++) blk0[t] = V[(int64_t)p * B * B + t];
+      load_block<B * B>(V + (int64_t)p * B * B, blk0);
     }
     if (NEED_D && sub == 0) {
 #pragma unroll
@@ -90,7 +110,8 @@ __global__ void __launch_bounds__(256) k_bsr(int nbr, const int* __restrict__ rp
     }
     for (; p < pend; p += G) {
       const int j = ci[p];
-      const T* blk = V + (int64_t)p * B * B;
+      T blk[B * B];
+      load_block<B * B>(V + (int64_t)p * B * B, blk);
       T xv[B];
       if (MODE == MODE_RESID0) {
         jacobi_first<T, B>(Dinv, b, j, omega, xv);
@@ -171,8 +192,7 @@ __global__ void __launch_bounds__(256) k_bsr_rect(int nbr, int nbc, const int* _
     pend = rp[i + 1];
     if (p < pend) {
       j0 = ci[p];
-#pragma unroll
-      for (int t = 0; t < BR * BC; t++) blk0[t] = V[(int64_t)p * BR * BC + t];
+      load_block<BR * BC>(V + (int64_t)p * BR * BC, blk0);
     }
   }
   pdl_wait();
@@ -189,7 +209,8 @@ __global__ void __launch_bounds__(256) k_bsr_rect(int nbr, int nbc, const int* _
     }
     for (p += G; p < pend; p += G) {
       const int j = ci[p];
-      const T* blk = V + (int64_t)p * BR * BC;
+      T blk[BR * BC];
+      load_block<BR * BC>(V + (int64_t)p * BR * BC, blk);
 #pragma unroll
       for (int c = 0; c < BC; c++) {
         const T xv = x[(int64_t)BC * j + c];
@@ -575,6 +596,7 @@ void scan_rec(cudaStream_t s, const int* in, int* out, int64_t n, int* total_dev
 template <class T>
 void bsr_op(cudaStream_t s, int mode, const Bsr& A, const T* V, const T* x, T* y, const T* b,
             const T* Dinv, double omega, const int* done, const ChebArg* ch) {
+  if (reinterpret_cast<uintptr_t>(V) % 16) TOMG_THROW(TOMG_E_INVALID, "block values not 16-byte aligned");
   const int G = lanes_for(A);
   const dim3 grid(ceil_div((int64_t)A.nbr * G, 256), batch_rhs());
   const bool cheb = mode == MODE_CHEB || mode == MODE_CHEB0;
@@ -612,6 +634,7 @@ template void bsr_op<double>(cudaStream_t, int, const Bsr&, const double*, const
 template <class T>
 void bsr_spmv_rect(cudaStream_t s, const Bsr& A, const T* V, const T* x, T* y, int accumulate,
                    const int* done) {
+  if (reinterpret_cast<uintptr_t>(V) % 16) TOMG_THROW(TOMG_E_INVALID, "block values not 16-byte aligned");
   const int G = lanes_for(A);
   const dim3 grid(ceil_div((int64_t)A.nbr * G, 256), batch_rhs());
 #define RL(R, C, GG) LAUNCH((k_bsr_rect<T, R, C, GG>), grid, 256, 0, s, A.nbr, A.nbc, A.rp, A.ci, V, x, y, accumulate, done)

@@ -44,7 +44,6 @@ namespace {
 
 constexpr int TEX = 32, TY = 4;              // elements of a layer tile in x and y
 constexpr int TNX = TEX + 1, TNY = TY + 1;   // nodes of a layer tile
-constexpr int ONX = TEX - 1, ONY = TY - 1;   // owned nodes per layer
 constexpr int ROWS = TEX * TY;               // 128 element rows: the tensor-memory lanes
 constexpr int NT = 2 * ROWS;                 // two threads per element row (bottom, top half)
 constexpr int LAYER_NODES = TNX * TNY;       // 165
@@ -156,13 +155,10 @@ __device__ __forceinline__ void tmem_st8(uint32_t taddr, const uint32_t* v) {
       : "memory");
 }
 
-// an integer |v| < 2^22 as an exact FP32 value, and back (rounding-free: the magic constant
-// 1.5 x 2^23 puts v in the last place of the significand)
+// an integer |v| < 2^22 as an exact FP32 value (rounding-free: the magic constant 1.5 x 2^23
+// puts v in the last place of the significand)
 __device__ __forceinline__ float int_to_f32(int v) {
   return __int_as_float(0x4B400000 + v) - 12582912.0f;
-}
-__device__ __forceinline__ int f32_to_int(float f) {
-  return __float_as_int(f + 12582912.0f) - 0x4B400000;
 }
 
 // node layer kk of the tile (FP64): values and mask bits of one node per thread

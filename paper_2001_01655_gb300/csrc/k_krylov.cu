@@ -18,7 +18,9 @@ constexpr int RED_MAX_BLOCKS = 2432;  // 16 blocks per SM on the 152-SM GB300
 
 // Vector kernels walk the DOFs in pairs (16-byte loads of FP64 vectors), one pair per thread
 // when the grid allows it, so every load of a thread is issued at once; an odd last DOF is
-// handled by the thread of pair index n / 2.
+// handled by the thread of pair index n / 2.  Each thread's share of a dot product is one chain
+// of FMAs in DOF order, written out so that the rounding does not depend on how the compiler
+// contracts a sum of two products (and two FP64 instructions per pair instead of three).
 template <class T> struct P2;
 template <> struct P2<double> { using type = double2; };
 template <> struct P2<float> { using type = float2; };
@@ -44,7 +46,7 @@ __global__ void __launch_bounds__(RED_THREADS) k_dot(const double* __restrict__ 
   const int64_t np = (n + 1) / 2;
   for (int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; k < np; k += (int64_t)gridDim.x * blockDim.x) {
     const double2 a = ld2(x, k, n), b = ld2(y, k, n);
-    s += a.x * b.x + a.y * b.y;
+    s = fma(a.y, b.y, fma(a.x, b.x, s));
   }
   s = block_sum(s, sred);
   if (threadIdx.x == 0) partials[blockIdx.x] = s;
@@ -90,13 +92,13 @@ __global__ void __launch_bounds__(RED_THREADS) k_xr(double* __restrict__ x, doub
     if (2 * k + 1 < n) {
       reinterpret_cast<double2*>(x)[k] = make_double2(x0, x1);
       reinterpret_cast<double2*>(r)[k] = make_double2(r0, r1);
-      if (r32) reinterpret_cast<float2*>(r32)[k] = make_float2((float)r0, (float)r1);
-      s += r0 * r0 + r1 * r1;
+      if (r32) reinterpret_cast<float2*>(r32)[k] = make_float2(d2f_bits(r0), d2f_bits(r1));
+      s = fma(r1, r1, fma(r0, r0, s));
     } else {
       x[2 * k] = x0;
       r[2 * k] = r0;
-      if (r32) r32[2 * k] = (float)r0;
-      s += r0 * r0;
+      if (r32) r32[2 * k] = d2f_bits(r0);
+      s = fma(r0, r0, s);
     }
   }
   s = block_sum(s, sred);
@@ -126,6 +128,9 @@ __global__ void k_p(double* __restrict__ p, const double* __restrict__ z, int64_
   }
 }
 
+__device__ __forceinline__ double to_f64(float v) { return f2d_bits(v); }
+__device__ __forceinline__ double to_f64(double v) { return v; }
+
 template <class T>
 __global__ void __launch_bounds__(RED_THREADS) k_zdots(const T* __restrict__ z, double* z64,
                                                        const double* __restrict__ r,
@@ -150,16 +155,16 @@ __global__ void __launch_bounds__(RED_THREADS) k_zdots(const T* __restrict__ z, 
   const int64_t np = (n + 1) / 2;
   for (int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; k < np; k += (int64_t)gridDim.x * blockDim.x) {
     const auto zv = ld2(z, k, n);
-    const double z0 = (double)zv.x, z1 = (double)zv.y;
+    const double z0 = to_f64(zv.x), z1 = to_f64(zv.y);
     const double2 rv = ld2(r, k, n);
     if (copy) {
       if (2 * k + 1 < n) reinterpret_cast<double2*>(z64)[k] = make_double2(z0, z1);
       else z64[2 * k] = z0;
     }
-    a += z0 * rv.x + z1 * rv.y;
+    a = fma(z1, rv.y, fma(z0, rv.x, a));
     if (q) {
       const double2 qv = ld2(q, k, n);
-      b += z0 * qv.x + z1 * qv.y;
+      b = fma(z1, qv.y, fma(z0, qv.x, b));
     }
   }
   a = block_sum(a, sred);
