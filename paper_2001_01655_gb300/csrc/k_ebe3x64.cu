@@ -504,6 +504,7 @@ k_ebe3x64_tiles(int nx, int ny, int nz, int nz_tile, int nzc, const uint4* __res
 // in ascending tile order, then the outer operator's finishing: A x = x on fixed DOFs, y = A x
 // with the partials of x . y and FIN_ALPHA in the last block (MODE_APPLY), or y = b - A x.
 constexpr int FIN_THREADS = 256;
+constexpr int FIN_NPT = 4;  // nodes per thread: one block reduction of the dot per 1024 nodes
 constexpr int X64_NZ_TILE = 8;  // element layers per tile
 
 __device__ __forceinline__ int tiles_of(int i, int n_t, int w, int* t0) {
@@ -541,15 +542,17 @@ k_ebe3x64_nodes(int nx, int ny, int nz, int gx, int gy, int nzc,
   }
   if (solve_done(done)) return;
   double dotv = 0.0;
-  const int64_t node = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (node < nn) {
+  for (int r = 0; r < FIN_NPT; r++) {  // FIN_NPT nodes per thread, FIN_THREADS apart
+    const int64_t node = ((int64_t)blockIdx.x * FIN_NPT + r) * FIN_THREADS + threadIdx.x;
+    if (node >= nn) break;
     int i, j, k;
     node_ijk(node, nx, ny, 3, i, j, k);
     int tx, ty, tz;
     const int cx = tiles_of(i, gx, TEX, &tx), cy = tiles_of(j, gy, TY, &ty);
     const int cz = tiles_of(k, nzc, nz_tile, &tz);
-    double acc[3] = {0.0, 0.0, 0.0};
-    // fixed trip counts (the absent second tiles of an axis are skipped by predicate)
+    // the first tile's partial starts the sum; the others are added in a fixed order (fixed
+    // trip counts, the absent second tiles of an axis skipped by predicate)
+    double acc[3];
 #pragma unroll
     for (int a = 0; a < 2; a++)
 #pragma unroll
@@ -562,7 +565,10 @@ k_ebe3x64_nodes(int nx, int ny, int nz, int gx, int gy, int nzc,
           const int slot = ((k - bz * nz_tile) * TNY + (j - by * TY)) * TNX + (i - bx * TEX);
           const double* pp = pbuf + (t * slots + slot) * 3;
 #pragma unroll
-          for (int q = 0; q < 3; q++) acc[q] += __ldg(pp + q);
+          for (int q = 0; q < 3; q++) {
+            const double v = __ldg(pp + q);
+            acc[q] = (a | bb | d) ? acc[q] + v : v;
+          }
         }
     const unsigned m = mask[node];
     double xv[3], Ax[3];
@@ -575,7 +581,7 @@ k_ebe3x64_nodes(int nx, int ny, int nz, int gx, int gy, int nzc,
 #pragma unroll
       for (int q = 0; q < 3; q++) {
         y[3 * node + q] = Ax[q];
-        dotv += xv[q] * Ax[q];
+        dotv = fma(xv[q], Ax[q], dotv);
       }
     } else {
 #pragma unroll
@@ -620,7 +626,7 @@ void launch(cudaStream_t s, const Ebe& op, const void* Bimg, double c, const dou
          reinterpret_cast<const uint4*>(Bimg), (const double*)op.E, c, op.mask, x, pbuf, done,
          sc);
   const int64_t nn = (int64_t)(op.nx + 1) * (op.ny + 1) * (op.nz + 1);
-  LAUNCH((k_ebe3x64_nodes<MODE, X64_NZ_TILE>), dim3(ceil_div(nn, FIN_THREADS), batch_rhs()),
+  LAUNCH((k_ebe3x64_nodes<MODE, X64_NZ_TILE>), dim3(ceil_div(nn, FIN_THREADS * FIN_NPT), batch_rhs()),
          FIN_THREADS, 0, s, op.nx, op.ny, op.nz, g.gx, g.gy, g.nzc, (const double*)pbuf, op.mask,
          x, y, b, done, partials, sc);
 }
@@ -670,7 +676,7 @@ bool ebe3x_operand(double nu, uint32_t* img, double* c) {
 int ebe3x_operand_words() { return B_BYTES / 4; }
 
 int ebe3x_blocks(const Ebe& op) {
-  return ceil_div((int64_t)(op.nx + 1) * (op.ny + 1) * (op.nz + 1), FIN_THREADS);
+  return ceil_div((int64_t)(op.nx + 1) * (op.ny + 1) * (op.nz + 1), FIN_THREADS * FIN_NPT);
 }
 
 int64_t ebe3x_buffer_doubles(const Ebe& op) {

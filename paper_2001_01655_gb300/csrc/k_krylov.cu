@@ -14,7 +14,9 @@ namespace tomg {
 namespace {
 
 constexpr int RED_THREADS = 256;
-constexpr int RED_MAX_BLOCKS = 2432;  // 16 blocks per SM on the 152-SM GB300
+// one full wave (8 resident blocks of 256 threads per SM on the 152-SM GB300): twice the
+// elements per thread of two waves, so the block reductions take half the FP64 share
+constexpr int RED_MAX_BLOCKS = 1216;
 
 // Vector kernels walk the DOFs in pairs (16-byte loads of FP64 vectors), one pair per thread
 // when the grid allows it, so every load of a thread is issued at once; an odd last DOF is
