@@ -640,20 +640,97 @@ __global__ void k_dinv_scale(int64_t nodes, const double* __restrict__ Dinv,
   }
 }
 
+// FP32 step of the power iteration on a geometric level: w = scale Dinv32 t (B x B blocks),
+// scale = 1/||u|| of the previous step read from the device, and ||w|| with 1/||w|| formed by
+// the last block (per-thread sums of squares in FP32, combined in FP64 in a fixed order)
+template <int B>
+__global__ void __launch_bounds__(256) k_dinv_scale32(int64_t nodes, const float* __restrict__ Dinv,
+                                                      const float* __restrict__ t,
+                                                      const double* __restrict__ scale,
+                                                      float* __restrict__ w, double* partials,
+                                                      double* out, unsigned* ticket) {
+  __shared__ double sred[32];
+  const float sc = (float)*scale;
+  float ss = 0.f;
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < nodes;
+       i += (int64_t)gridDim.x * blockDim.x) {
+    const float* D = Dinv + (int64_t)B * B * i;
+    float tv[B];
+#pragma unroll
+    for (int c = 0; c < B; c++) tv[c] = t[B * i + c];
+#pragma unroll
+    for (int q = 0; q < B; q++) {
+      float v = 0.f;
+#pragma unroll
+      for (int c = 0; c < B; c++) v = fmaf(D[q * B + c], tv[c], v);
+      const float wv = sc * v;
+      w[B * i + q] = wv;
+      ss = fmaf(wv, wv, ss);
+    }
+  }
+  const double tot = block_sum((double)ss, sred);
+  if (threadIdx.x == 0) partials[blockIdx.x] = tot;
+  if (last_block(ticket, gridDim.x)) {
+    double a = 0.0;
+    for (int q = threadIdx.x; q < (int)gridDim.x; q += blockDim.x) a += __ldcg(partials + q);
+    a = block_sum(a, sred);
+    if (threadIdx.x == 0) {
+      const double nrm = sqrt(a);
+      out[0] = nrm;
+      out[1] = nrm > 0.0 ? 1.0 / nrm : 0.0;
+    }
+  }
+}
+
 void splitmix_uniform(cudaStream_t s, int64_t n, int level, double* v) {
   LAUNCH(k_power_init, ceil_div(n, 256), 256, 0, s, n, level, v);
 }
 
-void power_alloc(PowerState& ps, int64_t nodes, int bs, int iters) {
+constexpr int PW32_BLOCKS = 1216;  // one full wave of 256-thread blocks on the 152-SM GB300
+
+void power_alloc(PowerState& ps, int64_t nodes, int bs, int iters, bool f32) {
   const int64_t n = nodes * bs;
   ps.nodes = nodes;
   ps.bs = bs;
   ps.iters = iters;
   ps.v.resize(n);
-  ps.w.resize(n);
-  ps.t.resize(n);
-  ps.parts.resize(256);
+  if (f32) {
+    ps.v32.resize(n);
+    ps.w32.resize(n);
+    ps.t32.resize(n);
+    ps.ticket.resize(1);
+    ps.ticket.zero(alloc_stream());
+  } else {
+    ps.w.resize(n);
+    ps.t.resize(n);
+  }
+  ps.parts.resize(std::max(256, PW32_BLOCKS));
   ps.nrm.resize(2 * (iters + 1));
+}
+
+void power_enqueue_f32(cudaStream_t s, PowerState& ps, const float* Dinv32, int level,
+                       const std::function<void(const float*, float*)>& apply) {
+  // u_0 = the FP64 path's splitmix64 vector rounded to FP32; w = (1/||u_it||) D^-1 A u_it,
+  // rho_it = ||w||, u_{it+1} = w, all vectors in FP32
+  const int64_t nodes = ps.nodes, n = nodes * ps.bs;
+  const int gp = 256;
+  LAUNCH(k_power_init, ceil_div(n, 256), 256, 0, s, n, level, ps.v.p);
+  LAUNCH(k_sumsq_partials, gp, 256, 0, s, n, ps.v.p, ps.parts.p);
+  LAUNCH(k_norm_finish, 1, 256, 0, s, ps.parts.p, gp, ps.nrm.p);
+  cast_f64_f32(s, ps.v.p, ps.v32.p, n);
+  float* a = ps.v32.p;
+  float* c = ps.w32.p;
+  const int g = std::max(1, std::min(PW32_BLOCKS, ceil_div(nodes, 256)));
+  for (int it = 0; it < ps.iters; it++) {
+    apply(a, ps.t32.p);
+    const double* sc = ps.nrm.p + 2 * it + 1;
+    double* o = ps.nrm.p + 2 * (it + 1);
+    if (ps.bs == 2) LAUNCH(k_dinv_scale32<2>, g, 256, 0, s, nodes, Dinv32, ps.t32.p, sc, c, ps.parts.p, o, ps.ticket.p);
+    else if (ps.bs == 3) LAUNCH(k_dinv_scale32<3>, g, 256, 0, s, nodes, Dinv32, ps.t32.p, sc, c, ps.parts.p, o, ps.ticket.p);
+    else if (ps.bs == 6) LAUNCH(k_dinv_scale32<6>, g, 256, 0, s, nodes, Dinv32, ps.t32.p, sc, c, ps.parts.p, o, ps.ticket.p);
+    else TOMG_THROW(TOMG_E_INVALID, "unsupported block %d", ps.bs);
+    std::swap(a, c);
+  }
 }
 
 void power_enqueue(cudaStream_t s, PowerState& ps, const double* Dinv, int level,

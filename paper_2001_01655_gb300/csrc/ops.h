@@ -273,12 +273,18 @@ double spectral_radius_op(cudaStream_t s, int64_t nodes, int bs, const double* D
 // s), power_result (copies rho back on s and synchronises s)
 struct PowerState {
   DBuf<double> v, w, t, parts, nrm;
+  DBuf<float> v32, w32, t32;  // iteration vectors of the FP32 variant
+  DBuf<unsigned> ticket;
   int64_t nodes = 0;
   int bs = 0, iters = 0;
 };
-void power_alloc(PowerState& ps, int64_t nodes, int bs, int iters);
+void power_alloc(PowerState& ps, int64_t nodes, int bs, int iters, bool f32 = false);
 void power_enqueue(cudaStream_t s, PowerState& ps, const double* Dinv, int level,
                    const std::function<void(const double*, double*)>& apply);
+// the same iteration with FP32 vectors, operator and block inverses (Dinv32), for the
+// Chebyshev interval of a mixed-precision cycle; norms accumulated and kept in FP64
+void power_enqueue_f32(cudaStream_t s, PowerState& ps, const float* Dinv32, int level,
+                       const std::function<void(const float*, float*)>& apply);
 double power_result(cudaStream_t s, const PowerState& ps);
 // P = T - omega Dinv (A T) on the pattern of AT
 void amg_smooth_prolongator(cudaStream_t s, const Bsr& AT, const double* ATV, const int* agg,

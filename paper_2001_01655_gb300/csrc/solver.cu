@@ -820,7 +820,6 @@ void setup(tomg_problem* P, const tomg_options& opt) {
   SetupTrace tr(s);
   // side-stream power iterations (declared before the join guard, released after it)
   std::vector<PowerState> cheb_pw;
-  DBuf<float> pw32a, pw32b;  // FP32 operands of those estimates (mixed precision)
   StreamJoin side_join;
   P->L.clear();
   P->jacobi_only = (opt.pc == TOMG_PC_JACOBI);
@@ -916,31 +915,26 @@ void setup(tomg_problem* P, const tomg_options& opt) {
     // before any of the buffers involved is released.
     if (opt.smoother == 1 && n_geo >= 2) {
       ensure_side_streams(P);
+      // with an FP32 V-cycle the estimate runs in FP32 on the cycle's own operator and block
+      // inverses (norms in FP64): the bound only sets the Chebyshev interval, and FP64 vector
+      // work here competes with the FP64-bound algebraic setup on GB300's narrow FP64 pipe
+      const bool f32 = opt.prec != TOMG_PREC_FP64;
       cheb_pw.resize(n_geo - 1);
       for (int l = 0; l + 1 < n_geo; l++)
-        power_alloc(cheb_pw[l], P->L[l]->nn, P->L[l]->b, 20);
-      // with an FP32 V-cycle the operator of the estimate is the cycle's own FP32 operator (the
-      // FP64 iteration vectors and norms stay): the bound only sets the Chebyshev interval, and
-      // on hex8 grids the FP64 fine operator (an assembled 243-entry stencil per node on
-      // GB300's narrow FP64 pipe) made these 20 applies the longest phase of the setup
-      const bool f32 = opt.prec != TOMG_PREC_FP64;
-      if (f32) {
-        pw32a.resize(P->n);
-        pw32b.resize(P->n);
-      }
+        power_alloc(cheb_pw[l], P->L[l]->nn, P->L[l]->b, 20, f32);
       CK(cudaEventRecord(P->ev_fork, s));
       CK(cudaStreamWaitEvent(P->side, P->ev_fork, 0));
       for (int l = 0; l + 1 < n_geo; l++) {
         Level& Lv = *P->L[l];
-        power_enqueue(P->side, cheb_pw[l], Lv.D64.p, l, [&](const double* xv, double* yv) {
-          if (f32) {
-            cast_f64_f32(P->side, xv, pw32a.p, Lv.n);
-            level_op<float>(P, P->side, l, MODE_APPLY, pw32a.p, pw32b.p, nullptr, nullptr);
-            cast_f32_f64(P->side, pw32b.p, yv, Lv.n);
-          } else {
+        if (f32) {
+          power_enqueue_f32(P->side, cheb_pw[l], Lv.D32.p, l, [&](const float* xv, float* yv) {
+            level_op<float>(P, P->side, l, MODE_APPLY, xv, yv, nullptr, nullptr);
+          });
+        } else {
+          power_enqueue(P->side, cheb_pw[l], Lv.D64.p, l, [&](const double* xv, double* yv) {
             level_op<double>(P, P->side, l, MODE_APPLY, xv, yv, nullptr, nullptr);
-          }
-        });
+          });
+        }
       }
       CK(cudaEventRecord(P->ev_side, P->side));
       side_join.arm(s, P->ev_side);
