@@ -283,6 +283,16 @@ tomg_status tomg_time_fine_operator(tomg_problem* prob, int op, int prec, int re
  * tomg_solve of the problem reports TOMG_E_TIMEOUT and clears the record.  polls <= 0 restores
  * normal launches.  No fault is involved.  Process-wide, not thread-safe; for tests only. */
 tomg_status tomg_debug_tc_wait_limit(int polls);
+/* Test hook of the failure path of the grid barriers in the two single-launch (cooperative)
+ * kernels of the setup: the MIS-2 rounds of the aggregation and the coarsest level's Cholesky
+ * factorisation and inverse (Sec. 3.2).  With polls > 0, launches made after this call give up
+ * a barrier wait at its `polls`-th poll (default 2^24 polls; polls = 1 gives up at once,
+ * without looking at the barrier, so with more than one block the wait always runs out); the
+ * block that gives up records it, every other block leaves at its next wait, and the
+ * tomg_setup in progress reports TOMG_E_TIMEOUT.
+ * polls <= 0 restores the defaults.  No fault is involved.  Process-wide, not thread-safe; for
+ * tests only. */
+tomg_status tomg_debug_grid_wait_limit(int polls);
 /* Allocation-free y = A_0 x with FP32 arithmetic: the same computation as
  * tomg_level_apply(prob, 0, TOMG_PREC_FP32_VCYCLE, x, y, 1), for callers that must not
  * allocate device memory where they apply the operator (memory owned by another allocator,

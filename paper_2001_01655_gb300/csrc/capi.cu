@@ -627,3 +627,8 @@ extern "C" tomg_status tomg_debug_tc_wait_limit(int polls) {
   tomg::ebe3d_tc_set_wait_limit(polls);
   return TOMG_OK;
 }
+
+extern "C" tomg_status tomg_debug_grid_wait_limit(int polls) {
+  tomg::set_grid_wait_limit(polls);
+  return TOMG_OK;
+}

@@ -83,14 +83,15 @@ __global__ void k_strength(int nbr, int b, const int* __restrict__ rp, const int
 //   sync[4] error, sync[5] rounds run
 constexpr unsigned MIS_WAIT_LIMIT = 1u << 24;
 
-__device__ __forceinline__ bool grid_barrier(unsigned* sync, unsigned nblocks) {
-  return grid_sync(sync, sync + 4, nblocks, MIS_WAIT_LIMIT);
-}
+int g_grid_wait_polls = 0;  // test hook: > 0 replaces the grid barriers' wait limits
 
 __global__ void __launch_bounds__(256) k_mis2_loop(int n, int level, const int* __restrict__ srp,
                                                    const int* __restrict__ sci, int* state,
                                                    uint64_t* v, uint64_t* m1, unsigned* sync,
-                                                   int max_rounds) {
+                                                   int max_rounds, unsigned wait_limit) {
+  auto grid_barrier = [&](unsigned* sy, unsigned nblocks) {
+    return grid_sync(sy, sy + 4, nblocks, wait_limit);
+  };
   __shared__ unsigned red[8];
   const int stride = gridDim.x * blockDim.x;
   const int t0 = blockIdx.x * blockDim.x + threadIdx.x;
@@ -500,6 +501,11 @@ void amg_strength_fill(cudaStream_t s, const Bsr& A, const double* V, double bet
   CK(cudaStreamSynchronize(s));
 }
 
+void set_grid_wait_limit(int polls) { g_grid_wait_polls = polls; }
+unsigned grid_wait_limit(unsigned dflt) {  // polls = 1: the kernels' limit 0, give up at once
+  return g_grid_wait_polls > 0 ? (unsigned)(g_grid_wait_polls - 1) : dflt;
+}
+
 int amg_mis2(cudaStream_t s, int n, const int* srp, const int* sci, int level, int* state,
              uint64_t* v, uint64_t* m1, int* flag_host, int* flag_dev) {
   (void)flag_dev;
@@ -523,7 +529,7 @@ int amg_mis2(cudaStream_t s, int n, const int* srp, const int* sci, int level, i
   cfg.attrs = at;
   cfg.numAttrs = 1;
   CK(cudaLaunchKernelEx(&cfg, k_mis2_loop, n, level, srp, sci, state, v, m1, sync.p,
-                        MAX_ROUNDS));
+                        MAX_ROUNDS, grid_wait_limit(MIS_WAIT_LIMIT)));
   g_launches++;
   unsigned h[6];
   CK(cudaMemcpyAsync(h, sync.p, sizeof(h), cudaMemcpyDeviceToHost, s));

@@ -369,7 +369,8 @@ __device__ void potrf_tile(int n, int k0, const double* A, InvSmem& m, int* fail
 }
 
 __global__ void __launch_bounds__(INV_THREADS) k_spd_inverse(int n, double* A, double* Y,
-                                                             int* fail, unsigned* sync) {
+                                                             int* fail, unsigned* sync,
+                                                             unsigned wait_limit) {
   __shared__ InvSmem m;
   const int t = threadIdx.x, tx = t & 31, ty = t >> 5;
   const int G = gridDim.x, bid = blockIdx.x;
@@ -425,7 +426,7 @@ __global__ void __launch_bounds__(INV_THREADS) k_spd_inverse(int n, double* A, d
         }
       }
     }
-    if (!grid_sync(sync, sync + 2, G, INV_WAIT_LIMIT)) return;
+    if (!grid_sync(sync, sync + 2, G, wait_limit)) return;
     // ---- phase 2: X_b = L_bb^-1 B_b, the trailing update
     const int n_x = b + 1;  // tiles j <= b of block row b
     const int nt = (rest + 31) / 32;
@@ -467,7 +468,7 @@ __global__ void __launch_bounds__(INV_THREADS) k_spd_inverse(int n, double* A, d
         }
       }
     }
-    if (!grid_sync(sync, sync + 2, G, INV_WAIT_LIMIT)) return;
+    if (!grid_sync(sync, sync + 2, G, wait_limit)) return;
   }
 
   // ---- A^-1 = Y^T Y: entry (i, j), j <= i, sums Y_ti Y_tj over t = i .. n - 1 in order.
@@ -635,7 +636,8 @@ int dense_spd_inverse(cudaStream_t s, int n, double* A, double* work) {
   at[0].val.cooperative = 1;
   cfg.attrs = at;
   cfg.numAttrs = 1;
-  CK(cudaLaunchKernelEx(&cfg, k_spd_inverse, n, A, work, fail.p, sync.p));
+  CK(cudaLaunchKernelEx(&cfg, k_spd_inverse, n, A, work, fail.p, sync.p,
+                        grid_wait_limit(INV_WAIT_LIMIT)));
   g_launches++;
   int f = 0;
   unsigned err = 0;

@@ -103,6 +103,10 @@ bool ebe3x_error(cudaStream_t s);  // a wait of the FP64 tensor-core kernel ran 
 // polls of the tensor-core kernel's in-loop MMA waits in later launches (0 = the default);
 // a test shortens it to make the waits run out and exercise the error path
 void ebe3d_tc_set_wait_limit(int polls);
+// polls of the grid barriers of the cooperative kernels (MIS-2 rounds, coarse inverse) in later
+// launches (0 = each kernel's default); a test shortens it to make the waits run out
+void set_grid_wait_limit(int polls);
+unsigned grid_wait_limit(unsigned dflt);
 // element stiffness of the unit quad4 / hex8 element for a constitutive matrix D (3x3 / 6x6,
 // row-major), 2x2(x2) Gauss rule
 void element_stiffness_D(int dim, const double* D, std::vector<double>& Ke);

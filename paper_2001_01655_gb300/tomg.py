@@ -104,6 +104,7 @@ _SIGS = {
                                     C.POINTER(C.c_size_t)]),
     "tomg_server_retire": (C.c_int, [_P, _P, C.c_int]),
     "tomg_debug_tc_wait_limit": (C.c_int, [C.c_int]),
+    "tomg_debug_grid_wait_limit": (C.c_int, [C.c_int]),
     "tomg_server_destroy": (C.c_int, [_P]),
 }
 
@@ -501,6 +502,12 @@ class Problem:
 def debug_tc_wait_limit(polls: int):
     """Shorten the tensor-core kernel's MMA waits (tomg_debug_tc_wait_limit; 0 = default)."""
     _check(load().tomg_debug_tc_wait_limit(int(polls)))
+
+
+def debug_grid_wait_limit(polls: int):
+    """Shorten the grid-barrier waits of the cooperative setup kernels
+    (tomg_debug_grid_wait_limit; 0 = default)."""
+    _check(load().tomg_debug_grid_wait_limit(int(polls)))
 
 
 class Server:

@@ -202,6 +202,34 @@ def test_coarse_inverse_many_blocks(lib, ctx, dim, grid):
         assert relerr(P.coarse_solve(bc), np.linalg.solve(Ac, bc)) < 1e-9
 
 
+@pytest.mark.gpu
+@pytest.mark.parametrize("pc,kw", [("gmg", dict(n_levels=2)), ("amg", dict(max_coarse_dofs=300))])
+def test_grid_barrier_timeout_path(lib, ctx, pc, kw):
+    """The bounded waits of the setup's single-launch kernels, run out on purpose without a
+    fault: the coarsest level's Cholesky factorisation and inverse (Sec. 3.2; both hierarchies)
+    and the MIS-2 rounds of the aggregation (AMG).  With tomg_debug_grid_wait_limit(1) a block
+    gives up its grid-barrier wait after a poll, every other block leaves at its next wait, and
+    the setup reports TOMG_E_TIMEOUT.  With the hook cleared, a setup gives the coarse solve of
+    before, bit for bit."""
+    p = W.random_problem(2, 64, 32, seed=21, contrast="minmax")
+    p.rho[:] = 0.5 + 0.5 * p.rho
+    P = make(lib, ctx, p)
+    P.setup(pc=pc, prec="fp64", **kw)
+    nc = P.level_info(P.num_levels() - 1)["n_dofs"]
+    assert nc > 32  # more than one block of the coarse inverse
+    bc = np.random.default_rng(4).standard_normal(nc)
+    x_ref = P.coarse_solve(bc)
+    lib.debug_grid_wait_limit(1)
+    try:
+        with pytest.raises(lib.TomgError) as ei:
+            P.setup(pc=pc, prec="fp64", **kw)
+        assert ei.value.status == lib.E_TIMEOUT, ei.value
+    finally:
+        lib.debug_grid_wait_limit(0)
+    P.setup(pc=pc, prec="fp64", **kw)
+    assert np.array_equal(P.coarse_solve(bc), x_ref)
+
+
 @pytest.mark.parametrize("dim,grid", [(2, (30, 14, 1)), (2, (45, 21, 1)), (3, (8, 6, 5))])
 def test_amg_setup_parity(lib, ctx, dim, grid):
     p = W.random_problem(dim, *grid, seed=14, contrast="threshold")
